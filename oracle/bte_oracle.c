@@ -1,0 +1,494 @@
+/*
+ * bte_oracle.c -- plain FP64 CPU oracle for the phonon BTE hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library and
+ * its Python binding) may link, load or call this file.  Only the test suite,
+ * the smoke check and the benchmark's CPU-baseline leg use it.  It shares no
+ * source, header, table or constant with the CUDA path.
+ *
+ * It follows the method of arXiv:2305.19400 Sec. 3.1 literally:
+ *   Eq. 4  BTE under the relaxation-time approximation,
+ *   Eq. 5  finite-volume form with the surface upwind flux -|v|_b * sum I s.n A,
+ *   Eq. 3  cell update u = u0 + dt (s(u0) - (1/V) sum_i A_i f(u0)) (explicit),
+ *   Eq. 6  ghost intensity at walls: I0_b (isothermal) or I_{r,b} (symmetry),
+ * and, for the temperature step the paper defers to its references, this
+ * reading: a per-cell reduction G_b = sum_d w_d I,
+ * a Newton solve of sum_b W beta_b I0_b(T)/v_b = sum_b beta_b G_b / v_b for the
+ * pseudo-temperature T_p that sets I0, and of sum_b W I0_b(T)/v_b = sum_b G_b/v_b
+ * for the lattice (energy) temperature T_L, with W = sum_d w_d.
+ *
+ * Everything is a plain loop in the order cell -> direction -> band (the
+ * paper's default loop nest, Sec. 3.3), FP64, no blocking, no fusion.
+ * OpenMP only splits the independent per-cell loops.
+ *
+ * Parity status: every function here is pinned by the CPU tests (quadrature
+ * exactness and an independent adaptive integral, direction-set moments,
+ * Newton against bracketing, Jacobi against a dense LU solve, hand-computed
+ * steps, equilibrium, energy conservation, Casimir and Fourier limits,
+ * relabelling symmetry).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* CODATA 2018 exact/recommended values. */
+static const double ORC_HBAR = 1.054571817e-34; /* J s */
+static const double ORC_KB = 1.380649e-23;      /* J/K */
+static const double ORC_PI = 3.14159265358979323846;
+
+enum { ORC_ISOTHERMAL = 0, ORC_SPECULAR = 1 };
+enum { ORC_IMPLICIT = 0, ORC_EXPLICIT = 1 };
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Legendre nodes and weights on [-1, 1] (textbook: Newton iteration on  */
+/* the Legendre polynomial P_n from the three-term recurrence).                */
+/* ------------------------------------------------------------------------ */
+int orc_gauss_legendre(int n, double* x, double* w) {
+  if (n < 1 || n > 512) return -1;
+  for (int i = 0; i < n; ++i) {
+    long double z = cosl(3.14159265358979323846264338327950288L * (i + 0.75L) / (n + 0.5L));
+    long double dp = 0.0L;
+    for (int it = 0; it < 100; ++it) {
+      long double p0 = 1.0L, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      /* P_n = p1, P_{n-1} = p0; derivative from (1 - z^2) P_n' = n (P_{n-1} - z P_n) */
+      dp = n * (p0 - z * p1) / (1.0L - z * z);
+      long double dz = p1 / dp;
+      z -= dz;
+      if (fabsl(dz) < 1e-30L) break;
+    }
+    /* recompute the derivative at the converged node */
+    long double p0 = 1.0L, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (p0 - z * p1) / (1.0L - z * z);
+    x[i] = (double)(-z); /* ascending order */
+    w[i] = (double)(2.0L / ((1.0L - z * z) * dp * dp));
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Band equilibrium intensity (Debye-type band, Bose-Einstein occupation):    */
+/*   I0_b(T) = g_b hbar / (8 pi^3 v_b^2) * int_{lo}^{hi} w^3 / (exp(hbar w / kB T) - 1) dw */
+/* by n_gauss-point Gauss-Legendre on each band interval; dI0_b/dT from the    */
+/* same nodes: d/dT [1/(e^x - 1)] = n (1 + n) x / T with x = hbar w/(kB T).    */
+/* ------------------------------------------------------------------------ */
+void orc_I0(int nb, const double* wlo, const double* whi, const double* vg, const double* g, int ngauss,
+            const double* xg, const double* wg, double T, double* I0, double* dI0) {
+  for (int b = 0; b < nb; ++b) {
+    double half = 0.5 * (whi[b] - wlo[b]);
+    double mid = 0.5 * (whi[b] + wlo[b]);
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = 0; i < ngauss; ++i) {
+      double om = mid + half * xg[i];
+      double x = ORC_HBAR * om / (ORC_KB * T);
+      double n = 1.0 / expm1(x);
+      s0 += wg[i] * om * om * om * n;
+      s1 += wg[i] * om * om * om * n * (1.0 + n) * x / T;
+    }
+    double pref = g[b] * ORC_HBAR / (8.0 * ORC_PI * ORC_PI * ORC_PI * vg[b] * vg[b]) * half;
+    I0[b] = pref * s0;
+    if (dI0) dI0[b] = pref * s1;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Discrete direction sets (Sec. 3.1: 20 directions in 2-D, 20 x 20 = 400 in   */
+/* 3-D).  S_d is the control-angle integral of the unit vector s, w_d the      */
+/* solid angle; rx/ry/rz give the mirror direction across an x/y/z wall (the   */
+/* index r of Eq. 6).                                                          */
+/* ------------------------------------------------------------------------ */
+int orc_dirs_inplane(int n, double* S, double* w, int* rx, int* ry, int* rz) {
+  if (n < 4 || n % 4) return -1;
+  for (int d = 0; d < n; ++d) {
+    double phi = (d + 0.5) * 2.0 * ORC_PI / n;
+    w[d] = 4.0 * ORC_PI / n;
+    S[3 * d + 0] = w[d] * cos(phi);
+    S[3 * d + 1] = w[d] * sin(phi);
+    S[3 * d + 2] = 0.0;
+    rx[d] = ((n / 2 - 1 - d) % n + n) % n; /* phi -> pi - phi */
+    ry[d] = n - 1 - d;                      /* phi -> -phi     */
+    rz[d] = d;                              /* no z component  */
+  }
+  return 0;
+}
+
+int orc_dirs_polar_azim(int ntheta, int nphi, double* S, double* w, int* rx, int* ry, int* rz) {
+  if (ntheta < 2 || ntheta % 2 || nphi < 4 || nphi % 4) return -1;
+  double dth = ORC_PI / ntheta, dph = 2.0 * ORC_PI / nphi;
+  for (int i = 0; i < ntheta; ++i) {
+    double t1 = i * dth, t2 = (i + 1) * dth;
+    double J = 0.5 * (t2 - t1) - 0.25 * (sin(2.0 * t2) - sin(2.0 * t1)); /* int sin^2 */
+    for (int j = 0; j < nphi; ++j) {
+      double p1 = j * dph, p2 = (j + 1) * dph;
+      int d = i * nphi + j;
+      w[d] = dph * (cos(t1) - cos(t2));
+      S[3 * d + 0] = J * (sin(p2) - sin(p1));
+      S[3 * d + 1] = J * (cos(p1) - cos(p2));
+      S[3 * d + 2] = dph * 0.5 * (sin(t2) * sin(t2) - sin(t1) * sin(t1));
+      rx[d] = i * nphi + ((nphi / 2 - 1 - j) % nphi + nphi) % nphi; /* phi -> pi - phi  */
+      ry[d] = i * nphi + (nphi - 1 - j);                            /* phi -> -phi      */
+      rz[d] = (ntheta - 1 - i) * nphi + j;                          /* theta -> pi - theta */
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Problem description.                                                       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int dim, nx, ny, nz;
+  double dx, dy, dz;
+  int nd;
+  const double* S; /* [nd][3] */
+  const double* w; /* [nd] */
+  const int* rx;
+  const int* ry;
+  const int* rz;
+  int nb;
+  const double* wlo;
+  const double* whi;
+  const double* vg;
+  const double* beta; /* 1/tau */
+  const double* g;
+  int ngauss;
+  const double* glx; /* Gauss-Legendre nodes on [-1,1] (from orc_gauss_legendre) */
+  const double* glw;
+  int bc_type[6];
+  const double* bc_T[6]; /* per face temperatures on isothermal sides */
+  int newton_maxit;
+  double newton_rtol;
+} orc_problem;
+
+static long ncells(const orc_problem* p) { return (long)p->nx * p->ny * p->nz; }
+
+static long nfaces(const orc_problem* p, int side) {
+  if (side < 2) return (long)p->ny * p->nz;
+  if (side < 4) return (long)p->nx * p->nz;
+  return (long)p->nx * p->ny;
+}
+
+/* face index of cell (i,j,k) on a side: x sides j + ny k, y sides i + nx k, z sides i + nx j */
+static long face_index(const orc_problem* p, int side, int i, int j, int k) {
+  if (side < 2) return j + (long)p->ny * k;
+  if (side < 4) return i + (long)p->nx * k;
+  return i + (long)p->nx * j;
+}
+
+/* I0 of every wall face (isothermal sides) at its wall temperature.  Layout:
+ * for side s in 0..5, nfaces(s) rows of nb values, concatenated. */
+static double* wall_I0(const orc_problem* p) {
+  long tot = 0;
+  for (int s = 0; s < 2 * p->dim; ++s) tot += nfaces(p, s);
+  double* out = (double*)calloc((size_t)tot * p->nb + 1, sizeof(double));
+  long off = 0;
+  for (int s = 0; s < 2 * p->dim; ++s) {
+    long nf = nfaces(p, s);
+    if (p->bc_type[s] == ORC_ISOTHERMAL)
+      for (long f = 0; f < nf; ++f) orc_I0(p->nb, p->wlo, p->whi, p->vg, p->g, p->ngauss, p->glx, p->glw, p->bc_T[s][f], out + (off + f) * p->nb, NULL);
+    off += nf;
+  }
+  return out;
+}
+
+static long wall_offset(const orc_problem* p, int side) {
+  long off = 0;
+  for (int s = 0; s < side; ++s) off += nfaces(p, s);
+  return off;
+}
+
+/* Upwind value along one axis for (cell P = (i,j,k), direction d, band b):
+ * the neighbour on the side the direction comes from, or the ghost of Eq. 6
+ * when that side is a wall.  `Isrc` is the field the upwind value is read from. */
+static double upwind_value(const orc_problem* p, const double* Isrc, const double* I0wall, int ax, int i, int j, int k,
+                           int d, int b) {
+  int nd = p->nd, nb = p->nb;
+  int c[3] = {i, j, k};
+  int n[3] = {p->nx, p->ny, p->nz};
+  double s = p->S[3 * d + ax];
+  int side, q = c[ax];
+  if (s > 0) { /* comes from the low side */
+    if (q > 0) { c[ax] = q - 1; return Isrc[(((long)c[2] * p->ny + c[1]) * p->nx + c[0]) * nd * nb + (long)d * nb + b]; }
+    side = 2 * ax;
+  } else { /* comes from the high side */
+    if (q < n[ax] - 1) { c[ax] = q + 1; return Isrc[(((long)c[2] * p->ny + c[1]) * p->nx + c[0]) * nd * nb + (long)d * nb + b]; }
+    side = 2 * ax + 1;
+  }
+  if (p->bc_type[side] == ORC_ISOTHERMAL) {
+    long f = wall_offset(p, side) + face_index(p, side, i, j, k);
+    return I0wall[f * nb + b];
+  }
+  /* symmetry: the reflected direction of the same cell */
+  const int* r = ax == 0 ? p->rx : (ax == 1 ? p->ry : p->rz);
+  long P = ((long)k * p->ny + j) * p->nx + i;
+  return Isrc[P * nd * nb + (long)r[d] * nb + b];
+}
+
+/* One intensity update for (P, d, b).
+ * Implicit (backward Euler, one point-Jacobi sweep of the inner iteration):
+ *   I^{k+1} = [I^n/dt + beta I0^k + v sum_ax c_ax I_up^k] / [1/dt + beta + v sum_ax c_ax],
+ *   c_ax = |S_{d,ax}| / (w_d Delta_ax)  (outflow faces use the cell's own value).
+ * Explicit (forward Euler, Eq. 3 with Eq. 5):
+ *   I^{n+1} = I^n + dt [ beta (I0^n - I^n) - v sum_ax c_ax (I^n - I_up^n) ]. */
+double orc_update_one(const orc_problem* p, double dt, int scheme, const double* In, const double* Ik, const double* I0,
+                      const double* I0wall, long P, int d, int b) {
+  int nd = p->nd, nb = p->nb;
+  int i = (int)(P % p->nx), j = (int)((P / p->nx) % p->ny), k = (int)(P / ((long)p->nx * p->ny));
+  double delta[3] = {p->dx, p->dy, p->dz};
+  double beta = p->beta[b], v = p->vg[b];
+  double in = In[P * nd * nb + (long)d * nb + b];
+  double i0 = I0[P * nb + b];
+  if (scheme == ORC_EXPLICIT) {
+    double flux = 0.0;
+    for (int ax = 0; ax < p->dim; ++ax) {
+      double s = p->S[3 * d + ax];
+      if (s == 0.0) continue;
+      double c = fabs(s) / (p->w[d] * delta[ax]);
+      flux += c * (in - upwind_value(p, In, I0wall, ax, i, j, k, d, b));
+    }
+    return in + dt * (beta * (i0 - in) - v * flux);
+  }
+  double num = in / dt + beta * i0, den = 1.0 / dt + beta;
+  for (int ax = 0; ax < p->dim; ++ax) {
+    double s = p->S[3 * d + ax];
+    if (s == 0.0) continue;
+    double c = fabs(s) / (p->w[d] * delta[ax]);
+    num += v * c * upwind_value(p, Ik, I0wall, ax, i, j, k, d, b);
+    den += v * c;
+  }
+  return num / den;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Temperature from an energy: solve sum_b a_b I0_b(T) = E by Newton from a     */
+/* guess, stop when |dT| <= rtol T; bisection on [1, 5000] K as the fallback.  */
+/* a_b = W/v_b gives T_L (energy), a_b = W beta_b / v_b gives T_p.             */
+/* Returns 0 (Newton), 1 (bisection fallback), -1 (no root in [1, 5000]).      */
+/* ------------------------------------------------------------------------ */
+int orc_solve_T(const orc_problem* p, const double* a, double E, double Tguess, double* Tout) {
+  int nb = p->nb;
+  double* I0 = (double*)malloc(sizeof(double) * 2 * nb);
+  double* dI0 = I0 + nb;
+  double T = Tguess;
+  int ok = 0;
+  if (T >= 1.0 && T <= 5000.0 && isfinite(T)) {
+    for (int it = 0; it < p->newton_maxit; ++it) {
+      orc_I0(nb, p->wlo, p->whi, p->vg, p->g, p->ngauss, p->glx, p->glw, T, I0, dI0);
+      double F = -E, dF = 0.0;
+      for (int b = 0; b < nb; ++b) { F += a[b] * I0[b]; dF += a[b] * dI0[b]; }
+      double dT = -F / dF;
+      T += dT;
+      if (!isfinite(T) || T < 1.0 || T > 5000.0) break;
+      if (fabs(dT) <= p->newton_rtol * T) { ok = 1; break; }
+    }
+  }
+  int status = 0;
+  if (!ok) {
+    double lo = 1.0, hi = 5000.0, flo, fhi;
+    orc_I0(nb, p->wlo, p->whi, p->vg, p->g, p->ngauss, p->glx, p->glw, lo, I0, NULL);
+    flo = -E; for (int b = 0; b < nb; ++b) flo += a[b] * I0[b];
+    orc_I0(nb, p->wlo, p->whi, p->vg, p->g, p->ngauss, p->glx, p->glw, hi, I0, NULL);
+    fhi = -E; for (int b = 0; b < nb; ++b) fhi += a[b] * I0[b];
+    if (!(flo <= 0.0 && fhi >= 0.0)) { free(I0); *Tout = NAN; return -1; }
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * lo; ++it) {
+      double mid = 0.5 * (lo + hi), f = -E;
+      orc_I0(nb, p->wlo, p->whi, p->vg, p->g, p->ngauss, p->glx, p->glw, mid, I0, NULL);
+      for (int b = 0; b < nb; ++b) f += a[b] * I0[b];
+      if (f < 0.0) lo = mid; else hi = mid;
+    }
+    T = 0.5 * (lo + hi);
+    status = 1;
+  }
+  free(I0);
+  *Tout = T;
+  return status;
+}
+
+/* Per-cell reduction (Sec. 3.2 temperature update): G_b = sum_d w_d I_{d,b},
+ * E_L = sum_b G_b / v_b, E_p = sum_b beta_b G_b / v_b.  `row` is one cell's [nd][nb]. */
+void orc_cell_energy(const orc_problem* p, const double* row, double* EL, double* Ep) {
+  double eL = 0.0, ep = 0.0;
+  for (int b = 0; b < p->nb; ++b) {
+    double G = 0.0;
+    for (int d = 0; d < p->nd; ++d) G += p->w[d] * row[(long)d * p->nb + b];
+    eL += G / p->vg[b];
+    ep += p->beta[b] * G / p->vg[b];
+  }
+  *EL = eL;
+  *Ep = ep;
+}
+
+static double total_weight(const orc_problem* p) {
+  double W = 0.0;
+  for (int d = 0; d < p->nd; ++d) W += p->w[d];
+  return W;
+}
+
+/* Temperatures of one cell from its intensity row.  With every beta_b = 0 the
+ * T_p equation is empty (I0 never enters the update); T_p is then set to T_L. */
+int orc_cell_temperatures(const orc_problem* p, const double* row, double TpGuess, double TLGuess, double* Tp,
+                          double* TL) {
+  int nb = p->nb;
+  double W = total_weight(p);
+  double* aL = (double*)malloc(sizeof(double) * 2 * nb);
+  double* ap = aL + nb;
+  double bsum = 0.0;
+  for (int b = 0; b < nb; ++b) { aL[b] = W / p->vg[b]; ap[b] = W * p->beta[b] / p->vg[b]; bsum += p->beta[b]; }
+  double EL, Ep;
+  orc_cell_energy(p, row, &EL, &Ep);
+  int fb = 0;
+  int sL = orc_solve_T(p, aL, EL, TLGuess, TL);
+  if (sL < 0) { free(aL); return -1; }
+  fb += sL;
+  if (bsum > 0.0) {
+    int sp = orc_solve_T(p, ap, Ep, TpGuess, Tp);
+    if (sp < 0) { free(aL); return -1; }
+    fb += sp;
+  } else {
+    *Tp = *TL;
+  }
+  free(aL);
+  return fb;
+}
+
+/* Equilibrium initial state (Sec. 3.2: I = I_init[b] for all d at the uniform T). */
+int orc_init_state(const orc_problem* p, const double* Tcells, double* I, double* Tp, double* TL, double* I0) {
+  long nc = ncells(p);
+  int nd = p->nd, nb = p->nb;
+  for (long P = 0; P < nc; ++P) {
+    orc_I0(nb, p->wlo, p->whi, p->vg, p->g, p->ngauss, p->glx, p->glw, Tcells[P], I0 + P * nb, NULL);
+    for (int d = 0; d < nd; ++d)
+      for (int b = 0; b < nb; ++b) I[P * nd * nb + (long)d * nb + b] = I0[P * nb + b];
+    Tp[P] = TL[P] = Tcells[P];
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The time loop.  For each step: I^n = I; for k in 0..ninner-1:                */
+/*   (i) intensity update for every (P, d, b) from I^n, I^k, I0^k (walls: Eq.6) */
+/*   (ii) per-cell reduction, (iii) T_p and T_L by Newton, (iv) I0 = I0(T_p).   */
+/* The explicit scheme takes one pass (ninner = 1) of the forward-Euler update. */
+/* Returns the number of bisection fallbacks, or -1 on an unsolvable cell.     */
+/* ------------------------------------------------------------------------ */
+long orc_run(const orc_problem* p, double dt, int nsteps, int ninner, int scheme, double* I, double* Tp, double* TL,
+             double* I0) {
+  long nc = ncells(p);
+  int nd = p->nd, nb = p->nb;
+  size_t n = (size_t)nc * nd * nb;
+  double* In = (double*)malloc(n * sizeof(double));
+  double* Inew = (double*)malloc(n * sizeof(double));
+  double* I0wall = wall_I0(p);
+  long fallbacks = 0, bad = 0;
+  if (scheme == ORC_EXPLICIT) ninner = 1;
+  for (int step = 0; step < nsteps; ++step) {
+    memcpy(In, I, n * sizeof(double));
+    for (int k = 0; k < ninner; ++k) {
+      const double* Ik = (scheme == ORC_EXPLICIT) ? In : I;
+#pragma omp parallel for schedule(static)
+      for (long P = 0; P < nc; ++P)
+        for (int d = 0; d < nd; ++d)
+          for (int b = 0; b < nb; ++b)
+            Inew[P * nd * nb + (long)d * nb + b] = orc_update_one(p, dt, scheme, In, Ik, I0, I0wall, P, d, b);
+#pragma omp parallel for schedule(static) reduction(+ : fallbacks, bad)
+      for (long P = 0; P < nc; ++P) {
+        int s = orc_cell_temperatures(p, Inew + P * nd * nb, Tp[P], TL[P], &Tp[P], &TL[P]);
+        if (s < 0) bad += 1; else fallbacks += s;
+        orc_I0(nb, p->wlo, p->whi, p->vg, p->g, p->ngauss, p->glx, p->glw, Tp[P], I0 + P * nb, NULL);
+      }
+      memcpy(I, Inew, n * sizeof(double));
+    }
+  }
+  free(In);
+  free(Inew);
+  free(I0wall);
+  return bad ? -1 : fallbacks;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Heat flux.  Cell: q(P) = sum_b sum_d S_d I_{d,b}.  Wall: the mean over the   */
+/* side's faces of sum_b sum_d (S_d . n_out) I_face, with I_face the cell value */
+/* for outgoing directions and the Eq. 6 ghost for incoming ones (positive =    */
+/* energy leaving through that wall).                                         */
+/* ------------------------------------------------------------------------ */
+int orc_flux(const orc_problem* p, const double* I, double* q_cells, double* q_walls) {
+  long nc = ncells(p);
+  int nd = p->nd, nb = p->nb;
+  double* I0wall = wall_I0(p);
+  if (q_cells) {
+#pragma omp parallel for schedule(static)
+    for (long P = 0; P < nc; ++P) {
+      for (int ax = 0; ax < p->dim; ++ax) {
+        double q = 0.0;
+        for (int d = 0; d < nd; ++d)
+          for (int b = 0; b < nb; ++b) q += p->S[3 * d + ax] * I[P * nd * nb + (long)d * nb + b];
+        q_cells[P * p->dim + ax] = q;
+      }
+    }
+  }
+  if (q_walls) {
+    for (int side = 0; side < 2 * p->dim; ++side) {
+      int ax = side / 2;
+      double nsign = (side % 2) ? 1.0 : -1.0;
+      int n[3] = {p->nx, p->ny, p->nz};
+      double acc = 0.0;
+      long cnt = 0;
+      for (int k = 0; k < p->nz; ++k)
+        for (int j = 0; j < p->ny; ++j)
+          for (int i = 0; i < p->nx; ++i) {
+            int c[3] = {i, j, k};
+            if (c[ax] != ((side % 2) ? n[ax] - 1 : 0)) continue;
+            long P = ((long)k * p->ny + j) * p->nx + i;
+            for (int d = 0; d < nd; ++d) {
+              double sn = p->S[3 * d + ax] * nsign;
+              for (int b = 0; b < nb; ++b) {
+                double If;
+                if (sn > 0) If = I[P * nd * nb + (long)d * nb + b];
+                else if (p->bc_type[side] == ORC_ISOTHERMAL)
+                  If = I0wall[(wall_offset(p, side) + face_index(p, side, i, j, k)) * nb + b];
+                else {
+                  const int* r = ax == 0 ? p->rx : (ax == 1 ? p->ry : p->rz);
+                  If = I[P * nd * nb + (long)r[d] * nb + b];
+                }
+                acc += sn * If;
+              }
+            }
+            cnt += 1;
+          }
+      q_walls[side] = acc / (double)cnt;
+    }
+  }
+  free(I0wall);
+  return 0;
+}
+
+/* Every wall face's ghost I0 (isothermal sides; zeros elsewhere), exposed for
+ * the sampled per-element checks. */
+int orc_wall_I0(const orc_problem* p, double* out) {
+  double* w = wall_I0(p);
+  long tot = 0;
+  for (int s = 0; s < 2 * p->dim; ++s) tot += nfaces(p, s);
+  memcpy(out, w, (size_t)tot * p->nb * sizeof(double));
+  free(w);
+  return 0;
+}

@@ -1,0 +1,385 @@
+"""Pins of the FP64 CPU oracle against facts fixed by mathematics and physics.
+
+Each check is chosen so that a plausible slip in the oracle -- a dropped term,
+a wrong sign or index, a transposed operand -- fails at least one of them.
+None of them re-types the oracle's own formula; they use closed forms,
+independent library routines (scipy adaptive quadrature, root bracketing,
+dense LU), hand-worked steps and conservation laws.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize
+
+from oracle import oracle as O
+from paper_2305_19400_gb300 import workloads as W
+
+HBAR = 1.054571817e-34
+KB = 1.380649e-23
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- quadrature
+def test_gauss_legendre_exact_to_degree_31():
+    x, w = O.gauss_legendre(16)
+    assert np.all(np.diff(x) > 0)
+    for k in range(32):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.sum(w * x ** k) - exact) < 1e-14, k
+    # degree 32 is the first one a 16-point rule cannot integrate exactly
+    assert abs(np.sum(w * x ** 32) - 2.0 / 33) > 1e-12
+
+
+def _be_integral(lo, hi, T):
+    f = lambda om: om ** 3 / math.expm1(HBAR * om / (KB * T))
+    val, err = integrate.quad(f, lo, hi, epsabs=0.0, epsrel=1.2e-14, limit=200)
+    return val
+
+
+@pytest.mark.parametrize("T", [250.0, 300.0, 400.0])
+def test_I0_against_adaptive_quadrature(T):
+    bands = W.make_bands(40, 15, 19402)
+    I0, _ = O.I0(bands, T)
+    for b in range(bands.nb):
+        ref = bands.degeneracy[b] * HBAR / (8 * math.pi ** 3 * bands.vg[b] ** 2) * \
+            _be_integral(bands.omega_lo[b], bands.omega_hi[b], T)
+        assert abs(I0[b] - ref) <= 1e-12 * ref, (b, I0[b], ref)
+
+
+def test_I0_wide_bands_against_adaptive_quadrature():
+    bands = W.make_bands(4, 0, 19401)
+    for T in (250.0, 300.0, 400.0):
+        I0, _ = O.I0(bands, T)
+        for b in range(bands.nb):
+            ref = HBAR / (8 * math.pi ** 3 * bands.vg[b] ** 2) * _be_integral(bands.omega_lo[b], bands.omega_hi[b], T)
+            assert abs(I0[b] - ref) <= 1e-10 * ref
+
+
+def test_I0_bands_add_up_to_the_planck_closed_form():
+    """Many narrow bands with v = 1, g = 1 covering [0, 60 kT/hbar] sum to
+    hbar/(8 pi^3) * (kT/hbar)^4 * pi^4/15 (the Bose-Einstein integral)."""
+    T = 300.0
+    top = 60.0 * KB * T / HBAR
+    n = 300
+    edges = np.linspace(0.0, top, n + 1)
+    bands = W.Bands(edges[:-1], edges[1:], np.ones(n), np.ones(n), np.ones(n))
+    I0, _ = O.I0(bands, T)
+    exact = HBAR / (8 * math.pi ** 3) * (KB * T / HBAR) ** 4 * math.pi ** 4 / 15.0
+    assert abs(I0.sum() - exact) <= 1e-13 * exact
+
+
+def test_dI0_dT_against_central_difference():
+    bands = W.make_bands(40, 15, 19402)
+    T, h = 300.0, 1e-3
+    _, d = O.I0(bands, T)
+    up, _ = O.I0(bands, T + h)
+    dn, _ = O.I0(bands, T - h)
+    fd = (up - dn) / (2 * h)
+    assert np.all(np.abs(d - fd) <= 1e-7 * np.abs(fd))
+
+
+# ------------------------------------------------------------ direction sets
+@pytest.mark.parametrize("kind", ["inplane16", "inplane20", "pa20x20", "pa4x8"])
+def test_direction_set_moments_and_reflections(kind):
+    if kind.startswith("inplane"):
+        n = int(kind[7:])
+        S, w, r = O.dirs_inplane(n)
+        half = (4 * math.pi / n) / math.sin(math.pi / n)    # sum over S_x > 0 of S_x, closed form
+    else:
+        nt, nph = map(int, kind[2:].split("x"))
+        S, w, r = O.dirs_polar_azim(nt, nph)
+        half = math.pi                                       # int_{s_x>0} s_x dOmega
+        # z half-range moment is pi as well, and the z-reflection flips S_z
+        assert abs(S[S[:, 2] > 0, 2].sum() - math.pi) < 1e-13
+    assert abs(w.sum() - 4 * math.pi) < 1e-13
+    assert np.all(np.abs(S.sum(axis=0)) < 1e-13)
+    assert abs(S[S[:, 0] > 0, 0].sum() - half) < 1e-13
+    assert abs(S[S[:, 1] > 0, 1].sum() - half) < 1e-13
+    nd = len(w)
+    for ax in range(3):
+        rr = r[ax]
+        assert np.array_equal(rr[rr], np.arange(nd))                  # involution
+        assert np.allclose(w[rr], w, rtol=1e-13, atol=0)               # weights kept (to rounding)
+        assert np.allclose(S[rr, ax], -S[:, ax], atol=1e-14)          # normal part flips
+        other = [a for a in range(3) if a != ax]
+        assert np.allclose(S[rr][:, other], S[:, other], atol=1e-14)   # tangential part kept
+    # no direction lies in a wall plane (upwind side always defined)
+    assert np.all(S[:, 0] != 0) and np.all(S[:, 1] != 0)
+
+
+# ---------------------------------------------------------------- Newton
+def test_newton_matches_bracketing_root():
+    wl = W.cfg2(4, 4)
+    p = O.Problem(wl.geoms[0], O.dirs_for(wl.dirs), wl.bands)
+    Wt = 4 * math.pi
+    a = Wt * wl.bands.beta / wl.bands.vg
+    for Ttrue in (251.3, 300.0, 333.3, 399.9):
+        I0, _ = O.I0(wl.bands, Ttrue)
+        E = float(np.dot(a, I0))
+        f = lambda T: float(np.dot(a, O.I0(wl.bands, T)[0])) - E
+        ref = optimize.brentq(f, 200.0, 500.0, xtol=1e-13, rtol=4 * np.finfo(float).eps, maxiter=500)
+        for guess in (300.0, 250.0, 4999.0, 1.5):
+            T, status = p.solve_T(a, E, guess)
+            assert status in (0, 1)
+            assert abs(T - ref) <= 1e-12 * ref, (Ttrue, guess, T, ref)
+            assert abs(T - Ttrue) <= 1e-12 * Ttrue
+    # an energy with no temperature in [1, 5000] K is reported, not invented
+    T, status = p.solve_T(a, -1.0, 300.0)
+    assert status == -1
+
+
+def test_energy_is_monotone_so_the_root_is_unique():
+    bands = W.make_bands(40, 15, 19402)
+    a = 4 * math.pi / bands.vg
+    Ts = np.linspace(5.0, 4000.0, 400)
+    E = np.array([np.dot(a, O.I0(bands, T)[0]) for T in Ts])
+    assert np.all(np.diff(E) > 0)
+
+
+# ------------------------------------------------------ hand-worked update
+def _two_cell_problem(dt, v, beta, T_hot, T_cold):
+    g = W.Geometry(2, 2, 1, 1, 10e-9, 10e-9, 10e-9)
+    g.bc = [(W.BC_ISOTHERMAL, np.array([T_hot])), (W.BC_ISOTHERMAL, np.array([T_cold])),
+            (W.BC_SPECULAR, None), (W.BC_SPECULAR, None)]
+    S = np.array([[2 * math.pi, 0, 0], [-2 * math.pi, 0, 0]])
+    w = np.array([2 * math.pi, 2 * math.pi])
+    r = np.array([[1, 0], [0, 1], [0, 1]], dtype=np.int32)
+    bands = W.Bands(np.array([0.0]), np.array([5e13]), np.array([v]), np.array([beta]), np.array([1.0]))
+    return O.Problem(g, (S, w, r), bands), bands
+
+
+def test_two_cell_step_by_hand():
+    gold = json.load(open(os.path.join(GOLDEN, "two_cell_step.json")))
+    Th, Tc, dt = gold["T_hot"], gold["T_cold"], gold["dt_imp"]
+    dx = 10e-9
+    # v c = v |S_x| / (w dx) = v / dx = 2/dt ; beta = 1/dt
+    v = 2.0 / dt * dx
+    p, bands = _two_cell_problem(dt, v, 1.0 / dt, Th, Tc)
+    A = O.I0(bands, Tc)[0][0]
+    B = O.I0(bands, Th)[0][0]
+    st = p.init_state(Tc)
+    I0w = p.wall_I0()
+    for key, (ca, cb) in gold["expected_implicit_in_units_of_A_B"].items():
+        P, d = int(key[1]), int(key[3])
+        got = p.update_one(dt, O.IMPLICIT, st["I"], st["I"], st["I0"], I0w, P, d, 0)
+        assert abs(got - (ca * A + cb * B)) <= 1e-14 * A, key
+    # explicit: beta = 0 and dt * v * c = 1/2
+    p2, _ = _two_cell_problem(dt, v, 0.0, Th, Tc)
+    dt_e = 0.5 / (v / dx)
+    st2 = p2.init_state(Tc)
+    I0w2 = p2.wall_I0()
+    for key, (ca, cb) in gold["expected_explicit_in_units_of_A_B"].items():
+        P, d = int(key[1]), int(key[3])
+        got = p2.update_one(dt_e, O.EXPLICIT, st2["I"], st2["I"], st2["I0"], I0w2, P, d, 0)
+        assert abs(got - (ca * A + cb * B)) <= 1e-14 * A, key
+
+
+# ------------------------------------------------------ Jacobi vs dense LU
+def _assemble_backward_euler(geom, S, w, r, bands, dt, In, I0wall_by_side):
+    """Dense system of one backward-Euler step with beta = 0, written from Eq. 5/6:
+    (1/dt) I_P + v sum_faces (s.n A/V) I_face = (1/dt) I^n_P, I_face upwind."""
+    nx, ny = geom.nx, geom.ny
+    nd, nb = len(w), len(bands.vg)
+    N = nx * ny * nd * nb
+    idx = lambda i, j, d, b: ((j * nx + i) * nd + d) * nb + b
+    A = np.zeros((N, N))
+    rhs = np.zeros(N)
+    delta = (geom.dx, geom.dy)
+    for j in range(ny):
+        for i in range(nx):
+            for d in range(nd):
+                sdir = S[d] / w[d]
+                for b in range(nb):
+                    row = idx(i, j, d, b)
+                    v = bands.vg[b]
+                    A[row, row] += 1.0 / dt
+                    rhs[row] += In[(j * nx + i), d, b] / dt
+                    for ax, (lo_side, hi_side) in enumerate(((0, 1), (2, 3))):
+                        # two faces along this axis: low (n = -e) and high (n = +e)
+                        for side, nsgn in ((lo_side, -1.0), (hi_side, +1.0)):
+                            sn = sdir[ax] * nsgn
+                            coef = v * sn / delta[ax]
+                            if sn > 0:            # outflow through this face: own value
+                                A[row, row] += coef
+                                continue
+                            ci = [i, j]
+                            ci[ax] += int(nsgn)
+                            inside = 0 <= ci[0] < nx and 0 <= ci[1] < ny
+                            if inside:
+                                A[row, idx(ci[0], ci[1], d, b)] += coef
+                            elif geom.bc[side][0] == W.BC_ISOTHERMAL:
+                                rhs[row] -= coef * I0wall_by_side[side][b]
+                            else:
+                                A[row, idx(i, j, r[ax][d], b)] += coef
+    return A, rhs
+
+
+def test_jacobi_iterations_converge_to_dense_lu_solution():
+    g = W.Geometry(2, 4, 3, 1, 10e-9, 7e-9, 10e-9)
+    g.bc = [(W.BC_ISOTHERMAL, np.full(3, 310.0)), (W.BC_ISOTHERMAL, np.full(3, 300.0)),
+            (W.BC_SPECULAR, None), (W.BC_SPECULAR, None)]
+    S, w, r = O.dirs_inplane(8)
+    bands = W.make_bands(2, 0, 7)
+    bands.beta[:] = 0.0
+    p = O.Problem(g, (S, w, r), bands)
+    T0 = W.random_temperatures(12, 99, 295.0, 305.0)
+    st = p.init_state(T0)
+    In = st["I"].copy()
+    I0w = {s: O.I0(bands, 310.0 if s == 0 else 300.0)[0] for s in (0, 1)}
+    dt = 2e-12
+    A, rhs = _assemble_backward_euler(g, S, w, r, bands, dt, In, I0w)
+    x = np.linalg.solve(A, rhs).reshape(In.shape)
+    p.run(st, dt, 1, 400)
+    assert np.max(np.abs(st["I"] - x) / np.abs(x)) < 1e-13
+
+
+# ------------------------------------------------------ physics invariants
+def test_uniform_equilibrium_stays_at_round_off():
+    wl = W.cfg1()
+    g = wl.geoms[0]
+    W.uniform_walls(g, [W.BC_ISOTHERMAL, W.BC_SPECULAR, W.BC_ISOTHERMAL, W.BC_SPECULAR], [300.0, 0, 300.0, 0])
+    p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands)
+    st = p.init_state(300.0)
+    I_init = st["I"].copy()
+    p.run(st, wl.dt, 20, 5)
+    assert np.max(np.abs(st["I"] - I_init) / I_init) < 1e-14
+    assert np.max(np.abs(st["TL"] - 300.0)) < 1e-14 * 300
+    assert np.max(np.abs(st["Tp"] - 300.0)) < 1e-14 * 300
+    p.run(st, 2e-13, 50, 1, O.EXPLICIT)
+    assert np.max(np.abs(st["I"] - I_init) / I_init) < 1e-14
+
+
+def _specular_box(nx, ny, ndir, nbands, seed):
+    g = W.Geometry(2, nx, ny, 1, 10e-9, 10e-9, 10e-9)
+    W.uniform_walls(g, [W.BC_SPECULAR] * 4, [0] * 4)
+    bands = W.make_bands(nbands, 0, seed)
+    p = O.Problem(g, O.dirs_inplane(ndir), bands)
+    T0 = W.random_temperatures(nx * ny, seed + 1, 290.0, 310.0)
+    return p, p.init_state(T0)
+
+
+def _total_energy(p, I):
+    return sum(p.cell_energy(I[P])[0] for P in range(p.nc))
+
+
+def test_specular_enclosure_conserves_energy_explicit():
+    p, st = _specular_box(8, 6, 8, 3, 11)
+    E0 = _total_energy(p, st["I"])
+    T0 = st["TL"].copy()
+    p.run(st, 2e-13, 500, 1, O.EXPLICIT)
+    E1 = _total_energy(p, st["I"])
+    assert abs(E1 - E0) <= 1e-13 * E0
+    assert np.max(np.abs(st["TL"] - T0)) > 0.5      # the field did evolve
+
+
+def test_specular_enclosure_conserves_energy_implicit_converged():
+    p, st = _specular_box(6, 5, 8, 3, 12)
+    E0 = _total_energy(p, st["I"])
+    p.run(st, 1e-12, 10, 80)
+    E1 = _total_energy(p, st["I"])
+    assert abs(E1 - E0) <= 1e-11 * E0
+
+
+def _slab(nx, dx, dirs, bands, Th, Tc):
+    g = W.Geometry(2, nx, 1, 1, dx, dx, dx)
+    g.bc = [(W.BC_ISOTHERMAL, np.array([Th])), (W.BC_ISOTHERMAL, np.array([Tc])),
+            (W.BC_SPECULAR, None), (W.BC_SPECULAR, None)]
+    return O.Problem(g, dirs, bands)
+
+
+@pytest.mark.parametrize("dirset", ["inplane16", "pa4x8"])
+def test_ballistic_slab_matches_casimir_flux(dirset):
+    if dirset == "inplane16":
+        dirs = O.dirs_inplane(16)
+        Mplus = (4 * math.pi / 16) / math.sin(math.pi / 16)
+    else:
+        dirs = O.dirs_polar_azim(4, 8)
+        Mplus = math.pi
+    bands = W.make_bands(4, 0, 5)
+    bands.beta[:] = 0.0
+    Th, Tc = 310.0, 300.0
+    p = _slab(5, 10e-9, dirs, bands, Th, Tc)
+    st = p.init_state(Tc)
+    p.run(st, 1e-6, 4, 300)
+    q, qw = p.flux(st["I"])
+    exact = float(np.sum(O.I0(bands, Th)[0] - O.I0(bands, Tc)[0])) * Mplus
+    assert np.all(np.abs(q[:, 0] - exact) <= 1e-10 * exact)
+    assert abs(-qw[0] - exact) <= 1e-10 * exact      # into the domain at the hot wall
+    assert abs(qw[1] - exact) <= 1e-10 * exact       # out at the cold wall
+
+
+def test_diffusive_slab_matches_fourier_conduction():
+    """Gray band with mean free path far below the slab: interior flux = -k dT/dx,
+    k = tau v dI0/dT sum_d S_x^2 / w_d (Chapman-Enskog on the discrete set)."""
+    v, tau = 1e3, 1e-11
+    lam = v * tau
+    dx = lam / 2
+    nx = 80
+    bands = W.Bands(np.array([0.0]), np.array([4e13]), np.array([v]), np.array([1.0 / tau]), np.array([1.0]))
+    dirs = O.dirs_inplane(16)
+    S, w, _ = dirs
+    Th, Tc = 302.0, 298.0
+    p = _slab(nx, dx, dirs, bands, Th, Tc)
+    x = (np.arange(nx) + 0.5) / nx
+    st = p.init_state(Th + (Tc - Th) * x)
+    p.run(st, 5e-11, 240, 60)
+    q, _ = p.flux(st["I"])
+    T = st["TL"]
+    inner = slice(nx // 4, 3 * nx // 4)
+    xc = (np.arange(nx) + 0.5) * dx
+    slope, icpt = np.polyfit(xc[inner], T[inner], 1)
+    fit = slope * xc[inner] + icpt
+    r2 = 1 - np.sum((T[inner] - fit) ** 2) / np.sum((T[inner] - T[inner].mean()) ** 2)
+    assert r2 > 0.999
+    Tm = float(T[inner].mean())
+    dI0 = O.I0(bands, Tm)[1][0]
+    k = tau * v * dI0 * float(np.sum(S[:, 0] ** 2 / w))
+    qint = float(np.mean(q[inner, 0]))
+    assert np.max(np.abs(q[inner, 0] - qint)) <= 1e-4 * abs(qint)       # steady: flux uniform
+    assert abs(qint - (-k * slope)) <= 0.02 * abs(qint), (qint, -k * slope)
+
+
+# ------------------------------------------------------ relabelling symmetry
+def test_direction_relabelling_leaves_temperature_unchanged():
+    wl = W.cfg1()
+    g = wl.geoms[0]
+    g.nx, g.ny = 7, 5
+    W.uniform_walls(g, [W.BC_ISOTHERMAL, W.BC_SPECULAR, W.BC_ISOTHERMAL, W.BC_SPECULAR], [310.0, 0, 300.0, 0])
+    S, w, r = O.dirs_inplane(16)
+    perm = np.random.default_rng(3).permutation(16)
+    inv = np.argsort(perm)
+    S2, w2 = S[perm], w[perm]
+    r2 = np.stack([inv[r[a][perm]] for a in range(3)]).astype(np.int32)
+    T0 = W.random_temperatures(35, 4, 295.0, 305.0)
+    out = []
+    for dirs in ((S, w, r), (S2, w2, r2)):
+        p = O.Problem(g, dirs, wl.bands)
+        st = p.init_state(T0)
+        p.run(st, wl.dt, 5, 4)
+        out.append((st["TL"].copy(), st["Tp"].copy(), st["I"][:, inv if dirs[0] is S2 else slice(None)].copy()))
+    assert np.max(np.abs(out[0][0] - out[1][0])) <= 1e-13 * 300
+    assert np.max(np.abs(out[0][1] - out[1][1])) <= 1e-13 * 300
+    assert np.max(np.abs(out[0][2] - out[1][2]) / out[0][2]) <= 1e-13
+
+
+def test_mirrored_geometry_gives_mirrored_temperature():
+    wl = W.cfg1()
+    bands = wl.bands
+    S, w, r = O.dirs_inplane(16)
+    nx, ny = 6, 4
+    T0 = W.random_temperatures(nx * ny, 8, 295.0, 305.0).reshape(ny, nx)
+    res = []
+    for mirror in (False, True):
+        g = W.Geometry(2, nx, ny, 1, 10e-9, 10e-9, 10e-9)
+        hot, cold = (W.BC_ISOTHERMAL, np.full(ny, 310.0)), (W.BC_SPECULAR, None)
+        g.bc = [cold, hot] if mirror else [hot, cold]
+        g.bc += [(W.BC_ISOTHERMAL, np.full(nx, 300.0)), (W.BC_SPECULAR, None)]
+        p = O.Problem(g, (S, w, r), bands)
+        st = p.init_state((T0[:, ::-1] if mirror else T0).ravel())
+        p.run(st, wl.dt, 4, 4)
+        T = st["TL"].reshape(ny, nx)
+        res.append(T[:, ::-1] if mirror else T)
+    assert np.max(np.abs(res[0] - res[1])) <= 1e-12 * 300
