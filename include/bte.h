@@ -1,0 +1,183 @@
+/*
+ * bte.h -- C ABI of libbte, a GB300 (sm_103a) solver for the hot path of the
+ * non-gray phonon Boltzmann transport equation of arXiv:2305.19400, Sec. 3.
+ *
+ * What one call of bte_step computes (Sec. 3.1, Eq. 4-6, and the temperature
+ * update of Sec. 2.2/3.2): for every cell P, direction d and band-polarisation b
+ * the finite-volume update of the intensity I[P][d][b] -- upwind face fluxes
+ * plus relaxation toward the band equilibrium intensity I0_b(T) -- with wall
+ * ghosts from Eq. 6, then the per-cell reduction over (d, b) to an energy, the
+ * nonlinear temperature solve and the I0 refresh.  Every step runs as CUDA
+ * kernels on the caller's stream; nothing runs on the host between launches.
+ *
+ * Conventions for every entry point:
+ *  - Return value: BTE_OK (0) or a negative BTE_E_* code; BTE_W_FALLBACK (+1)
+ *    is success with at least one bisection fallback in a temperature solve.
+ *    The library never exits, aborts or traps the device.  bte_last_error()
+ *    gives a one-line message for the last failing call on that handle.
+ *  - Pointers documented as "host" are read (or written) during the call and
+ *    stay owned by the caller.  Pointers documented as "device" are CUDA
+ *    device pointers on the device that was current at bte_init_mesh.
+ *  - Call order: bte_init_mesh -> bte_set_bands -> [bte_bind_workspace] ->
+ *    bte_set_bc (every side of every geometry) -> bte_set_initial (every
+ *    geometry) -> bte_step / bte_get_* any number of times -> bte_destroy.
+ *    Anything else returns BTE_E_STATE.
+ *  - Handles are not thread-safe; use one handle per host thread.
+ */
+#ifndef BTE_H
+#define BTE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define BTE_OK 0
+#define BTE_E_ARG (-1)       /* bad argument (null pointer, size, index, value) */
+#define BTE_E_STATE (-2)     /* call out of order */
+#define BTE_E_CUDA (-3)      /* a CUDA runtime call failed (message names it) */
+#define BTE_E_NOMEM (-4)     /* workspace too small or device allocation failed */
+#define BTE_E_NONFINITE (-5) /* a cell energy or temperature became NaN/Inf */
+#define BTE_E_TIMEOUT (-6)   /* a bounded device-side wait gave up */
+#define BTE_W_FALLBACK 1     /* success; some temperature solves fell back to bisection */
+
+/* ---- enumerations ---- */
+enum { BTE_DIRS_INPLANE = 0, BTE_DIRS_POLAR_AZIM = 1 };
+enum { BTE_FP64 = 0, BTE_FP32 = 1, BTE_BF16 = 2 };
+enum { BTE_BC_ISOTHERMAL = 0, BTE_BC_SPECULAR = 1 };
+enum { BTE_IMPLICIT_JACOBI = 0, BTE_EXPLICIT = 1 };
+enum { BTE_T_PSEUDO = 0, BTE_T_LATTICE = 1 };
+
+typedef struct bte_ctx* bte_handle;
+
+/* One structured Cartesian geometry.  dim = 2 (nz must be 1) or 3.  Cell sizes
+ * in metres.  Cell (i,j,k) has local index i + nx*(j + ny*k). */
+typedef struct {
+  int dim, nx, ny, nz;
+  double dx, dy, dz;
+} bte_geom;
+
+/* Solver options (bte_default_opts fills the defaults shown).
+ *  dir_kind   BTE_DIRS_INPLANE: n_inplane directions in the x-y plane
+ *             (phi_d = (d+1/2) 2 pi/n, n % 4 == 0; Sec. 3.1 uses 16-20);
+ *             BTE_DIRS_POLAR_AZIM: n_polar x n_azim control angles
+ *             (n_polar even, n_azim % 4 == 0; 20 x 20 = 400 in Sec. 3.1).
+ *  precision  storage of I and the sweep arithmetic: BTE_FP64 (default),
+ *             BTE_FP32 or BTE_BF16; the reduction, temperature solve and I0
+ *             are FP64 in every mode.
+ *  learned    must be 0 (warm-started Halley/Newton temperature solve).
+ *  n_gauss    Gauss-Legendre points per band for I0_b(T) (default 16, <= 32).
+ *  newton_rtol target relative accuracy of the temperature solve (1e-14).
+ *  newton_maxit iteration cap before the bisection fallback (50).
+ *  cuda_stream cudaStream_t every launch and copy uses (NULL: legacy default stream). */
+typedef struct {
+  int dir_kind;
+  int n_inplane, n_polar, n_azim;
+  int precision;
+  int learned;
+  int n_gauss;
+  double newton_rtol;
+  int newton_maxit;
+  void* cuda_stream;
+} bte_opts;
+
+/* Per-call statistics of bte_step (filled only when a non-NULL pointer is
+ * passed; that makes the call wait for the stream to finish). */
+typedef struct {
+  long long updates;          /* cell*dir*band updates performed */
+  long long solve_evals;      /* band-quadrature evaluations in temperature solves */
+  long long solves;           /* temperature solves (cells x inner iterations) */
+  long long fallbacks;        /* bisection fallbacks */
+  long long nonfinite;        /* cells whose energy or temperature was not finite */
+  int launches;               /* kernels launched by the call */
+  double gpu_ms;              /* device time between the first and last launch */
+} bte_stats;
+
+/* Fills *opts with the defaults listed above.  Returns BTE_E_ARG on NULL. */
+int bte_default_opts(bte_opts* opts);
+
+/* Creates a solver for n_geom >= 1 independent geometries sharing one
+ * direction set and band table (Sec. 3.1 discretisation).  geoms: host array
+ * of n_geom.  opts: host, may be NULL for defaults.  *out receives the handle
+ * (NULL on failure).  No device memory is allocated yet. */
+int bte_init_mesh(bte_handle* out, int n_geom, const bte_geom* geoms, const bte_opts* opts);
+
+/* Band-polarisation table (Sec. 3.1: 40 bands -> 55 band-polarisations).
+ * Host arrays of nb values: band edges omega_lo < omega_hi [rad/s], group
+ * velocity vg > 0 [m/s], scattering rate beta = 1/tau >= 0 [1/s], degeneracy
+ * > 0.  I0_b(T) = g_b hbar/(8 pi^3 v_b^2) int w^3/(exp(hbar w/kB T)-1) dw over
+ * the band (Debye-type band, Bose-Einstein occupation).  1 <= nb <= 256. */
+int bte_set_bands(bte_handle h, int nb, const double* omega_lo, const double* omega_hi, const double* vg,
+                  const double* beta, const double* degeneracy);
+
+/* Device bytes the solver needs (valid after bte_set_bands), and binding of a
+ * caller-owned device buffer of at least that size (e.g. a torch.empty
+ * uint8 tensor).  The buffer must stay alive until bte_destroy; the library
+ * never frees it.  Without a bound buffer the library cudaMallocs its own at
+ * the first call that needs device memory and frees it in bte_destroy.
+ * bte_bind_workspace returns BTE_E_NOMEM if bytes is too small, BTE_E_STATE
+ * after device memory is already in use. */
+size_t bte_workspace_bytes(bte_handle h);
+int bte_bind_workspace(bte_handle h, void* dev_ptr, size_t bytes);
+
+/* Wall condition of one side (0:-x 1:+x 2:-y 3:+y 4:-z 5:+z) of geometry
+ * `geom` (Eq. 6).  BTE_BC_ISOTHERMAL: ghost intensity I0_b(T_face); T_faces is
+ * a host array with one temperature per face on that side (x sides: j+ny*k,
+ * y sides: i+nx*k, z sides: i+nx*j) or NULL to use T_uniform for all.
+ * BTE_BC_SPECULAR (symmetry): ghost = same cell, mirrored direction. */
+int bte_set_bc(bte_handle h, int geom, int side, int type, const double* T_faces, double T_uniform);
+
+/* Equilibrium initial state (Sec. 3.2): I[P][d][b] = I0_b(T_P) for all d and
+ * T_p = T_L = T_P.  T_cells: host array of the geometry's cells, or NULL for
+ * T_uniform everywhere.  Temperatures must lie in [1, 5000] K. */
+int bte_set_initial(bte_handle h, int geom, const double* T_cells, double T_uniform);
+
+/* Advances every geometry by nsteps time steps of size dt [s].
+ * scheme BTE_IMPLICIT_JACOBI: backward Euler, each step solved by ninner
+ *   point-Jacobi inner iterations; each inner iteration is one sweep
+ *   I^{k+1} = [I^n/dt + beta I0^k + v sum_ax c_ax I_up^k]/[1/dt + beta + v sum_ax c_ax]
+ *   (c_ax = |S_ax|/(w_d Delta_ax)), then reduction, T_p solve, I0 refresh.
+ * scheme BTE_EXPLICIT: forward Euler (Eq. 3 with Eq. 5), ninner ignored.
+ * stats: host, may be NULL (then the call only queues work and returns). */
+int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_stats* stats);
+
+/* Cell temperatures of one geometry: BTE_T_PSEUDO (T_p, the temperature whose
+ * equilibrium the relaxation term drives toward) or BTE_T_LATTICE (T_L, the
+ * energy-equivalent temperature).  out: ncells doubles, host or device
+ * (out_on_device != 0).  Waits for the stream. */
+int bte_get_T(bte_handle h, int geom, int which, double* out, int out_on_device);
+
+/* Heat flux of one geometry.  q_cells: ncells*dim doubles, q(P) = sum_b sum_d
+ * S_d I[P][d][b] (W/m^2), or NULL.  q_walls: 2*dim doubles, per side the mean
+ * over its faces of sum_b sum_d (S_d . n_out) I_face (upwind face value,
+ * ghost for incoming directions; positive = leaving), or NULL.  Host or
+ * device per out_on_device.  Waits for the stream. */
+int bte_get_flux(bte_handle h, int geom, double* q_cells, double* q_walls, int out_on_device);
+
+/* Copies the intensity of one geometry out as FP64 [cell][dir][band]
+ * (ncells*nd*nb doubles, unpadded), host or device. */
+int bte_get_intensity(bte_handle h, int geom, double* out, int out_on_device);
+
+/* Replaces the intensity of one geometry with `in` (FP64 [cell][dir][band],
+ * host or device per in_on_device) and sets T_p to Tp_cells (host/device,
+ * ncells) -- a checkpoint restore.  I0 is recomputed from T_p. */
+int bte_set_intensity(bte_handle h, int geom, const double* in, const double* Tp_cells, int in_on_device);
+
+/* Direction table the solver uses: S (nd*3, control-angle integrals of the
+ * unit vector), w (nd, solid angles), refl (3*nd, mirror direction across an
+ * x, y, z wall).  Host arrays; any may be NULL.  Returns nd (>0) or an error. */
+int bte_get_directions(bte_handle h, double* S, double* w, int* refl);
+
+/* Frees everything the library allocated (not a bound workspace). */
+int bte_destroy(bte_handle h);
+
+/* Last error message of the handle ("" if none); h may be NULL for errors
+ * from bte_init_mesh.  The string lives until the next call on the handle. */
+const char* bte_last_error(bte_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BTE_H */

@@ -1,0 +1,264 @@
+"""Thin Python binding of libbte (include/bte.h): same entry-point names,
+argument marshalling only.  Every step of the hot path runs in the library's
+CUDA kernels; there is no CPU fallback.  PyTorch supplies device memory
+(workspace, device-side outputs) and the CUDA stream.
+
+Loading fails loudly (RuntimeError) when libbte.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libbte.so")
+
+BTE_OK, BTE_W_FALLBACK = 0, 1
+BTE_E = {-1: "BTE_E_ARG", -2: "BTE_E_STATE", -3: "BTE_E_CUDA", -4: "BTE_E_NOMEM", -5: "BTE_E_NONFINITE",
+         -6: "BTE_E_TIMEOUT"}
+BTE_DIRS_INPLANE, BTE_DIRS_POLAR_AZIM = 0, 1
+BTE_FP64, BTE_FP32, BTE_BF16 = 0, 1, 2
+BTE_BC_ISOTHERMAL, BTE_BC_SPECULAR = 0, 1
+BTE_IMPLICIT_JACOBI, BTE_EXPLICIT = 0, 1
+BTE_T_PSEUDO, BTE_T_LATTICE = 0, 1
+
+
+class bte_geom(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double)]
+
+
+class bte_opts(C.Structure):
+    _fields_ = [("dir_kind", C.c_int), ("n_inplane", C.c_int), ("n_polar", C.c_int), ("n_azim", C.c_int),
+                ("precision", C.c_int), ("learned", C.c_int), ("n_gauss", C.c_int), ("newton_rtol", C.c_double),
+                ("newton_maxit", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class bte_stats(C.Structure):
+    _fields_ = [("updates", C.c_longlong), ("solve_evals", C.c_longlong), ("solves", C.c_longlong),
+                ("fallbacks", C.c_longlong), ("nonfinite", C.c_longlong), ("launches", C.c_int),
+                ("gpu_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# Every symbol include/bte.h declares, with its ctypes signature.
+_dp, _ip, _vp, _h = C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p, C.c_void_p
+SIGNATURES = {
+    "bte_default_opts": (C.c_int, [C.POINTER(bte_opts)]),
+    "bte_init_mesh": (C.c_int, [C.POINTER(_h), C.c_int, C.POINTER(bte_geom), C.POINTER(bte_opts)]),
+    "bte_set_bands": (C.c_int, [_h, C.c_int, _dp, _dp, _dp, _dp, _dp]),
+    "bte_workspace_bytes": (C.c_size_t, [_h]),
+    "bte_bind_workspace": (C.c_int, [_h, _vp, C.c_size_t]),
+    "bte_set_bc": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, _dp, C.c_double]),
+    "bte_set_initial": (C.c_int, [_h, C.c_int, _dp, C.c_double]),
+    "bte_step": (C.c_int, [_h, C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(bte_stats)]),
+    "bte_get_T": (C.c_int, [_h, C.c_int, C.c_int, _vp, C.c_int]),
+    "bte_get_flux": (C.c_int, [_h, C.c_int, _vp, _vp, C.c_int]),
+    "bte_get_intensity": (C.c_int, [_h, C.c_int, _vp, C.c_int]),
+    "bte_set_intensity": (C.c_int, [_h, C.c_int, _vp, _vp, C.c_int]),
+    "bte_get_directions": (C.c_int, [_h, _dp, _dp, _ip]),
+    "bte_destroy": (C.c_int, [_h]),
+    "bte_last_error": (C.c_char_p, [_h]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libbte.so (RuntimeError if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libbte.so is not built ({LIB_PATH}); run paper_2305_19400_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class BTEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{BTE_E.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(h, rc):
+    if rc < 0:
+        msg = lib().bte_last_error(h)
+        raise BTEError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(x):
+    """Host numpy array -> double*, torch tensor -> device/host address, None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return C.c_void_p(x.ctypes.data)
+    return C.c_void_p(x.data_ptr())
+
+
+# ---- entry points with the C names -----------------------------------------
+def bte_default_opts():
+    o = bte_opts()
+    lib().bte_default_opts(C.byref(o))
+    return o
+
+
+def bte_init_mesh(geoms, opts=None):
+    arr = (bte_geom * len(geoms))(*geoms)
+    h = C.c_void_p()
+    rc = lib().bte_init_mesh(C.byref(h), len(geoms), arr, C.byref(opts) if opts is not None else None)
+    _check(None, rc)
+    return h
+
+
+def bte_set_bands(h, omega_lo, omega_hi, vg, beta, degeneracy):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (omega_lo, omega_hi, vg, beta, degeneracy)]
+    return _check(h, lib().bte_set_bands(h, len(arrs[0]), *[a.ctypes.data_as(_dp) for a in arrs]))
+
+
+def bte_workspace_bytes(h):
+    return int(lib().bte_workspace_bytes(h))
+
+
+def bte_bind_workspace(h, tensor):
+    return _check(h, lib().bte_bind_workspace(h, C.c_void_p(tensor.data_ptr()), tensor.numel() * tensor.element_size()))
+
+
+def bte_set_bc(h, geom, side, kind, T_faces=None, T_uniform=300.0):
+    arr = None if T_faces is None else np.ascontiguousarray(T_faces, dtype=np.float64)
+    return _check(h, lib().bte_set_bc(h, geom, side, kind, None if arr is None else arr.ctypes.data_as(_dp), float(T_uniform)))
+
+
+def bte_set_initial(h, geom, T_cells=None, T_uniform=300.0):
+    arr = None if T_cells is None else np.ascontiguousarray(T_cells, dtype=np.float64)
+    return _check(h, lib().bte_set_initial(h, geom, None if arr is None else arr.ctypes.data_as(_dp), float(T_uniform)))
+
+
+def bte_step(h, dt, nsteps, ninner, scheme=BTE_IMPLICIT_JACOBI, want_stats=True):
+    st = bte_stats() if want_stats else None
+    rc = lib().bte_step(h, float(dt), int(nsteps), int(ninner), int(scheme), C.byref(st) if st is not None else None)
+    _check(h, rc)
+    return rc, (st.as_dict() if st is not None else None)
+
+
+def bte_get_T(h, geom, which, out):
+    """out: float64 numpy array (host) or torch CUDA tensor (device)."""
+    on_dev = 0 if isinstance(out, np.ndarray) else 1
+    return _check(h, lib().bte_get_T(h, geom, which, _ptr(out), on_dev))
+
+
+def bte_get_flux(h, geom, q_cells=None, q_walls=None, on_device=False):
+    return _check(h, lib().bte_get_flux(h, geom, _ptr(q_cells), _ptr(q_walls), 1 if on_device else 0))
+
+
+def bte_get_intensity(h, geom, out):
+    on_dev = 0 if isinstance(out, np.ndarray) else 1
+    return _check(h, lib().bte_get_intensity(h, geom, _ptr(out), on_dev))
+
+
+def bte_set_intensity(h, geom, I, Tp):
+    on_dev = 0 if isinstance(I, np.ndarray) else 1
+    if on_dev == 0:
+        I = np.ascontiguousarray(I, dtype=np.float64)
+        Tp = np.ascontiguousarray(Tp, dtype=np.float64)
+    return _check(h, lib().bte_set_intensity(h, geom, _ptr(I), _ptr(Tp), on_dev))
+
+
+def bte_get_directions(h):
+    nd = _check(h, lib().bte_get_directions(h, None, None, None))
+    S = np.zeros((nd, 3)); w = np.zeros(nd); r = np.zeros((3, nd), dtype=np.int32)
+    lib().bte_get_directions(h, S.ctypes.data_as(_dp), w.ctypes.data_as(_dp), r.ctypes.data_as(_ip))
+    return S, w, r
+
+
+def bte_destroy(h):
+    return _check(None, lib().bte_destroy(h))
+
+
+def bte_last_error(h):
+    m = lib().bte_last_error(h)
+    return m.decode() if m else ""
+
+
+# ---- convenience: a solver built from a workload description ---------------
+class Solver:
+    """Marshals a workload (paper_2305_19400_gb300.workloads) into the C calls.
+
+    Device memory comes from a torch uint8 tensor bound as the workspace; the
+    stream is the given torch stream (default: torch's current stream).
+    """
+
+    def __init__(self, workload, precision=BTE_FP64, stream=None, bind_workspace=True, n_gauss=16, T_init=None):
+        import torch
+
+        self.wl = workload
+        self.torch = torch
+        o = bte_default_opts()
+        d = workload.dirs
+        if d.kind == "inplane":
+            o.dir_kind, o.n_inplane = BTE_DIRS_INPLANE, d.n_inplane
+        else:
+            o.dir_kind, o.n_polar, o.n_azim = BTE_DIRS_POLAR_AZIM, d.n_polar, d.n_azim
+        o.precision = precision
+        o.n_gauss = n_gauss
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        o.cuda_stream = self.stream.cuda_stream
+        geoms = [bte_geom(g.dim, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz) for g in workload.geoms]
+        self.h = bte_init_mesh(geoms, o)
+        b = workload.bands
+        bte_set_bands(self.h, b.omega_lo, b.omega_hi, b.vg, b.beta, b.degeneracy)
+        self.ws = None
+        if bind_workspace:
+            nbytes = bte_workspace_bytes(self.h)
+            self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            off = (-self.ws.data_ptr()) % 256
+            self.ws_view = self.ws[off:off + nbytes]
+            bte_bind_workspace(self.h, self.ws_view)
+        for gi, g in enumerate(workload.geoms):
+            for side, (kind, T) in enumerate(g.bc):
+                bte_set_bc(self.h, gi, side, kind, T, 300.0)
+            bte_set_initial(self.h, gi, None if T_init is None else T_init[gi], g.T_init)
+
+    def step(self, nsteps=None, ninner=None, dt=None, scheme=BTE_IMPLICIT_JACOBI, want_stats=True):
+        wl = self.wl
+        return bte_step(self.h, wl.dt if dt is None else dt, wl.nsteps if nsteps is None else nsteps,
+                        wl.ninner if ninner is None else ninner, scheme, want_stats)
+
+    def T(self, geom=0, which=BTE_T_LATTICE):
+        g = self.wl.geoms[geom]
+        out = np.zeros(g.ncells)
+        bte_get_T(self.h, geom, which, out)
+        return out
+
+    def intensity(self, geom=0):
+        g = self.wl.geoms[geom]
+        out = np.zeros((g.ncells, self.wl.dirs.nd, self.wl.bands.nb))
+        bte_get_intensity(self.h, geom, out)
+        return out
+
+    def flux(self, geom=0):
+        g = self.wl.geoms[geom]
+        q = np.zeros((g.ncells, g.dim))
+        qw = np.zeros(2 * g.dim)
+        bte_get_flux(self.h, geom, q, qw)
+        return q, qw
+
+    def close(self):
+        if self.h is not None:
+            bte_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,668 @@
+// bte_capi.cu -- the extern "C" entry points of libbte (declared in include/bte.h).
+//
+// A handle owns: the host copies of the direction and band tables, the
+// per-geometry bookkeeping, and one device workspace (caller-bound or
+// library-allocated) carved into the buffers listed in bte_internal.h.  Every
+// kernel and copy goes to the stream given in bte_opts.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/bte.h"
+#include "bte_internal.h"
+#include "bte_tables.h"
+
+using namespace bte;
+
+struct bte_ctx {
+  std::string err;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bte_opts opts{};
+  // geometry
+  std::vector<bte_geom> geoms;
+  std::vector<long long> cell0;
+  std::vector<long long> face0;  // [geom*6 + side]
+  std::vector<int> cls;
+  std::vector<std::tuple<int, double, double, double>> cls_key;
+  long long ncells = 0, nfaces = 0;
+  int max_side_faces = 0, max_geom_cells = 0;
+  // directions
+  int nd = 0;
+  std::vector<double> S, w;
+  std::vector<int> refl;
+  double Wtot = 0.0;
+  // bands
+  int nb = 0, nbp = 0, ng = 16;
+  std::vector<double> wlo, whi, vg, beta, deg;
+  bool solve_tp = false;
+  // state
+  bool bands_set = false;
+  std::vector<std::array<int, 6>> bc_type;
+  std::vector<std::array<bool, 6>> bc_set;
+  std::vector<bool> init_set;
+  bool TL_valid = false;
+  // launch shape
+  int lpc = 0, cpb = 0, threads = 0;
+  std::vector<WorkItem> items;
+  // device memory
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false, mem_ready = false;
+  char* Ibuf[3] = {nullptr, nullptr, nullptr};
+  int cur = 0;
+  double *I0cell = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr, *I0wall = nullptr, *coef = nullptr;
+  double *wdir = nullptr, *Sdev = nullptr, *node_c = nullptr, *node_C = nullptr, *a_p = nullptr, *a_L = nullptr;
+  double *inv_v = nullptr, *beta_d = nullptr, *scratch_faces = nullptr, *scratch_T = nullptr, *scratch_out = nullptr;
+  double* scratch_q = nullptr;
+  std::vector<DevGeom> dgeoms;
+  DirInfo* dirs_d = nullptr;
+  DevGeom* geoms_d = nullptr;
+  WorkItem* items_d = nullptr;
+  DevCounters* counters = nullptr;
+  // coefficient cache
+  double coef_dt = -1.0;
+  int coef_scheme = -1;
+  std::vector<double> coef_host;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_init_err;
+
+int fail(bte_ctx* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf; else g_init_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(h, call)                                                                        \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail((h), BTE_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t elem_bytes(int precision) { return precision == BTE_FP64 ? 8 : (precision == BTE_FP32 ? 4 : 2); }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+long long side_faces(const bte_geom& g, int side) {
+  if (side < 2) return (long long)g.ny * g.nz;
+  if (side < 4) return (long long)g.nx * g.nz;
+  return (long long)g.nx * g.ny;
+}
+
+ThermoTables thermo(const bte_ctx* h) {
+  ThermoTables t;
+  t.node_c = h->node_c;
+  t.node_C = h->node_C;
+  t.a_p = h->a_p;
+  t.a_L = h->a_L;
+  t.inv_v = h->inv_v;
+  t.beta = h->beta_d;
+  t.ng = h->ng;
+  t.nbp = h->nbp;
+  t.nb = h->nb;
+  return t;
+}
+
+// Workspace layout; with base == nullptr only the size is computed.
+size_t carve(bte_ctx* h, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  };
+  const size_t row = (size_t)h->nd * h->nbp;
+  const size_t ibytes = (size_t)h->ncells * row * elem_bytes(h->opts.precision);
+  for (int i = 0; i < 3; ++i) h->Ibuf[i] = take(ibytes);
+  h->I0cell = (double*)take((size_t)h->ncells * h->nbp * 8);
+  h->Tp = (double*)take((size_t)h->ncells * 8);
+  h->TL = (double*)take((size_t)h->ncells * 8);
+  h->EL = (double*)take((size_t)h->ncells * 8);
+  h->I0wall = (double*)take((size_t)std::max(h->nfaces, 1LL) * h->nbp * 8);
+  h->coef = (double*)take((size_t)h->cls_key.size() * 5 * row * 8);
+  h->wdir = (double*)take((size_t)h->nd * 8);
+  h->Sdev = (double*)take((size_t)h->nd * 3 * 8);
+  h->dirs_d = (DirInfo*)take((size_t)h->nd * sizeof(DirInfo));
+  h->node_c = (double*)take((size_t)h->nbp * h->ng * 8);
+  h->node_C = (double*)take((size_t)h->nbp * h->ng * 8);
+  h->a_p = (double*)take((size_t)h->nbp * 8);
+  h->a_L = (double*)take((size_t)h->nbp * 8);
+  h->inv_v = (double*)take((size_t)h->nbp * 8);
+  h->beta_d = (double*)take((size_t)h->nbp * 8);
+  h->geoms_d = (DevGeom*)take(h->geoms.size() * sizeof(DevGeom));
+  h->items_d = (WorkItem*)take(h->items.size() * sizeof(WorkItem));
+  h->counters = (DevCounters*)take(sizeof(DevCounters));
+  h->scratch_faces = (double*)take((size_t)std::max(h->max_side_faces, 1) * 8);
+  h->scratch_T = (double*)take((size_t)std::max(h->max_side_faces, h->max_geom_cells) * 8);
+  h->scratch_out = (double*)take(64);
+  h->scratch_q = (double*)take((size_t)std::max(h->max_geom_cells, 1) * 3 * 8);
+  return off;
+}
+
+void build_items(bte_ctx* h) {
+  h->lpc = h->nbp / 2;  // FP64: two bands per lane (double2)
+  h->cpb = std::max(1, 256 / h->lpc);
+  h->threads = h->cpb * h->lpc;
+  h->items.clear();
+  for (size_t gi = 0; gi < h->geoms.size(); ++gi) {
+    const bte_geom& g = h->geoms[gi];
+    const int nc = g.nx * g.ny * g.nz;
+    for (int c = 0; c < nc; c += h->cpb) h->items.push_back(WorkItem{(int)gi, c, std::min(h->cpb, nc - c), 0});
+  }
+}
+
+int ensure_memory(bte_ctx* h) {
+  if (h->mem_ready) return BTE_OK;
+  if (!h->bands_set) return fail(h, BTE_E_STATE, "bte_set_bands must come first");
+  const size_t need = carve(h, nullptr);
+  if (!h->ws) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) return fail(h, BTE_E_NOMEM, "cudaMalloc(%zu bytes): %s", need, cudaGetErrorString(e));
+    h->ws = (char*)p;
+    h->ws_bytes = need;
+    h->ws_owned = true;
+  }
+  carve(h, h->ws);
+  cudaStream_t s = h->stream;
+  // I buffers start at zero so padding bands are zero everywhere.
+  const size_t ibytes = (size_t)h->ncells * h->nd * h->nbp * elem_bytes(h->opts.precision);
+  for (int i = 0; i < 3; ++i) CUDA_TRY(h, cudaMemsetAsync(h->Ibuf[i], 0, ibytes, s));
+  CUDA_TRY(h, cudaMemsetAsync(h->I0wall, 0, (size_t)std::max(h->nfaces, 1LL) * h->nbp * 8, s));
+  // direction tables
+  std::vector<DirInfo> di(h->nd);
+  for (int d = 0; d < h->nd; ++d) {
+    di[d].up = (h->S[3 * d] > 0) | ((h->S[3 * d + 1] > 0) << 1) | ((h->S[3 * d + 2] > 0) << 2);
+    di[d].rx = h->refl[d];
+    di[d].ry = h->refl[h->nd + d];
+    di[d].rz = h->refl[2 * h->nd + d];
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->dirs_d, di.data(), di.size() * sizeof(DirInfo), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->wdir, h->w.data(), h->nd * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->Sdev, h->S.data(), h->nd * 3 * 8, cudaMemcpyHostToDevice, s));
+  // band tables
+  std::vector<double> nc, nC, ap, aL, iv, be;
+  build_thermo(h->nb, h->nbp, h->ng, h->wlo.data(), h->whi.data(), h->vg.data(), h->beta.data(), h->deg.data(),
+               h->Wtot, nc, nC, ap, aL, iv, be);
+  CUDA_TRY(h, cudaMemcpyAsync(h->node_c, nc.data(), nc.size() * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->node_C, nC.data(), nC.size() * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->a_p, ap.data(), ap.size() * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->a_L, aL.data(), aL.size() * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->inv_v, iv.data(), iv.size() * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->beta_d, be.data(), be.size() * 8, cudaMemcpyHostToDevice, s));
+  // geometry + work list
+  std::vector<DevGeom>& dg = h->dgeoms;
+  dg.assign(h->geoms.size(), DevGeom{});
+  for (size_t gi = 0; gi < h->geoms.size(); ++gi) {
+    const bte_geom& g = h->geoms[gi];
+    DevGeom& o = dg[gi];
+    o.nx = g.nx; o.ny = g.ny; o.nz = g.nz; o.dim = g.dim;
+    o.cell0 = h->cell0[gi];
+    for (int s6 = 0; s6 < 6; ++s6) {
+      o.face0[s6] = h->face0[gi * 6 + s6];
+      o.bc[s6] = h->bc_type[gi][s6];
+    }
+    o.cls = h->cls[gi];
+    o.pad = 0;
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->geoms_d, dg.data(), dg.size() * sizeof(DevGeom), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->items_d, h->items.data(), h->items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, sizeof(DevCounters), s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  h->mem_ready = true;
+  return BTE_OK;
+}
+
+int upload_geoms(bte_ctx* h) {
+  std::vector<DevGeom>& dg = h->dgeoms;
+  for (size_t gi = 0; gi < h->geoms.size(); ++gi)
+    for (int s6 = 0; s6 < 6; ++s6) dg[gi].bc[s6] = h->bc_type[gi][s6];
+  CUDA_TRY(h, cudaMemcpyAsync(h->geoms_d, dg.data(), dg.size() * sizeof(DevGeom), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return BTE_OK;
+}
+
+int ensure_coef(bte_ctx* h, double dt, int scheme) {
+  if (h->coef_dt == dt && h->coef_scheme == scheme) return BTE_OK;
+  const size_t per = (size_t)5 * h->nd * h->nbp;
+  h->coef_host.assign(per * h->cls_key.size(), 0.0);
+  for (size_t c = 0; c < h->cls_key.size(); ++c) {
+    const double delta[3] = {std::get<1>(h->cls_key[c]), std::get<2>(h->cls_key[c]), std::get<3>(h->cls_key[c])};
+    build_coef(std::get<0>(h->cls_key[c]), delta, h->nd, h->S.data(), h->w.data(), h->nb, h->nbp, h->vg.data(),
+               h->beta.data(), dt, scheme == BTE_EXPLICIT, h->coef_host.data() + c * per);
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->coef, h->coef_host.data(), h->coef_host.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->coef_dt = dt;
+  h->coef_scheme = scheme;
+  return BTE_OK;
+}
+
+int check_geom(bte_ctx* h, int geom) {
+  if (!h) return BTE_E_ARG;
+  if (geom < 0 || geom >= (int)h->geoms.size()) return fail(h, BTE_E_ARG, "geometry index %d out of range", geom);
+  return BTE_OK;
+}
+
+bool ready_to_step(bte_ctx* h, std::string& why) {
+  for (size_t gi = 0; gi < h->geoms.size(); ++gi) {
+    for (int s6 = 0; s6 < 2 * h->geoms[gi].dim; ++s6)
+      if (!h->bc_set[gi][s6]) { why = "bte_set_bc missing for geometry " + std::to_string(gi) + " side " + std::to_string(s6); return false; }
+    if (!h->init_set[gi]) { why = "bte_set_initial missing for geometry " + std::to_string(gi); return false; }
+  }
+  return true;
+}
+
+int ensure_TL(bte_ctx* h) {
+  if (h->TL_valid) return BTE_OK;
+  // warm start from T_p (or the previous T_L when T_p is not solved)
+  CUDA_TRY(h, launch_solve_TL(h->TL, h->EL, h->solve_tp ? h->Tp : h->TL, h->ncells, thermo(h),
+                              h->opts.newton_rtol, h->opts.newton_maxit, h->counters, h->stream));
+  h->TL_valid = true;
+  return BTE_OK;
+}
+
+int copy_out(bte_ctx* h, double* out, const double* src, size_t n, int on_device) {
+  CUDA_TRY(h, cudaMemcpyAsync(out, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return BTE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bte_default_opts(bte_opts* o) {
+  if (!o) return BTE_E_ARG;
+  std::memset(o, 0, sizeof *o);
+  o->dir_kind = BTE_DIRS_POLAR_AZIM;
+  o->n_inplane = 16;
+  o->n_polar = 20;
+  o->n_azim = 20;
+  o->precision = BTE_FP64;
+  o->learned = 0;
+  o->n_gauss = 16;
+  o->newton_rtol = 1e-14;
+  o->newton_maxit = 50;
+  o->cuda_stream = nullptr;
+  return BTE_OK;
+}
+
+int bte_init_mesh(bte_handle* out, int n_geom, const bte_geom* geoms, const bte_opts* opts) {
+  if (!out) return fail(nullptr, BTE_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_geom < 1 || !geoms) return fail(nullptr, BTE_E_ARG, "need n_geom >= 1 and a geometry array");
+  bte_opts o;
+  if (opts) o = *opts; else bte_default_opts(&o);
+  if (o.precision != BTE_FP64) return fail(nullptr, BTE_E_ARG, "precision %d is not available (FP64 only)", o.precision);
+  if (o.learned != 0) return fail(nullptr, BTE_E_ARG, "learned mode is not available");
+  if (o.n_gauss < 1 || o.n_gauss > kMaxGauss) return fail(nullptr, BTE_E_ARG, "n_gauss must be in 1..%d", kMaxGauss);
+  if (!(o.newton_rtol > 0 && o.newton_rtol < 1e-3) || o.newton_maxit < 1)
+    return fail(nullptr, BTE_E_ARG, "newton_rtol must be in (0, 1e-3) and newton_maxit >= 1");
+  long long total = 0;
+  for (int i = 0; i < n_geom; ++i) {
+    const bte_geom& g = geoms[i];
+    if (!(g.dim == 2 || g.dim == 3) || g.nx < 1 || g.ny < 1 || g.nz < 1 || (g.dim == 2 && g.nz != 1))
+      return fail(nullptr, BTE_E_ARG, "geometry %d: bad dim/size", i);
+    if (!(g.dx > 0 && g.dy > 0 && (g.dim == 2 || g.dz > 0))) return fail(nullptr, BTE_E_ARG, "geometry %d: cell sizes must be > 0", i);
+    const long long nc = (long long)g.nx * g.ny * g.nz;
+    if (nc > (1LL << 30)) return fail(nullptr, BTE_E_ARG, "geometry %d: too many cells", i);
+    total += nc;
+  }
+  bte_ctx* h = new bte_ctx();
+  h->opts = o;
+  h->ng = o.n_gauss;
+  h->stream = (cudaStream_t)o.cuda_stream;
+  cudaGetDevice(&h->dev);
+  int rc;
+  if (o.dir_kind == BTE_DIRS_INPLANE) rc = build_dirs_inplane(o.n_inplane, h->S, h->w, h->refl);
+  else if (o.dir_kind == BTE_DIRS_POLAR_AZIM) rc = build_dirs_polar_azim(o.n_polar, o.n_azim, h->S, h->w, h->refl);
+  else rc = -1;
+  if (rc != 0) {
+    delete h;
+    return fail(nullptr, BTE_E_ARG, "bad direction set (in-plane needs n %% 4 == 0; polar x azimuthal needs even n_polar and n_azim %% 4 == 0)");
+  }
+  h->nd = (int)h->w.size();
+  for (double x : h->w) h->Wtot += x;
+  h->geoms.assign(geoms, geoms + n_geom);
+  h->ncells = total;
+  long long c0 = 0, f0 = 0;
+  std::map<std::tuple<int, double, double, double>, int> keys;
+  for (int i = 0; i < n_geom; ++i) {
+    bte_geom g = geoms[i];
+    if (g.dim == 2) g.dz = g.dz > 0 ? g.dz : 1.0;
+    h->geoms[i] = g;
+    h->cell0.push_back(c0);
+    const long long nc = (long long)g.nx * g.ny * g.nz;
+    h->max_geom_cells = std::max<long long>(h->max_geom_cells, nc);
+    c0 += nc;
+    for (int s6 = 0; s6 < 6; ++s6) {
+      h->face0.push_back(f0);
+      if (s6 < 2 * g.dim) {
+        f0 += side_faces(g, s6);
+        h->max_side_faces = std::max<long long>(h->max_side_faces, side_faces(g, s6));
+      }
+    }
+    auto key = std::make_tuple(g.dim, g.dx, g.dy, g.dim == 3 ? g.dz : 0.0);
+    auto it = keys.find(key);
+    if (it == keys.end()) {
+      const int id = (int)h->cls_key.size();
+      keys[key] = id;
+      h->cls_key.push_back(key);
+      h->cls.push_back(id);
+    } else {
+      h->cls.push_back(it->second);
+    }
+  }
+  h->nfaces = f0;
+  h->bc_type.assign(n_geom, {BTE_BC_SPECULAR, BTE_BC_SPECULAR, BTE_BC_SPECULAR, BTE_BC_SPECULAR, BTE_BC_SPECULAR, BTE_BC_SPECULAR});
+  h->bc_set.assign(n_geom, {false, false, false, false, false, false});
+  h->init_set.assign(n_geom, false);
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, BTE_E_CUDA, "cudaEventCreate failed");
+  }
+  *out = h;
+  return BTE_OK;
+}
+
+int bte_set_bands(bte_handle h, int nb, const double* wlo, const double* whi, const double* vg, const double* beta,
+                  const double* deg) {
+  if (!h) return BTE_E_ARG;
+  if (h->bands_set) return fail(h, BTE_E_STATE, "bands are already set");
+  if (nb < 1 || nb > kMaxBands || !wlo || !whi || !vg || !beta || !deg)
+    return fail(h, BTE_E_ARG, "need 1 <= nb <= %d and five band arrays", kMaxBands);
+  for (int b = 0; b < nb; ++b) {
+    if (!(std::isfinite(wlo[b]) && std::isfinite(whi[b]) && wlo[b] >= 0 && whi[b] > wlo[b]))
+      return fail(h, BTE_E_ARG, "band %d: need 0 <= omega_lo < omega_hi", b);
+    if (!(std::isfinite(vg[b]) && vg[b] > 0)) return fail(h, BTE_E_ARG, "band %d: vg must be > 0", b);
+    if (!(std::isfinite(beta[b]) && beta[b] >= 0)) return fail(h, BTE_E_ARG, "band %d: beta must be >= 0", b);
+    if (!(std::isfinite(deg[b]) && deg[b] > 0)) return fail(h, BTE_E_ARG, "band %d: degeneracy must be > 0", b);
+  }
+  h->nb = nb;
+  h->nbp = (nb + 7) / 8 * 8;
+  h->wlo.assign(wlo, wlo + nb);
+  h->whi.assign(whi, whi + nb);
+  h->vg.assign(vg, vg + nb);
+  h->beta.assign(beta, beta + nb);
+  h->deg.assign(deg, deg + nb);
+  h->solve_tp = false;
+  for (int b = 0; b < nb; ++b) h->solve_tp |= beta[b] > 0;
+  build_items(h);
+  h->bands_set = true;
+  return BTE_OK;
+}
+
+size_t bte_workspace_bytes(bte_handle h) {
+  if (!h || !h->bands_set) return 0;
+  bte_ctx tmp = *h;  // carve() writes pointers; keep h untouched
+  return carve(&tmp, nullptr);
+}
+
+int bte_bind_workspace(bte_handle h, void* dev_ptr, size_t bytes) {
+  if (!h) return BTE_E_ARG;
+  if (!h->bands_set) return fail(h, BTE_E_STATE, "bte_set_bands must come before bte_bind_workspace");
+  if (h->mem_ready || h->ws) return fail(h, BTE_E_STATE, "device memory is already in use");
+  if (!dev_ptr) return fail(h, BTE_E_ARG, "dev_ptr is NULL");
+  if (((uintptr_t)dev_ptr) & 255) return fail(h, BTE_E_ARG, "workspace must be 256-byte aligned");
+  const size_t need = bte_workspace_bytes(h);
+  if (bytes < need) return fail(h, BTE_E_NOMEM, "workspace of %zu bytes is smaller than the %zu needed", bytes, need);
+  h->ws = (char*)dev_ptr;
+  h->ws_bytes = bytes;
+  h->ws_owned = false;
+  return BTE_OK;
+}
+
+int bte_set_bc(bte_handle h, int geom, int side, int type, const double* T_faces, double T_uniform) {
+  int rc = check_geom(h, geom);
+  if (rc) return rc;
+  if (!h->bands_set) return fail(h, BTE_E_STATE, "bte_set_bands must come before bte_set_bc");
+  const bte_geom& g = h->geoms[geom];
+  if (side < 0 || side >= 2 * g.dim) return fail(h, BTE_E_ARG, "side %d out of range for a %dD geometry", side, g.dim);
+  if (type != BTE_BC_ISOTHERMAL && type != BTE_BC_SPECULAR) return fail(h, BTE_E_ARG, "unknown wall type %d", type);
+  const long long nf = side_faces(g, side);
+  std::vector<double> T;
+  if (type == BTE_BC_ISOTHERMAL) {
+    T.assign(nf, T_uniform);
+    if (T_faces) T.assign(T_faces, T_faces + nf);
+    for (double t : T)
+      if (!(t >= kTmin && t <= kTmax)) return fail(h, BTE_E_ARG, "wall temperature %g outside [1, 5000] K", t);
+  }
+  if ((rc = ensure_memory(h))) return rc;
+  if (type == BTE_BC_ISOTHERMAL) {
+    CUDA_TRY(h, cudaMemcpyAsync(h->scratch_T, T.data(), nf * 8, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, launch_wall_I0(h->I0wall + h->face0[geom * 6 + side] * h->nbp, h->scratch_T, nf, thermo(h), h->stream));
+  }
+  const bool changed = h->bc_type[geom][side] != type;
+  h->bc_type[geom][side] = type;
+  h->bc_set[geom][side] = true;
+  if (changed && (rc = upload_geoms(h))) return rc;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return BTE_OK;
+}
+
+int bte_set_initial(bte_handle h, int geom, const double* T_cells, double T_uniform) {
+  int rc = check_geom(h, geom);
+  if (rc) return rc;
+  if (!h->bands_set) return fail(h, BTE_E_STATE, "bte_set_bands must come before bte_set_initial");
+  const bte_geom& g = h->geoms[geom];
+  const long long nc = (long long)g.nx * g.ny * g.nz;
+  std::vector<double> T(nc, T_uniform);
+  if (T_cells) T.assign(T_cells, T_cells + nc);
+  for (double t : T)
+    if (!(t >= kTmin && t <= kTmax)) return fail(h, BTE_E_ARG, "initial temperature %g outside [1, 5000] K", t);
+  if ((rc = ensure_memory(h))) return rc;
+  CUDA_TRY(h, cudaMemcpyAsync(h->scratch_T, T.data(), nc * 8, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, launch_init_cells((double*)h->Ibuf[h->cur], h->I0cell, h->Tp, h->TL, h->EL, h->scratch_T,
+                                h->cell0[geom], (int)nc, h->nd, thermo(h), h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->init_set[geom] = true;
+  h->TL_valid = false;  // T_L is recomputed from E_L on request
+  return BTE_OK;
+}
+
+int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_stats* stats) {
+  if (!h) return BTE_E_ARG;
+  std::string why;
+  if (!h->mem_ready || !ready_to_step(h, why)) return fail(h, BTE_E_STATE, "not ready to step: %s", why.empty() ? "no state" : why.c_str());
+  if (!(dt > 0 && std::isfinite(dt))) return fail(h, BTE_E_ARG, "dt must be > 0");
+  if (nsteps < 0) return fail(h, BTE_E_ARG, "nsteps must be >= 0");
+  if (scheme != BTE_IMPLICIT_JACOBI && scheme != BTE_EXPLICIT) return fail(h, BTE_E_ARG, "unknown scheme %d", scheme);
+  if (scheme == BTE_EXPLICIT) ninner = 1;
+  if (ninner < 1) return fail(h, BTE_E_ARG, "ninner must be >= 1");
+  int rc = ensure_coef(h, dt, scheme);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  if (stats) {
+    CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, sizeof(DevCounters), s));
+    CUDA_TRY(h, cudaEventRecord(h->ev0, s));
+  }
+  SweepArgs a{};
+  a.I0cell = h->I0cell;
+  a.Tp = h->Tp;
+  a.EL = h->EL;
+  a.I0wall = h->I0wall;
+  a.coef = h->coef;
+  a.dirs = h->dirs_d;
+  a.wdir = h->wdir;
+  a.geoms = h->geoms_d;
+  a.items = h->items_d;
+  a.nitems = (int)h->items.size();
+  a.nd = h->nd;
+  a.lpc = h->lpc;
+  a.solve_tp = h->solve_tp ? 1 : 0;
+  a.accept_rel = std::cbrt(h->opts.newton_rtol / 4.0);
+  a.maxit = h->opts.newton_maxit;
+  a.counters = h->counters;
+  a.th = thermo(h);
+  int dim = 2;
+  for (auto& g : h->geoms) dim = std::max(dim, g.dim);
+  const int grid = (int)std::min<size_t>(h->items.size(), 65535);
+  int launches = 0;
+  for (int st = 0; st < nsteps; ++st) {
+    const int n = h->cur;
+    int k = n;
+    for (int it = 0; it < ninner; ++it) {
+      int o = 0;
+      while (o == n || o == k) ++o;
+      a.In = h->Ibuf[n];
+      a.Ik = h->Ibuf[k];
+      a.Iout = h->Ibuf[o];
+      CUDA_TRY(h, launch_sweep_fp64(a, dim, h->threads, grid, s));
+      ++launches;
+      k = o;
+    }
+    h->cur = k;
+  }
+  if (nsteps > 0) h->TL_valid = false;
+  if (stats) {
+    CUDA_TRY(h, cudaEventRecord(h->ev1, s));
+    CUDA_TRY(h, cudaEventSynchronize(h->ev1));
+    DevCounters c;
+    CUDA_TRY(h, cudaMemcpy(&c, h->counters, sizeof c, cudaMemcpyDeviceToHost));
+    float ms = 0.f;
+    CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    stats->updates = (long long)h->ncells * h->nd * h->nb * (long long)ninner * nsteps;
+    stats->solve_evals = (long long)c.evals;
+    stats->solves = (long long)c.solves;
+    stats->fallbacks = (long long)c.fallbacks;
+    stats->nonfinite = (long long)c.nonfinite;
+    stats->launches = launches;
+    stats->gpu_ms = ms;
+    if (c.nonfinite) return fail(h, BTE_E_NONFINITE, "%llu cells had a non-finite energy or no temperature in [1, 5000] K", (unsigned long long)c.nonfinite);
+    if (c.fallbacks) return BTE_W_FALLBACK;
+  }
+  return BTE_OK;
+}
+
+int bte_get_T(bte_handle h, int geom, int which, double* out, int on_device) {
+  int rc = check_geom(h, geom);
+  if (rc) return rc;
+  if (!out) return fail(h, BTE_E_ARG, "out is NULL");
+  if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "geometry %d has no state", geom);
+  if (which != BTE_T_PSEUDO && which != BTE_T_LATTICE) return fail(h, BTE_E_ARG, "which must be BTE_T_PSEUDO or BTE_T_LATTICE");
+  const bte_geom& g = h->geoms[geom];
+  const size_t nc = (size_t)g.nx * g.ny * g.nz;
+  const double* src;
+  if (which == BTE_T_PSEUDO && h->solve_tp) {
+    src = h->Tp;
+  } else {
+    if ((rc = ensure_TL(h))) return rc;
+    src = h->TL;
+  }
+  return copy_out(h, out, src + h->cell0[geom], nc, on_device);
+}
+
+int bte_get_flux(bte_handle h, int geom, double* q_cells, double* q_walls, int on_device) {
+  int rc = check_geom(h, geom);
+  if (rc) return rc;
+  if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "geometry %d has no state", geom);
+  const bte_geom& g = h->geoms[geom];
+  const int nc = g.nx * g.ny * g.nz;
+  const double* I = (const double*)h->Ibuf[h->cur];
+  cudaStream_t s = h->stream;
+  if (q_cells) {
+    if (on_device) {
+      CUDA_TRY(h, launch_flux_cells(I, q_cells, h->dirs_d, h->Sdev, h->cell0[geom], nc, h->nd, h->nbp, g.dim, s));
+    } else {
+      CUDA_TRY(h, launch_flux_cells(I, h->scratch_q, h->dirs_d, h->Sdev, h->cell0[geom], nc, h->nd, h->nbp, g.dim, s));
+      CUDA_TRY(h, cudaMemcpyAsync(q_cells, h->scratch_q, (size_t)nc * g.dim * 8, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  if (q_walls) {
+    double res[6] = {0, 0, 0, 0, 0, 0};
+    for (int side = 0; side < 2 * g.dim; ++side) {
+      const int nf = (int)side_faces(g, side);
+      CUDA_TRY(h, launch_flux_faces(I, h->I0wall, h->geoms_d, geom, side, h->dirs_d, h->Sdev, h->nd, h->nbp,
+                                    h->scratch_faces, nf, s));
+      CUDA_TRY(h, launch_mean(h->scratch_faces, nf, h->scratch_out + side, s));
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(res, h->scratch_out, 2 * g.dim * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    if (on_device) CUDA_TRY(h, cudaMemcpy(q_walls, res, 2 * g.dim * 8, cudaMemcpyHostToDevice));
+    else std::memcpy(q_walls, res, 2 * g.dim * 8);
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  return BTE_OK;
+}
+
+int bte_get_intensity(bte_handle h, int geom, double* out, int on_device) {
+  int rc = check_geom(h, geom);
+  if (rc) return rc;
+  if (!out) return fail(h, BTE_E_ARG, "out is NULL");
+  if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "geometry %d has no state", geom);
+  const bte_geom& g = h->geoms[geom];
+  const long long nc = (long long)g.nx * g.ny * g.nz;
+  const double* I = (const double*)h->Ibuf[h->cur] + h->cell0[geom] * h->nd * h->nbp;
+  if (on_device) {
+    CUDA_TRY(h, launch_pack_fp64(I, out, nc, h->nd, h->nb, h->nbp, 0, h->stream));
+  } else {
+    CUDA_TRY(h, cudaMemcpy2DAsync(out, h->nb * 8, I, h->nbp * 8, h->nb * 8, (size_t)nc * h->nd, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return BTE_OK;
+}
+
+int bte_set_intensity(bte_handle h, int geom, const double* in, const double* Tp_cells, int on_device) {
+  int rc = check_geom(h, geom);
+  if (rc) return rc;
+  if (!in || !Tp_cells) return fail(h, BTE_E_ARG, "in and Tp_cells are required");
+  if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "bte_set_initial must come first for geometry %d", geom);
+  const bte_geom& g = h->geoms[geom];
+  const long long nc = (long long)g.nx * g.ny * g.nz;
+  double* I = (double*)h->Ibuf[h->cur] + h->cell0[geom] * h->nd * h->nbp;
+  cudaStream_t s = h->stream;
+  if (on_device) {
+    CUDA_TRY(h, launch_pack_fp64(in, I, nc, h->nd, h->nb, h->nbp, 1, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->Tp + h->cell0[geom], Tp_cells, nc * 8, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CUDA_TRY(h, cudaMemcpy2DAsync(I, h->nbp * 8, in, h->nb * 8, h->nb * 8, (size_t)nc * h->nd, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->Tp + h->cell0[geom], Tp_cells, nc * 8, cudaMemcpyHostToDevice, s));
+  }
+  CUDA_TRY(h, launch_I0_from_T(h->I0cell + h->cell0[geom] * h->nbp, h->Tp + h->cell0[geom], nc, thermo(h), s));
+  CUDA_TRY(h, launch_energy_L(I, h->EL + h->cell0[geom], h->wdir, nc, h->nd, thermo(h), s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  h->TL_valid = false;
+  return BTE_OK;
+}
+
+int bte_get_directions(bte_handle h, double* S, double* w, int* refl) {
+  if (!h) return BTE_E_ARG;
+  if (S) std::memcpy(S, h->S.data(), h->S.size() * 8);
+  if (w) std::memcpy(w, h->w.data(), h->w.size() * 8);
+  if (refl) std::memcpy(refl, h->refl.data(), h->refl.size() * sizeof(int));
+  return h->nd;
+}
+
+int bte_destroy(bte_handle h) {
+  if (!h) return BTE_E_ARG;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  if (h->ws_owned && h->ws) cudaFree(h->ws);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+  return BTE_OK;
+}
+
+const char* bte_last_error(bte_handle h) {
+  if (!h) return g_init_err.c_str();
+  return h->err.c_str();
+}
+
+}  // extern "C"

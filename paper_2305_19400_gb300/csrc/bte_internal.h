@@ -1,0 +1,117 @@
+// bte_internal.h -- definitions shared by the library's own translation units.
+//
+// Device data layout (all in one workspace, see bte_capi.cu):
+//   I buffers      3 x [cell][dir][nbp]      storage type per precision mode
+//   I0cell         [cell][nbp]  double        I0_b(T_p) of every cell
+//   Tp, TL, EL     [cell]       double        temperatures, lattice energy
+//   I0wall         [wall face][nbp] double    Eq. 6 ghost for isothermal faces
+//   coef           [class][5][dir][nbp] double  sweep coefficients (A_n, A_x, A_y, A_z, A_s)
+//   node_c, node_C [nbp][ng]    double        Gauss nodes: hbar*omega/kB and weights
+//   per-band / per-direction / per-geometry tables, work list, counters.
+// nbp is nb rounded up to a multiple of 8, so one (cell, dir) row is a whole
+// number of 16-byte vectors in every precision.  Padding bands carry zero
+// coefficients and stay zero.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace bte {
+
+constexpr double kHbar = 1.054571817e-34;  // J s (CODATA 2018)
+constexpr double kBoltz = 1.380649e-23;    // J/K (CODATA 2018, exact)
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxGauss = 32;
+constexpr int kMaxBands = 256;
+constexpr double kTmin = 1.0, kTmax = 5000.0;  // bracket of the temperature solves
+
+enum Side { XLO = 0, XHI = 1, YLO = 2, YHI = 3, ZLO = 4, ZHI = 5 };
+
+// One geometry as the kernels see it.
+struct DevGeom {
+  int nx, ny, nz, dim;
+  long long cell0;        // global index of the first cell
+  long long face0[6];     // first global wall-face row of each side (isothermal sides)
+  int bc[6];              // BTE_BC_* per side
+  int cls;                // coefficient-table class (cells with equal dx, dy, dz)
+  int pad;
+};
+
+// A run of consecutive cells of one geometry processed by one CTA.
+struct WorkItem {
+  int geom;
+  int cell_begin;  // local cell index
+  int cell_count;
+  int pad;
+};
+
+// Per direction: bit a of `up` set when S_{d,a} > 0 (upwind neighbour on the low
+// side along axis a); mirror directions across x, y, z walls.
+struct DirInfo {
+  int up;
+  int rx, ry, rz;
+};
+
+// Counters written by the kernels (atomics), read back for bte_stats.
+struct DevCounters {
+  unsigned long long evals;
+  unsigned long long solves;
+  unsigned long long fallbacks;
+  unsigned long long nonfinite;
+};
+
+struct ThermoTables {
+  const double* node_c;   // [nbp][ng] hbar*omega_i/kB (K)
+  const double* node_C;   // [nbp][ng] I0_b(T) = sum_i node_C / expm1(node_c / T)
+  const double* a_p;      // [nbp] W beta_b / v_b  (T_p equation weights)
+  const double* a_L;      // [nbp] W / v_b         (T_L equation weights)
+  const double* inv_v;    // [nbp] 1/v_b (0 on padding)
+  const double* beta;     // [nbp]
+  int ng;
+  int nbp;
+  int nb;
+};
+
+struct SweepArgs {
+  const void* In;       // I^n   (storage type)
+  const void* Ik;       // I^k   (storage type; == In for explicit)
+  void* Iout;           // I^{k+1}
+  double* I0cell;       // in: I0^k, out: I0^{k+1}
+  double* Tp;           // in/out
+  double* EL;           // out
+  const double* I0wall;
+  const double* coef;   // [cls][5][nd][nbp]
+  const DirInfo* dirs;
+  const double* wdir;   // [nd]
+  const DevGeom* geoms;
+  const WorkItem* items;
+  int nitems;
+  int nd;
+  int lpc;              // lanes per cell = nbp / values-per-lane
+  int solve_tp;         // 0 when every beta_b == 0 (T_p then unused)
+  double accept_rel;    // accept a Halley step + Taylor I0 refresh when |dT| <= accept_rel*T
+  int maxit;
+  DevCounters* counters;
+  ThermoTables th;
+};
+
+// Launchers (bte_kernels.cu)
+cudaError_t launch_sweep_fp64(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
+cudaError_t launch_init_cells(double* I, double* I0cell, double* Tp, double* TL, double* EL, const double* Tcells,
+                              long long cell0, int ncells, int nd, ThermoTables th, cudaStream_t s);
+cudaError_t launch_wall_I0(double* I0wall, const double* Tfaces, long long nfaces, ThermoTables th, cudaStream_t s);
+cudaError_t launch_solve_TL(double* TL, const double* EL, const double* Tguess, long long ncells, ThermoTables th,
+                            double rtol, int maxit, DevCounters* counters, cudaStream_t s);
+cudaError_t launch_flux_cells(const double* I, double* q, const DirInfo* dirs, const double* S, long long cell0,
+                              int ncells, int nd, int nbp, int dim, cudaStream_t s);
+cudaError_t launch_flux_faces(const double* I, const double* I0wall, const DevGeom* geoms, int geom, int side,
+                              const DirInfo* dirs, const double* S, int nd, int nbp, double* face_out, int nfaces,
+                              cudaStream_t s);
+cudaError_t launch_mean(const double* v, int n, double* out, cudaStream_t s);
+cudaError_t launch_I0_from_T(double* I0cell, const double* Tp, long long ncells, ThermoTables th, cudaStream_t s);
+cudaError_t launch_pack_fp64(const double* src, double* dst, long long ncells, int nd, int nb, int nbp, int to_padded,
+                             cudaStream_t s);
+cudaError_t launch_energy_L(const double* I, double* EL, const double* wdir, long long ncells, int nd, ThermoTables th,
+                            cudaStream_t s);
+
+}  // namespace bte

@@ -1,0 +1,307 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bar (FP64 mode): temperatures within rel 1e-12, intensities within rel 1e-11,
+fluxes within 1e-11 of the absolute flux sum sum_{d,b} |S_d| I_{d,b} of each
+cell (the size of the terms that cancel in q).  Sizes are chosen so the oracle
+finishes in seconds while the grid spans many CTA tiles and a ragged last
+tile; one test runs the full 128x128 x 400 x 55 grid in the benchmark's launch
+configuration and checks sampled outputs one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2305_19400_gb300 import bte, workloads as W
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+RTOL_T = 1e-12
+RTOL_I = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2305_19400_gb300 import build as B
+    B.build()
+    O.build()
+
+
+def oracle_run(wl, geom_index=0, T_init=None, nsteps=None, ninner=None, scheme=O.IMPLICIT, dt=None):
+    g = wl.geoms[geom_index]
+    p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands)
+    st = p.init_state(g.T_init if T_init is None else T_init)
+    p.run(st, wl.dt if dt is None else dt, wl.nsteps if nsteps is None else nsteps,
+          wl.ninner if ninner is None else ninner, scheme)
+    return p, st
+
+
+def assert_close_T(got, ref, rtol=RTOL_T, what="T"):
+    err = np.max(np.abs(got - ref) / np.abs(ref))
+    assert err <= rtol, f"{what}: max rel err {err:.3e} > {rtol:.0e}"
+    return err
+
+
+def assert_close_I(got, ref, rtol=RTOL_I):
+    err = np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300))
+    assert err <= rtol, f"I: max rel err {err:.3e}"
+    return err
+
+
+def assert_close_flux(p, I_ref, q, qw, q_ref, qw_ref, tol=1e-11):
+    S = p.S
+    scale = np.einsum("da,cdb->ca", np.abs(S[:, : q.shape[1]]), np.abs(I_ref))   # per cell, per axis
+    assert np.all(np.abs(q - q_ref) <= tol * scale), np.max(np.abs(q - q_ref) / scale)
+    wall_scale = scale.max()
+    assert np.all(np.abs(qw - qw_ref) <= tol * wall_scale)
+
+
+def gpu_run(wl, T_init=None, nsteps=None, ninner=None, scheme=bte.BTE_IMPLICIT_JACOBI, dt=None, **kw):
+    s = bte.Solver(wl, T_init=T_init, **kw)
+    rc, st = s.step(nsteps=nsteps, ninner=ninner, dt=dt, scheme=scheme)
+    return s, rc, st
+
+
+# --------------------------------------------------------------------------
+def test_cfg1_full_run_matches_oracle():
+    """2-D 20x20, 16 in-plane directions, 4 bands, 100 steps x 10 inner iterations."""
+    wl = W.cfg1()
+    s, rc, st = gpu_run(wl)
+    assert rc == 0 and st["nonfinite"] == 0
+    assert st["launches"] == 1000
+    p, ost = oracle_run(wl)
+    assert_close_T(s.T(0, bte.BTE_T_LATTICE), ost["TL"], what="T_L")
+    assert_close_T(s.T(0, bte.BTE_T_PSEUDO), ost["Tp"], what="T_p")
+    I = s.intensity(0)
+    assert_close_I(I, ost["I"])
+    q, qw = s.flux(0)
+    q_ref, qw_ref = p.flux(ost["I"])
+    assert_close_flux(p, ost["I"], q, qw, q_ref, qw_ref)
+    # the hot wall heated the domain, and T_L != T_p away from equilibrium
+    assert ost["TL"].max() > 300.5
+    s.close()
+
+
+def test_cfg2_shape_reduced_grid_matches_oracle():
+    """400 directions x 55 band-pols on a ragged 19x13 grid with the hot-spot wall."""
+    wl = W.cfg2(19, 13)
+    s, rc, st = gpu_run(wl, nsteps=3, ninner=15)
+    assert rc == 0
+    p, ost = oracle_run(wl, nsteps=3, ninner=15)
+    assert_close_T(s.T(0, bte.BTE_T_LATTICE), ost["TL"], what="T_L")
+    assert_close_T(s.T(0, bte.BTE_T_PSEUDO), ost["Tp"], what="T_p")
+    assert_close_I(s.intensity(0), ost["I"])
+    q, qw = s.flux(0)
+    q_ref, qw_ref = p.flux(ost["I"])
+    assert_close_flux(p, ost["I"], q, qw, q_ref, qw_ref)
+    s.close()
+
+
+def test_explicit_scheme_matches_oracle():
+    wl = W.cfg1()
+    T0 = W.random_temperatures(400, 21, 295.0, 305.0)
+    s, rc, st = gpu_run(wl, T_init=[T0], nsteps=40, ninner=1, scheme=bte.BTE_EXPLICIT, dt=2e-13)
+    assert st["launches"] == 40
+    p, ost = oracle_run(wl, T_init=T0, nsteps=40, ninner=1, scheme=O.EXPLICIT, dt=2e-13)
+    assert_close_T(s.T(0, bte.BTE_T_LATTICE), ost["TL"], what="T_L")
+    assert_close_T(s.T(0, bte.BTE_T_PSEUDO), ost["Tp"], what="T_p")
+    assert_close_I(s.intensity(0), ost["I"])
+    s.close()
+
+
+def test_3d_mixed_walls_matches_oracle():
+    g = W.Geometry(3, 5, 4, 3, 10e-9, 8e-9, 12e-9)
+    g.bc = [(W.BC_ISOTHERMAL, np.full(12, 300.0)), (W.BC_ISOTHERMAL, W.random_temperatures(12, 5, 300.0, 310.0)),
+            (W.BC_SPECULAR, None), (W.BC_SPECULAR, None),
+            (W.BC_ISOTHERMAL, np.full(20, 302.0)), (W.BC_SPECULAR, None)]
+    wl = W.Workload("3d", [g], W.Dirs("polar_azim", n_polar=4, n_azim=8), W.make_bands(40, 15, 19403), 1e-12, 3, 6)
+    T0 = W.random_temperatures(60, 6, 298.0, 303.0)
+    s, rc, st = gpu_run(wl, T_init=[T0])
+    p, ost = oracle_run(wl, T_init=T0)
+    assert_close_T(s.T(0, bte.BTE_T_LATTICE), ost["TL"], what="T_L")
+    assert_close_T(s.T(0, bte.BTE_T_PSEUDO), ost["Tp"], what="T_p")
+    assert_close_I(s.intensity(0), ost["I"])
+    q, qw = s.flux(0)
+    q_ref, qw_ref = p.flux(ost["I"])
+    assert_close_flux(p, ost["I"], q, qw, q_ref, qw_ref)
+    s.close()
+
+
+def test_several_geometries_in_one_handle_match_oracle_one_by_one():
+    geoms = []
+    for (nx, ny, th) in ((7, 5, 312.0), (1, 1, 305.0), (13, 3, 301.5), (2, 9, 318.0)):
+        g = W.Geometry(2, nx, ny, 1, 10e-9, 10e-9, 10e-9)
+        W.uniform_walls(g, [W.BC_ISOTHERMAL, W.BC_ISOTHERMAL, W.BC_SPECULAR, W.BC_SPECULAR], [th, 300.0, 0, 0])
+        geoms.append(g)
+    geoms[2].dx = 7e-9  # a second cell-size class
+    wl = W.Workload("batch", geoms, W.Dirs("inplane", n_inplane=16), W.make_bands(40, 15, 19405), 1e-12, 4, 5)
+    s, rc, st = gpu_run(wl)
+    for gi in range(len(geoms)):
+        p, ost = oracle_run(wl, geom_index=gi)
+        assert_close_T(s.T(gi, bte.BTE_T_LATTICE), ost["TL"], what=f"T_L[{gi}]")
+        assert_close_T(s.T(gi, bte.BTE_T_PSEUDO), ost["Tp"], what=f"T_p[{gi}]")
+        assert_close_I(s.intensity(gi), ost["I"])
+    s.close()
+
+
+def test_ballistic_slab_on_gpu_reaches_casimir_flux():
+    """All beta_b = 0: the T_p solve is skipped and T_p reports T_L."""
+    bands = W.make_bands(4, 0, 5)
+    bands.beta[:] = 0.0
+    g = W.Geometry(2, 5, 1, 1, 10e-9, 10e-9, 10e-9)
+    g.bc = [(W.BC_ISOTHERMAL, np.array([310.0])), (W.BC_ISOTHERMAL, np.array([300.0])),
+            (W.BC_SPECULAR, None), (W.BC_SPECULAR, None)]
+    g.T_init = 300.0
+    wl = W.Workload("casimir", [g], W.Dirs("inplane", n_inplane=16), bands, 1e-6, 4, 300)
+    s, rc, st = gpu_run(wl)
+    q, qw = s.flux(0)
+    Mplus = (4 * math.pi / 16) / math.sin(math.pi / 16)
+    exact = float(np.sum(O.I0(bands, 310.0)[0] - O.I0(bands, 300.0)[0])) * Mplus
+    assert np.all(np.abs(q[:, 0] - exact) <= 1e-10 * exact)
+    assert abs(qw[1] - exact) <= 1e-10 * exact
+    assert np.array_equal(s.T(0, bte.BTE_T_PSEUDO), s.T(0, bte.BTE_T_LATTICE))
+    s.close()
+
+
+def test_specular_enclosure_conserves_energy_on_gpu():
+    g = W.Geometry(2, 9, 7, 1, 10e-9, 10e-9, 10e-9)
+    W.uniform_walls(g, [W.BC_SPECULAR] * 4, [0] * 4)
+    wl = W.Workload("box", [g], W.Dirs("polar_azim", n_polar=4, n_azim=8), W.make_bands(40, 15, 3), 2e-13, 200, 1)
+    T0 = W.random_temperatures(63, 9, 290.0, 310.0)
+    s = bte.Solver(wl, T_init=[T0])
+    p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands)
+    E0 = sum(p.cell_energy(r)[0] for r in s.intensity(0))
+    s.step(scheme=bte.BTE_EXPLICIT)
+    E1 = sum(p.cell_energy(r)[0] for r in s.intensity(0))
+    assert abs(E1 - E0) <= 1e-13 * E0
+    s.close()
+
+
+def test_restart_from_checkpoint_continues_the_run():
+    wl = W.cfg2(9, 6)
+    a = bte.Solver(wl)
+    a.step(nsteps=2, ninner=5)
+    I_ck, Tp_ck = a.intensity(0), a.T(0, bte.BTE_T_PSEUDO)
+    a.step(nsteps=2, ninner=5)
+    b = bte.Solver(wl)
+    bte.bte_set_intensity(b.h, 0, I_ck, Tp_ck)
+    b.step(nsteps=2, ninner=5)
+    assert_close_T(b.T(0, bte.BTE_T_LATTICE), a.T(0, bte.BTE_T_LATTICE), rtol=1e-14)
+    assert_close_I(b.intensity(0), a.intensity(0), rtol=1e-13)
+    a.close(); b.close()
+
+
+def test_runs_are_deterministic_and_workspace_binding_does_not_matter():
+    wl = W.cfg2(11, 10)
+    a = bte.Solver(wl)
+    a.step(nsteps=2, ninner=4)
+    b = bte.Solver(wl, bind_workspace=False)
+    b.step(nsteps=2, ninner=4)
+    assert np.array_equal(a.intensity(0), b.intensity(0))
+    assert np.array_equal(a.T(0, bte.BTE_T_PSEUDO), b.T(0, bte.BTE_T_PSEUDO))
+    a.close(); b.close()
+
+
+def test_call_order_and_argument_errors():
+    wl = W.cfg1()
+    g = wl.geoms[0]
+    h = bte.bte_init_mesh([bte.bte_geom(2, g.nx, g.ny, 1, g.dx, g.dy, g.dz)],
+                          _opts_inplane(16))
+    with pytest.raises(bte.BTEError) as e:
+        bte.bte_set_bc(h, 0, 0, bte.BTE_BC_ISOTHERMAL, None, 300.0)
+    assert e.value.code == -2                      # bands first
+    b = wl.bands
+    bte.bte_set_bands(h, b.omega_lo, b.omega_hi, b.vg, b.beta, b.degeneracy)
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(bte.BTEError) as e:
+        bte.bte_bind_workspace(h, small)
+    assert e.value.code == -4                      # too small
+    with pytest.raises(bte.BTEError) as e:
+        bte.bte_step(h, 1e-12, 1, 1)
+    assert e.value.code == -2                      # no state yet
+    with pytest.raises(bte.BTEError) as e:
+        bte.bte_set_bc(h, 0, 4, bte.BTE_BC_SPECULAR)
+    assert e.value.code == -1                      # no z side in 2-D
+    with pytest.raises(bte.BTEError) as e:
+        bte.bte_set_bc(h, 0, 0, bte.BTE_BC_ISOTHERMAL, None, 6000.0)
+    assert e.value.code == -1
+    for side in range(4):
+        bte.bte_set_bc(h, 0, side, bte.BTE_BC_ISOTHERMAL, None, 300.0)
+    with pytest.raises(bte.BTEError) as e:
+        bte.bte_step(h, 1e-12, 1, 1)
+    assert e.value.code == -2                      # initial state missing
+    bte.bte_set_initial(h, 0, None, 300.0)
+    with pytest.raises(bte.BTEError) as e:
+        bte.bte_step(h, -1.0, 1, 1)
+    assert e.value.code == -1
+    rc, st = bte.bte_step(h, 1e-12, 1, 1)
+    assert rc == 0 and st["launches"] == 1
+    bte.bte_destroy(h)
+
+
+def _opts_inplane(n):
+    o = bte.bte_default_opts()
+    o.dir_kind, o.n_inplane = bte.BTE_DIRS_INPLANE, n
+    o.cuda_stream = torch.cuda.current_stream().cuda_stream
+    return o
+
+
+# ------------------------------------------------------------ full size
+@pytest.fixture(scope="module")
+def full_cfg2():
+    """The benchmark's workload and launch configuration: 128x128 x 400 x 55, FP64."""
+    wl = W.cfg2()
+    s = bte.Solver(wl)
+    s.step(nsteps=2, ninner=15)
+    yield wl, s
+    s.close()
+
+
+def test_full_size_single_iteration_sampled_against_oracle(full_cfg2):
+    wl, s = full_cfg2
+    g = wl.geoms[0]
+    I_n = s.intensity(0)
+    Tp_n = s.T(0, bte.BTE_T_PSEUDO)
+    rc, st = s.step(nsteps=1, ninner=1)
+    I_1 = s.intensity(0)
+    Tp_1 = s.T(0, bte.BTE_T_PSEUDO)
+    TL_1 = s.T(0, bte.BTE_T_LATTICE)
+    p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands)
+    rng = np.random.default_rng(1)
+    nc, nd, nb = I_n.shape
+    # cells: random interior ones plus every corner and edge-middle cell, ragged tile boundaries included
+    cells = set(rng.integers(0, nc, 40).tolist())
+    cells |= {0, g.nx - 1, nc - g.nx, nc - 1, g.nx // 2, nc - g.nx // 2, (g.ny // 2) * g.nx, (g.ny // 2) * g.nx + g.nx - 1}
+    I0 = np.zeros((nc, nb))
+    for P in cells:
+        I0[P] = O.I0(wl.bands, Tp_n[P])[0]
+    I0w = p.wall_I0()
+    worst = 0.0
+    for P in sorted(cells):
+        for d in rng.integers(0, nd, 12):
+            for b in rng.integers(0, nb, 4):
+                ref = p.update_one(wl.dt, O.IMPLICIT, I_n, I_n, I0, I0w, P, d, b)
+                worst = max(worst, abs(I_1[P, d, b] - ref) / abs(ref))
+        Tp_ref, TL_ref = p.cell_temperatures(I_1[P], Tp_n[P], Tp_n[P])
+        assert abs(Tp_1[P] - Tp_ref) <= RTOL_T * Tp_ref
+        assert abs(TL_1[P] - TL_ref) <= RTOL_T * TL_ref
+    assert worst <= 1e-12, worst
+
+
+def test_full_size_equilibrium_is_preserved():
+    wl = W.cfg2()
+    g = wl.geoms[0]
+    g.bc = [(W.BC_ISOTHERMAL, np.full(g.ny, 300.0)), (W.BC_ISOTHERMAL, np.full(g.ny, 300.0)),
+            (W.BC_SPECULAR, None), (W.BC_SPECULAR, None)]
+    s = bte.Solver(wl)
+    s.step(nsteps=1, ninner=15)
+    assert np.max(np.abs(s.T(0, bte.BTE_T_PSEUDO) - 300.0)) <= 1e-13 * 300
+    assert np.max(np.abs(s.T(0, bte.BTE_T_LATTICE) - 300.0)) <= 1e-13 * 300
+    q, qw = s.flux(0)
+    I0 = O.I0(wl.bands, 300.0)[0]
+    assert np.max(np.abs(q)) <= 1e-12 * 4 * math.pi * I0.sum()
+    s.close()
