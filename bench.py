@@ -1,0 +1,330 @@
+"""Throughput benchmark of the phonon-BTE hot path (cell*direction*band updates/s).
+
+Workload (default): 2-D 128x128 cells, 400 directions (20 polar x 20 azimuthal),
+55 band-polarisations, FP64 intensities, hot-spot wall, implicit Euler with 15
+point-Jacobi inner iterations per time step.  One benchmark step is one time
+step: 15 inner iterations, each the fused sweep (upwind fluxes, wall ghosts,
+relaxation), per-cell reduction, T_p solve and I0 refresh.
+
+Arms:
+  (default)          the CUDA library, inputs resident in HBM, CUDA-event timing.
+  --impl reference   the plain FP64 CPU oracle on this machine's host cores, on a
+                     bounded sub-grid sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run; every rank runs one replica of the
+workload on its own GPU (the path has no exchange step between replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell·dir·band updates/s and % HBM roofline at stated max|ΔT| vs FP64 oracle"
+UNIT = "updates/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_2305_19400_gb300", "csrc", "bte_kernels.cu")
+# FP64 pipe peak: the nominal 1.25 TFLOP/s corresponds to 2 DFMA/clk/SM on 152 SMs at 2070 MHz.
+FP64_PEAK_FLOPS = 2 * 2 * 152 * 2.070e9
+# Algorithmic work of one 2-D implicit update: A_n*I^n + A_x*I_x + A_y*I_y + A_s*I0 (4 mul + 3 add)
+# and the reduction G_b += w_d*I (1 mul + 1 add); bytes: I^n read, I^k read once, I^{k+1} written.
+FLOPS_PER_UPDATE_2D = 9
+BYTES_PER_UPDATE_FP64 = 24
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=128)
+    ap.add_argument("--ny", type=int, default=128)
+    ap.add_argument("--ninner", type=int, default=15)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def read_peaks():
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_per_update():
+    """DRAM bytes per update of the sweep from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None
+    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    if rec.get("kernel_source_sha") != sha:
+        return None
+    return rec.get("dram_bytes_per_update")
+
+
+# ----------------------------------------------------------------------------- reference arm
+def reference_sample(nx_sub=16, ny_sub=16):
+    from paper_2305_19400_gb300 import workloads as W
+    wl = W.cfg2(nx_sub, ny_sub, nsteps=1, ninner=15)
+    return wl
+
+
+def run_oracle_sample(wl):
+    """One time step (15 inner iterations) of the oracle on the sample; returns (updates, seconds)."""
+    from oracle import oracle as O
+    g = wl.geoms[0]
+    p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands)
+    st = p.init_state(g.T_init)
+    t0 = time.perf_counter()
+    p.run(st, wl.dt, wl.nsteps, wl.ninner)
+    return wl.updates, time.perf_counter() - t0
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    wl = reference_sample()
+    for _ in range(args.warmup):
+        run_oracle_sample(wl)
+    tot_u, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        u, s = run_oracle_sample(wl)
+        tot_u += u
+        tot_s += s
+    v = tot_u / tot_s
+    cores = O.num_threads()
+    sample = (f"{wl.geoms[0].nx}x{wl.geoms[0].ny} sub-grid of the 128x128 workload (same directions, bands, walls), "
+              f"1 time step x {wl.ninner} inner iterations per benchmark step")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "2d_128x128_400dir_55band_fp64", "sample": sample},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def cpu_baseline_for(args):
+    """The oracle as it stands on this host's cores: the full grid for one time step
+    (15 inner iterations), about 10-30 s of CPU work."""
+    from oracle import oracle as O
+    from paper_2305_19400_gb300 import workloads as W
+    O.build()
+    wl = W.cfg2(args.nx, args.ny, nsteps=1, ninner=args.ninner)
+    u, s = run_oracle_sample(wl)
+    return {"value": u / s, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"full {args.nx}x{args.ny} grid, 1 time step x {args.ninner} inner iterations ({u:.3g} updates, {s:.1f} s)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    world, rank, local = dist_env()
+    import numpy as np
+    import torch
+
+    from paper_2305_19400_gb300 import build as B, bte, workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    wl = W.cfg2(args.nx, args.ny, nsteps=1, ninner=args.ninner)
+    g = wl.geoms[0]
+    solver = bte.Solver(wl, stream=stream)
+    updates_per_step = wl.dof * args.ninner
+
+    def step():
+        rc, st = bte.bte_step(solver.h, wl.dt, 1, args.ninner, bte.BTE_IMPLICIT_JACOBI, want_stats=False)
+        return rc
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    launches = args.steps * args.ninner
+    value = world * updates_per_step * args.steps / (ms_max * 1e-3)
+
+    # sanity: the state is finite and physical after the timed run
+    TL = solver.T(0, bte.BTE_T_LATTICE)
+    assert np.all(np.isfinite(TL)) and TL.min() > 299.0 and TL.max() < 311.0, (TL.min(), TL.max())
+
+    # ---- end to end through the C ABI with host buffers: per step, the hot-wall
+    # temperatures go host->device (bte_set_bc), one time step runs, and the
+    # lattice temperatures come back device->host (bte_get_T).
+    e2e = None
+    if not args.no_e2e:
+        Tw = torch.from_numpy(W.hot_spot_profile(g.ny, 300.0, 10.0, 8.0)).pin_memory()
+        Tout = torch.empty(g.ncells, dtype=torch.float64).pin_memory()
+        import ctypes as C
+        L = bte.lib()
+        twp = C.cast(C.c_void_p(Tw.data_ptr()), C.POINTER(C.c_double))
+        k_e2e = max(3, min(args.steps, 20))
+        for _ in range(2):
+            L.bte_set_bc(solver.h, 0, 0, bte.BTE_BC_ISOTHERMAL, twp, 300.0)
+            step()
+            L.bte_get_T(solver.h, 0, bte.BTE_T_LATTICE, C.c_void_p(Tout.data_ptr()), 0)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            rc = L.bte_set_bc(solver.h, 0, 0, bte.BTE_BC_ISOTHERMAL, twp, 300.0)
+            assert rc == 0, bte.bte_last_error(solver.h)
+            step()
+            rc = L.bte_get_T(solver.h, 0, bte.BTE_T_LATTICE, C.c_void_p(Tout.data_ptr()), 0)
+            assert rc == 0, bte.bte_last_error(solver.h)
+        dt_e2e = time.perf_counter() - t0
+        te = torch.tensor([dt_e2e], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * updates_per_step * k_e2e / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": Tw.numel() * 8, "d2h_bytes_per_step": Tout.numel() * 8, "steps": k_e2e}
+    solver.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    peaks, peak_src = read_peaks()
+    launch_s = ms_max * 1e-3 / launches
+    upd_launch = updates_per_step / args.ninner
+    flops = FLOPS_PER_UPDATE_2D * upd_launch / launch_s
+    hbm = BYTES_PER_UPDATE_FP64 * upd_launch / launch_s / 1e9
+    tpu = traffic_per_update()
+    roofline = {"bound": "alu", "achieved": flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": flops / FP64_PEAK_FLOPS,
+                "traffic": (tpu * upd_launch) if tpu else None,
+                "kernel": "sweep_fp64_kernel<2>",
+                "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
+                "hbm": {"achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"],
+                        "peak_source": f"hbm_gbs of {peak_src} peaks"}}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_for(args)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"2d_{args.nx}x{args.ny}_400dir_55band_fp64", "cells": g.ncells, "directions": 400,
+                      "band_pols": 55, "inner_iterations_per_step": args.ninner, "dt_s": wl.dt,
+                      "scheme": "implicit Euler, point-Jacobi inner iterations",
+                      "l2": "inputs larger than L2 (three FP64 intensity buffers of %.2f GB each)" % (wl.dof * 8 / 1e9),
+                      "parallelism": f"replicas x{world}"},
+           "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
