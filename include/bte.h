@@ -170,6 +170,23 @@ int bte_set_intensity(bte_handle h, int geom, const double* in, const double* Tp
  * x, y, z wall).  Host arrays; any may be NULL.  Returns nd (>0) or an error. */
 int bte_get_directions(bte_handle h, double* S, double* w, int* refl);
 
+/* Per-side mean outgoing wall flux of one geometry (the q_walls of
+ * bte_get_flux), computed without allocating device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * -- processes with a fixed device-memory budget or whose device memory is
+ * owned by another allocator, and latency-critical loops where an allocation
+ * would synchronize the device.  Its per-face scratch is a static device array
+ * inside libbte.so (65536 doubles + 8, about 512 KB, held by every GPU that
+ * loads the library until the process exits), so a wall may have at most
+ * 65536 faces (larger walls return BTE_E_ARG).  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress, once per
+ * device); make that first call before any stream capture.  All calls share
+ * the array, which keeps the last call's contents; every face slot is written
+ * before it is read, so nothing needs clearing, but calls that overlap on the
+ * GPU (other streams, other host threads) race on it.  q_walls: 2*dim doubles,
+ * host or device per out_on_device.  Waits for the handle's stream. */
+int bte_get_wall_flux_noalloc(bte_handle h, int geom, double* q_walls, int out_on_device);
+
 /* Frees everything the library allocated (not a bound workspace). */
 int bte_destroy(bte_handle h);
 

@@ -61,6 +61,7 @@ SIGNATURES = {
     "bte_get_intensity": (C.c_int, [_h, C.c_int, _vp, C.c_int]),
     "bte_set_intensity": (C.c_int, [_h, C.c_int, _vp, _vp, C.c_int]),
     "bte_get_directions": (C.c_int, [_h, _dp, _dp, _ip]),
+    "bte_get_wall_flux_noalloc": (C.c_int, [_h, C.c_int, _vp, C.c_int]),
     "bte_destroy": (C.c_int, [_h]),
     "bte_last_error": (C.c_char_p, [_h]),
 }
@@ -178,6 +179,12 @@ def bte_get_directions(h):
     S = np.zeros((nd, 3)); w = np.zeros(nd); r = np.zeros((3, nd), dtype=np.int32)
     lib().bte_get_directions(h, S.ctypes.data_as(_dp), w.ctypes.data_as(_dp), r.ctypes.data_as(_ip))
     return S, w, r
+
+
+def bte_get_wall_flux_noalloc(h, geom, q_walls):
+    """q_walls: float64 numpy array (host) or torch CUDA tensor (device), 2*dim values."""
+    on_dev = 0 if isinstance(q_walls, np.ndarray) else 1
+    return _check(h, lib().bte_get_wall_flux_noalloc(h, geom, _ptr(q_walls), on_dev))
 
 
 def bte_destroy(h):

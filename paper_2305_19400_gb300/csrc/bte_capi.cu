@@ -285,6 +285,38 @@ int copy_out(bte_ctx* h, double* out, const double* src, size_t n, int on_device
 
 }  // namespace
 
+namespace bte {
+
+int flux_view(bte_ctx* h, int geom, FluxView* out) {
+  int rc = check_geom(h, geom);
+  if (rc) return rc;
+  if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "geometry %d has no state", geom);
+  const bte_geom& g = h->geoms[geom];
+  out->I = (const double*)h->Ibuf[h->cur];
+  out->I0wall = h->I0wall;
+  out->geoms = h->geoms_d;
+  out->dirs = h->dirs_d;
+  out->S = h->Sdev;
+  out->nd = h->nd;
+  out->nbp = h->nbp;
+  out->dim = g.dim;
+  for (int s6 = 0; s6 < 6; ++s6) out->nfaces[s6] = s6 < 2 * g.dim ? (int)side_faces(g, s6) : 0;
+  out->stream = h->stream;
+  return BTE_OK;
+}
+
+int set_handle_error(bte_ctx* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  return code;
+}
+
+}  // namespace bte
+
 extern "C" {
 
 int bte_default_opts(bte_opts* o) {

@@ -16,6 +16,8 @@
 #include <cstddef>
 #include <cstdint>
 
+struct bte_ctx;
+
 namespace bte {
 
 constexpr double kHbar = 1.054571817e-34;  // J s (CODATA 2018)
@@ -113,5 +115,20 @@ cudaError_t launch_pack_fp64(const double* src, double* dst, long long ncells, i
                              cudaStream_t s);
 cudaError_t launch_energy_L(const double* I, double* EL, const double* wdir, long long ncells, int nd, ThermoTables th,
                             cudaStream_t s);
+
+// Read-only view of one geometry's device state, for entry points that live
+// outside bte_capi.cu (bte_noalloc.cu).  flux_view returns BTE_E_* codes.
+struct FluxView {
+  const double* I;        // current intensity buffer (FP64, padded rows)
+  const double* I0wall;
+  const DevGeom* geoms;
+  const DirInfo* dirs;
+  const double* S;        // [nd][3]
+  int nd, nbp, dim;
+  int nfaces[6];          // faces per side (0 for sides beyond 2*dim)
+  cudaStream_t stream;
+};
+int flux_view(bte_ctx* h, int geom, FluxView* out);
+int set_handle_error(bte_ctx* h, int code, const char* fmt, ...);
 
 }  // namespace bte
