@@ -65,13 +65,15 @@ typedef struct {
  *             BTE_DIRS_POLAR_AZIM: n_polar x n_azim control angles
  *             (n_polar even, n_azim % 4 == 0; 20 x 20 = 400 in Sec. 3.1).
  *  precision  storage of I and the sweep arithmetic: BTE_FP64 (default),
- *             BTE_FP32 or BTE_BF16; the reduction, temperature solve and I0
- *             are FP64 in every mode.
+ *             BTE_FP32 or BTE_BF16 (FP32 arithmetic); the reduction, the
+ *             temperature solve and I0 are FP64 in every mode.
  *  learned    must be 0 (warm-started Halley/Newton temperature solve).
  *  n_gauss    Gauss-Legendre points per band for I0_b(T) (default 16, <= 32).
  *  newton_rtol target relative accuracy of the temperature solve (1e-14).
  *  newton_maxit iteration cap before the bisection fallback (50).
- *  cuda_stream cudaStream_t every launch and copy uses (NULL: legacy default stream). */
+ *  cuda_stream cudaStream_t every launch and copy uses (NULL: legacy default stream).
+ *  T_ref      reference temperature of the FP32/BF16 modes, which store the
+ *             deviation I - I0_b(T_ref) (default 300 K; ignored in FP64). */
 typedef struct {
   int dir_kind;
   int n_inplane, n_polar, n_azim;
@@ -81,6 +83,7 @@ typedef struct {
   double newton_rtol;
   int newton_maxit;
   void* cuda_stream;
+  double T_ref;
 } bte_opts;
 
 /* Per-call statistics of bte_step (filled only when a non-NULL pointer is
@@ -186,6 +189,7 @@ int bte_get_directions(bte_handle h, double* S, double* w, int* refl);
  * GPU (other streams, other host threads) race on it.  q_walls: 2*dim doubles,
  * host or device per out_on_device.  Waits for the handle's stream. */
 int bte_get_wall_flux_noalloc(bte_handle h, int geom, double* q_walls, int out_on_device);
+/* (FP64-mode handles only; other precisions return BTE_E_ARG.) */
 
 /* Frees everything the library allocated (not a bound workspace). */
 int bte_destroy(bte_handle h);

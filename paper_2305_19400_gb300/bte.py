@@ -33,7 +33,7 @@ class bte_geom(C.Structure):
 class bte_opts(C.Structure):
     _fields_ = [("dir_kind", C.c_int), ("n_inplane", C.c_int), ("n_polar", C.c_int), ("n_azim", C.c_int),
                 ("precision", C.c_int), ("learned", C.c_int), ("n_gauss", C.c_int), ("newton_rtol", C.c_double),
-                ("newton_maxit", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("newton_maxit", C.c_int), ("cuda_stream", C.c_void_p), ("T_ref", C.c_double)]
 
 
 class bte_stats(C.Structure):

@@ -58,7 +58,11 @@ struct bte_ctx {
   bool ws_owned = false, mem_ready = false;
   char* Ibuf[3] = {nullptr, nullptr, nullptr};
   int cur = 0;
-  double *I0cell = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr, *I0wall = nullptr, *coef = nullptr;
+  double *I0cell = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr, *I0wall = nullptr;
+  void* coef = nullptr;
+  double *J = nullptr, *Teval = nullptr, *I0ref = nullptr, *scratch_pack = nullptr;
+  float *I0wall_dev = nullptr, *wdir32 = nullptr;
+  long long pack_cells = 0;
   double *wdir = nullptr, *Sdev = nullptr, *node_c = nullptr, *node_C = nullptr, *a_p = nullptr, *a_L = nullptr;
   double *inv_v = nullptr, *beta_d = nullptr, *scratch_faces = nullptr, *scratch_T = nullptr, *scratch_out = nullptr;
   double* scratch_q = nullptr;
@@ -104,6 +108,21 @@ long long side_faces(const bte_geom& g, int side) {
   return (long long)g.nx * g.ny;
 }
 
+ThermoTables thermo_of(const double* nc, const double* nC, const double* ap, const double* aL, const double* iv,
+                       const double* be, int ng, int nbp, int nb) {
+  ThermoTables t;
+  t.node_c = nc;
+  t.node_C = nC;
+  t.a_p = ap;
+  t.a_L = aL;
+  t.inv_v = iv;
+  t.beta = be;
+  t.ng = ng;
+  t.nbp = nbp;
+  t.nb = nb;
+  return t;
+}
+
 ThermoTables thermo(const bte_ctx* h) {
   ThermoTables t;
   t.node_c = h->node_c;
@@ -130,11 +149,16 @@ size_t carve(bte_ctx* h, char* base) {
   const size_t ibytes = (size_t)h->ncells * row * elem_bytes(h->opts.precision);
   for (int i = 0; i < 3; ++i) h->Ibuf[i] = take(ibytes);
   h->I0cell = (double*)take((size_t)h->ncells * h->nbp * 8);
+  h->J = (double*)take((size_t)h->ncells * 3 * h->nbp * 8);
+  h->Teval = (double*)take((size_t)h->ncells * 8);
+  h->I0ref = (double*)take((size_t)h->nbp * 8);
+  h->I0wall_dev = (float*)take((size_t)std::max(h->nfaces, 1LL) * h->nbp * 4);
+  h->wdir32 = (float*)take((size_t)h->nd * 4);
   h->Tp = (double*)take((size_t)h->ncells * 8);
   h->TL = (double*)take((size_t)h->ncells * 8);
   h->EL = (double*)take((size_t)h->ncells * 8);
   h->I0wall = (double*)take((size_t)std::max(h->nfaces, 1LL) * h->nbp * 8);
-  h->coef = (double*)take((size_t)h->cls_key.size() * 5 * row * 8);
+  h->coef = take((size_t)h->cls_key.size() * 5 * row * (h->opts.precision == BTE_FP64 ? 8 : 4));
   h->wdir = (double*)take((size_t)h->nd * 8);
   h->Sdev = (double*)take((size_t)h->nd * 3 * 8);
   h->dirs_d = (DirInfo*)take((size_t)h->nd * sizeof(DirInfo));
@@ -151,11 +175,15 @@ size_t carve(bte_ctx* h, char* base) {
   h->scratch_T = (double*)take((size_t)std::max(h->max_side_faces, h->max_geom_cells) * 8);
   h->scratch_out = (double*)take(64);
   h->scratch_q = (double*)take((size_t)std::max(h->max_geom_cells, 1) * 3 * 8);
+  // host <-> FP64 staging of whole cell rows for the reduced-precision modes (64 MB at most)
+  h->pack_cells = h->opts.precision == BTE_FP64 ? 0
+                : std::max(1LL, std::min<long long>(h->max_geom_cells, (64LL << 20) / ((long long)h->nd * h->nb * 8)));
+  h->scratch_pack = (double*)take((size_t)h->pack_cells * h->nd * h->nb * 8);
   return off;
 }
 
 void build_items(bte_ctx* h) {
-  h->lpc = h->nbp / 2;  // FP64: two bands per lane (double2)
+  h->lpc = h->nbp / values_per_lane(h->opts.precision);  // one 16-byte vector of bands per lane
   h->cpb = std::max(1, 256 / h->lpc);
   h->threads = h->cpb * h->lpc;
   h->items.clear();
@@ -205,6 +233,17 @@ int ensure_memory(bte_ctx* h) {
   CUDA_TRY(h, cudaMemcpyAsync(h->a_L, aL.data(), aL.size() * 8, cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaMemcpyAsync(h->inv_v, iv.data(), iv.size() * 8, cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaMemcpyAsync(h->beta_d, be.data(), be.size() * 8, cudaMemcpyHostToDevice, s));
+  {
+    std::vector<float> w32(h->w.begin(), h->w.end());
+    CUDA_TRY(h, cudaMemcpyAsync(h->wdir32, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice, s));
+    // I0_b(T_ref): the reference the reduced-precision modes store deviations from
+    const double tref = h->opts.T_ref;
+    CUDA_TRY(h, cudaMemcpyAsync(h->scratch_T, &tref, 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, launch_wall_I0(h->I0ref, h->scratch_T, 1, thermo_of(h->node_c, h->node_C, h->a_p, h->a_L, h->inv_v,
+                                                                      h->beta_d, h->ng, h->nbp, h->nb), s));
+    CUDA_TRY(h, cudaMemsetAsync(h->I0wall_dev, 0, (size_t)std::max(h->nfaces, 1LL) * h->nbp * 4, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+  }
   // geometry + work list
   std::vector<DevGeom>& dg = h->dgeoms;
   dg.assign(h->geoms.size(), DevGeom{});
@@ -246,7 +285,12 @@ int ensure_coef(bte_ctx* h, double dt, int scheme) {
     build_coef(std::get<0>(h->cls_key[c]), delta, h->nd, h->S.data(), h->w.data(), h->nb, h->nbp, h->vg.data(),
                h->beta.data(), dt, scheme == BTE_EXPLICIT, h->coef_host.data() + c * per);
   }
-  CUDA_TRY(h, cudaMemcpyAsync(h->coef, h->coef_host.data(), h->coef_host.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  if (h->opts.precision == BTE_FP64) {
+    CUDA_TRY(h, cudaMemcpyAsync(h->coef, h->coef_host.data(), h->coef_host.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  } else {
+    std::vector<float> c32(h->coef_host.begin(), h->coef_host.end());
+    CUDA_TRY(h, cudaMemcpyAsync(h->coef, c32.data(), c32.size() * 4, cudaMemcpyHostToDevice, h->stream));
+  }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->coef_dt = dt;
   h->coef_scheme = scheme;
@@ -292,6 +336,7 @@ int flux_view(bte_ctx* h, int geom, FluxView* out) {
   if (rc) return rc;
   if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "geometry %d has no state", geom);
   const bte_geom& g = h->geoms[geom];
+  out->precision = h->opts.precision;
   out->I = (const double*)h->Ibuf[h->cur];
   out->I0wall = h->I0wall;
   out->geoms = h->geoms_d;
@@ -332,6 +377,7 @@ int bte_default_opts(bte_opts* o) {
   o->newton_rtol = 1e-14;
   o->newton_maxit = 50;
   o->cuda_stream = nullptr;
+  o->T_ref = 300.0;
   return BTE_OK;
 }
 
@@ -341,7 +387,9 @@ int bte_init_mesh(bte_handle* out, int n_geom, const bte_geom* geoms, const bte_
   if (n_geom < 1 || !geoms) return fail(nullptr, BTE_E_ARG, "need n_geom >= 1 and a geometry array");
   bte_opts o;
   if (opts) o = *opts; else bte_default_opts(&o);
-  if (o.precision != BTE_FP64) return fail(nullptr, BTE_E_ARG, "precision %d is not available (FP64 only)", o.precision);
+  if (o.precision != BTE_FP64 && o.precision != BTE_FP32 && o.precision != BTE_BF16)
+    return fail(nullptr, BTE_E_ARG, "unknown precision %d", o.precision);
+  if (!(o.T_ref >= kTmin && o.T_ref <= kTmax)) return fail(nullptr, BTE_E_ARG, "T_ref must lie in [1, 5000] K");
   if (o.learned != 0) return fail(nullptr, BTE_E_ARG, "learned mode is not available");
   if (o.n_gauss < 1 || o.n_gauss > kMaxGauss) return fail(nullptr, BTE_E_ARG, "n_gauss must be in 1..%d", kMaxGauss);
   if (!(o.newton_rtol > 0 && o.newton_rtol < 1e-3) || o.newton_maxit < 1)
@@ -479,6 +527,9 @@ int bte_set_bc(bte_handle h, int geom, int side, int type, const double* T_faces
   if (type == BTE_BC_ISOTHERMAL) {
     CUDA_TRY(h, cudaMemcpyAsync(h->scratch_T, T.data(), nf * 8, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, launch_wall_I0(h->I0wall + h->face0[geom * 6 + side] * h->nbp, h->scratch_T, nf, thermo(h), h->stream));
+    if (h->opts.precision != BTE_FP64)
+      CUDA_TRY(h, launch_wall_dev(h->I0wall_dev + h->face0[geom * 6 + side] * h->nbp,
+                                  h->I0wall + h->face0[geom * 6 + side] * h->nbp, h->I0ref, nf, h->nbp, h->stream));
   }
   const bool changed = h->bc_type[geom][side] != type;
   h->bc_type[geom][side] = type;
@@ -500,8 +551,8 @@ int bte_set_initial(bte_handle h, int geom, const double* T_cells, double T_unif
     if (!(t >= kTmin && t <= kTmax)) return fail(h, BTE_E_ARG, "initial temperature %g outside [1, 5000] K", t);
   if ((rc = ensure_memory(h))) return rc;
   CUDA_TRY(h, cudaMemcpyAsync(h->scratch_T, T.data(), nc * 8, cudaMemcpyHostToDevice, h->stream));
-  CUDA_TRY(h, launch_init_cells((double*)h->Ibuf[h->cur], h->I0cell, h->Tp, h->TL, h->EL, h->scratch_T,
-                                h->cell0[geom], (int)nc, h->nd, thermo(h), h->stream));
+  CUDA_TRY(h, launch_init_cells(h->opts.precision, h->Ibuf[h->cur], h->I0cell, h->J, h->Tp, h->Teval, h->TL, h->EL,
+                                h->scratch_T, h->I0ref, h->cell0[geom], (int)nc, h->nd, thermo(h), h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->init_set[geom] = true;
   h->TL_valid = false;  // T_L is recomputed from E_L on request
@@ -527,18 +578,24 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
   SweepArgs a{};
   a.I0cell = h->I0cell;
   a.Tp = h->Tp;
+  a.Teval = h->Teval;
+  a.J = h->J;
   a.EL = h->EL;
   a.I0wall = h->I0wall;
+  a.I0wall_dev = h->I0wall_dev;
+  a.I0ref = h->I0ref;
   a.coef = h->coef;
   a.dirs = h->dirs_d;
   a.wdir = h->wdir;
+  a.wdir32 = h->wdir32;
+  a.Wtot = h->Wtot;
   a.geoms = h->geoms_d;
   a.items = h->items_d;
   a.nitems = (int)h->items.size();
   a.nd = h->nd;
   a.lpc = h->lpc;
   a.solve_tp = h->solve_tp ? 1 : 0;
-  a.accept_rel = std::cbrt(h->opts.newton_rtol / 4.0);
+  a.trust_rel = std::cbrt(h->opts.newton_rtol / 4.0);
   a.maxit = h->opts.newton_maxit;
   a.counters = h->counters;
   a.th = thermo(h);
@@ -555,7 +612,7 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
       a.In = h->Ibuf[n];
       a.Ik = h->Ibuf[k];
       a.Iout = h->Ibuf[o];
-      CUDA_TRY(h, launch_sweep_fp64(a, dim, h->threads, grid, s));
+      CUDA_TRY(h, launch_sweep(h->opts.precision, a, dim, h->threads, grid, s));
       ++launches;
       k = o;
     }
@@ -606,13 +663,14 @@ int bte_get_flux(bte_handle h, int geom, double* q_cells, double* q_walls, int o
   if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "geometry %d has no state", geom);
   const bte_geom& g = h->geoms[geom];
   const int nc = g.nx * g.ny * g.nz;
-  const double* I = (const double*)h->Ibuf[h->cur];
+  const void* I = h->Ibuf[h->cur];
+  const int prec = h->opts.precision;
   cudaStream_t s = h->stream;
   if (q_cells) {
     if (on_device) {
-      CUDA_TRY(h, launch_flux_cells(I, q_cells, h->dirs_d, h->Sdev, h->cell0[geom], nc, h->nd, h->nbp, g.dim, s));
+      CUDA_TRY(h, launch_flux_cells(prec, I, h->I0ref, q_cells, h->Sdev, h->cell0[geom], nc, h->nd, h->nbp, g.dim, s));
     } else {
-      CUDA_TRY(h, launch_flux_cells(I, h->scratch_q, h->dirs_d, h->Sdev, h->cell0[geom], nc, h->nd, h->nbp, g.dim, s));
+      CUDA_TRY(h, launch_flux_cells(prec, I, h->I0ref, h->scratch_q, h->Sdev, h->cell0[geom], nc, h->nd, h->nbp, g.dim, s));
       CUDA_TRY(h, cudaMemcpyAsync(q_cells, h->scratch_q, (size_t)nc * g.dim * 8, cudaMemcpyDeviceToHost, s));
     }
   }
@@ -620,8 +678,8 @@ int bte_get_flux(bte_handle h, int geom, double* q_cells, double* q_walls, int o
     double res[6] = {0, 0, 0, 0, 0, 0};
     for (int side = 0; side < 2 * g.dim; ++side) {
       const int nf = (int)side_faces(g, side);
-      CUDA_TRY(h, launch_flux_faces(I, h->I0wall, h->geoms_d, geom, side, h->dirs_d, h->Sdev, h->nd, h->nbp,
-                                    h->scratch_faces, nf, s));
+      CUDA_TRY(h, launch_flux_faces(prec, I, h->I0ref, h->I0wall, h->geoms_d, geom, side, h->dirs_d, h->Sdev, h->nd,
+                                    h->nbp, h->scratch_faces, nf, s));
       CUDA_TRY(h, launch_mean(h->scratch_faces, nf, h->scratch_out + side, s));
     }
     CUDA_TRY(h, cudaMemcpyAsync(res, h->scratch_out, 2 * g.dim * 8, cudaMemcpyDeviceToHost, s));
@@ -640,11 +698,21 @@ int bte_get_intensity(bte_handle h, int geom, double* out, int on_device) {
   if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "geometry %d has no state", geom);
   const bte_geom& g = h->geoms[geom];
   const long long nc = (long long)g.nx * g.ny * g.nz;
-  const double* I = (const double*)h->Ibuf[h->cur] + h->cell0[geom] * h->nd * h->nbp;
+  const int prec = h->opts.precision;
+  const size_t es = elem_bytes(prec);
+  const char* I = h->Ibuf[h->cur] + (size_t)h->cell0[geom] * h->nd * h->nbp * es;
   if (on_device) {
-    CUDA_TRY(h, launch_pack_fp64(I, out, nc, h->nd, h->nb, h->nbp, 0, h->stream));
-  } else {
+    CUDA_TRY(h, launch_pack(prec, nullptr, out, I, nullptr, h->I0ref, nc, h->nd, h->nb, h->nbp, 0, h->stream));
+  } else if (prec == BTE_FP64) {
     CUDA_TRY(h, cudaMemcpy2DAsync(out, h->nb * 8, I, h->nbp * 8, h->nb * 8, (size_t)nc * h->nd, cudaMemcpyDeviceToHost, h->stream));
+  } else {
+    for (long long c0 = 0; c0 < nc; c0 += h->pack_cells) {
+      const long long n = std::min(h->pack_cells, nc - c0);
+      CUDA_TRY(h, launch_pack(prec, nullptr, h->scratch_pack, I + (size_t)c0 * h->nd * h->nbp * es, nullptr, h->I0ref, n,
+                              h->nd, h->nb, h->nbp, 0, h->stream));
+      CUDA_TRY(h, cudaMemcpyAsync(out + (size_t)c0 * h->nd * h->nb, h->scratch_pack, (size_t)n * h->nd * h->nb * 8,
+                                  cudaMemcpyDeviceToHost, h->stream));
+    }
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return BTE_OK;
@@ -657,17 +725,30 @@ int bte_set_intensity(bte_handle h, int geom, const double* in, const double* Tp
   if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "bte_set_initial must come first for geometry %d", geom);
   const bte_geom& g = h->geoms[geom];
   const long long nc = (long long)g.nx * g.ny * g.nz;
-  double* I = (double*)h->Ibuf[h->cur] + h->cell0[geom] * h->nd * h->nbp;
+  const int prec = h->opts.precision;
+  const size_t es = elem_bytes(prec);
+  char* I = h->Ibuf[h->cur] + (size_t)h->cell0[geom] * h->nd * h->nbp * es;
   cudaStream_t s = h->stream;
   if (on_device) {
-    CUDA_TRY(h, launch_pack_fp64(in, I, nc, h->nd, h->nb, h->nbp, 1, s));
+    CUDA_TRY(h, launch_pack(prec, in, nullptr, nullptr, I, h->I0ref, nc, h->nd, h->nb, h->nbp, 1, s));
     CUDA_TRY(h, cudaMemcpyAsync(h->Tp + h->cell0[geom], Tp_cells, nc * 8, cudaMemcpyDeviceToDevice, s));
-  } else {
+  } else if (prec == BTE_FP64) {
     CUDA_TRY(h, cudaMemcpy2DAsync(I, h->nbp * 8, in, h->nb * 8, h->nb * 8, (size_t)nc * h->nd, cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync(h->Tp + h->cell0[geom], Tp_cells, nc * 8, cudaMemcpyHostToDevice, s));
+  } else {
+    for (long long c0 = 0; c0 < nc; c0 += h->pack_cells) {
+      const long long n = std::min(h->pack_cells, nc - c0);
+      CUDA_TRY(h, cudaMemcpyAsync(h->scratch_pack, in + (size_t)c0 * h->nd * h->nb, (size_t)n * h->nd * h->nb * 8,
+                                  cudaMemcpyHostToDevice, s));
+      CUDA_TRY(h, launch_pack(prec, h->scratch_pack, nullptr, nullptr, I + (size_t)c0 * h->nd * h->nbp * es, h->I0ref, n,
+                              h->nd, h->nb, h->nbp, 1, s));
+      CUDA_TRY(h, cudaStreamSynchronize(s));
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->Tp + h->cell0[geom], Tp_cells, nc * 8, cudaMemcpyHostToDevice, s));
   }
-  CUDA_TRY(h, launch_I0_from_T(h->I0cell + h->cell0[geom] * h->nbp, h->Tp + h->cell0[geom], nc, thermo(h), s));
-  CUDA_TRY(h, launch_energy_L(I, h->EL + h->cell0[geom], h->wdir, nc, h->nd, thermo(h), s));
+  CUDA_TRY(h, launch_state_from_Tp(h->I0cell + h->cell0[geom] * h->nbp, h->J + h->cell0[geom] * 3 * h->nbp,
+                                   h->Tp + h->cell0[geom], h->Teval + h->cell0[geom], nc, thermo(h), s));
+  CUDA_TRY(h, launch_energy_L(prec, I, h->I0ref, h->EL + h->cell0[geom], h->wdir, nc, h->nd, thermo(h), s));
   CUDA_TRY(h, cudaStreamSynchronize(s));
   h->TL_valid = false;
   return BTE_OK;

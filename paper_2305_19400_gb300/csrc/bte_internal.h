@@ -2,7 +2,9 @@
 //
 // Device data layout (all in one workspace, see bte_capi.cu):
 //   I buffers      3 x [cell][dir][nbp]      storage type per precision mode
+//                                            (FP32/BF16 store I - I0_b(T_ref))
 //   I0cell         [cell][nbp]  double        I0_b(T_p) of every cell
+//   J, Teval       [cell][3][nbp], [cell]     cached quadrature model per cell
 //   Tp, TL, EL     [cell]       double        temperatures, lattice energy
 //   I0wall         [wall face][nbp] double    Eq. 6 ghost for isothermal faces
 //   coef           [class][5][dir][nbp] double  sweep coefficients (A_n, A_x, A_y, A_z, A_s)
@@ -75,51 +77,63 @@ struct ThermoTables {
 };
 
 struct SweepArgs {
-  const void* In;       // I^n   (storage type)
-  const void* Ik;       // I^k   (storage type; == In for explicit)
-  void* Iout;           // I^{k+1}
-  double* I0cell;       // in: I0^k, out: I0^{k+1}
-  double* Tp;           // in/out
-  double* EL;           // out
-  const double* I0wall;
-  const double* coef;   // [cls][5][nd][nbp]
+  const void* In;           // I^n   (storage type; deviation from I0ref in the reduced modes)
+  const void* Ik;           // I^k   (== In for the explicit scheme)
+  void* Iout;               // I^{k+1}
+  double* I0cell;           // [cell][nbp] in: I0^k, out: I0^{k+1}
+  double* Tp;               // [cell] in/out
+  double* Teval;            // [cell] evaluation point of the cached quadrature model
+  double* J;                // [cell][3][nbp] I0, dI0/dT, d2I0/dT2 at Teval
+  double* EL;               // [cell] out
+  const double* I0wall;     // [face][nbp] FP64 ghosts
+  const float* I0wall_dev;  // [face][nbp] FP32 ghosts minus I0ref (reduced modes)
+  const double* I0ref;      // [nbp] I0_b(T_ref) (reduced modes)
+  const void* coef;         // [cls][5][nd][nbp] double (FP64) or float (reduced)
   const DirInfo* dirs;
-  const double* wdir;   // [nd]
+  const double* wdir;       // [nd]
+  const float* wdir32;      // [nd]
   const DevGeom* geoms;
   const WorkItem* items;
   int nitems;
   int nd;
-  int lpc;              // lanes per cell = nbp / values-per-lane
-  int solve_tp;         // 0 when every beta_b == 0 (T_p then unused)
-  double accept_rel;    // accept a Halley step + Taylor I0 refresh when |dT| <= accept_rel*T
+  int lpc;                  // lanes per cell = nbp / values per lane
+  int solve_tp;             // 0 when every beta_b == 0 (T_p then unused)
+  double trust_rel;         // cached model accepted when |T - T_e| <= trust_rel * T
   int maxit;
+  double Wtot;              // sum of direction weights
   DevCounters* counters;
   ThermoTables th;
 };
 
-// Launchers (bte_kernels.cu)
-cudaError_t launch_sweep_fp64(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
-cudaError_t launch_init_cells(double* I, double* I0cell, double* Tp, double* TL, double* EL, const double* Tcells,
-                              long long cell0, int ncells, int nd, ThermoTables th, cudaStream_t s);
+// Launchers (bte_kernels.cu).  precision: BTE_FP64 = 0, BTE_FP32 = 1, BTE_BF16 = 2.
+int values_per_lane(int precision);
+cudaError_t launch_sweep(int precision, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
+cudaError_t launch_init_cells(int precision, void* I, double* I0cell, double* J, double* Tp, double* Te, double* TL,
+                              double* EL, const double* Tcells, const double* I0ref, long long cell0, int ncells, int nd,
+                              ThermoTables th, cudaStream_t s);
+cudaError_t launch_state_from_Tp(double* I0cell, double* J, const double* Tp, double* Te, long long ncells,
+                                 ThermoTables th, cudaStream_t s);
 cudaError_t launch_wall_I0(double* I0wall, const double* Tfaces, long long nfaces, ThermoTables th, cudaStream_t s);
+cudaError_t launch_wall_dev(float* out, const double* I0wall, const double* I0ref, long long nfaces, int nbp,
+                            cudaStream_t s);
 cudaError_t launch_solve_TL(double* TL, const double* EL, const double* Tguess, long long ncells, ThermoTables th,
                             double rtol, int maxit, DevCounters* counters, cudaStream_t s);
-cudaError_t launch_flux_cells(const double* I, double* q, const DirInfo* dirs, const double* S, long long cell0,
-                              int ncells, int nd, int nbp, int dim, cudaStream_t s);
-cudaError_t launch_flux_faces(const double* I, const double* I0wall, const DevGeom* geoms, int geom, int side,
-                              const DirInfo* dirs, const double* S, int nd, int nbp, double* face_out, int nfaces,
-                              cudaStream_t s);
+cudaError_t launch_flux_cells(int precision, const void* I, const double* I0ref, double* q, const double* S,
+                              long long cell0, int ncells, int nd, int nbp, int dim, cudaStream_t s);
+cudaError_t launch_flux_faces(int precision, const void* I, const double* I0ref, const double* I0wall,
+                              const DevGeom* geoms, int geom, int side, const DirInfo* dirs, const double* S, int nd,
+                              int nbp, double* face_out, int nfaces, cudaStream_t s);
 cudaError_t launch_mean(const double* v, int n, double* out, cudaStream_t s);
-cudaError_t launch_I0_from_T(double* I0cell, const double* Tp, long long ncells, ThermoTables th, cudaStream_t s);
-cudaError_t launch_pack_fp64(const double* src, double* dst, long long ncells, int nd, int nb, int nbp, int to_padded,
-                             cudaStream_t s);
-cudaError_t launch_energy_L(const double* I, double* EL, const double* wdir, long long ncells, int nd, ThermoTables th,
-                            cudaStream_t s);
+cudaError_t launch_pack(int precision, const double* src, double* dst_out, const void* Isrc, void* Idst,
+                        const double* I0ref, long long ncells, int nd, int nb, int nbp, int to_padded, cudaStream_t s);
+cudaError_t launch_energy_L(int precision, const void* I, const double* I0ref, double* EL, const double* wdir,
+                            long long ncells, int nd, ThermoTables th, cudaStream_t s);
 
 // Read-only view of one geometry's device state, for entry points that live
 // outside bte_capi.cu (bte_noalloc.cu).  flux_view returns BTE_E_* codes.
 struct FluxView {
-  const double* I;        // current intensity buffer (FP64, padded rows)
+  int precision;          // storage of I (BTE_FP64 = 0, BTE_FP32 = 1, BTE_BF16 = 2)
+  const double* I;        // current intensity buffer (padded rows; FP64 only when precision == 0)
   const double* I0wall;
   const DevGeom* geoms;
   const DirInfo* dirs;

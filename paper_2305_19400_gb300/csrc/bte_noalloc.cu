@@ -115,6 +115,8 @@ extern "C" int bte_get_wall_flux_noalloc(bte_handle h, int geom, double* q_walls
   int rc = flux_view(h, geom, &v);
   if (rc) return rc;
   if (!q_walls) return set_handle_error(h, BTE_E_ARG, "q_walls is NULL");
+  if (v.precision != BTE_FP64)
+    return set_handle_error(h, BTE_E_ARG, "the no-allocation wall flux serves FP64 handles only");
   for (int side = 0; side < 2 * v.dim; ++side)
     if (v.nfaces[side] > kNoAllocMaxFaces)
       return set_handle_error(h, BTE_E_ARG, "wall %d has %d faces; the no-allocation path holds at most %d per wall",
