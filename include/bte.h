@@ -73,7 +73,11 @@ typedef struct {
  *  newton_maxit iteration cap before the bisection fallback (50).
  *  cuda_stream cudaStream_t every launch and copy uses (NULL: legacy default stream).
  *  T_ref      reference temperature of the FP32/BF16 modes, which store the
- *             deviation I - I0_b(T_ref) (default 300 K; ignored in FP64). */
+ *             deviation I - I0_b(T_ref) (default 300 K; ignored in FP64).
+ *  use_graph  1: each time step's ninner sweep launches are captured once in a
+ *             CUDA graph (per scheme, ninner and buffer rotation) and replayed
+ *             on cuda_stream; 0 (default): launched one by one.
+ *  autotune   1: the first bte_step runs bte_autotune (default 0). */
 typedef struct {
   int dir_kind;
   int n_inplane, n_polar, n_azim;
@@ -84,6 +88,8 @@ typedef struct {
   int newton_maxit;
   void* cuda_stream;
   double T_ref;
+  int use_graph;
+  int autotune;
 } bte_opts;
 
 /* Per-call statistics of bte_step (filled only when a non-NULL pointer is
@@ -145,6 +151,13 @@ int bte_set_initial(bte_handle h, int geom, const double* T_cells, double T_unif
  * scheme BTE_EXPLICIT: forward Euler (Eq. 3 with Eq. 5), ninner ignored.
  * stats: host, may be NULL (then the call only queues work and returns). */
 int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_stats* stats);
+
+/* Times the sweep over candidate launch shapes (cells per CTA x grid size,
+ * persistent grids of 2/4/8 CTAs per SM or one CTA per work item) with the
+ * current state and keeps the fastest for this handle.  The timing launches
+ * write only a spare intensity buffer (no solver state changes).  `report`
+ * (host, may be NULL) receives a CSV table of the candidates. */
+int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t report_len);
 
 /* Cell temperatures of one geometry: BTE_T_PSEUDO (T_p, the temperature whose
  * equilibrium the relaxation term drives toward) or BTE_T_LATTICE (T_L, the

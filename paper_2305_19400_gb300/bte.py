@@ -33,7 +33,8 @@ class bte_geom(C.Structure):
 class bte_opts(C.Structure):
     _fields_ = [("dir_kind", C.c_int), ("n_inplane", C.c_int), ("n_polar", C.c_int), ("n_azim", C.c_int),
                 ("precision", C.c_int), ("learned", C.c_int), ("n_gauss", C.c_int), ("newton_rtol", C.c_double),
-                ("newton_maxit", C.c_int), ("cuda_stream", C.c_void_p), ("T_ref", C.c_double)]
+                ("newton_maxit", C.c_int), ("cuda_stream", C.c_void_p), ("T_ref", C.c_double),
+                ("use_graph", C.c_int), ("autotune", C.c_int)]
 
 
 class bte_stats(C.Structure):
@@ -56,6 +57,7 @@ SIGNATURES = {
     "bte_set_bc": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, _dp, C.c_double]),
     "bte_set_initial": (C.c_int, [_h, C.c_int, _dp, C.c_double]),
     "bte_step": (C.c_int, [_h, C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(bte_stats)]),
+    "bte_autotune": (C.c_int, [_h, C.c_double, C.c_int, C.c_char_p, C.c_size_t]),
     "bte_get_T": (C.c_int, [_h, C.c_int, C.c_int, _vp, C.c_int]),
     "bte_get_flux": (C.c_int, [_h, C.c_int, _vp, _vp, C.c_int]),
     "bte_get_intensity": (C.c_int, [_h, C.c_int, _vp, C.c_int]),
@@ -151,6 +153,12 @@ def bte_step(h, dt, nsteps, ninner, scheme=BTE_IMPLICIT_JACOBI, want_stats=True)
     return rc, (st.as_dict() if st is not None else None)
 
 
+def bte_autotune(h, dt, scheme=BTE_IMPLICIT_JACOBI):
+    buf = C.create_string_buffer(4096)
+    _check(h, lib().bte_autotune(h, float(dt), int(scheme), buf, 4096))
+    return buf.value.decode()
+
+
 def bte_get_T(h, geom, which, out):
     """out: float64 numpy array (host) or torch CUDA tensor (device)."""
     on_dev = 0 if isinstance(out, np.ndarray) else 1
@@ -204,7 +212,8 @@ class Solver:
     stream is the given torch stream (default: torch's current stream).
     """
 
-    def __init__(self, workload, precision=BTE_FP64, stream=None, bind_workspace=True, n_gauss=16, T_init=None):
+    def __init__(self, workload, precision=BTE_FP64, stream=None, bind_workspace=True, n_gauss=16, T_init=None,
+                 use_graph=False, autotune=False):
         import torch
 
         self.wl = workload
@@ -217,6 +226,8 @@ class Solver:
             o.dir_kind, o.n_polar, o.n_azim = BTE_DIRS_POLAR_AZIM, d.n_polar, d.n_azim
         o.precision = precision
         o.n_gauss = n_gauss
+        o.use_graph = 1 if use_graph else 0
+        o.autotune = 1 if autotune else 0
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         o.cuda_stream = self.stream.cuda_stream
         geoms = [bte_geom(g.dim, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz) for g in workload.geoms]

@@ -50,7 +50,15 @@ struct bte_ctx {
   std::vector<bool> init_set;
   bool TL_valid = false;
   // launch shape
-  int lpc = 0, cpb = 0, threads = 0;
+  int lpc = 0, dteam = 1, cpb = 0, threads = 0, grid = 0, pd = 1, pf = 0;
+  // CUDA graphs of one time step, keyed by (scheme, ninner, starting buffer)
+  struct GraphEntry {
+    int scheme, ninner, cur_in, cur_out;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
+  std::string tune_report;
   std::vector<WorkItem> items;
   // device memory
   char* ws = nullptr;
@@ -61,7 +69,10 @@ struct bte_ctx {
   double *I0cell = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr, *I0wall = nullptr;
   void* coef = nullptr;
   double *J = nullptr, *Teval = nullptr, *I0ref = nullptr, *scratch_pack = nullptr;
-  float *I0wall_dev = nullptr, *wdir32 = nullptr;
+  float *I0wall_dev = nullptr, *wdir32 = nullptr, *vb32 = nullptr, *bb32 = nullptr;
+  float4* dirc = nullptr;
+  FixItem* fix = nullptr;
+  unsigned* fix_count = nullptr;
   long long pack_cells = 0;
   double *wdir = nullptr, *Sdev = nullptr, *node_c = nullptr, *node_C = nullptr, *a_p = nullptr, *a_L = nullptr;
   double *inv_v = nullptr, *beta_d = nullptr, *scratch_faces = nullptr, *scratch_T = nullptr, *scratch_out = nullptr;
@@ -158,7 +169,12 @@ size_t carve(bte_ctx* h, char* base) {
   h->TL = (double*)take((size_t)h->ncells * 8);
   h->EL = (double*)take((size_t)h->ncells * 8);
   h->I0wall = (double*)take((size_t)std::max(h->nfaces, 1LL) * h->nbp * 8);
-  h->coef = take((size_t)h->cls_key.size() * 5 * row * (h->opts.precision == BTE_FP64 ? 8 : 4));
+  h->coef = take((size_t)h->cls_key.size() * row * (h->opts.precision == BTE_FP64 ? 5 * 8 : 2 * 4));
+  h->dirc = (float4*)take((size_t)h->cls_key.size() * h->nd * sizeof(float4));
+  h->vb32 = (float*)take((size_t)h->nbp * 4);
+  h->bb32 = (float*)take((size_t)h->nbp * 4);
+  h->fix = (FixItem*)take((size_t)std::max<long long>(h->ncells, 1) * sizeof(FixItem));
+  h->fix_count = (unsigned*)take(16);
   h->wdir = (double*)take((size_t)h->nd * 8);
   h->Sdev = (double*)take((size_t)h->nd * 3 * 8);
   h->dirs_d = (DirInfo*)take((size_t)h->nd * sizeof(DirInfo));
@@ -169,7 +185,7 @@ size_t carve(bte_ctx* h, char* base) {
   h->inv_v = (double*)take((size_t)h->nbp * 8);
   h->beta_d = (double*)take((size_t)h->nbp * 8);
   h->geoms_d = (DevGeom*)take(h->geoms.size() * sizeof(DevGeom));
-  h->items_d = (WorkItem*)take(h->items.size() * sizeof(WorkItem));
+  h->items_d = (WorkItem*)take((size_t)std::max<long long>(h->ncells, 1) * sizeof(WorkItem));  // room for 1 cell per item
   h->counters = (DevCounters*)take(sizeof(DevCounters));
   h->scratch_faces = (double*)take((size_t)std::max(h->max_side_faces, 1) * 8);
   h->scratch_T = (double*)take((size_t)std::max(h->max_side_faces, h->max_geom_cells) * 8);
@@ -182,16 +198,40 @@ size_t carve(bte_ctx* h, char* base) {
   return off;
 }
 
-void build_items(bte_ctx* h) {
-  h->lpc = h->nbp / values_per_lane(h->opts.precision);  // one 16-byte vector of bands per lane
-  h->cpb = std::max(1, 256 / h->lpc);
-  h->threads = h->cpb * h->lpc;
+// Work list: runs of at most cpb consecutive cells along x.  2-D geometries are
+// walked row by row (the upwind row is nx cells back, well inside L2).  3-D
+// geometries are walked in column blocks of cpb x by cells marching in z, so
+// the z-upwind plane of a block (cpb*by cells back) is still in L2 when reused.
+void build_items(bte_ctx* h, int cpb = 0) {
+  h->lpc = h->nbp / values_per_lane(h->opts.precision);  // one vector of bands per lane
+  // a cell team covers dteam directions per step: ~896 contiguous bytes of a row
+  const int rowb = h->nbp * (int)elem_bytes(h->opts.precision);
+  h->dteam = std::max(1, std::min(896 / rowb, 256 / h->lpc));
+  const int team = h->lpc * h->dteam;
+  h->cpb = cpb > 0 ? cpb : std::max(1, 256 / team);
+  h->threads = h->cpb * team;
   h->items.clear();
   for (size_t gi = 0; gi < h->geoms.size(); ++gi) {
     const bte_geom& g = h->geoms[gi];
-    const int nc = g.nx * g.ny * g.nz;
-    for (int c = 0; c < nc; c += h->cpb) h->items.push_back(WorkItem{(int)gi, c, std::min(h->cpb, nc - c), 0});
+    if (g.nz == 1) {
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; i += h->cpb)
+          h->items.push_back(WorkItem{(int)gi, j * g.nx + i, std::min(h->cpb, g.nx - i), 0});
+      continue;
+    }
+    const int bx = h->cpb, by = std::max(1, 256 / h->cpb);
+    for (int j0 = 0; j0 < g.ny; j0 += by)
+      for (int i0 = 0; i0 < g.nx; i0 += bx)
+        for (int k = 0; k < g.nz; ++k)
+          for (int j = j0; j < std::min(g.ny, j0 + by); ++j)
+            h->items.push_back(WorkItem{(int)gi, (k * g.ny + j) * g.nx + i0, std::min(bx, g.nx - i0), 0});
   }
+  h->grid = (int)std::min<size_t>(h->items.size(), 65535);
+}
+
+void drop_graphs(bte_ctx* h) {
+  for (auto& e : h->graphs) cudaGraphExecDestroy(e.exec);
+  h->graphs.clear();
 }
 
 int ensure_memory(bte_ctx* h) {
@@ -233,6 +273,14 @@ int ensure_memory(bte_ctx* h) {
   CUDA_TRY(h, cudaMemcpyAsync(h->a_L, aL.data(), aL.size() * 8, cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaMemcpyAsync(h->inv_v, iv.data(), iv.size() * 8, cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaMemcpyAsync(h->beta_d, be.data(), be.size() * 8, cudaMemcpyHostToDevice, s));
+  {
+    std::vector<float> v32(h->nbp, 0.f), b32(h->nbp, 0.f);
+    for (int b = 0; b < h->nb; ++b) { v32[b] = (float)h->vg[b]; b32[b] = (float)h->beta[b]; }
+    CUDA_TRY(h, cudaMemcpyAsync(h->vb32, v32.data(), v32.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->bb32, b32.data(), b32.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemsetAsync(h->fix_count, 0, 16, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+  }
   {
     std::vector<float> w32(h->w.begin(), h->w.end());
     CUDA_TRY(h, cudaMemcpyAsync(h->wdir32, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice, s));
@@ -278,18 +326,28 @@ int upload_geoms(bte_ctx* h) {
 
 int ensure_coef(bte_ctx* h, double dt, int scheme) {
   if (h->coef_dt == dt && h->coef_scheme == scheme) return BTE_OK;
-  const size_t per = (size_t)5 * h->nd * h->nbp;
-  h->coef_host.assign(per * h->cls_key.size(), 0.0);
-  for (size_t c = 0; c < h->cls_key.size(); ++c) {
-    const double delta[3] = {std::get<1>(h->cls_key[c]), std::get<2>(h->cls_key[c]), std::get<3>(h->cls_key[c])};
-    build_coef(std::get<0>(h->cls_key[c]), delta, h->nd, h->S.data(), h->w.data(), h->nb, h->nbp, h->vg.data(),
-               h->beta.data(), dt, scheme == BTE_EXPLICIT, h->coef_host.data() + c * per);
-  }
+  drop_graphs(h);  // captured launches carry dt in their arguments
+  const size_t plane = (size_t)h->nd * h->nbp;
+  const size_t ncls = h->cls_key.size();
   if (h->opts.precision == BTE_FP64) {
+    h->coef_host.assign(5 * plane * ncls, 0.0);
+    for (size_t c = 0; c < ncls; ++c) {
+      const double delta[3] = {std::get<1>(h->cls_key[c]), std::get<2>(h->cls_key[c]), std::get<3>(h->cls_key[c])};
+      build_coef(std::get<0>(h->cls_key[c]), delta, h->nd, h->S.data(), h->w.data(), h->nb, h->nbp, h->vg.data(),
+                 h->beta.data(), dt, scheme == BTE_EXPLICIT, h->coef_host.data() + c * 5 * plane);
+    }
     CUDA_TRY(h, cudaMemcpyAsync(h->coef, h->coef_host.data(), h->coef_host.size() * 8, cudaMemcpyHostToDevice, h->stream));
   } else {
-    std::vector<float> c32(h->coef_host.begin(), h->coef_host.end());
-    CUDA_TRY(h, cudaMemcpyAsync(h->coef, c32.data(), c32.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    std::vector<float> pq(2 * plane * ncls), dc(4 * (size_t)h->nd * ncls);
+    for (size_t c = 0; c < ncls; ++c) {
+      const double delta[3] = {std::get<1>(h->cls_key[c]), std::get<2>(h->cls_key[c]), std::get<3>(h->cls_key[c])};
+      build_pq(std::get<0>(h->cls_key[c]), delta, h->nd, h->S.data(), h->w.data(), h->nb, h->nbp, h->vg.data(),
+               h->beta.data(), dt, scheme == BTE_EXPLICIT, pq.data() + c * 2 * plane, pq.data() + c * 2 * plane + plane,
+               dc.data() + c * 4 * h->nd);
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->coef, pq.data(), pq.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->dirc, dc.data(), dc.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->coef_dt = dt;
@@ -325,6 +383,71 @@ int copy_out(bte_ctx* h, double* out, const double* src, size_t n, int on_device
   CUDA_TRY(h, cudaMemcpyAsync(out, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return BTE_OK;
+}
+
+}  // namespace
+
+namespace {
+
+SweepArgs sweep_args(bte_ctx* h) {
+  SweepArgs a{};
+  a.I0cell = h->I0cell;
+  a.Tp = h->Tp;
+  a.Teval = h->Teval;
+  a.J = h->J;
+  a.EL = h->EL;
+  a.I0wall = h->I0wall;
+  a.I0wall_dev = h->I0wall_dev;
+  a.I0ref = h->I0ref;
+  a.coef = h->coef;
+  a.dirs = h->dirs_d;
+  a.wdir = h->wdir;
+  a.wdir32 = h->wdir32;
+  a.Wtot = h->Wtot;
+  a.geoms = h->geoms_d;
+  a.items = h->items_d;
+  a.nitems = (int)h->items.size();
+  a.nd = h->nd;
+  a.lpc = h->lpc;
+  a.dteam = h->dteam;
+  a.solve_tp = h->solve_tp ? 1 : 0;
+  a.trust_rel = std::cbrt(h->opts.newton_rtol / 4.0);
+  a.maxit = h->opts.newton_maxit;
+  a.counters = h->counters;
+  a.dry = 0;
+  a.pf_dirs = h->pf;
+  a.explicit_scheme = h->coef_scheme == BTE_EXPLICIT ? 1 : 0;
+  a.dt32 = (float)h->coef_dt;
+  a.rdt32 = (float)(1.0 / h->coef_dt);
+  a.dirc = h->dirc;
+  a.vb32 = h->vb32;
+  a.bb32 = h->bb32;
+  a.fix = h->fix;
+  a.fix_count = h->fix_count;
+  a.th = thermo(h);
+  return a;
+}
+
+// One time step: ninner sweeps rotating the three intensity buffers from *cur.
+cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, cudaStream_t s, int* cur) {
+  int dim = 2;
+  for (auto& g : h->geoms) dim = std::max(dim, g.dim);
+  const int n = *cur;
+  int k = n;
+  for (int it = 0; it < ninner; ++it) {
+    int o = 0;
+    while (o == n || o == k) ++o;
+    a.In = h->Ibuf[n];
+    a.Ik = h->Ibuf[k];
+    a.Iout = h->Ibuf[o];
+    cudaError_t e = cudaMemsetAsync(h->fix_count, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = launch_sweep(h->opts.precision, h->pd, a, dim, h->threads, h->grid, s);
+    if (e == cudaSuccess && h->solve_tp) e = launch_fixup(a, s);
+    if (e != cudaSuccess) return e;
+    k = o;
+  }
+  *cur = k;
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -378,6 +501,8 @@ int bte_default_opts(bte_opts* o) {
   o->newton_maxit = 50;
   o->cuda_stream = nullptr;
   o->T_ref = 300.0;
+  o->use_graph = 0;
+  o->autotune = 0;
   return BTE_OK;
 }
 
@@ -418,6 +543,10 @@ int bte_init_mesh(bte_handle* out, int n_geom, const bte_geom* geoms, const bte_
     return fail(nullptr, BTE_E_ARG, "bad direction set (in-plane needs n %% 4 == 0; polar x azimuthal needs even n_polar and n_azim %% 4 == 0)");
   }
   h->nd = (int)h->w.size();
+  if (h->nd > 4096) {
+    delete h;
+    return fail(nullptr, BTE_E_ARG, "at most 4096 directions");
+  }
   for (double x : h->w) h->Wtot += x;
   h->geoms.assign(geoms, geoms + n_geom);
   h->ncells = total;
@@ -570,53 +699,45 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
   if (ninner < 1) return fail(h, BTE_E_ARG, "ninner must be >= 1");
   int rc = ensure_coef(h, dt, scheme);
   if (rc) return rc;
+  if (h->opts.autotune && h->tune_report.empty()) {
+    if ((rc = bte_autotune(h, dt, scheme, nullptr, 0)) != BTE_OK) return rc;
+  }
   cudaStream_t s = h->stream;
   if (stats) {
     CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, sizeof(DevCounters), s));
     CUDA_TRY(h, cudaEventRecord(h->ev0, s));
   }
-  SweepArgs a{};
-  a.I0cell = h->I0cell;
-  a.Tp = h->Tp;
-  a.Teval = h->Teval;
-  a.J = h->J;
-  a.EL = h->EL;
-  a.I0wall = h->I0wall;
-  a.I0wall_dev = h->I0wall_dev;
-  a.I0ref = h->I0ref;
-  a.coef = h->coef;
-  a.dirs = h->dirs_d;
-  a.wdir = h->wdir;
-  a.wdir32 = h->wdir32;
-  a.Wtot = h->Wtot;
-  a.geoms = h->geoms_d;
-  a.items = h->items_d;
-  a.nitems = (int)h->items.size();
-  a.nd = h->nd;
-  a.lpc = h->lpc;
-  a.solve_tp = h->solve_tp ? 1 : 0;
-  a.trust_rel = std::cbrt(h->opts.newton_rtol / 4.0);
-  a.maxit = h->opts.newton_maxit;
-  a.counters = h->counters;
-  a.th = thermo(h);
-  int dim = 2;
-  for (auto& g : h->geoms) dim = std::max(dim, g.dim);
-  const int grid = (int)std::min<size_t>(h->items.size(), 65535);
+  SweepArgs a = sweep_args(h);
   int launches = 0;
   for (int st = 0; st < nsteps; ++st) {
-    const int n = h->cur;
-    int k = n;
-    for (int it = 0; it < ninner; ++it) {
-      int o = 0;
-      while (o == n || o == k) ++o;
-      a.In = h->Ibuf[n];
-      a.Ik = h->Ibuf[k];
-      a.Iout = h->Ibuf[o];
-      CUDA_TRY(h, launch_sweep(h->opts.precision, a, dim, h->threads, grid, s));
-      ++launches;
-      k = o;
+    if (h->opts.use_graph) {
+      cudaGraphExec_t exec = nullptr;
+      int cur_out = -1;
+      for (auto& e : h->graphs)
+        if (e.scheme == scheme && e.ninner == ninner && e.cur_in == h->cur) { exec = e.exec; cur_out = e.cur_out; }
+      if (!exec) {
+        if (!h->cap_stream) CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int cur = h->cur;
+        cudaError_t e = enqueue_step(h, a, ninner, h->cap_stream, &cur);
+        cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          return fail(h, BTE_E_CUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(h, BTE_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        h->graphs.push_back({scheme, ninner, h->cur, cur, exec});
+        cur_out = cur;
+      }
+      CUDA_TRY(h, cudaGraphLaunch(exec, s));
+      h->cur = cur_out;
+    } else {
+      CUDA_TRY(h, enqueue_step(h, a, ninner, s, &h->cur));
     }
-    h->cur = k;
+    launches += ninner;
   }
   if (nsteps > 0) h->TL_valid = false;
   if (stats) {
@@ -635,6 +756,83 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
     stats->gpu_ms = ms;
     if (c.nonfinite) return fail(h, BTE_E_NONFINITE, "%llu cells had a non-finite energy or no temperature in [1, 5000] K", (unsigned long long)c.nonfinite);
     if (c.fallbacks) return BTE_W_FALLBACK;
+  }
+  return BTE_OK;
+}
+
+int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t report_len) {
+  if (!h) return BTE_E_ARG;
+  std::string why;
+  if (!h->mem_ready || !ready_to_step(h, why)) return fail(h, BTE_E_STATE, "not ready to tune: %s", why.empty() ? "no state" : why.c_str());
+  if (!(dt > 0 && std::isfinite(dt))) return fail(h, BTE_E_ARG, "dt must be > 0");
+  if (scheme != BTE_IMPLICIT_JACOBI && scheme != BTE_EXPLICIT) return fail(h, BTE_E_ARG, "unknown scheme %d", scheme);
+  int rc = ensure_coef(h, dt, scheme);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev);
+  const int spare = (h->cur + 1) % 3;  // timing launches write here; the state is untouched (dry epilogue)
+  struct Cand { int cpb, grid, pd, pf; float ms; };
+  std::vector<Cand> tried;
+  const int tpc_list[2] = {128, 256};
+  const int pd_list[2] = {1, 2};
+  const int pf_list[3] = {0, 8, 16};
+  int best_cpb = h->cpb, best_grid = h->grid, best_pd = h->pd, best_pf = h->pf;
+  float best_ms = 1e30f;
+  int dim = 2;
+  for (auto& g : h->geoms) dim = std::max(dim, g.dim);
+  for (int tpc : tpc_list) {
+    const int cpb = std::max(1, tpc / (h->lpc * h->dteam));
+    bool seen = false;
+    for (auto& c : tried) seen |= c.cpb == cpb;
+    if (seen) continue;
+    build_items(h, cpb);
+    CUDA_TRY(h, cudaMemcpyAsync(h->items_d, h->items.data(), h->items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+    const int nit = (int)h->items.size();
+    const int grids[3] = {std::min(nit, 65535), std::min(nit, 2 * sms), std::min(nit, 4 * sms)};
+    for (int gi = 0; gi < 3; ++gi)
+      for (int pd : pd_list)
+      for (int pf : pf_list) {
+        const int grid = grids[gi];
+        bool dup = false;
+        for (auto& c : tried) dup |= c.cpb == cpb && c.grid == grid && c.pd == pd && c.pf == pf;
+        if (dup) continue;
+        SweepArgs a = sweep_args(h);
+        a.dry = 1;
+        a.pf_dirs = pf;
+        a.counters = nullptr;
+        a.In = a.Ik = h->Ibuf[h->cur];
+        a.Iout = h->Ibuf[spare];
+        CUDA_TRY(h, launch_sweep(h->opts.precision, pd, a, dim, h->threads, grid, s));
+        CUDA_TRY(h, cudaEventRecord(h->ev0, s));
+        for (int r = 0; r < 3; ++r) CUDA_TRY(h, launch_sweep(h->opts.precision, pd, a, dim, h->threads, grid, s));
+        CUDA_TRY(h, cudaEventRecord(h->ev1, s));
+        CUDA_TRY(h, cudaEventSynchronize(h->ev1));
+        float ms = 0.f;
+        CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        ms /= 3.f;
+        tried.push_back({cpb, grid, pd, pf, ms});
+        if (ms < best_ms) { best_ms = ms; best_cpb = cpb; best_grid = grid; best_pd = pd; best_pf = pf; }
+      }
+  }
+  build_items(h, best_cpb);
+  h->grid = best_grid;
+  h->pd = best_pd;
+  h->pf = best_pf;
+  CUDA_TRY(h, cudaMemcpyAsync(h->items_d, h->items.data(), h->items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  drop_graphs(h);
+  char buf[256];
+  h->tune_report = "cells_per_cta,threads,grid,min_ctas_variant,l2_prefetch_dirs,ms_per_launch\n";
+  for (auto& c : tried) {
+    snprintf(buf, sizeof buf, "%d,%d,%d,%d,%d,%.4f\n", c.cpb, c.cpb * h->lpc * h->dteam, c.grid, c.pd, c.pf, c.ms);
+    h->tune_report += buf;
+  }
+  snprintf(buf, sizeof buf, "chosen,%d,%d,%d,%d,%d\n", best_cpb, best_cpb * h->lpc * h->dteam, best_grid, best_pd, best_pf);
+  h->tune_report += buf;
+  if (report && report_len) {
+    std::strncpy(report, h->tune_report.c_str(), report_len - 1);
+    report[report_len - 1] = 0;
   }
   return BTE_OK;
 }
@@ -766,6 +964,8 @@ int bte_destroy(bte_handle h) {
   if (!h) return BTE_E_ARG;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ws_owned && h->ws) cudaFree(h->ws);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);

@@ -56,6 +56,13 @@ struct DirInfo {
   int rx, ry, rz;
 };
 
+// A cell whose temperature the sweep could not settle on its cached model.
+struct FixItem {
+  long long P;  // global cell
+  double Ep;    // right-hand side of the T_p equation: sum_b beta_b G_b / v_b
+  double T0;    // start temperature of the exact solve
+};
+
 // Counters written by the kernels (atomics), read back for bte_stats.
 struct DevCounters {
   unsigned long long evals;
@@ -88,7 +95,14 @@ struct SweepArgs {
   const double* I0wall;     // [face][nbp] FP64 ghosts
   const float* I0wall_dev;  // [face][nbp] FP32 ghosts minus I0ref (reduced modes)
   const double* I0ref;      // [nbp] I0_b(T_ref) (reduced modes)
-  const void* coef;         // [cls][5][nd][nbp] double (FP64) or float (reduced)
+  const void* coef;         // FP64: [cls][5][nd][nbp] A_n, A_x, A_y, A_z, A_s;
+                            // reduced: [cls][2][nd][nbp] float P, Q with
+                            // I' = P I^n + Q (v_b sum_ax c_ax I_up + beta_b dI0)
+  const float4* dirc;       // reduced: [cls][nd] (c_x, c_y, c_z, sum), c_ax = |S_d,ax|/(w_d Delta_ax)
+  const float* vb32;        // [nbp] v_b (reduced)
+  const float* bb32;        // [nbp] beta_b (reduced)
+  FixItem* fix;             // cells handed to the fix-up kernel
+  unsigned* fix_count;
   const DirInfo* dirs;
   const double* wdir;       // [nd]
   const float* wdir32;      // [nd]
@@ -96,18 +110,27 @@ struct SweepArgs {
   const WorkItem* items;
   int nitems;
   int nd;
-  int lpc;                  // lanes per cell = nbp / values per lane
+  int lpc;                  // lanes per direction row = nbp / values per lane
+  int dteam;                // directions one cell team covers per step (team = lpc * dteam lanes)
   int solve_tp;             // 0 when every beta_b == 0 (T_p then unused)
   double trust_rel;         // cached model accepted when |T - T_e| <= trust_rel * T
   int maxit;
   double Wtot;              // sum of direction weights
+  int dry;                  // 1: timing run, the epilogue writes no solver state
+  int pf_dirs;              // directions per L2 prefetch chunk (0: no prefetch)
+  int explicit_scheme;      // reduced modes compute P, Q on the fly from these:
+  float dt32, rdt32;        // dt and 1/dt
   DevCounters* counters;
   ThermoTables th;
 };
 
 // Launchers (bte_kernels.cu).  precision: BTE_FP64 = 0, BTE_FP32 = 1, BTE_BF16 = 2.
 int values_per_lane(int precision);
-cudaError_t launch_sweep(int precision, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
+cudaError_t launch_sweep(int precision, int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
+cudaError_t launch_sweep_fp64(int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
+cudaError_t launch_sweep_fp32(int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
+cudaError_t launch_sweep_bf16(int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
+cudaError_t launch_fixup(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_init_cells(int precision, void* I, double* I0cell, double* J, double* Tp, double* Te, double* TL,
                               double* EL, const double* Tcells, const double* I0ref, long long cell0, int ncells, int nd,
                               ThermoTables th, cudaStream_t s);

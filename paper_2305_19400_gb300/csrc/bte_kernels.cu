@@ -1,4 +1,6 @@
-// bte_kernels.cu -- CUDA kernels of the phonon BTE hot path (sm_103a).
+// bte_kernels.cu -- CUDA kernels around the sweep (sm_103a): temperature fix-up,
+// initial state, wall ghosts, T_L, heat flux, state packing.  The sweep itself
+// (described below) lives in bte_sweep.cuh.
 //
 // sweep_kernel<DIM, S>: one launch per inner iteration.  A CTA owns a run of
 //   cells of one geometry; each cell is served by `lpc` lanes, lane l holding
@@ -25,97 +27,12 @@
 //   I0 is refreshed from the accepted model.
 // The HBM stream per update is I^n read, I^{k+1} written and I^k read once
 // (neighbour rows come from L2 while adjacent cells are processed together).
-#include <cuda_bf16.h>
-
-#include "bte_internal.h"
+#include "bte_store.cuh"
 
 namespace bte {
 
 namespace {
 
-enum SolveMode { M_MODEL = 0, M_HALLEY = 1, M_BISECT = 2, M_FINAL = 3, M_ACCEPT = 4, M_DONE = 5 };
-
-// ---------------------------------------------------------------------------
-// Storage traits: V values per vector load, arithmetic type A.
-template <typename S> struct Tr;
-
-template <> struct Tr<double> {
-  static constexpr int V = 2;
-  using A = double;
-  static __device__ __forceinline__ void ld(const double* p, A (&x)[V]) {
-    const double2 v = *reinterpret_cast<const double2*>(p);
-    x[0] = v.x; x[1] = v.y;
-  }
-  static __device__ __forceinline__ void ld_stream(const double* p, A (&x)[V]) {
-    const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
-    x[0] = v.x; x[1] = v.y;
-  }
-  static __device__ __forceinline__ void st(double* p, const A (&x)[V]) {
-    __stcs(reinterpret_cast<double2*>(p), make_double2(x[0], x[1]));
-  }
-  static __device__ __forceinline__ double to_double(double v) { return v; }
-};
-
-template <> struct Tr<float> {
-  static constexpr int V = 4;
-  using A = float;
-  static __device__ __forceinline__ void ld(const float* p, A (&x)[V]) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-  }
-  static __device__ __forceinline__ void ld_stream(const float* p, A (&x)[V]) {
-    const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
-    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-  }
-  static __device__ __forceinline__ void st(float* p, const A (&x)[V]) {
-    __stcs(reinterpret_cast<float4*>(p), make_float4(x[0], x[1], x[2], x[3]));
-  }
-  static __device__ __forceinline__ double to_double(float v) { return (double)v; }
-};
-
-template <> struct Tr<__nv_bfloat16> {
-  static constexpr int V = 4;
-  using A = float;
-  static __device__ __forceinline__ void unpack(const uint2 v, A (&x)[V]) {
-    x[0] = __uint_as_float(v.x << 16);
-    x[1] = __uint_as_float(v.x & 0xffff0000u);
-    x[2] = __uint_as_float(v.y << 16);
-    x[3] = __uint_as_float(v.y & 0xffff0000u);
-  }
-  static __device__ __forceinline__ void ld(const __nv_bfloat16* p, A (&x)[V]) {
-    unpack(*reinterpret_cast<const uint2*>(p), x);
-  }
-  static __device__ __forceinline__ void ld_stream(const __nv_bfloat16* p, A (&x)[V]) {
-    unpack(__ldcs(reinterpret_cast<const uint2*>(p)), x);
-  }
-  static __device__ __forceinline__ void st(__nv_bfloat16* p, const A (&x)[V]) {
-    const __nv_bfloat162 h0 = __floats2bfloat162_rn(x[0], x[1]);  // round to nearest even
-    const __nv_bfloat162 h1 = __floats2bfloat162_rn(x[2], x[3]);
-    __stcs(reinterpret_cast<uint2*>(p),
-           make_uint2(*reinterpret_cast<const unsigned*>(&h0), *reinterpret_cast<const unsigned*>(&h1)));
-  }
-  static __device__ __forceinline__ double to_double(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
-};
-
-// V consecutive values of type A from global memory (16-byte loads).
-template <typename A, int V>
-__device__ __forceinline__ void ldgv(const A* p, A (&x)[V]) {
-  if constexpr (sizeof(A) == 8) {
-#pragma unroll
-    for (int i = 0; i < V; i += 2) {
-      const double2 v = __ldg(reinterpret_cast<const double2*>(p + i));
-      x[i] = v.x; x[i + 1] = v.y;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < V; i += 4) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(p + i));
-      x[i] = v.x; x[i + 1] = v.y; x[i + 2] = v.z; x[i + 3] = v.w;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Band quadrature.  I0_b(T) = sum_i C_i / expm1(c_i / T) (Gauss-Legendre on the
 // band).  With n = 1/(e^x - 1), x = c/T:  dn/dT = n(1+n) x/T and
 // d2n/dT2 = n(1+n) (x/T^2) ((1+2n) x - 2).
@@ -143,295 +60,93 @@ __device__ __forceinline__ void band_I0_d2(const double* __restrict__ c, const d
   d2 = s2 * rT * rT;
 }
 
-// ---------------------------------------------------------------------------
-// Upwind value along axis AX for one lane of cell P in direction d.  Wall data
-// use compile-time side indices so DevGeom stays in registers.
-template <int AX, typename S>
-__device__ __forceinline__ void upwind(const S* __restrict__ Ik, const SweepArgs& a, const DevGeom& g, const DirInfo& di,
-                                       long long P, int ci, int cj, int ck, long long row, int d, int b0,
-                                       typename Tr<S>::A (&x)[Tr<S>::V]) {
-  using T = Tr<S>;
-  const int c = AX == 0 ? ci : (AX == 1 ? cj : ck);
-  const int n = AX == 0 ? g.nx : (AX == 1 ? g.ny : g.nz);
-  const long long stride = AX == 0 ? 1 : (AX == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
-  const bool from_low = (di.up >> AX) & 1;
-  const int nbp = a.th.nbp;
-  if (from_low ? c > 0 : c < n - 1) {
-    T::ld(Ik + (P + (from_low ? -stride : stride)) * row + (long long)d * nbp + b0, x);
-    return;
-  }
-  const int bc = from_low ? g.bc[2 * AX] : g.bc[2 * AX + 1];
-  if (bc == 0) {  // isothermal wall: I0_b of the face (as a deviation in the reduced modes)
-    const long long f0 = from_low ? g.face0[2 * AX] : g.face0[2 * AX + 1];
-    const long long f =
-        f0 + (AX == 0 ? cj + (long long)g.ny * ck : (AX == 1 ? ci + (long long)g.nx * ck : ci + (long long)g.nx * cj));
-    if constexpr (sizeof(S) == 8) ldgv<double, T::V>(a.I0wall + f * nbp + b0, x);
-    else ldgv<float, T::V>(a.I0wall_dev + f * nbp + b0, x);
-    return;
-  }
-  const int r = AX == 0 ? di.rx : (AX == 1 ? di.ry : di.rz);  // symmetry wall: mirrored direction
-  T::ld(Ik + P * row + (long long)r * nbp + b0, x);
-}
-
-template <int DIM, typename S>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
-  using T = Tr<S>;
-  using A = typename T::A;
-  constexpr int V = T::V;
-  constexpr bool kDev = sizeof(S) != 8;  // reduced modes store deviations
-  extern __shared__ double sm[];
-  __shared__ unsigned long long cnt_evals, cnt_solves, cnt_fb, cnt_bad;
-  const int lpc = a.lpc, nd = a.nd, nbp = a.th.nbp, ng = a.th.ng;
-  const int slot = threadIdx.x / lpc, lane = threadIdx.x - slot * lpc;
-  double* red = sm;                   // [blockDim.x][3]
-  double* cst = sm + 3 * blockDim.x;  // [cells per CTA][8] solve state
-  const S* __restrict__ In = reinterpret_cast<const S*>(a.In);
-  const S* __restrict__ Ik = reinterpret_cast<const S*>(a.Ik);
-  S* __restrict__ Io = reinterpret_cast<S*>(a.Iout);
-  const A* __restrict__ coef = reinterpret_cast<const A*>(a.coef);
-  const long long row = (long long)nd * nbp;
-  const int b0 = V * lane;
-  if (threadIdx.x == 0) { cnt_evals = 0; cnt_solves = 0; cnt_fb = 0; cnt_bad = 0; }
-
-  for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-    const WorkItem wi = a.items[item];
-    const DevGeom g = a.geoms[wi.geom];
-    const bool active = slot < wi.cell_count;
-    const int lc = wi.cell_begin + (active ? slot : 0);
-    const int ci = lc % g.nx, cj = (lc / g.nx) % g.ny, ck = lc / (g.nx * g.ny);
-    const long long P = g.cell0 + lc;
-    double G[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) G[v] = 0.0;
-
-    if (active) {
-      A src[V];  // I0 of the cell (deviation in the reduced modes)
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const double i0 = a.I0cell[P * nbp + b0 + v];
-        src[v] = kDev ? (A)(i0 - a.I0ref[b0 + v]) : (A)i0;
+// Exact temperature solve of the cells the sweep could not settle on their
+// cached model: one warp per cell, lanes over bands.  Halley steps on the FP64
+// band quadrature from T0 (each evaluation becomes the cell's cached model),
+// bisection on [1, 5000] K as the fallback, then the I0 refresh.
+__global__ void fixup_kernel(SweepArgs a) {
+  const int warps = blockDim.x / 32;
+  const int lane = threadIdx.x & 31;
+  const int nbp = a.th.nbp, ng = a.th.ng;
+  const unsigned count = *a.fix_count;
+  unsigned long long evals = 0, fb = 0, bad = 0;
+  for (unsigned w = blockIdx.x * warps + threadIdx.x / 32; w < count; w += gridDim.x * warps) {
+    const FixItem it = a.fix[w];
+    const long long P = it.P;
+    const double Ep = it.Ep;
+    double T = it.T0, lo = kTmin, hi = kTmax, delta = 0.0;
+    int mode = 0, iters = 0;  // 0 Halley, 1 bisection, 2 final
+    bool done = false;
+    for (int loop = 0; loop < a.maxit + 224 && !done; ++loop) {
+      const double rT = 1.0 / T;
+      double F = 0.0, F1 = 0.0, F2 = 0.0;
+      for (int b = lane; b < nbp; b += 32) {
+        double f, d1, d2;
+        band_I0_d2(a.th.node_c + b * ng, a.th.node_C + b * ng, ng, rT, f, d1, d2);
+        a.J[(P * 3 + 0) * nbp + b] = f;
+        a.J[(P * 3 + 1) * nbp + b] = d1;
+        a.J[(P * 3 + 2) * nbp + b] = d2;
+        const double ap = a.th.a_p[b];
+        F = fma(ap, f, F);
+        F1 = fma(ap, d1, F1);
+        F2 = fma(ap, d2, F2);
       }
-      A hi[V], lo[V];  // compensated float sums (reduced modes)
-#pragma unroll
-      for (int v = 0; v < V; ++v) { hi[v] = 0; lo[v] = 0; }
-      const size_t plane = (size_t)nd * nbp;
-      const A* __restrict__ cf = coef + (size_t)g.cls * 5 * plane + b0;
-      const S* __restrict__ inrow = In + P * row + b0;
-      S* __restrict__ outrow = Io + P * row + b0;
-#pragma unroll 2
-      for (int d = 0; d < nd; ++d) {
-        const DirInfo di = a.dirs[d];
-        const size_t co = (size_t)d * nbp;
-        A An[V], Ax[V], Ay[V], As[V], vn[V], ux[V], uy[V], r[V];
-        ldgv<A, V>(cf + co, An);
-        ldgv<A, V>(cf + plane + co, Ax);
-        ldgv<A, V>(cf + 2 * plane + co, Ay);
-        ldgv<A, V>(cf + 4 * plane + co, As);
-        T::ld_stream(inrow + co, vn);
-        upwind<0, S>(Ik, a, g, di, P, ci, cj, ck, row, d, b0, ux);
-        upwind<1, S>(Ik, a, g, di, P, ci, cj, ck, row, d, b0, uy);
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          r[v] = An[v] * vn[v];
-          r[v] = fma(Ax[v], ux[v], r[v]);
-          r[v] = fma(Ay[v], uy[v], r[v]);
+      for (int o = 16; o > 0; o >>= 1) {
+        F += __shfl_xor_sync(0xffffffffu, F, o);
+        F1 += __shfl_xor_sync(0xffffffffu, F1, o);
+        F2 += __shfl_xor_sync(0xffffffffu, F2, o);
+      }
+      F -= Ep;
+      ++evals;
+      if (mode == 0) {
+        ++iters;
+        bool badstep = !(isfinite(F) && isfinite(F1) && F1 > 0.0);
+        double Tn = T;
+        if (!badstep) {
+          const double newton = -F / F1;
+          const double h = F * F2 / (2.0 * F1 * F1);
+          delta = fabs(h) < 0.5 ? newton / (1.0 - h) : newton;
+          Tn = T + delta;
+          badstep = !(Tn >= kTmin && Tn <= kTmax) || iters > a.maxit;
         }
-        if (DIM == 3) {
-          A Az[V], uz[V];
-          ldgv<A, V>(cf + 3 * plane + co, Az);
-          upwind<2, S>(Ik, a, g, di, P, ci, cj, ck, row, d, b0, uz);
-#pragma unroll
-          for (int v = 0; v < V; ++v) r[v] = fma(Az[v], uz[v], r[v]);
-        }
-#pragma unroll
-        for (int v = 0; v < V; ++v) r[v] = fma(As[v], src[v], r[v]);
-        T::st(outrow + co, r);
-        if constexpr (!kDev) {
-          const double wd = __ldg(a.wdir + d);
-#pragma unroll
-          for (int v = 0; v < V; ++v) G[v] = fma(wd, (double)r[v], G[v]);
+        if (badstep) {
+          mode = 1;
+          lo = kTmin;
+          hi = kTmax;
+          T = 0.5 * (lo + hi);
+          ++fb;
+        } else if (fabs(delta) <= a.trust_rel * Tn) {
+          done = true;
         } else {
-          // the reduction sees the stored (rounded) value
-          const float wd = __ldg(a.wdir32 + d);
-#pragma unroll
-          for (int v = 0; v < V; ++v) {
-            float val = r[v];
-            if constexpr (sizeof(S) == 2) val = __bfloat162float(__float2bfloat16_rn(val));
-            const float p = wd * val;  // TwoSum of (hi + p)
-            const float s = hi[v] + p;
-            const float bb = s - hi[v];
-            lo[v] += (hi[v] - (s - bb)) + (p - bb);
-            hi[v] = s;
-          }
+          T = Tn;
         }
-      }
-      if constexpr (kDev) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) G[v] = fma(a.Wtot, a.I0ref[b0 + v], (double)hi[v] + (double)lo[v]);
+      } else if (mode == 1) {
+        if (F < 0.0) lo = T; else hi = T;
+        T = 0.5 * (lo + hi);
+        ++iters;
+        if (hi - lo <= 4e-16 * hi || iters >= a.maxit + 200) mode = 2;
+      } else {
+        delta = 0.0;
+        done = true;
+        if (T <= kTmin * (1.0 + 1e-9) || T >= kTmax * (1.0 - 1e-9)) ++bad;
       }
     }
-
-    // ---- per-cell reduction: E_L = sum_b G_b / v_b, E_p = sum_b beta_b G_b / v_b
-    {
-      double eL = 0.0, ep = 0.0;
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const double e = G[v] * a.th.inv_v[b0 + v];
-        eL += e;
-        ep = fma(a.th.beta[b0 + v], e, ep);
-      }
-      red[3 * threadIdx.x + 0] = eL;
-      red[3 * threadIdx.x + 1] = ep;
+    if (!done) { ++bad; delta = 0.0; }
+    // I0 refresh from the (just written) model at T
+    const double hd2 = 0.5 * delta * delta;
+    for (int b = lane; b < nbp; b += 32) {
+      const long long j = (P * 3) * nbp + b;
+      a.I0cell[P * nbp + b] = fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], delta, a.J[j]));
     }
-    __syncthreads();
     if (lane == 0) {
-      double EL = 0.0, Ep = 0.0;
-      for (int l = 0; l < lpc; ++l) {
-        EL += red[3 * (threadIdx.x + l) + 0];
-        Ep += red[3 * (threadIdx.x + l) + 1];
-      }
-      double* s = cst + 8 * slot;
-      s[0] = Ep;
-      s[1] = active ? a.Teval[P] : 300.0;  // evaluation point of the cached model
-      s[2] = kTmin;
-      s[3] = kTmax;
-      s[5] = 0.0;  // iterations
-      s[6] = 0.0;  // accepted step from the evaluation point
-      s[7] = 0.0;  // 1 when the accepted data come from a fresh exact evaluation
-      int mode = M_DONE;
-      if (active) {
-        a.EL[P] = EL;
-        if (!isfinite(EL) || !isfinite(Ep)) {
-          atomicAdd(&cnt_bad, 1ULL);
-        } else if (a.solve_tp) {
-          mode = M_MODEL;
-          atomicAdd(&cnt_solves, 1ULL);
-        }
-      }
-      s[4] = (double)mode;
+      a.Teval[P] = T;
+      a.Tp[P] = T + delta;
     }
-    __syncthreads();
-
-    // ---- T_p solve (lockstep over the CTA's cells) and I0 refresh.  Exact
-    // evaluations go straight to the cached model J (with T_e), so J and T_e
-    // always describe the same point and nothing is held in registers across
-    // the barriers.
-    if (a.solve_tp) {
-      const int maxloop = a.maxit + 224;
-      double* const Jf = a.J + (P * 3 + 0) * nbp + b0;
-      double* const Jd1 = a.J + (P * 3 + 1) * nbp + b0;
-      double* const Jd2 = a.J + (P * 3 + 2) * nbp + b0;
-      for (int it = 0; it < maxloop; ++it) {
-        double* s = cst + 8 * slot;
-        const int mode = (int)s[4];
-        const double Te = s[1];
-        if (mode < M_ACCEPT) {
-          double F = 0.0, F1 = 0.0, F2 = 0.0;
-          const double rT = 1.0 / Te;
-          for (int v = 0; v < V; ++v) {
-            double f, d1, d2;
-            if (mode == M_MODEL) {  // cached quadratic model at T_e
-              f = Jf[v];
-              d1 = Jd1[v];
-              d2 = Jd2[v];
-            } else {  // exact quadrature at T_e, which becomes the cached model
-              band_I0_d2(a.th.node_c + (b0 + v) * ng, a.th.node_C + (b0 + v) * ng, ng, rT, f, d1, d2);
-              Jf[v] = f;
-              Jd1[v] = d1;
-              Jd2[v] = d2;
-            }
-            const double ap = a.th.a_p[b0 + v];
-            F = fma(ap, f, F);
-            F1 = fma(ap, d1, F1);
-            F2 = fma(ap, d2, F2);
-          }
-          red[3 * threadIdx.x + 0] = F;
-          red[3 * threadIdx.x + 1] = F1;
-          red[3 * threadIdx.x + 2] = F2;
-        }
-        __syncthreads();
-        if (lane == 0 && mode < M_ACCEPT) {
-          double F = -s[0], F1 = 0.0, F2 = 0.0;
-          for (int l = 0; l < lpc; ++l) {
-            F += red[3 * (threadIdx.x + l) + 0];
-            F1 += red[3 * (threadIdx.x + l) + 1];
-            F2 += red[3 * (threadIdx.x + l) + 2];
-          }
-          if (mode != M_MODEL) {
-            a.Teval[P] = Te;
-            atomicAdd(&cnt_evals, 1ULL);
-          }
-          int next = mode;
-          if (mode == M_MODEL) {
-            // root of F + F1 d + F2 d^2 / 2 nearest 0
-            const double disc = F1 * F1 - 2.0 * F * F2;
-            const double delta = (disc >= 0.0 && F1 > 0.0) ? -2.0 * F / (F1 + sqrt(disc)) : -F / F1;
-            const double Tn = Te + delta;
-            if (isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn) {
-              next = M_ACCEPT;
-              s[6] = delta;
-            } else {
-              next = M_HALLEY;
-              s[1] = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[P];
-            }
-          } else if (mode == M_HALLEY) {
-            s[5] += 1.0;
-            bool bad = !(isfinite(F) && isfinite(F1) && F1 > 0.0);
-            double Tn = Te, delta = 0.0;
-            if (!bad) {
-              const double newton = -F / F1;
-              const double h = F * F2 / (2.0 * F1 * F1);
-              delta = fabs(h) < 0.5 ? newton / (1.0 - h) : newton;
-              Tn = Te + delta;
-              bad = !(Tn >= kTmin && Tn <= kTmax) || s[5] > a.maxit;
-            }
-            if (bad) {
-              next = M_BISECT;
-              s[2] = kTmin;
-              s[3] = kTmax;
-              s[1] = 0.5 * (kTmin + kTmax);
-              atomicAdd(&cnt_fb, 1ULL);
-            } else if (fabs(delta) <= a.trust_rel * Tn) {
-              next = M_ACCEPT;
-              s[6] = delta;
-            } else {
-              s[1] = Tn;
-            }
-          } else if (mode == M_BISECT) {
-            if (F < 0.0) s[2] = Te; else s[3] = Te;
-            s[1] = 0.5 * (s[2] + s[3]);
-            s[5] += 1.0;
-            if (s[3] - s[2] <= 4e-16 * s[3] || s[5] >= a.maxit + 200) next = M_FINAL;
-          } else {  // M_FINAL: exact data at the bisected temperature
-            s[6] = 0.0;
-            next = M_ACCEPT;
-            if (Te <= kTmin * (1.0 + 1e-9) || Te >= kTmax * (1.0 - 1e-9)) atomicAdd(&cnt_bad, 1ULL);
-          }
-          s[4] = (double)next;
-        }
-        __syncthreads();
-        const int m2 = (int)s[4];
-        if (m2 == M_ACCEPT && mode < M_ACCEPT) {  // I0 refresh from the model at T_e
-          const double dlt = s[6];
-          const double hd2 = 0.5 * dlt * dlt;
-          for (int v = 0; v < V; ++v) a.I0cell[P * nbp + b0 + v] = fma(Jd2[v], hd2, fma(Jd1[v], dlt, Jf[v]));
-          if (lane == 0) a.Tp[P] = Te + dlt;
-        }
-        __syncthreads();
-        if (lane == 0 && m2 == M_ACCEPT) s[4] = (double)M_DONE;
-        const int pending = (lane == 0 && (int)s[4] < M_ACCEPT) ? 1 : 0;
-        if (!__syncthreads_or(pending)) break;
-      }
-      if (lane == 0 && (int)cst[8 * slot + 4] < M_ACCEPT) atomicAdd(&cnt_bad, 1ULL);
-    }
-    __syncthreads();
   }
-  __syncthreads();
-  if (threadIdx.x == 0 && a.counters) {
-    if (cnt_evals) atomicAdd(&a.counters->evals, cnt_evals);
-    if (cnt_solves) atomicAdd(&a.counters->solves, cnt_solves);
-    if (cnt_fb) atomicAdd(&a.counters->fallbacks, cnt_fb);
-    if (cnt_bad) atomicAdd(&a.counters->nonfinite, cnt_bad);
+  if (lane == 0 && a.counters) {
+    if (evals) atomicAdd(&a.counters->evals, evals);
+    if (fb) atomicAdd(&a.counters->fallbacks, fb);
+    if (bad) atomicAdd(&a.counters->nonfinite, bad);
   }
 }
 
@@ -563,13 +278,6 @@ __device__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// Full intensity value (FP64) of element e of a padded row set.
-template <typename S>
-__device__ __forceinline__ double full_I(const S* I, long long e, int b, const double* I0ref) {
-  if constexpr (sizeof(S) == 8) return (double)I[e];
-  else return I0ref[b] + Tr<S>::to_double(I[e]);
-}
-
 // Cell heat flux q(P) = sum_b sum_d S_d I_{d,b}: one CTA per cell.
 template <typename S>
 __global__ void flux_cells_kernel(const S* I, const double* I0ref, double* q, const double* Sd, long long cell0,
@@ -681,23 +389,19 @@ inline int grid_for(long long n, int threads) {
 
 inline int cell_grid(long long ncells) { return (int)(ncells < 152 * 16 ? (ncells < 1 ? 1 : ncells) : 152 * 16); }
 
-template <typename S>
-cudaError_t sweep_dispatch(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
-  const int cpb = threads / a.lpc;
-  const size_t smem = (3 * (size_t)threads + 8 * (size_t)cpb) * sizeof(double);
-  if (dim == 3) sweep_kernel<3, S><<<grid, threads, smem, s>>>(a);
-  else sweep_kernel<2, S><<<grid, threads, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
 }  // namespace
 
 int values_per_lane(int precision) { return precision == 0 ? 2 : 4; }
 
-cudaError_t launch_sweep(int precision, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
-  if (precision == 0) return sweep_dispatch<double>(a, dim, threads, grid, s);
-  if (precision == 1) return sweep_dispatch<float>(a, dim, threads, grid, s);
-  return sweep_dispatch<__nv_bfloat16>(a, dim, threads, grid, s);
+cudaError_t launch_sweep(int precision, int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
+  if (precision == 0) return launch_sweep_fp64(pd, a, dim, threads, grid, s);
+  if (precision == 1) return launch_sweep_fp32(pd, a, dim, threads, grid, s);
+  return launch_sweep_bf16(pd, a, dim, threads, grid, s);
+}
+
+cudaError_t launch_fixup(const SweepArgs& a, cudaStream_t s) {
+  fixup_kernel<<<152, 128, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_init_cells(int precision, void* I, double* I0cell, double* J, double* Tp, double* Te, double* TL,

@@ -1,0 +1,428 @@
+// bte_sweep.cuh -- the sweep kernel of one inner iteration (sm_103a).
+//
+// sweep_kernel<DIM, S, MINB>: a CTA owns a run of cells of one geometry; each
+// cell is served by a team of lpc x dteam lanes.  Lane (q, l) holds the V
+// consecutive bands V*l.. as one vector (FP64: 2 doubles, FP32: 4 floats,
+// BF16: 4 bf16) and walks the directions d = q, q + dteam, ...; a team step
+// thus covers dteam consecutive directions of the cell's row, ~0.9 KB of
+// contiguous memory per array, which is what keeps HBM streaming at full
+// rate (one 16-byte vector per row per step reaches only ~70 %).  For every
+// (cell, direction, band) (Sec. 3.1, Eq. 5):
+//   FP64     I^{k+1} = A_n I^n + A_x I_up,x^k + A_y I_up,y^k (+ A_z I_up,z^k) + A_s I0^k
+//   FP32/BF16 I^{k+1} = P I^n + Q (v_b sum_ax c_ax I_up,ax^k + beta_b I0^k)
+// (implicit: point-Jacobi sweep of backward Euler; explicit: forward Euler with
+// I^k = I^n).  The upwind value is the neighbour cell on the side S_d comes
+// from, or the Eq. 6 ghost at a wall (I0 of the wall face, or the cell's own
+// value in the mirrored direction).  FP32 and BF16 store the deviation
+// I - I0_b(T_ref): the update is affine with coefficients summing to one, so
+// the deviation obeys the same update with I0 and wall ghosts shifted.
+// Each lane accumulates its part of G_b = sum_d w_d I^{k+1}_{d,b} in registers
+// (FP64, or a compensated float pair); the epilogue adds the dteam partials
+// per band in a fixed order, reduces the bands to E_L and E_p and solves the
+// T_p equation on the
+// cell's cached quadratic model of I0_b(T) (I0, dI0/dT, d2I0/dT2 at its last
+// exact evaluation point T_e).  The model root is accepted inside the trust
+// radius |T - T_e| <= trust_rel T, where the Taylor remainder is below the
+// solve tolerance, and I0 is refreshed from it; other cells go to the fix-up
+// kernel (exact FP64 band quadrature).
+// Memory: I^n is read once, I^{k+1} written once, and each I^k row read from
+// DRAM once (adjacent cells, processed together, re-read it from L2).  Loads of
+// I^n and upwind I^k for a lane's next direction are issued before the current
+// one is computed; optionally one lane per cell also prefetches the next
+// pf_dirs directions of its rows into L2 with the bulk-copy engine.  MINB is
+// the launch-bounds minimum of resident CTAs per SM (a register cap).
+#pragma once
+#include "bte_store.cuh"
+
+namespace bte {
+namespace sweep {
+
+// L2 prefetch of `bytes` (multiple of 16) from a 16-byte aligned global address
+// (bulk-async copy engine; a hint, nothing waits on it).
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Rows [d, d + n) of I^n for cell P and of I^k for every neighbour P may take
+// an upwind value from, into L2.
+template <int DIM, typename S>
+__device__ __forceinline__ void prefetch_rows(const SweepArgs& a, int gnx, int gny, int gnz, const S* In, const S* Ik,
+                                              long long P, int ci, int cj, int ck, long long row, int d, int n) {
+  const unsigned bytes = (unsigned)n * a.th.nbp * sizeof(S);
+  const size_t off = (size_t)d * a.th.nbp;
+  prefetch_l2(In + P * row + off, bytes);
+  if (ci > 0) prefetch_l2(Ik + (P - 1) * row + off, bytes);
+  if (ci < gnx - 1) prefetch_l2(Ik + (P + 1) * row + off, bytes);
+  if (cj > 0) prefetch_l2(Ik + (P - gnx) * row + off, bytes);
+  if (cj < gny - 1) prefetch_l2(Ik + (P + gnx) * row + off, bytes);
+  if (DIM == 3) {
+    const long long pl = (long long)gnx * gny;
+    if (ck > 0) prefetch_l2(Ik + (P - pl) * row + off, bytes);
+    if (ck < gnz - 1) prefetch_l2(Ik + (P + pl) * row + off, bytes);
+  }
+}
+
+// Long-latency operands of one direction for one lane.
+template <typename S>
+struct Far {
+  typename Tr<S>::A vn[Tr<S>::V], ux[Tr<S>::V], uy[Tr<S>::V], uz[Tr<S>::V];
+};
+
+// Per-cell addressing of one lane: its rows in I^n, I^k, I^{k+1} (band offset
+// applied), the element strides to the x/y/z neighbours and which sides are
+// walls, so a direction's upwind address is one select and one add.
+template <typename S>
+struct CellAddr {
+  const S* in;
+  const S* ik;
+  S* out;
+  long long sx, sy, sz;
+  int wall;      // bit 2*ax: low wall along ax, bit 2*ax+1: high wall
+  int ci, cj, ck;
+};
+
+// Eq. 6 ghost of a wall side for (cell, direction d): I0 of the face
+// (isothermal; a deviation from I0_b(T_ref) in the reduced modes) or the
+// cell's own value in the mirrored direction (specular).
+template <int AX, typename S>
+__device__ __forceinline__ void wall_ghost(const SweepArgs& a, const DevGeom* gp, const CellAddr<S>& c, const int4 di,
+                                        bool from_low, int b0, typename Tr<S>::A (&x)[Tr<S>::V]) {
+  using T = Tr<S>;
+  const int nbp = a.th.nbp;
+  const int side = 2 * AX + (from_low ? 0 : 1);
+  const int bc = gp->bc[side];  // wall data stay in memory (L1): only wall cells get here
+  if (bc == 0) {
+    const long long f0 = gp->face0[side];
+    const long long f = f0 + (AX == 0 ? c.cj + (long long)gp->ny * c.ck
+                                      : (AX == 1 ? c.ci + (long long)gp->nx * c.ck : c.ci + (long long)gp->nx * c.cj));
+    if constexpr (sizeof(S) == 8) ldgv<double, T::V>(a.I0wall + f * nbp + b0, x);
+    else ldgv<float, T::V>(a.I0wall_dev + f * nbp + b0, x);
+    return;
+  }
+  const int r = AX == 0 ? di.y : (AX == 1 ? di.z : di.w);
+  T::ld(c.ik + (long long)r * nbp, x);
+}
+
+template <int AX, typename S>
+__device__ __forceinline__ void load_up(const SweepArgs& a, const DevGeom* gp, const CellAddr<S>& c, const int4 di,
+                                        long long off, int b0, typename Tr<S>::A (&x)[Tr<S>::V]) {
+  const bool from_low = (di.x >> AX) & 1;
+  const int wbit = 2 * AX + (from_low ? 0 : 1);
+  if (!((c.wall >> wbit) & 1)) {
+    const long long st = AX == 0 ? c.sx : (AX == 1 ? c.sy : c.sz);
+    Tr<S>::ld(c.ik + (from_low ? -st : st) + off, x);
+  } else {
+    wall_ghost<AX, S>(a, gp, c, di, from_low, b0, x);
+  }
+}
+
+template <int DIM, typename S>
+__device__ __forceinline__ void load_far(Far<S>& o, const SweepArgs& a, const DevGeom* gp, const CellAddr<S>& c,
+                                         const int4 di, long long off, int b0) {
+  Tr<S>::ld_stream(c.in + off, o.vn);
+  load_up<0, S>(a, gp, c, di, off, b0, o.ux);
+  load_up<1, S>(a, gp, c, di, off, b0, o.uy);
+  if (DIM == 3) load_up<2, S>(a, gp, c, di, off, b0, o.uz);
+}
+
+// Shared per-direction table of the current cell-size class.
+struct DirSm {
+  int4 info;     // up flags, rx, ry, rz
+  float4 c;      // reduced modes: c_ax = |S_d,ax| / (w_d Delta_ax)
+  double w;      // w_d
+  float w32;
+  float pad;
+};
+
+template <int DIM, typename S, int MINB>
+__global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
+  using T = Tr<S>;
+  using A = typename T::A;
+  constexpr int V = T::V;
+  constexpr bool kDev = sizeof(S) != 8;  // reduced modes store deviations
+  extern __shared__ double sm[];
+  __shared__ unsigned long long cnt_solves, cnt_bad;
+  __shared__ int cur_cls;
+  const int lpc = a.lpc, nd = a.nd, nbp = a.th.nbp, dstep = a.dteam;
+  const int team = lpc * dstep;                       // lanes per cell
+  const int cpb = blockDim.x / team;
+  const int slot = threadIdx.x / team, tl = threadIdx.x - slot * team;
+  const int dg = tl / lpc, lane = tl - dg * lpc;      // direction offset in a step, band vector
+  DirSm* dsm = reinterpret_cast<DirSm*>(sm);          // [nd]
+  double* gsm = sm + (sizeof(DirSm) / 8) * nd;        // [blockDim.x][V] per-lane band partials
+  double* red = gsm + (size_t)V * blockDim.x;         // [cpb * lpc][5]
+  double* cst = red + 5 * (size_t)cpb * lpc;          // [cpb][2] per-cell solve state
+  const S* __restrict__ In = reinterpret_cast<const S*>(a.In);
+  const S* __restrict__ Ik = reinterpret_cast<const S*>(a.Ik);
+  S* __restrict__ Io = reinterpret_cast<S*>(a.Iout);
+  const A* __restrict__ coef = reinterpret_cast<const A*>(a.coef);
+  const long long row = (long long)nd * nbp;
+  const int b0 = V * lane;
+  if (threadIdx.x == 0) { cnt_solves = 0; cnt_bad = 0; cur_cls = -1; }
+  A vb[V], bb[V];  // per-lane band constants (reduced modes)
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    vb[v] = kDev ? (A)a.vb32[b0 + v] : (A)0;
+    bb[v] = kDev ? (A)a.bb32[b0 + v] : (A)0;
+  }
+  __syncthreads();
+
+  for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    const WorkItem wi = a.items[item];
+    const DevGeom* gp = a.geoms + wi.geom;
+    const int gnx = gp->nx, gny = gp->ny, gcls = gp->cls;
+    const int gnz = DIM == 3 ? gp->nz : 1;
+    if (gcls != cur_cls) {  // (block-uniform) direction table of this cell-size class
+      __syncthreads();
+      for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+        const DirInfo di = a.dirs[d];
+        DirSm e;
+        e.info = make_int4(di.up, di.rx, di.ry, di.rz);
+        e.c = kDev ? a.dirc[(size_t)gcls * nd + d] : make_float4(0.f, 0.f, 0.f, 0.f);
+        e.w = a.wdir[d];
+        e.w32 = a.wdir32[d];
+        e.pad = 0.f;
+        dsm[d] = e;
+      }
+      if (threadIdx.x == 0) cur_cls = gcls;
+      __syncthreads();
+    }
+    const bool active = slot < wi.cell_count;
+    const int lc = wi.cell_begin + (active ? slot : 0);
+    const int ci = lc % gnx, cj = (lc / gnx) % gny, ck = lc / (gnx * gny);
+    const long long P = gp->cell0 + lc;
+    double G[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) G[v] = 0.0;
+
+    if (active) {
+      A src[V];  // FP64: I0 of the cell; reduced: beta_b * (I0 - I0ref)
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const double i0 = a.I0cell[P * nbp + b0 + v];
+        src[v] = kDev ? bb[v] * (A)(i0 - a.I0ref[b0 + v]) : (A)i0;
+      }
+      const size_t plane = (size_t)nd * nbp;
+      const A* __restrict__ cf = coef + (size_t)gcls * 5 * plane + b0;
+      CellAddr<S> c;
+      c.in = In + P * row + b0;
+      c.ik = Ik + P * row + b0;
+      c.out = Io + P * row + b0;
+      c.sx = row;
+      c.sy = (long long)gnx * row;
+      c.sz = (long long)gnx * gny * row;
+      c.ci = ci; c.cj = cj; c.ck = ck;
+      c.wall = (ci == 0) | ((ci == gnx - 1) << 1) | ((cj == 0) << 2) | ((cj == gny - 1) << 3) |
+               (DIM == 3 ? ((ck == 0) << 4) | ((ck == gnz - 1) << 5) : 0);
+      const int pf = a.pf_dirs;
+      if (pf > 0 && tl == 0) prefetch_rows<DIM, S>(a, gnx, gny, gnz, In, Ik, P, ci, cj, ck, row, 0, min(pf, nd));
+      float acc[V];  // reduced modes: FP32 partial band sums, flushed to G every 16 steps
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = 0.f;
+      int nacc = 0;
+      // One direction of this lane: d, row offset off, operands in `cur`.
+      auto step = [&](const Far<S>& cur, int d, long long off) {
+        A r[V];
+        if constexpr (!kDev) {
+          A An[V], Ax[V], Ay[V], As[V];
+          ldgv<A, V>(cf + off, An);
+          ldgv<A, V>(cf + plane + off, Ax);
+          ldgv<A, V>(cf + 2 * plane + off, Ay);
+          ldgv<A, V>(cf + 4 * plane + off, As);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            r[v] = An[v] * cur.vn[v];
+            r[v] = fma(Ax[v], cur.ux[v], r[v]);
+            r[v] = fma(Ay[v], cur.uy[v], r[v]);
+          }
+          if (DIM == 3) {
+            A Az[V];
+            ldgv<A, V>(cf + 3 * plane + off, Az);
+#pragma unroll
+            for (int v = 0; v < V; ++v) r[v] = fma(Az[v], cur.uz[v], r[v]);
+          }
+#pragma unroll
+          for (int v = 0; v < V; ++v) r[v] = fma(As[v], src[v], r[v]);
+          T::st(c.out + off, r);
+          const double wd = dsm[d].w;
+#pragma unroll
+          for (int v = 0; v < V; ++v) G[v] = fma(wd, (double)r[v], G[v]);
+        } else {
+          // P and Q from v_b, beta_b and sum_ax c_ax (no table loads):
+          // implicit Q = 1/(1/dt + beta_b + v_b sum c), P = Q/dt; explicit P = 1 - dt(beta_b + v_b sum c), Q = dt
+          const float4 cc = dsm[d].c;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const A rate = fma(vb[v], cc.w, bb[v]);
+            A Pc, Qc;
+            if (a.explicit_scheme) {
+              Qc = a.dt32;
+              Pc = fma(-a.dt32, rate, 1.0f);
+            } else {
+              asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(Qc) : "f"(a.rdt32 + rate));
+              Pc = Qc * a.rdt32;
+            }
+            A f = cc.x * cur.ux[v];
+            f = fma(cc.y, cur.uy[v], f);
+            if (DIM == 3) f = fma(cc.z, cur.uz[v], f);
+            const A t = fma(vb[v], f, src[v]);
+            r[v] = fma(Qc, t, Pc * cur.vn[v]);
+          }
+          T::st(c.out + off, r);
+          const float wd = dsm[d].w32;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            float val = r[v];
+            if constexpr (sizeof(S) == 2) val = __bfloat162float(__float2bfloat16_rn(val));  // the stored value
+            acc[v] = fma(wd, val, acc[v]);
+          }
+          if (++nacc == 16) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) { G[v] += (double)acc[v]; acc[v] = 0.f; }
+            nacc = 0;
+          }
+        }
+      };
+      // This lane's directions are dg, dg + dstep, ...; operands of the next one
+      // are loaded before the current one is computed (two buffers, no copies).
+      const long long ostep = (long long)dstep * nbp;
+      int d = dg;
+      long long off = (long long)dg * nbp;
+      Far<S> A0, A1;
+      if (d < nd) load_far<DIM, S>(A0, a, gp, c, dsm[d].info, off, b0);
+      while (d < nd) {
+        const int d1 = d + dstep;
+        if (d1 < nd) load_far<DIM, S>(A1, a, gp, c, dsm[d1].info, off + ostep, b0);
+        if (pf > 0 && tl == 0 && d % pf == 0 && d + pf < nd)
+          prefetch_rows<DIM, S>(a, gnx, gny, gnz, In, Ik, P, ci, cj, ck, row, d + pf, min(pf, nd - d - pf));
+        step(A0, d, off);
+        if (d1 >= nd) break;
+        const int d2 = d1 + dstep;
+        if (d2 < nd) load_far<DIM, S>(A0, a, gp, c, dsm[d2].info, off + 2 * ostep, b0);
+        step(A1, d1, off + ostep);
+        d = d2;
+        off += 2 * ostep;
+      }
+      if constexpr (kDev) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) G[v] += (double)acc[v];
+      }
+    }
+
+    // ---- per-cell reduction.  The lanes of a cell hold band partials over their
+    // direction subsets; the band owners (dg == 0) add them in a fixed order to
+    // G_b, then E_L = sum_b G_b / v_b, E_p = sum_b beta_b G_b / v_b and the sums of
+    // the T_p equation's terms on the cached quadratic model around T_e.
+#pragma unroll
+    for (int v = 0; v < V; ++v) gsm[(size_t)threadIdx.x * V + v] = G[v];
+    __syncthreads();
+    if (dg == 0) {
+      double eL = 0.0, ep = 0.0, F = 0.0, F1 = 0.0, F2 = 0.0;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        double Gb = kDev ? a.Wtot * a.I0ref[b0 + v] : 0.0;
+        for (int q = 0; q < dstep; ++q) Gb += gsm[(size_t)(slot * team + q * lpc + lane) * V + v];
+        const double e = Gb * a.th.inv_v[b0 + v];
+        eL += e;
+        ep = fma(a.th.beta[b0 + v], e, ep);
+      }
+      if (active && a.solve_tp) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const double ap = a.th.a_p[b0 + v];
+          F = fma(ap, a.J[(P * 3 + 0) * nbp + b0 + v], F);
+          F1 = fma(ap, a.J[(P * 3 + 1) * nbp + b0 + v], F1);
+          F2 = fma(ap, a.J[(P * 3 + 2) * nbp + b0 + v], F2);
+        }
+      }
+      double* r5 = red + 5 * (size_t)(slot * lpc + lane);
+      r5[0] = eL;
+      r5[1] = ep;
+      r5[2] = F;
+      r5[3] = F1;
+      r5[4] = F2;
+    }
+    __syncthreads();
+    if (tl == 0) {
+      double EL = 0.0, Ep = 0.0, Fs = 0.0, F1s = 0.0, F2s = 0.0;
+      for (int l = 0; l < lpc; ++l) {
+        const double* r5 = red + 5 * (size_t)(slot * lpc + l);
+        EL += r5[0];
+        Ep += r5[1];
+        Fs += r5[2];
+        F1s += r5[3];
+        F2s += r5[4];
+      }
+      Fs -= Ep;  // residual of the T_p equation on the model at T_e
+      double* st = cst + 2 * slot;
+      st[0] = 0.0;   // accepted step from T_e
+      st[1] = 0.0;   // 1 when the cached model is accepted
+      if (active) {
+        if (!a.dry) a.EL[P] = EL;
+        if (!isfinite(EL) || !isfinite(Ep)) {
+          atomicAdd(&cnt_bad, 1ULL);
+        } else if (a.solve_tp) {
+          atomicAdd(&cnt_solves, 1ULL);
+          // root of Fs + F1s d + F2s d^2 / 2 nearest 0
+          const double Te = a.Teval[P];
+          const double disc = F1s * F1s - 2.0 * Fs * F2s;
+          const double delta = (disc >= 0.0 && F1s > 0.0) ? -2.0 * Fs / (F1s + sqrt(disc)) : -Fs / F1s;
+          const double Tn = Te + delta;
+          if ((isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn) || a.dry) {
+            st[0] = delta;
+            st[1] = 1.0;
+          } else {  // exact quadrature needed: hand the cell to the fix-up kernel
+            const unsigned k = atomicAdd(a.fix_count, 1u);
+            FixItem fi;
+            fi.P = P;
+            fi.Ep = Ep;
+            fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[P];
+            a.fix[k] = fi;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (dg == 0 && active && a.solve_tp && !a.dry && cst[2 * slot + 1] != 0.0) {  // I0 refresh from the model
+      const double dlt = cst[2 * slot];
+      const double hd2 = 0.5 * dlt * dlt;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const long long j = (P * 3) * nbp + b0 + v;
+        a.I0cell[P * nbp + b0 + v] = fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], dlt, a.J[j]));
+      }
+      if (lane == 0) a.Tp[P] = a.Teval[P] + dlt;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && a.counters) {
+    if (cnt_solves) atomicAdd(&a.counters->solves, cnt_solves);
+    if (cnt_bad) atomicAdd(&a.counters->nonfinite, cnt_bad);
+  }
+}
+
+template <typename S, int MINB>
+cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
+  const int team = a.lpc * a.dteam, cpb = threads / team;
+  const size_t smem = sizeof(DirSm) * (size_t)a.nd + (size_t)Tr<S>::V * threads * sizeof(double) +
+                      5 * (size_t)cpb * a.lpc * sizeof(double) + 2 * (size_t)cpb * sizeof(double);
+  if (dim == 3) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(sweep_kernel<3, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sweep_kernel<3, S, MINB><<<grid, threads, smem, s>>>(a);
+  } else {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(sweep_kernel<2, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sweep_kernel<2, S, MINB><<<grid, threads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// variant: 1 -> at least 2 resident CTAs per SM (<= 128 registers), 2 -> 3 CTAs (<= 80 registers)
+template <typename S>
+cudaError_t launch(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
+  if (variant >= 2) return launch_minb<S, 3>(a, dim, threads, grid, s);
+  return launch_minb<S, 2>(a, dim, threads, grid, s);
+}
+
+}  // namespace sweep
+}  // namespace bte

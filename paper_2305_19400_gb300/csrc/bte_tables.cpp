@@ -171,4 +171,32 @@ void build_coef(int dim, const double delta[3], int nd, const double* S, const d
   }
 }
 
+// Reduced-precision form of the same update: I' = P I^n + Q (v_b sum_ax c_ax I_up + beta_b I0),
+// P and Q per (d, b) as float, c_ax = |S_d,ax|/(w_d Delta_ax) per direction.
+//   implicit: Q = 1/(1/dt + beta_b + v_b sum c), P = Q/dt;  explicit: P = 1 - dt(beta_b + v_b sum c), Q = dt.
+void build_pq(int dim, const double delta[3], int nd, const double* S, const double* w, int nb, int nbp,
+              const double* vg, const double* beta, double dt, int explicit_scheme, float* P, float* Q, float* dirc) {
+  for (size_t e = 0; e < (size_t)nd * nbp; ++e) P[e] = Q[e] = 0.0f;
+  for (int d = 0; d < nd; ++d) {
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int ax = 0; ax < dim; ++ax) c[ax] = std::fabs(S[3 * d + ax]) / (w[d] * delta[ax]);
+    dirc[4 * d + 0] = (float)c[0];
+    dirc[4 * d + 1] = (float)c[1];
+    dirc[4 * d + 2] = (float)c[2];
+    dirc[4 * d + 3] = (float)(c[0] + c[1] + c[2]);
+    const double csum = c[0] + c[1] + c[2];
+    for (int b = 0; b < nb; ++b) {
+      const size_t o = (size_t)d * nbp + b;
+      if (explicit_scheme) {
+        P[o] = (float)(1.0 - dt * (beta[b] + vg[b] * csum));
+        Q[o] = (float)dt;
+      } else {
+        const double inv = 1.0 / (1.0 / dt + beta[b] + vg[b] * csum);
+        P[o] = (float)(inv / dt);
+        Q[o] = (float)inv;
+      }
+    }
+  }
+}
+
 }  // namespace bte

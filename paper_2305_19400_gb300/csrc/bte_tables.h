@@ -14,4 +14,7 @@ void build_thermo(int nb, int nbp, int ng, const double* wlo, const double* whi,
 void build_coef(int dim, const double delta[3], int nd, const double* S, const double* w, int nb, int nbp,
                 const double* vg, const double* beta, double dt, int explicit_scheme, double* out);
 
+void build_pq(int dim, const double delta[3], int nd, const double* S, const double* w, int nb, int nbp,
+              const double* vg, const double* beta, double dt, int explicit_scheme, float* P, float* Q, float* dirc);
+
 }  // namespace bte
