@@ -35,7 +35,7 @@ METRIC = "cell·dir·band updates/s and % HBM roofline at stated max|ΔT| vs FP6
 UNIT = "updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.json")
-KERNEL_SRC = os.path.join(ROOT, "paper_2305_19400_gb300", "csrc", "bte_kernels.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2305_19400_gb300", "csrc", f) for f in ("bte_sweep.cuh", "bte_store.cuh")]
 # FP64 pipe peak: the nominal 1.25 TFLOP/s corresponds to 2 DFMA/clk/SM on 152 SMs at 2070 MHz.
 FP64_PEAK_FLOPS = 2 * 2 * 152 * 2.070e9
 # Algorithmic work of one 2-D implicit update: A_n*I^n + A_x*I_x + A_y*I_y + A_s*I0 (4 mul + 3 add)
@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--ninner", type=int, default=15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="plain launches: no autotuning, no CUDA graph")
     return ap.parse_args()
 
 
@@ -134,7 +136,10 @@ def traffic_per_update():
         rec = json.load(open(TRAFFIC_FILE))
     except (OSError, ValueError):
         return None
-    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    hsh = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        hsh.update(open(f, "rb").read())
+    sha = hsh.hexdigest()[:16]
     if rec.get("kernel_source_sha") != sha:
         return None
     return rec.get("dram_bytes_per_update")
@@ -199,6 +204,45 @@ def cpu_baseline_for(args):
             "sample": f"full {args.nx}x{args.ny} grid, 1 time step x {args.ninner} inner iterations ({u:.3g} updates, {s:.1f} s)"}
 
 
+def run_variants(peaks):
+    """The reduced-precision and batched forms of the path, each on its own workload:
+    FP32 and BF16 storage on the 3-D 64^3 x 400 x 55 workload (15 inner iterations per
+    step) and the 48-geometry FP32 batch (12 inner iterations), all with CUDA graphs and
+    the autotuner.  Device-timed like the main line; bytes per update are the algorithmic
+    3 x storage size."""
+    import torch
+    from paper_2305_19400_gb300 import bte, workloads as W
+    out = []
+    cases = [("fp32_3d_64^3", W.cfg3(64), bte.BTE_FP32, 4, 15), ("bf16_3d_64^3", W.cfg3(64, "bf16"), bte.BTE_BF16, 4, 15),
+             ("fp32_batch_48_geometries", W.cfg5(), bte.BTE_FP32, 3, 12)]
+    for name, wl, prec, steps, ninner in cases:
+        s = bte.Solver(wl, precision=prec, use_graph=True)
+        choice = bte.bte_autotune(s.h, wl.dt).strip().splitlines()[-1]
+        s.step(nsteps=1, ninner=ninner, want_stats=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            s.step(nsteps=1, ninner=ninner, want_stats=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ups = wl.dof * ninner * steps / (ms * 1e-3)
+        bpu = 12 if prec == bte.BTE_FP32 else 6
+        gbs = ups * bpu / 1e9
+        out.append({"workload": name, "dtype": "f32" if prec == bte.BTE_FP32 else "bf16-storage/f32", "value": ups,
+                    "unit": UNIT, "ms_per_step": ms / steps, "inner_iterations_per_step": ninner,
+                    "cells": sum(g.ncells for g in wl.geoms),
+                    "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": gbs / peaks["hbm_gbs"], "bytes_per_update": bpu},
+                    "launch": choice})
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -220,7 +264,9 @@ def main():
     stream = torch.cuda.current_stream()
     wl = W.cfg2(args.nx, args.ny, nsteps=1, ninner=args.ninner)
     g = wl.geoms[0]
-    solver = bte.Solver(wl, stream=stream)
+    tuned = not args.no_tune
+    solver = bte.Solver(wl, stream=stream, use_graph=tuned)
+    tune_choice = bte.bte_autotune(solver.h, wl.dt).strip().splitlines()[-1] if tuned else "untuned"
     updates_per_step = wl.dof * args.ninner
 
     def step():
@@ -311,6 +357,9 @@ def main():
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_for(args)
+    variants = None
+    if world == 1 and not args.no_variants:
+        variants = run_variants(peaks)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -318,8 +367,11 @@ def main():
                       "band_pols": 55, "inner_iterations_per_step": args.ninner, "dt_s": wl.dt,
                       "scheme": "implicit Euler, point-Jacobi inner iterations",
                       "l2": "inputs larger than L2 (three FP64 intensity buffers of %.2f GB each)" % (wl.dof * 8 / 1e9),
+                      "launch": ("CUDA graph per time step, autotuned (cells_per_cta,threads,grid,min_ctas,l2_prefetch): "
+                                 + tune_choice) if tuned else "eager launches, default tiles",
                       "parallelism": f"replicas x{world}"},
-           "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
+           "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+           "variants": variants}
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -62,12 +62,6 @@ __device__ __forceinline__ void prefetch_rows(const SweepArgs& a, int gnx, int g
   }
 }
 
-// Long-latency operands of one direction for one lane.
-template <typename S>
-struct Far {
-  typename Tr<S>::A vn[Tr<S>::V], ux[Tr<S>::V], uy[Tr<S>::V], uz[Tr<S>::V];
-};
-
 // Per-cell addressing of one lane: its rows in I^n, I^k, I^{k+1} (band offset
 // applied), the element strides to the x/y/z neighbours and which sides are
 // walls, so a direction's upwind address is one select and one add.
@@ -81,48 +75,51 @@ struct CellAddr {
   int ci, cj, ck;
 };
 
-// Eq. 6 ghost of a wall side for (cell, direction d): I0 of the face
-// (isothermal; a deviation from I0_b(T_ref) in the reduced modes) or the
+// Address of the Eq. 6 ghost of a wall side for (cell, direction): I0 of the
+// face (isothermal; a deviation from I0_b(T_ref) in the reduced modes) or the
 // cell's own value in the mirrored direction (specular).
 template <int AX, typename S>
-__device__ __forceinline__ void wall_ghost(const SweepArgs& a, const DevGeom* gp, const CellAddr<S>& c, const int4 di,
-                                        bool from_low, int b0, typename Tr<S>::A (&x)[Tr<S>::V]) {
-  using T = Tr<S>;
+__device__ __forceinline__ const void* wall_ghost_src(const SweepArgs& a, const DevGeom* gp, const CellAddr<S>& c,
+                                                      const int4 di, bool from_low, int b0) {
   const int nbp = a.th.nbp;
   const int side = 2 * AX + (from_low ? 0 : 1);
-  const int bc = gp->bc[side];  // wall data stay in memory (L1): only wall cells get here
-  if (bc == 0) {
-    const long long f0 = gp->face0[side];
-    const long long f = f0 + (AX == 0 ? c.cj + (long long)gp->ny * c.ck
-                                      : (AX == 1 ? c.ci + (long long)gp->nx * c.ck : c.ci + (long long)gp->nx * c.cj));
-    if constexpr (sizeof(S) == 8) ldgv<double, T::V>(a.I0wall + f * nbp + b0, x);
-    else ldgv<float, T::V>(a.I0wall_dev + f * nbp + b0, x);
-    return;
+  if (gp->bc[side] == 0) {  // wall data stay in memory (L1): only wall cells get here
+    const long long f = gp->face0[side] + (AX == 0 ? c.cj + (long long)gp->ny * c.ck
+                                                  : (AX == 1 ? c.ci + (long long)gp->nx * c.ck : c.ci + (long long)gp->nx * c.cj));
+    if constexpr (sizeof(S) == 8) return a.I0wall + f * nbp + b0;
+    else return a.I0wall_dev + f * nbp + b0;
   }
   const int r = AX == 0 ? di.y : (AX == 1 ? di.z : di.w);
-  T::ld(c.ik + (long long)r * nbp, x);
+  return c.ik + (long long)r * nbp;
 }
 
+// Address of the upwind value along axis AX for direction row offset `off`.
 template <int AX, typename S>
-__device__ __forceinline__ void load_up(const SweepArgs& a, const DevGeom* gp, const CellAddr<S>& c, const int4 di,
-                                        long long off, int b0, typename Tr<S>::A (&x)[Tr<S>::V]) {
+__device__ __forceinline__ const void* upwind_src(const SweepArgs& a, const DevGeom* gp, const CellAddr<S>& c,
+                                                  const int4 di, long long off, int b0) {
   const bool from_low = (di.x >> AX) & 1;
   const int wbit = 2 * AX + (from_low ? 0 : 1);
   if (!((c.wall >> wbit) & 1)) {
     const long long st = AX == 0 ? c.sx : (AX == 1 ? c.sy : c.sz);
-    Tr<S>::ld(c.ik + (from_low ? -st : st) + off, x);
-  } else {
-    wall_ghost<AX, S>(a, gp, c, di, from_low, b0, x);
+    return c.ik + (from_low ? -st : st) + off;
   }
+  return wall_ghost_src<AX, S>(a, gp, c, di, from_low, b0);
 }
 
-template <int DIM, typename S>
-__device__ __forceinline__ void load_far(Far<S>& o, const SweepArgs& a, const DevGeom* gp, const CellAddr<S>& c,
-                                         const int4 di, long long off, int b0) {
-  Tr<S>::ld_stream(c.in + off, o.vn);
-  load_up<0, S>(a, gp, c, di, off, b0, o.ux);
-  load_up<1, S>(a, gp, c, di, off, b0, o.uy);
-  if (DIM == 3) load_up<2, S>(a, gp, c, di, off, b0, o.uz);
+// Asynchronous global -> shared copy of one lane vector (16 or 8 bytes), L2 only.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(unsigned smem, const void* g) {
+  if constexpr (BYTES == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem), "l"(g) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Operand vector of this lane from the staging ring.
+template <typename S>
+__device__ __forceinline__ void ld_stage(const char* p, typename Tr<S>::A (&x)[Tr<S>::V]) {
+  Tr<S>::ld(reinterpret_cast<const S*>(p), x);
 }
 
 // Shared per-direction table of the current cell-size class.
@@ -133,6 +130,8 @@ struct DirSm {
   float w32;
   float pad;
 };
+
+constexpr int kStages = 4;  // depth of the cp.async staging ring
 
 template <int DIM, typename S, int MINB>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
@@ -152,6 +151,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   double* gsm = sm + (sizeof(DirSm) / 8) * nd;        // [blockDim.x][V] per-lane band partials
   double* red = gsm + (size_t)V * blockDim.x;         // [cpb * lpc][5]
   double* cst = red + 5 * (size_t)cpb * lpc;          // [cpb][2] per-cell solve state
+  // staging ring of the far operands: [kStages][kOps][blockDim.x] x 16 bytes
+  char* ring = reinterpret_cast<char*>(
+      (reinterpret_cast<uintptr_t>(cst + 2 * (size_t)cpb) + 15) & ~static_cast<uintptr_t>(15));
   const S* __restrict__ In = reinterpret_cast<const S*>(a.In);
   const S* __restrict__ Ik = reinterpret_cast<const S*>(a.Ik);
   S* __restrict__ Io = reinterpret_cast<S*>(a.Iout);
@@ -220,8 +222,63 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[v] = 0.f;
       int nacc = 0;
-      // One direction of this lane: d, row offset off, operands in `cur`.
-      auto step = [&](const Far<S>& cur, int d, long long off) {
+      // This lane's directions are d_j = dg + j*dstep.  Their operands (I^n and the
+      // upwind I^k or wall ghost per axis) are copied global -> shared kStages-1
+      // directions ahead with cp.async; each thread waits only for its own copies.
+      constexpr int kOps = DIM == 3 ? 4 : 3;
+      constexpr int kVB = V * (int)sizeof(S);
+      const int nsteps = dg < nd ? (nd - dg + dstep - 1) / dstep : 0;
+      auto slot = [&](int st, int op) -> char* {
+        return ring + ((size_t)(st * kOps + op) * blockDim.x + threadIdx.x) * 16;
+      };
+      auto issue = [&](int j) {
+        if (j < nsteps) {
+          const int d = dg + j * dstep;
+          const long long off = (long long)d * nbp;
+          const int4 di = dsm[d].info;
+          const int st = j % kStages;
+          cp_async<kVB>((unsigned)__cvta_generic_to_shared(slot(st, 0)), c.in + off);
+#pragma unroll
+          for (int ax = 0; ax < DIM; ++ax) {
+            const void* src_p = ax == 0 ? upwind_src<0, S>(a, gp, c, di, off, b0)
+                              : (ax == 1 ? upwind_src<1, S>(a, gp, c, di, off, b0) : upwind_src<2, S>(a, gp, c, di, off, b0));
+            const bool iso_ghost = (sizeof(S) == 2) && ((c.wall >> (2 * ax + (((di.x >> ax) & 1) ? 0 : 1))) & 1) &&
+                                   gp->bc[2 * ax + (((di.x >> ax) & 1) ? 0 : 1)] == 0;
+            if (iso_ghost) cp_async<16>((unsigned)__cvta_generic_to_shared(slot(st, 1 + ax)), src_p);  // float4 ghost
+            else cp_async<kVB>((unsigned)__cvta_generic_to_shared(slot(st, 1 + ax)), src_p);
+          }
+        }
+        cp_async_commit();
+      };
+      // Upwind operand of axis ax for direction d from its slot (BF16 iso ghosts are float4).
+      auto read_up = [&](int st, int ax, const int4 di, A (&x)[V]) {
+        if constexpr (sizeof(S) == 2) {
+          const bool lowside = (di.x >> ax) & 1;
+          const int side = 2 * ax + (lowside ? 0 : 1);
+          if (((c.wall >> side) & 1) && gp->bc[side] == 0) {
+            const float4 f = *reinterpret_cast<const float4*>(slot(st, 1 + ax));
+            x[0] = f.x; x[1] = f.y; x[2] = f.z; x[3] = f.w;
+            return;
+          }
+        }
+        ld_stage<S>(slot(st, 1 + ax), x);
+      };
+#pragma unroll
+      for (int j = 0; j < kStages - 1; ++j) issue(j);
+      for (int j = 0; j < nsteps; ++j) {
+        issue(j + kStages - 1);
+        cp_async_wait<kStages - 1>();
+        const int d = dg + j * dstep;
+        const long long off = (long long)d * nbp;
+        const int st = j % kStages;
+        if (pf > 0 && tl == 0 && d % pf == 0 && d + pf < nd)
+          prefetch_rows<DIM, S>(a, gnx, gny, gnz, In, Ik, P, ci, cj, ck, row, d + pf, min(pf, nd - d - pf));
+        const int4 di = dsm[d].info;
+        A vn[V], ux[V], uy[V], uz[V];
+        ld_stage<S>(slot(st, 0), vn);
+        read_up(st, 0, di, ux);
+        read_up(st, 1, di, uy);
+        if (DIM == 3) read_up(st, 2, di, uz);
         A r[V];
         if constexpr (!kDev) {
           A An[V], Ax[V], Ay[V], As[V];
@@ -231,15 +288,15 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
           ldgv<A, V>(cf + 4 * plane + off, As);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
-            r[v] = An[v] * cur.vn[v];
-            r[v] = fma(Ax[v], cur.ux[v], r[v]);
-            r[v] = fma(Ay[v], cur.uy[v], r[v]);
+            r[v] = An[v] * vn[v];
+            r[v] = fma(Ax[v], ux[v], r[v]);
+            r[v] = fma(Ay[v], uy[v], r[v]);
           }
           if (DIM == 3) {
             A Az[V];
             ldgv<A, V>(cf + 3 * plane + off, Az);
 #pragma unroll
-            for (int v = 0; v < V; ++v) r[v] = fma(Az[v], cur.uz[v], r[v]);
+            for (int v = 0; v < V; ++v) r[v] = fma(Az[v], uz[v], r[v]);
           }
 #pragma unroll
           for (int v = 0; v < V; ++v) r[v] = fma(As[v], src[v], r[v]);
@@ -262,11 +319,11 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
               asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(Qc) : "f"(a.rdt32 + rate));
               Pc = Qc * a.rdt32;
             }
-            A f = cc.x * cur.ux[v];
-            f = fma(cc.y, cur.uy[v], f);
-            if (DIM == 3) f = fma(cc.z, cur.uz[v], f);
+            A f = cc.x * ux[v];
+            f = fma(cc.y, uy[v], f);
+            if (DIM == 3) f = fma(cc.z, uz[v], f);
             const A t = fma(vb[v], f, src[v]);
-            r[v] = fma(Qc, t, Pc * cur.vn[v]);
+            r[v] = fma(Qc, t, Pc * vn[v]);
           }
           T::st(c.out + off, r);
           const float wd = dsm[d].w32;
@@ -282,27 +339,8 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
             nacc = 0;
           }
         }
-      };
-      // This lane's directions are dg, dg + dstep, ...; operands of the next one
-      // are loaded before the current one is computed (two buffers, no copies).
-      const long long ostep = (long long)dstep * nbp;
-      int d = dg;
-      long long off = (long long)dg * nbp;
-      Far<S> A0, A1;
-      if (d < nd) load_far<DIM, S>(A0, a, gp, c, dsm[d].info, off, b0);
-      while (d < nd) {
-        const int d1 = d + dstep;
-        if (d1 < nd) load_far<DIM, S>(A1, a, gp, c, dsm[d1].info, off + ostep, b0);
-        if (pf > 0 && tl == 0 && d % pf == 0 && d + pf < nd)
-          prefetch_rows<DIM, S>(a, gnx, gny, gnz, In, Ik, P, ci, cj, ck, row, d + pf, min(pf, nd - d - pf));
-        step(A0, d, off);
-        if (d1 >= nd) break;
-        const int d2 = d1 + dstep;
-        if (d2 < nd) load_far<DIM, S>(A0, a, gp, c, dsm[d2].info, off + 2 * ostep, b0);
-        step(A1, d1, off + ostep);
-        d = d2;
-        off += 2 * ostep;
       }
+      cp_async_wait<0>();
       if constexpr (kDev) {
 #pragma unroll
         for (int v = 0; v < V; ++v) G[v] += (double)acc[v];
@@ -406,7 +444,8 @@ template <typename S, int MINB>
 cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   const int team = a.lpc * a.dteam, cpb = threads / team;
   const size_t smem = sizeof(DirSm) * (size_t)a.nd + (size_t)Tr<S>::V * threads * sizeof(double) +
-                      5 * (size_t)cpb * a.lpc * sizeof(double) + 2 * (size_t)cpb * sizeof(double);
+                      5 * (size_t)cpb * a.lpc * sizeof(double) + 2 * (size_t)cpb * sizeof(double) + 16 +
+                      (size_t)kStages * (dim == 3 ? 4 : 3) * threads * 16;
   if (dim == 3) {
     if (smem > 48 * 1024) cudaFuncSetAttribute(sweep_kernel<3, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     sweep_kernel<3, S, MINB><<<grid, threads, smem, s>>>(a);
