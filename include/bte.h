@@ -67,7 +67,11 @@ typedef struct {
  *  precision  storage of I and the sweep arithmetic: BTE_FP64 (default),
  *             BTE_FP32 or BTE_BF16 (FP32 arithmetic); the reduction, the
  *             temperature solve and I0 are FP64 in every mode.
- *  learned    must be 0 (warm-started Halley/Newton temperature solve).
+ *  learned    0 (default): cells the cached-model solve cannot settle start
+ *             their exact solve from the model root; 1: they start from the
+ *             trained networks' guess (net A: E_p -> T, then surrogate Newton
+ *             steps on net B: T -> I0_b) before the exact FP64 refinement.
+ *             Requires bte_train_mlp before the first bte_step.
  *  n_gauss    Gauss-Legendre points per band for I0_b(T) (default 16, <= 32).
  *  newton_rtol target relative accuracy of the temperature solve (1e-14).
  *  newton_maxit iteration cap before the bisection fallback (50).
@@ -203,6 +207,38 @@ int bte_get_directions(bte_handle h, double* S, double* w, int* refl);
  * host or device per out_on_device.  Waits for the handle's stream. */
 int bte_get_wall_flux_noalloc(bte_handle h, int geom, double* q_walls, int out_on_device);
 /* (FP64-mode handles only; other precisions return BTE_E_ARG.) */
+
+/* Learned temperature / equilibrium guess (the path's pattern (4)): trains
+ * two 1-64-64-k tanh networks with FP32 weights on the device -- net A maps
+ * the normalised scattering-weighted energy E_p to T, net B maps T to the 55
+ * (nb) normalised ratios I0_b(T)/I0_b(T_ref) -- on n_pairs samples of T
+ * uniform in [T_lo, T_hi] K labelled by the library's FP64 band quadrature;
+ * `epochs` passes of Adam (minibatch 1024, learning rate 2e-3 decaying to
+ * 2e-4).  Forward, backward and update run in the library's kernels; training
+ * allocates its sample and activation buffers stream-ordered on cuda_stream
+ * and frees them before returning.  loss (host, may be NULL): 2 doubles, the
+ * final mean squared error of nets A and B in normalised units.
+ * 1024 <= n_pairs <= 2^26, 1 <= T_lo < T_hi <= 5000, epochs >= 1. */
+int bte_train_mlp(bte_handle h, long long n_pairs, double T_lo, double T_hi, int epochs, unsigned long long seed,
+                  double* loss);
+
+/* Parameters of net 0 (A) or 1 (B) as FP32 host arrays in the layout
+ * W1[64], b1[64], W2[64][64], b2[64], W3[k][64], b3[k] (k = 1 or nb).
+ * bte_mlp_params returns the parameter count (out may be NULL to query it). */
+int bte_mlp_params(bte_handle h, int net, float* out, int n);
+int bte_mlp_set_params(bte_handle h, int net, const float* in, int n);
+
+/* Mean squared error and its gradient for net 0/1 on n samples (host arrays):
+ * x[n] inputs, y[k][n] targets (sample index fastest), grad in the parameter
+ * layout, loss (may be NULL).  Uses the same device kernels as training. */
+int bte_mlp_grad(bte_handle h, int net, const float* x, const float* y, int n, float* grad, double* loss);
+
+/* Solves sum_b W beta_b I0_b(T)/v_b = Ep[i] for n energies (host arrays),
+ * starting from T0[i] (or 300 K when T0 is NULL) or, with learned = 1, from
+ * the trained networks' guess; exact FP64 Halley refinement to the solve
+ * tolerance, bisection fallback.  T_out[i] (NaN when no root lies in
+ * [1, 5000] K) and evals[i] (exact quadrature evaluations; may be NULL). */
+int bte_solve_T(bte_handle h, const double* Ep, const double* T0, int n, int learned, double* T_out, int* evals);
 
 /* Frees everything the library allocated (not a bound workspace). */
 int bte_destroy(bte_handle h);

@@ -64,6 +64,12 @@ SIGNATURES = {
     "bte_set_intensity": (C.c_int, [_h, C.c_int, _vp, _vp, C.c_int]),
     "bte_get_directions": (C.c_int, [_h, _dp, _dp, _ip]),
     "bte_get_wall_flux_noalloc": (C.c_int, [_h, C.c_int, _vp, C.c_int]),
+    "bte_train_mlp": (C.c_int, [_h, C.c_longlong, C.c_double, C.c_double, C.c_int, C.c_ulonglong, _dp]),
+    "bte_mlp_params": (C.c_int, [_h, C.c_int, C.POINTER(C.c_float), C.c_int]),
+    "bte_mlp_set_params": (C.c_int, [_h, C.c_int, C.POINTER(C.c_float), C.c_int]),
+    "bte_mlp_grad": (C.c_int, [_h, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int,
+                               C.POINTER(C.c_float), _dp]),
+    "bte_solve_T": (C.c_int, [_h, _dp, _dp, C.c_int, C.c_int, _dp, _ip]),
     "bte_destroy": (C.c_int, [_h]),
     "bte_last_error": (C.c_char_p, [_h]),
 }
@@ -195,6 +201,51 @@ def bte_get_wall_flux_noalloc(h, geom, q_walls):
     return _check(h, lib().bte_get_wall_flux_noalloc(h, geom, _ptr(q_walls), on_dev))
 
 
+def bte_train_mlp(h, n_pairs, T_lo, T_hi, epochs, seed=1):
+    loss = np.zeros(2)
+    _check(h, lib().bte_train_mlp(h, int(n_pairs), float(T_lo), float(T_hi), int(epochs), int(seed),
+                                  loss.ctypes.data_as(_dp)))
+    return loss
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def bte_mlp_params(h, net):
+    n = _check(h, lib().bte_mlp_params(h, int(net), None, 0))
+    out = np.zeros(n, dtype=np.float32)
+    _check(h, lib().bte_mlp_params(h, int(net), _fp(out), n))
+    return out
+
+
+def bte_mlp_set_params(h, net, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    return _check(h, lib().bte_mlp_set_params(h, int(net), _fp(p), p.size))
+
+
+def bte_mlp_grad(h, net, x, y):
+    """x: (n,), y: (k, n) float32; returns (grad, loss)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    n = x.size
+    g = np.zeros(_check(h, lib().bte_mlp_params(h, int(net), None, 0)), dtype=np.float32)
+    loss = C.c_double()
+    _check(h, lib().bte_mlp_grad(h, int(net), _fp(x), _fp(y), n, _fp(g), C.byref(loss)))
+    return g, loss.value
+
+
+def bte_solve_T(h, Ep, T0=None, learned=False):
+    Ep = np.ascontiguousarray(Ep, dtype=np.float64)
+    n = Ep.size
+    T = np.zeros(n)
+    ev = np.zeros(n, dtype=np.int32)
+    t0 = None if T0 is None else np.ascontiguousarray(T0, dtype=np.float64)
+    _check(h, lib().bte_solve_T(h, Ep.ctypes.data_as(_dp), None if t0 is None else t0.ctypes.data_as(_dp), n,
+                                1 if learned else 0, T.ctypes.data_as(_dp), ev.ctypes.data_as(_ip)))
+    return T, ev
+
+
 def bte_destroy(h):
     return _check(None, lib().bte_destroy(h))
 
@@ -213,7 +264,7 @@ class Solver:
     """
 
     def __init__(self, workload, precision=BTE_FP64, stream=None, bind_workspace=True, n_gauss=16, T_init=None,
-                 use_graph=False, autotune=False):
+                 use_graph=False, autotune=False, learned=False):
         import torch
 
         self.wl = workload
@@ -227,6 +278,7 @@ class Solver:
         o.precision = precision
         o.n_gauss = n_gauss
         o.use_graph = 1 if use_graph else 0
+        o.learned = 1 if learned else 0
         o.autotune = 1 if autotune else 0
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         o.cuda_stream = self.stream.cuda_stream

@@ -17,6 +17,7 @@
 
 #include "../../include/bte.h"
 #include "bte_internal.h"
+#include "bte_mlp.cuh"
 #include "bte_tables.h"
 
 using namespace bte;
@@ -73,6 +74,11 @@ struct bte_ctx {
   float4* dirc = nullptr;
   FixItem* fix = nullptr;
   unsigned* fix_count = nullptr;
+  // learned guess: parameters of nets A and B, Adam state, normalisation
+  float *mlp_p = nullptr, *mlp_g = nullptr, *mlp_m = nullptr, *mlp_v = nullptr;
+  double *mlp_rlo = nullptr, *mlp_rhi = nullptr, *mlp_elohi = nullptr;
+  bool mlp_trained = false;
+  double mlp_Tlo = 0.0, mlp_Thi = 0.0, mlp_Elo = 0.0, mlp_Ehi = 0.0;
   long long pack_cells = 0;
   double *wdir = nullptr, *Sdev = nullptr, *node_c = nullptr, *node_C = nullptr, *a_p = nullptr, *a_L = nullptr;
   double *inv_v = nullptr, *beta_d = nullptr, *scratch_faces = nullptr, *scratch_T = nullptr, *scratch_out = nullptr;
@@ -175,6 +181,14 @@ size_t carve(bte_ctx* h, char* base) {
   h->bb32 = (float*)take((size_t)h->nbp * 4);
   h->fix = (FixItem*)take((size_t)std::max<long long>(h->ncells, 1) * sizeof(FixItem));
   h->fix_count = (unsigned*)take(16);
+  const size_t np = (size_t)mlp_param_total(h->nb);
+  h->mlp_p = (float*)take(np * 4);
+  h->mlp_g = (float*)take(np * 4);
+  h->mlp_m = (float*)take(np * 4);
+  h->mlp_v = (float*)take(np * 4);
+  h->mlp_rlo = (double*)take((size_t)h->nbp * 8);
+  h->mlp_rhi = (double*)take((size_t)h->nbp * 8);
+  h->mlp_elohi = (double*)take(16);
   h->wdir = (double*)take((size_t)h->nd * 8);
   h->Sdev = (double*)take((size_t)h->nd * 3 * 8);
   h->dirs_d = (DirInfo*)take((size_t)h->nd * sizeof(DirInfo));
@@ -389,6 +403,21 @@ int copy_out(bte_ctx* h, double* out, const double* src, size_t n, int on_device
 
 namespace {
 
+MLPView mlp_view(const bte_ctx* h) {
+  MLPView m;
+  m.A = h->mlp_p;
+  m.B = h->mlp_p + mlp_param_count(1);
+  m.nb = h->nb;
+  m.T_lo = h->mlp_Tlo;
+  m.T_hi = h->mlp_Thi;
+  m.E_lo = h->mlp_Elo;
+  m.E_hi = h->mlp_Ehi;
+  m.r_lo = h->mlp_rlo;
+  m.r_hi = h->mlp_rhi;
+  m.I0ref = h->I0ref;
+  return m;
+}
+
 SweepArgs sweep_args(bte_ctx* h) {
   SweepArgs a{};
   a.I0cell = h->I0cell;
@@ -442,7 +471,14 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, cudaStream_t s, in
     a.Iout = h->Ibuf[o];
     cudaError_t e = cudaMemsetAsync(h->fix_count, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = launch_sweep(h->opts.precision, h->pd, a, dim, h->threads, h->grid, s);
-    if (e == cudaSuccess && h->solve_tp) e = launch_fixup(a, s);
+    if (e == cudaSuccess && h->solve_tp) {
+      if (h->opts.learned) {
+        const MLPView m = mlp_view(h);
+        e = launch_fixup(a, &m, s);
+      } else {
+        e = launch_fixup(a, nullptr, s);
+      }
+    }
     if (e != cudaSuccess) return e;
     k = o;
   }
@@ -515,7 +551,7 @@ int bte_init_mesh(bte_handle* out, int n_geom, const bte_geom* geoms, const bte_
   if (o.precision != BTE_FP64 && o.precision != BTE_FP32 && o.precision != BTE_BF16)
     return fail(nullptr, BTE_E_ARG, "unknown precision %d", o.precision);
   if (!(o.T_ref >= kTmin && o.T_ref <= kTmax)) return fail(nullptr, BTE_E_ARG, "T_ref must lie in [1, 5000] K");
-  if (o.learned != 0) return fail(nullptr, BTE_E_ARG, "learned mode is not available");
+  if (o.learned != 0 && o.learned != 1) return fail(nullptr, BTE_E_ARG, "learned must be 0 or 1");
   if (o.n_gauss < 1 || o.n_gauss > kMaxGauss) return fail(nullptr, BTE_E_ARG, "n_gauss must be in 1..%d", kMaxGauss);
   if (!(o.newton_rtol > 0 && o.newton_rtol < 1e-3) || o.newton_maxit < 1)
     return fail(nullptr, BTE_E_ARG, "newton_rtol must be in (0, 1e-3) and newton_maxit >= 1");
@@ -699,6 +735,7 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
   if (ninner < 1) return fail(h, BTE_E_ARG, "ninner must be >= 1");
   int rc = ensure_coef(h, dt, scheme);
   if (rc) return rc;
+  if (h->opts.learned && !h->mlp_trained) return fail(h, BTE_E_STATE, "learned mode needs bte_train_mlp first");
   if (h->opts.autotune && h->tune_report.empty()) {
     if ((rc = bte_autotune(h, dt, scheme, nullptr, 0)) != BTE_OK) return rc;
   }
@@ -958,6 +995,199 @@ int bte_get_directions(bte_handle h, double* S, double* w, int* refl) {
   if (w) std::memcpy(w, h->w.data(), h->w.size() * 8);
   if (refl) std::memcpy(refl, h->refl.data(), h->refl.size() * sizeof(int));
   return h->nd;
+}
+
+// ---- learned guess ---------------------------------------------------------
+namespace {
+
+// Xavier-uniform weights and zero biases for one net (host SplitMix64 stream).
+void mlp_init_host(std::vector<float>& p, int k, unsigned long long seed) {
+  p.assign(mlp_param_count(k), 0.f);
+  unsigned long long st = seed;
+  auto next = [&]() {
+    st += 0x9E3779B97F4A7C15ULL;
+    unsigned long long z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  auto fill = [&](size_t off, int fan_in, int fan_out, int n) {
+    const double a = std::sqrt(6.0 / (fan_in + fan_out));
+    for (int i = 0; i < n; ++i) p[off + i] = (float)((2.0 * next() - 1.0) * a);
+  };
+  fill(0, 1, kHidden, kHidden);                                      // W1
+  fill(2 * kHidden, kHidden, kHidden, kHidden * kHidden);           // W2
+  fill(3 * kHidden + kHidden * kHidden, kHidden, k, k * kHidden);   // W3
+}
+
+int mlp_net_offset(const bte_ctx* h, int net, int* k) {
+  *k = net == 0 ? 1 : h->nb;
+  return net == 0 ? 0 : mlp_param_count(1);
+}
+
+}  // namespace
+
+int bte_train_mlp(bte_handle h, long long n_pairs, double T_lo, double T_hi, int epochs, unsigned long long seed,
+                  double* loss) {
+  if (!h) return BTE_E_ARG;
+  int rc = ensure_memory(h);
+  if (rc) return rc;
+  if (n_pairs < 1024 || n_pairs > (1LL << 26)) return fail(h, BTE_E_ARG, "n_pairs must lie in [1024, 2^26]");
+  if (!(T_lo >= kTmin && T_hi <= kTmax && T_hi > T_lo + 1.0)) return fail(h, BTE_E_ARG, "need 1 <= T_lo < T_hi <= 5000 K");
+  if (epochs < 1) return fail(h, BTE_E_ARG, "epochs must be >= 1");
+  cudaStream_t s = h->stream;
+  const int n = (int)n_pairs, nb = h->nb, B = 1024;
+  // normalisation
+  h->mlp_Tlo = T_lo;
+  h->mlp_Thi = T_hi;
+  CUDA_TRY(h, launch_mlp_norm(thermo(h), T_lo, T_hi, h->I0ref, h->mlp_rlo, h->mlp_rhi, h->mlp_elohi, s));
+  double el[2];
+  CUDA_TRY(h, cudaMemcpyAsync(el, h->mlp_elohi, 16, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  h->mlp_Elo = el[0];
+  h->mlp_Ehi = el[1];
+  // temporary training buffers (stream-ordered allocation, freed before returning)
+  const size_t pair_f = (size_t)n * (2 + nb), act_f = (size_t)(4 * kHidden + 2 * nb) * B, part_f = 8192;
+  float* tmp = nullptr;
+  CUDA_TRY(h, cudaMallocAsync((void**)&tmp, (pair_f + act_f + part_f) * 4, s));
+  float* xA = tmp;
+  float* yA = xA + n;
+  float* yB = yA + n;
+  float* act = yB + (size_t)nb * n;
+  float* part = act + act_f;
+  cudaError_t e = launch_mlp_pairs(thermo(h), T_lo, T_hi, h->I0ref, h->mlp_rlo, h->mlp_rhi, h->mlp_elohi, seed, n, xA,
+                                   yA, yB, s);
+  double losses[2] = {0.0, 0.0};
+  for (int net = 0; net < 2 && e == cudaSuccess; ++net) {
+    int k;
+    const int off = mlp_net_offset(h, net, &k);
+    const int np = mlp_param_count(k);
+    std::vector<float> init;
+    mlp_init_host(init, k, seed * 2654435761ULL + 17 + net);
+    e = cudaMemcpyAsync(h->mlp_p + off, init.data(), np * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->mlp_m + off, 0, np * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->mlp_v + off, 0, np * 4, s);
+    const float* X = net == 0 ? xA : yA;
+    const float* Tg = net == 0 ? yA : yB;
+    const int steps_per_epoch = std::max(1, n / B);
+    int t = 0;
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+      const float lr = 2e-3f * std::pow(0.1f, (float)ep / (float)std::max(1, epochs - 1));  // decay to lr/10
+      for (int st = 0; st < steps_per_epoch && e == cudaSuccess; ++st) {
+        const int o = (int)(((long long)st * B + (long long)ep * 7919) % (n - B + 1));
+        e = mlp_forward_backward(h->mlp_p + off, k, X + o, n, Tg + o, n, B, h->mlp_g + off, act, part, s);
+        if (e == cudaSuccess) e = launch_adam(h->mlp_p + off, h->mlp_g + off, h->mlp_m + off, h->mlp_v + off, np, lr, ++t, s);
+      }
+    }
+    // loss over the first min(n, 8192) pairs with the trained weights
+    const int Bev = std::min(n, 8192);
+    float* evact = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&evact, ((size_t)(4 * kHidden + 2 * k) * Bev + 4 * (size_t)np) * 4, s);
+    if (e == cudaSuccess)
+      e = mlp_forward_backward(h->mlp_p + off, k, X, n, Tg, n, Bev, evact + (size_t)(4 * kHidden + 2 * k) * Bev,
+                               evact, part, s);
+    std::vector<float> hp((k * (size_t)Bev + 255) / 256);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, hp.size() * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (float v : hp) losses[net] += v;
+    if (evact) cudaFreeAsync(evact, s);
+  }
+  cudaFreeAsync(tmp, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(h, BTE_E_CUDA, "training: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  h->mlp_trained = true;
+  if (loss) {
+    loss[0] = losses[0];
+    loss[1] = losses[1];
+  }
+  return BTE_OK;
+}
+
+int bte_mlp_params(bte_handle h, int net, float* out, int n) {
+  if (!h || (net != 0 && net != 1)) return BTE_E_ARG;
+  int rc = ensure_memory(h);
+  if (rc) return rc;
+  int k;
+  const int off = mlp_net_offset(h, net, &k);
+  const int np = mlp_param_count(k);
+  if (!out) return np;
+  if (n < np) return fail(h, BTE_E_ARG, "need %d floats", np);
+  CUDA_TRY(h, cudaMemcpy(out, h->mlp_p + off, np * 4, cudaMemcpyDeviceToHost));
+  return np;
+}
+
+int bte_mlp_set_params(bte_handle h, int net, const float* in, int n) {
+  if (!h || (net != 0 && net != 1) || !in) return BTE_E_ARG;
+  int rc = ensure_memory(h);
+  if (rc) return rc;
+  int k;
+  const int off = mlp_net_offset(h, net, &k);
+  const int np = mlp_param_count(k);
+  if (n != np) return fail(h, BTE_E_ARG, "net %d has %d parameters", net, np);
+  CUDA_TRY(h, cudaMemcpy(h->mlp_p + off, in, np * 4, cudaMemcpyHostToDevice));
+  return BTE_OK;
+}
+
+int bte_mlp_grad(bte_handle h, int net, const float* x, const float* y, int n, float* grad, double* loss) {
+  if (!h || (net != 0 && net != 1) || !x || !y || !grad || n < 1 || n > 65536) return BTE_E_ARG;
+  int rc = ensure_memory(h);
+  if (rc) return rc;
+  int k;
+  const int off = mlp_net_offset(h, net, &k);
+  const int np = mlp_param_count(k);
+  cudaStream_t s = h->stream;
+  const size_t act_f = (size_t)(4 * kHidden + 2 * k) * n, parts = ((size_t)k * n + 255) / 256;
+  float* tmp = nullptr;
+  CUDA_TRY(h, cudaMallocAsync((void**)&tmp, ((size_t)n + (size_t)k * n + act_f + parts + np) * 4, s));
+  float* dx = tmp;
+  float* dy = dx + n;
+  float* act = dy + (size_t)k * n;
+  float* part = act + act_f;
+  float* g = part + parts;
+  cudaError_t e = cudaMemcpyAsync(dx, x, (size_t)n * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, (size_t)k * n * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = mlp_forward_backward(h->mlp_p + off, k, dx, n, dy, n, n, g, act, part, s);
+  std::vector<float> hp(parts);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(grad, g, (size_t)np * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, parts * 4, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(tmp, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || e2 != cudaSuccess) return fail(h, BTE_E_CUDA, "mlp grad: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  if (loss) {
+    double l = 0.0;
+    for (float v : hp) l += v;
+    *loss = l;
+  }
+  return BTE_OK;
+}
+
+int bte_solve_T(bte_handle h, const double* Ep, const double* T0, int n, int learned, double* T_out, int* evals) {
+  if (!h || !Ep || !T_out || n < 1) return BTE_E_ARG;
+  int rc = ensure_memory(h);
+  if (rc) return rc;
+  if (learned && !h->mlp_trained) return fail(h, BTE_E_STATE, "bte_train_mlp must come first");
+  if (!h->solve_tp) return fail(h, BTE_E_STATE, "every beta_b is zero: the T_p equation is empty");
+  cudaStream_t s = h->stream;
+  double* tmp = nullptr;
+  CUDA_TRY(h, cudaMallocAsync((void**)&tmp, (size_t)n * (3 * 8 + 4), s));
+  double* dE = tmp;
+  double* dT0 = dE + n;
+  double* dT = dT0 + n;
+  int* dev = (int*)(dT + n);
+  cudaError_t e = cudaMemcpyAsync(dE, Ep, (size_t)n * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && T0) e = cudaMemcpyAsync(dT0, T0, (size_t)n * 8, cudaMemcpyHostToDevice, s);
+  const MLPView m = mlp_view(h);
+  if (e == cudaSuccess)
+    e = launch_solve_batch(thermo(h), dE, T0 ? dT0 : nullptr, n, std::cbrt(h->opts.newton_rtol / 4.0),
+                           h->opts.newton_maxit, learned ? &m : nullptr, dT, dev, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(T_out, dT, (size_t)n * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && evals) e = cudaMemcpyAsync(evals, dev, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(tmp, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || e2 != cudaSuccess) return fail(h, BTE_E_CUDA, "solve: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  return BTE_OK;
 }
 
 int bte_destroy(bte_handle h) {

@@ -130,7 +130,20 @@ cudaError_t launch_sweep(int precision, int pd, const SweepArgs& a, int dim, int
 cudaError_t launch_sweep_fp64(int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
 cudaError_t launch_sweep_fp32(int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
 cudaError_t launch_sweep_bf16(int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
-cudaError_t launch_fixup(const SweepArgs& a, cudaStream_t s);
+struct MLPView;
+cudaError_t launch_fixup(const SweepArgs& a, const MLPView* mlp, cudaStream_t s);
+// learned guess (bte_mlp.cu)
+int mlp_param_total(int nb);
+cudaError_t launch_mlp_norm(ThermoTables th, double T_lo, double T_hi, const double* I0ref, double* r_lo, double* r_hi,
+                            double* E_lohi, cudaStream_t s);
+cudaError_t launch_mlp_pairs(ThermoTables th, double T_lo, double T_hi, const double* I0ref, const double* r_lo,
+                             const double* r_hi, const double* E_lohi, unsigned long long seed, int n, float* xA,
+                             float* yA, float* yB, cudaStream_t s);
+cudaError_t mlp_forward_backward(const float* p, int k, const float* X, int ldx, const float* Tg, int ldt, int B,
+                                 float* grad, float* act, float* part, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, int step, cudaStream_t s);
+cudaError_t launch_solve_batch(ThermoTables th, const double* Ep, const double* T0, int n, double trust_rel, int maxit,
+                               const MLPView* mlp, double* Tout, int* evals, cudaStream_t s);
 cudaError_t launch_init_cells(int precision, void* I, double* I0cell, double* J, double* Tp, double* Te, double* TL,
                               double* EL, const double* Tcells, const double* I0ref, long long cell0, int ncells, int nd,
                               ThermoTables th, cudaStream_t s);

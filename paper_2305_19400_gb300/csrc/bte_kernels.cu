@@ -27,120 +27,46 @@
 //   I0 is refreshed from the accepted model.
 // The HBM stream per update is I^n read, I^{k+1} written and I^k read once
 // (neighbour rows come from L2 while adjacent cells are processed together).
+#include "bte_mlp.cuh"
+#include "bte_quad.cuh"
+#include "bte_solve.cuh"
 #include "bte_store.cuh"
 
 namespace bte {
 
 namespace {
 
-// Band quadrature.  I0_b(T) = sum_i C_i / expm1(c_i / T) (Gauss-Legendre on the
-// band).  With n = 1/(e^x - 1), x = c/T:  dn/dT = n(1+n) x/T and
-// d2n/dT2 = n(1+n) (x/T^2) ((1+2n) x - 2).
-__device__ __forceinline__ double band_I0(const double* __restrict__ c, const double* __restrict__ C, int ng,
-                                          double rT) {
-  double s = 0.0;
-  for (int i = 0; i < ng; ++i) s = fma(C[i], 1.0 / expm1(c[i] * rT), s);
-  return s;
-}
-
-__device__ __forceinline__ void band_I0_d2(const double* __restrict__ c, const double* __restrict__ C, int ng,
-                                           double rT, double& f, double& d1, double& d2) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int i = 0; i < ng; ++i) {
-    const double x = c[i] * rT;
-    const double n = 1.0 / expm1(x);
-    const double qx = fma(n, n, n) * x;
-    const double u = fma(2.0 * n, x, x) - 2.0;
-    s0 = fma(C[i], n, s0);
-    s1 = fma(C[i], qx, s1);
-    s2 = fma(C[i] * qx, u, s2);
-  }
-  f = s0;
-  d1 = s1 * rT;
-  d2 = s2 * rT * rT;
-}
-
 // Exact temperature solve of the cells the sweep could not settle on their
-// cached model: one warp per cell, lanes over bands.  Halley steps on the FP64
-// band quadrature from T0 (each evaluation becomes the cell's cached model),
-// bisection on [1, 5000] K as the fallback, then the I0 refresh.
-__global__ void fixup_kernel(SweepArgs a) {
+// cached model: one warp per cell.  The start is the model root (plain mode)
+// or the learned guess (net A, then surrogate Newton steps on net B); the
+// exact FP64 quadrature then refines it (each evaluation becomes the cell's
+// cached model) and I0 is refreshed.
+__global__ void fixup_kernel(SweepArgs a, int learned, MLPView m) {
+  extern __shared__ float fsm[];  // per warp: 2*nb + 4*kHidden floats (learned mode)
   const int warps = blockDim.x / 32;
-  const int lane = threadIdx.x & 31;
-  const int nbp = a.th.nbp, ng = a.th.ng;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x / 32;
+  const int nbp = a.th.nbp;
+  float* ybuf = fsm + (size_t)wid * (2 * nbp + 4 * kHidden);
+  float* hbuf = ybuf + 2 * nbp;
   const unsigned count = *a.fix_count;
   unsigned long long evals = 0, fb = 0, bad = 0;
-  for (unsigned w = blockIdx.x * warps + threadIdx.x / 32; w < count; w += gridDim.x * warps) {
+  for (unsigned w = blockIdx.x * warps + wid; w < count; w += gridDim.x * warps) {
     const FixItem it = a.fix[w];
     const long long P = it.P;
-    const double Ep = it.Ep;
-    double T = it.T0, lo = kTmin, hi = kTmax, delta = 0.0;
-    int mode = 0, iters = 0;  // 0 Halley, 1 bisection, 2 final
-    bool done = false;
-    for (int loop = 0; loop < a.maxit + 224 && !done; ++loop) {
-      const double rT = 1.0 / T;
-      double F = 0.0, F1 = 0.0, F2 = 0.0;
-      for (int b = lane; b < nbp; b += 32) {
-        double f, d1, d2;
-        band_I0_d2(a.th.node_c + b * ng, a.th.node_C + b * ng, ng, rT, f, d1, d2);
-        a.J[(P * 3 + 0) * nbp + b] = f;
-        a.J[(P * 3 + 1) * nbp + b] = d1;
-        a.J[(P * 3 + 2) * nbp + b] = d2;
-        const double ap = a.th.a_p[b];
-        F = fma(ap, f, F);
-        F1 = fma(ap, d1, F1);
-        F2 = fma(ap, d2, F2);
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        F += __shfl_xor_sync(0xffffffffu, F, o);
-        F1 += __shfl_xor_sync(0xffffffffu, F1, o);
-        F2 += __shfl_xor_sync(0xffffffffu, F2, o);
-      }
-      F -= Ep;
-      ++evals;
-      if (mode == 0) {
-        ++iters;
-        bool badstep = !(isfinite(F) && isfinite(F1) && F1 > 0.0);
-        double Tn = T;
-        if (!badstep) {
-          const double newton = -F / F1;
-          const double h = F * F2 / (2.0 * F1 * F1);
-          delta = fabs(h) < 0.5 ? newton / (1.0 - h) : newton;
-          Tn = T + delta;
-          badstep = !(Tn >= kTmin && Tn <= kTmax) || iters > a.maxit;
-        }
-        if (badstep) {
-          mode = 1;
-          lo = kTmin;
-          hi = kTmax;
-          T = 0.5 * (lo + hi);
-          ++fb;
-        } else if (fabs(delta) <= a.trust_rel * Tn) {
-          done = true;
-        } else {
-          T = Tn;
-        }
-      } else if (mode == 1) {
-        if (F < 0.0) lo = T; else hi = T;
-        T = 0.5 * (lo + hi);
-        ++iters;
-        if (hi - lo <= 4e-16 * hi || iters >= a.maxit + 200) mode = 2;
-      } else {
-        delta = 0.0;
-        done = true;
-        if (T <= kTmin * (1.0 + 1e-9) || T >= kTmax * (1.0 - 1e-9)) ++bad;
-      }
-    }
-    if (!done) { ++bad; delta = 0.0; }
-    // I0 refresh from the (just written) model at T
-    const double hd2 = 0.5 * delta * delta;
+    const double T0 = learned ? mlp_guess_T(m, a.th.a_p, it.Ep, 2, ybuf, hbuf) : it.T0;
+    const SolveResult r = exact_solve_warp(a.th, it.Ep, T0, a.trust_rel, a.maxit, a.J + (P * 3) * nbp);
+    evals += r.evals;
+    fb += r.fallback;
+    bad += r.bad;
+    // I0 refresh from the (just written) model at r.Te
+    const double hd2 = 0.5 * r.delta * r.delta;
     for (int b = lane; b < nbp; b += 32) {
       const long long j = (P * 3) * nbp + b;
-      a.I0cell[P * nbp + b] = fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], delta, a.J[j]));
+      a.I0cell[P * nbp + b] = fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], r.delta, a.J[j]));
     }
     if (lane == 0) {
-      a.Teval[P] = T;
-      a.Tp[P] = T + delta;
+      a.Teval[P] = r.Te;
+      a.Tp[P] = r.Te + r.delta;
     }
   }
   if (lane == 0 && a.counters) {
@@ -399,8 +325,11 @@ cudaError_t launch_sweep(int precision, int pd, const SweepArgs& a, int dim, int
   return launch_sweep_bf16(pd, a, dim, threads, grid, s);
 }
 
-cudaError_t launch_fixup(const SweepArgs& a, cudaStream_t s) {
-  fixup_kernel<<<152, 128, 0, s>>>(a);
+cudaError_t launch_fixup(const SweepArgs& a, const MLPView* mlp, cudaStream_t s) {
+  const size_t sm = mlp ? 4 * (2 * (size_t)a.th.nbp + 4 * kHidden) * sizeof(float) : 0;
+  MLPView m{};
+  if (mlp) m = *mlp;
+  fixup_kernel<<<152, 128, sm, s>>>(a, mlp ? 1 : 0, m);
   return cudaGetLastError();
 }
 
