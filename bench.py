@@ -297,7 +297,7 @@ def main():
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    launches = args.steps * args.ninner
+    launches = 2 * args.steps * args.ninner   # sweep + fix-up kernel per inner iteration
     value = world * updates_per_step * args.steps / (ms_max * 1e-3)
 
     # sanity: the state is finite and physical after the timed run
@@ -342,7 +342,8 @@ def main():
             dist.destroy_process_group()
         return 0
     peaks, peak_src = read_peaks()
-    launch_s = ms_max * 1e-3 / launches
+    # the whole step time (sweeps and fix-ups) charged to the sweeps: a lower bound of the sweep's own rate
+    launch_s = ms_max * 1e-3 / (args.steps * args.ninner)
     upd_launch = updates_per_step / args.ninner
     flops = FLOPS_PER_UPDATE_2D * upd_launch / launch_s
     hbm = BYTES_PER_UPDATE_FP64 * upd_launch / launch_s / 1e9

@@ -41,6 +41,7 @@ extern "C" {
 #define BTE_E_NOMEM (-4)     /* workspace too small or device allocation failed */
 #define BTE_E_NONFINITE (-5) /* a cell energy or temperature became NaN/Inf */
 #define BTE_E_TIMEOUT (-6)   /* a bounded device-side wait gave up */
+#define BTE_E_EXCHANGE (-7)  /* the band-range exchange callback returned non-zero */
 #define BTE_W_FALLBACK 1     /* success; some temperature solves fell back to bisection */
 
 /* ---- enumerations ---- */
@@ -124,6 +125,37 @@ int bte_init_mesh(bte_handle* out, int n_geom, const bte_geom* geoms, const bte_
  * the band (Debye-type band, Bose-Einstein occupation).  1 <= nb <= 256. */
 int bte_set_bands(bte_handle h, int nb, const double* omega_lo, const double* omega_hi, const double* vg,
                   const double* beta, const double* degeneracy);
+
+/* Band partition (Sec. 3.3: the bands couple only through the temperature
+ * update, which needs a per-cell sum over bands).  After bte_set_bands and
+ * before any call that needs device memory (bte_bind_workspace,
+ * bte_workspace_bytes, bte_set_bc, bte_set_initial), bte_set_band_range makes
+ * this handle store and sweep only bands [band_lo, band_hi) of the table; the
+ * temperature solve still uses every band.  Each inner iteration then runs
+ * sweep -> exchange -> cell solve -> fix-up: the sweep writes this handle's
+ * per-cell partial sums (E_L, E_p) over its bands, and the callback given to
+ * bte_set_exchange must replace them by their sum over all ranks' band ranges
+ * (an all-reduce), after which every rank solves the same T_p for every cell.
+ * The ranges of the ranks must tile [0, nb) and every rank must use the same
+ * mesh, directions, table, walls, initial state, dt and options.
+ *   fn(buf, count, cuda_stream, user): buf is a device array of count
+ *   (= 2 * total cells) doubles, [cell][E_L, E_p]: the caller's dev_buf when
+ *   that is not NULL (device memory of at least 2 * total cells doubles that
+ *   stays alive while the handle steps), else an array inside the library's
+ *   workspace.  The partials are complete in stream order on cuda_stream (a
+ *   cudaStream_t) when fn is called, and fn must leave the sums in buf in that
+ *   stream's order (it may synchronize the stream).  fn returns 0 on success;
+ *   any other value makes bte_step return BTE_E_EXCHANGE.  `user` is passed
+ *   through.  The library calls fn from the thread that called bte_step.
+ * A band-range handle steps without CUDA graphs (opts.use_graph is ignored),
+ * bte_step returns BTE_E_STATE until an exchange is set, bte_get_flux and
+ * bte_get_wall_flux_noalloc return the partial sums over this handle's bands,
+ * bte_get_intensity / bte_set_intensity cover [cell][dir][band_lo..band_hi),
+ * and bte_set_intensity needs Tp_cells (E_L comes from the next step's sums).
+ * bte_set_band_range returns BTE_E_ARG unless 0 <= band_lo < band_hi <= nb. */
+typedef int (*bte_allreduce_fn)(double* dev_buf, long long count, void* cuda_stream, void* user);
+int bte_set_band_range(bte_handle h, int band_lo, int band_hi);
+int bte_set_exchange(bte_handle h, bte_allreduce_fn fn, void* user, double* dev_buf);
 
 /* Device bytes the solver needs (valid after bte_set_bands), and binding of a
  * caller-owned device buffer of at least that size (e.g. a torch.empty

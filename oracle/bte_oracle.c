@@ -344,18 +344,17 @@ static double total_weight(const orc_problem* p) {
   return W;
 }
 
-/* Temperatures of one cell from its intensity row.  With every beta_b = 0 the
- * T_p equation is empty (I0 never enters the update); T_p is then set to T_L. */
-int orc_cell_temperatures(const orc_problem* p, const double* row, double TpGuess, double TLGuess, double* Tp,
-                          double* TL) {
+/* Temperatures of one cell from its energies E_L, E_p (sums over every band).
+ * With every beta_b = 0 the T_p equation is empty (I0 never enters the
+ * update); T_p is then set to T_L. */
+int orc_temperatures_from_energy(const orc_problem* p, double EL, double Ep, double TpGuess, double TLGuess,
+                                 double* Tp, double* TL) {
   int nb = p->nb;
   double W = total_weight(p);
   double* aL = (double*)malloc(sizeof(double) * 2 * nb);
   double* ap = aL + nb;
   double bsum = 0.0;
   for (int b = 0; b < nb; ++b) { aL[b] = W / p->vg[b]; ap[b] = W * p->beta[b] / p->vg[b]; bsum += p->beta[b]; }
-  double EL, Ep;
-  orc_cell_energy(p, row, &EL, &Ep);
   int fb = 0;
   int sL = orc_solve_T(p, aL, EL, TLGuess, TL);
   if (sL < 0) { free(aL); return -1; }
@@ -369,6 +368,14 @@ int orc_cell_temperatures(const orc_problem* p, const double* row, double TpGues
   }
   free(aL);
   return fb;
+}
+
+/* Temperatures of one cell from its intensity row. */
+int orc_cell_temperatures(const orc_problem* p, const double* row, double TpGuess, double TLGuess, double* Tp,
+                          double* TL) {
+  double EL, Ep;
+  orc_cell_energy(p, row, &EL, &Ep);
+  return orc_temperatures_from_energy(p, EL, Ep, TpGuess, TLGuess, Tp, TL);
 }
 
 /* Equilibrium initial state (Sec. 3.2: I = I_init[b] for all d at the uniform T). */
@@ -422,6 +429,69 @@ long orc_run(const orc_problem* p, double dt, int nsteps, int ninner, int scheme
   free(In);
   free(Inew);
   free(I0wall);
+  return bad ? -1 : fallbacks;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same time loop with the bands partitioned (Sec. 3.3): this caller owns   */
+/* bands [b0, b1) and updates only those entries of I.  The bands couple only   */
+/* through the temperature step, so after each sweep the caller's partial       */
+/* energies E_L, E_p over its bands go to `sum` (buf = [cell][E_L, E_p], 2 nc    */
+/* values), which must replace them by their totals over all owners; then the  */
+/* temperatures are solved from the totals and I0 is refreshed for every band. */
+/* sum returns 0 on success.  Returns as orc_run, or -2 when sum failed.       */
+/* ------------------------------------------------------------------------ */
+typedef int (*orc_sum_fn)(double* buf, long count, void* user);
+
+long orc_run_bands(const orc_problem* p, int b0, int b1, double dt, int nsteps, int ninner, int scheme, double* I,
+                   double* Tp, double* TL, double* I0, orc_sum_fn sum, void* user) {
+  long nc = ncells(p);
+  int nd = p->nd, nb = p->nb;
+  if (b0 < 0 || b1 > nb || b0 >= b1) return -3;
+  size_t n = (size_t)nc * nd * nb;
+  double* In = (double*)malloc(n * sizeof(double));
+  double* Inew = (double*)malloc(n * sizeof(double));
+  double* E = (double*)malloc((size_t)nc * 2 * sizeof(double));
+  double* I0wall = wall_I0(p);
+  long fallbacks = 0, bad = 0, failed = 0;
+  if (scheme == ORC_EXPLICIT) ninner = 1;
+  for (int step = 0; step < nsteps && !failed; ++step) {
+    memcpy(In, I, n * sizeof(double));
+    for (int k = 0; k < ninner; ++k) {
+      const double* Ik = (scheme == ORC_EXPLICIT) ? In : I;
+      memcpy(Inew, I, n * sizeof(double));
+#pragma omp parallel for schedule(static)
+      for (long P = 0; P < nc; ++P)
+        for (int d = 0; d < nd; ++d)
+          for (int b = b0; b < b1; ++b)
+            Inew[P * nd * nb + (long)d * nb + b] = orc_update_one(p, dt, scheme, In, Ik, I0, I0wall, P, d, b);
+#pragma omp parallel for schedule(static)
+      for (long P = 0; P < nc; ++P) {  /* partial reduction over the owned bands */
+        double eL = 0.0, ep = 0.0;
+        for (int b = b0; b < b1; ++b) {
+          double G = 0.0;
+          for (int d = 0; d < nd; ++d) G += p->w[d] * Inew[P * nd * nb + (long)d * nb + b];
+          eL += G / p->vg[b];
+          ep += p->beta[b] * G / p->vg[b];
+        }
+        E[2 * P] = eL;
+        E[2 * P + 1] = ep;
+      }
+      if (sum(E, 2 * nc, user) != 0) { failed = 1; break; }
+#pragma omp parallel for schedule(static) reduction(+ : fallbacks, bad)
+      for (long P = 0; P < nc; ++P) {
+        int s = orc_temperatures_from_energy(p, E[2 * P], E[2 * P + 1], Tp[P], TL[P], &Tp[P], &TL[P]);
+        if (s < 0) bad += 1; else fallbacks += s;
+        orc_I0(nb, p->wlo, p->whi, p->vg, p->g, p->ngauss, p->glx, p->glw, Tp[P], I0 + P * nb, NULL);
+      }
+      memcpy(I, Inew, n * sizeof(double));
+    }
+  }
+  free(In);
+  free(Inew);
+  free(E);
+  free(I0wall);
+  if (failed) return -2;
   return bad ? -1 : fallbacks;
 }
 

@@ -79,11 +79,18 @@ def lib():
             L.orc_init_state.argtypes = [P, dp, dp, dp, dp, dp]
             L.orc_run.argtypes = [P, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp]
             L.orc_run.restype = C.c_long
+            L.orc_run_bands.argtypes = [P, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp,
+                                        SUM_FN, C.c_void_p]
+            L.orc_run_bands.restype = C.c_long
             L.orc_flux.argtypes = [P, dp, dp, dp]
             L.orc_wall_I0.argtypes = [P, dp]
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
+
+
+# int (*)(double* buf, long count, void* user)
+SUM_FN = C.CFUNCTYPE(C.c_int, C.POINTER(C.c_double), C.c_long, C.c_void_p)
 
 
 def _dp(a):
@@ -204,6 +211,29 @@ class Problem:
                           _dp(st["I"]), _dp(st["Tp"]), _dp(st["TL"]), _dp(st["I0"]))
         if r < 0:
             raise RuntimeError("oracle: a cell has no temperature in [1, 5000] K")
+        return int(r)
+
+    def run_bands(self, st, b0: int, b1: int, total, dt: float, nsteps: int, ninner: int,
+                  scheme: int = IMPLICIT) -> int:
+        """The time loop over bands [b0, b1) only (Sec. 3.3 band partition).
+        total(E) receives the (ncells, 2) partial energies [E_L, E_p] of these
+        bands and returns their totals over all band owners (same shape)."""
+        def cb(buf, count, user):
+            try:
+                E = np.ctypeslib.as_array(buf, shape=(count,)).reshape(-1, 2)
+                E[:] = total(E.copy())
+                return 0
+            except Exception:
+                import traceback
+                traceback.print_exc()
+                return 1
+        fn = SUM_FN(cb)
+        r = lib().orc_run_bands(self.ptr, int(b0), int(b1), float(dt), int(nsteps), int(ninner), int(scheme),
+                                _dp(st["I"]), _dp(st["Tp"]), _dp(st["TL"]), _dp(st["I0"]), fn, None)
+        if r == -2:
+            raise RuntimeError("oracle: the band-sum callback failed")
+        if r < 0:
+            raise RuntimeError("oracle: a cell has no temperature in [1, 5000] K (or a bad band range)")
         return int(r)
 
     # -- pieces used by sampled checks ---------------------------------------

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(PKG, "libbte.so")
 
 BTE_OK, BTE_W_FALLBACK = 0, 1
 BTE_E = {-1: "BTE_E_ARG", -2: "BTE_E_STATE", -3: "BTE_E_CUDA", -4: "BTE_E_NOMEM", -5: "BTE_E_NONFINITE",
-         -6: "BTE_E_TIMEOUT"}
+         -6: "BTE_E_TIMEOUT", -7: "BTE_E_EXCHANGE"}
 BTE_DIRS_INPLANE, BTE_DIRS_POLAR_AZIM = 0, 1
 BTE_FP64, BTE_FP32, BTE_BF16 = 0, 1, 2
 BTE_BC_ISOTHERMAL, BTE_BC_SPECULAR = 0, 1
@@ -48,10 +48,14 @@ class bte_stats(C.Structure):
 
 # Every symbol include/bte.h declares, with its ctypes signature.
 _dp, _ip, _vp, _h = C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p, C.c_void_p
+# int (*)(double* buf, long long count, void* cuda_stream, void* user)
+bte_allreduce_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p)
 SIGNATURES = {
     "bte_default_opts": (C.c_int, [C.POINTER(bte_opts)]),
     "bte_init_mesh": (C.c_int, [C.POINTER(_h), C.c_int, C.POINTER(bte_geom), C.POINTER(bte_opts)]),
     "bte_set_bands": (C.c_int, [_h, C.c_int, _dp, _dp, _dp, _dp, _dp]),
+    "bte_set_band_range": (C.c_int, [_h, C.c_int, C.c_int]),
+    "bte_set_exchange": (C.c_int, [_h, bte_allreduce_fn, _vp, _vp]),
     "bte_workspace_bytes": (C.c_size_t, [_h]),
     "bte_bind_workspace": (C.c_int, [_h, _vp, C.c_size_t]),
     "bte_set_bc": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, _dp, C.c_double]),
@@ -132,6 +136,25 @@ def bte_init_mesh(geoms, opts=None):
 def bte_set_bands(h, omega_lo, omega_hi, vg, beta, degeneracy):
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (omega_lo, omega_hi, vg, beta, degeneracy)]
     return _check(h, lib().bte_set_bands(h, len(arrs[0]), *[a.ctypes.data_as(_dp) for a in arrs]))
+
+
+def bte_set_band_range(h, band_lo, band_hi):
+    return _check(h, lib().bte_set_band_range(h, int(band_lo), int(band_hi)))
+
+
+def bte_set_exchange(h, fn, dev_buf=None):
+    """fn(buf_ptr, count, stream_ptr) -> int, called from bte_step.  Returns the
+    ctypes callback object, which the caller must keep alive while stepping."""
+    def tramp(buf, count, stream, user):
+        try:
+            return int(fn(buf, count, stream) or 0)
+        except Exception:  # an exception cannot cross the C frame: report it as a failed exchange
+            import traceback
+            traceback.print_exc()
+            return 1
+    cb = bte_allreduce_fn(tramp)
+    _check(h, lib().bte_set_exchange(h, cb, None, _ptr(dev_buf)))
+    return cb
 
 
 def bte_workspace_bytes(h):
@@ -255,6 +278,24 @@ def bte_last_error(h):
     return m.decode() if m else ""
 
 
+def allreduce_exchange(group=None):
+    """Exchange for band-range handles (Sec. 3.3): sums a float64 tensor of
+    per-cell (E_L, E_p) partials in place over the ranks of a torch.distributed
+    group.  NCCL reduces the device tensor on the current stream; other
+    backends (gloo) reduce a host copy."""
+    import torch
+    import torch.distributed as dist
+
+    def fn(buf):
+        if buf.is_cuda and dist.get_backend(group) != "nccl":
+            host = buf.cpu()
+            dist.all_reduce(host, group=group)
+            buf.copy_(host)
+        else:
+            dist.all_reduce(buf, group=group)
+    return fn
+
+
 # ---- convenience: a solver built from a workload description ---------------
 class Solver:
     """Marshals a workload (paper_2305_19400_gb300.workloads) into the C calls.
@@ -264,7 +305,11 @@ class Solver:
     """
 
     def __init__(self, workload, precision=BTE_FP64, stream=None, bind_workspace=True, n_gauss=16, T_init=None,
-                 use_graph=False, autotune=False, learned=False):
+                 use_graph=False, autotune=False, learned=False, band_range=None, exchange=None):
+        """band_range=(lo, hi) stores and sweeps only bands [lo, hi); exchange(buf)
+        then sums the float64 CUDA tensor buf of per-cell (E_L, E_p) partials
+        over the ranks in place (e.g. allreduce_exchange()); it runs with this
+        solver's stream current."""
         import torch
 
         self.wl = workload
@@ -286,6 +331,18 @@ class Solver:
         self.h = bte_init_mesh(geoms, o)
         b = workload.bands
         bte_set_bands(self.h, b.omega_lo, b.omega_hi, b.vg, b.beta, b.degeneracy)
+        self.band_range = (0, b.nb) if band_range is None else tuple(int(x) for x in band_range)
+        if band_range is not None:
+            bte_set_band_range(self.h, *self.band_range)
+        if exchange is not None:
+            ncells = sum(g.ncells for g in workload.geoms)
+            self.xbuf = torch.empty(2 * ncells, dtype=torch.float64, device="cuda")
+
+            def run_exchange(buf_ptr, count, stream_ptr):
+                with torch.cuda.stream(self.stream):
+                    exchange(self.xbuf)
+                return 0
+            self._xcb = bte_set_exchange(self.h, run_exchange, self.xbuf)
         self.ws = None
         if bind_workspace:
             nbytes = bte_workspace_bytes(self.h)
@@ -311,7 +368,7 @@ class Solver:
 
     def intensity(self, geom=0):
         g = self.wl.geoms[geom]
-        out = np.zeros((g.ncells, self.wl.dirs.nd, self.wl.bands.nb))
+        out = np.zeros((g.ncells, self.wl.dirs.nd, self.band_range[1] - self.band_range[0]))
         bte_get_intensity(self.h, geom, out)
         return out
 

@@ -41,7 +41,13 @@ struct bte_ctx {
   std::vector<int> refl;
   double Wtot = 0.0;
   // bands
-  int nb = 0, nbp = 0, ng = 16;
+  int nb = 0, nbp = 0, ng = 16;           // bands stored by this handle (padded: nbp)
+  int nb_all = 0, nbp_all = 0, band0 = 0; // every band of the table; first stored band
+  bte_allreduce_fn exchange = nullptr;    // band-range handles: sums per-cell partials over ranks
+  void* exchange_user = nullptr;
+  double* exchange_buf = nullptr;         // caller's device array for the partials (else Epart)
+  int exchange_rc = 0;                    // last non-zero return of the exchange callback
+  bool EL_partial = false;                // E_L not yet summed over the ranks (after bte_set_intensity)
   std::vector<double> wlo, whi, vg, beta, deg;
   bool solve_tp = false;
   // state
@@ -70,6 +76,8 @@ struct bte_ctx {
   double *I0cell = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr, *I0wall = nullptr;
   void* coef = nullptr;
   double *J = nullptr, *Teval = nullptr, *I0ref = nullptr, *scratch_pack = nullptr;
+  double* I0ref_o = nullptr;  // I0_b(T_ref) of the stored bands (aliases I0ref unless a band range is set)
+  double* Epart = nullptr;    // band-range handles: [ncells][2] partial (E_L, E_p) for the exchange
   float *I0wall_dev = nullptr, *wdir32 = nullptr, *vb32 = nullptr, *bb32 = nullptr;
   float4* dirc = nullptr;
   FixItem* fix = nullptr;
@@ -125,21 +133,6 @@ long long side_faces(const bte_geom& g, int side) {
   return (long long)g.nx * g.ny;
 }
 
-ThermoTables thermo_of(const double* nc, const double* nC, const double* ap, const double* aL, const double* iv,
-                       const double* be, int ng, int nbp, int nb) {
-  ThermoTables t;
-  t.node_c = nc;
-  t.node_C = nC;
-  t.a_p = ap;
-  t.a_L = aL;
-  t.inv_v = iv;
-  t.beta = be;
-  t.ng = ng;
-  t.nbp = nbp;
-  t.nb = nb;
-  return t;
-}
-
 ThermoTables thermo(const bte_ctx* h) {
   ThermoTables t;
   t.node_c = h->node_c;
@@ -149,8 +142,20 @@ ThermoTables thermo(const bte_ctx* h) {
   t.inv_v = h->inv_v;
   t.beta = h->beta_d;
   t.ng = h->ng;
-  t.nbp = h->nbp;
-  t.nb = h->nb;
+  t.nbp = h->nbp_all;
+  t.nb = h->nb_all;
+  t.nbo = h->nbp;
+  t.nbr = h->nb;
+  t.band0 = h->band0;
+  return t;
+}
+
+// The same tables seen as a handle storing every band (for all-band outputs).
+ThermoTables thermo_all(const bte_ctx* h) {
+  ThermoTables t = thermo(h);
+  t.nbo = h->nbp_all;
+  t.nbr = h->nb_all;
+  t.band0 = 0;
   return t;
 }
 
@@ -166,9 +171,12 @@ size_t carve(bte_ctx* h, char* base) {
   const size_t ibytes = (size_t)h->ncells * row * elem_bytes(h->opts.precision);
   for (int i = 0; i < 3; ++i) h->Ibuf[i] = take(ibytes);
   h->I0cell = (double*)take((size_t)h->ncells * h->nbp * 8);
-  h->J = (double*)take((size_t)h->ncells * 3 * h->nbp * 8);
+  h->J = (double*)take((size_t)h->ncells * 3 * h->nbp_all * 8);
   h->Teval = (double*)take((size_t)h->ncells * 8);
-  h->I0ref = (double*)take((size_t)h->nbp * 8);
+  h->I0ref = (double*)take((size_t)h->nbp_all * 8);
+  const bool ranged = h->nb != h->nb_all;
+  h->I0ref_o = ranged ? (double*)take((size_t)h->nbp * 8) : h->I0ref;
+  h->Epart = ranged ? (double*)take((size_t)std::max(h->ncells, 1LL) * 2 * 8) : nullptr;
   h->I0wall_dev = (float*)take((size_t)std::max(h->nfaces, 1LL) * h->nbp * 4);
   h->wdir32 = (float*)take((size_t)h->nd * 4);
   h->Tp = (double*)take((size_t)h->ncells * 8);
@@ -181,22 +189,22 @@ size_t carve(bte_ctx* h, char* base) {
   h->bb32 = (float*)take((size_t)h->nbp * 4);
   h->fix = (FixItem*)take((size_t)std::max<long long>(h->ncells, 1) * sizeof(FixItem));
   h->fix_count = (unsigned*)take(16);
-  const size_t np = (size_t)mlp_param_total(h->nb);
+  const size_t np = (size_t)mlp_param_total(h->nb_all);
   h->mlp_p = (float*)take(np * 4);
   h->mlp_g = (float*)take(np * 4);
   h->mlp_m = (float*)take(np * 4);
   h->mlp_v = (float*)take(np * 4);
-  h->mlp_rlo = (double*)take((size_t)h->nbp * 8);
-  h->mlp_rhi = (double*)take((size_t)h->nbp * 8);
+  h->mlp_rlo = (double*)take((size_t)h->nbp_all * 8);
+  h->mlp_rhi = (double*)take((size_t)h->nbp_all * 8);
   h->mlp_elohi = (double*)take(16);
   h->wdir = (double*)take((size_t)h->nd * 8);
   h->Sdev = (double*)take((size_t)h->nd * 3 * 8);
   h->dirs_d = (DirInfo*)take((size_t)h->nd * sizeof(DirInfo));
-  h->node_c = (double*)take((size_t)h->nbp * h->ng * 8);
-  h->node_C = (double*)take((size_t)h->nbp * h->ng * 8);
-  h->a_p = (double*)take((size_t)h->nbp * 8);
-  h->a_L = (double*)take((size_t)h->nbp * 8);
-  h->inv_v = (double*)take((size_t)h->nbp * 8);
+  h->node_c = (double*)take((size_t)h->nbp_all * h->ng * 8);
+  h->node_C = (double*)take((size_t)h->nbp_all * h->ng * 8);
+  h->a_p = (double*)take((size_t)h->nbp_all * 8);
+  h->a_L = (double*)take((size_t)h->nbp_all * 8);
+  h->inv_v = (double*)take((size_t)h->nbp * 8);   // stored bands
   h->beta_d = (double*)take((size_t)h->nbp * 8);
   h->geoms_d = (DevGeom*)take(h->geoms.size() * sizeof(DevGeom));
   h->items_d = (WorkItem*)take((size_t)std::max<long long>(h->ncells, 1) * sizeof(WorkItem));  // room for 1 cell per item
@@ -279,17 +287,22 @@ int ensure_memory(bte_ctx* h) {
   CUDA_TRY(h, cudaMemcpyAsync(h->Sdev, h->S.data(), h->nd * 3 * 8, cudaMemcpyHostToDevice, s));
   // band tables
   std::vector<double> nc, nC, ap, aL, iv, be;
-  build_thermo(h->nb, h->nbp, h->ng, h->wlo.data(), h->whi.data(), h->vg.data(), h->beta.data(), h->deg.data(),
-               h->Wtot, nc, nC, ap, aL, iv, be);
+  build_thermo(h->nb_all, h->nbp_all, h->ng, h->wlo.data(), h->whi.data(), h->vg.data(), h->beta.data(),
+               h->deg.data(), h->Wtot, nc, nC, ap, aL, iv, be);
   CUDA_TRY(h, cudaMemcpyAsync(h->node_c, nc.data(), nc.size() * 8, cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaMemcpyAsync(h->node_C, nC.data(), nC.size() * 8, cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaMemcpyAsync(h->a_p, ap.data(), ap.size() * 8, cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaMemcpyAsync(h->a_L, aL.data(), aL.size() * 8, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(h, cudaMemcpyAsync(h->inv_v, iv.data(), iv.size() * 8, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(h, cudaMemcpyAsync(h->beta_d, be.data(), be.size() * 8, cudaMemcpyHostToDevice, s));
   {
-    std::vector<float> v32(h->nbp, 0.f), b32(h->nbp, 0.f);
-    for (int b = 0; b < h->nb; ++b) { v32[b] = (float)h->vg[b]; b32[b] = (float)h->beta[b]; }
+    std::vector<double> iv_o(h->nbp, 0.0), be_o(h->nbp, 0.0);  // stored bands, zero on padding
+    for (int b = 0; b < h->nb; ++b) { iv_o[b] = iv[h->band0 + b]; be_o[b] = be[h->band0 + b]; }
+    CUDA_TRY(h, cudaMemcpyAsync(h->inv_v, iv_o.data(), iv_o.size() * 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->beta_d, be_o.data(), be_o.size() * 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+  }
+  {
+    std::vector<float> v32(h->nbp, 0.f), b32(h->nbp, 0.f);  // stored bands
+    for (int b = 0; b < h->nb; ++b) { v32[b] = (float)h->vg[h->band0 + b]; b32[b] = (float)h->beta[h->band0 + b]; }
     CUDA_TRY(h, cudaMemcpyAsync(h->vb32, v32.data(), v32.size() * 4, cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync(h->bb32, b32.data(), b32.size() * 4, cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemsetAsync(h->fix_count, 0, 16, s));
@@ -301,8 +314,11 @@ int ensure_memory(bte_ctx* h) {
     // I0_b(T_ref): the reference the reduced-precision modes store deviations from
     const double tref = h->opts.T_ref;
     CUDA_TRY(h, cudaMemcpyAsync(h->scratch_T, &tref, 8, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(h, launch_wall_I0(h->I0ref, h->scratch_T, 1, thermo_of(h->node_c, h->node_C, h->a_p, h->a_L, h->inv_v,
-                                                                      h->beta_d, h->ng, h->nbp, h->nb), s));
+    CUDA_TRY(h, launch_wall_I0(h->I0ref, h->scratch_T, 1, thermo_all(h), s));
+    if (h->I0ref_o != h->I0ref) {
+      CUDA_TRY(h, cudaMemsetAsync(h->I0ref_o, 0, (size_t)h->nbp * 8, s));
+      CUDA_TRY(h, cudaMemcpyAsync(h->I0ref_o, h->I0ref + h->band0, (size_t)h->nb * 8, cudaMemcpyDeviceToDevice, s));
+    }
     CUDA_TRY(h, cudaMemsetAsync(h->I0wall_dev, 0, (size_t)std::max(h->nfaces, 1LL) * h->nbp * 4, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
   }
@@ -347,17 +363,18 @@ int ensure_coef(bte_ctx* h, double dt, int scheme) {
     h->coef_host.assign(5 * plane * ncls, 0.0);
     for (size_t c = 0; c < ncls; ++c) {
       const double delta[3] = {std::get<1>(h->cls_key[c]), std::get<2>(h->cls_key[c]), std::get<3>(h->cls_key[c])};
-      build_coef(std::get<0>(h->cls_key[c]), delta, h->nd, h->S.data(), h->w.data(), h->nb, h->nbp, h->vg.data(),
-                 h->beta.data(), dt, scheme == BTE_EXPLICIT, h->coef_host.data() + c * 5 * plane);
+      build_coef(std::get<0>(h->cls_key[c]), delta, h->nd, h->S.data(), h->w.data(), h->nb, h->nbp,
+                 h->vg.data() + h->band0, h->beta.data() + h->band0, dt, scheme == BTE_EXPLICIT,
+                 h->coef_host.data() + c * 5 * plane);
     }
     CUDA_TRY(h, cudaMemcpyAsync(h->coef, h->coef_host.data(), h->coef_host.size() * 8, cudaMemcpyHostToDevice, h->stream));
   } else {
     std::vector<float> pq(2 * plane * ncls), dc(4 * (size_t)h->nd * ncls);
     for (size_t c = 0; c < ncls; ++c) {
       const double delta[3] = {std::get<1>(h->cls_key[c]), std::get<2>(h->cls_key[c]), std::get<3>(h->cls_key[c])};
-      build_pq(std::get<0>(h->cls_key[c]), delta, h->nd, h->S.data(), h->w.data(), h->nb, h->nbp, h->vg.data(),
-               h->beta.data(), dt, scheme == BTE_EXPLICIT, pq.data() + c * 2 * plane, pq.data() + c * 2 * plane + plane,
-               dc.data() + c * 4 * h->nd);
+      build_pq(std::get<0>(h->cls_key[c]), delta, h->nd, h->S.data(), h->w.data(), h->nb, h->nbp,
+               h->vg.data() + h->band0, h->beta.data() + h->band0, dt, scheme == BTE_EXPLICIT,
+               pq.data() + c * 2 * plane, pq.data() + c * 2 * plane + plane, dc.data() + c * 4 * h->nd);
     }
     CUDA_TRY(h, cudaMemcpyAsync(h->coef, pq.data(), pq.size() * 4, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(h->dirc, dc.data(), dc.size() * 4, cudaMemcpyHostToDevice, h->stream));
@@ -407,7 +424,7 @@ MLPView mlp_view(const bte_ctx* h) {
   MLPView m;
   m.A = h->mlp_p;
   m.B = h->mlp_p + mlp_param_count(1);
-  m.nb = h->nb;
+  m.nb = h->nb_all;
   m.T_lo = h->mlp_Tlo;
   m.T_hi = h->mlp_Thi;
   m.E_lo = h->mlp_Elo;
@@ -427,7 +444,9 @@ SweepArgs sweep_args(bte_ctx* h) {
   a.EL = h->EL;
   a.I0wall = h->I0wall;
   a.I0wall_dev = h->I0wall_dev;
-  a.I0ref = h->I0ref;
+  a.I0ref = h->I0ref_o;
+  a.Epart = h->exchange_buf ? h->exchange_buf : h->Epart;
+  a.partial = h->Epart ? 1 : 0;
   a.coef = h->coef;
   a.dirs = h->dirs_d;
   a.wdir = h->wdir;
@@ -471,6 +490,16 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, cudaStream_t s, in
     a.Iout = h->Ibuf[o];
     cudaError_t e = cudaMemsetAsync(h->fix_count, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = launch_sweep(h->opts.precision, h->pd, a, dim, h->threads, h->grid, s);
+    if (e == cudaSuccess && a.partial) {
+      // band-range handle: the caller sums the per-cell (E_L, E_p) partials over
+      // the ranks that hold the other bands, then every rank solves every cell
+      const int xr = h->exchange(a.Epart, 2 * h->ncells, (void*)s, h->exchange_user);
+      if (xr != 0) {
+        h->exchange_rc = xr;
+        return cudaErrorUnknown;
+      }
+      e = launch_solve_cells(a, h->ncells, s);
+    }
     if (e == cudaSuccess && h->solve_tp) {
       if (h->opts.learned) {
         const MLPView m = mlp_view(h);
@@ -639,8 +668,9 @@ int bte_set_bands(bte_handle h, int nb, const double* wlo, const double* whi, co
     if (!(std::isfinite(beta[b]) && beta[b] >= 0)) return fail(h, BTE_E_ARG, "band %d: beta must be >= 0", b);
     if (!(std::isfinite(deg[b]) && deg[b] > 0)) return fail(h, BTE_E_ARG, "band %d: degeneracy must be > 0", b);
   }
-  h->nb = nb;
-  h->nbp = (nb + 7) / 8 * 8;
+  h->nb = h->nb_all = nb;
+  h->nbp = h->nbp_all = (nb + 7) / 8 * 8;
+  h->band0 = 0;
   h->wlo.assign(wlo, wlo + nb);
   h->whi.assign(whi, whi + nb);
   h->vg.assign(vg, vg + nb);
@@ -650,6 +680,29 @@ int bte_set_bands(bte_handle h, int nb, const double* wlo, const double* whi, co
   for (int b = 0; b < nb; ++b) h->solve_tp |= beta[b] > 0;
   build_items(h);
   h->bands_set = true;
+  return BTE_OK;
+}
+
+int bte_set_band_range(bte_handle h, int band_lo, int band_hi) {
+  if (!h) return BTE_E_ARG;
+  if (!h->bands_set) return fail(h, BTE_E_STATE, "bte_set_bands must come before bte_set_band_range");
+  if (h->mem_ready || h->ws) return fail(h, BTE_E_STATE, "bte_set_band_range must come before device memory is in use");
+  if (!(0 <= band_lo && band_lo < band_hi && band_hi <= h->nb_all))
+    return fail(h, BTE_E_ARG, "need 0 <= band_lo < band_hi <= %d", h->nb_all);
+  h->band0 = band_lo;
+  h->nb = band_hi - band_lo;
+  h->nbp = (h->nb + 7) / 8 * 8;
+  build_items(h);
+  return BTE_OK;
+}
+
+int bte_set_exchange(bte_handle h, bte_allreduce_fn fn, void* user, double* dev_buf) {
+  if (!h) return BTE_E_ARG;
+  if (!fn) return fail(h, BTE_E_ARG, "fn is NULL");
+  if (((uintptr_t)dev_buf) & 7) return fail(h, BTE_E_ARG, "dev_buf must be 8-byte aligned");
+  h->exchange = fn;
+  h->exchange_user = user;
+  h->exchange_buf = dev_buf;
   return BTE_OK;
 }
 
@@ -694,7 +747,8 @@ int bte_set_bc(bte_handle h, int geom, int side, int type, const double* T_faces
     CUDA_TRY(h, launch_wall_I0(h->I0wall + h->face0[geom * 6 + side] * h->nbp, h->scratch_T, nf, thermo(h), h->stream));
     if (h->opts.precision != BTE_FP64)
       CUDA_TRY(h, launch_wall_dev(h->I0wall_dev + h->face0[geom * 6 + side] * h->nbp,
-                                  h->I0wall + h->face0[geom * 6 + side] * h->nbp, h->I0ref, nf, h->nbp, h->stream));
+                                  h->I0wall + h->face0[geom * 6 + side] * h->nbp, h->I0ref_o, nf, h->nbp,
+                                  h->stream));
   }
   const bool changed = h->bc_type[geom][side] != type;
   h->bc_type[geom][side] = type;
@@ -717,7 +771,7 @@ int bte_set_initial(bte_handle h, int geom, const double* T_cells, double T_unif
   if ((rc = ensure_memory(h))) return rc;
   CUDA_TRY(h, cudaMemcpyAsync(h->scratch_T, T.data(), nc * 8, cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, launch_init_cells(h->opts.precision, h->Ibuf[h->cur], h->I0cell, h->J, h->Tp, h->Teval, h->TL, h->EL,
-                                h->scratch_T, h->I0ref, h->cell0[geom], (int)nc, h->nd, thermo(h), h->stream));
+                                h->scratch_T, h->I0ref_o, h->cell0[geom], (int)nc, h->nd, thermo(h), h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->init_set[geom] = true;
   h->TL_valid = false;  // T_L is recomputed from E_L on request
@@ -746,8 +800,11 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
   }
   SweepArgs a = sweep_args(h);
   int launches = 0;
+  const bool ranged = h->Epart != nullptr;
+  if (ranged && !h->exchange) return fail(h, BTE_E_STATE, "a band-range handle needs bte_set_exchange before stepping");
+  h->exchange_rc = 0;
   for (int st = 0; st < nsteps; ++st) {
-    if (h->opts.use_graph) {
+    if (h->opts.use_graph && !ranged) {  // the host-side exchange cannot sit inside a graph
       cudaGraphExec_t exec = nullptr;
       int cur_out = -1;
       for (auto& e : h->graphs)
@@ -772,11 +829,17 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
       CUDA_TRY(h, cudaGraphLaunch(exec, s));
       h->cur = cur_out;
     } else {
-      CUDA_TRY(h, enqueue_step(h, a, ninner, s, &h->cur));
+      const cudaError_t e = enqueue_step(h, a, ninner, s, &h->cur);
+      if (e != cudaSuccess && h->exchange_rc)
+        return fail(h, BTE_E_EXCHANGE, "the exchange callback returned %d", h->exchange_rc);
+      CUDA_TRY(h, e);
     }
-    launches += ninner;
+    launches += ninner * (1 + (h->solve_tp ? 1 : 0) + (ranged ? 1 : 0));  // sweep, fix-up, cell solve
   }
-  if (nsteps > 0) h->TL_valid = false;
+  if (nsteps > 0) {
+    h->TL_valid = false;
+    h->EL_partial = false;
+  }
   if (stats) {
     CUDA_TRY(h, cudaEventRecord(h->ev1, s));
     CUDA_TRY(h, cudaEventSynchronize(h->ev1));
@@ -886,6 +949,7 @@ int bte_get_T(bte_handle h, int geom, int which, double* out, int on_device) {
   if (which == BTE_T_PSEUDO && h->solve_tp) {
     src = h->Tp;
   } else {
+    if (h->EL_partial) return fail(h, BTE_E_STATE, "T_L of a band-range handle needs a step after bte_set_intensity");
     if ((rc = ensure_TL(h))) return rc;
     src = h->TL;
   }
@@ -903,9 +967,9 @@ int bte_get_flux(bte_handle h, int geom, double* q_cells, double* q_walls, int o
   cudaStream_t s = h->stream;
   if (q_cells) {
     if (on_device) {
-      CUDA_TRY(h, launch_flux_cells(prec, I, h->I0ref, q_cells, h->Sdev, h->cell0[geom], nc, h->nd, h->nbp, g.dim, s));
+      CUDA_TRY(h, launch_flux_cells(prec, I, h->I0ref_o, q_cells, h->Sdev, h->cell0[geom], nc, h->nd, h->nbp, g.dim, s));
     } else {
-      CUDA_TRY(h, launch_flux_cells(prec, I, h->I0ref, h->scratch_q, h->Sdev, h->cell0[geom], nc, h->nd, h->nbp, g.dim, s));
+      CUDA_TRY(h, launch_flux_cells(prec, I, h->I0ref_o, h->scratch_q, h->Sdev, h->cell0[geom], nc, h->nd, h->nbp, g.dim, s));
       CUDA_TRY(h, cudaMemcpyAsync(q_cells, h->scratch_q, (size_t)nc * g.dim * 8, cudaMemcpyDeviceToHost, s));
     }
   }
@@ -913,7 +977,7 @@ int bte_get_flux(bte_handle h, int geom, double* q_cells, double* q_walls, int o
     double res[6] = {0, 0, 0, 0, 0, 0};
     for (int side = 0; side < 2 * g.dim; ++side) {
       const int nf = (int)side_faces(g, side);
-      CUDA_TRY(h, launch_flux_faces(prec, I, h->I0ref, h->I0wall, h->geoms_d, geom, side, h->dirs_d, h->Sdev, h->nd,
+      CUDA_TRY(h, launch_flux_faces(prec, I, h->I0ref_o, h->I0wall, h->geoms_d, geom, side, h->dirs_d, h->Sdev, h->nd,
                                     h->nbp, h->scratch_faces, nf, s));
       CUDA_TRY(h, launch_mean(h->scratch_faces, nf, h->scratch_out + side, s));
     }
@@ -937,13 +1001,13 @@ int bte_get_intensity(bte_handle h, int geom, double* out, int on_device) {
   const size_t es = elem_bytes(prec);
   const char* I = h->Ibuf[h->cur] + (size_t)h->cell0[geom] * h->nd * h->nbp * es;
   if (on_device) {
-    CUDA_TRY(h, launch_pack(prec, nullptr, out, I, nullptr, h->I0ref, nc, h->nd, h->nb, h->nbp, 0, h->stream));
+    CUDA_TRY(h, launch_pack(prec, nullptr, out, I, nullptr, h->I0ref_o, nc, h->nd, h->nb, h->nbp, 0, h->stream));
   } else if (prec == BTE_FP64) {
     CUDA_TRY(h, cudaMemcpy2DAsync(out, h->nb * 8, I, h->nbp * 8, h->nb * 8, (size_t)nc * h->nd, cudaMemcpyDeviceToHost, h->stream));
   } else {
     for (long long c0 = 0; c0 < nc; c0 += h->pack_cells) {
       const long long n = std::min(h->pack_cells, nc - c0);
-      CUDA_TRY(h, launch_pack(prec, nullptr, h->scratch_pack, I + (size_t)c0 * h->nd * h->nbp * es, nullptr, h->I0ref, n,
+      CUDA_TRY(h, launch_pack(prec, nullptr, h->scratch_pack, I + (size_t)c0 * h->nd * h->nbp * es, nullptr, h->I0ref_o, n,
                               h->nd, h->nb, h->nbp, 0, h->stream));
       CUDA_TRY(h, cudaMemcpyAsync(out + (size_t)c0 * h->nd * h->nb, h->scratch_pack, (size_t)n * h->nd * h->nb * 8,
                                   cudaMemcpyDeviceToHost, h->stream));
@@ -965,7 +1029,7 @@ int bte_set_intensity(bte_handle h, int geom, const double* in, const double* Tp
   char* I = h->Ibuf[h->cur] + (size_t)h->cell0[geom] * h->nd * h->nbp * es;
   cudaStream_t s = h->stream;
   if (on_device) {
-    CUDA_TRY(h, launch_pack(prec, in, nullptr, nullptr, I, h->I0ref, nc, h->nd, h->nb, h->nbp, 1, s));
+    CUDA_TRY(h, launch_pack(prec, in, nullptr, nullptr, I, h->I0ref_o, nc, h->nd, h->nb, h->nbp, 1, s));
     CUDA_TRY(h, cudaMemcpyAsync(h->Tp + h->cell0[geom], Tp_cells, nc * 8, cudaMemcpyDeviceToDevice, s));
   } else if (prec == BTE_FP64) {
     CUDA_TRY(h, cudaMemcpy2DAsync(I, h->nbp * 8, in, h->nb * 8, h->nb * 8, (size_t)nc * h->nd, cudaMemcpyHostToDevice, s));
@@ -975,15 +1039,19 @@ int bte_set_intensity(bte_handle h, int geom, const double* in, const double* Tp
       const long long n = std::min(h->pack_cells, nc - c0);
       CUDA_TRY(h, cudaMemcpyAsync(h->scratch_pack, in + (size_t)c0 * h->nd * h->nb, (size_t)n * h->nd * h->nb * 8,
                                   cudaMemcpyHostToDevice, s));
-      CUDA_TRY(h, launch_pack(prec, h->scratch_pack, nullptr, nullptr, I + (size_t)c0 * h->nd * h->nbp * es, h->I0ref, n,
+      CUDA_TRY(h, launch_pack(prec, h->scratch_pack, nullptr, nullptr, I + (size_t)c0 * h->nd * h->nbp * es, h->I0ref_o, n,
                               h->nd, h->nb, h->nbp, 1, s));
       CUDA_TRY(h, cudaStreamSynchronize(s));
     }
     CUDA_TRY(h, cudaMemcpyAsync(h->Tp + h->cell0[geom], Tp_cells, nc * 8, cudaMemcpyHostToDevice, s));
   }
-  CUDA_TRY(h, launch_state_from_Tp(h->I0cell + h->cell0[geom] * h->nbp, h->J + h->cell0[geom] * 3 * h->nbp,
+  CUDA_TRY(h, launch_state_from_Tp(h->I0cell + h->cell0[geom] * h->nbp, h->J + h->cell0[geom] * 3 * h->nbp_all,
                                    h->Tp + h->cell0[geom], h->Teval + h->cell0[geom], nc, thermo(h), s));
-  CUDA_TRY(h, launch_energy_L(prec, I, h->I0ref, h->EL + h->cell0[geom], h->wdir, nc, h->nd, thermo(h), s));
+  if (h->Epart) {
+    h->EL_partial = true;  // this handle holds only its bands' share of E_L until the next step's exchange
+  } else {
+    CUDA_TRY(h, launch_energy_L(prec, I, h->I0ref_o, h->EL + h->cell0[geom], h->wdir, nc, h->nd, thermo(h), s));
+  }
   CUDA_TRY(h, cudaStreamSynchronize(s));
   h->TL_valid = false;
   return BTE_OK;
@@ -1022,7 +1090,7 @@ void mlp_init_host(std::vector<float>& p, int k, unsigned long long seed) {
 }
 
 int mlp_net_offset(const bte_ctx* h, int net, int* k) {
-  *k = net == 0 ? 1 : h->nb;
+  *k = net == 0 ? 1 : h->nb_all;
   return net == 0 ? 0 : mlp_param_count(1);
 }
 
@@ -1037,7 +1105,7 @@ int bte_train_mlp(bte_handle h, long long n_pairs, double T_lo, double T_hi, int
   if (!(T_lo >= kTmin && T_hi <= kTmax && T_hi > T_lo + 1.0)) return fail(h, BTE_E_ARG, "need 1 <= T_lo < T_hi <= 5000 K");
   if (epochs < 1) return fail(h, BTE_E_ARG, "epochs must be >= 1");
   cudaStream_t s = h->stream;
-  const int n = (int)n_pairs, nb = h->nb, B = 1024;
+  const int n = (int)n_pairs, nb = h->nb_all, B = 1024;
   // normalisation
   h->mlp_Tlo = T_lo;
   h->mlp_Thi = T_hi;

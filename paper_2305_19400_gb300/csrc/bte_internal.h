@@ -76,11 +76,14 @@ struct ThermoTables {
   const double* node_C;   // [nbp][ng] I0_b(T) = sum_i node_C / expm1(node_c / T)
   const double* a_p;      // [nbp] W beta_b / v_b  (T_p equation weights)
   const double* a_L;      // [nbp] W / v_b         (T_L equation weights)
-  const double* inv_v;    // [nbp] 1/v_b (0 on padding)
-  const double* beta;     // [nbp]
+  const double* inv_v;    // [nbo] 1/v_b of the stored bands (0 on padding)
+  const double* beta;     // [nbo] beta_b of the stored bands (0 on padding)
   int ng;
-  int nbp;
-  int nb;
+  int nbp;    // all bands, padded: width of node tables, J, a_p and a_L
+  int nb;     // all bands
+  int nbo;    // bands this handle stores (padded): width of I rows, I0cell, wall ghosts
+  int nbr;    // bands this handle stores (real): stored band b < nbr is global band band0 + b
+  int band0;  // global index of the first stored band (0 unless the handle owns a band range)
 };
 
 struct SweepArgs {
@@ -117,6 +120,8 @@ struct SweepArgs {
   int maxit;
   double Wtot;              // sum of direction weights
   int dry;                  // 1: timing run, the epilogue writes no solver state
+  int partial;              // 1: band-range handle; the epilogue writes per-cell partial (E_L, E_p)
+  double* Epart;            //    to Epart[cell][2] and the solve runs after the caller's all-reduce
   int pf_dirs;              // directions per L2 prefetch chunk (0: no prefetch)
   int explicit_scheme;      // reduced modes compute P, Q on the fly from these:
   float dt32, rdt32;        // dt and 1/dt
@@ -132,6 +137,7 @@ cudaError_t launch_sweep_fp32(int pd, const SweepArgs& a, int dim, int threads, 
 cudaError_t launch_sweep_bf16(int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
 struct MLPView;
 cudaError_t launch_fixup(const SweepArgs& a, const MLPView* mlp, cudaStream_t s);
+cudaError_t launch_solve_cells(const SweepArgs& a, long long ncells, cudaStream_t s);
 // learned guess (bte_mlp.cu)
 int mlp_param_total(int nb);
 cudaError_t launch_mlp_norm(ThermoTables th, double T_lo, double T_hi, const double* I0ref, double* r_lo, double* r_hi,

@@ -58,11 +58,11 @@ __global__ void fixup_kernel(SweepArgs a, int learned, MLPView m) {
     evals += r.evals;
     fb += r.fallback;
     bad += r.bad;
-    // I0 refresh from the (just written) model at r.Te
+    // I0 refresh of the stored bands from the (just written) model at r.Te
     const double hd2 = 0.5 * r.delta * r.delta;
-    for (int b = lane; b < nbp; b += 32) {
-      const long long j = (P * 3) * nbp + b;
-      a.I0cell[P * nbp + b] = fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], r.delta, a.J[j]));
+    for (int b = lane; b < a.th.nbo; b += 32) {
+      const long long j = (P * 3) * nbp + a.th.band0 + b;
+      a.I0cell[P * a.th.nbo + b] = b < a.th.nbr ? fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], r.delta, a.J[j])) : 0.0;
     }
     if (lane == 0) {
       a.Teval[P] = r.Te;
@@ -81,15 +81,17 @@ __global__ void fixup_kernel(SweepArgs a, int learned, MLPView m) {
 // T_e = T_p = T.  One CTA per cell (grid-stride); bands over threads.
 __device__ void cell_state_at(double* I0cell, double* J, long long P, double T, ThermoTables th, double* row) {
   const double rT = 1.0 / T;
-  for (int b = threadIdx.x; b < th.nbp; b += blockDim.x) {
+  for (int b = threadIdx.x; b < th.nbp; b += blockDim.x) {  // every band (the temperature model)
     double f, d1, d2;
     band_I0_d2(th.node_c + b * th.ng, th.node_C + b * th.ng, th.ng, rT, f, d1, d2);
     row[b] = f;
-    I0cell[P * th.nbp + b] = f;
     J[(P * 3 + 0) * th.nbp + b] = f;
     J[(P * 3 + 1) * th.nbp + b] = d1;
     J[(P * 3 + 2) * th.nbp + b] = d2;
   }
+  __syncthreads();
+  for (int b = threadIdx.x; b < th.nbo; b += blockDim.x)  // stored bands
+    I0cell[P * th.nbo + b] = b < th.nbr ? row[th.band0 + b] : 0.0;
 }
 
 // Equilibrium initial state: I = I0_b(T_P) for every direction (stored as the
@@ -104,10 +106,10 @@ __global__ void init_cells_kernel(S* I, double* I0cell, double* J, double* Tp, d
     const double T = Tcells[c];
     cell_state_at(I0cell, J, P, T, th, row);
     __syncthreads();
-    const long long n = (long long)nd * th.nbp;
+    const long long n = (long long)nd * th.nbo;
     for (long long e = threadIdx.x; e < n; e += blockDim.x) {
-      const int b = (int)(e % th.nbp);
-      const double v = sizeof(S) == 8 ? row[b] : row[b] - I0ref[b];
+      const int b = (int)(e % th.nbo);  // stored band; I0ref holds the stored bands
+      const double v = b < th.nbr ? (sizeof(S) == 8 ? row[th.band0 + b] : row[th.band0 + b] - I0ref[b]) : 0.0;
       if constexpr (sizeof(S) == 2) I[P * n + e] = __double2bfloat16(v);
       else I[P * n + e] = (S)v;
     }
@@ -136,11 +138,12 @@ __global__ void state_from_Tp_kernel(double* I0cell, double* J, const double* Tp
 
 // Wall ghost intensities (FP64): one thread per (face, band).
 __global__ void wall_I0_kernel(double* I0wall, const double* Tf, long long nfaces, ThermoTables th) {
-  const long long n = nfaces * th.nbp;
+  const long long n = nfaces * th.nbo;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const long long f = e / th.nbp;
-    const int b = (int)(e - f * th.nbp);
-    I0wall[e] = band_I0(th.node_c + b * th.ng, th.node_C + b * th.ng, th.ng, 1.0 / Tf[f]);
+    const long long f = e / th.nbo;
+    const int b = (int)(e - f * th.nbo);
+    const int bg = th.band0 + b;
+    I0wall[e] = b < th.nbr ? band_I0(th.node_c + bg * th.ng, th.node_C + bg * th.ng, th.ng, 1.0 / Tf[f]) : 0.0;
   }
 }
 
@@ -295,15 +298,78 @@ __global__ void energy_L_kernel(const S* I, const double* I0ref, double* EL, con
                                 int nd, ThermoTables th) {
   extern __shared__ double sh[];
   for (long long P = blockIdx.x; P < ncells; P += gridDim.x) {
-    const long long base = P * (long long)nd * th.nbp;
+    const long long base = P * (long long)nd * th.nbo;
     double acc = 0.0;
-    for (int b = threadIdx.x; b < th.nbp; b += blockDim.x) {
+    for (int b = threadIdx.x; b < th.nbo; b += blockDim.x) {
       double G = 0.0;
-      for (int d = 0; d < nd; ++d) G = fma(wdir[d], full_I(I, base + (long long)d * th.nbp + b, b, I0ref), G);
+      for (int d = 0; d < nd; ++d) G = fma(wdir[d], full_I(I, base + (long long)d * th.nbo + b, b, I0ref), G);
       acc = fma(G, th.inv_v[b], acc);
     }
     const double t = block_sum(acc, sh);
     if (threadIdx.x == 0) EL[P] = t;
+  }
+}
+
+// Temperature step of a band-range handle after the caller's all-reduce: one
+// warp per cell; E_L, E_p from Epart, the T_p equation on the cached quadratic
+// model of all bands, I0 refresh of the stored bands, the rest to the fix-up.
+__global__ void solve_cells_kernel(SweepArgs a, long long ncells) {
+  const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
+  const int nbp = a.th.nbp;
+  unsigned long long solves = 0, badc = 0;
+  for (long long P = blockIdx.x * (long long)warps + threadIdx.x / 32; P < ncells; P += (long long)gridDim.x * warps) {
+    const double EL = a.Epart[2 * P], Ep = a.Epart[2 * P + 1];
+    const bool finite = isfinite(EL) && isfinite(Ep);
+    if (!a.solve_tp) {  // every beta_b is zero: only E_L is kept
+      if (lane == 0) {
+        a.EL[P] = EL;
+        if (!finite) ++badc;
+      }
+      continue;
+    }
+    double F = 0.0, F1 = 0.0, F2 = 0.0;
+    for (int b = lane; b < nbp; b += 32) {
+      const double ap = a.th.a_p[b];
+      F = fma(ap, a.J[(P * 3 + 0) * nbp + b], F);
+      F1 = fma(ap, a.J[(P * 3 + 1) * nbp + b], F1);
+      F2 = fma(ap, a.J[(P * 3 + 2) * nbp + b], F2);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      F += __shfl_xor_sync(0xffffffffu, F, o);
+      F1 += __shfl_xor_sync(0xffffffffu, F1, o);
+      F2 += __shfl_xor_sync(0xffffffffu, F2, o);
+    }
+    F -= Ep;
+    const double Te = a.Teval[P];
+    const double disc = F1 * F1 - 2.0 * F * F2;
+    const double delta = (disc >= 0.0 && F1 > 0.0) ? -2.0 * F / (F1 + sqrt(disc)) : -F / F1;
+    const double Tn = Te + delta;
+    const bool ok = finite && isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn;
+    if (lane == 0) {
+      a.EL[P] = EL;
+      if (!finite) ++badc;
+      else ++solves;
+      if (finite && !ok) {
+        const unsigned k = atomicAdd(a.fix_count, 1u);
+        FixItem fi;
+        fi.P = P;
+        fi.Ep = Ep;
+        fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[P];
+        a.fix[k] = fi;
+      }
+      if (ok) a.Tp[P] = Tn;
+    }
+    if (ok) {
+      const double hd2 = 0.5 * delta * delta;
+      for (int b = lane; b < a.th.nbo; b += 32) {
+        const long long j = (P * 3) * nbp + a.th.band0 + b;
+        a.I0cell[P * a.th.nbo + b] = b < a.th.nbr ? fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], delta, a.J[j])) : 0.0;
+      }
+    }
+  }
+  if (lane == 0 && a.counters) {
+    if (solves) atomicAdd(&a.counters->solves, solves);
+    if (badc) atomicAdd(&a.counters->nonfinite, badc);
   }
 }
 
@@ -333,6 +399,11 @@ cudaError_t launch_fixup(const SweepArgs& a, const MLPView* mlp, cudaStream_t s)
   return cudaGetLastError();
 }
 
+cudaError_t launch_solve_cells(const SweepArgs& a, long long ncells, cudaStream_t s) {
+  solve_cells_kernel<<<cell_grid(ncells / 4 + 1), 128, 0, s>>>(a, ncells);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init_cells(int precision, void* I, double* I0cell, double* J, double* Tp, double* Te, double* TL,
                               double* EL, const double* Tcells, const double* I0ref, long long cell0, int ncells, int nd,
                               ThermoTables th, cudaStream_t s) {
@@ -350,12 +421,12 @@ cudaError_t launch_init_cells(int precision, void* I, double* I0cell, double* J,
 
 cudaError_t launch_state_from_Tp(double* I0cell, double* J, const double* Tp, double* Te, long long ncells,
                                  ThermoTables th, cudaStream_t s) {
-  state_from_Tp_kernel<<<cell_grid(ncells), 64, th.nbp * sizeof(double), s>>>(I0cell, J, Tp, Te, ncells, th);
+  state_from_Tp_kernel<<<cell_grid(ncells), 64, th.nbp * sizeof(double), s>>>(I0cell, J, Tp, Te, ncells, th);  // row: all bands
   return cudaGetLastError();
 }
 
 cudaError_t launch_wall_I0(double* I0wall, const double* Tfaces, long long nfaces, ThermoTables th, cudaStream_t s) {
-  wall_I0_kernel<<<grid_for(nfaces * th.nbp, 256), 256, 0, s>>>(I0wall, Tfaces, nfaces, th);
+  wall_I0_kernel<<<grid_for(nfaces * th.nbo, 256), 256, 0, s>>>(I0wall, Tfaces, nfaces, th);
   return cudaGetLastError();
 }
 

@@ -48,8 +48,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 template <int DIM, typename S>
 __device__ __forceinline__ void prefetch_rows(const SweepArgs& a, int gnx, int gny, int gnz, const S* In, const S* Ik,
                                               long long P, int ci, int cj, int ck, long long row, int d, int n) {
-  const unsigned bytes = (unsigned)n * a.th.nbp * sizeof(S);
-  const size_t off = (size_t)d * a.th.nbp;
+  const unsigned bytes = (unsigned)n * a.th.nbo * sizeof(S);
+  const size_t off = (size_t)d * a.th.nbo;
   prefetch_l2(In + P * row + off, bytes);
   if (ci > 0) prefetch_l2(Ik + (P - 1) * row + off, bytes);
   if (ci < gnx - 1) prefetch_l2(Ik + (P + 1) * row + off, bytes);
@@ -81,7 +81,7 @@ struct CellAddr {
 template <int AX, typename S>
 __device__ __forceinline__ const void* wall_ghost_src(const SweepArgs& a, const DevGeom* gp, const CellAddr<S>& c,
                                                       const int4 di, bool from_low, int b0) {
-  const int nbp = a.th.nbp;
+  const int nbp = a.th.nbo;
   const int side = 2 * AX + (from_low ? 0 : 1);
   if (gp->bc[side] == 0) {  // wall data stay in memory (L1): only wall cells get here
     const long long f = gp->face0[side] + (AX == 0 ? c.cj + (long long)gp->ny * c.ck
@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   extern __shared__ double sm[];
   __shared__ unsigned long long cnt_solves, cnt_bad;
   __shared__ int cur_cls;
-  const int lpc = a.lpc, nd = a.nd, nbp = a.th.nbp, dstep = a.dteam;
+  const int lpc = a.lpc, nd = a.nd, nbp = a.th.nbo, dstep = a.dteam;
+  const int nbp_all = a.th.nbp, band0 = a.th.band0, nbr = a.th.nbr;
   const int team = lpc * dstep;                       // lanes per cell
   const int cpb = blockDim.x / team;
   const int slot = threadIdx.x / team, tl = threadIdx.x - slot * team;
@@ -364,13 +365,13 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         eL += e;
         ep = fma(a.th.beta[b0 + v], e, ep);
       }
-      if (active && a.solve_tp) {
+      if (active && a.solve_tp && !a.partial) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const double ap = a.th.a_p[b0 + v];
-          F = fma(ap, a.J[(P * 3 + 0) * nbp + b0 + v], F);
-          F1 = fma(ap, a.J[(P * 3 + 1) * nbp + b0 + v], F1);
-          F2 = fma(ap, a.J[(P * 3 + 2) * nbp + b0 + v], F2);
+          F = fma(ap, a.J[(P * 3 + 0) * nbp_all + b0 + v], F);
+          F1 = fma(ap, a.J[(P * 3 + 1) * nbp_all + b0 + v], F1);
+          F2 = fma(ap, a.J[(P * 3 + 2) * nbp_all + b0 + v], F2);
         }
       }
       double* r5 = red + 5 * (size_t)(slot * lpc + lane);
@@ -395,7 +396,12 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       double* st = cst + 2 * slot;
       st[0] = 0.0;   // accepted step from T_e
       st[1] = 0.0;   // 1 when the cached model is accepted
-      if (active) {
+      if (active && a.partial) {  // band-range handle: partial sums for the caller's all-reduce
+        if (!a.dry) {
+          a.Epart[2 * P] = EL;
+          a.Epart[2 * P + 1] = Ep;
+        }
+      } else if (active) {
         if (!a.dry) a.EL[P] = EL;
         if (!isfinite(EL) || !isfinite(Ep)) {
           atomicAdd(&cnt_bad, 1ULL);
@@ -426,8 +432,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       const double hd2 = 0.5 * dlt * dlt;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        const long long j = (P * 3) * nbp + b0 + v;
-        a.I0cell[P * nbp + b0 + v] = fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], dlt, a.J[j]));
+        const long long j = (P * 3) * nbp_all + band0 + b0 + v;
+        a.I0cell[P * nbp + b0 + v] =
+            b0 + v < nbr ? fma(a.J[j + 2 * nbp_all], hd2, fma(a.J[j + nbp_all], dlt, a.J[j])) : 0.0;
       }
       if (lane == 0) a.Tp[P] = a.Teval[P] + dlt;
     }

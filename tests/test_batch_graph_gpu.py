@@ -63,7 +63,7 @@ def test_graph_replay_equals_eager_launches_bitwise():
     for nsteps, ninner in ((1, 5), (2, 5), (1, 4), (3, 5)):   # different buffer rotations and graph keys
         r1 = eager.step(nsteps=nsteps, ninner=ninner)[1]
         r2 = graph.step(nsteps=nsteps, ninner=ninner)[1]
-        assert r1["launches"] == r2["launches"] == nsteps * ninner
+        assert r1["launches"] == r2["launches"] == 2 * nsteps * ninner   # sweep + fix-up
     assert np.array_equal(eager.intensity(0), graph.intensity(0))
     assert np.array_equal(eager.T(0, bte.BTE_T_PSEUDO), graph.T(0, bte.BTE_T_PSEUDO))
     eager.close(); graph.close()

@@ -70,3 +70,6 @@ def test_null_handle_is_an_argument_error(lib):
     assert lib.bte_step(None, 1e-12, 1, 1, 0, None) == -1
     assert lib.bte_destroy(None) == -1
     assert lib.bte_workspace_bytes(None) == 0
+    assert lib.bte_set_band_range(None, 0, 1) == -1
+    from paper_2305_19400_gb300 import bte
+    assert lib.bte_set_exchange(None, bte.bte_allreduce_fn(), None, None) == -1

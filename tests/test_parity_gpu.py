@@ -72,7 +72,7 @@ def test_cfg1_full_run_matches_oracle():
     wl = W.cfg1()
     s, rc, st = gpu_run(wl)
     assert rc == 0 and st["nonfinite"] == 0
-    assert st["launches"] == 1000
+    assert st["launches"] == 2000                  # sweep + fix-up per inner iteration
     p, ost = oracle_run(wl)
     assert_close_T(s.T(0, bte.BTE_T_LATTICE), ost["TL"], what="T_L")
     assert_close_T(s.T(0, bte.BTE_T_PSEUDO), ost["Tp"], what="T_p")
@@ -105,7 +105,7 @@ def test_explicit_scheme_matches_oracle():
     wl = W.cfg1()
     T0 = W.random_temperatures(400, 21, 295.0, 305.0)
     s, rc, st = gpu_run(wl, T_init=[T0], nsteps=40, ninner=1, scheme=bte.BTE_EXPLICIT, dt=2e-13)
-    assert st["launches"] == 40
+    assert st["launches"] == 80
     p, ost = oracle_run(wl, T_init=T0, nsteps=40, ninner=1, scheme=O.EXPLICIT, dt=2e-13)
     assert_close_T(s.T(0, bte.BTE_T_LATTICE), ost["TL"], what="T_L")
     assert_close_T(s.T(0, bte.BTE_T_PSEUDO), ost["Tp"], what="T_p")
@@ -239,7 +239,7 @@ def test_call_order_and_argument_errors():
         bte.bte_step(h, -1.0, 1, 1)
     assert e.value.code == -1
     rc, st = bte.bte_step(h, 1e-12, 1, 1)
-    assert rc == 0 and st["launches"] == 1
+    assert rc == 0 and st["launches"] == 2
     bte.bte_destroy(h)
 
 
