@@ -40,7 +40,10 @@ KERNEL_SRCS = [os.path.join(ROOT, "paper_2305_19400_gb300", "csrc", f) for f in 
 FP64_PEAK_FLOPS = 2 * 2 * 152 * 2.070e9
 # Algorithmic work of one 2-D implicit update: A_n*I^n + A_x*I_x + A_y*I_y + A_s*I0 (4 mul + 3 add)
 # and the reduction G_b += w_d*I (1 mul + 1 add); bytes: I^n read, I^k read once, I^{k+1} written.
+# A_n*I^n is the same in every inner iteration of a step: computed (and kept) in the first,
+# so the later ones take 1 mul fewer.
 FLOPS_PER_UPDATE_2D = 9
+FLOPS_PER_UPDATE_2D_LATER = 8
 BYTES_PER_UPDATE_FP64 = 24
 
 
@@ -205,18 +208,29 @@ def cpu_baseline_for(args):
 
 
 def run_variants(peaks):
-    """The reduced-precision and batched forms of the path, each on its own workload:
-    FP32 and BF16 storage on the 3-D 64^3 x 400 x 55 workload (15 inner iterations per
-    step) and the 48-geometry FP32 batch (12 inner iterations), all with CUDA graphs and
-    the autotuner.  Device-timed like the main line; bytes per update are the algorithmic
-    3 x storage size."""
+    """The reduced-precision, learned and batched forms of the path, each on its own
+    workload: FP32 and BF16 storage on the 3-D 64^3 x 400 x 55 workload (15 inner
+    iterations per step), FP32 with the learned guess on the 3-D 100x100x50 workload
+    (networks trained on the GPU on 1e6 pairs over [250, 400] K before timing; 15 inner
+    iterations) and the 48-geometry FP32 batch (12 inner iterations), all with CUDA
+    graphs and the autotuner.  Device-timed like the main line; bytes per update are the
+    algorithmic 3 x storage size."""
     import torch
     from paper_2305_19400_gb300 import bte, workloads as W
     out = []
-    cases = [("fp32_3d_64^3", W.cfg3(64), bte.BTE_FP32, 4, 15), ("bf16_3d_64^3", W.cfg3(64, "bf16"), bte.BTE_BF16, 4, 15),
-             ("fp32_batch_48_geometries", W.cfg5(), bte.BTE_FP32, 3, 12)]
-    for name, wl, prec, steps, ninner in cases:
-        s = bte.Solver(wl, precision=prec, use_graph=True)
+    cases = [("fp32_3d_64^3", lambda: W.cfg3(64), bte.BTE_FP32, 4, 15, False),
+             ("bf16_3d_64^3", lambda: W.cfg3(64, "bf16"), bte.BTE_BF16, 4, 15, False),
+             ("fp32_learned_3d_100x100x50", lambda: W.cfg4(), bte.BTE_FP32, 3, 15, True),
+             ("fp32_batch_48_geometries", lambda: W.cfg5(), bte.BTE_FP32, 3, 12, False)]
+    for name, mk, prec, steps, ninner, learned in cases:
+        wl = mk()
+        s = bte.Solver(wl, precision=prec, use_graph=True, learned=learned)
+        extra = {}
+        if learned:
+            t0 = time.perf_counter()
+            loss = bte.bte_train_mlp(s.h, 1_000_000, 250.0, 400.0, 4, seed=1)
+            extra["mlp_training"] = {"pairs": 1_000_000, "epochs": 4, "loss_A": float(loss[0]),
+                                     "loss_B": float(loss[1]), "s": time.perf_counter() - t0}
         choice = bte.bte_autotune(s.h, wl.dt).strip().splitlines()[-1]
         s.step(nsteps=1, ninner=ninner, want_stats=False)
         torch.cuda.synchronize()
@@ -236,7 +250,10 @@ def run_variants(peaks):
                     "cells": sum(g.ncells for g in wl.geoms),
                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                  "frac": gbs / peaks["hbm_gbs"], "bytes_per_update": bpu},
-                    "launch": choice})
+                    "launch": choice, **extra})
+        if learned:
+            st = s.step(nsteps=1, ninner=ninner)[1]
+            out[-1]["solves_per_step"] = {k: st[k] for k in ("solves", "solve_evals", "fallbacks")}
         s.close()
         del s
         torch.cuda.empty_cache()
@@ -345,7 +362,8 @@ def main():
     # the whole step time (sweeps and fix-ups) charged to the sweeps: a lower bound of the sweep's own rate
     launch_s = ms_max * 1e-3 / (args.steps * args.ninner)
     upd_launch = updates_per_step / args.ninner
-    flops = FLOPS_PER_UPDATE_2D * upd_launch / launch_s
+    fpu = (FLOPS_PER_UPDATE_2D + (args.ninner - 1) * FLOPS_PER_UPDATE_2D_LATER) / args.ninner
+    flops = fpu * upd_launch / launch_s
     hbm = BYTES_PER_UPDATE_FP64 * upd_launch / launch_s / 1e9
     tpu = traffic_per_update()
     roofline = {"bound": "alu", "achieved": flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",

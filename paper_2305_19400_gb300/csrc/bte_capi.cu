@@ -482,10 +482,30 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, cudaStream_t s, in
   for (auto& g : h->geoms) dim = std::max(dim, g.dim);
   const int n = *cur;
   int k = n;
+  // FP64 implicit steps keep B = A_n I^n, the same in every inner iteration, in
+  // the third buffer: iteration 0 reads I^n and writes I^1 and B; iteration k
+  // reads B and I^k and overwrites the buffer I^n (or I^{k-2}) was in.
+  const bool use_b = h->opts.precision == BTE_FP64 && !a.explicit_scheme && ninner >= 2 && !a.dry;
+  int z = -1;
   for (int it = 0; it < ninner; ++it) {
     int o = 0;
-    while (o == n || o == k) ++o;
-    a.In = h->Ibuf[n];
+    a.bmode = 0;
+    a.Bout = nullptr;
+    if (use_b && it == 0) {
+      while (o == n) ++o;
+      z = 0;
+      while (z == n || z == o) ++z;
+      a.In = h->Ibuf[n];
+      a.Bout = h->Ibuf[z];
+      a.bmode = 1;
+    } else if (use_b) {
+      while (o == z || o == k) ++o;
+      a.In = h->Ibuf[z];
+      a.bmode = 2;
+    } else {
+      while (o == n || o == k) ++o;
+      a.In = h->Ibuf[n];
+    }
     a.Ik = h->Ibuf[k];
     a.Iout = h->Ibuf[o];
     cudaError_t e = cudaMemsetAsync(h->fix_count, 0, sizeof(unsigned), s);

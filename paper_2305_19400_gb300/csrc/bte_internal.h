@@ -90,6 +90,8 @@ struct SweepArgs {
   const void* In;           // I^n   (storage type; deviation from I0ref in the reduced modes)
   const void* Ik;           // I^k   (== In for the explicit scheme)
   void* Iout;               // I^{k+1}
+  void* Bout;               // FP64, bmode 1: receives B = A_n I^n (the inner-iteration invariant term)
+  int bmode;                // FP64 implicit: 0 In is I^n; 1 In is I^n and B is written; 2 In holds B
   double* I0cell;           // [cell][nbp] in: I0^k, out: I0^{k+1}
   double* Tp;               // [cell] in/out
   double* Teval;            // [cell] evaluation point of the cached quadrature model

@@ -70,6 +70,7 @@ struct CellAddr {
   const S* in;
   const S* ik;
   S* out;
+  S* bout;
   long long sx, sy, sz;
   int wall;      // bit 2*ax: low wall along ax, bit 2*ax+1: high wall
   int ci, cj, ck;
@@ -133,7 +134,10 @@ struct DirSm {
 
 constexpr int kStages = 4;  // depth of the cp.async staging ring
 
-template <int DIM, typename S, int MINB>
+// BM (FP64 implicit only): 0 plain; 1 also stores B = A_n I^n; 2 the In operand
+// holds B, so the update is B + A_x I_x + A_y I_y (+ A_z I_z) + A_s I0 (bitwise
+// the same value, one FP64 multiply fewer per update).
+template <int DIM, typename S, int MINB, int BM>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   using T = Tr<S>;
   using A = typename T::A;
@@ -211,6 +215,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       c.in = In + P * row + b0;
       c.ik = Ik + P * row + b0;
       c.out = Io + P * row + b0;
+      c.bout = BM == 1 ? reinterpret_cast<S*>(a.Bout) + P * row + b0 : nullptr;
       c.sx = row;
       c.sy = (long long)gnx * row;
       c.sz = (long long)gnx * gny * row;
@@ -282,14 +287,22 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         if (DIM == 3) read_up(st, 2, di, uz);
         A r[V];
         if constexpr (!kDev) {
-          A An[V], Ax[V], Ay[V], As[V];
-          ldgv<A, V>(cf + off, An);
+          A Ax[V], Ay[V], As[V];
           ldgv<A, V>(cf + plane + off, Ax);
           ldgv<A, V>(cf + 2 * plane + off, Ay);
           ldgv<A, V>(cf + 4 * plane + off, As);
+          if constexpr (BM == 2) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) r[v] = vn[v];
+          } else {
+            A An[V];
+            ldgv<A, V>(cf + off, An);
+#pragma unroll
+            for (int v = 0; v < V; ++v) r[v] = An[v] * vn[v];
+            if constexpr (BM == 1) T::st(c.bout + off, r);
+          }
 #pragma unroll
           for (int v = 0; v < V; ++v) {
-            r[v] = An[v] * vn[v];
             r[v] = fma(Ax[v], ux[v], r[v]);
             r[v] = fma(Ay[v], uy[v], r[v]);
           }
@@ -447,27 +460,40 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   }
 }
 
-template <typename S, int MINB>
+template <typename S, int MINB, int BM>
 cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   const int team = a.lpc * a.dteam, cpb = threads / team;
   const size_t smem = sizeof(DirSm) * (size_t)a.nd + (size_t)Tr<S>::V * threads * sizeof(double) +
                       5 * (size_t)cpb * a.lpc * sizeof(double) + 2 * (size_t)cpb * sizeof(double) + 16 +
                       (size_t)kStages * (dim == 3 ? 4 : 3) * threads * 16;
   if (dim == 3) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(sweep_kernel<3, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sweep_kernel<3, S, MINB><<<grid, threads, smem, s>>>(a);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(sweep_kernel<3, S, MINB, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sweep_kernel<3, S, MINB, BM><<<grid, threads, smem, s>>>(a);
   } else {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(sweep_kernel<2, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sweep_kernel<2, S, MINB><<<grid, threads, smem, s>>>(a);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(sweep_kernel<2, S, MINB, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sweep_kernel<2, S, MINB, BM><<<grid, threads, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
 
 // variant: 1 -> at least 2 resident CTAs per SM (<= 128 registers), 2 -> 3 CTAs (<= 80 registers)
+template <typename S, int BM>
+cudaError_t launch_bm(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
+  if (variant >= 2) return launch_minb<S, 3, BM>(a, dim, threads, grid, s);
+  return launch_minb<S, 2, BM>(a, dim, threads, grid, s);
+}
+
 template <typename S>
 cudaError_t launch(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
-  if (variant >= 2) return launch_minb<S, 3>(a, dim, threads, grid, s);
-  return launch_minb<S, 2>(a, dim, threads, grid, s);
+  if constexpr (sizeof(S) == 8) {
+    if (a.bmode == 1) return launch_bm<S, 1>(variant, a, dim, threads, grid, s);
+    if (a.bmode == 2) return launch_bm<S, 2>(variant, a, dim, threads, grid, s);
+  } else {
+    if (a.bmode != 0) return cudaErrorInvalidValue;  // the B form exists for FP64 storage only
+  }
+  return launch_bm<S, 0>(variant, a, dim, threads, grid, s);
 }
 
 }  // namespace sweep
