@@ -132,7 +132,16 @@ struct DirSm {
   float pad;
 };
 
-constexpr int kStages = 4;  // depth of the cp.async staging ring
+// Staging ring: per thread and stage, 16 bytes per operand.  Operands: I^n (or
+// B), the upwind value per axis, and in FP64 mode the coefficients A_x, A_y
+// (, A_z), A_s (A_n, needed once per step, is loaded directly).  FP64 3-D keeps
+// 3 stages so that two CTAs of 224 threads still fit an SM's shared memory.
+template <int DIM, typename S>
+struct Ring {
+  static constexpr bool kCoef = sizeof(S) == 8;
+  static constexpr int kOps = 1 + DIM + (kCoef ? DIM + 1 : 0);
+  static constexpr int kStages = (kCoef && DIM == 3) ? 3 : 4;
+};
 
 // BM (FP64 implicit only): 0 plain; 1 also stores B = A_n I^n; 2 the In operand
 // holds B, so the update is B + A_x I_x + A_y I_y (+ A_z I_z) + A_s I0 (bitwise
@@ -228,10 +237,33 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[v] = 0.f;
       int nacc = 0;
+      // FP64 mode: G_b = sum_d w_d I_d.  Over a run of directions with the same
+      // weight (one polar ring), each band sums I exactly in 64-bit fixed point
+      // on the integer pipe: unit 2^(E - 50) for the cell's I0 of exponent E, so
+      // a value up to 16 I0 adds at most 2^55 and a run of 256 cannot overflow;
+      // the run then enters G with one FP64 FMA (sum x w x unit).  Values with a
+      // larger exponent (or negative, NaN) take the FP64 FMA directly.  Terms
+      // below 2^-10 units are dropped (at most 1/4 unit per run).
+      unsigned long long facc[V];
+      long long fsc[V];  // unit exponent shifted into a double's exponent field
+      int fe0[V];        // largest exponent field summed in fixed point (-1: none)
+      long long wrun = 0;
+      int nrun = 0;
+      if constexpr (!kDev) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int e0 = (int)((unsigned long long)__double_as_longlong((double)src[v]) >> 52);  // src = I0 (>= 0)
+          const bool on = e0 >= 200 && e0 <= 1900;
+          facc[v] = 0ull;
+          fe0[v] = on ? e0 + 4 : -1;
+          fsc[v] = on ? (long long)(e0 - 1073) * (1LL << 52) : 0;
+        }
+      }
       // This lane's directions are d_j = dg + j*dstep.  Their operands (I^n and the
       // upwind I^k or wall ghost per axis) are copied global -> shared kStages-1
       // directions ahead with cp.async; each thread waits only for its own copies.
-      constexpr int kOps = DIM == 3 ? 4 : 3;
+      constexpr int kOps = Ring<DIM, S>::kOps;
+      constexpr int kStages = Ring<DIM, S>::kStages;
       constexpr int kVB = V * (int)sizeof(S);
       const int nsteps = dg < nd ? (nd - dg + dstep - 1) / dstep : 0;
       auto slot = [&](int st, int op) -> char* {
@@ -252,6 +284,12 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
                                    gp->bc[2 * ax + (((di.x >> ax) & 1) ? 0 : 1)] == 0;
             if (iso_ghost) cp_async<16>((unsigned)__cvta_generic_to_shared(slot(st, 1 + ax)), src_p);  // float4 ghost
             else cp_async<kVB>((unsigned)__cvta_generic_to_shared(slot(st, 1 + ax)), src_p);
+          }
+          if constexpr (Ring<DIM, S>::kCoef) {  // A_x, A_y (, A_z), A_s of this direction
+#pragma unroll
+            for (int k = 0; k < DIM; ++k)
+              cp_async<16>((unsigned)__cvta_generic_to_shared(slot(st, 1 + DIM + k)), cf + (size_t)(1 + k) * plane + off);
+            cp_async<16>((unsigned)__cvta_generic_to_shared(slot(st, 1 + 2 * DIM)), cf + 4 * plane + off);
           }
         }
         cp_async_commit();
@@ -288,9 +326,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         A r[V];
         if constexpr (!kDev) {
           A Ax[V], Ay[V], As[V];
-          ldgv<A, V>(cf + plane + off, Ax);
-          ldgv<A, V>(cf + 2 * plane + off, Ay);
-          ldgv<A, V>(cf + 4 * plane + off, As);
+          Tr<double>::ld(reinterpret_cast<const double*>(slot(st, 1 + DIM)), Ax);
+          Tr<double>::ld(reinterpret_cast<const double*>(slot(st, 2 + DIM)), Ay);
+          Tr<double>::ld(reinterpret_cast<const double*>(slot(st, 1 + 2 * DIM)), As);
           if constexpr (BM == 2) {
 #pragma unroll
             for (int v = 0; v < V; ++v) r[v] = vn[v];
@@ -308,7 +346,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
           }
           if (DIM == 3) {
             A Az[V];
-            ldgv<A, V>(cf + 3 * plane + off, Az);
+            Tr<double>::ld(reinterpret_cast<const double*>(slot(st, 3 + DIM)), Az);
 #pragma unroll
             for (int v = 0; v < V; ++v) r[v] = fma(Az[v], uz[v], r[v]);
           }
@@ -316,8 +354,34 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
           for (int v = 0; v < V; ++v) r[v] = fma(As[v], src[v], r[v]);
           T::st(c.out + off, r);
           const double wd = dsm[d].w;
+          const long long wb = __double_as_longlong(wd);
+          if (wb != wrun || nrun == 256) {  // close the run: sum x (w x unit)
 #pragma unroll
-          for (int v = 0; v < V; ++v) G[v] = fma(wd, (double)r[v], G[v]);
+            for (int v = 0; v < V; ++v) {
+              if (facc[v] != 0ull) G[v] = fma(__ull2double_rn(facc[v]), __longlong_as_double(wrun + fsc[v]), G[v]);
+              facc[v] = 0ull;
+            }
+            wrun = wb;
+            nrun = 0;
+          }
+          ++nrun;
+          bool big = false;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const unsigned long long rb = (unsigned long long)__double_as_longlong((double)r[v]);
+            const int e = (int)(rb >> 52);
+            const unsigned long long m = ((rb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 2;
+            const int sh = e == 0 ? 63 : min(fe0[v] - e, 63);  // zero (and subnormal) adds nothing
+            facc[v] += sh >= 0 ? (m >> sh) : 0ull;
+            big |= sh < 0;
+          }
+          if (__any_sync(__activemask(), big)) {  // rare: a value beyond the fixed-point range
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              const int e = (int)((unsigned long long)__double_as_longlong((double)r[v]) >> 52);
+              if (e != 0 && fe0[v] - e < 0) G[v] = fma(wd, (double)r[v], G[v]);
+            }
+          }
         } else {
           // P and Q from v_b, beta_b and sum_ax c_ax (no table loads):
           // implicit Q = 1/(1/dt + beta_b + v_b sum c), P = Q/dt; explicit P = 1 - dt(beta_b + v_b sum c), Q = dt
@@ -358,6 +422,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       if constexpr (kDev) {
 #pragma unroll
         for (int v = 0; v < V; ++v) G[v] += (double)acc[v];
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (facc[v] != 0ull) G[v] = fma(__ull2double_rn(facc[v]), __longlong_as_double(wrun + fsc[v]), G[v]);
       }
     }
 
@@ -465,7 +533,8 @@ cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cuda
   const int team = a.lpc * a.dteam, cpb = threads / team;
   const size_t smem = sizeof(DirSm) * (size_t)a.nd + (size_t)Tr<S>::V * threads * sizeof(double) +
                       5 * (size_t)cpb * a.lpc * sizeof(double) + 2 * (size_t)cpb * sizeof(double) + 16 +
-                      (size_t)kStages * (dim == 3 ? 4 : 3) * threads * 16;
+                      (size_t)(dim == 3 ? Ring<3, S>::kStages * Ring<3, S>::kOps : Ring<2, S>::kStages * Ring<2, S>::kOps) *
+                          threads * 16;
   if (dim == 3) {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(sweep_kernel<3, S, MINB, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
