@@ -386,7 +386,7 @@ def main():
                       "band_pols": 55, "inner_iterations_per_step": args.ninner, "dt_s": wl.dt,
                       "scheme": "implicit Euler, point-Jacobi inner iterations",
                       "l2": "inputs larger than L2 (three FP64 intensity buffers of %.2f GB each)" % (wl.dof * 8 / 1e9),
-                      "launch": ("CUDA graph per time step, autotuned (cells_per_cta,threads,grid,min_ctas,l2_prefetch): "
+                      "launch": ("CUDA graph per time step, autotuned (cells_per_cta,threads,grid,min_ctas_variant): "
                                  + tune_choice) if tuned else "eager launches, default tiles",
                       "parallelism": f"replicas x{world}"},
            "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,

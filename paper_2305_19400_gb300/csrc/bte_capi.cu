@@ -57,7 +57,7 @@ struct bte_ctx {
   std::vector<bool> init_set;
   bool TL_valid = false;
   // launch shape
-  int lpc = 0, dteam = 1, cpb = 0, threads = 0, grid = 0, pd = 1, pf = 0;
+  int lpc = 0, dteam = 1, cpb = 0, threads = 0, grid = 0, pd = 1;
   // CUDA graphs of one time step, keyed by (scheme, ninner, starting buffer)
   struct GraphEntry {
     int scheme, ninner, cur_in, cur_out;
@@ -222,8 +222,8 @@ size_t carve(bte_ctx* h, char* base) {
 
 // Work list: runs of at most cpb consecutive cells along x.  2-D geometries are
 // walked row by row (the upwind row is nx cells back, well inside L2).  3-D
-// geometries are walked in column blocks of cpb x by cells marching in z, so
-// the z-upwind plane of a block (cpb*by cells back) is still in L2 when reused.
+// geometries are walked in column blocks of bx x by cells marching in z, so
+// the z-upwind plane of a block (bx*by cells back) is still in L2 when reused.
 void build_items(bte_ctx* h, int cpb = 0) {
   h->lpc = h->nbp / values_per_lane(h->opts.precision);  // one vector of bands per lane
   // a cell team covers dteam directions per step: ~896 contiguous bytes of a row
@@ -241,12 +241,15 @@ void build_items(bte_ctx* h, int cpb = 0) {
           h->items.push_back(WorkItem{(int)gi, j * g.nx + i, std::min(h->cpb, g.nx - i), 0});
       continue;
     }
-    const int bx = h->cpb, by = std::max(1, 256 / h->cpb);
+    // blocks of bx x by = 256 cells (bx a multiple of cpb, near square): the z
+    // plane of a block stays in L2, and few upwind rows cross a block edge
+    const int bx = std::max(h->cpb, 16 / h->cpb * h->cpb), by = std::max(1, 256 / bx);
     for (int j0 = 0; j0 < g.ny; j0 += by)
       for (int i0 = 0; i0 < g.nx; i0 += bx)
         for (int k = 0; k < g.nz; ++k)
           for (int j = j0; j < std::min(g.ny, j0 + by); ++j)
-            h->items.push_back(WorkItem{(int)gi, (k * g.ny + j) * g.nx + i0, std::min(bx, g.nx - i0), 0});
+            for (int i = i0; i < std::min(g.nx, i0 + bx); i += h->cpb)
+              h->items.push_back(WorkItem{(int)gi, (k * g.ny + j) * g.nx + i, std::min(h->cpb, std::min(g.nx, i0 + bx) - i), 0});
   }
   h->grid = (int)std::min<size_t>(h->items.size(), 65535);
 }
@@ -463,7 +466,6 @@ SweepArgs sweep_args(bte_ctx* h) {
   a.maxit = h->opts.newton_maxit;
   a.counters = h->counters;
   a.dry = 0;
-  a.pf_dirs = h->pf;
   a.explicit_scheme = h->coef_scheme == BTE_EXPLICIT ? 1 : 0;
   a.dt32 = (float)h->coef_dt;
   a.rdt32 = (float)(1.0 / h->coef_dt);
@@ -892,12 +894,11 @@ int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t repor
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev);
   const int spare = (h->cur + 1) % 3;  // timing launches write here; the state is untouched (dry epilogue)
-  struct Cand { int cpb, grid, pd, pf; float ms; };
+  struct Cand { int cpb, grid, pd; float ms; };
   std::vector<Cand> tried;
   const int tpc_list[2] = {128, 256};
   const int pd_list[2] = {1, 2};
-  const int pf_list[3] = {0, 8, 16};
-  int best_cpb = h->cpb, best_grid = h->grid, best_pd = h->pd, best_pf = h->pf;
+  int best_cpb = h->cpb, best_grid = h->grid, best_pd = h->pd;
   float best_ms = 1e30f;
   int dim = 2;
   for (auto& g : h->geoms) dim = std::max(dim, g.dim);
@@ -911,15 +912,13 @@ int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t repor
     const int nit = (int)h->items.size();
     const int grids[3] = {std::min(nit, 65535), std::min(nit, 2 * sms), std::min(nit, 4 * sms)};
     for (int gi = 0; gi < 3; ++gi)
-      for (int pd : pd_list)
-      for (int pf : pf_list) {
+      for (int pd : pd_list) {
         const int grid = grids[gi];
         bool dup = false;
-        for (auto& c : tried) dup |= c.cpb == cpb && c.grid == grid && c.pd == pd && c.pf == pf;
+        for (auto& c : tried) dup |= c.cpb == cpb && c.grid == grid && c.pd == pd;
         if (dup) continue;
         SweepArgs a = sweep_args(h);
         a.dry = 1;
-        a.pf_dirs = pf;
         a.counters = nullptr;
         a.In = a.Ik = h->Ibuf[h->cur];
         a.Iout = h->Ibuf[spare];
@@ -931,24 +930,23 @@ int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t repor
         float ms = 0.f;
         CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
         ms /= 3.f;
-        tried.push_back({cpb, grid, pd, pf, ms});
-        if (ms < best_ms) { best_ms = ms; best_cpb = cpb; best_grid = grid; best_pd = pd; best_pf = pf; }
+        tried.push_back({cpb, grid, pd, ms});
+        if (ms < best_ms) { best_ms = ms; best_cpb = cpb; best_grid = grid; best_pd = pd; }
       }
   }
   build_items(h, best_cpb);
   h->grid = best_grid;
   h->pd = best_pd;
-  h->pf = best_pf;
   CUDA_TRY(h, cudaMemcpyAsync(h->items_d, h->items.data(), h->items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaStreamSynchronize(s));
   drop_graphs(h);
   char buf[256];
-  h->tune_report = "cells_per_cta,threads,grid,min_ctas_variant,l2_prefetch_dirs,ms_per_launch\n";
+  h->tune_report = "cells_per_cta,threads,grid,min_ctas_variant,ms_per_launch\n";
   for (auto& c : tried) {
-    snprintf(buf, sizeof buf, "%d,%d,%d,%d,%d,%.4f\n", c.cpb, c.cpb * h->lpc * h->dteam, c.grid, c.pd, c.pf, c.ms);
+    snprintf(buf, sizeof buf, "%d,%d,%d,%d,%.4f\n", c.cpb, c.cpb * h->lpc * h->dteam, c.grid, c.pd, c.ms);
     h->tune_report += buf;
   }
-  snprintf(buf, sizeof buf, "chosen,%d,%d,%d,%d,%d\n", best_cpb, best_cpb * h->lpc * h->dteam, best_grid, best_pd, best_pf);
+  snprintf(buf, sizeof buf, "chosen,%d,%d,%d,%d\n", best_cpb, best_cpb * h->lpc * h->dteam, best_grid, best_pd);
   h->tune_report += buf;
   if (report && report_len) {
     std::strncpy(report, h->tune_report.c_str(), report_len - 1);

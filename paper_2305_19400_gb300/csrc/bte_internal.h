@@ -124,7 +124,6 @@ struct SweepArgs {
   int dry;                  // 1: timing run, the epilogue writes no solver state
   int partial;              // 1: band-range handle; the epilogue writes per-cell partial (E_L, E_p)
   double* Epart;            //    to Epart[cell][2] and the solve runs after the caller's all-reduce
-  int pf_dirs;              // directions per L2 prefetch chunk (0: no prefetch)
   int explicit_scheme;      // reduced modes compute P, Q on the fly from these:
   float dt32, rdt32;        // dt and 1/dt
   DevCounters* counters;

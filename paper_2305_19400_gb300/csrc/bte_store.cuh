@@ -25,6 +25,10 @@ template <> struct Tr<double> {
     __stcs(reinterpret_cast<double2*>(p), make_double2(x[0], x[1]));
   }
   static __device__ __forceinline__ double to_double(double v) { return v; }
+  // V values from a 32-bit shared-memory address
+  static __device__ __forceinline__ void lds(unsigned sa, A (&x)[V]) {
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x[0]), "=d"(x[1]) : "r"(sa));
+  }
 };
 
 template <> struct Tr<float> {
@@ -42,6 +46,9 @@ template <> struct Tr<float> {
     __stcs(reinterpret_cast<float4*>(p), make_float4(x[0], x[1], x[2], x[3]));
   }
   static __device__ __forceinline__ double to_double(float v) { return (double)v; }
+  static __device__ __forceinline__ void lds(unsigned sa, A (&x)[V]) {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]) : "r"(sa));
+  }
 };
 
 template <> struct Tr<__nv_bfloat16> {
@@ -66,7 +73,17 @@ template <> struct Tr<__nv_bfloat16> {
            make_uint2(*reinterpret_cast<const unsigned*>(&h0), *reinterpret_cast<const unsigned*>(&h1)));
   }
   static __device__ __forceinline__ double to_double(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+  static __device__ __forceinline__ void lds(unsigned sa, A (&x)[V]) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(sa));
+    unpack(v, x);
+  }
 };
+
+// Four floats from a 32-bit shared-memory address.
+__device__ __forceinline__ void lds_f4(unsigned sa, float (&x)[4]) {
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]) : "r"(sa));
+}
 
 // V consecutive values of type A from global memory (16-byte loads).
 template <typename A, int V>

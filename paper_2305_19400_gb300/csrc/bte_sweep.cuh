@@ -26,41 +26,15 @@
 // solve tolerance, and I0 is refreshed from it; other cells go to the fix-up
 // kernel (exact FP64 band quadrature).
 // Memory: I^n is read once, I^{k+1} written once, and each I^k row read from
-// DRAM once (adjacent cells, processed together, re-read it from L2).  Loads of
-// I^n and upwind I^k for a lane's next direction are issued before the current
-// one is computed; optionally one lane per cell also prefetches the next
-// pf_dirs directions of its rows into L2 with the bulk-copy engine.  MINB is
-// the launch-bounds minimum of resident CTAs per SM (a register cap).
+// DRAM once (adjacent cells, processed together, re-read it from L2).  Each
+// thread copies the operands of its next directions into shared memory with
+// cp.async kStages-1 steps before it uses them.  MINB is the launch-bounds
+// minimum of resident CTAs per SM (a register cap).
 #pragma once
 #include "bte_store.cuh"
 
 namespace bte {
 namespace sweep {
-
-// L2 prefetch of `bytes` (multiple of 16) from a 16-byte aligned global address
-// (bulk-async copy engine; a hint, nothing waits on it).
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Rows [d, d + n) of I^n for cell P and of I^k for every neighbour P may take
-// an upwind value from, into L2.
-template <int DIM, typename S>
-__device__ __forceinline__ void prefetch_rows(const SweepArgs& a, int gnx, int gny, int gnz, const S* In, const S* Ik,
-                                              long long P, int ci, int cj, int ck, long long row, int d, int n) {
-  const unsigned bytes = (unsigned)n * a.th.nbo * sizeof(S);
-  const size_t off = (size_t)d * a.th.nbo;
-  prefetch_l2(In + P * row + off, bytes);
-  if (ci > 0) prefetch_l2(Ik + (P - 1) * row + off, bytes);
-  if (ci < gnx - 1) prefetch_l2(Ik + (P + 1) * row + off, bytes);
-  if (cj > 0) prefetch_l2(Ik + (P - gnx) * row + off, bytes);
-  if (cj < gny - 1) prefetch_l2(Ik + (P + gnx) * row + off, bytes);
-  if (DIM == 3) {
-    const long long pl = (long long)gnx * gny;
-    if (ck > 0) prefetch_l2(Ik + (P - pl) * row + off, bytes);
-    if (ck < gnz - 1) prefetch_l2(Ik + (P + pl) * row + off, bytes);
-  }
-}
 
 // Per-cell addressing of one lane: its rows in I^n, I^k, I^{k+1} (band offset
 // applied), the element strides to the x/y/z neighbours and which sides are
@@ -231,8 +205,6 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       c.ci = ci; c.cj = cj; c.ck = ck;
       c.wall = (ci == 0) | ((ci == gnx - 1) << 1) | ((cj == 0) << 2) | ((cj == gny - 1) << 3) |
                (DIM == 3 ? ((ck == 0) << 4) | ((ck == gnz - 1) << 5) : 0);
-      const int pf = a.pf_dirs;
-      if (pf > 0 && tl == 0) prefetch_rows<DIM, S>(a, gnx, gny, gnz, In, Ik, P, ci, cj, ck, row, 0, min(pf, nd));
       float acc[V];  // reduced modes: FP32 partial band sums, flushed to G every 16 steps
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[v] = 0.f;
@@ -266,46 +238,52 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       constexpr int kStages = Ring<DIM, S>::kStages;
       constexpr int kVB = V * (int)sizeof(S);
       const int nsteps = dg < nd ? (nd - dg + dstep - 1) / dstep : 0;
-      auto slot = [&](int st, int op) -> char* {
-        return ring + ((size_t)(st * kOps + op) * blockDim.x + threadIdx.x) * 16;
-      };
+      // ring slot (stage st, operand op) of this thread: 32-bit shared addresses
+      const unsigned rb0 = (unsigned)__cvta_generic_to_shared(ring) + threadIdx.x * 16u;
+      const unsigned ostr = blockDim.x * 16u, sstr = kOps * ostr;
+      const long long sx = c.sx, sy = c.sy, sz = c.sz;
       auto issue = [&](int j) {
         if (j < nsteps) {
           const int d = dg + j * dstep;
-          const long long off = (long long)d * nbp;
-          const int4 di = dsm[d].info;
-          const int st = j % kStages;
-          cp_async<kVB>((unsigned)__cvta_generic_to_shared(slot(st, 0)), c.in + off);
+          const int off = d * nbp;
+          const unsigned sb = rb0 + (unsigned)(j % kStages) * sstr;
+          cp_async<kVB>(sb, c.in + off);
+          if (c.wall == 0) {  // interior cell: the upwind rows are the neighbours' (the common case)
+            const int up = dsm[d].info.x;
+            cp_async<kVB>(sb + ostr, c.ik + off + ((up & 1) ? -sx : sx));
+            cp_async<kVB>(sb + 2 * ostr, c.ik + off + ((up & 2) ? -sy : sy));
+            if (DIM == 3) cp_async<kVB>(sb + 3 * ostr, c.ik + off + ((up & 4) ? -sz : sz));
+          } else {
+            const int4 di = dsm[d].info;
 #pragma unroll
-          for (int ax = 0; ax < DIM; ++ax) {
-            const void* src_p = ax == 0 ? upwind_src<0, S>(a, gp, c, di, off, b0)
-                              : (ax == 1 ? upwind_src<1, S>(a, gp, c, di, off, b0) : upwind_src<2, S>(a, gp, c, di, off, b0));
-            const bool iso_ghost = (sizeof(S) == 2) && ((c.wall >> (2 * ax + (((di.x >> ax) & 1) ? 0 : 1))) & 1) &&
-                                   gp->bc[2 * ax + (((di.x >> ax) & 1) ? 0 : 1)] == 0;
-            if (iso_ghost) cp_async<16>((unsigned)__cvta_generic_to_shared(slot(st, 1 + ax)), src_p);  // float4 ghost
-            else cp_async<kVB>((unsigned)__cvta_generic_to_shared(slot(st, 1 + ax)), src_p);
+            for (int ax = 0; ax < DIM; ++ax) {
+              const void* src_p = ax == 0 ? upwind_src<0, S>(a, gp, c, di, off, b0)
+                                : (ax == 1 ? upwind_src<1, S>(a, gp, c, di, off, b0) : upwind_src<2, S>(a, gp, c, di, off, b0));
+              const bool iso_ghost = (sizeof(S) == 2) && ((c.wall >> (2 * ax + (((di.x >> ax) & 1) ? 0 : 1))) & 1) &&
+                                     gp->bc[2 * ax + (((di.x >> ax) & 1) ? 0 : 1)] == 0;
+              if (iso_ghost) cp_async<16>(sb + (1 + ax) * ostr, src_p);  // float4 ghost
+              else cp_async<kVB>(sb + (1 + ax) * ostr, src_p);
+            }
           }
           if constexpr (Ring<DIM, S>::kCoef) {  // A_x, A_y (, A_z), A_s of this direction
 #pragma unroll
-            for (int k = 0; k < DIM; ++k)
-              cp_async<16>((unsigned)__cvta_generic_to_shared(slot(st, 1 + DIM + k)), cf + (size_t)(1 + k) * plane + off);
-            cp_async<16>((unsigned)__cvta_generic_to_shared(slot(st, 1 + 2 * DIM)), cf + 4 * plane + off);
+            for (int k = 0; k < DIM; ++k) cp_async<16>(sb + (1 + DIM + k) * ostr, cf + (size_t)(1 + k) * plane + off);
+            cp_async<16>(sb + (1 + 2 * DIM) * ostr, cf + 4 * plane + off);
           }
         }
         cp_async_commit();
       };
-      // Upwind operand of axis ax for direction d from its slot (BF16 iso ghosts are float4).
-      auto read_up = [&](int st, int ax, const int4 di, A (&x)[V]) {
+      // Upwind operand of axis ax from its slot (BF16 iso ghosts are float4).
+      auto read_up = [&](unsigned sb, int ax, const int4 di, A (&x)[V]) {
         if constexpr (sizeof(S) == 2) {
           const bool lowside = (di.x >> ax) & 1;
           const int side = 2 * ax + (lowside ? 0 : 1);
           if (((c.wall >> side) & 1) && gp->bc[side] == 0) {
-            const float4 f = *reinterpret_cast<const float4*>(slot(st, 1 + ax));
-            x[0] = f.x; x[1] = f.y; x[2] = f.z; x[3] = f.w;
+            lds_f4(sb + (1 + ax) * ostr, x);
             return;
           }
         }
-        ld_stage<S>(slot(st, 1 + ax), x);
+        T::lds(sb + (1 + ax) * ostr, x);
       };
 #pragma unroll
       for (int j = 0; j < kStages - 1; ++j) issue(j);
@@ -313,22 +291,20 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         issue(j + kStages - 1);
         cp_async_wait<kStages - 1>();
         const int d = dg + j * dstep;
-        const long long off = (long long)d * nbp;
-        const int st = j % kStages;
-        if (pf > 0 && tl == 0 && d % pf == 0 && d + pf < nd)
-          prefetch_rows<DIM, S>(a, gnx, gny, gnz, In, Ik, P, ci, cj, ck, row, d + pf, min(pf, nd - d - pf));
+        const int off = d * nbp;
+        const unsigned sb = rb0 + (unsigned)(j % kStages) * sstr;
         const int4 di = dsm[d].info;
         A vn[V], ux[V], uy[V], uz[V];
-        ld_stage<S>(slot(st, 0), vn);
-        read_up(st, 0, di, ux);
-        read_up(st, 1, di, uy);
-        if (DIM == 3) read_up(st, 2, di, uz);
+        T::lds(sb, vn);
+        read_up(sb, 0, di, ux);
+        read_up(sb, 1, di, uy);
+        if (DIM == 3) read_up(sb, 2, di, uz);
         A r[V];
         if constexpr (!kDev) {
           A Ax[V], Ay[V], As[V];
-          Tr<double>::ld(reinterpret_cast<const double*>(slot(st, 1 + DIM)), Ax);
-          Tr<double>::ld(reinterpret_cast<const double*>(slot(st, 2 + DIM)), Ay);
-          Tr<double>::ld(reinterpret_cast<const double*>(slot(st, 1 + 2 * DIM)), As);
+          Tr<double>::lds(sb + (1 + DIM) * ostr, Ax);
+          Tr<double>::lds(sb + (2 + DIM) * ostr, Ay);
+          Tr<double>::lds(sb + (1 + 2 * DIM) * ostr, As);
           if constexpr (BM == 2) {
 #pragma unroll
             for (int v = 0; v < V; ++v) r[v] = vn[v];
@@ -346,7 +322,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
           }
           if (DIM == 3) {
             A Az[V];
-            Tr<double>::ld(reinterpret_cast<const double*>(slot(st, 3 + DIM)), Az);
+            Tr<double>::lds(sb + (3 + DIM) * ostr, Az);
 #pragma unroll
             for (int v = 0; v < V; ++v) r[v] = fma(Az[v], uz[v], r[v]);
           }
