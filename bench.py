@@ -369,7 +369,7 @@ def main():
     roofline = {"bound": "alu", "achieved": flops / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": flops / FP64_PEAK_FLOPS,
                 "traffic": (tpu * upd_launch) if tpu else None,
-                "kernel": "sweep_fp64_kernel<2>",
+                "kernel": "sweep_kernel<2, double, MINB, 2> (inner iterations 2..15; iteration 1 is BM=1)",
                 "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
                 "hbm": {"achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"],
                         "peak_source": f"hbm_gbs of {peak_src} peaks"}}

@@ -407,8 +407,8 @@ bool ready_to_step(bte_ctx* h, std::string& why) {
 int ensure_TL(bte_ctx* h) {
   if (h->TL_valid) return BTE_OK;
   // warm start from T_p (or the previous T_L when T_p is not solved)
-  CUDA_TRY(h, launch_solve_TL(h->TL, h->EL, h->solve_tp ? h->Tp : h->TL, h->ncells, thermo(h),
-                              h->opts.newton_rtol, h->opts.newton_maxit, h->counters, h->stream));
+  CUDA_TRY(h, launch_solve_TL(h->TL, h->EL, h->solve_tp ? h->Tp : h->TL, h->J, h->Teval, h->ncells, thermo(h),
+                              std::cbrt(h->opts.newton_rtol / 4.0), h->opts.newton_maxit, h->counters, h->stream));
   h->TL_valid = true;
   return BTE_OK;
 }

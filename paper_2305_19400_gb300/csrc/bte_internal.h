@@ -159,8 +159,9 @@ cudaError_t launch_state_from_Tp(double* I0cell, double* J, const double* Tp, do
 cudaError_t launch_wall_I0(double* I0wall, const double* Tfaces, long long nfaces, ThermoTables th, cudaStream_t s);
 cudaError_t launch_wall_dev(float* out, const double* I0wall, const double* I0ref, long long nfaces, int nbp,
                             cudaStream_t s);
-cudaError_t launch_solve_TL(double* TL, const double* EL, const double* Tguess, long long ncells, ThermoTables th,
-                            double rtol, int maxit, DevCounters* counters, cudaStream_t s);
+cudaError_t launch_solve_TL(double* TL, const double* EL, const double* Tguess, const double* J, const double* Teval,
+                            long long ncells, ThermoTables th, double trust_rel, int maxit, DevCounters* counters,
+                            cudaStream_t s);
 cudaError_t launch_flux_cells(int precision, const void* I, const double* I0ref, double* q, const double* S,
                               long long cell0, int ncells, int nd, int nbp, int dim, cudaStream_t s);
 cudaError_t launch_flux_faces(int precision, const void* I, const double* I0ref, const double* I0wall,

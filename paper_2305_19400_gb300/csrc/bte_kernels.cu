@@ -153,44 +153,53 @@ __global__ void wall_dev_kernel(float* out, const double* I0wall, const double* 
     out[e] = (float)(I0wall[e] - I0ref[e % nbp]);
 }
 
-// Lattice temperature: sum_b a_L,b I0_b(T) = E_L per cell, Newton from the
-// guess with bisection fallback.  One thread per cell (evaluated on request).
-__global__ void solve_TL_kernel(double* TL, const double* EL, const double* Tguess, long long ncells, ThermoTables th,
-                                double rtol, int maxit, DevCounters* counters) {
-  for (long long P = blockIdx.x * (long long)blockDim.x + threadIdx.x; P < ncells;
-       P += (long long)gridDim.x * blockDim.x) {
+// Lattice temperature: sum_b a_L,b I0_b(T) = E_L per cell (evaluated on
+// request).  One warp per cell: the root of the cell's cached quadratic model
+// of I0_b(T) around T_e (the one the T_p solve keeps) when it lies inside the
+// trust radius, else Halley on the exact band quadrature from there (or from
+// the guess), bisection as the fallback.
+__global__ void solve_TL_kernel(double* TL, const double* EL, const double* Tguess, const double* J,
+                                const double* Teval, long long ncells, ThermoTables th, double trust_rel, int maxit,
+                                DevCounters* counters) {
+  const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
+  const int nbp = th.nbp;
+  for (long long P = blockIdx.x * (long long)warps + threadIdx.x / 32; P < ncells; P += (long long)gridDim.x * warps) {
     const double E = EL[P];
-    double T = Tguess[P];
-    bool ok = false;
-    if (isfinite(E) && T >= kTmin && T <= kTmax) {
-      for (int it = 0; it < maxit; ++it) {
-        const double rT = 1.0 / T;
-        double F = -E, dF = 0.0;
-        for (int b = 0; b < th.nb; ++b) {
-          double f, d1, d2;
-          band_I0_d2(th.node_c + b * th.ng, th.node_C + b * th.ng, th.ng, rT, f, d1, d2);
-          F = fma(th.a_L[b], f, F);
-          dF = fma(th.a_L[b], d1, dF);
-        }
-        const double dT = -F / dF;
-        T += dT;
-        if (!(T >= kTmin && T <= kTmax)) break;
-        if (fabs(dT) <= rtol * T) { ok = true; break; }
+    if (!isfinite(E)) {
+      if (lane == 0) {
+        TL[P] = E;
+        if (counters) atomicAdd(&counters->nonfinite, 1ULL);
       }
+      continue;
     }
-    if (!ok && isfinite(E)) {
-      if (counters) atomicAdd(&counters->fallbacks, 1ULL);
-      double lo = kTmin, hi = kTmax;
-      for (int it = 0; it < 200 && hi - lo > 4e-16 * hi; ++it) {
-        const double mid = 0.5 * (lo + hi), rT = 1.0 / mid;
-        double F = -E;
-        for (int b = 0; b < th.nb; ++b) F = fma(th.a_L[b], band_I0(th.node_c + b * th.ng, th.node_C + b * th.ng, th.ng, rT), F);
-        if (F < 0.0) lo = mid; else hi = mid;
-      }
-      T = 0.5 * (lo + hi);
+    double F = 0.0, F1 = 0.0, F2 = 0.0;
+    for (int b = lane; b < nbp; b += 32) {
+      const double w = th.a_L[b];
+      F = fma(w, J[(P * 3 + 0) * nbp + b], F);
+      F1 = fma(w, J[(P * 3 + 1) * nbp + b], F1);
+      F2 = fma(w, J[(P * 3 + 2) * nbp + b], F2);
     }
-    if (!isfinite(E) && counters) atomicAdd(&counters->nonfinite, 1ULL);
-    TL[P] = isfinite(E) ? T : E;
+    for (int o = 16; o > 0; o >>= 1) {
+      F += __shfl_xor_sync(0xffffffffu, F, o);
+      F1 += __shfl_xor_sync(0xffffffffu, F1, o);
+      F2 += __shfl_xor_sync(0xffffffffu, F2, o);
+    }
+    F -= E;
+    const double Te = Teval[P];
+    const double disc = F1 * F1 - 2.0 * F * F2;
+    const double delta = (disc >= 0.0 && F1 > 0.0) ? -2.0 * F / (F1 + sqrt(disc)) : -F / F1;
+    const double Tn = Te + delta;
+    if (isfinite(Tn) && fabs(delta) <= trust_rel * Tn) {
+      if (lane == 0) TL[P] = Tn;
+      continue;
+    }
+    const double start = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : Tguess[P];
+    const SolveResult r = exact_solve_warp(th, E, start, trust_rel, maxit, nullptr, th.a_L);
+    if (lane == 0) {
+      TL[P] = r.Te + r.delta;
+      if (counters && r.fallback) atomicAdd(&counters->fallbacks, 1ULL);
+      if (counters && r.bad) atomicAdd(&counters->nonfinite, 1ULL);
+    }
   }
 }
 
@@ -436,9 +445,11 @@ cudaError_t launch_wall_dev(float* out, const double* I0wall, const double* I0re
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve_TL(double* TL, const double* EL, const double* Tguess, long long ncells, ThermoTables th,
-                            double rtol, int maxit, DevCounters* counters, cudaStream_t s) {
-  solve_TL_kernel<<<grid_for(ncells, 128), 128, 0, s>>>(TL, EL, Tguess, ncells, th, rtol, maxit, counters);
+cudaError_t launch_solve_TL(double* TL, const double* EL, const double* Tguess, const double* J, const double* Teval,
+                            long long ncells, ThermoTables th, double trust_rel, int maxit, DevCounters* counters,
+                            cudaStream_t s) {
+  solve_TL_kernel<<<cell_grid(ncells / 4 + 1), 128, 0, s>>>(TL, EL, Tguess, J, Teval, ncells, th, trust_rel, maxit,
+                                                            counters);
   return cudaGetLastError();
 }
 

@@ -12,14 +12,15 @@ struct SolveResult {
   int bad;       // 1 when no temperature in [1, 5000] K was found
 };
 
-// Solves sum_b a_p,b I0_b(T) = Ep from T0 by Halley steps on the exact band
+// Solves sum_b w_b I0_b(T) = Ep (w = a_p unless given) from T0 by Halley steps on the exact band
 // quadrature (F, F', F'' from one evaluation), bisection on [1, 5000] K as the
 // fallback.  A step delta is accepted when |delta| <= trust_rel * T, where the
 // second-order Taylor model at the evaluation point is accurate to the solve
 // tolerance.  Each evaluation's I0, dI0/dT, d2I0/dT2 per band are written to
 // Jrow ([3][nbp], may be null).  All 32 lanes of the warp must call it.
 __device__ inline SolveResult exact_solve_warp(const ThermoTables& th, double Ep, double T0, double trust_rel, int maxit,
-                                               double* Jrow) {
+                                               double* Jrow, const double* wts = nullptr) {
+  const double* wb = wts ? wts : th.a_p;
   const int lane = threadIdx.x & 31;
   const int nbp = th.nbp, ng = th.ng;
   double T = (T0 >= kTmin && T0 <= kTmax && isfinite(T0)) ? T0 : 300.0;
@@ -38,7 +39,7 @@ __device__ inline SolveResult exact_solve_warp(const ThermoTables& th, double Ep
         Jrow[nbp + b] = d1;
         Jrow[2 * nbp + b] = d2;
       }
-      const double ap = th.a_p[b];
+      const double ap = wb[b];
       F = fma(ap, f, F);
       F1 = fma(ap, d1, F1);
       F2 = fma(ap, d2, F2);
