@@ -1,32 +1,16 @@
-// bte_kernels.cu -- CUDA kernels around the sweep (sm_103a): temperature fix-up,
-// initial state, wall ghosts, T_L, heat flux, state packing.  The sweep itself
-// (described below) lives in bte_sweep.cuh.
-//
-// sweep_kernel<DIM, S>: one launch per inner iteration.  A CTA owns a run of
-//   cells of one geometry; each cell is served by `lpc` lanes, lane l holding
-//   V consecutive bands as one vector (FP64: 2 doubles, FP32: 4 floats, BF16:
-//   4 bf16).  Each lane walks every direction d (Sec. 3.1, Eq. 5):
-//     implicit  I^{k+1} = A_n I^n + A_x I_up,x^k + A_y I_up,y^k (+ A_z I_up,z^k) + A_s I0^k
-//     explicit  same form with forward-Euler coefficients and I^k = I^n
-//   The upwind value is the neighbour cell on the side S_d comes from, or the
-//   Eq. 6 ghost at a wall (I0 of the wall face, or the cell's own value in the
-//   mirrored direction).  The FP32 and BF16 modes store the deviation
-//   I - I0_b(T_ref): the update is affine with coefficients summing to one, so
-//   the deviation obeys the same update with I0 and wall ghosts shifted by
-//   I0_b(T_ref), and rounding acts on the small deviation only.
-//   The lane accumulates G_b = sum_d w_d I^{k+1}_{d,b} in registers (FP64, or a
-//   compensated float pair in the reduced modes), so the reduction needs no
-//   shuffles.  The epilogue reduces the cell's lanes to E_L and E_p and solves
-//   the T_p equation:
-//     * first on the cell's cached quadratic model of I0_b(T) around its last
-//       exact evaluation point T_e (I0, dI0/dT, d2I0/dT2 per band); the model
-//       root is accepted when |T - T_e| <= trust_rel*T, where the Taylor
-//       remainder is below the solve tolerance;
-//     * otherwise by Halley steps on the exact FP64 band quadrature, which also
-//       refresh the cached model; bisection on [1, 5000] K is the fallback.
-//   I0 is refreshed from the accepted model.
-// The HBM stream per update is I^n read, I^{k+1} written and I^k read once
-// (neighbour rows come from L2 while adjacent cells are processed together).
+// bte_kernels.cu -- CUDA kernels around the sweep (sm_103a).  The sweep itself
+// (upwind update, walls, per-cell reduction, cached-model T_p solve, I0
+// refresh; Sec. 3.1, Eq. 4-6) lives in bte_sweep.cuh.  Here:
+//   fixup_kernel        exact FP64 T_p solve (Halley on the band quadrature,
+//                       bisection fallback) for the cells the model left, which
+//                       also refreshes their cached model and I0;
+//   solve_cells_kernel  the T_p step of a band-range handle after the caller's
+//                       all-reduce of the per-cell energy partials (Sec. 3.3);
+//   init_cells / state_from_Tp / wall_I0 / wall_dev
+//                       equilibrium state, cached models and Eq. 6 ghosts;
+//   solve_TL_kernel     T_L on request (cached model first, exact otherwise);
+//   flux_cells / flux_faces / mean / pack / energy_L
+//                       heat flux, FP64 <-> storage packing, E_L after a restore.
 #include "bte_mlp.cuh"
 #include "bte_quad.cuh"
 #include "bte_solve.cuh"
@@ -392,7 +376,7 @@ inline int cell_grid(long long ncells) { return (int)(ncells < 152 * 16 ? (ncell
 
 }  // namespace
 
-int values_per_lane(int precision) { return precision == 0 ? 2 : 4; }
+int values_per_lane(int precision) { return precision == 0 ? 2 : (precision == 1 ? 4 : 8); }
 
 cudaError_t launch_sweep(int precision, int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   if (precision == 0) return launch_sweep_fp64(pd, a, dim, threads, grid, s);

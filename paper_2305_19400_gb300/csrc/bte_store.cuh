@@ -51,39 +51,40 @@ template <> struct Tr<float> {
   }
 };
 
+// BF16: a lane holds 8 bands (one 16-byte vector), so the per-step overhead of
+// the sweep is spread over as many updates as FP32 moves in 32 bytes.
 template <> struct Tr<__nv_bfloat16> {
-  static constexpr int V = 4;
+  static constexpr int V = 8;
   using A = float;
-  static __device__ __forceinline__ void unpack(const uint2 v, A (&x)[V]) {
-    x[0] = __uint_as_float(v.x << 16);
-    x[1] = __uint_as_float(v.x & 0xffff0000u);
-    x[2] = __uint_as_float(v.y << 16);
-    x[3] = __uint_as_float(v.y & 0xffff0000u);
+  static __device__ __forceinline__ void unpack(const uint4 v, A (&x)[V]) {
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      x[2 * i] = __uint_as_float(w[i] << 16);
+      x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+  }
+  static __device__ __forceinline__ unsigned pack2(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);  // round to nearest even
+    return *reinterpret_cast<const unsigned*>(&h);
   }
   static __device__ __forceinline__ void ld(const __nv_bfloat16* p, A (&x)[V]) {
-    unpack(*reinterpret_cast<const uint2*>(p), x);
+    unpack(*reinterpret_cast<const uint4*>(p), x);
   }
   static __device__ __forceinline__ void ld_stream(const __nv_bfloat16* p, A (&x)[V]) {
-    unpack(__ldcs(reinterpret_cast<const uint2*>(p)), x);
+    unpack(__ldcs(reinterpret_cast<const uint4*>(p)), x);
   }
   static __device__ __forceinline__ void st(__nv_bfloat16* p, const A (&x)[V]) {
-    const __nv_bfloat162 h0 = __floats2bfloat162_rn(x[0], x[1]);  // round to nearest even
-    const __nv_bfloat162 h1 = __floats2bfloat162_rn(x[2], x[3]);
-    __stcs(reinterpret_cast<uint2*>(p),
-           make_uint2(*reinterpret_cast<const unsigned*>(&h0), *reinterpret_cast<const unsigned*>(&h1)));
+    __stcs(reinterpret_cast<uint4*>(p),
+           make_uint4(pack2(x[0], x[1]), pack2(x[2], x[3]), pack2(x[4], x[5]), pack2(x[6], x[7])));
   }
   static __device__ __forceinline__ double to_double(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
   static __device__ __forceinline__ void lds(unsigned sa, A (&x)[V]) {
-    uint2 v;
-    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(sa));
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(sa));
     unpack(v, x);
   }
 };
-
-// Four floats from a 32-bit shared-memory address.
-__device__ __forceinline__ void lds_f4(unsigned sa, float (&x)[4]) {
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]) : "r"(sa));
-}
 
 // V consecutive values of type A from global memory (16-byte loads).
 template <typename A, int V>

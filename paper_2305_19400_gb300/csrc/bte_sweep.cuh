@@ -3,7 +3,7 @@
 // sweep_kernel<DIM, S, MINB>: a CTA owns a run of cells of one geometry; each
 // cell is served by a team of lpc x dteam lanes.  Lane (q, l) holds the V
 // consecutive bands V*l.. as one vector (FP64: 2 doubles, FP32: 4 floats,
-// BF16: 4 bf16) and walks the directions d = q, q + dteam, ...; a team step
+// BF16: 8 bf16) and walks the directions d = q, q + dteam, ...; a team step
 // thus covers dteam consecutive directions of the cell's row, ~0.9 KB of
 // contiguous memory per array, which is what keeps HBM streaming at full
 // rate (one 16-byte vector per row per step reaches only ~70 %).  For every
@@ -31,6 +31,8 @@
 // cp.async kStages-1 steps before it uses them.  MINB is the launch-bounds
 // minimum of resident CTAs per SM (a register cap).
 #pragma once
+#include <type_traits>
+
 #include "bte_store.cuh"
 
 namespace bte {
@@ -242,13 +244,19 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       const unsigned rb0 = (unsigned)__cvta_generic_to_shared(ring) + threadIdx.x * 16u;
       const unsigned ostr = blockDim.x * 16u, sstr = kOps * ostr;
       const long long sx = c.sx, sy = c.sy, sz = c.sz;
+      // BF16: the step loop is compiled twice, for interior cells (no wall
+      // logic at all) and for wall cells (per-axis Eq. 6 ghosts; isothermal
+      // ghosts are read at use).  The other modes run one loop with a per-step
+      // interior test (a second copy measured slower there).
+      auto run = [&](auto interior_tag) {
+      constexpr bool kInterior = decltype(interior_tag)::value;
       auto issue = [&](int j) {
         if (j < nsteps) {
           const int d = dg + j * dstep;
           const int off = d * nbp;
           const unsigned sb = rb0 + (unsigned)(j % kStages) * sstr;
           cp_async<kVB>(sb, c.in + off);
-          if (c.wall == 0) {  // interior cell: the upwind rows are the neighbours' (the common case)
+          if (kInterior || c.wall == 0) {  // interior cell: the upwind rows are the neighbours' (the common case)
             const int up = dsm[d].info.x;
             cp_async<kVB>(sb + ostr, c.ik + off + ((up & 1) ? -sx : sx));
             cp_async<kVB>(sb + 2 * ostr, c.ik + off + ((up & 2) ? -sy : sy));
@@ -261,8 +269,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
                                 : (ax == 1 ? upwind_src<1, S>(a, gp, c, di, off, b0) : upwind_src<2, S>(a, gp, c, di, off, b0));
               const bool iso_ghost = (sizeof(S) == 2) && ((c.wall >> (2 * ax + (((di.x >> ax) & 1) ? 0 : 1))) & 1) &&
                                      gp->bc[2 * ax + (((di.x >> ax) & 1) ? 0 : 1)] == 0;
-              if (iso_ghost) cp_async<16>(sb + (1 + ax) * ostr, src_p);  // float4 ghost
-              else cp_async<kVB>(sb + (1 + ax) * ostr, src_p);
+              if (!iso_ghost) cp_async<kVB>(sb + (1 + ax) * ostr, src_p);  // BF16 iso ghosts: read at use
             }
           }
           if constexpr (Ring<DIM, S>::kCoef) {  // A_x, A_y (, A_z), A_s of this direction
@@ -273,14 +280,20 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         }
         cp_async_commit();
       };
-      // Upwind operand of axis ax from its slot (BF16 iso ghosts are float4).
-      auto read_up = [&](unsigned sb, int ax, const int4 di, A (&x)[V]) {
+      // Upwind operand of axis ax from its slot.  A BF16 cell on an isothermal
+      // wall reads that wall's FP32 ghost deviations (8 floats, cached wall data)
+      // straight from memory instead.
+      auto read_up = [&](unsigned sb, int ax, const int4 di, const int off, A (&x)[V]) {
         if constexpr (sizeof(S) == 2) {
-          const bool lowside = (di.x >> ax) & 1;
-          const int side = 2 * ax + (lowside ? 0 : 1);
-          if (((c.wall >> side) & 1) && gp->bc[side] == 0) {
-            lds_f4(sb + (1 + ax) * ostr, x);
-            return;
+          if constexpr (!kInterior) {
+            const bool lowside = (di.x >> ax) & 1;
+            const int side = 2 * ax + (lowside ? 0 : 1);
+            if (((c.wall >> side) & 1) && gp->bc[side] == 0) {
+              const void* g = ax == 0 ? upwind_src<0, S>(a, gp, c, di, off, b0)
+                            : (ax == 1 ? upwind_src<1, S>(a, gp, c, di, off, b0) : upwind_src<2, S>(a, gp, c, di, off, b0));
+              ldgv<float, V>(reinterpret_cast<const float*>(g), x);
+              return;
+            }
           }
         }
         T::lds(sb + (1 + ax) * ostr, x);
@@ -296,9 +309,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         const int4 di = dsm[d].info;
         A vn[V], ux[V], uy[V], uz[V];
         T::lds(sb, vn);
-        read_up(sb, 0, di, ux);
-        read_up(sb, 1, di, uy);
-        if (DIM == 3) read_up(sb, 2, di, uz);
+        read_up(sb, 0, di, off, ux);
+        read_up(sb, 1, di, off, uy);
+        if (DIM == 3) read_up(sb, 2, di, off, uz);
         A r[V];
         if constexpr (!kDev) {
           A Ax[V], Ay[V], As[V];
@@ -393,6 +406,13 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
             nacc = 0;
           }
         }
+      }
+      };
+      if constexpr (sizeof(S) == 2) {
+        if (c.wall == 0) run(std::true_type{});
+        else run(std::false_type{});
+      } else {
+        run(std::false_type{});
       }
       cp_async_wait<0>();
       if constexpr (kDev) {

@@ -253,9 +253,10 @@ def _opts_inplane(n):
 # ------------------------------------------------------------ full size
 @pytest.fixture(scope="module")
 def full_cfg2():
-    """The benchmark's workload and launch configuration: 128x128 x 400 x 55, FP64."""
+    """The benchmark's workload and launch configuration: 128x128 x 400 x 55, FP64,
+    CUDA-graph replay of autotuned launches."""
     wl = W.cfg2()
-    s = bte.Solver(wl)
+    s = bte.Solver(wl, use_graph=True, autotune=True)
     s.step(nsteps=2, ninner=15)
     yield wl, s
     s.close()
@@ -289,6 +290,57 @@ def test_full_size_single_iteration_sampled_against_oracle(full_cfg2):
         Tp_ref, TL_ref = p.cell_temperatures(I_1[P], Tp_n[P], Tp_n[P])
         assert abs(Tp_1[P] - Tp_ref) <= RTOL_T * Tp_ref
         assert abs(TL_1[P] - TL_ref) <= RTOL_T * TL_ref
+    assert worst <= 1e-12, worst
+
+
+def test_full_size_second_inner_iteration_sampled_against_oracle(full_cfg2):
+    """Inner iteration 2 of a step (the form that reads B = A_n I^n and sums the
+    directions in fixed point) at full size: for sampled cells the oracle rebuilds
+    iteration 1 on the cell and its neighbours from I^n, solves the cell's T_p
+    from it, then takes iteration 2 element by element."""
+    wl, s = full_cfg2
+    g = wl.geoms[0]
+    I_n = s.intensity(0)
+    Tp_n = s.T(0, bte.BTE_T_PSEUDO)
+    s.step(nsteps=1, ninner=2)
+    I_2 = s.intensity(0)
+    Tp_2 = s.T(0, bte.BTE_T_PSEUDO)
+    p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands)
+    nc, nd, nb = I_n.shape
+    I0w = p.wall_I0()
+    rng = np.random.default_rng(2)
+    cells = {0, g.nx - 1, nc - 1, (g.ny // 2) * g.nx, (g.ny // 2) * g.nx + g.nx // 2}
+    cells |= set(rng.integers(0, nc, 5).tolist())
+
+    def neighbours(P):
+        i, j = P % g.nx, P // g.nx
+        out = {P}
+        if i > 0: out.add(P - 1)
+        if i < g.nx - 1: out.add(P + 1)
+        if j > 0: out.add(P - g.nx)
+        if j < g.ny - 1: out.add(P + g.nx)
+        return out
+    need = set().union(*(neighbours(P) for P in cells))
+    I0_0 = np.zeros((nc, nb))
+    for Q in need:
+        I0_0[Q] = O.I0(wl.bands, Tp_n[Q])[0]
+    I_1 = np.zeros_like(I_n)
+    for Q in need:  # iteration 1 rows (I^k = I^n)
+        for d in range(nd):
+            for b in range(nb):
+                I_1[Q, d, b] = p.update_one(wl.dt, O.IMPLICIT, I_n, I_n, I0_0, I0w, Q, d, b)
+    I0_1 = np.zeros((nc, nb))
+    worst = 0.0
+    for P in sorted(cells):
+        Tp_1, _ = p.cell_temperatures(I_1[P], Tp_n[P], Tp_n[P])
+        I0_1[P] = O.I0(wl.bands, Tp_1)[0]
+        for d in rng.integers(0, nd, 16):
+            for b in rng.integers(0, nb, 4):
+                ref = p.update_one(wl.dt, O.IMPLICIT, I_n, I_1, I0_1, I0w, P, d, b)
+                worst = max(worst, abs(I_2[P, d, b] - ref) / abs(ref))
+        # T_p after iteration 2 from the GPU's own row 2 (checks the fused reduction and solve)
+        Tp_ref, _ = p.cell_temperatures(I_2[P], Tp_1, Tp_1)
+        assert abs(Tp_2[P] - Tp_ref) <= RTOL_T * Tp_ref
     assert worst <= 1e-12, worst
 
 
