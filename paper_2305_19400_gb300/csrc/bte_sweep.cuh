@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       c.ci = ci; c.cj = cj; c.ck = ck;
       c.wall = (ci == 0) | ((ci == gnx - 1) << 1) | ((cj == 0) << 2) | ((cj == gny - 1) << 3) |
                (DIM == 3 ? ((ck == 0) << 4) | ((ck == gnz - 1) << 5) : 0);
-      float acc[V];  // reduced modes: FP32 partial band sums, flushed to G every 16 steps
+      float acc[V];  // reduced modes: FP32 partial band sums, flushed to G periodically
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[v] = 0.f;
       int nacc = 0;
@@ -392,15 +392,20 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
             const A t = fma(vb[v], f, src[v]);
             r[v] = fma(Qc, t, Pc * vn[v]);
           }
-          T::st(c.out + off, r);
+          if constexpr (sizeof(S) == 2) {
+            // store the rounded values and sum exactly what was stored
+            const uint4 w = make_uint4(T::pack2(r[0], r[1]), T::pack2(r[2], r[3]), T::pack2(r[4], r[5]), T::pack2(r[6], r[7]));
+            __stcs(reinterpret_cast<uint4*>(c.out + off), w);
+            T::unpack(w, r);
+          } else {
+            T::st(c.out + off, r);
+          }
           const float wd = dsm[d].w32;
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            float val = r[v];
-            if constexpr (sizeof(S) == 2) val = __bfloat162float(__float2bfloat16_rn(val));  // the stored value
-            acc[v] = fma(wd, val, acc[v]);
-          }
-          if (++nacc == 16) {
+          for (int v = 0; v < V; ++v) acc[v] = fma(wd, r[v], acc[v]);
+          // FP32 partials go to FP64 every 16 directions (every 64 for BF16 storage,
+          // whose 2^-8 rounding dwarfs the float sum's)
+          if (++nacc == (sizeof(S) == 2 ? 64 : 16)) {
 #pragma unroll
             for (int v = 0; v < V; ++v) { G[v] += (double)acc[v]; acc[v] = 0.f; }
             nacc = 0;
