@@ -203,8 +203,18 @@ def cpu_baseline_for(args):
     O.build()
     wl = W.cfg2(args.nx, args.ny, nsteps=1, ninner=args.ninner)
     u, s = run_oracle_sample(wl)
+    # the paper's own device (the FP64 variant of the same name): 20 of its 100 steps
+    pd = W.paper_hot_spot(nsteps=20)
+    g = pd.geoms[0]
+    p = O.Problem(g, O.dirs_for(pd.dirs), pd.bands)
+    st = p.init_state(g.T_init)
+    t0 = time.perf_counter()
+    p.run(st, pd.dt, pd.nsteps, pd.ninner)
+    sp = time.perf_counter() - t0
     return {"value": u / s, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"full {args.nx}x{args.ny} grid, 1 time step x {args.ninner} inner iterations ({u:.3g} updates, {s:.1f} s)"}
+            "sample": f"full {args.nx}x{args.ny} grid, 1 time step x {args.ninner} inner iterations ({u:.3g} updates, {s:.1f} s)",
+            "paper_device": {"value": pd.dof * pd.nsteps / sp, "unit": UNIT, "ms_per_step": 1e3 * sp / pd.nsteps,
+                             "sample": f"120x120 x 20 x 55, 20 of the 100 steps of 1 ns, one inner iteration each ({sp:.1f} s)"}}
 
 
 def run_variants(peaks):
@@ -212,16 +222,18 @@ def run_variants(peaks):
     workload: FP32 and BF16 storage on the 3-D 64^3 x 400 x 55 workload (15 inner
     iterations per step), FP32 with the learned guess on the 3-D 100x100x50 workload
     (networks trained on the GPU on 1e6 pairs over [250, 400] K before timing; 15 inner
-    iterations) and the 48-geometry FP32 batch (12 inner iterations), all with CUDA
-    graphs and the autotuner.  Device-timed like the main line; bytes per update are the
-    algorithmic 3 x storage size."""
+    iterations), the 48-geometry FP32 batch (12 inner iterations) and the paper's own
+    device in FP64 (120x120 x 20 in-plane directions x 55, 100 steps of 1 ns, one
+    inner iteration each), all with CUDA graphs and the autotuner.  Device-timed like
+    the main line; bytes per update are the algorithmic 3 x storage size."""
     import torch
     from paper_2305_19400_gb300 import bte, workloads as W
     out = []
     cases = [("fp32_3d_64^3", lambda: W.cfg3(64), bte.BTE_FP32, 4, 15, False),
              ("bf16_3d_64^3", lambda: W.cfg3(64, "bf16"), bte.BTE_BF16, 4, 15, False),
              ("fp32_learned_3d_100x100x50", lambda: W.cfg4(), bte.BTE_FP32, 3, 15, True),
-             ("fp32_batch_48_geometries", lambda: W.cfg5(), bte.BTE_FP32, 3, 12, False)]
+             ("fp32_batch_48_geometries", lambda: W.cfg5(), bte.BTE_FP32, 3, 12, False),
+             ("fp64_paper_device_120x120_20dir", lambda: W.paper_hot_spot(), bte.BTE_FP64, 100, 1, False)]
     for name, mk, prec, steps, ninner, learned in cases:
         wl = mk()
         s = bte.Solver(wl, precision=prec, use_graph=True, learned=learned)
@@ -237,20 +249,26 @@ def run_variants(peaks):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(steps):
-            s.step(nsteps=1, ninner=ninner, want_stats=False)
+        s.step(nsteps=steps, ninner=ninner, want_stats=False)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         ups = wl.dof * ninner * steps / (ms * 1e-3)
-        bpu = 12 if prec == bte.BTE_FP32 else 6
+        bpu = {bte.BTE_FP64: 24, bte.BTE_FP32: 12, bte.BTE_BF16: 6}[prec]
         gbs = ups * bpu / 1e9
-        out.append({"workload": name, "dtype": "f32" if prec == bte.BTE_FP32 else "bf16-storage/f32", "value": ups,
-                    "unit": UNIT, "ms_per_step": ms / steps, "inner_iterations_per_step": ninner,
-                    "cells": sum(g.ncells for g in wl.geoms),
-                    "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                 "frac": gbs / peaks["hbm_gbs"], "bytes_per_update": bpu},
-                    "launch": choice, **extra})
+        hbm = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": gbs / peaks["hbm_gbs"], "bytes_per_update": bpu}
+        if prec == bte.BTE_FP64:  # FP64-pipe bound; 9 flop per update without the B reuse (one inner iteration)
+            fl = ups * (FLOPS_PER_UPDATE_2D if ninner == 1 else
+                        (FLOPS_PER_UPDATE_2D + (ninner - 1) * FLOPS_PER_UPDATE_2D_LATER) / ninner)
+            roof = {"bound": "alu", "achieved": fl / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                    "frac": fl / FP64_PEAK_FLOPS, "hbm": hbm}
+        else:
+            roof = hbm
+        dtype = {bte.BTE_FP64: "f64", bte.BTE_FP32: "f32", bte.BTE_BF16: "bf16-storage/f32"}[prec]
+        out.append({"workload": name, "dtype": dtype, "value": ups,
+                    "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "inner_iterations_per_step": ninner,
+                    "cells": sum(g.ncells for g in wl.geoms), "roofline": roof, "launch": choice, **extra})
         if learned:
             st = s.step(nsteps=1, ninner=ninner)[1]
             out[-1]["solves_per_step"] = {k: st[k] for k in ("solves", "solve_evals", "fallbacks")}

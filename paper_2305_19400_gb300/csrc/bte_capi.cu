@@ -226,9 +226,11 @@ size_t carve(bte_ctx* h, char* base) {
 // the z-upwind plane of a block (bx*by cells back) is still in L2 when reused.
 void build_items(bte_ctx* h, int cpb = 0) {
   h->lpc = h->nbp / values_per_lane(h->opts.precision);  // one vector of bands per lane
-  // a cell team covers dteam directions per step: ~896 contiguous bytes of a row
+  // a cell team covers dteam directions per step: ~896 contiguous bytes of a row,
+  // but at least ~32 steps per lane, so the per-cell epilogue stays a small share
+  // when there are few directions
   const int rowb = h->nbp * (int)elem_bytes(h->opts.precision);
-  h->dteam = std::max(1, std::min(896 / rowb, 256 / h->lpc));
+  h->dteam = std::max(1, std::min(std::min(896 / rowb, 256 / h->lpc), h->nd / 32));
   const int team = h->lpc * h->dteam;
   h->cpb = cpb > 0 ? cpb : std::max(1, 256 / team);
   h->threads = h->cpb * team;

@@ -170,6 +170,25 @@ def hot_spot_profile(n: int, T_base: float, dT: float, r_cells: float) -> np.nda
 # The five workloads (sizes, seeds, walls).  Seeds are 19400 + workload number.
 # ---------------------------------------------------------------------------
 
+
+def paper_hot_spot(n: int = 120, nsteps: int = 100, ninner: int = 1) -> "Workload":
+    """The paper's demonstration device (Sec. 3.1-3.2): a 2-D square of side
+    525 um on an n x n grid (n = 120), 20 uniformly spaced in-plane directions,
+    40 frequency bands giving 55 band-pols, initial equilibrium at 300 K.  The
+    -x wall is isothermal with a centred Gaussian hot spot (350 K peak, 1/e^2
+    distance 10 um), the +x wall is the 300 K cold wall, +-y are symmetric.
+    Time step 1 ns (100 steps = 100 ns).  The band table comes from the
+    synthetic generator (seed 19406): the paper gives no dispersion or
+    relaxation-time data."""
+    side = 525e-6
+    d = side / n
+    g = Geometry(2, n, n, 1, d, d, d)
+    g.bc = [(BC_ISOTHERMAL, hot_spot_profile(n, 300.0, 50.0, 10e-6 / d)),
+            (BC_ISOTHERMAL, np.full(n, 300.0)),
+            (BC_SPECULAR, None), (BC_SPECULAR, None)]
+    return Workload(f"paper_2d_{n}x{n}_20dir_55band_fp64", [g], Dirs("inplane", n_inplane=20),
+                    make_bands(40, 15, 19406), 1e-9, nsteps, ninner, "fp64")
+
 def cfg1() -> Workload:
     """2-D 20x20, 10 nm cells, 16 in-plane directions, 4 bands; -x wall 305 K, others 300 K."""
     g = Geometry(2, 20, 20, 1, 10e-9, 10e-9, 10e-9)

@@ -101,6 +101,28 @@ def test_cfg2_shape_reduced_grid_matches_oracle():
     s.close()
 
 
+def test_paper_hot_spot_device_matches_oracle():
+    """The paper's device: 120x120 cells over 525 um, 20 in-plane directions,
+    55 band-pols, 350 K Gaussian hot spot, 1 ns steps with one inner iteration
+    each (graph replay), 6 steps."""
+    wl = W.paper_hot_spot(nsteps=6)
+    s, rc, st = gpu_run(wl, nsteps=6, ninner=1, use_graph=True)
+    assert rc == 0 and st["nonfinite"] == 0
+    p, ost = oracle_run(wl, nsteps=6, ninner=1)
+    TL = s.T(0, bte.BTE_T_LATTICE)
+    assert_close_T(TL, ost["TL"], what="T_L")
+    assert_close_T(s.T(0, bte.BTE_T_PSEUDO), ost["Tp"], what="T_p")
+    assert_close_I(s.intensity(0), ost["I"])
+    q, qw = s.flux(0)
+    q_ref, qw_ref = p.flux(ost["I"])
+    assert_close_flux(p, ost["I"], q, qw, q_ref, qw_ref)
+    g = wl.geoms[0]
+    T2 = TL.reshape(g.ny, g.nx)
+    assert T2[g.ny // 2, 0] > 301.0                         # the hot spot heats the cells next to it
+    assert np.max(np.abs(T2[:, -1] - 300.0)) < T2[g.ny // 2, 0] - 300.0   # more than the cold side
+    s.close()
+
+
 def test_explicit_scheme_matches_oracle():
     wl = W.cfg1()
     T0 = W.random_temperatures(400, 21, 295.0, 305.0)
