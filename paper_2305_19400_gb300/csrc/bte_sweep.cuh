@@ -139,11 +139,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   const int dg = tl / lpc, lane = tl - dg * lpc;      // direction offset in a step, band vector
   DirSm* dsm = reinterpret_cast<DirSm*>(sm);          // [nd]
   double* gsm = sm + (sizeof(DirSm) / 8) * nd;        // [blockDim.x][V] per-lane band partials
-  double* red = gsm + (size_t)V * blockDim.x;         // [cpb * lpc][5]
-  double* cst = red + 5 * (size_t)cpb * lpc;          // [cpb][2] per-cell solve state
+  double* red = gsm + (size_t)V * blockDim.x;         // [cpb * lpc][5] per-band-vector sums
   // staging ring of the far operands: [kStages][kOps][blockDim.x] x 16 bytes
   char* ring = reinterpret_cast<char*>(
-      (reinterpret_cast<uintptr_t>(cst + 2 * (size_t)cpb) + 15) & ~static_cast<uintptr_t>(15));
+      (reinterpret_cast<uintptr_t>(red + 5 * (size_t)cpb * lpc) + 15) & ~static_cast<uintptr_t>(15));
   const S* __restrict__ In = reinterpret_cast<const S*>(a.In);
   const S* __restrict__ Ik = reinterpret_cast<const S*>(a.Ik);
   S* __restrict__ Io = reinterpret_cast<S*>(a.Iout);
@@ -151,6 +150,8 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   const long long row = (long long)nd * nbp;
   const int b0 = V * lane;
   if (threadIdx.x == 0) { cnt_solves = 0; cnt_bad = 0; cur_cls = -1; }
+  const int wid = threadIdx.x >> 5, wl = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;  // full warps (a trailing partial warp takes no cell)
   A vb[V], bb[V];  // per-lane band constants (reduced modes)
 #pragma unroll
   for (int v = 0; v < V; ++v) {
@@ -433,16 +434,22 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
     // ---- per-cell reduction.  The lanes of a cell hold band partials over their
     // direction subsets; the band owners (dg == 0) add them in a fixed order to
     // G_b, then E_L = sum_b G_b / v_b, E_p = sum_b beta_b G_b / v_b and the sums of
-    // the T_p equation's terms on the cached quadratic model around T_e.
+    // the T_p equation's terms on the cached quadratic model around T_e, per band
+    // vector.  Then one warp per cell adds the band vectors (shuffle tree),
+    // solves the model and refreshes all of the cell's I0.  Two barriers per
+    // item: every read of gsm precedes the second, every read of red precedes
+    // the next item's first.
+    double* gb = gsm;
+    double* rb = red;
 #pragma unroll
-    for (int v = 0; v < V; ++v) gsm[(size_t)threadIdx.x * V + v] = G[v];
+    for (int v = 0; v < V; ++v) gb[(size_t)threadIdx.x * V + v] = G[v];
     __syncthreads();
     if (dg == 0) {
       double eL = 0.0, ep = 0.0, F = 0.0, F1 = 0.0, F2 = 0.0;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         double Gb = kDev ? a.Wtot * a.I0ref[b0 + v] : 0.0;
-        for (int q = 0; q < dstep; ++q) Gb += gsm[(size_t)(slot * team + q * lpc + lane) * V + v];
+        for (int q = 0; q < dstep; ++q) Gb += gb[(size_t)(slot * team + q * lpc + lane) * V + v];
         const double e = Gb * a.th.inv_v[b0 + v];
         eL += e;
         ep = fma(a.th.beta[b0 + v], e, ep);
@@ -456,7 +463,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
           F2 = fma(ap, a.J[(P * 3 + 2) * nbp_all + b0 + v], F2);
         }
       }
-      double* r5 = red + 5 * (size_t)(slot * lpc + lane);
+      double* r5 = rb + 5 * (size_t)(slot * lpc + lane);
       r5[0] = eL;
       r5[1] = ep;
       r5[2] = F;
@@ -464,63 +471,63 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       r5[4] = F2;
     }
     __syncthreads();
-    if (tl == 0) {
+    for (int cs = wid; wid < nwarps && cs < wi.cell_count; cs += nwarps) {  // warp per cell
+      const long long Pc = gp->cell0 + wi.cell_begin + cs;
       double EL = 0.0, Ep = 0.0, Fs = 0.0, F1s = 0.0, F2s = 0.0;
-      for (int l = 0; l < lpc; ++l) {
-        const double* r5 = red + 5 * (size_t)(slot * lpc + l);
+      for (int l = wl; l < lpc; l += 32) {
+        const double* r5 = rb + 5 * (size_t)(cs * lpc + l);
         EL += r5[0];
         Ep += r5[1];
         Fs += r5[2];
         F1s += r5[3];
         F2s += r5[4];
       }
-      Fs -= Ep;  // residual of the T_p equation on the model at T_e
-      double* st = cst + 2 * slot;
-      st[0] = 0.0;   // accepted step from T_e
-      st[1] = 0.0;   // 1 when the cached model is accepted
-      if (active && a.partial) {  // band-range handle: partial sums for the caller's all-reduce
-        if (!a.dry) {
-          a.Epart[2 * P] = EL;
-          a.Epart[2 * P + 1] = Ep;
+      for (int o = 16; o > 0; o >>= 1) {
+        EL += __shfl_xor_sync(0xffffffffu, EL, o);
+        Ep += __shfl_xor_sync(0xffffffffu, Ep, o);
+        Fs += __shfl_xor_sync(0xffffffffu, Fs, o);
+        F1s += __shfl_xor_sync(0xffffffffu, F1s, o);
+        F2s += __shfl_xor_sync(0xffffffffu, F2s, o);
+      }
+      const bool lead = wl == 0;  // writes the cell's outputs
+      if (a.partial) {  // band-range handle: partial sums for the caller's all-reduce
+        if (lead && !a.dry) {
+          a.Epart[2 * Pc] = EL;
+          a.Epart[2 * Pc + 1] = Ep;
         }
-      } else if (active) {
-        if (!a.dry) a.EL[P] = EL;
-        if (!isfinite(EL) || !isfinite(Ep)) {
-          atomicAdd(&cnt_bad, 1ULL);
-        } else if (a.solve_tp) {
-          atomicAdd(&cnt_solves, 1ULL);
-          // root of Fs + F1s d + F2s d^2 / 2 nearest 0
-          const double Te = a.Teval[P];
-          const double disc = F1s * F1s - 2.0 * Fs * F2s;
-          const double delta = (disc >= 0.0 && F1s > 0.0) ? -2.0 * Fs / (F1s + sqrt(disc)) : -Fs / F1s;
-          const double Tn = Te + delta;
-          if ((isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn) || a.dry) {
-            st[0] = delta;
-            st[1] = 1.0;
-          } else {  // exact quadrature needed: hand the cell to the fix-up kernel
-            const unsigned k = atomicAdd(a.fix_count, 1u);
-            FixItem fi;
-            fi.P = P;
-            fi.Ep = Ep;
-            fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[P];
-            a.fix[k] = fi;
+        continue;
+      }
+      if (lead && !a.dry) a.EL[Pc] = EL;
+      if (!isfinite(EL) || !isfinite(Ep)) {
+        if (lead) atomicAdd(&cnt_bad, 1ULL);
+        continue;
+      }
+      if (!a.solve_tp) continue;
+      if (lead) atomicAdd(&cnt_solves, 1ULL);
+      // root of (F - E_p) + F1 d + F2 d^2 / 2 nearest 0
+      Fs -= Ep;
+      const double Te = a.Teval[Pc];
+      const double disc = F1s * F1s - 2.0 * Fs * F2s;
+      const double delta = (disc >= 0.0 && F1s > 0.0) ? -2.0 * Fs / (F1s + sqrt(disc)) : -Fs / F1s;
+      const double Tn = Te + delta;
+      if (isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn) {
+        if (!a.dry) {  // I0 refresh of every band of the cell from the model
+          const double hd2 = 0.5 * delta * delta;
+          for (int b = wl; b < nbp; b += 32) {
+            const long long j = (Pc * 3) * nbp_all + band0 + b;
+            a.I0cell[Pc * nbp + b] = b < nbr ? fma(a.J[j + 2 * nbp_all], hd2, fma(a.J[j + nbp_all], delta, a.J[j])) : 0.0;
           }
+          if (lead) a.Tp[Pc] = Tn;
         }
+      } else if (lead && !a.dry) {  // exact quadrature needed: hand the cell to the fix-up kernel
+        const unsigned k = atomicAdd(a.fix_count, 1u);
+        FixItem fi;
+        fi.P = Pc;
+        fi.Ep = Ep;
+        fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[Pc];
+        a.fix[k] = fi;
       }
     }
-    __syncthreads();
-    if (dg == 0 && active && a.solve_tp && !a.dry && cst[2 * slot + 1] != 0.0) {  // I0 refresh from the model
-      const double dlt = cst[2 * slot];
-      const double hd2 = 0.5 * dlt * dlt;
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const long long j = (P * 3) * nbp_all + band0 + b0 + v;
-        a.I0cell[P * nbp + b0 + v] =
-            b0 + v < nbr ? fma(a.J[j + 2 * nbp_all], hd2, fma(a.J[j + nbp_all], dlt, a.J[j])) : 0.0;
-      }
-      if (lane == 0) a.Tp[P] = a.Teval[P] + dlt;
-    }
-    __syncthreads();
   }
   __syncthreads();
   if (threadIdx.x == 0 && a.counters) {
@@ -533,7 +540,7 @@ template <typename S, int MINB, int BM>
 cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   const int team = a.lpc * a.dteam, cpb = threads / team;
   const size_t smem = sizeof(DirSm) * (size_t)a.nd + (size_t)Tr<S>::V * threads * sizeof(double) +
-                      5 * (size_t)cpb * a.lpc * sizeof(double) + 2 * (size_t)cpb * sizeof(double) + 16 +
+                      5 * (size_t)cpb * a.lpc * sizeof(double) + 16 +
                       (size_t)(dim == 3 ? Ring<3, S>::kStages * Ring<3, S>::kOps : Ring<2, S>::kStages * Ring<2, S>::kOps) *
                           threads * 16;
   if (dim == 3) {
