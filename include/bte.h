@@ -65,6 +65,8 @@ typedef struct {
  *             (phi_d = (d+1/2) 2 pi/n, n % 4 == 0; Sec. 3.1 uses 16-20);
  *             BTE_DIRS_POLAR_AZIM: n_polar x n_azim control angles
  *             (n_polar even, n_azim % 4 == 0; 20 x 20 = 400 in Sec. 3.1).
+ *             At most 2048 directions (the sweep keeps the direction table
+ *             in shared memory); more return BTE_E_ARG.
  *  precision  storage of I and the sweep arithmetic: BTE_FP64 (default),
  *             BTE_FP32 or BTE_BF16 (FP32 arithmetic); the reduction, the
  *             temperature solve and I0 are FP64 in every mode.

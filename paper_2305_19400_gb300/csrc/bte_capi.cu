@@ -632,9 +632,9 @@ int bte_init_mesh(bte_handle* out, int n_geom, const bte_geom* geoms, const bte_
     return fail(nullptr, BTE_E_ARG, "bad direction set (in-plane needs n %% 4 == 0; polar x azimuthal needs even n_polar and n_azim %% 4 == 0)");
   }
   h->nd = (int)h->w.size();
-  if (h->nd > 4096) {
+  if (h->nd > 2048) {  // the sweep keeps the direction table in shared memory
     delete h;
-    return fail(nullptr, BTE_E_ARG, "at most 4096 directions");
+    return fail(nullptr, BTE_E_ARG, "at most 2048 directions");
   }
   for (double x : h->w) h->Wtot += x;
   h->geoms.assign(geoms, geoms + n_geom);
