@@ -1,6 +1,6 @@
 // bte_sweep.cuh -- the sweep kernel of one inner iteration (sm_103a).
 //
-// sweep_kernel<DIM, S, MINB>: a CTA owns a run of cells of one geometry; each
+// sweep_kernel<DIM, S, MINB, BM>: a CTA owns a run of cells of one geometry; each
 // cell is served by a team of lpc x dteam lanes.  Lane (q, l) holds the V
 // consecutive bands V*l.. as one vector (FP64: 2 doubles, FP32: 4 floats,
 // BF16: 8 bf16) and walks the directions d = q, q + dteam, ...; a team step
@@ -17,14 +17,16 @@
 // I - I0_b(T_ref): the update is affine with coefficients summing to one, so
 // the deviation obeys the same update with I0 and wall ghosts shifted.
 // Each lane accumulates its part of G_b = sum_d w_d I^{k+1}_{d,b} in registers
-// (FP64, or a compensated float pair); the epilogue adds the dteam partials
-// per band in a fixed order, reduces the bands to E_L and E_p and solves the
-// T_p equation on the
-// cell's cached quadratic model of I0_b(T) (I0, dI0/dT, d2I0/dT2 at its last
-// exact evaluation point T_e).  The model root is accepted inside the trust
-// radius |T - T_e| <= trust_rel T, where the Taylor remainder is below the
-// solve tolerance, and I0 is refreshed from it; other cells go to the fix-up
-// kernel (exact FP64 band quadrature).
+// (FP64: exact fixed-point sums per run of equal-weight directions; reduced
+// modes: float partials flushed to FP64).  The epilogue of an item: the band
+// owners add the dteam partials per band in a fixed order and reduce their
+// bands to E_L, E_p and the model sums; then one warp per cell adds those with
+// a shuffle tree and solves the T_p equation on the cell's cached quadratic
+// model of I0_b(T) (I0, dI0/dT, d2I0/dT2 at its last exact evaluation point
+// T_e).  The model root is accepted inside the trust radius
+// |T - T_e| <= trust_rel T, where the Taylor remainder is below the solve
+// tolerance, and the warp refreshes the cell's I0 from it; other cells go to
+// the fix-up kernel (exact FP64 band quadrature).  Two CTA barriers per item.
 // Memory: I^n is read once, I^{k+1} written once, and each I^k row read from
 // DRAM once (adjacent cells, processed together, re-read it from L2).  Each
 // thread copies the operands of its next directions into shared memory with
