@@ -178,7 +178,17 @@ typedef struct {
   const double* bc_T[6]; /* per face temperatures on isothermal sides */
   int newton_maxit;
   double newton_rtol;
+  /* Temperature-dependent relaxation (Sec. 2.2: tau depends on T; the paper
+     gives no law): beta_b(T) = beta_b (T / beta_Tref)^beta_exp with T the
+     cell's T_p, one exponent for all bands; beta_exp = 0 keeps tau fixed. */
+  double beta_exp;
+  double beta_Tref;
 } orc_problem;
+
+/* beta_b(T) / beta_b for a cell at temperature T. */
+static double beta_scale(const orc_problem* p, double T) {
+  return p->beta_exp == 0.0 ? 1.0 : pow(T / p->beta_Tref, p->beta_exp);
+}
 
 static long ncells(const orc_problem* p) { return (long)p->nx * p->ny * p->nz; }
 
@@ -244,18 +254,19 @@ static double upwind_value(const orc_problem* p, const double* Isrc, const doubl
   return Isrc[P * nd * nb + (long)r[d] * nb + b];
 }
 
-/* One intensity update for (P, d, b).
+/* One intensity update for (P, d, b), with beta = beta_b * bscale (bscale is
+ * beta_b(T_p)/beta_b of the cell, 1 when tau does not depend on T).
  * Implicit (backward Euler, one point-Jacobi sweep of the inner iteration):
  *   I^{k+1} = [I^n/dt + beta I0^k + v sum_ax c_ax I_up^k] / [1/dt + beta + v sum_ax c_ax],
  *   c_ax = |S_{d,ax}| / (w_d Delta_ax)  (outflow faces use the cell's own value).
  * Explicit (forward Euler, Eq. 3 with Eq. 5):
  *   I^{n+1} = I^n + dt [ beta (I0^n - I^n) - v sum_ax c_ax (I^n - I_up^n) ]. */
 double orc_update_one(const orc_problem* p, double dt, int scheme, const double* In, const double* Ik, const double* I0,
-                      const double* I0wall, long P, int d, int b) {
+                      const double* I0wall, long P, int d, int b, double bscale) {
   int nd = p->nd, nb = p->nb;
   int i = (int)(P % p->nx), j = (int)((P / p->nx) % p->ny), k = (int)(P / ((long)p->nx * p->ny));
   double delta[3] = {p->dx, p->dy, p->dz};
-  double beta = p->beta[b], v = p->vg[b];
+  double beta = p->beta[b] * bscale, v = p->vg[b];
   double in = In[P * nd * nb + (long)d * nb + b];
   double i0 = I0[P * nb + b];
   if (scheme == ORC_EXPLICIT) {
@@ -345,6 +356,9 @@ static double total_weight(const orc_problem* p) {
 }
 
 /* Temperatures of one cell from its energies E_L, E_p (sums over every band).
+ * With beta_b(T) = beta_b s(T) (one factor for all bands) the T_p balance
+ * sum_b W beta_b(T) I0_b(T)/v_b = sum_b beta_b(T) G_b/v_b at T = T_p carries
+ * s(T_p) > 0 on both sides, so it is solved with the reference beta_b.
  * With every beta_b = 0 the T_p equation is empty (I0 never enters the
  * update); T_p is then set to T_L. */
 int orc_temperatures_from_energy(const orc_problem* p, double EL, double Ep, double TpGuess, double TLGuess,
@@ -413,10 +427,12 @@ long orc_run(const orc_problem* p, double dt, int nsteps, int ninner, int scheme
     for (int k = 0; k < ninner; ++k) {
       const double* Ik = (scheme == ORC_EXPLICIT) ? In : I;
 #pragma omp parallel for schedule(static)
-      for (long P = 0; P < nc; ++P)
+      for (long P = 0; P < nc; ++P) {
+        const double bs = beta_scale(p, Tp[P]);
         for (int d = 0; d < nd; ++d)
           for (int b = 0; b < nb; ++b)
-            Inew[P * nd * nb + (long)d * nb + b] = orc_update_one(p, dt, scheme, In, Ik, I0, I0wall, P, d, b);
+            Inew[P * nd * nb + (long)d * nb + b] = orc_update_one(p, dt, scheme, In, Ik, I0, I0wall, P, d, b, bs);
+      }
 #pragma omp parallel for schedule(static) reduction(+ : fallbacks, bad)
       for (long P = 0; P < nc; ++P) {
         int s = orc_cell_temperatures(p, Inew + P * nd * nb, Tp[P], TL[P], &Tp[P], &TL[P]);
@@ -461,10 +477,12 @@ long orc_run_bands(const orc_problem* p, int b0, int b1, double dt, int nsteps, 
       const double* Ik = (scheme == ORC_EXPLICIT) ? In : I;
       memcpy(Inew, I, n * sizeof(double));
 #pragma omp parallel for schedule(static)
-      for (long P = 0; P < nc; ++P)
+      for (long P = 0; P < nc; ++P) {
+        const double bs = beta_scale(p, Tp[P]);
         for (int d = 0; d < nd; ++d)
           for (int b = b0; b < b1; ++b)
-            Inew[P * nd * nb + (long)d * nb + b] = orc_update_one(p, dt, scheme, In, Ik, I0, I0wall, P, d, b);
+            Inew[P * nd * nb + (long)d * nb + b] = orc_update_one(p, dt, scheme, In, Ik, I0, I0wall, P, d, b, bs);
+      }
 #pragma omp parallel for schedule(static)
       for (long P = 0; P < nc; ++P) {  /* partial reduction over the owned bands */
         double eL = 0.0, ep = 0.0;

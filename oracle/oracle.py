@@ -54,6 +54,7 @@ class _Problem(C.Structure):
         ("bc_T", C.POINTER(C.c_double) * 6),
         ("newton_maxit", C.c_int),
         ("newton_rtol", C.c_double),
+        ("beta_exp", C.c_double), ("beta_Tref", C.c_double),
     ]
 
 
@@ -70,7 +71,7 @@ def lib():
             L.orc_dirs_inplane.argtypes = [C.c_int, dp, dp, ip, ip, ip]
             L.orc_dirs_polar_azim.argtypes = [C.c_int, C.c_int, dp, dp, ip, ip, ip]
             P = C.POINTER(_Problem)
-            L.orc_update_one.argtypes = [P, C.c_double, C.c_int, dp, dp, dp, dp, C.c_long, C.c_int, C.c_int]
+            L.orc_update_one.argtypes = [P, C.c_double, C.c_int, dp, dp, dp, dp, C.c_long, C.c_int, C.c_int, C.c_double]
             L.orc_update_one.restype = C.c_double
             L.orc_solve_T.argtypes = [P, dp, C.c_double, C.c_double, dp]
             L.orc_cell_energy.argtypes = [P, dp, dp, dp]
@@ -156,7 +157,9 @@ class Problem:
     so tests may permute or hand-build direction sets.
     """
 
-    def __init__(self, geom, dirs, bands, ngauss: int = 16, newton_rtol: float = 1e-14, newton_maxit: int = 50):
+    def __init__(self, geom, dirs, bands, ngauss: int = 16, newton_rtol: float = 1e-14, newton_maxit: int = 50,
+                 beta_exp: float = 0.0, beta_Tref: float = 300.0):
+        """beta_exp != 0: beta_b(T) = beta_b (T_p / beta_Tref)^beta_exp per cell."""
         self.geom = geom
         S, w, r = dirs
         self.S = np.ascontiguousarray(S, dtype=np.float64)
@@ -189,6 +192,8 @@ class Problem:
                 p.bc_T[s] = C.POINTER(C.c_double)()
         p.newton_maxit = newton_maxit
         p.newton_rtol = newton_rtol
+        p.beta_exp = float(beta_exp)
+        p.beta_Tref = float(beta_Tref)
         self._p = p
         self.nc = geom.nx * geom.ny * geom.nz
 
@@ -243,9 +248,10 @@ class Problem:
         lib().orc_wall_I0(self.ptr, _dp(out))
         return out
 
-    def update_one(self, dt, scheme, In, Ik, I0cells, I0wall, P, d, b) -> float:
+    def update_one(self, dt, scheme, In, Ik, I0cells, I0wall, P, d, b, bscale=1.0) -> float:
+        """bscale: beta_b(T_p)/beta_b of cell P (1 when tau does not depend on T)."""
         return float(lib().orc_update_one(self.ptr, float(dt), int(scheme), _dp(In), _dp(Ik), _dp(I0cells),
-                                          _dp(I0wall), int(P), int(d), int(b)))
+                                          _dp(I0wall), int(P), int(d), int(b), float(bscale)))
 
     def cell_energy(self, row):
         row = np.ascontiguousarray(row, dtype=np.float64)

@@ -383,3 +383,47 @@ def test_mirrored_geometry_gives_mirrored_temperature():
         T = st["TL"].reshape(ny, nx)
         res.append(T[:, ::-1] if mirror else T)
     assert np.max(np.abs(res[0] - res[1])) <= 1e-12 * 300
+
+
+def test_temperature_dependent_relaxation_rate_is_measured_from_one_step():
+    """beta_b(T) = beta_b (T_p / T_ref)^p (Sec. 2.2, tau depends on T): one
+    explicit step of a single mirror-walled cell with an isotropic perturbation
+    is pure relaxation, so each band's measured rate (I1 - I)/(dt (I0 - I))
+    must equal beta_b (T_p/T_ref)^p at the cell's T_p (not at T_L, which
+    differs here)."""
+    g = W.Geometry(2, 1, 1, 1, 10e-9, 10e-9, 10e-9)
+    W.uniform_walls(g, [W.BC_SPECULAR] * 4, [0.0] * 4)
+    bands = W.make_bands(4, 1, 47)
+    dirs = O.dirs_for(W.Dirs("inplane", n_inplane=8))
+    p_exp, Tref, dt = 2.0, 300.0, 1e-13   # dt beta ~ 3e-4: stable, and I1 - I well above round-off
+    prob = O.Problem(g, dirs, bands, beta_exp=p_exp, beta_Tref=Tref)
+    st = prob.init_state(320.0)
+    st["I"][0, :, 0] *= 1.01            # band 0 above its equilibrium, the same in every direction
+    st["I"][0, :, 2] *= 0.995
+    Tp, TL = prob.cell_temperatures(st["I"][0], 320.0, 320.0)
+    assert abs(Tp - TL) > 1e-3            # the two temperatures differ, so the law's argument is checked
+    st["Tp"][0], st["TL"][0] = Tp, TL
+    st["I0"][0] = O.I0(bands, Tp)[0]
+    I_before = st["I"].copy()
+    prob.run(st, dt, 1, 1, O.EXPLICIT)
+    for b in range(bands.nb):
+        dI = st["I"][0, 3, b] - I_before[0, 3, b]
+        drive = O.I0(bands, Tp)[0][b] - I_before[0, 3, b]
+        if abs(drive) < 1e-12 * I_before[0, 3, b]:
+            continue                        # bands at equilibrium do not move
+        rate = dI / (dt * drive)
+        assert abs(rate / (bands.beta[b] * (Tp / Tref) ** p_exp) - 1.0) <= 1e-10, b
+
+
+def test_temperature_dependent_relaxation_conserves_energy():
+    """Relaxation with beta_b(T_p) still conserves energy in a mirror box (the
+    law's factor is common to all bands, so the T_p balance holds)."""
+    g = W.Geometry(2, 5, 4, 1, 10e-9, 10e-9, 10e-9)
+    W.uniform_walls(g, [W.BC_SPECULAR] * 4, [0.0] * 4)
+    bands = W.make_bands(6, 2, 48)
+    prob = O.Problem(g, O.dirs_for(W.Dirs("inplane", n_inplane=8)), bands, beta_exp=1.5, beta_Tref=300.0)
+    st = prob.init_state(W.random_temperatures(20, 11, 280.0, 330.0))
+    E0 = sum(prob.cell_energy(r)[0] for r in st["I"])
+    prob.run(st, 2e-13, 50, 1, O.EXPLICIT)
+    E1 = sum(prob.cell_energy(r)[0] for r in st["I"])
+    assert abs(E1 - E0) <= 1e-13 * E0
