@@ -80,11 +80,17 @@ typedef struct {
  *  newton_maxit iteration cap before the bisection fallback (50).
  *  cuda_stream cudaStream_t every launch and copy uses (NULL: legacy default stream).
  *  T_ref      reference temperature of the FP32/BF16 modes, which store the
- *             deviation I - I0_b(T_ref) (default 300 K; ignored in FP64).
+ *             deviation I - I0_b(T_ref), and of beta_T_exp (default 300 K).
  *  use_graph  1: each time step's ninner sweep launches are captured once in a
  *             CUDA graph (per scheme, ninner and buffer rotation) and replayed
  *             on cuda_stream; 0 (default): launched one by one.
- *  autotune   1: the first bte_step runs bte_autotune (default 0). */
+ *  autotune   1: the first bte_step runs bte_autotune (default 0).
+ *  beta_T_exp temperature dependence of the relaxation rates (Sec. 2.2: tau
+ *             depends on T; the paper gives no law): beta_b(T) = beta_b
+ *             (T_p / T_ref)^beta_T_exp per cell, T_p the cell's current
+ *             pseudo-temperature, beta_b the table value (at T_ref).  0
+ *             (default) keeps tau fixed; |beta_T_exp| <= 16.  The factor is
+ *             common to all bands, so the T_p equation keeps its root. */
 typedef struct {
   int dir_kind;
   int n_inplane, n_polar, n_azim;
@@ -97,6 +103,7 @@ typedef struct {
   double T_ref;
   int use_graph;
   int autotune;
+  double beta_T_exp;
 } bte_opts;
 
 /* Per-call statistics of bte_step (filled only when a non-NULL pointer is

@@ -34,7 +34,7 @@ class bte_opts(C.Structure):
     _fields_ = [("dir_kind", C.c_int), ("n_inplane", C.c_int), ("n_polar", C.c_int), ("n_azim", C.c_int),
                 ("precision", C.c_int), ("learned", C.c_int), ("n_gauss", C.c_int), ("newton_rtol", C.c_double),
                 ("newton_maxit", C.c_int), ("cuda_stream", C.c_void_p), ("T_ref", C.c_double),
-                ("use_graph", C.c_int), ("autotune", C.c_int)]
+                ("use_graph", C.c_int), ("autotune", C.c_int), ("beta_T_exp", C.c_double)]
 
 
 class bte_stats(C.Structure):
@@ -305,7 +305,8 @@ class Solver:
     """
 
     def __init__(self, workload, precision=BTE_FP64, stream=None, bind_workspace=True, n_gauss=16, T_init=None,
-                 use_graph=False, autotune=False, learned=False, band_range=None, exchange=None):
+                 use_graph=False, autotune=False, learned=False, band_range=None, exchange=None, beta_exp=0.0,
+                 T_ref=None):
         """band_range=(lo, hi) stores and sweeps only bands [lo, hi); exchange(buf)
         then sums the float64 CUDA tensor buf of per-cell (E_L, E_p) partials
         over the ranks in place (e.g. allreduce_exchange()); it runs with this
@@ -325,6 +326,9 @@ class Solver:
         o.use_graph = 1 if use_graph else 0
         o.learned = 1 if learned else 0
         o.autotune = 1 if autotune else 0
+        o.beta_T_exp = float(beta_exp)
+        if T_ref is not None:
+            o.T_ref = float(T_ref)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         o.cuda_stream = self.stream.cuda_stream
         geoms = [bte_geom(g.dim, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz) for g in workload.geoms]

@@ -469,6 +469,8 @@ SweepArgs sweep_args(bte_ctx* h) {
   a.counters = h->counters;
   a.dry = 0;
   a.explicit_scheme = h->coef_scheme == BTE_EXPLICIT ? 1 : 0;
+  a.beta_exp = h->opts.beta_T_exp;
+  a.beta_Tref = h->opts.T_ref;
   a.dt32 = (float)h->coef_dt;
   a.rdt32 = (float)(1.0 / h->coef_dt);
   a.dirc = h->dirc;
@@ -592,6 +594,7 @@ int bte_default_opts(bte_opts* o) {
   o->T_ref = 300.0;
   o->use_graph = 0;
   o->autotune = 0;
+  o->beta_T_exp = 0.0;
   return BTE_OK;
 }
 
@@ -604,6 +607,7 @@ int bte_init_mesh(bte_handle* out, int n_geom, const bte_geom* geoms, const bte_
   if (o.precision != BTE_FP64 && o.precision != BTE_FP32 && o.precision != BTE_BF16)
     return fail(nullptr, BTE_E_ARG, "unknown precision %d", o.precision);
   if (!(o.T_ref >= kTmin && o.T_ref <= kTmax)) return fail(nullptr, BTE_E_ARG, "T_ref must lie in [1, 5000] K");
+  if (!(std::fabs(o.beta_T_exp) <= 16.0)) return fail(nullptr, BTE_E_ARG, "beta_T_exp must lie in [-16, 16]");
   if (o.learned != 0 && o.learned != 1) return fail(nullptr, BTE_E_ARG, "learned must be 0 or 1");
   if (o.n_gauss < 1 || o.n_gauss > kMaxGauss) return fail(nullptr, BTE_E_ARG, "n_gauss must be in 1..%d", kMaxGauss);
   if (!(o.newton_rtol > 0 && o.newton_rtol < 1e-3) || o.newton_maxit < 1)

@@ -124,6 +124,8 @@ struct SweepArgs {
   int dry;                  // 1: timing run, the epilogue writes no solver state
   int partial;              // 1: band-range handle; the epilogue writes per-cell partial (E_L, E_p)
   double* Epart;            //    to Epart[cell][2] and the solve runs after the caller's all-reduce
+  double beta_exp;          // beta_b(T) = beta_b (T_p / beta_Tref)^beta_exp per cell (0: fixed tau)
+  double beta_Tref;
   int explicit_scheme;      // reduced modes compute P, Q on the fly from these:
   float dt32, rdt32;        // dt and 1/dt
   DevCounters* counters;

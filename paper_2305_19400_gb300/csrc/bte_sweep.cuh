@@ -124,7 +124,9 @@ struct Ring {
 // BM (FP64 implicit only): 0 plain; 1 also stores B = A_n I^n; 2 the In operand
 // holds B, so the update is B + A_x I_x + A_y I_y (+ A_z I_z) + A_s I0 (bitwise
 // the same value, one FP64 multiply fewer per update).
-template <int DIM, typename S, int MINB, int BM>
+// TT (FP64 only): the relaxation rates depend on T (beta_exp != 0); the
+// reduced modes scale beta per cell outside the step loop and need no variant.
+template <int DIM, typename S, int MINB, int BM, bool TT>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   using T = Tr<S>;
   using A = typename T::A;
@@ -191,7 +193,17 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
     for (int v = 0; v < V; ++v) G[v] = 0.0;
 
     if (active) {
-      A src[V];  // FP64: I0 of the cell; reduced: beta_b * (I0 - I0ref)
+      // temperature-dependent relaxation: beta_b(T_p) = beta_b s with
+      // s = (T_p / T_ref)^p of this cell (s = 1 when tau does not depend on T)
+      const bool tT = kDev ? a.beta_exp != 0.0 : TT;
+      const double bsc = tT ? pow(a.Tp[P] / a.beta_Tref, a.beta_exp) : 1.0;
+      if constexpr (kDev) {
+        if (tT) {
+#pragma unroll
+          for (int v = 0; v < V; ++v) bb[v] = a.bb32[b0 + v] * (float)bsc;
+        }
+      }
+      A src[V];  // FP64: I0 of the cell; reduced: beta_b(T_p) * (I0 - I0ref)
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const double i0 = a.I0cell[P * nbp + b0 + v];
@@ -342,8 +354,17 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
 #pragma unroll
             for (int v = 0; v < V; ++v) r[v] = fma(Az[v], uz[v], r[v]);
           }
+          if constexpr (!TT) {
 #pragma unroll
-          for (int v = 0; v < V; ++v) r[v] = fma(As[v], src[v], r[v]);
+            for (int v = 0; v < V; ++v) r[v] = fma(As[v], src[v], r[v]);
+          } else if (a.explicit_scheme) {  // A_n -> A_n + (1 - s) A_s, A_s -> s A_s
+#pragma unroll
+            for (int v = 0; v < V; ++v) r[v] = fma((1.0 - bsc) * As[v], vn[v], fma(bsc * As[v], src[v], r[v]));
+          } else {  // every coefficient x 1/(1 + (s - 1) A_s), A_s also x s
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+              r[v] = fma(bsc * As[v], src[v], r[v]) * __drcp_rn(fma(bsc - 1.0, As[v], 1.0));
+          }
           T::st(c.out + off, r);
           const double wd = dsm[d].w;
           const long long wb = __double_as_longlong(wd);
@@ -538,7 +559,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   }
 }
 
-template <typename S, int MINB, int BM>
+template <typename S, int MINB, int BM, bool TT>
 cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   const int team = a.lpc * a.dteam, cpb = threads / team;
   const size_t smem = sizeof(DirSm) * (size_t)a.nd + (size_t)Tr<S>::V * threads * sizeof(double) +
@@ -547,32 +568,37 @@ cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cuda
                           threads * 16;
   if (dim == 3) {
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(sweep_kernel<3, S, MINB, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sweep_kernel<3, S, MINB, BM><<<grid, threads, smem, s>>>(a);
+      cudaFuncSetAttribute(sweep_kernel<3, S, MINB, BM, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sweep_kernel<3, S, MINB, BM, TT><<<grid, threads, smem, s>>>(a);
   } else {
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(sweep_kernel<2, S, MINB, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sweep_kernel<2, S, MINB, BM><<<grid, threads, smem, s>>>(a);
+      cudaFuncSetAttribute(sweep_kernel<2, S, MINB, BM, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sweep_kernel<2, S, MINB, BM, TT><<<grid, threads, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
 
 // variant: 1 -> at least 2 resident CTAs per SM (<= 128 registers), 2 -> 3 CTAs (<= 80 registers)
-template <typename S, int BM>
+template <typename S, int BM, bool TT>
 cudaError_t launch_bm(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
-  if (variant >= 2) return launch_minb<S, 3, BM>(a, dim, threads, grid, s);
-  return launch_minb<S, 2, BM>(a, dim, threads, grid, s);
+  if (variant >= 2) return launch_minb<S, 3, BM, TT>(a, dim, threads, grid, s);
+  return launch_minb<S, 2, BM, TT>(a, dim, threads, grid, s);
 }
 
 template <typename S>
 cudaError_t launch(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   if constexpr (sizeof(S) == 8) {
-    if (a.bmode == 1) return launch_bm<S, 1>(variant, a, dim, threads, grid, s);
-    if (a.bmode == 2) return launch_bm<S, 2>(variant, a, dim, threads, grid, s);
+    if (a.beta_exp != 0.0) {
+      if (a.bmode == 1) return launch_bm<S, 1, true>(variant, a, dim, threads, grid, s);
+      if (a.bmode == 2) return launch_bm<S, 2, true>(variant, a, dim, threads, grid, s);
+      return launch_bm<S, 0, true>(variant, a, dim, threads, grid, s);
+    }
+    if (a.bmode == 1) return launch_bm<S, 1, false>(variant, a, dim, threads, grid, s);
+    if (a.bmode == 2) return launch_bm<S, 2, false>(variant, a, dim, threads, grid, s);
   } else {
     if (a.bmode != 0) return cudaErrorInvalidValue;  // the B form exists for FP64 storage only
   }
-  return launch_bm<S, 0>(variant, a, dim, threads, grid, s);
+  return launch_bm<S, 0, false>(variant, a, dim, threads, grid, s);
 }
 
 }  // namespace sweep

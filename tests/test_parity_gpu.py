@@ -379,3 +379,37 @@ def test_full_size_equilibrium_is_preserved():
     I0 = O.I0(wl.bands, 300.0)[0]
     assert np.max(np.abs(q)) <= 1e-12 * 4 * math.pi * I0.sum()
     s.close()
+
+
+# ------------------------------------------------- temperature-dependent tau
+@pytest.mark.parametrize("precision,scheme,p_exp", [(bte.BTE_FP64, bte.BTE_IMPLICIT_JACOBI, 1.0),
+                                                    (bte.BTE_FP64, bte.BTE_EXPLICIT, -0.7),
+                                                    (bte.BTE_FP32, bte.BTE_IMPLICIT_JACOBI, 1.5)])
+def test_temperature_dependent_relaxation_matches_oracle(precision, scheme, p_exp):
+    """beta_b(T) = beta_b (T_p / 300 K)^p per cell (Sec. 2.2), hot-spot wall,
+    400 directions x 55 band-pols on a ragged grid; FP64 to rel 1e-12 on T,
+    FP32 to 1e-4 K."""
+    wl = W.cfg2(13, 9)
+    explicit = scheme == bte.BTE_EXPLICIT
+    nsteps, ninner, dt = (30, 1, 2e-13) if explicit else (4, 10, wl.dt)
+    g = wl.geoms[0]
+    T0 = W.random_temperatures(g.ncells, 17, 320.0, 340.0)   # away from T_ref: the rates differ by ~10 %
+    s = bte.Solver(wl, precision=precision, beta_exp=p_exp, T_ref=300.0, T_init=[T0])
+    rc, st = s.step(nsteps=nsteps, ninner=ninner, dt=dt, scheme=scheme)
+    assert rc >= 0 and st["nonfinite"] == 0
+    p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands, beta_exp=p_exp, beta_Tref=300.0)
+    ost = p.init_state(T0)
+    p.run(ost, dt, nsteps, ninner, O.EXPLICIT if explicit else O.IMPLICIT)
+    TL, Tp = s.T(0, bte.BTE_T_LATTICE), s.T(0, bte.BTE_T_PSEUDO)
+    if precision == bte.BTE_FP64:
+        assert_close_T(TL, ost["TL"], what="T_L")
+        assert_close_T(Tp, ost["Tp"], what="T_p")
+        assert_close_I(s.intensity(0), ost["I"])
+    else:
+        assert np.max(np.abs(TL - ost["TL"])) <= 1e-4 and np.max(np.abs(Tp - ost["Tp"])) <= 1e-4
+    # the law changes the answer: a fixed-tau run differs by far more than the tolerance
+    q = O.Problem(g, O.dirs_for(wl.dirs), wl.bands)
+    fixed = q.init_state(T0)
+    q.run(fixed, dt, nsteps, ninner, O.EXPLICIT if explicit else O.IMPLICIT)
+    assert np.max(np.abs(fixed["TL"] - ost["TL"])) > 1e-3
+    s.close()
