@@ -122,7 +122,8 @@ typedef struct {
 int bte_default_opts(bte_opts* opts);
 
 /* Creates a solver for n_geom >= 1 independent geometries sharing one
- * direction set and band table (Sec. 3.1 discretisation).  geoms: host array
+ * direction set and band table (Sec. 3.1 discretisation); all of them 2-D or
+ * all 3-D (a mixture returns BTE_E_ARG).  geoms: host array
  * of n_geom.  opts: host, may be NULL for defaults.  *out receives the handle
  * (NULL on failure).  No device memory is allocated yet. */
 int bte_init_mesh(bte_handle* out, int n_geom, const bte_geom* geoms, const bte_opts* opts);

@@ -617,6 +617,8 @@ int bte_init_mesh(bte_handle* out, int n_geom, const bte_geom* geoms, const bte_
     const bte_geom& g = geoms[i];
     if (!(g.dim == 2 || g.dim == 3) || g.nx < 1 || g.ny < 1 || g.nz < 1 || (g.dim == 2 && g.nz != 1))
       return fail(nullptr, BTE_E_ARG, "geometry %d: bad dim/size", i);
+    if (g.dim != geoms[0].dim)  // one sweep launch serves every geometry of a handle
+      return fail(nullptr, BTE_E_ARG, "geometry %d: every geometry of a handle must have the same dim", i);
     if (!(g.dx > 0 && g.dy > 0 && (g.dim == 2 || g.dz > 0))) return fail(nullptr, BTE_E_ARG, "geometry %d: cell sizes must be > 0", i);
     const long long nc = (long long)g.nx * g.ny * g.nz;
     if (nc > (1LL << 30)) return fail(nullptr, BTE_E_ARG, "geometry %d: too many cells", i);

@@ -52,10 +52,20 @@ def test_init_mesh_rejects_bad_geometry(lib, geom):
     assert e.value.code == -1
 
 
+def test_init_mesh_rejects_mixed_dimensions(lib):
+    from paper_2305_19400_gb300 import bte
+    g2 = bte.bte_geom(2, 4, 4, 1, 1e-8, 1e-8, 1e-8)
+    g3 = bte.bte_geom(3, 4, 4, 4, 1e-8, 1e-8, 1e-8)
+    with pytest.raises(bte.BTEError) as e:
+        bte.bte_init_mesh([g2, g3])
+    assert e.value.code == -1 and "same dim" in str(e.value)
+
+
 def test_init_mesh_rejects_bad_direction_sets_and_options(lib):
     from paper_2305_19400_gb300 import bte
     g = bte.bte_geom(2, 4, 4, 1, 1e-8, 1e-8, 1e-8)
-    for field, val in (("n_gauss", 0), ("n_gauss", 99), ("newton_rtol", 0.0), ("newton_maxit", 0)):
+    for field, val in (("n_gauss", 0), ("n_gauss", 99), ("newton_rtol", 0.0), ("newton_maxit", 0),
+                       ("beta_T_exp", 17.0), ("beta_T_exp", float("nan")), ("T_ref", 0.5)):
         o = bte.bte_default_opts()
         setattr(o, field, val)
         with pytest.raises(bte.BTEError):
