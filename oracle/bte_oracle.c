@@ -39,7 +39,7 @@ static const double ORC_HBAR = 1.054571817e-34; /* J s */
 static const double ORC_KB = 1.380649e-23;      /* J/K */
 static const double ORC_PI = 3.14159265358979323846;
 
-enum { ORC_ISOTHERMAL = 0, ORC_SPECULAR = 1 };
+enum { ORC_ISOTHERMAL = 0, ORC_SPECULAR = 1, ORC_DIFFUSE = 2 };
 enum { ORC_IMPLICIT = 0, ORC_EXPLICIT = 1 };
 
 int orc_num_threads(void) {
@@ -248,9 +248,22 @@ static double upwind_value(const orc_problem* p, const double* Isrc, const doubl
     long f = wall_offset(p, side) + face_index(p, side, i, j, k);
     return I0wall[f * nb + b];
   }
+  long P = ((long)k * p->ny + j) * p->nx + i;
+  if (p->bc_type[side] == ORC_DIFFUSE) {
+    /* diffuse wall: every incoming direction gets the same intensity, set so
+       that the wall returns the band's whole outgoing energy flux:
+       sum_{out} |S_ax| I_d / sum_{in} |S_ax| (out: moving into the wall) */
+    double num = 0.0, den = 0.0;
+    for (int e = 0; e < nd; ++e) {
+      double se = p->S[3 * e + ax];
+      int outgoing = (side & 1) ? (se > 0) : (se < 0);
+      if (outgoing) num += fabs(se) * Isrc[P * nd * nb + (long)e * nb + b];
+      else if (se != 0.0) den += fabs(se);
+    }
+    return num / den;
+  }
   /* symmetry: the reflected direction of the same cell */
   const int* r = ax == 0 ? p->rx : (ax == 1 ? p->ry : p->rz);
-  long P = ((long)k * p->ny + j) * p->nx + i;
   return Isrc[P * nd * nb + (long)r[d] * nb + b];
 }
 
@@ -516,8 +529,8 @@ long orc_run_bands(const orc_problem* p, int b0, int b1, double dt, int nsteps, 
 /* ------------------------------------------------------------------------ */
 /* Heat flux.  Cell: q(P) = sum_b sum_d S_d I_{d,b}.  Wall: the mean over the   */
 /* side's faces of sum_b sum_d (S_d . n_out) I_face, with I_face the cell value */
-/* for outgoing directions and the Eq. 6 ghost for incoming ones (positive =    */
-/* energy leaving through that wall).                                         */
+/* for outgoing directions and the wall's ghost for incoming ones (positive =   */
+/* energy leaving through that wall; zero at a diffuse wall).                 */
 /* ------------------------------------------------------------------------ */
 int orc_flux(const orc_problem* p, const double* I, double* q_cells, double* q_walls) {
   long nc = ncells(p);
@@ -550,14 +563,9 @@ int orc_flux(const orc_problem* p, const double* I, double* q_cells, double* q_w
             for (int d = 0; d < nd; ++d) {
               double sn = p->S[3 * d + ax] * nsign;
               for (int b = 0; b < nb; ++b) {
-                double If;
-                if (sn > 0) If = I[P * nd * nb + (long)d * nb + b];
-                else if (p->bc_type[side] == ORC_ISOTHERMAL)
-                  If = I0wall[(wall_offset(p, side) + face_index(p, side, i, j, k)) * nb + b];
-                else {
-                  const int* r = ax == 0 ? p->rx : (ax == 1 ? p->ry : p->rz);
-                  If = I[P * nd * nb + (long)r[d] * nb + b];
-                }
+                if (sn == 0.0) continue;
+                /* leaving: the cell's value; entering: the wall's ghost (Eq. 6 or diffuse) */
+                double If = sn > 0 ? I[P * nd * nb + (long)d * nb + b] : upwind_value(p, I, I0wall, ax, i, j, k, d, b);
                 acc += sn * If;
               }
             }

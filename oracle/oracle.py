@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "bte_oracle.c")
 LIB = os.path.join(HERE, "_build", "liborc.so")
 
-ISOTHERMAL, SPECULAR = 0, 1
+ISOTHERMAL, SPECULAR, DIFFUSE = 0, 1, 2
 IMPLICIT, EXPLICIT = 0, 1
 
 _lock = threading.Lock()
@@ -188,7 +188,7 @@ class Problem:
                 p.bc_type[s] = ISOTHERMAL
                 p.bc_T[s] = _dp(T)
             else:
-                p.bc_type[s] = SPECULAR
+                p.bc_type[s] = DIFFUSE if (s < 2 * geom.dim and geom.bc[s][0] == DIFFUSE) else SPECULAR
                 p.bc_T[s] = C.POINTER(C.c_double)()
         p.newton_maxit = newton_maxit
         p.newton_rtol = newton_rtol

@@ -32,6 +32,7 @@ MASK64 = (1 << 64) - 1
 # Boundary-condition kinds and side numbering used by every caller.
 BC_ISOTHERMAL = 0
 BC_SPECULAR = 1
+BC_DIFFUSE = 2   # fully diffuse wall: incoming intensity isotropic, carrying the outgoing energy flux
 SIDES = ("-x", "+x", "-y", "+y", "-z", "+z")
 
 

@@ -427,3 +427,53 @@ def test_temperature_dependent_relaxation_conserves_energy():
     prob.run(st, 2e-13, 50, 1, O.EXPLICIT)
     E1 = sum(prob.cell_energy(r)[0] for r in st["I"])
     assert abs(E1 - E0) <= 1e-13 * E0
+
+
+def _diffuse_box(nx, ny, kinds):
+    g = W.Geometry(2, nx, ny, 1, 10e-9, 10e-9, 10e-9)
+    g.bc = [(k, None if k != W.BC_ISOTHERMAL else np.full(ny if s < 2 else nx, T)) for s, (k, T) in enumerate(kinds)]
+    return g
+
+
+def test_diffuse_enclosure_conserves_energy_and_its_walls_carry_no_net_flux():
+    """A diffuse wall returns each band's whole outgoing energy flux, spread
+    evenly over the incoming directions: a box of such walls conserves energy
+    and every wall's net flux vanishes."""
+    g = _diffuse_box(5, 4, [(W.BC_DIFFUSE, None)] * 4)
+    bands = W.make_bands(5, 2, 49)
+    prob = O.Problem(g, O.dirs_for(W.Dirs("polar_azim", n_polar=4, n_azim=8)), bands)
+    st = prob.init_state(W.random_temperatures(20, 12, 280.0, 330.0))
+    E0 = sum(prob.cell_energy(r)[0] for r in st["I"])
+    prob.run(st, 2e-13, 40, 1, O.EXPLICIT)
+    E1 = sum(prob.cell_energy(r)[0] for r in st["I"])
+    assert abs(E1 - E0) <= 1e-13 * E0
+    q, qw = prob.flux(st["I"])
+    scale = np.max(np.abs(q))
+    assert scale > 0 and np.all(np.abs(qw) <= 1e-12 * scale)
+
+
+def test_diffuse_walls_keep_an_isotropic_equilibrium():
+    g = _diffuse_box(4, 3, [(W.BC_DIFFUSE, None), (W.BC_ISOTHERMAL, 300.0), (W.BC_DIFFUSE, None), (W.BC_DIFFUSE, None)])
+    g.bc[1] = (W.BC_ISOTHERMAL, np.full(3, 300.0))
+    bands = W.make_bands(4, 1, 50)
+    prob = O.Problem(g, O.dirs_for(W.Dirs("inplane", n_inplane=12)), bands)
+    st = prob.init_state(300.0)
+    I_start = st["I"].copy()
+    prob.run(st, 1e-12, 5, 4)
+    assert np.max(np.abs(st["I"] - I_start) / I_start) <= 1e-14
+
+
+def test_diffuse_side_walls_scatter_heat_back():
+    """Ballistic channel between a hot and a cold wall: rough (diffuse) side
+    walls send phonons back, so less heat reaches the cold wall than with
+    mirror side walls."""
+    q_out = {}
+    for side_kind in (W.BC_SPECULAR, W.BC_DIFFUSE):
+        g = _diffuse_box(8, 3, [(W.BC_ISOTHERMAL, 310.0), (W.BC_ISOTHERMAL, 300.0), (side_kind, None), (side_kind, None)])
+        bands = W.make_bands(3, 1, 51)
+        bands.beta[:] = 1e6                     # nearly ballistic
+        prob = O.Problem(g, O.dirs_for(W.Dirs("inplane", n_inplane=16)), bands)
+        st = prob.init_state(300.0)
+        prob.run(st, 1e-12, 60, 8)
+        q_out[side_kind] = prob.flux(st["I"])[1][1]     # heat leaving through the cold +x wall
+    assert q_out[W.BC_SPECULAR] > 0 and 0 < q_out[W.BC_DIFFUSE] < 0.9 * q_out[W.BC_SPECULAR], q_out
