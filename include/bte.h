@@ -47,7 +47,7 @@ extern "C" {
 /* ---- enumerations ---- */
 enum { BTE_DIRS_INPLANE = 0, BTE_DIRS_POLAR_AZIM = 1 };
 enum { BTE_FP64 = 0, BTE_FP32 = 1, BTE_BF16 = 2 };
-enum { BTE_BC_ISOTHERMAL = 0, BTE_BC_SPECULAR = 1 };
+enum { BTE_BC_ISOTHERMAL = 0, BTE_BC_SPECULAR = 1, BTE_BC_DIFFUSE = 2 };
 enum { BTE_IMPLICIT_JACOBI = 0, BTE_EXPLICIT = 1 };
 enum { BTE_T_PSEUDO = 0, BTE_T_LATTICE = 1 };
 
@@ -181,7 +181,12 @@ int bte_bind_workspace(bte_handle h, void* dev_ptr, size_t bytes);
  * `geom` (Eq. 6).  BTE_BC_ISOTHERMAL: ghost intensity I0_b(T_face); T_faces is
  * a host array with one temperature per face on that side (x sides: j+ny*k,
  * y sides: i+nx*k, z sides: i+nx*j) or NULL to use T_uniform for all.
- * BTE_BC_SPECULAR (symmetry): ghost = same cell, mirrored direction. */
+ * BTE_BC_SPECULAR (symmetry): ghost = same cell, mirrored direction.
+ * BTE_BC_DIFFUSE (a rough wall; an extension beyond Eq. 6): every incoming
+ * direction of band b gets sum_out |S_d.n| I_d,b / sum_in |S_d.n| of the wall
+ * cell's current iterate (out: moving into the wall), so the wall returns
+ * each band's whole energy flux isotropically.  T_faces and T_uniform are
+ * ignored for it. */
 int bte_set_bc(bte_handle h, int geom, int side, int type, const double* T_faces, double T_uniform);
 
 /* Equilibrium initial state (Sec. 3.2): I[P][d][b] = I0_b(T_P) for all d and

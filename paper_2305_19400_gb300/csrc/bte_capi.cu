@@ -337,7 +337,8 @@ int ensure_memory(bte_ctx* h) {
     o.cell0 = h->cell0[gi];
     for (int s6 = 0; s6 < 6; ++s6) {
       o.face0[s6] = h->face0[gi * 6 + s6];
-      o.bc[s6] = h->bc_type[gi][s6];
+      // a diffuse side reads its ghost row like an isothermal one (refreshed each inner iteration)
+      o.bc[s6] = h->bc_type[gi][s6] == BTE_BC_DIFFUSE ? BTE_BC_ISOTHERMAL : h->bc_type[gi][s6];
     }
     o.cls = h->cls[gi];
     o.pad = 0;
@@ -353,7 +354,8 @@ int ensure_memory(bte_ctx* h) {
 int upload_geoms(bte_ctx* h) {
   std::vector<DevGeom>& dg = h->dgeoms;
   for (size_t gi = 0; gi < h->geoms.size(); ++gi)
-    for (int s6 = 0; s6 < 6; ++s6) dg[gi].bc[s6] = h->bc_type[gi][s6];
+    for (int s6 = 0; s6 < 6; ++s6)  // a diffuse side reads its (refreshed) ghost row like an isothermal one
+      dg[gi].bc[s6] = h->bc_type[gi][s6] == BTE_BC_DIFFUSE ? BTE_BC_ISOTHERMAL : h->bc_type[gi][s6];
   CUDA_TRY(h, cudaMemcpyAsync(h->geoms_d, dg.data(), dg.size() * sizeof(DevGeom), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return BTE_OK;
@@ -482,6 +484,21 @@ SweepArgs sweep_args(bte_ctx* h) {
   return a;
 }
 
+// Diffuse wall ghosts from intensity buffer I (before a sweep that reads I as
+// its upwind field, and before wall fluxes).  *launches counts the kernels.
+cudaError_t refresh_diffuse(bte_ctx* h, const void* I, cudaStream_t s, int* launches = nullptr) {
+  for (size_t gi = 0; gi < h->geoms.size(); ++gi)
+    for (int side = 0; side < 2 * h->geoms[gi].dim; ++side) {
+      if (h->bc_type[gi][side] != BTE_BC_DIFFUSE) continue;
+      const cudaError_t e = launch_diffuse_ghosts(
+          h->opts.precision, I, h->I0ref_o, h->I0wall, h->opts.precision == BTE_FP64 ? nullptr : h->I0wall_dev,
+          h->geoms_d, (int)gi, side, h->Sdev, h->nd, h->nbp, (int)side_faces(h->geoms[gi], side), s);
+      if (e != cudaSuccess) return e;
+      if (launches) ++*launches;
+    }
+  return cudaSuccess;
+}
+
 // One time step: ninner sweeps rotating the three intensity buffers from *cur.
 cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, cudaStream_t s, int* cur) {
   int dim = 2;
@@ -515,6 +532,7 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, cudaStream_t s, in
     a.Ik = h->Ibuf[k];
     a.Iout = h->Ibuf[o];
     cudaError_t e = cudaMemsetAsync(h->fix_count, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = refresh_diffuse(h, a.Ik, s);
     if (e == cudaSuccess) e = launch_sweep(h->opts.precision, h->pd, a, dim, h->threads, h->grid, s);
     if (e == cudaSuccess && a.partial) {
       // band-range handle: the caller sums the per-cell (E_L, E_p) partials over
@@ -552,6 +570,10 @@ int flux_view(bte_ctx* h, int geom, FluxView* out) {
   const bte_geom& g = h->geoms[geom];
   out->precision = h->opts.precision;
   out->I = (const double*)h->Ibuf[h->cur];
+  {  // diffuse wall ghosts of the current state (a kernel launch, no allocation)
+    const cudaError_t e = refresh_diffuse(h, h->Ibuf[h->cur], h->stream);
+    if (e != cudaSuccess) return fail(h, BTE_E_CUDA, "diffuse wall ghosts: %s", cudaGetErrorString(e));
+  }
   out->I0wall = h->I0wall;
   out->geoms = h->geoms_d;
   out->dirs = h->dirs_d;
@@ -762,7 +784,8 @@ int bte_set_bc(bte_handle h, int geom, int side, int type, const double* T_faces
   if (!h->bands_set) return fail(h, BTE_E_STATE, "bte_set_bands must come before bte_set_bc");
   const bte_geom& g = h->geoms[geom];
   if (side < 0 || side >= 2 * g.dim) return fail(h, BTE_E_ARG, "side %d out of range for a %dD geometry", side, g.dim);
-  if (type != BTE_BC_ISOTHERMAL && type != BTE_BC_SPECULAR) return fail(h, BTE_E_ARG, "unknown wall type %d", type);
+  if (type != BTE_BC_ISOTHERMAL && type != BTE_BC_SPECULAR && type != BTE_BC_DIFFUSE)
+    return fail(h, BTE_E_ARG, "unknown wall type %d", type);
   const long long nf = side_faces(g, side);
   std::vector<double> T;
   if (type == BTE_BC_ISOTHERMAL) {
@@ -864,7 +887,11 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
         return fail(h, BTE_E_EXCHANGE, "the exchange callback returned %d", h->exchange_rc);
       CUDA_TRY(h, e);
     }
-    launches += ninner * (1 + (h->solve_tp ? 1 : 0) + (ranged ? 1 : 0));  // sweep, fix-up, cell solve
+    int ndiff = 0;
+    for (auto& bt : h->bc_type)
+      for (int t : bt) ndiff += t == BTE_BC_DIFFUSE;
+    // sweep, fix-up, cell solve, diffuse wall ghosts
+    launches += ninner * (1 + (h->solve_tp ? 1 : 0) + (ranged ? 1 : 0) + ndiff);
   }
   if (nsteps > 0) {
     h->TL_valid = false;
@@ -1001,6 +1028,7 @@ int bte_get_flux(bte_handle h, int geom, double* q_cells, double* q_walls, int o
   }
   if (q_walls) {
     double res[6] = {0, 0, 0, 0, 0, 0};
+    CUDA_TRY(h, refresh_diffuse(h, I, s));  // diffuse ghosts of the current state
     for (int side = 0; side < 2 * g.dim; ++side) {
       const int nf = (int)side_faces(g, side);
       CUDA_TRY(h, launch_flux_faces(prec, I, h->I0ref_o, h->I0wall, h->geoms_d, geom, side, h->dirs_d, h->Sdev, h->nd,

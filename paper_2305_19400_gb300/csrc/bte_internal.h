@@ -141,6 +141,9 @@ cudaError_t launch_sweep_bf16(int pd, const SweepArgs& a, int dim, int threads, 
 struct MLPView;
 cudaError_t launch_fixup(const SweepArgs& a, const MLPView* mlp, cudaStream_t s);
 cudaError_t launch_solve_cells(const SweepArgs& a, long long ncells, cudaStream_t s);
+cudaError_t launch_diffuse_ghosts(int precision, const void* I, const double* I0ref, double* I0wall, float* I0wall_dev,
+                                  const DevGeom* geoms, int geom, int side, const double* S, int nd, int nbp,
+                                  int nfaces, cudaStream_t s);
 // learned guess (bte_mlp.cu)
 int mlp_param_total(int nb);
 cudaError_t launch_mlp_norm(ThermoTables th, double T_lo, double T_hi, const double* I0ref, double* r_lo, double* r_hi,

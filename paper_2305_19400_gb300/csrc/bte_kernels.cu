@@ -11,6 +11,8 @@
 //   solve_TL_kernel     T_L on request (cached model first, exact otherwise);
 //   flux_cells / flux_faces / mean / pack / energy_L
 //                       heat flux, FP64 <-> storage packing, E_L after a restore.
+#include <algorithm>
+
 #include "bte_mlp.cuh"
 #include "bte_quad.cuh"
 #include "bte_solve.cuh"
@@ -366,6 +368,45 @@ __global__ void solve_cells_kernel(SweepArgs a, long long ncells) {
   }
 }
 
+// Diffuse wall ghosts of one side of one geometry: for every face, per band,
+// sum over the directions leaving through the wall of |S_d,ax| I_d, divided by
+// sum over the entering directions of |S_d,ax|, from the wall cell's current
+// iterate, into the FP64 ghost row (and the FP32 deviation row in the reduced
+// modes).  One warp per face, lanes over bands, directions in order.
+template <typename S>
+__global__ void diffuse_ghost_kernel(const S* I, const double* I0ref, double* I0wall, float* I0wall_dev,
+                                     const DevGeom* geoms, int geom, int side, const double* Sd, int nd, int nbp,
+                                     int nfaces) {
+  const DevGeom g = geoms[geom];
+  const int ax = side >> 1;
+  const bool high = side & 1;
+  const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
+  const long long row = (long long)nd * nbp;
+  for (int f = blockIdx.x * warps + threadIdx.x / 32; f < nfaces; f += gridDim.x * warps) {
+    int i, j, k;  // wall cell of face f (x sides: j + ny k, y sides: i + nx k, z sides: i + nx j)
+    if (ax == 0) { i = high ? g.nx - 1 : 0; j = f % g.ny; k = f / g.ny; }
+    else if (ax == 1) { j = high ? g.ny - 1 : 0; i = f % g.nx; k = f / g.nx; }
+    else { k = high ? g.nz - 1 : 0; i = f % g.nx; j = f / g.nx; }
+    const long long P = g.cell0 + ((long long)k * g.ny + j) * g.nx + i;
+    double den = 0.0;
+    for (int d = 0; d < nd; ++d) {
+      const double sd = Sd[3 * d + ax];
+      if (!(high ? sd > 0.0 : sd < 0.0) && sd != 0.0) den += fabs(sd);
+    }
+    for (int b = lane; b < nbp; b += 32) {
+      double num = 0.0;
+      for (int d = 0; d < nd; ++d) {
+        const double sd = Sd[3 * d + ax];
+        if (high ? sd > 0.0 : sd < 0.0) num += fabs(sd) * full_I(I, P * row + (long long)d * nbp + b, b, I0ref);
+      }
+      const double v = num / den;
+      const long long e = (g.face0[side] + f) * nbp + b;
+      I0wall[e] = v;
+      if (I0wall_dev) I0wall_dev[e] = (float)(v - I0ref[b]);
+    }
+  }
+}
+
 inline int grid_for(long long n, int threads) {
   long long g = (n + threads - 1) / threads;
   if (g > 152LL * 64) g = 152LL * 64;
@@ -389,6 +430,22 @@ cudaError_t launch_fixup(const SweepArgs& a, const MLPView* mlp, cudaStream_t s)
   MLPView m{};
   if (mlp) m = *mlp;
   fixup_kernel<<<152, 128, sm, s>>>(a, mlp ? 1 : 0, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diffuse_ghosts(int precision, const void* I, const double* I0ref, double* I0wall, float* I0wall_dev,
+                                  const DevGeom* geoms, int geom, int side, const double* S, int nd, int nbp,
+                                  int nfaces, cudaStream_t s) {
+  const int grid = (int)std::min<long long>((nfaces + 3) / 4, 152LL * 16);
+  if (precision == 0)
+    diffuse_ghost_kernel<double><<<grid, 128, 0, s>>>((const double*)I, I0ref, I0wall, nullptr, geoms, geom, side, S, nd,
+                                                      nbp, nfaces);
+  else if (precision == 1)
+    diffuse_ghost_kernel<float><<<grid, 128, 0, s>>>((const float*)I, I0ref, I0wall, I0wall_dev, geoms, geom, side, S, nd,
+                                                     nbp, nfaces);
+  else
+    diffuse_ghost_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>((const __nv_bfloat16*)I, I0ref, I0wall, I0wall_dev, geoms,
+                                                             geom, side, S, nd, nbp, nfaces);
   return cudaGetLastError();
 }
 

@@ -145,14 +145,15 @@ class Workload:
 
 
 def uniform_walls(geom: Geometry, kinds, temps):
-    """Fill geom.bc from per-side kinds and uniform temperatures (None for specular)."""
+    """Fill geom.bc from per-side kinds and uniform temperatures (None for
+    specular and diffuse sides)."""
     geom.bc = []
     nsides = 2 * geom.dim
     for s in range(nsides):
         if kinds[s] == BC_ISOTHERMAL:
             geom.bc.append((BC_ISOTHERMAL, np.full(geom.nfaces(s), float(temps[s]))))
         else:
-            geom.bc.append((BC_SPECULAR, None))
+            geom.bc.append((BC_DIFFUSE if kinds[s] == BC_DIFFUSE else BC_SPECULAR, None))
     return geom
 
 
