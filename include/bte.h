@@ -48,7 +48,7 @@ extern "C" {
 enum { BTE_DIRS_INPLANE = 0, BTE_DIRS_POLAR_AZIM = 1 };
 enum { BTE_FP64 = 0, BTE_FP32 = 1, BTE_BF16 = 2 };
 enum { BTE_BC_ISOTHERMAL = 0, BTE_BC_SPECULAR = 1, BTE_BC_DIFFUSE = 2 };
-enum { BTE_IMPLICIT_JACOBI = 0, BTE_EXPLICIT = 1 };
+enum { BTE_IMPLICIT_JACOBI = 0, BTE_EXPLICIT = 1, BTE_IMPLICIT_GS = 2 };
 enum { BTE_T_PSEUDO = 0, BTE_T_LATTICE = 1 };
 
 typedef struct bte_ctx* bte_handle;
@@ -200,14 +200,24 @@ int bte_set_initial(bte_handle h, int geom, const double* T_cells, double T_unif
  *   I^{k+1} = [I^n/dt + beta I0^k + v sum_ax c_ax I_up^k]/[1/dt + beta + v sum_ax c_ax]
  *   (c_ax = |S_ax|/(w_d Delta_ax)), then reduction, T_p solve, I0 refresh.
  * scheme BTE_EXPLICIT: forward Euler (Eq. 3 with Eq. 5), ninner ignored.
+ * scheme BTE_IMPLICIT_GS (FP64 storage only, else BTE_E_ARG): backward Euler
+ *   with sweep-ordered (Gauss-Seidel) inner iterations, an extension beyond
+ *   the paper's point-Jacobi form: each (d, b) visits the cells in its upwind
+ *   order, so an interior upwind neighbour holds its value of the current
+ *   inner iteration; mirror and diffuse wall ghosts and I0 stay at I^k.  The
+ *   fixed point is the same backward-Euler solution; fewer inner iterations
+ *   reach a given residual.  Two kernels per inner iteration (the pass, then
+ *   the per-cell reduction and T_p step), plus one with beta_T_exp != 0.
  * stats: host, may be NULL (then the call only queues work and returns). */
 int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_stats* stats);
 
 /* Times the sweep over candidate launch shapes (cells per CTA x grid size,
  * persistent grids of 2/4/8 CTAs per SM or one CTA per work item) with the
- * current state and keeps the fastest for this handle.  The timing launches
- * write only a spare intensity buffer (no solver state changes).  `report`
- * (host, may be NULL) receives a CSV table of the candidates. */
+ * current state and keeps the fastest for this handle.  With scheme
+ * BTE_IMPLICIT_GS it times the sweep-ordered pass instead, over directions
+ * per CTA and the column-tile size.  The timing launches write only a spare
+ * intensity buffer (no solver state changes).  `report` (host, may be NULL)
+ * receives a CSV table of the candidates. */
 int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t report_len);
 
 /* Cell temperatures of one geometry: BTE_T_PSEUDO (T_p, the temperature whose

@@ -40,7 +40,7 @@ static const double ORC_KB = 1.380649e-23;      /* J/K */
 static const double ORC_PI = 3.14159265358979323846;
 
 enum { ORC_ISOTHERMAL = 0, ORC_SPECULAR = 1, ORC_DIFFUSE = 2 };
-enum { ORC_IMPLICIT = 0, ORC_EXPLICIT = 1 };
+enum { ORC_IMPLICIT = 0, ORC_EXPLICIT = 1, ORC_GAUSS_SEIDEL = 2 };
 
 int orc_num_threads(void) {
 #ifdef _OPENMP
@@ -304,6 +304,72 @@ double orc_update_one(const orc_problem* p, double dt, int scheme, const double*
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sweep-ordered (Gauss-Seidel) inner iteration of the implicit scheme.         */
+/* The backward-Euler equation of (P, d, b) is the implicit update above; in    */
+/* this form the cells of each (d, b) are visited in the direction's upwind     */
+/* order, so an interior upwind neighbour already holds its value of the        */
+/* current inner iteration (Inew).  Mirror and diffuse wall ghosts, and I0,     */
+/* stay at the previous iterate I^k, as in the Jacobi form.  With all walls     */
+/* isothermal one pass solves the streaming part exactly for the given I0.      */
+/* ------------------------------------------------------------------------ */
+static double gs_update_one(const orc_problem* p, double dt, const double* In, const double* Ik, const double* Inew,
+                            const double* I0, const double* I0wall, int i, int j, int k, int d, int b, double bscale) {
+  int nd = p->nd, nb = p->nb;
+  long P = ((long)k * p->ny + j) * p->nx + i;
+  double delta[3] = {p->dx, p->dy, p->dz};
+  int c[3] = {i, j, k}, n[3] = {p->nx, p->ny, p->nz};
+  double beta = p->beta[b] * bscale, v = p->vg[b];
+  double num = In[P * nd * nb + (long)d * nb + b] / dt + beta * I0[P * nb + b], den = 1.0 / dt + beta;
+  for (int ax = 0; ax < p->dim; ++ax) {
+    double s = p->S[3 * d + ax];
+    if (s == 0.0) continue;
+    double cc = fabs(s) / (p->w[d] * delta[ax]);
+    int q = c[ax] + (s > 0 ? -1 : 1); /* upwind neighbour along ax */
+    double up;
+    if (q >= 0 && q < n[ax]) {
+      int u[3] = {i, j, k};
+      u[ax] = q;
+      up = Inew[(((long)u[2] * p->ny + u[1]) * p->nx + u[0]) * nd * nb + (long)d * nb + b];
+    } else {
+      up = upwind_value(p, Ik, I0wall, ax, i, j, k, d, b);
+    }
+    num += v * cc * up;
+    den += v * cc;
+  }
+  return num / den;
+}
+
+/* The sweep-ordered update of one (P, d, b) given the current pass's field
+ * Inew (for sampled checks of a pass computed elsewhere). */
+double orc_gs_update_one(const orc_problem* p, double dt, const double* In, const double* Ik, const double* Inew,
+                         const double* I0, const double* I0wall, long P, int d, int b, double bscale) {
+  int i = (int)(P % p->nx), j = (int)((P / p->nx) % p->ny), k = (int)(P / ((long)p->nx * p->ny));
+  return gs_update_one(p, dt, In, Ik, Inew, I0, I0wall, i, j, k, d, b, bscale);
+}
+
+/* One sweep-ordered pass over bands [b0, b1): every (d, b) walks the grid with
+ * each axis in the order the direction travels (ascending when S_{d,ax} >= 0). */
+static void gs_pass(const orc_problem* p, double dt, const double* In, const double* Ik, double* Inew, const double* I0,
+                    const double* I0wall, const double* Tp, int b0, int b1) {
+  int nd = p->nd;
+#pragma omp parallel for schedule(dynamic)
+  for (int d = 0; d < nd; ++d)
+    for (int b = b0; b < b1; ++b)
+      for (int kk = 0; kk < p->nz; ++kk) {
+        int k = p->S[3 * d + 2] >= 0 ? kk : p->nz - 1 - kk;
+        for (int jj = 0; jj < p->ny; ++jj) {
+          int j = p->S[3 * d + 1] >= 0 ? jj : p->ny - 1 - jj;
+          for (int ii = 0; ii < p->nx; ++ii) {
+            int i = p->S[3 * d + 0] >= 0 ? ii : p->nx - 1 - ii;
+            long P = ((long)k * p->ny + j) * p->nx + i;
+            Inew[P * nd * p->nb + (long)d * p->nb + b] =
+                gs_update_one(p, dt, In, Ik, Inew, I0, I0wall, i, j, k, d, b, beta_scale(p, Tp[P]));
+          }
+        }
+      }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Temperature from an energy: solve sum_b a_b I0_b(T) = E by Newton from a     */
 /* guess, stop when |dT| <= rtol T; bisection on [1, 5000] K as the fallback.  */
 /* a_b = W/v_b gives T_L (energy), a_b = W beta_b / v_b gives T_p.             */
@@ -423,6 +489,7 @@ int orc_init_state(const orc_problem* p, const double* Tcells, double* I, double
 /*   (i) intensity update for every (P, d, b) from I^n, I^k, I0^k (walls: Eq.6) */
 /*   (ii) per-cell reduction, (iii) T_p and T_L by Newton, (iv) I0 = I0(T_p).   */
 /* The explicit scheme takes one pass (ninner = 1) of the forward-Euler update. */
+/* ORC_GAUSS_SEIDEL replaces (i) by the sweep-ordered pass (gs_pass).           */
 /* Returns the number of bisection fallbacks, or -1 on an unsolvable cell.     */
 /* ------------------------------------------------------------------------ */
 long orc_run(const orc_problem* p, double dt, int nsteps, int ninner, int scheme, double* I, double* Tp, double* TL,
@@ -439,12 +506,16 @@ long orc_run(const orc_problem* p, double dt, int nsteps, int ninner, int scheme
     memcpy(In, I, n * sizeof(double));
     for (int k = 0; k < ninner; ++k) {
       const double* Ik = (scheme == ORC_EXPLICIT) ? In : I;
+      if (scheme == ORC_GAUSS_SEIDEL) {
+        gs_pass(p, dt, In, Ik, Inew, I0, I0wall, Tp, 0, nb);
+      } else {
 #pragma omp parallel for schedule(static)
-      for (long P = 0; P < nc; ++P) {
-        const double bs = beta_scale(p, Tp[P]);
-        for (int d = 0; d < nd; ++d)
-          for (int b = 0; b < nb; ++b)
-            Inew[P * nd * nb + (long)d * nb + b] = orc_update_one(p, dt, scheme, In, Ik, I0, I0wall, P, d, b, bs);
+        for (long P = 0; P < nc; ++P) {
+          const double bs = beta_scale(p, Tp[P]);
+          for (int d = 0; d < nd; ++d)
+            for (int b = 0; b < nb; ++b)
+              Inew[P * nd * nb + (long)d * nb + b] = orc_update_one(p, dt, scheme, In, Ik, I0, I0wall, P, d, b, bs);
+        }
       }
 #pragma omp parallel for schedule(static) reduction(+ : fallbacks, bad)
       for (long P = 0; P < nc; ++P) {
@@ -489,12 +560,16 @@ long orc_run_bands(const orc_problem* p, int b0, int b1, double dt, int nsteps, 
     for (int k = 0; k < ninner; ++k) {
       const double* Ik = (scheme == ORC_EXPLICIT) ? In : I;
       memcpy(Inew, I, n * sizeof(double));
+      if (scheme == ORC_GAUSS_SEIDEL) {
+        gs_pass(p, dt, In, Ik, Inew, I0, I0wall, Tp, b0, b1);
+      } else {
 #pragma omp parallel for schedule(static)
-      for (long P = 0; P < nc; ++P) {
-        const double bs = beta_scale(p, Tp[P]);
-        for (int d = 0; d < nd; ++d)
-          for (int b = b0; b < b1; ++b)
-            Inew[P * nd * nb + (long)d * nb + b] = orc_update_one(p, dt, scheme, In, Ik, I0, I0wall, P, d, b, bs);
+        for (long P = 0; P < nc; ++P) {
+          const double bs = beta_scale(p, Tp[P]);
+          for (int d = 0; d < nd; ++d)
+            for (int b = b0; b < b1; ++b)
+              Inew[P * nd * nb + (long)d * nb + b] = orc_update_one(p, dt, scheme, In, Ik, I0, I0wall, P, d, b, bs);
+        }
       }
 #pragma omp parallel for schedule(static)
       for (long P = 0; P < nc; ++P) {  /* partial reduction over the owned bands */

@@ -21,7 +21,7 @@ SRC = os.path.join(HERE, "bte_oracle.c")
 LIB = os.path.join(HERE, "_build", "liborc.so")
 
 ISOTHERMAL, SPECULAR, DIFFUSE = 0, 1, 2
-IMPLICIT, EXPLICIT = 0, 1
+IMPLICIT, EXPLICIT, GAUSS_SEIDEL = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -73,6 +73,8 @@ def lib():
             P = C.POINTER(_Problem)
             L.orc_update_one.argtypes = [P, C.c_double, C.c_int, dp, dp, dp, dp, C.c_long, C.c_int, C.c_int, C.c_double]
             L.orc_update_one.restype = C.c_double
+            L.orc_gs_update_one.argtypes = [P, C.c_double, dp, dp, dp, dp, dp, C.c_long, C.c_int, C.c_int, C.c_double]
+            L.orc_gs_update_one.restype = C.c_double
             L.orc_solve_T.argtypes = [P, dp, C.c_double, C.c_double, dp]
             L.orc_cell_energy.argtypes = [P, dp, dp, dp]
             L.orc_cell_energy.restype = None
@@ -252,6 +254,11 @@ class Problem:
         """bscale: beta_b(T_p)/beta_b of cell P (1 when tau does not depend on T)."""
         return float(lib().orc_update_one(self.ptr, float(dt), int(scheme), _dp(In), _dp(Ik), _dp(I0cells),
                                           _dp(I0wall), int(P), int(d), int(b), float(bscale)))
+
+    def gs_update_one(self, dt, In, Ik, Inew, I0cells, I0wall, P, d, b, bscale=1.0) -> float:
+        """Sweep-ordered update of (P, d, b): interior upwind values from Inew."""
+        return float(lib().orc_gs_update_one(self.ptr, float(dt), _dp(In), _dp(Ik), _dp(Inew), _dp(I0cells),
+                                             _dp(I0wall), int(P), int(d), int(b), float(bscale)))
 
     def cell_energy(self, row):
         row = np.ascontiguousarray(row, dtype=np.float64)

@@ -21,7 +21,7 @@ BTE_E = {-1: "BTE_E_ARG", -2: "BTE_E_STATE", -3: "BTE_E_CUDA", -4: "BTE_E_NOMEM"
 BTE_DIRS_INPLANE, BTE_DIRS_POLAR_AZIM = 0, 1
 BTE_FP64, BTE_FP32, BTE_BF16 = 0, 1, 2
 BTE_BC_ISOTHERMAL, BTE_BC_SPECULAR = 0, 1
-BTE_IMPLICIT_JACOBI, BTE_EXPLICIT = 0, 1
+BTE_IMPLICIT_JACOBI, BTE_EXPLICIT, BTE_IMPLICIT_GS = 0, 1, 2
 BTE_T_PSEUDO, BTE_T_LATTICE = 0, 1
 
 

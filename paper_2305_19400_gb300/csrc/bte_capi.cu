@@ -67,6 +67,11 @@ struct bte_ctx {
   cudaStream_t cap_stream = nullptr;
   std::string tune_report;
   std::vector<WorkItem> items;
+  // sweep-ordered pass: directions grouped by octant, units, CTA layout and tiles
+  std::vector<int> gs_dirs;
+  std::vector<GsUnit> gs_units;
+  int gs_ndc = 1, gs_tx = 128, gs_ty = 1, gs_threads = 0;
+  std::string gs_tune_report;
   // device memory
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -96,6 +101,9 @@ struct bte_ctx {
   DevGeom* geoms_d = nullptr;
   WorkItem* items_d = nullptr;
   DevCounters* counters = nullptr;
+  GsUnit* gs_units_d = nullptr;
+  int* gs_dirs_d = nullptr;
+  double* bscale = nullptr;  // [cell] beta_b(T_p)/beta_b for the sweep-ordered pass
   // coefficient cache
   double coef_dt = -1.0;
   int coef_scheme = -1;
@@ -209,6 +217,9 @@ size_t carve(bte_ctx* h, char* base) {
   h->geoms_d = (DevGeom*)take(h->geoms.size() * sizeof(DevGeom));
   h->items_d = (WorkItem*)take((size_t)std::max<long long>(h->ncells, 1) * sizeof(WorkItem));  // room for 1 cell per item
   h->counters = (DevCounters*)take(sizeof(DevCounters));
+  h->gs_units_d = (GsUnit*)take(std::max<size_t>(h->geoms.size() * h->nd, 1) * sizeof(GsUnit));
+  h->gs_dirs_d = (int*)take((size_t)h->nd * 4);
+  h->bscale = (double*)take((size_t)std::max(h->ncells, 1LL) * 8);
   h->scratch_faces = (double*)take((size_t)std::max(h->max_side_faces, 1) * 8);
   h->scratch_T = (double*)take((size_t)std::max(h->max_side_faces, h->max_geom_cells) * 8);
   h->scratch_out = (double*)take(64);
@@ -254,6 +265,47 @@ void build_items(bte_ctx* h, int cpb = 0) {
               h->items.push_back(WorkItem{(int)gi, (k * g.ny + j) * g.nx + i, std::min(h->cpb, std::min(g.nx, i0 + bx) - i), 0});
   }
   h->grid = (int)std::min<size_t>(h->items.size(), 65535);
+}
+
+// Sweep-ordered pass.  Directions whose upwind sides agree (one octant) share
+// a visiting order; a unit is up to ndc of them over one geometry, one CTA per
+// unit.  2-D grids are walked in strips of tx columns, 3-D grids in tx x ty
+// column tiles.  The CTA has lpc/2 lanes per (cell, direction) row (two FP64
+// bands per lane) and as many cell slots as fit 256 threads.
+void build_gs(bte_ctx* h, int ndc, int tx, int ty) {
+  int dim = 2;
+  for (auto& g : h->geoms) dim = std::max(dim, g.dim);
+  const int noct = 1 << dim;
+  h->gs_dirs.clear();
+  h->gs_units.clear();
+  std::vector<int> start(noct + 1, 0);
+  for (int o = 0; o < noct; ++o) {
+    start[o] = (int)h->gs_dirs.size();
+    for (int d = 0; d < h->nd; ++d) {
+      const int up = (h->S[3 * d] > 0) | ((h->S[3 * d + 1] > 0) << 1) | ((h->S[3 * d + 2] > 0) << 2);
+      if ((up & (noct - 1)) == o) h->gs_dirs.push_back(d);
+    }
+  }
+  start[noct] = (int)h->gs_dirs.size();
+  const int lanes = h->nbp / 2;
+  ndc = std::max(1, std::min(ndc, 256 / lanes));
+  for (size_t gi = 0; gi < h->geoms.size(); ++gi)
+    for (int o = 0; o < noct; ++o)
+      for (int c = start[o]; c < start[o + 1]; c += ndc)
+        h->gs_units.push_back(GsUnit{(int)gi, c, std::min(ndc, start[o + 1] - c), 0});
+  h->gs_ndc = ndc;
+  h->gs_tx = std::max(1, tx);
+  h->gs_ty = std::max(1, ty);
+  const int team = lanes * ndc;
+  h->gs_threads = team * std::max(1, 256 / team);
+}
+
+int upload_gs(bte_ctx* h, cudaStream_t s) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->gs_dirs_d, h->gs_dirs.data(), h->gs_dirs.size() * 4, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->gs_units_d, h->gs_units.data(), h->gs_units.size() * sizeof(GsUnit),
+                              cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  return BTE_OK;
 }
 
 void drop_graphs(bte_ctx* h) {
@@ -347,6 +399,13 @@ int ensure_memory(bte_ctx* h) {
   CUDA_TRY(h, cudaMemcpyAsync(h->items_d, h->items.data(), h->items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, sizeof(DevCounters), s));
   CUDA_TRY(h, cudaStreamSynchronize(s));
+  {
+    int dim = 2;
+    for (auto& g : h->geoms) dim = std::max(dim, g.dim);
+    build_gs(h, 1, dim == 3 ? 8 : 128, dim == 3 ? 8 : 1);
+    const int rc = upload_gs(h, s);
+    if (rc) return rc;
+  }
   h->mem_ready = true;
   return BTE_OK;
 }
@@ -480,6 +539,13 @@ SweepArgs sweep_args(bte_ctx* h) {
   a.bb32 = h->bb32;
   a.fix = h->fix;
   a.fix_count = h->fix_count;
+  a.gs_units = h->gs_units_d;
+  a.gs_dirs = h->gs_dirs_d;
+  a.gs_nunits = (int)h->gs_units.size();
+  a.gs_ndc = h->gs_ndc;
+  a.gs_tx = h->gs_tx;
+  a.gs_ty = h->gs_ty;
+  a.bscale = h->bscale;
   a.th = thermo(h);
   return a;
 }
@@ -500,7 +566,9 @@ cudaError_t refresh_diffuse(bte_ctx* h, const void* I, cudaStream_t s, int* laun
 }
 
 // One time step: ninner sweeps rotating the three intensity buffers from *cur.
-cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, cudaStream_t s, int* cur) {
+// scheme BTE_IMPLICIT_GS runs the sweep-ordered pass and the per-cell step as
+// two kernels in place of the fused Jacobi sweep.
+cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaStream_t s, int* cur) {
   int dim = 2;
   for (auto& g : h->geoms) dim = std::max(dim, g.dim);
   const int n = *cur;
@@ -533,7 +601,14 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, cudaStream_t s, in
     a.Iout = h->Ibuf[o];
     cudaError_t e = cudaMemsetAsync(h->fix_count, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = refresh_diffuse(h, a.Ik, s);
-    if (e == cudaSuccess) e = launch_sweep(h->opts.precision, h->pd, a, dim, h->threads, h->grid, s);
+    if (scheme == BTE_IMPLICIT_GS) {
+      if (e == cudaSuccess && a.beta_exp != 0.0)
+        e = launch_beta_scale(h->bscale, h->Tp, a.beta_Tref, a.beta_exp, h->ncells, s);
+      if (e == cudaSuccess) e = launch_gs_sweep(a, dim, h->gs_threads, s);
+      if (e == cudaSuccess) e = launch_gs_reduce(a, h->ncells, s);
+    } else if (e == cudaSuccess) {
+      e = launch_sweep(h->opts.precision, h->pd, a, dim, h->threads, h->grid, s);
+    }
     if (e == cudaSuccess && a.partial) {
       // band-range handle: the caller sums the per-cell (E_L, E_p) partials over
       // the ranks that hold the other bands, then every rank solves every cell
@@ -837,13 +912,17 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
   if (!h->mem_ready || !ready_to_step(h, why)) return fail(h, BTE_E_STATE, "not ready to step: %s", why.empty() ? "no state" : why.c_str());
   if (!(dt > 0 && std::isfinite(dt))) return fail(h, BTE_E_ARG, "dt must be > 0");
   if (nsteps < 0) return fail(h, BTE_E_ARG, "nsteps must be >= 0");
-  if (scheme != BTE_IMPLICIT_JACOBI && scheme != BTE_EXPLICIT) return fail(h, BTE_E_ARG, "unknown scheme %d", scheme);
+  if (scheme != BTE_IMPLICIT_JACOBI && scheme != BTE_EXPLICIT && scheme != BTE_IMPLICIT_GS)
+    return fail(h, BTE_E_ARG, "unknown scheme %d", scheme);
+  if (scheme == BTE_IMPLICIT_GS && h->opts.precision != BTE_FP64)
+    return fail(h, BTE_E_ARG, "the sweep-ordered scheme needs FP64 storage");
   if (scheme == BTE_EXPLICIT) ninner = 1;
   if (ninner < 1) return fail(h, BTE_E_ARG, "ninner must be >= 1");
-  int rc = ensure_coef(h, dt, scheme);
+  const int cscheme = scheme == BTE_EXPLICIT ? BTE_EXPLICIT : BTE_IMPLICIT_JACOBI;  // coefficient set
+  int rc = ensure_coef(h, dt, cscheme);
   if (rc) return rc;
   if (h->opts.learned && !h->mlp_trained) return fail(h, BTE_E_STATE, "learned mode needs bte_train_mlp first");
-  if (h->opts.autotune && h->tune_report.empty()) {
+  if (h->opts.autotune && (scheme == BTE_IMPLICIT_GS ? h->gs_tune_report.empty() : h->tune_report.empty())) {
     if ((rc = bte_autotune(h, dt, scheme, nullptr, 0)) != BTE_OK) return rc;
   }
   cudaStream_t s = h->stream;
@@ -867,7 +946,7 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
         cudaGraph_t graph = nullptr;
         CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
         int cur = h->cur;
-        cudaError_t e = enqueue_step(h, a, ninner, h->cap_stream, &cur);
+        cudaError_t e = enqueue_step(h, a, ninner, scheme, h->cap_stream, &cur);
         cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
           if (graph) cudaGraphDestroy(graph);
@@ -882,7 +961,7 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
       CUDA_TRY(h, cudaGraphLaunch(exec, s));
       h->cur = cur_out;
     } else {
-      const cudaError_t e = enqueue_step(h, a, ninner, s, &h->cur);
+      const cudaError_t e = enqueue_step(h, a, ninner, scheme, s, &h->cur);
       if (e != cudaSuccess && h->exchange_rc)
         return fail(h, BTE_E_EXCHANGE, "the exchange callback returned %d", h->exchange_rc);
       CUDA_TRY(h, e);
@@ -890,8 +969,10 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
     int ndiff = 0;
     for (auto& bt : h->bc_type)
       for (int t : bt) ndiff += t == BTE_BC_DIFFUSE;
-    // sweep, fix-up, cell solve, diffuse wall ghosts
-    launches += ninner * (1 + (h->solve_tp ? 1 : 0) + (ranged ? 1 : 0) + ndiff);
+    // sweep (sweep-ordered: pass + per-cell step, and the beta scale with tau(T)),
+    // fix-up, cell solve, diffuse wall ghosts
+    const int sweep_k = scheme == BTE_IMPLICIT_GS ? 2 + (h->opts.beta_T_exp != 0.0 ? 1 : 0) : 1;
+    launches += ninner * (sweep_k + (h->solve_tp ? 1 : 0) + (ranged ? 1 : 0) + ndiff);
   }
   if (nsteps > 0) {
     h->TL_valid = false;
@@ -917,14 +998,82 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
   return BTE_OK;
 }
 
+namespace {
+
+void copy_report(const std::string& r, char* report, size_t report_len) {
+  if (report && report_len) {
+    std::strncpy(report, r.c_str(), report_len - 1);
+    report[report_len - 1] = 0;
+  }
+}
+
+// Sweep-ordered pass: directions per CTA x column-tile size, timed on a spare buffer.
+int autotune_gs(bte_ctx* h, char* report, size_t report_len) {
+  cudaStream_t s = h->stream;
+  int dim = 2;
+  for (auto& g : h->geoms) dim = std::max(dim, g.dim);
+  const int spare = (h->cur + 1) % 3;
+  struct Cand { int ndc, tx, ty; float ms; };
+  std::vector<Cand> tried;
+  const int tiles2[3][2] = {{64, 1}, {128, 1}, {256, 1}};
+  const int tiles3[3][2] = {{4, 4}, {8, 8}, {16, 16}};
+  Cand best{h->gs_ndc, h->gs_tx, h->gs_ty, 1e30f};
+  if (h->opts.beta_T_exp != 0.0)
+    CUDA_TRY(h, launch_beta_scale(h->bscale, h->Tp, h->opts.T_ref, h->opts.beta_T_exp, h->ncells, s));
+  for (int ndc = 1; ndc <= 2; ++ndc)
+    for (int t = 0; t < 3; ++t) {
+      const int tx = dim == 3 ? tiles3[t][0] : tiles2[t][0], ty = dim == 3 ? tiles3[t][1] : tiles2[t][1];
+      build_gs(h, ndc, tx, ty);
+      bool dup = false;
+      for (auto& c : tried) dup |= c.ndc == h->gs_ndc && c.tx == tx && c.ty == ty;
+      if (dup) continue;
+      int rc = upload_gs(h, s);
+      if (rc) return rc;
+      SweepArgs a = sweep_args(h);
+      a.bmode = 0;
+      a.Bout = nullptr;
+      a.In = a.Ik = h->Ibuf[h->cur];
+      a.Iout = h->Ibuf[spare];
+      CUDA_TRY(h, launch_gs_sweep(a, dim, h->gs_threads, s));
+      CUDA_TRY(h, cudaEventRecord(h->ev0, s));
+      for (int r = 0; r < 3; ++r) CUDA_TRY(h, launch_gs_sweep(a, dim, h->gs_threads, s));
+      CUDA_TRY(h, cudaEventRecord(h->ev1, s));
+      CUDA_TRY(h, cudaEventSynchronize(h->ev1));
+      float ms = 0.f;
+      CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+      tried.push_back({h->gs_ndc, tx, ty, ms / 3.f});
+      if (ms / 3.f < best.ms) best = tried.back();
+    }
+  build_gs(h, best.ndc, best.tx, best.ty);
+  int rc = upload_gs(h, s);
+  if (rc) return rc;
+  drop_graphs(h);
+  char buf[128];
+  h->gs_tune_report = "directions_per_cta,tile_x,tile_y,threads,ms_per_pass\n";
+  for (auto& c : tried) {
+    snprintf(buf, sizeof buf, "%d,%d,%d,%d,%.4f\n", c.ndc, c.tx, c.ty, (h->nbp / 2) * c.ndc * std::max(1, 256 / ((h->nbp / 2) * c.ndc)), c.ms);
+    h->gs_tune_report += buf;
+  }
+  snprintf(buf, sizeof buf, "chosen,%d,%d,%d,%d\n", best.ndc, best.tx, best.ty, h->gs_threads);
+  h->gs_tune_report += buf;
+  copy_report(h->gs_tune_report, report, report_len);
+  return BTE_OK;
+}
+
+}  // namespace
+
 int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t report_len) {
   if (!h) return BTE_E_ARG;
   std::string why;
   if (!h->mem_ready || !ready_to_step(h, why)) return fail(h, BTE_E_STATE, "not ready to tune: %s", why.empty() ? "no state" : why.c_str());
   if (!(dt > 0 && std::isfinite(dt))) return fail(h, BTE_E_ARG, "dt must be > 0");
-  if (scheme != BTE_IMPLICIT_JACOBI && scheme != BTE_EXPLICIT) return fail(h, BTE_E_ARG, "unknown scheme %d", scheme);
-  int rc = ensure_coef(h, dt, scheme);
+  if (scheme != BTE_IMPLICIT_JACOBI && scheme != BTE_EXPLICIT && scheme != BTE_IMPLICIT_GS)
+    return fail(h, BTE_E_ARG, "unknown scheme %d", scheme);
+  if (scheme == BTE_IMPLICIT_GS && h->opts.precision != BTE_FP64)
+    return fail(h, BTE_E_ARG, "the sweep-ordered scheme needs FP64 storage");
+  int rc = ensure_coef(h, dt, scheme == BTE_EXPLICIT ? BTE_EXPLICIT : BTE_IMPLICIT_JACOBI);
   if (rc) return rc;
+  if (scheme == BTE_IMPLICIT_GS) return autotune_gs(h, report, report_len);
   cudaStream_t s = h->stream;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev);

@@ -49,6 +49,15 @@ struct WorkItem {
   int pad;
 };
 
+// Sweep-ordered (Gauss-Seidel) pass: one unit = the directions dir0 .. dir0+ndc-1
+// of the octant list (all with the same upwind sides) over one geometry.
+struct GsUnit {
+  int geom;
+  int dir0;  // first entry in SweepArgs::gs_dirs
+  int ndc;   // directions in this unit (<= SweepArgs::gs_ndc)
+  int pad;
+};
+
 // Per direction: bit a of `up` set when S_{d,a} > 0 (upwind neighbour on the low
 // side along axis a); mirror directions across x, y, z walls.
 struct DirInfo {
@@ -129,6 +138,13 @@ struct SweepArgs {
   int explicit_scheme;      // reduced modes compute P, Q on the fly from these:
   float dt32, rdt32;        // dt and 1/dt
   DevCounters* counters;
+  // sweep-ordered pass (scheme BTE_IMPLICIT_GS, FP64)
+  const GsUnit* gs_units;
+  const int* gs_dirs;       // direction indices grouped by octant
+  int gs_nunits;
+  int gs_ndc;               // directions per unit (the CTA layout)
+  int gs_tx, gs_ty;         // cross-section of a column tile (2-D: gs_tx cells along x)
+  const double* bscale;     // [cell] beta_b(T_p)/beta_b (beta_exp != 0), written before each pass
   ThermoTables th;
 };
 
@@ -141,6 +157,12 @@ cudaError_t launch_sweep_bf16(int pd, const SweepArgs& a, int dim, int threads, 
 struct MLPView;
 cudaError_t launch_fixup(const SweepArgs& a, const MLPView* mlp, cudaStream_t s);
 cudaError_t launch_solve_cells(const SweepArgs& a, long long ncells, cudaStream_t s);
+// sweep-ordered pass (bte_gs.cu) and its per-cell step (bte_kernels.cu): the
+// pass writes Iout; the reduction writes E_L, E_p of the stored bands to Epart
+// (partial) or solves T_p and refreshes I0 at once (whole handle)
+cudaError_t launch_gs_sweep(const SweepArgs& a, int dim, int threads, cudaStream_t s);
+cudaError_t launch_gs_reduce(const SweepArgs& a, long long ncells, cudaStream_t s);
+cudaError_t launch_beta_scale(double* out, const double* Tp, double Tref, double p, long long ncells, cudaStream_t s);
 cudaError_t launch_diffuse_ghosts(int precision, const void* I, const double* I0ref, double* I0wall, float* I0wall_dev,
                                   const DevGeom* geoms, int geom, int side, const double* S, int nd, int nbp,
                                   int nfaces, cudaStream_t s);

@@ -6,6 +6,8 @@
 //                       also refreshes their cached model and I0;
 //   solve_cells_kernel  the T_p step of a band-range handle after the caller's
 //                       all-reduce of the per-cell energy partials (Sec. 3.3);
+//   gs_reduce_kernel    per-cell energies (and the T_p step) after a
+//                       sweep-ordered pass (bte_gs.cu);
 //   init_cells / state_from_Tp / wall_I0 / wall_dev
 //                       equilibrium state, cached models and Eq. 6 ghosts;
 //   solve_TL_kernel     T_L on request (cached model first, exact otherwise);
@@ -305,67 +307,121 @@ __global__ void energy_L_kernel(const S* I, const double* I0ref, double* EL, con
   }
 }
 
-// Temperature step of a band-range handle after the caller's all-reduce: one
-// warp per cell; E_L, E_p from Epart, the T_p equation on the cached quadratic
-// model of all bands, I0 refresh of the stored bands, the rest to the fix-up.
-__global__ void solve_cells_kernel(SweepArgs a, long long ncells) {
-  const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
+// T_p step of one cell from its energies (E_L, E_p over every band), by one
+// warp: the T_p equation on the cell's cached quadratic model of all bands,
+// I0 refresh of the stored bands inside the trust radius, the rest to the
+// fix-up list.
+__device__ void solve_cell_warp(const SweepArgs& a, long long P, double EL, double Ep, int lane,
+                                unsigned long long& solves, unsigned long long& badc) {
   const int nbp = a.th.nbp;
-  unsigned long long solves = 0, badc = 0;
-  for (long long P = blockIdx.x * (long long)warps + threadIdx.x / 32; P < ncells; P += (long long)gridDim.x * warps) {
-    const double EL = a.Epart[2 * P], Ep = a.Epart[2 * P + 1];
-    const bool finite = isfinite(EL) && isfinite(Ep);
-    if (!a.solve_tp) {  // every beta_b is zero: only E_L is kept
-      if (lane == 0) {
-        a.EL[P] = EL;
-        if (!finite) ++badc;
-      }
-      continue;
-    }
-    double F = 0.0, F1 = 0.0, F2 = 0.0;
-    for (int b = lane; b < nbp; b += 32) {
-      const double ap = a.th.a_p[b];
-      F = fma(ap, a.J[(P * 3 + 0) * nbp + b], F);
-      F1 = fma(ap, a.J[(P * 3 + 1) * nbp + b], F1);
-      F2 = fma(ap, a.J[(P * 3 + 2) * nbp + b], F2);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      F += __shfl_xor_sync(0xffffffffu, F, o);
-      F1 += __shfl_xor_sync(0xffffffffu, F1, o);
-      F2 += __shfl_xor_sync(0xffffffffu, F2, o);
-    }
-    F -= Ep;
-    const double Te = a.Teval[P];
-    const double disc = F1 * F1 - 2.0 * F * F2;
-    const double delta = (disc >= 0.0 && F1 > 0.0) ? -2.0 * F / (F1 + sqrt(disc)) : -F / F1;
-    const double Tn = Te + delta;
-    const bool ok = finite && isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn;
+  const bool finite = isfinite(EL) && isfinite(Ep);
+  if (!a.solve_tp) {  // every beta_b is zero: only E_L is kept
     if (lane == 0) {
       a.EL[P] = EL;
       if (!finite) ++badc;
-      else ++solves;
-      if (finite && !ok) {
-        const unsigned k = atomicAdd(a.fix_count, 1u);
-        FixItem fi;
-        fi.P = P;
-        fi.Ep = Ep;
-        fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[P];
-        a.fix[k] = fi;
-      }
-      if (ok) a.Tp[P] = Tn;
     }
-    if (ok) {
-      const double hd2 = 0.5 * delta * delta;
-      for (int b = lane; b < a.th.nbo; b += 32) {
-        const long long j = (P * 3) * nbp + a.th.band0 + b;
-        a.I0cell[P * a.th.nbo + b] = b < a.th.nbr ? fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], delta, a.J[j])) : 0.0;
-      }
+    return;
+  }
+  double F = 0.0, F1 = 0.0, F2 = 0.0;
+  for (int b = lane; b < nbp; b += 32) {
+    const double ap = a.th.a_p[b];
+    F = fma(ap, a.J[(P * 3 + 0) * nbp + b], F);
+    F1 = fma(ap, a.J[(P * 3 + 1) * nbp + b], F1);
+    F2 = fma(ap, a.J[(P * 3 + 2) * nbp + b], F2);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    F += __shfl_xor_sync(0xffffffffu, F, o);
+    F1 += __shfl_xor_sync(0xffffffffu, F1, o);
+    F2 += __shfl_xor_sync(0xffffffffu, F2, o);
+  }
+  F -= Ep;
+  const double Te = a.Teval[P];
+  const double disc = F1 * F1 - 2.0 * F * F2;
+  const double delta = (disc >= 0.0 && F1 > 0.0) ? -2.0 * F / (F1 + sqrt(disc)) : -F / F1;
+  const double Tn = Te + delta;
+  const bool ok = finite && isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn;
+  if (lane == 0) {
+    a.EL[P] = EL;
+    if (!finite) ++badc;
+    else ++solves;
+    if (finite && !ok) {
+      const unsigned k = atomicAdd(a.fix_count, 1u);
+      FixItem fi;
+      fi.P = P;
+      fi.Ep = Ep;
+      fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[P];
+      a.fix[k] = fi;
+    }
+    if (ok) a.Tp[P] = Tn;
+  }
+  if (ok) {
+    const double hd2 = 0.5 * delta * delta;
+    for (int b = lane; b < a.th.nbo; b += 32) {
+      const long long j = (P * 3) * nbp + a.th.band0 + b;
+      a.I0cell[P * a.th.nbo + b] = b < a.th.nbr ? fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], delta, a.J[j])) : 0.0;
     }
   }
+}
+
+__device__ void flush_counters(const SweepArgs& a, int lane, unsigned long long solves, unsigned long long badc) {
   if (lane == 0 && a.counters) {
     if (solves) atomicAdd(&a.counters->solves, solves);
     if (badc) atomicAdd(&a.counters->nonfinite, badc);
   }
+}
+
+// Temperature step of a band-range handle after the caller's all-reduce: one
+// warp per cell, E_L and E_p from Epart.
+__global__ void solve_cells_kernel(SweepArgs a, long long ncells) {
+  const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
+  unsigned long long solves = 0, badc = 0;
+  for (long long P = blockIdx.x * (long long)warps + threadIdx.x / 32; P < ncells; P += (long long)gridDim.x * warps)
+    solve_cell_warp(a, P, a.Epart[2 * P], a.Epart[2 * P + 1], lane, solves, badc);
+  flush_counters(a, lane, solves, badc);
+}
+
+// Per-cell step after a sweep-ordered pass (FP64 storage): one warp per cell,
+// lanes over pairs of stored bands, directions in order:
+// G_b = sum_d w_d I^{k+1}_{d,b}, E_L = sum_b G_b / v_b, E_p = sum_b beta_b G_b / v_b
+// over the stored bands.  A band-range handle writes them to Epart for the
+// caller's all-reduce; a whole handle solves T_p and refreshes I0 at once.
+__global__ void gs_reduce_kernel(SweepArgs a, long long ncells) {
+  const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
+  const int nbo = a.th.nbo, nd = a.nd, lpc = nbo / 2;
+  const double* __restrict__ I = reinterpret_cast<const double*>(a.Iout);
+  unsigned long long solves = 0, badc = 0;
+  for (long long P = blockIdx.x * (long long)warps + threadIdx.x / 32; P < ncells; P += (long long)gridDim.x * warps) {
+    const double* row = I + P * (long long)nd * nbo;
+    double el = 0.0, ep = 0.0;
+    for (int lp = lane; lp < lpc; lp += 32) {
+      const int b0 = 2 * lp;
+      double g0 = 0.0, g1 = 0.0;
+#pragma unroll 4
+      for (int d = 0; d < nd; ++d) {
+        const double2 v = __ldcs(reinterpret_cast<const double2*>(row + (long long)d * nbo + b0));
+        const double w = a.wdir[d];
+        g0 = fma(w, v.x, g0);
+        g1 = fma(w, v.y, g1);
+      }
+      const double e0 = g0 * a.th.inv_v[b0], e1 = g1 * a.th.inv_v[b0 + 1];
+      el += e0 + e1;
+      ep = fma(a.th.beta[b0], e0, ep);
+      ep = fma(a.th.beta[b0 + 1], e1, ep);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      el += __shfl_xor_sync(0xffffffffu, el, o);
+      ep += __shfl_xor_sync(0xffffffffu, ep, o);
+    }
+    if (a.partial) {
+      if (lane == 0) {
+        a.Epart[2 * P] = el;
+        a.Epart[2 * P + 1] = ep;
+      }
+    } else {
+      solve_cell_warp(a, P, el, ep, lane, solves, badc);
+    }
+  }
+  flush_counters(a, lane, solves, badc);
 }
 
 // Diffuse wall ghosts of one side of one geometry: for every face, per band,
@@ -451,6 +507,11 @@ cudaError_t launch_diffuse_ghosts(int precision, const void* I, const double* I0
 
 cudaError_t launch_solve_cells(const SweepArgs& a, long long ncells, cudaStream_t s) {
   solve_cells_kernel<<<cell_grid(ncells / 4 + 1), 128, 0, s>>>(a, ncells);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_reduce(const SweepArgs& a, long long ncells, cudaStream_t s) {
+  gs_reduce_kernel<<<cell_grid(ncells / 8 + 1), 256, 0, s>>>(a, ncells);
   return cudaGetLastError();
 }
 

@@ -59,7 +59,7 @@ class ThreadExchange:
         return fn
 
 
-def run_ranks(wl, ranges, nsteps, ninner, precision=bte.BTE_FP64):
+def run_ranks(wl, ranges, nsteps, ninner, precision=bte.BTE_FP64, scheme=bte.BTE_IMPLICIT_JACOBI):
     x = ThreadExchange(len(ranges))
     solvers = [bte.Solver(wl, precision=precision, stream=torch.cuda.Stream(), band_range=r, exchange=x.member(i))
                for i, r in enumerate(ranges)]
@@ -67,7 +67,7 @@ def run_ranks(wl, ranges, nsteps, ninner, precision=bte.BTE_FP64):
 
     def body(i):
         try:
-            stats[i] = solvers[i].step(nsteps=nsteps, ninner=ninner)[1]
+            stats[i] = solvers[i].step(nsteps=nsteps, ninner=ninner, scheme=scheme)[1]
         except Exception as e:  # re-raised below
             errs.append(e)
             x.bar.abort()
@@ -80,11 +80,11 @@ def run_ranks(wl, ranges, nsteps, ninner, precision=bte.BTE_FP64):
     return solvers, stats, x
 
 
-def oracle_run(wl, nsteps, ninner):
+def oracle_run(wl, nsteps, ninner, scheme=O.IMPLICIT):
     g = wl.geoms[0]
     p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands)
     st = p.init_state(g.T_init)
-    p.run(st, wl.dt, nsteps, ninner)
+    p.run(st, wl.dt, nsteps, ninner, scheme)
     return p, st
 
 
@@ -118,6 +118,25 @@ def test_band_ranks_match_the_oracle(name):
     qw = sum(s.flux(0)[1] for s in solvers)
     assert np.max(np.abs(q - q_ref)) <= 1e-10 * np.max(np.abs(q_ref))
     assert np.max(np.abs(qw - qw_ref)) <= 1e-10 * np.max(np.abs(q_ref))
+    for s in solvers:
+        s.close()
+
+
+def test_sweep_ordered_band_ranks_match_the_oracle():
+    """The sweep-ordered scheme on band ranges: pass, per-cell partials,
+    exchange, cell solve, fix-up per inner iteration."""
+    mk, ranges, nsteps, ninner = CASES["cfg2_small"]
+    wl = mk()
+    solvers, stats, x = run_ranks(wl, ranges, nsteps, ninner, scheme=bte.BTE_IMPLICIT_GS)
+    _, ref = oracle_run(wl, nsteps, ninner, O.GAUSS_SEIDEL)
+    assert x.calls == [nsteps * ninner] * len(ranges)
+    assert all(s["launches"] == 4 * nsteps * ninner for s in stats)   # pass, reduction, cell solve, fix-up
+    for s in solvers:
+        for which, key in ((bte.BTE_T_LATTICE, "TL"), (bte.BTE_T_PSEUDO, "Tp")):
+            assert np.max(np.abs(s.T(0, which) - ref[key]) / ref[key]) <= 1e-12, key
+    I = ref["I"]
+    for s, (b0, b1) in zip(solvers, ranges):
+        assert np.max(np.abs(s.intensity(0) - I[:, :, b0:b1]) / np.abs(I[:, :, b0:b1])) <= 1e-11
     for s in solvers:
         s.close()
 

@@ -236,6 +236,63 @@ def test_jacobi_iterations_converge_to_dense_lu_solution():
     assert np.max(np.abs(st["I"] - x) / np.abs(x)) < 1e-13
 
 
+def _small_lu_case(all_isothermal):
+    g = W.Geometry(2, 4, 3, 1, 10e-9, 7e-9, 10e-9)
+    side = [(W.BC_ISOTHERMAL, np.full(3, 310.0)), (W.BC_ISOTHERMAL, np.full(3, 300.0))]
+    if all_isothermal:
+        g.bc = side + [(W.BC_ISOTHERMAL, np.full(4, 305.0)), (W.BC_ISOTHERMAL, np.full(4, 295.0))]
+    else:
+        g.bc = side + [(W.BC_SPECULAR, None), (W.BC_SPECULAR, None)]
+    S, w, r = O.dirs_inplane(8)
+    bands = W.make_bands(2, 0, 7)
+    bands.beta[:] = 0.0
+    p = O.Problem(g, (S, w, r), bands)
+    st = p.init_state(W.random_temperatures(12, 99, 295.0, 305.0))
+    I0w = {s: O.I0(bands, T)[0] for s, T in zip(range(4), (310.0, 300.0, 305.0, 295.0))}
+    dt = 2e-12
+    A, rhs = _assemble_backward_euler(g, S, w, r, bands, dt, st["I"].copy(), I0w)
+    return p, st, dt, np.linalg.solve(A, rhs).reshape(st["I"].shape)
+
+
+def test_gauss_seidel_iterations_converge_to_dense_lu_solution():
+    """The sweep-ordered form solves the same backward-Euler system."""
+    p, st, dt, x = _small_lu_case(all_isothermal=False)
+    p.run(st, dt, 1, 200, O.GAUSS_SEIDEL)
+    assert np.max(np.abs(st["I"] - x) / np.abs(x)) < 1e-13
+
+
+def test_one_gauss_seidel_pass_is_exact_when_every_ghost_is_fixed():
+    """Isothermal walls and beta = 0: in upwind order the system is triangular,
+    so one pass is the exact solution; one Jacobi pass is not."""
+    p, st, dt, x = _small_lu_case(all_isothermal=True)
+    stj = {k: v.copy() for k, v in st.items()}
+    p.run(st, dt, 1, 1, O.GAUSS_SEIDEL)
+    assert np.max(np.abs(st["I"] - x) / np.abs(x)) < 1e-13
+    p.run(stj, dt, 1, 1, O.IMPLICIT)
+    assert np.max(np.abs(stj["I"] - x) / np.abs(x)) > 1e-4
+
+
+def test_gauss_seidel_converges_faster_than_jacobi():
+    """Same fixed point; after a few inner iterations the sweep-ordered error
+    is the smaller one (mirror walls, scattering on)."""
+    wl = W.cfg2(9, 7)
+    g = wl.geoms[0]
+    p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands)
+    ref = p.init_state(g.T_init)
+    p.run(ref, wl.dt, 1, 200, O.GAUSS_SEIDEL)
+    ref_j = p.init_state(g.T_init)
+    p.run(ref_j, wl.dt, 1, 200, O.IMPLICIT)
+    assert np.max(np.abs(ref["Tp"] - ref_j["Tp"]) / ref["Tp"]) < 1e-13
+    for m in (2, 4, 6):
+        a = p.init_state(g.T_init)
+        b = p.init_state(g.T_init)
+        p.run(a, wl.dt, 1, m, O.GAUSS_SEIDEL)
+        p.run(b, wl.dt, 1, m, O.IMPLICIT)
+        err_gs = np.max(np.abs(a["I"] - ref["I"]))
+        err_j = np.max(np.abs(b["I"] - ref["I"]))
+        assert err_gs < 0.5 * err_j, (m, err_gs, err_j)
+
+
 # ------------------------------------------------------ physics invariants
 def test_uniform_equilibrium_stays_at_round_off():
     wl = W.cfg1()
