@@ -282,6 +282,62 @@ def run_variants(peaks):
     return out
 
 
+def run_gs_variant(peaks):
+    """Sweep-ordered (Gauss-Seidel) against point-Jacobi inner iterations on the
+    128x128 x 400 x 55 FP64 workload with dt = 10 ps (transport CFL up to 7.7,
+    where the inner iterations converge slowly).  Per scheme: the device time of
+    one inner iteration (3 steps x 15 inner iterations, CUDA graph, autotuned),
+    the T_L error of one step after m inner iterations against a 60-iteration
+    sweep-ordered step, and from both the time of a step that reaches a
+    tolerance."""
+    import numpy as np
+    import torch
+    from paper_2305_19400_gb300 import bte, workloads as W
+    dt = 1e-11
+    wl = W.cfg2()
+    g = wl.geoms[0]
+    GS, JAC = bte.BTE_IMPLICIT_GS, bte.BTE_IMPLICIT_JACOBI
+    ref = bte.Solver(wl)
+    ref.step(nsteps=1, ninner=60, dt=dt, scheme=GS, want_stats=False)
+    T_ref = ref.T(0, bte.BTE_T_LATTICE)
+    ref.close()
+    del ref
+    ms_list = (2, 4, 6, 8, 10, 12, 16, 20, 25, 30, 35, 40, 50)
+    res = {}
+    for name, sch in (("sweep_ordered", GS), ("jacobi", JAC)):
+        s = bte.Solver(wl, use_graph=True, autotune=True)
+        s.step(nsteps=1, ninner=15, dt=dt, scheme=sch, want_stats=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.step(nsteps=3, ninner=15, dt=dt, scheme=sch, want_stats=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_inner = e0.elapsed_time(e1) / 45
+        errs = {}
+        for m in ms_list:
+            bte.bte_set_initial(s.h, 0, None, g.T_init)
+            s.step(nsteps=1, ninner=m, dt=dt, scheme=sch, want_stats=False)
+            errs[m] = float(np.max(np.abs(s.T(0, bte.BTE_T_LATTICE) - T_ref)))
+        res[name] = {"ms_per_inner_iteration": ms_inner, "updates_per_s": wl.dof / (ms_inner * 1e-3),
+                     "max_abs_dTL_K_after_m": errs}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    for tol in (1e-4, 1e-6):
+        for name in res:
+            m = next((m for m in ms_list if res[name]["max_abs_dTL_K_after_m"][m] <= tol), None)
+            res[name][f"inner_iterations_to_{tol:g}K"] = m
+            res[name][f"ms_per_step_to_{tol:g}K"] = None if m is None else m * res[name]["ms_per_inner_iteration"]
+    gs = res["sweep_ordered"]
+    fl = gs["updates_per_s"] * FLOPS_PER_UPDATE_2D_LATER
+    return {"workload": "fp64_sweep_ordered_vs_jacobi_2d_128x128_dt10ps", "dtype": "f64", "value": gs["updates_per_s"],
+            "unit": UNIT, "dt_s": dt, "schemes": res,
+            "roofline": {"bound": "alu", "achieved": fl / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                         "frac": fl / FP64_PEAK_FLOPS}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -411,6 +467,7 @@ def main():
     variants = None
     if world == 1 and not args.no_variants:
         variants = run_variants(peaks)
+        variants.append(run_gs_variant(peaks))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "strong" if partitioned else "weak",

@@ -380,48 +380,108 @@ __global__ void solve_cells_kernel(SweepArgs a, long long ncells) {
   flush_counters(a, lane, solves, badc);
 }
 
-// Per-cell step after a sweep-ordered pass (FP64 storage): one warp per cell,
-// lanes over pairs of stored bands, directions in order:
+// Per-cell step after a sweep-ordered pass (FP64 storage): one CTA of 8 warps
+// per cell.  Warp w sums the directions [w nd/8, (w+1) nd/8) for every stored
+// band (lanes over band pairs); the 8 partials are added in warp order in
+// shared memory (deterministic), then warp 0 forms
 // G_b = sum_d w_d I^{k+1}_{d,b}, E_L = sum_b G_b / v_b, E_p = sum_b beta_b G_b / v_b
-// over the stored bands.  A band-range handle writes them to Epart for the
-// caller's all-reduce; a whole handle solves T_p and refreshes I0 at once.
-__global__ void gs_reduce_kernel(SweepArgs a, long long ncells) {
-  const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
+// and either writes them to Epart (band-range handle, for the caller's
+// all-reduce) or solves T_p and refreshes I0 at once (whole handle).
+// Within a warp the sums over a run of equal-weight directions are exact
+// 64-bit fixed-point additions on the integer pipe (unit 2^(E-50) for the
+// cell's I0 of exponent E; a value up to 32 I0 adds at most 2^55, so a run of
+// 256 cannot overflow), closed by one FP64 FMA (sum x w x unit).  Values
+// beyond that range (or negative, NaN) take the FP64 FMA directly.
+constexpr int kRedWarps = 8;
+
+__global__ void __launch_bounds__(256, 4) gs_reduce_kernel(SweepArgs a, long long ncells) {
+  extern __shared__ double gpart[];  // [kRedWarps][nbo]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nbo = a.th.nbo, nd = a.nd, lpc = nbo / 2;
+  const int d0 = (int)((long long)wid * nd / kRedWarps), d1 = (int)((long long)(wid + 1) * nd / kRedWarps);
   const double* __restrict__ I = reinterpret_cast<const double*>(a.Iout);
   unsigned long long solves = 0, badc = 0;
-  for (long long P = blockIdx.x * (long long)warps + threadIdx.x / 32; P < ncells; P += (long long)gridDim.x * warps) {
+  for (long long P = blockIdx.x; P < ncells; P += gridDim.x) {
     const double* row = I + P * (long long)nd * nbo;
-    double el = 0.0, ep = 0.0;
     for (int lp = lane; lp < lpc; lp += 32) {
       const int b0 = 2 * lp;
-      double g0 = 0.0, g1 = 0.0;
-#pragma unroll 4
-      for (int d = 0; d < nd; ++d) {
-        const double2 v = __ldcs(reinterpret_cast<const double2*>(row + (long long)d * nbo + b0));
-        const double w = a.wdir[d];
-        g0 = fma(w, v.x, g0);
-        g1 = fma(w, v.y, g1);
+      double G[2] = {0.0, 0.0};
+      unsigned long long facc[2] = {0ull, 0ull};
+      long long fsc[2];
+      int fe0[2];
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int e0 = (int)((unsigned long long)__double_as_longlong(a.I0cell[P * nbo + b0 + v]) >> 52);
+        const bool on = e0 >= 200 && e0 <= 1900;
+        fe0[v] = on ? e0 + 4 : -1;
+        fsc[v] = on ? (long long)(e0 - 1073) * (1LL << 52) : 0;
       }
-      const double e0 = g0 * a.th.inv_v[b0], e1 = g1 * a.th.inv_v[b0 + 1];
-      el += e0 + e1;
-      ep = fma(a.th.beta[b0], e0, ep);
-      ep = fma(a.th.beta[b0 + 1], e1, ep);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      el += __shfl_xor_sync(0xffffffffu, el, o);
-      ep += __shfl_xor_sync(0xffffffffu, ep, o);
-    }
-    if (a.partial) {
-      if (lane == 0) {
-        a.Epart[2 * P] = el;
-        a.Epart[2 * P + 1] = ep;
+      long long wrun = d0 < d1 ? __double_as_longlong(a.wdir[d0]) : 0;
+      int nrun = 0;
+      auto add = [&](double2 x, int d) {
+        const long long wb = __double_as_longlong(a.wdir[d]);
+        if (wb != wrun || nrun == 256) {  // close the run: sum x (w x unit)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            if (facc[v] != 0ull) G[v] = fma(__ull2double_rn(facc[v]), __longlong_as_double(wrun + fsc[v]), G[v]);
+            facc[v] = 0ull;
+          }
+          wrun = wb;
+          nrun = 0;
+        }
+        ++nrun;
+        const double xv[2] = {x.x, x.y};
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const unsigned long long rb = (unsigned long long)__double_as_longlong(xv[v]);
+          const int e = (int)(rb >> 52);  // sign bit included: negative values take the FP64 path
+          const unsigned long long m = ((rb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 2;
+          const int sh = e == 0 ? 63 : min(fe0[v] - e, 63);  // zero (and subnormal) adds nothing
+          if (sh >= 0) facc[v] += m >> sh;
+          else G[v] = fma(a.wdir[d], xv[v], G[v]);
+        }
+      };
+      int d = d0;
+      for (; d + 4 <= d1; d += 4) {
+        double2 x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = __ldcs(reinterpret_cast<const double2*>(row + (long long)(d + u) * nbo + b0));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) add(x[u], d + u);
       }
-    } else {
-      solve_cell_warp(a, P, el, ep, lane, solves, badc);
+      for (; d < d1; ++d) add(__ldcs(reinterpret_cast<const double2*>(row + (long long)d * nbo + b0)), d);
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        if (facc[v] != 0ull) G[v] = fma(__ull2double_rn(facc[v]), __longlong_as_double(wrun + fsc[v]), G[v]);
+        gpart[wid * nbo + b0 + v] = G[v];
+      }
     }
+    __syncthreads();
+    if (wid == 0) {
+      double el = 0.0, ep = 0.0;
+      for (int b = lane; b < nbo; b += 32) {
+        double G = gpart[b];
+        for (int w = 1; w < kRedWarps; ++w) G += gpart[w * nbo + b];
+        const double e = G * a.th.inv_v[b];
+        el += e;
+        ep = fma(a.th.beta[b], e, ep);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        el += __shfl_xor_sync(0xffffffffu, el, o);
+        ep += __shfl_xor_sync(0xffffffffu, ep, o);
+      }
+      if (a.partial) {
+        if (lane == 0) {
+          a.Epart[2 * P] = el;
+          a.Epart[2 * P + 1] = ep;
+        }
+      } else {
+        solve_cell_warp(a, P, el, ep, lane, solves, badc);
+      }
+    }
+    __syncthreads();
   }
-  flush_counters(a, lane, solves, badc);
+  if (wid == 0) flush_counters(a, lane, solves, badc);
 }
 
 // Diffuse wall ghosts of one side of one geometry: for every face, per band,
@@ -511,7 +571,8 @@ cudaError_t launch_solve_cells(const SweepArgs& a, long long ncells, cudaStream_
 }
 
 cudaError_t launch_gs_reduce(const SweepArgs& a, long long ncells, cudaStream_t s) {
-  gs_reduce_kernel<<<cell_grid(ncells / 8 + 1), 256, 0, s>>>(a, ncells);
+  const int grid = (int)std::min<long long>(std::max(ncells, 1LL), 152LL * 64);
+  gs_reduce_kernel<<<grid, 32 * kRedWarps, (size_t)kRedWarps * a.th.nbo * sizeof(double), s>>>(a, ncells);
   return cudaGetLastError();
 }
 
