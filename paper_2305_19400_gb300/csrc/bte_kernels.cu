@@ -431,14 +431,24 @@ __global__ void __launch_bounds__(256, 4) gs_reduce_kernel(SweepArgs a, long lon
         }
         ++nrun;
         const double xv[2] = {x.x, x.y};
+        bool big = false;
 #pragma unroll
         for (int v = 0; v < 2; ++v) {
           const unsigned long long rb = (unsigned long long)__double_as_longlong(xv[v]);
           const int e = (int)(rb >> 52);  // sign bit included: negative values take the FP64 path
           const unsigned long long m = ((rb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 2;
           const int sh = e == 0 ? 63 : min(fe0[v] - e, 63);  // zero (and subnormal) adds nothing
-          if (sh >= 0) facc[v] += m >> sh;
-          else G[v] = fma(a.wdir[d], xv[v], G[v]);
+          facc[v] += sh >= 0 ? (m >> sh) : 0ull;
+          big |= sh < 0;
+        }
+        // rare: a value beyond the fixed-point range (a warp-uniform branch, so
+        // no FP64 instruction is issued in the common case)
+        if (__any_sync(__activemask(), big)) {
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            const int e = (int)((unsigned long long)__double_as_longlong(xv[v]) >> 52);
+            if (e != 0 && fe0[v] - e < 0) G[v] = fma(a.wdir[d], xv[v], G[v]);
+          }
         }
       };
       int d = d0;
