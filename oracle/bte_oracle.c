@@ -663,3 +663,204 @@ int orc_wall_I0(const orc_problem* p, double* out) {
   free(w);
   return 0;
 }
+
+/* ======================================================================== */
+/* Unstructured meshes (Sec. 3.1, Eq. 5 with the face sum written out; Sec.  */
+/* 3.3 mesh input).  A mesh is a face list: cells with volumes V_P, faces     */
+/* with an owner, a neighbour (-1 on the boundary) and the area vector n A    */
+/* pointing out of the owner.  For (P, d, b) each face f of P has            */
+/*   g_f = (S_d . n_f A_f) / (w_d V_P)   (n_f out of P),                      */
+/* outflow (g_f > 0) uses the cell's own value and inflow (g_f < 0) the       */
+/* upwind one: the neighbour's, or at a boundary face its ghost (isothermal:  */
+/* I0_b(T_face); mirror: the cell's own value in the direction reflected     */
+/* across the face, whose normal must lie along an axis; diffuse: every       */
+/* incoming direction gets sum_out (S.n) I / sum_in |S.n| of the cell).       */
+/* Implicit (one point-Jacobi sweep of the inner iteration):                  */
+/*   I^{k+1} = [I^n/dt + beta I0 + v sum_{g<0} |g| I_up^k] / [1/dt + beta + v sum_{g>0} g] */
+/* Explicit: I^{n+1} = I^n + dt [beta (I0 - I^n) - v sum_f g_f I_f^n].       */
+/* The problem's direction and band tables are used; its grid fields not.     */
+/* ======================================================================== */
+typedef struct {
+  int dim;
+  long nc, nf;
+  const double* vol;   /* [nc] */
+  const long* owner;   /* [nf] */
+  const long* nbr;     /* [nf] -1 on the boundary */
+  const double* nA;    /* [nf][3] */
+  const int* btype;    /* [nf] ORC_* on boundary faces */
+  const double* Twall; /* [nf] isothermal face temperature */
+} orc_umesh;
+
+/* cell -> faces (CSR), built once per call that needs it */
+static void um_cell_faces(const orc_umesh* m, long** ptr_out, long** list_out) {
+  long* ptr = (long*)calloc((size_t)m->nc + 1, sizeof(long));
+  long* list = (long*)malloc(sizeof(long) * (size_t)(2 * m->nf));
+  for (long f = 0; f < m->nf; ++f) {
+    ptr[m->owner[f] + 1]++;
+    if (m->nbr[f] >= 0) ptr[m->nbr[f] + 1]++;
+  }
+  for (long P = 0; P < m->nc; ++P) ptr[P + 1] += ptr[P];
+  long* fill = (long*)calloc((size_t)m->nc, sizeof(long));
+  for (long f = 0; f < m->nf; ++f) {
+    list[ptr[m->owner[f]] + fill[m->owner[f]]++] = f;
+    if (m->nbr[f] >= 0) list[ptr[m->nbr[f]] + fill[m->nbr[f]]++] = f;
+  }
+  free(fill);
+  *ptr_out = ptr;
+  *list_out = list;
+}
+
+/* axis of a boundary face's normal (the largest component) */
+static int um_axis(const orc_umesh* m, long f) {
+  const double* a = m->nA + 3 * f;
+  int ax = 0;
+  for (int k = 1; k < 3; ++k)
+    if (fabs(a[k]) > fabs(a[ax])) ax = k;
+  return ax;
+}
+
+/* ghost value of boundary face f (owner P) for incoming direction d, band b */
+static double um_ghost(const orc_problem* p, const orc_umesh* m, const double* Isrc, const double* I0w, long f, int d,
+                       int b) {
+  int nd = p->nd, nb = p->nb;
+  long P = m->owner[f];
+  if (m->btype[f] == ORC_ISOTHERMAL) return I0w[f * nb + b];
+  if (m->btype[f] == ORC_DIFFUSE) {
+    const double* n = m->nA + 3 * f;
+    double num = 0.0, den = 0.0;
+    for (int e = 0; e < nd; ++e) {
+      double sn = p->S[3 * e] * n[0] + p->S[3 * e + 1] * n[1] + p->S[3 * e + 2] * n[2];
+      if (sn > 0) num += sn * Isrc[P * nd * nb + (long)e * nb + b];
+      else den -= sn;
+    }
+    return num / den;
+  }
+  int ax = um_axis(m, f);
+  const int* r = ax == 0 ? p->rx : (ax == 1 ? p->ry : p->rz);
+  return Isrc[P * nd * nb + (long)r[d] * nb + b];
+}
+
+static double um_update_one(const orc_problem* p, const orc_umesh* m, const long* fptr, const long* flist, double dt,
+                            int scheme, const double* In, const double* Ik, const double* I0, const double* I0w, long P,
+                            int d, int b, double bscale) {
+  int nd = p->nd, nb = p->nb;
+  double beta = p->beta[b] * bscale, v = p->vg[b];
+  double in = In[P * nd * nb + (long)d * nb + b], i0 = I0[P * nb + b];
+  const double* S = p->S + 3 * d;
+  const double* Isrc = scheme == ORC_EXPLICIT ? In : Ik;
+  double inflow = 0.0, gout = 0.0, flux = 0.0;
+  for (long q = fptr[P]; q < fptr[P + 1]; ++q) {
+    long f = flist[q];
+    double sgn = m->owner[f] == P ? 1.0 : -1.0;
+    const double* n = m->nA + 3 * f;
+    double g = sgn * (S[0] * n[0] + S[1] * n[1] + S[2] * n[2]) / (p->w[d] * m->vol[P]);
+    if (g > 0) {
+      gout += g;
+      flux += g * in;
+    } else if (g < 0) {
+      long nbc = m->owner[f] == P ? m->nbr[f] : m->owner[f];
+      double up = nbc >= 0 ? Isrc[nbc * nd * nb + (long)d * nb + b] : um_ghost(p, m, Isrc, I0w, f, d, b);
+      inflow += -g * up;
+      flux += g * up;
+    }
+  }
+  if (scheme == ORC_EXPLICIT) return in + dt * (beta * (i0 - in) - v * flux);
+  return (in / dt + beta * i0 + v * inflow) / (1.0 / dt + beta + v * gout);
+}
+
+double orc_umesh_update_one(const orc_problem* p, const orc_umesh* m, double dt, int scheme, const double* In,
+                            const double* Ik, const double* I0, const double* I0w, long P, int d, int b) {
+  long *fptr, *flist;
+  um_cell_faces(m, &fptr, &flist);
+  double r = um_update_one(p, m, fptr, flist, dt, scheme, In, Ik, I0, I0w, P, d, b, 1.0);
+  free(fptr);
+  free(flist);
+  return r;
+}
+
+/* I0_b(T_face) of every isothermal boundary face: out[nf][nb] (0 elsewhere) */
+void orc_umesh_wall_I0(const orc_problem* p, const orc_umesh* m, double* out) {
+  for (long f = 0; f < m->nf; ++f) {
+    if (m->nbr[f] < 0 && m->btype[f] == ORC_ISOTHERMAL)
+      orc_I0(p->nb, p->wlo, p->whi, p->vg, p->g, p->ngauss, p->glx, p->glw, m->Twall[f], out + f * p->nb, NULL);
+    else
+      for (int b = 0; b < p->nb; ++b) out[f * p->nb + b] = 0.0;
+  }
+}
+
+/* The time loop of orc_run on an unstructured mesh (implicit point-Jacobi
+ * inner iterations or explicit steps), the same reduction, temperature solves
+ * and I0 refresh per cell.  Returns the bisection fallbacks, -1 on an
+ * unsolvable cell. */
+long orc_umesh_run(const orc_problem* p, const orc_umesh* m, double dt, int nsteps, int ninner, int scheme, double* I,
+                   double* Tp, double* TL, double* I0) {
+  long nc = m->nc;
+  int nd = p->nd, nb = p->nb;
+  size_t n = (size_t)nc * nd * nb;
+  double* In = (double*)malloc(n * sizeof(double));
+  double* Inew = (double*)malloc(n * sizeof(double));
+  double* I0w = (double*)malloc((size_t)(m->nf > 0 ? m->nf : 1) * nb * sizeof(double));
+  long *fptr, *flist;
+  um_cell_faces(m, &fptr, &flist);
+  orc_umesh_wall_I0(p, m, I0w);
+  long fallbacks = 0, bad = 0;
+  if (scheme == ORC_EXPLICIT) ninner = 1;
+  for (int step = 0; step < nsteps; ++step) {
+    memcpy(In, I, n * sizeof(double));
+    for (int k = 0; k < ninner; ++k) {
+#pragma omp parallel for schedule(static)
+      for (long P = 0; P < nc; ++P) {
+        const double bs = beta_scale(p, Tp[P]);
+        for (int d = 0; d < nd; ++d)
+          for (int b = 0; b < nb; ++b)
+            Inew[P * nd * nb + (long)d * nb + b] = um_update_one(p, m, fptr, flist, dt, scheme, In, I, I0, I0w, P, d, b, bs);
+      }
+#pragma omp parallel for schedule(static) reduction(+ : fallbacks, bad)
+      for (long P = 0; P < nc; ++P) {
+        int s = orc_cell_temperatures(p, Inew + P * nd * nb, Tp[P], TL[P], &Tp[P], &TL[P]);
+        if (s < 0) bad += 1; else fallbacks += s;
+        orc_I0(nb, p->wlo, p->whi, p->vg, p->g, p->ngauss, p->glx, p->glw, Tp[P], I0 + P * nb, NULL);
+      }
+      memcpy(I, Inew, n * sizeof(double));
+    }
+  }
+  free(In);
+  free(Inew);
+  free(I0w);
+  free(fptr);
+  free(flist);
+  return bad ? -1 : fallbacks;
+}
+
+/* Heat flux: per cell q(P) = sum_b sum_d S_d I_{d,b} (3 components), and per
+ * boundary face the net heat flow out of the domain,
+ * Q_f = sum_b sum_d (S_d . n_f A_f) I_face (own value leaving, ghost entering),
+ * 0 on interior faces. */
+void orc_umesh_flux(const orc_problem* p, const orc_umesh* m, const double* I, double* q, double* Qf) {
+  int nd = p->nd, nb = p->nb;
+  double* I0w = (double*)malloc((size_t)(m->nf > 0 ? m->nf : 1) * nb * sizeof(double));
+  orc_umesh_wall_I0(p, m, I0w);
+  for (long P = 0; P < m->nc; ++P)
+    for (int c = 0; c < 3; ++c) {
+      double s = 0.0;
+      for (int d = 0; d < nd; ++d)
+        for (int b = 0; b < nb; ++b) s += p->S[3 * d + c] * I[P * nd * nb + (long)d * nb + b];
+      q[3 * P + c] = s;
+    }
+  for (long f = 0; f < m->nf; ++f) {
+    Qf[f] = 0.0;
+    if (m->nbr[f] >= 0) continue;
+    long P = m->owner[f];
+    const double* n = m->nA + 3 * f;
+    double s = 0.0;
+    for (int d = 0; d < nd; ++d) {
+      double sn = p->S[3 * d] * n[0] + p->S[3 * d + 1] * n[1] + p->S[3 * d + 2] * n[2];
+      for (int b = 0; b < nb; ++b) {
+        double If = sn > 0 ? I[P * nd * nb + (long)d * nb + b] : um_ghost(p, m, I, I0w, f, d, b);
+        s += sn * If;
+      }
+    }
+    Qf[f] = s;
+  }
+  free(I0w);
+}

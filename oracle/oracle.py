@@ -88,6 +88,15 @@ def lib():
             L.orc_flux.argtypes = [P, dp, dp, dp]
             L.orc_wall_I0.argtypes = [P, dp]
             L.orc_num_threads.restype = C.c_int
+            U = C.POINTER(_UMesh)
+            L.orc_umesh_run.argtypes = [P, U, C.c_double, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp]
+            L.orc_umesh_run.restype = C.c_long
+            L.orc_umesh_update_one.argtypes = [P, U, C.c_double, C.c_int, dp, dp, dp, dp, C.c_long, C.c_int, C.c_int]
+            L.orc_umesh_update_one.restype = C.c_double
+            L.orc_umesh_wall_I0.argtypes = [P, U, dp]
+            L.orc_umesh_wall_I0.restype = None
+            L.orc_umesh_flux.argtypes = [P, U, dp, dp, dp]
+            L.orc_umesh_flux.restype = None
             _lib = L
     return _lib
 
@@ -286,3 +295,94 @@ class Problem:
         qw = np.zeros(6)
         lib().orc_flux(self.ptr, _dp(I), _dp(q), _dp(qw))
         return q, qw[: 2 * self.geom.dim]
+
+
+class _UMesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nc", C.c_long), ("nf", C.c_long), ("vol", C.POINTER(C.c_double)),
+                ("owner", C.POINTER(C.c_long)), ("nbr", C.POINTER(C.c_long)), ("nA", C.POINTER(C.c_double)),
+                ("btype", C.POINTER(C.c_int)), ("Twall", C.POINTER(C.c_double))]
+
+
+class UMeshProblem:
+    """An unstructured mesh (paper_2305_19400_gb300.mesh.UMesh face list) with
+    its direction set, bands and boundary conditions.
+
+    bc: {tag: (kind, T)} with kind ISOTHERMAL (T a float, or an array over the
+    mesh's faces indexed by face id), SPECULAR or DIFFUSE (T ignored).  The
+    direction and band tables live in a Problem on a one-cell grid."""
+
+    def __init__(self, mesh, dirs, bands, bc, ngauss: int = 16, newton_rtol: float = 1e-14, newton_maxit: int = 50,
+                 beta_exp: float = 0.0, beta_Tref: float = 300.0):
+        class _G:  # one-cell placeholder grid for the tables
+            pass
+        g = _G()
+        g.dim, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz = mesh.dim, 1, 1, 1, 1.0, 1.0, 1.0
+        g.bc = [(SPECULAR, None)] * (2 * mesh.dim)
+        self.tables = Problem(g, dirs, bands, ngauss, newton_rtol, newton_maxit, beta_exp, beta_Tref)
+        self.mesh = mesh
+        self.nd, self.nb, self.nc = self.tables.nd, self.tables.nb, mesh.ncells
+        nf = mesh.nfaces
+        self.vol = np.ascontiguousarray(mesh.volume, dtype=np.float64)
+        self.owner = np.ascontiguousarray(mesh.owner, dtype=np.int64)
+        self.nbr = np.ascontiguousarray(mesh.neighbor, dtype=np.int64)
+        self.nA = np.ascontiguousarray(mesh.nA, dtype=np.float64)
+        self.btype = np.full(nf, SPECULAR, dtype=np.int32)
+        self.Twall = np.zeros(nf)
+        for f in np.nonzero(self.nbr < 0)[0]:
+            kind, T = bc[int(mesh.tag[f])]
+            self.btype[f] = kind
+            if kind == ISOTHERMAL:
+                self.Twall[f] = T if np.isscalar(T) else T[f]
+        m = _UMesh()
+        m.dim, m.nc, m.nf = mesh.dim, self.nc, nf
+        m.vol, m.nA, m.Twall = _dp(self.vol), _dp(self.nA), _dp(self.Twall)
+        m.owner = self.owner.ctypes.data_as(C.POINTER(C.c_long))
+        m.nbr = self.nbr.ctypes.data_as(C.POINTER(C.c_long))
+        m.btype = _ip(self.btype)
+        self._m = m
+
+    @property
+    def ptr(self):
+        return C.byref(self._m)
+
+    def init_state(self, T_cells):
+        T = np.ascontiguousarray(np.broadcast_to(np.asarray(T_cells, dtype=np.float64), (self.nc,)))
+        st = {"I": np.zeros((self.nc, self.nd, self.nb)), "Tp": T.copy(), "TL": T.copy(),
+              "I0": np.zeros((self.nc, self.nb))}
+        for P in range(self.nc):
+            st["I0"][P] = I0(_BandView(self.tables), T[P], len(self.tables.glx))[0]
+            st["I"][P] = st["I0"][P][None, :]
+        return st
+
+    def run(self, st, dt, nsteps, ninner, scheme=IMPLICIT) -> int:
+        r = lib().orc_umesh_run(self.tables.ptr, self.ptr, float(dt), int(nsteps), int(ninner), int(scheme),
+                                _dp(st["I"]), _dp(st["Tp"]), _dp(st["TL"]), _dp(st["I0"]))
+        if r < 0:
+            raise RuntimeError("oracle: a cell has no temperature in [1, 5000] K")
+        return int(r)
+
+    def wall_I0(self):
+        out = np.zeros((max(self.mesh.nfaces, 1), self.nb))
+        lib().orc_umesh_wall_I0(self.tables.ptr, self.ptr, _dp(out))
+        return out
+
+    def update_one(self, dt, scheme, In, Ik, I0cells, I0wall, P, d, b) -> float:
+        return float(lib().orc_umesh_update_one(self.tables.ptr, self.ptr, float(dt), int(scheme), _dp(In), _dp(Ik),
+                                                _dp(I0cells), _dp(I0wall), int(P), int(d), int(b)))
+
+    def flux(self, I):
+        """(q[nc, 3] per cell, Q[nfaces] net outflow per boundary face)."""
+        I = np.ascontiguousarray(I, dtype=np.float64)
+        q = np.zeros((self.nc, 3)); Q = np.zeros(self.mesh.nfaces)
+        lib().orc_umesh_flux(self.tables.ptr, self.ptr, _dp(I), _dp(q), _dp(Q))
+        return q, Q
+
+    def cell_energy(self, row):
+        return self.tables.cell_energy(row)
+
+
+class _BandView:
+    """The band arrays of a Problem in the attribute form I0() takes."""
+
+    def __init__(self, prob):
+        self.omega_lo, self.omega_hi, self.vg, self.beta, self.degeneracy = prob.bands
