@@ -1,0 +1,108 @@
+/* bte_umesh.h -- the phonon BTE hot path on unstructured meshes.
+ *
+ * The paper's discretisation (Sec. 3.1, Eq. 5) integrates the BTE over a
+ * control volume and turns the advection into a sum over the cell's faces;
+ * its meshes come from Gmsh or MEDIT files or an internal generator (Sec.
+ * 3.3).  This interface takes such a mesh as a face list and runs the same
+ * per-iteration update as bte.h on it:
+ *   for every cell P, direction d, band b and face f of P, with
+ *   g_f = (S_d . n_f A_f) / (w_d V_P) (n_f pointing out of P),
+ *   outflow faces (g_f > 0) use the cell's own value and inflow faces
+ *   (g_f < 0) the upwind value: the neighbour's, or the boundary ghost.
+ *   Implicit (one point-Jacobi sweep per inner iteration):
+ *     I^{k+1} = [I^n/dt + beta_b I0_b + v_b sum_{g<0} |g| I_up^k]
+ *               / [1/dt + beta_b + v_b sum_{g>0} g]
+ *   Explicit (Eq. 3): I^{n+1} = I^n + dt [beta_b (I0_b - I^n) - v_b sum_f g_f I_f^n].
+ * followed by the per-cell reduction, the T_p solve and the I0 refresh of
+ * bte.h (all FP64).  Storage is FP64 only.
+ *
+ * Boundary faces carry an integer tag; each tag gets one condition:
+ *   BTE_BC_ISOTHERMAL  ghost I0_b(T_face) (Eq. 6);
+ *   BTE_BC_SPECULAR    ghost = the cell's own value in the direction mirrored
+ *                      across the face (Eq. 6); every face of the tag must be
+ *                      normal to a coordinate axis (the direction sets are
+ *                      mirror-symmetric only across the axis planes);
+ *   BTE_BC_DIFFUSE     every incoming direction gets
+ *                      sum_out (S.n) I / sum_in |S.n| of the cell (zero net flux).
+ *
+ * Call order: bte_umesh_create -> bte_umesh_set_bands -> bte_umesh_set_bc
+ * (every boundary tag) -> bte_umesh_set_initial -> bte_umesh_step / getters.
+ * Every function returns a BTE_* status of bte.h (0 on success) and leaves a
+ * message for bte_umesh_last_error.  Device memory is allocated by the
+ * handle (cudaMalloc) and freed by bte_umesh_destroy.
+ */
+#ifndef BTE_UMESH_H
+#define BTE_UMESH_H
+
+#include "bte.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bte_umesh_ctx* bte_umesh;
+
+/* A mesh as a face list (host arrays, copied by bte_umesh_create).
+ *  dim        2 (areas and edge lengths per unit depth, nA[f][2] = 0) or 3.
+ *  volume     [ncells] cell volumes (> 0).
+ *  owner      [nfaces] cell that owns the face (0 <= owner < ncells).
+ *  neighbor   [nfaces] the other cell, or -1 on the boundary.
+ *  nA         [nfaces][3] area vector, pointing out of the owner.
+ *  tag        [nfaces] boundary tag (>= 0) of boundary faces; ignored on
+ *             interior faces.
+ * A cell may have at most 64 faces. */
+typedef struct {
+  int dim;
+  long long ncells, nfaces;
+  const double* volume;
+  const long long* owner;
+  const long long* neighbor;
+  const double* nA;
+  const int* tag;
+} bte_umesh_desc;
+
+/* Creates a handle.  opts: as in bte.h (precision must be BTE_FP64; learned
+ * and beta_T_exp must be 0); may be NULL for the defaults.  *out receives
+ * the handle, NULL on failure (message in bte_umesh_last_error(NULL)). */
+int bte_umesh_create(const bte_umesh_desc* mesh, const bte_opts* opts, bte_umesh* out);
+
+/* Band table, as bte_set_bands. */
+int bte_umesh_set_bands(bte_umesh u, int nb, const double* omega_lo, const double* omega_hi, const double* vg,
+                        const double* beta, const double* degeneracy);
+
+/* Condition of every boundary face with tag `tag`.  type: BTE_BC_ISOTHERMAL
+ * (T_faces: host [nfaces] temperatures indexed by face id, read on this
+ * tag's faces, or NULL for T_uniform), BTE_BC_SPECULAR or BTE_BC_DIFFUSE
+ * (T ignored).  A tag no boundary face carries returns BTE_E_ARG. */
+int bte_umesh_set_bc(bte_umesh u, int tag, int type, const double* T_faces, double T_uniform);
+
+/* Equilibrium initial state at T_cells (host [ncells], or NULL for T_uniform). */
+int bte_umesh_set_initial(bte_umesh u, const double* T_cells, double T_uniform);
+
+/* nsteps time steps of dt [s]; scheme BTE_IMPLICIT_JACOBI (ninner inner
+ * iterations) or BTE_EXPLICIT (ninner ignored).  Each inner iteration is a
+ * sweep kernel, the per-cell step and the fix-up (and one kernel per tag
+ * with diffuse faces).  stats: as bte_step, may be NULL. */
+int bte_umesh_step(bte_umesh u, double dt, int nsteps, int ninner, int scheme, bte_stats* stats);
+
+/* Cell temperatures (BTE_T_PSEUDO or BTE_T_LATTICE) into out: ncells doubles,
+ * host (on_device = 0) or device memory (1). */
+int bte_umesh_get_T(bte_umesh u, int which, double* out, int on_device);
+
+/* Intensities into host out[ncells][nd][nb]. */
+int bte_umesh_get_intensity(bte_umesh u, double* out);
+
+/* Heat flux: q (host [ncells][3], may be NULL) = sum_b sum_d S_d I_{d,b} per
+ * cell; Q (host [nfaces], may be NULL) = the net heat flow out through each
+ * boundary face, sum_b sum_d (S_d . n_f A_f) I_face (own value leaving,
+ * ghost entering), 0 on interior faces. */
+int bte_umesh_get_flux(bte_umesh u, double* q, double* Q);
+
+const char* bte_umesh_last_error(bte_umesh u);
+void bte_umesh_destroy(bte_umesh u);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTE_UMESH_H */

@@ -20,7 +20,7 @@ BTE_E = {-1: "BTE_E_ARG", -2: "BTE_E_STATE", -3: "BTE_E_CUDA", -4: "BTE_E_NOMEM"
          -6: "BTE_E_TIMEOUT", -7: "BTE_E_EXCHANGE"}
 BTE_DIRS_INPLANE, BTE_DIRS_POLAR_AZIM = 0, 1
 BTE_FP64, BTE_FP32, BTE_BF16 = 0, 1, 2
-BTE_BC_ISOTHERMAL, BTE_BC_SPECULAR = 0, 1
+BTE_BC_ISOTHERMAL, BTE_BC_SPECULAR, BTE_BC_DIFFUSE = 0, 1, 2
 BTE_IMPLICIT_JACOBI, BTE_EXPLICIT, BTE_IMPLICIT_GS = 0, 1, 2
 BTE_T_PSEUDO, BTE_T_LATTICE = 0, 1
 
@@ -46,7 +46,13 @@ class bte_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-# Every symbol include/bte.h declares, with its ctypes signature.
+class bte_umesh_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("ncells", C.c_longlong), ("nfaces", C.c_longlong),
+                ("volume", C.POINTER(C.c_double)), ("owner", C.POINTER(C.c_longlong)),
+                ("neighbor", C.POINTER(C.c_longlong)), ("nA", C.POINTER(C.c_double)), ("tag", C.POINTER(C.c_int))]
+
+
+# Every symbol include/bte.h and include/bte_umesh.h declare, with its ctypes signature.
 _dp, _ip, _vp, _h = C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p, C.c_void_p
 # int (*)(double* buf, long long count, void* cuda_stream, void* user)
 bte_allreduce_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p)
@@ -76,6 +82,16 @@ SIGNATURES = {
     "bte_solve_T": (C.c_int, [_h, _dp, _dp, C.c_int, C.c_int, _dp, _ip]),
     "bte_destroy": (C.c_int, [_h]),
     "bte_last_error": (C.c_char_p, [_h]),
+    "bte_umesh_create": (C.c_int, [C.POINTER(bte_umesh_desc), C.POINTER(bte_opts), C.POINTER(_h)]),
+    "bte_umesh_set_bands": (C.c_int, [_h, C.c_int, _dp, _dp, _dp, _dp, _dp]),
+    "bte_umesh_set_bc": (C.c_int, [_h, C.c_int, C.c_int, _dp, C.c_double]),
+    "bte_umesh_set_initial": (C.c_int, [_h, _dp, C.c_double]),
+    "bte_umesh_step": (C.c_int, [_h, C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(bte_stats)]),
+    "bte_umesh_get_T": (C.c_int, [_h, C.c_int, _vp, C.c_int]),
+    "bte_umesh_get_intensity": (C.c_int, [_h, _dp]),
+    "bte_umesh_get_flux": (C.c_int, [_h, _dp, _dp]),
+    "bte_umesh_last_error": (C.c_char_p, [_h]),
+    "bte_umesh_destroy": (None, [_h]),
 }
 
 _lib = None
@@ -393,3 +409,90 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- unstructured meshes
+def _ucheck(u, rc):
+    if rc < 0:
+        msg = lib().bte_umesh_last_error(u)
+        raise BTEError(rc, msg.decode() if msg else "")
+    return rc
+
+
+class UMeshSolver:
+    """Marshals an unstructured mesh (paper_2305_19400_gb300.mesh.UMesh face
+    list), a direction set and a band table into the bte_umesh_* calls.
+
+    bc: {tag: (kind, T)} with kind BTE_BC_ISOTHERMAL (T a float, or an array
+    over the mesh's faces indexed by face id), BTE_BC_SPECULAR or
+    BTE_BC_DIFFUSE (T ignored)."""
+
+    def __init__(self, mesh, dirs, bands, bc, T_init=None, stream=None, n_gauss=16):
+        import torch
+        o = bte_default_opts()
+        if dirs.kind == "inplane":
+            o.dir_kind, o.n_inplane = BTE_DIRS_INPLANE, dirs.n_inplane
+        else:
+            o.dir_kind, o.n_polar, o.n_azim = BTE_DIRS_POLAR_AZIM, dirs.n_polar, dirs.n_azim
+        o.n_gauss = n_gauss
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        o.cuda_stream = self.stream.cuda_stream
+        self.mesh, self.dirs, self.bands = mesh, dirs, bands
+        self._keep = [np.ascontiguousarray(mesh.volume, dtype=np.float64),
+                      np.ascontiguousarray(mesh.owner, dtype=np.int64),
+                      np.ascontiguousarray(mesh.neighbor, dtype=np.int64),
+                      np.ascontiguousarray(mesh.nA, dtype=np.float64),
+                      np.ascontiguousarray(mesh.tag, dtype=np.int32)]
+        vol, own, nbr, nA, tag = self._keep
+        d = bte_umesh_desc()
+        d.dim, d.ncells, d.nfaces = mesh.dim, mesh.ncells, mesh.nfaces
+        d.volume = vol.ctypes.data_as(_dp)
+        d.owner = own.ctypes.data_as(C.POINTER(C.c_longlong))
+        d.neighbor = nbr.ctypes.data_as(C.POINTER(C.c_longlong))
+        d.nA = nA.ctypes.data_as(_dp)
+        d.tag = tag.ctypes.data_as(_ip)
+        h = C.c_void_p()
+        _ucheck(None, lib().bte_umesh_create(C.byref(d), C.byref(o), C.byref(h)))
+        self.h = h
+        b = bands
+        arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (b.omega_lo, b.omega_hi, b.vg, b.beta, b.degeneracy)]
+        _ucheck(h, lib().bte_umesh_set_bands(h, len(arrs[2]), *(a.ctypes.data_as(_dp) for a in arrs)))
+        for t, (kind, T) in bc.items():
+            if kind == BTE_BC_ISOTHERMAL and not np.isscalar(T):
+                Tf = np.ascontiguousarray(T, dtype=np.float64)
+                _ucheck(h, lib().bte_umesh_set_bc(h, int(t), kind, Tf.ctypes.data_as(_dp), 0.0))
+            else:
+                _ucheck(h, lib().bte_umesh_set_bc(h, int(t), kind, None, float(T) if T is not None else 0.0))
+        if T_init is None:
+            _ucheck(h, lib().bte_umesh_set_initial(h, None, float(mesh.T_init)))
+        else:
+            Tc = np.ascontiguousarray(np.broadcast_to(np.asarray(T_init, dtype=np.float64), (mesh.ncells,)))
+            _ucheck(h, lib().bte_umesh_set_initial(h, Tc.ctypes.data_as(_dp), 0.0))
+
+    def step(self, dt, nsteps, ninner, scheme=BTE_IMPLICIT_JACOBI, want_stats=True):
+        st = bte_stats() if want_stats else None
+        rc = lib().bte_umesh_step(self.h, float(dt), int(nsteps), int(ninner), int(scheme),
+                                  C.byref(st) if st is not None else None)
+        _ucheck(self.h, rc)
+        return rc, (st.as_dict() if st is not None else None)
+
+    def T(self, which=BTE_T_LATTICE):
+        out = np.zeros(self.mesh.ncells)
+        _ucheck(self.h, lib().bte_umesh_get_T(self.h, which, out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
+    def intensity(self):
+        out = np.zeros((self.mesh.ncells, self.dirs.nd, len(self.bands.vg)))
+        _ucheck(self.h, lib().bte_umesh_get_intensity(self.h, out.ctypes.data_as(_dp)))
+        return out
+
+    def flux(self):
+        q = np.zeros((self.mesh.ncells, 3))
+        Q = np.zeros(self.mesh.nfaces)
+        _ucheck(self.h, lib().bte_umesh_get_flux(self.h, q.ctypes.data_as(_dp), Q.ctypes.data_as(_dp)))
+        return q, Q
+
+    def close(self):
+        if self.h:
+            lib().bte_umesh_destroy(self.h)
+            self.h = None

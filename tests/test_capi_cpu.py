@@ -1,5 +1,6 @@
 """CPU checks of the C ABI: the library builds for sm_103a, loads, exports every
-symbol include/bte.h declares, and rejects bad arguments before touching CUDA."""
+symbol the headers in include/ declare, and rejects bad arguments before
+touching CUDA."""
 import ctypes as C
 import os
 import re
@@ -7,7 +8,8 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "bte.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
 
 
 @pytest.fixture(scope="module")
@@ -18,7 +20,7 @@ def lib():
 
 
 def declared_symbols():
-    src = open(HEADER).read()
+    src = "".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(bte_[a-zA-Z_]+)\s*\(", src)))
 
