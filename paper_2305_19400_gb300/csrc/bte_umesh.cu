@@ -35,7 +35,8 @@ namespace {
 constexpr int kMaxCellFaces = 64;
 
 struct UArgs {
-  const double* In;
+  const double* In;        // I^n, or B = (I^n/dt) R (implicit, BM = 2)
+  double* Bout;            // BM = 1: receives B
   const double* Ik;
   double* Iout;
   const double* I0cell;
@@ -57,7 +58,10 @@ struct UArgs {
 
 __device__ __forceinline__ double2 ld2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
 
-template <bool EXPL>
+// EXPL: explicit scheme.  BM (implicit): 0 In is I^n; 1 In is I^n and B =
+// (I^n/dt) R is stored; 2 In holds B (the same in every inner iteration of a
+// step), so the update is R (beta I0 + v sum |g| I_up) + B.
+template <bool EXPL, int BM>
 __global__ void __launch_bounds__(256) umesh_sweep_kernel(UArgs a) {
   const int team = a.lpc * a.dteam;
   const int cpb = blockDim.x / team;
@@ -78,7 +82,7 @@ __global__ void __launch_bounds__(256) umesh_sweep_kernel(UArgs a) {
       double f0 = 0.0, f1 = 0.0;  // sum over inflow faces of |g| I_up
       for (int e = e0; e < e1; ++e) {
         const double ge = a.g[(long long)e * a.nd + d];
-        if (ge < 0.0) {
+        if (__double_as_longlong(ge) < 0) {  // inflow: the sign bit, tested on the integer pipe
           const long long up = a.cf_up[e];
           double2 u;
           if (up >= 0) {
@@ -97,10 +101,16 @@ __global__ void __launch_bounds__(256) umesh_sweep_kernel(UArgs a) {
         const double go = a.gout[P * a.nd + d];
         r0 = fma(a.dt, fma(be0, i0.x - in.x, -v0 * fma(go, in.x, -f0)), in.x);
         r1 = fma(a.dt, fma(be1, i0.y - in.y, -v1 * fma(go, in.y, -f1)), in.y);
-      } else {  // [I^n/dt + beta I0 + v sum |g| I_up] x R, R = 1 / [1/dt + beta + v gout]
+      } else {  // R [beta I0 + v sum |g| I_up] + (I^n/dt) R, R = 1 / [1/dt + beta + v gout]
         const double2 rr = ld2(a.R + off);
-        r0 = fma(v0, f0, fma(in.x, a.rdt, bi0)) * rr.x;
-        r1 = fma(v1, f1, fma(in.y, a.rdt, bi1)) * rr.y;
+        double B0 = in.x, B1 = in.y;
+        if (BM != 2) {
+          B0 = in.x * a.rdt * rr.x;
+          B1 = in.y * a.rdt * rr.y;
+          if (BM == 1) *reinterpret_cast<double2*>(a.Bout + off) = make_double2(B0, B1);
+        }
+        r0 = fma(rr.x, fma(v0, f0, bi0), B0);
+        r1 = fma(rr.y, fma(v1, f1, bi1), B1);
       }
       *reinterpret_cast<double2*>(a.Iout + off) = make_double2(r0, r1);
     }
@@ -158,6 +168,7 @@ __global__ void umesh_diffuse_kernel(const double* I, const long long* bfs, int 
     const double* row = I + P * (long long)nd * nbp;
     for (int b = lane; b < nbp; b += 32) {
       double num = 0.0, den = 0.0;
+#pragma unroll 8
       for (int e = 0; e < nd; ++e) {
         const double sn = S[3 * e] * n[0] + S[3 * e + 1] * n[1] + S[3 * e + 2] * n[2];
         if (sn > 0.0) num = fma(sn, row[(long long)e * nbp + b], num);
@@ -638,19 +649,38 @@ int bte_umesh_step(bte_umesh u, double dt, int nsteps, int ninner, int scheme, b
   const int cpb = threads / (u->lpc * u->dteam);
   const int grid = (int)std::min<long long>((u->nc + cpb - 1) / cpb, 65535);
   int launches = 0;
+  // implicit steps of two or more inner iterations keep B = (I^n/dt) R in the
+  // third buffer: iteration 0 reads I^n and writes I^1 and B; iteration k reads
+  // B and I^k and overwrites the buffer I^n (or I^{k-2}) was in
+  const bool use_b = scheme != BTE_EXPLICIT && ninner >= 2;
   for (int st = 0; st < nsteps; ++st) {
     const int n = u->cur;
-    int k = n;
+    int k = n, z = -1;
     for (int it = 0; it < ninner; ++it) {
-      int o = 0;
-      while (o == n || o == k) ++o;
-      a.In = u->I[n];
+      int o = 0, bm = 0;
+      if (use_b && it == 0) {
+        while (o == n) ++o;
+        z = 0;
+        while (z == n || z == o) ++z;
+        a.In = u->I[n];
+        a.Bout = u->I[z];
+        bm = 1;
+      } else if (use_b) {
+        while (o == z || o == k) ++o;
+        a.In = u->I[z];
+        bm = 2;
+      } else {
+        while (o == n || o == k) ++o;
+        a.In = u->I[n];
+      }
       a.Ik = u->I[k];
       a.Iout = u->I[o];
       UTRY(u, cudaMemsetAsync(u->fix_count, 0, 4, s));
       UTRY(u, refresh_diffuse(u, a.Ik));
-      if (scheme == BTE_EXPLICIT) umesh_sweep_kernel<true><<<grid, threads, 0, s>>>(a);
-      else umesh_sweep_kernel<false><<<grid, threads, 0, s>>>(a);
+      if (scheme == BTE_EXPLICIT) umesh_sweep_kernel<true, 0><<<grid, threads, 0, s>>>(a);
+      else if (bm == 1) umesh_sweep_kernel<false, 1><<<grid, threads, 0, s>>>(a);
+      else if (bm == 2) umesh_sweep_kernel<false, 2><<<grid, threads, 0, s>>>(a);
+      else umesh_sweep_kernel<false, 0><<<grid, threads, 0, s>>>(a);
       UTRY(u, cudaGetLastError());
       SweepArgs c = cell_args(u, a.Iout);
       UTRY(u, launch_gs_reduce(c, u->nc, s));
