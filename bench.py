@@ -338,6 +338,52 @@ def run_gs_variant(peaks):
                          "frac": fl / FP64_PEAK_FLOPS}}
 
 
+def run_umesh_variant(peaks):
+    """Unstructured mesh: a 1.28 um square of 128x128 grid squares split into
+    32768 jittered triangles, 400 directions (20 x 20) x 55 band-pols, FP64,
+    walls hot 305 K / cold 300 K / mirror / diffuse, 15 inner iterations per
+    step, device-timed like the main line.  Flops per update: the B-form update
+    (2 FMAs) plus one FMA per inflow face and the reduction's FMA, the inflow
+    count averaged over the mesh's (cell, direction) pairs."""
+    import numpy as np
+    import torch
+    from paper_2305_19400_gb300 import bte, mesh as M, workloads as W
+    m = M.tri_grid(128, 128, 1280e-9, 1280e-9, jitter=0.25, seed=7)
+    dirs = W.Dirs("polar_azim", n_polar=20, n_azim=20)
+    bands = W.make_bands(40, 15, 19406)
+    bc = {0: (bte.BTE_BC_ISOTHERMAL, 305.0), 1: (bte.BTE_BC_ISOTHERMAL, 300.0),
+          2: (bte.BTE_BC_SPECULAR, None), 3: (bte.BTE_BC_DIFFUSE, None)}
+    s = bte.UMeshSolver(m, dirs, bands, bc)
+    dt, ninner, steps = 1e-12, 15, 3
+    s.step(dt, 1, ninner, want_stats=False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.step(dt, steps, ninner, want_stats=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    dof = m.ncells * dirs.nd * len(bands.vg)
+    ups = dof * ninner * steps / (ms * 1e-3)
+    # inflow faces per (cell, direction): the in-plane part of S_d points along the azimuth
+    phi = (np.arange(dirs.n_azim) + 0.5) * 2 * np.pi / dirs.n_azim
+    sdir = np.stack([np.cos(phi), np.sin(phi)], axis=1)
+    sn = m.nA[:, :2] @ sdir.T                       # [face, azimuth], out of the owner
+    inflow = (sn < 0).sum() + (sn[m.neighbor >= 0] > 0).sum()
+    nin = inflow / (m.ncells * dirs.n_azim)
+    flops = 2.0 * (2 + nin) + 2.0
+    fl = ups * flops
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return {"workload": "fp64_unstructured_32768_triangles_400dir", "dtype": "f64", "value": ups, "unit": UNIT,
+            "ms_per_step": ms / steps, "steps": steps, "inner_iterations_per_step": ninner, "cells": m.ncells,
+            "inflow_faces_per_cell_direction": float(nin),
+            "roofline": {"bound": "alu", "achieved": fl / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                         "frac": fl / FP64_PEAK_FLOPS, "flop_per_update": flops}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -468,6 +514,7 @@ def main():
     if world == 1 and not args.no_variants:
         variants = run_variants(peaks)
         variants.append(run_gs_variant(peaks))
+        variants.append(run_umesh_variant(peaks))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "strong" if partitioned else "weak",

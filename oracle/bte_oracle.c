@@ -39,7 +39,7 @@ static const double ORC_HBAR = 1.054571817e-34; /* J s */
 static const double ORC_KB = 1.380649e-23;      /* J/K */
 static const double ORC_PI = 3.14159265358979323846;
 
-enum { ORC_ISOTHERMAL = 0, ORC_SPECULAR = 1, ORC_DIFFUSE = 2 };
+enum { ORC_ISOTHERMAL = 0, ORC_SPECULAR = 1, ORC_DIFFUSE = 2, ORC_PARTIAL = 3 };
 enum { ORC_IMPLICIT = 0, ORC_EXPLICIT = 1, ORC_GAUSS_SEIDEL = 2 };
 
 int orc_num_threads(void) {
@@ -183,6 +183,9 @@ typedef struct {
      cell's T_p, one exponent for all bands; beta_exp = 0 keeps tau fixed. */
   double beta_exp;
   double beta_Tref;
+  /* specularity of ORC_PARTIAL sides: the incoming intensity is spec x the
+     mirror value + (1 - spec) x the diffuse value */
+  double spec[6];
 } orc_problem;
 
 /* beta_b(T) / beta_b for a cell at temperature T. */
@@ -249,7 +252,8 @@ static double upwind_value(const orc_problem* p, const double* Isrc, const doubl
     return I0wall[f * nb + b];
   }
   long P = ((long)k * p->ny + j) * p->nx + i;
-  if (p->bc_type[side] == ORC_DIFFUSE) {
+  double diffuse = 0.0, mirror = 0.0;
+  if (p->bc_type[side] == ORC_DIFFUSE || p->bc_type[side] == ORC_PARTIAL) {
     /* diffuse wall: every incoming direction gets the same intensity, set so
        that the wall returns the band's whole outgoing energy flux:
        sum_{out} |S_ax| I_d / sum_{in} |S_ax| (out: moving into the wall) */
@@ -260,11 +264,14 @@ static double upwind_value(const orc_problem* p, const double* Isrc, const doubl
       if (outgoing) num += fabs(se) * Isrc[P * nd * nb + (long)e * nb + b];
       else if (se != 0.0) den += fabs(se);
     }
-    return num / den;
+    diffuse = num / den;
+    if (p->bc_type[side] == ORC_DIFFUSE) return diffuse;
   }
   /* symmetry: the reflected direction of the same cell */
   const int* r = ax == 0 ? p->rx : (ax == 1 ? p->ry : p->rz);
-  return Isrc[P * nd * nb + (long)r[d] * nb + b];
+  mirror = Isrc[P * nd * nb + (long)r[d] * nb + b];
+  if (p->bc_type[side] == ORC_PARTIAL) return p->spec[side] * mirror + (1.0 - p->spec[side]) * diffuse;
+  return mirror;
 }
 
 /* One intensity update for (P, d, b), with beta = beta_b * bscale (bscale is

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "bte_oracle.c")
 LIB = os.path.join(HERE, "_build", "liborc.so")
 
-ISOTHERMAL, SPECULAR, DIFFUSE = 0, 1, 2
+ISOTHERMAL, SPECULAR, DIFFUSE, PARTIAL = 0, 1, 2, 3
 IMPLICIT, EXPLICIT, GAUSS_SEIDEL = 0, 1, 2
 
 _lock = threading.Lock()
@@ -55,6 +55,7 @@ class _Problem(C.Structure):
         ("newton_maxit", C.c_int),
         ("newton_rtol", C.c_double),
         ("beta_exp", C.c_double), ("beta_Tref", C.c_double),
+        ("spec", C.c_double * 6),
     ]
 
 
@@ -199,8 +200,11 @@ class Problem:
                 p.bc_type[s] = ISOTHERMAL
                 p.bc_T[s] = _dp(T)
             else:
-                p.bc_type[s] = DIFFUSE if (s < 2 * geom.dim and geom.bc[s][0] == DIFFUSE) else SPECULAR
+                kind = geom.bc[s][0] if s < 2 * geom.dim else SPECULAR
+                p.bc_type[s] = kind if kind in (DIFFUSE, PARTIAL) else SPECULAR
                 p.bc_T[s] = C.POINTER(C.c_double)()
+                if kind == PARTIAL:  # (PARTIAL, specularity)
+                    p.spec[s] = float(geom.bc[s][1])
         p.newton_maxit = newton_maxit
         p.newton_rtol = newton_rtol
         p.beta_exp = float(beta_exp)

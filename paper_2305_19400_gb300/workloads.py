@@ -33,6 +33,7 @@ MASK64 = (1 << 64) - 1
 BC_ISOTHERMAL = 0
 BC_SPECULAR = 1
 BC_DIFFUSE = 2   # fully diffuse wall: incoming intensity isotropic, carrying the outgoing energy flux
+BC_PARTIAL = 3   # partially specular wall: (BC_PARTIAL, p) mixes p x mirror + (1 - p) x diffuse
 SIDES = ("-x", "+x", "-y", "+y", "-z", "+z")
 
 
@@ -146,12 +147,15 @@ class Workload:
 
 def uniform_walls(geom: Geometry, kinds, temps):
     """Fill geom.bc from per-side kinds and uniform temperatures (None for
-    specular and diffuse sides)."""
+    specular and diffuse sides; for partially specular sides temps gives the
+    specularity p)."""
     geom.bc = []
     nsides = 2 * geom.dim
     for s in range(nsides):
         if kinds[s] == BC_ISOTHERMAL:
             geom.bc.append((BC_ISOTHERMAL, np.full(geom.nfaces(s), float(temps[s]))))
+        elif kinds[s] == BC_PARTIAL:
+            geom.bc.append((BC_PARTIAL, float(temps[s])))
         else:
             geom.bc.append((BC_DIFFUSE if kinds[s] == BC_DIFFUSE else BC_SPECULAR, None))
     return geom

@@ -534,3 +534,58 @@ def test_diffuse_side_walls_scatter_heat_back():
         prob.run(st, 1e-12, 60, 8)
         q_out[side_kind] = prob.flux(st["I"])[1][1]     # heat leaving through the cold +x wall
     assert q_out[W.BC_SPECULAR] > 0 and 0 < q_out[W.BC_DIFFUSE] < 0.9 * q_out[W.BC_SPECULAR], q_out
+
+
+# ------------------------------------------------------ partially specular walls
+def _partial_box(p_spec, nx=6, ny=5, seed=71):
+    g = W.Geometry(2, nx, ny, 1, 10e-9, 10e-9, 10e-9)
+    W.uniform_walls(g, [W.BC_PARTIAL] * 4, [p_spec] * 4)
+    return g
+
+
+def test_partial_specularity_reduces_to_mirror_and_diffuse_walls():
+    """p = 1 is the mirror wall and p = 0 the diffuse wall, to the last bit."""
+    bands = W.make_bands(4, 1, 72)
+    dirs = O.dirs_inplane(12)
+    T0 = W.random_temperatures(30, 73, 290.0, 310.0)
+    for p_spec, kind in ((1.0, W.BC_SPECULAR), (0.0, W.BC_DIFFUSE)):
+        a = O.Problem(_partial_box(p_spec), dirs, bands)
+        gb = W.Geometry(2, 6, 5, 1, 10e-9, 10e-9, 10e-9)
+        W.uniform_walls(gb, [kind] * 4, [0.0] * 4)
+        b = O.Problem(gb, dirs, bands)
+        sa, sb = a.init_state(T0), b.init_state(T0)
+        a.run(sa, 1e-12, 3, 4)
+        b.run(sb, 1e-12, 3, 4)
+        assert np.array_equal(sa["I"], sb["I"]), p_spec
+
+
+def test_one_explicit_step_is_the_specularity_mix_of_its_limits():
+    """For one explicit step from a fixed state the update is linear in the
+    ghost, and the ghost is p x mirror + (1 - p) x diffuse."""
+    bands = W.make_bands(4, 1, 74)
+    dirs = O.dirs_inplane(12)
+    T0 = W.random_temperatures(30, 75, 290.0, 310.0)
+    warm = O.Problem(_partial_box(0.5), dirs, bands)     # an anisotropic start: a few steps first
+    start = warm.init_state(T0)
+    warm.run(start, 2e-13, 5, 1, O.EXPLICIT)
+    out = {}
+    for p_spec in (0.0, 0.3, 1.0):
+        pr = O.Problem(_partial_box(p_spec), dirs, bands)
+        st = {k: v.copy() for k, v in start.items()}
+        pr.run(st, 2e-13, 1, 1, O.EXPLICIT)
+        out[p_spec] = st["I"]
+    mix = 0.3 * out[1.0] + 0.7 * out[0.0]
+    assert np.max(np.abs(out[0.3] - mix) / out[0.3]) < 1e-14
+    assert np.max(np.abs(out[1.0] - out[0.0]) / out[0.3]) > 1e-6     # the limits differ
+
+
+def test_partially_specular_enclosure_conserves_energy_with_no_net_wall_flux():
+    pr = O.Problem(_partial_box(0.4), O.dirs_inplane(12), W.make_bands(4, 1, 76))
+    st = pr.init_state(W.random_temperatures(30, 77, 290.0, 310.0))
+    E0 = _total_energy(pr, st["I"])
+    T0 = st["TL"].copy()
+    pr.run(st, 2e-13, 200, 1, O.EXPLICIT)
+    assert abs(_total_energy(pr, st["I"]) - E0) <= 1e-13 * E0
+    assert np.max(np.abs(st["TL"] - T0)) > 0.1
+    q, qw = pr.flux(st["I"])
+    assert np.all(np.abs(qw) <= 1e-12 * np.max(np.abs(q)))
