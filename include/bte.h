@@ -47,7 +47,7 @@ extern "C" {
 /* ---- enumerations ---- */
 enum { BTE_DIRS_INPLANE = 0, BTE_DIRS_POLAR_AZIM = 1 };
 enum { BTE_FP64 = 0, BTE_FP32 = 1, BTE_BF16 = 2 };
-enum { BTE_BC_ISOTHERMAL = 0, BTE_BC_SPECULAR = 1, BTE_BC_DIFFUSE = 2 };
+enum { BTE_BC_ISOTHERMAL = 0, BTE_BC_SPECULAR = 1, BTE_BC_DIFFUSE = 2, BTE_BC_PARTIAL = 3 };
 enum { BTE_IMPLICIT_JACOBI = 0, BTE_EXPLICIT = 1, BTE_IMPLICIT_GS = 2 };
 enum { BTE_T_PSEUDO = 0, BTE_T_LATTICE = 1 };
 
@@ -188,6 +188,17 @@ int bte_bind_workspace(bte_handle h, void* dev_ptr, size_t bytes);
  * each band's whole energy flux isotropically.  T_faces and T_uniform are
  * ignored for it. */
 int bte_set_bc(bte_handle h, int geom, int side, int type, const double* T_faces, double T_uniform);
+
+/* Makes one side partially specular (BTE_BC_PARTIAL; an extension beyond
+ * Eq. 6): every incoming direction d of band b gets
+ *   p x I_{mirror(d),b} + (1 - p) x sum_out |S.n| I_b / sum_in |S.n|
+ * of the wall cell's current iterate, i.e. a fraction p of the energy
+ * reflected as by a mirror and the rest as by a diffuse wall; p = 1 is
+ * BTE_BC_SPECULAR, p = 0 BTE_BC_DIFFUSE.  0 <= p <= 1, else BTE_E_ARG.  The
+ * side's ghost rows (faces x directions x bands in the storage type) are
+ * allocated with cudaMalloc outside any bound workspace (BTE_E_NOMEM on
+ * failure) and refreshed by one kernel before every sweep. */
+int bte_set_specularity(bte_handle h, int geom, int side, double p);
 
 /* Equilibrium initial state (Sec. 3.2): I[P][d][b] = I0_b(T_P) for all d and
  * T_p = T_L = T_P.  T_cells: host array of the geometry's cells, or NULL for

@@ -20,7 +20,7 @@ BTE_E = {-1: "BTE_E_ARG", -2: "BTE_E_STATE", -3: "BTE_E_CUDA", -4: "BTE_E_NOMEM"
          -6: "BTE_E_TIMEOUT", -7: "BTE_E_EXCHANGE"}
 BTE_DIRS_INPLANE, BTE_DIRS_POLAR_AZIM = 0, 1
 BTE_FP64, BTE_FP32, BTE_BF16 = 0, 1, 2
-BTE_BC_ISOTHERMAL, BTE_BC_SPECULAR, BTE_BC_DIFFUSE = 0, 1, 2
+BTE_BC_ISOTHERMAL, BTE_BC_SPECULAR, BTE_BC_DIFFUSE, BTE_BC_PARTIAL = 0, 1, 2, 3
 BTE_IMPLICIT_JACOBI, BTE_EXPLICIT, BTE_IMPLICIT_GS = 0, 1, 2
 BTE_T_PSEUDO, BTE_T_LATTICE = 0, 1
 
@@ -65,6 +65,7 @@ SIGNATURES = {
     "bte_workspace_bytes": (C.c_size_t, [_h]),
     "bte_bind_workspace": (C.c_int, [_h, _vp, C.c_size_t]),
     "bte_set_bc": (C.c_int, [_h, C.c_int, C.c_int, C.c_int, _dp, C.c_double]),
+    "bte_set_specularity": (C.c_int, [_h, C.c_int, C.c_int, C.c_double]),
     "bte_set_initial": (C.c_int, [_h, C.c_int, _dp, C.c_double]),
     "bte_step": (C.c_int, [_h, C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(bte_stats)]),
     "bte_autotune": (C.c_int, [_h, C.c_double, C.c_int, C.c_char_p, C.c_size_t]),
@@ -372,7 +373,10 @@ class Solver:
             bte_bind_workspace(self.h, self.ws_view)
         for gi, g in enumerate(workload.geoms):
             for side, (kind, T) in enumerate(g.bc):
-                bte_set_bc(self.h, gi, side, kind, T, 300.0)
+                if kind == BTE_BC_PARTIAL:  # (BTE_BC_PARTIAL, specularity)
+                    _check(self.h, lib().bte_set_specularity(self.h, gi, side, float(T)))
+                else:
+                    bte_set_bc(self.h, gi, side, kind, T, 300.0)
             bte_set_initial(self.h, gi, None if T_init is None else T_init[gi], g.T_init)
 
     def step(self, nsteps=None, ninner=None, dt=None, scheme=BTE_IMPLICIT_JACOBI, want_stats=True):

@@ -54,6 +54,8 @@ struct bte_ctx {
   bool bands_set = false;
   std::vector<std::array<int, 6>> bc_type;
   std::vector<std::array<bool, 6>> bc_set;
+  std::vector<std::array<double, 6>> spec;   // specularity of partially specular sides
+  std::vector<std::array<void*, 6>> gdir;    // their per-direction ghost rows (cudaMalloc, owned)
   std::vector<bool> init_set;
   bool TL_valid = false;
   // launch shape
@@ -308,6 +310,10 @@ int upload_gs(bte_ctx* h, cudaStream_t s) {
   return BTE_OK;
 }
 
+// Wall codes the kernels read: a diffuse side reads its (refreshed) ghost row
+// like an isothermal one (0); a partially specular side its per-direction rows (3).
+int dev_bc(int type) { return type == BTE_BC_DIFFUSE ? 0 : (type == BTE_BC_PARTIAL ? 3 : type); }
+
 void drop_graphs(bte_ctx* h) {
   for (auto& e : h->graphs) cudaGraphExecDestroy(e.exec);
   h->graphs.clear();
@@ -389,8 +395,8 @@ int ensure_memory(bte_ctx* h) {
     o.cell0 = h->cell0[gi];
     for (int s6 = 0; s6 < 6; ++s6) {
       o.face0[s6] = h->face0[gi * 6 + s6];
-      // a diffuse side reads its ghost row like an isothermal one (refreshed each inner iteration)
-      o.bc[s6] = h->bc_type[gi][s6] == BTE_BC_DIFFUSE ? BTE_BC_ISOTHERMAL : h->bc_type[gi][s6];
+      o.bc[s6] = dev_bc(h->bc_type[gi][s6]);
+      o.gdir[s6] = h->gdir[gi][s6];
     }
     o.cls = h->cls[gi];
     o.pad = 0;
@@ -413,8 +419,11 @@ int ensure_memory(bte_ctx* h) {
 int upload_geoms(bte_ctx* h) {
   std::vector<DevGeom>& dg = h->dgeoms;
   for (size_t gi = 0; gi < h->geoms.size(); ++gi)
-    for (int s6 = 0; s6 < 6; ++s6)  // a diffuse side reads its (refreshed) ghost row like an isothermal one
-      dg[gi].bc[s6] = h->bc_type[gi][s6] == BTE_BC_DIFFUSE ? BTE_BC_ISOTHERMAL : h->bc_type[gi][s6];
+    for (int s6 = 0; s6 < 6; ++s6) {
+      dg[gi].bc[s6] = dev_bc(h->bc_type[gi][s6]);
+      dg[gi].gdir[s6] = h->gdir[gi][s6];
+    }
+  drop_graphs(h);  // the launches of a step depend on the wall kinds
   CUDA_TRY(h, cudaMemcpyAsync(h->geoms_d, dg.data(), dg.size() * sizeof(DevGeom), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return BTE_OK;
@@ -565,6 +574,22 @@ cudaError_t refresh_diffuse(bte_ctx* h, const void* I, cudaStream_t s, int* laun
   return cudaSuccess;
 }
 
+// Per-direction ghost rows of the partially specular sides from intensity
+// buffer I (before a sweep that reads I as its upwind field, and before wall
+// fluxes).  *launches counts the kernels.
+cudaError_t refresh_partial(bte_ctx* h, const void* I, cudaStream_t s, int* launches = nullptr) {
+  for (size_t gi = 0; gi < h->geoms.size(); ++gi)
+    for (int side = 0; side < 2 * h->geoms[gi].dim; ++side) {
+      if (h->bc_type[gi][side] != BTE_BC_PARTIAL) continue;
+      const cudaError_t e = launch_partial_ghosts(h->opts.precision, I, h->I0ref_o, h->geoms_d, (int)gi, side, h->Sdev,
+                                                  h->dirs_d, h->nd, h->nbp, (int)side_faces(h->geoms[gi], side),
+                                                  h->spec[gi][side], h->gdir[gi][side], s);
+      if (e != cudaSuccess) return e;
+      if (launches) ++*launches;
+    }
+  return cudaSuccess;
+}
+
 // One time step: ninner sweeps rotating the three intensity buffers from *cur.
 // scheme BTE_IMPLICIT_GS runs the sweep-ordered pass and the per-cell step as
 // two kernels in place of the fused Jacobi sweep.
@@ -601,6 +626,7 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaSt
     a.Iout = h->Ibuf[o];
     cudaError_t e = cudaMemsetAsync(h->fix_count, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = refresh_diffuse(h, a.Ik, s);
+    if (e == cudaSuccess) e = refresh_partial(h, a.Ik, s);
     if (scheme == BTE_IMPLICIT_GS) {
       if (e == cudaSuccess && a.beta_exp != 0.0)
         e = launch_beta_scale(h->bscale, h->Tp, a.beta_Tref, a.beta_exp, h->ncells, s);
@@ -645,8 +671,9 @@ int flux_view(bte_ctx* h, int geom, FluxView* out) {
   const bte_geom& g = h->geoms[geom];
   out->precision = h->opts.precision;
   out->I = (const double*)h->Ibuf[h->cur];
-  {  // diffuse wall ghosts of the current state (a kernel launch, no allocation)
-    const cudaError_t e = refresh_diffuse(h, h->Ibuf[h->cur], h->stream);
+  {  // diffuse and partially specular wall ghosts of the current state (kernel launches, no allocation)
+    cudaError_t e = refresh_diffuse(h, h->Ibuf[h->cur], h->stream);
+    if (e == cudaSuccess) e = refresh_partial(h, h->Ibuf[h->cur], h->stream);
     if (e != cudaSuccess) return fail(h, BTE_E_CUDA, "diffuse wall ghosts: %s", cudaGetErrorString(e));
   }
   out->I0wall = h->I0wall;
@@ -773,6 +800,8 @@ int bte_init_mesh(bte_handle* out, int n_geom, const bte_geom* geoms, const bte_
   h->nfaces = f0;
   h->bc_type.assign(n_geom, {BTE_BC_SPECULAR, BTE_BC_SPECULAR, BTE_BC_SPECULAR, BTE_BC_SPECULAR, BTE_BC_SPECULAR, BTE_BC_SPECULAR});
   h->bc_set.assign(n_geom, {false, false, false, false, false, false});
+  h->spec.assign(n_geom, {0, 0, 0, 0, 0, 0});
+  h->gdir.assign(n_geom, {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr});
   h->init_set.assign(n_geom, false);
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
     delete h;
@@ -886,6 +915,27 @@ int bte_set_bc(bte_handle h, int geom, int side, int type, const double* T_faces
   return BTE_OK;
 }
 
+int bte_set_specularity(bte_handle h, int geom, int side, double p) {
+  int rc = check_geom(h, geom);
+  if (rc) return rc;
+  if (!h->bands_set) return fail(h, BTE_E_STATE, "bte_set_bands must come before bte_set_specularity");
+  const bte_geom& g = h->geoms[geom];
+  if (side < 0 || side >= 2 * g.dim) return fail(h, BTE_E_ARG, "side %d out of range for a %dD geometry", side, g.dim);
+  if (!(p >= 0.0 && p <= 1.0)) return fail(h, BTE_E_ARG, "specularity must lie in [0, 1]");
+  if ((rc = ensure_memory(h))) return rc;
+  if (!h->gdir[geom][side]) {
+    const size_t bytes = (size_t)side_faces(g, side) * h->nd * h->nbp * elem_bytes(h->opts.precision);
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return fail(h, BTE_E_NOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    h->gdir[geom][side] = q;
+  }
+  h->spec[geom][side] = p;
+  h->bc_type[geom][side] = BTE_BC_PARTIAL;
+  h->bc_set[geom][side] = true;
+  return upload_geoms(h);
+}
+
 int bte_set_initial(bte_handle h, int geom, const double* T_cells, double T_uniform) {
   int rc = check_geom(h, geom);
   if (rc) return rc;
@@ -966,9 +1016,9 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
         return fail(h, BTE_E_EXCHANGE, "the exchange callback returned %d", h->exchange_rc);
       CUDA_TRY(h, e);
     }
-    int ndiff = 0;
+    int ndiff = 0;  // ghost refresh launches: diffuse and partially specular sides
     for (auto& bt : h->bc_type)
-      for (int t : bt) ndiff += t == BTE_BC_DIFFUSE;
+      for (int t : bt) ndiff += t == BTE_BC_DIFFUSE || t == BTE_BC_PARTIAL;
     // sweep (sweep-ordered: pass + per-cell step, and the beta scale with tau(T)),
     // fix-up, cell solve, diffuse wall ghosts
     const int sweep_k = scheme == BTE_IMPLICIT_GS ? 2 + (h->opts.beta_T_exp != 0.0 ? 1 : 0) : 1;
@@ -1177,7 +1227,8 @@ int bte_get_flux(bte_handle h, int geom, double* q_cells, double* q_walls, int o
   }
   if (q_walls) {
     double res[6] = {0, 0, 0, 0, 0, 0};
-    CUDA_TRY(h, refresh_diffuse(h, I, s));  // diffuse ghosts of the current state
+    CUDA_TRY(h, refresh_diffuse(h, I, s));  // diffuse and partially specular ghosts of the current state
+    CUDA_TRY(h, refresh_partial(h, I, s));
     for (int side = 0; side < 2 * g.dim; ++side) {
       const int nf = (int)side_faces(g, side);
       CUDA_TRY(h, launch_flux_faces(prec, I, h->I0ref_o, h->I0wall, h->geoms_d, geom, side, h->dirs_d, h->Sdev, h->nd,
@@ -1468,6 +1519,9 @@ int bte_destroy(bte_handle h) {
   drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ws_owned && h->ws) cudaFree(h->ws);
+  for (auto& sides : h->gdir)
+    for (void* p : sides)
+      if (p) cudaFree(p);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   delete h;

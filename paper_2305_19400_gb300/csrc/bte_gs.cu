@@ -32,13 +32,16 @@ __device__ __forceinline__ double2 ldcg2(const double* p) { return __ldcg(reinte
 __device__ __forceinline__ void st2(double* p, double x, double y) { *reinterpret_cast<double2*>(p) = make_double2(x, y); }
 
 // Upwind value along one axis (this thread's two bands): the neighbour's value
-// of this pass, or the Eq. 6 ghost at a wall (isothermal row, or the cell's
-// own previous iterate in the mirrored direction).
+// of this pass, or the Eq. 6 ghost at a wall (isothermal or diffuse row, the
+// side's per-direction row when partially specular, or the cell's own previous
+// iterate in the mirrored direction).  face: the wall face's index on its side.
 __device__ __forceinline__ double2 upwind(const SweepArgs& a, const DevGeom* gp, const double* Io, const double* Ik,
                                           int side, bool interior, long long base, long long step, long long Prow,
                                           int rdir, long long face, int nbp, int b0) {
   if (interior) return ldcg2(Io + base + step);
   if (gp->bc[side] == 0) return ldg2(a.I0wall + (gp->face0[side] + face) * nbp + b0);
+  if (gp->bc[side] == 3)
+    return ldg2(reinterpret_cast<const double*>(gp->gdir[side]) + face * ((long long)a.nd * nbp) + (base - Prow));
   return ldg2(Ik + Prow + (long long)rdir * nbp + b0);
 }
 

@@ -36,9 +36,10 @@ struct DevGeom {
   int nx, ny, nz, dim;
   long long cell0;        // global index of the first cell
   long long face0[6];     // first global wall-face row of each side (isothermal sides)
-  int bc[6];              // BTE_BC_* per side
+  int bc[6];              // 0 ghost row (isothermal, diffuse), 1 mirror, 3 per-direction ghost rows
   int cls;                // coefficient-table class (cells with equal dx, dy, dz)
   int pad;
+  const void* gdir[6];    // bc 3 (partially specular): [side face][dir][nbo] ghosts, storage type
 };
 
 // A run of consecutive cells of one geometry processed by one CTA.
@@ -166,6 +167,11 @@ cudaError_t launch_beta_scale(double* out, const double* Tp, double Tref, double
 cudaError_t launch_diffuse_ghosts(int precision, const void* I, const double* I0ref, double* I0wall, float* I0wall_dev,
                                   const DevGeom* geoms, int geom, int side, const double* S, int nd, int nbp,
                                   int nfaces, cudaStream_t s);
+// Partially specular side: per face, direction and band, p x the cell's mirrored
+// value + (1 - p) x the diffuse value, into out [face][dir][nbp] (storage type).
+cudaError_t launch_partial_ghosts(int precision, const void* I, const double* I0ref, const DevGeom* geoms, int geom,
+                                  int side, const double* S, const DirInfo* dirs, int nd, int nbp, int nfaces,
+                                  double p, void* out, cudaStream_t s);
 // learned guess (bte_mlp.cu)
 int mlp_param_total(int nb);
 cudaError_t launch_mlp_norm(ThermoTables th, double T_lo, double T_hi, const double* I0ref, double* r_lo, double* r_hi,

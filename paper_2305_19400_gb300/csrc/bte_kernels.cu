@@ -252,6 +252,7 @@ __global__ void flux_faces_kernel(const S* I, const double* I0ref, const double*
       double v;
       if (sn > 0.0) v = full_I(I, base + e, b, I0ref);
       else if (g.bc[side] == 0) v = I0wall[(g.face0[side] + f) * nbp + b];
+      else if (g.bc[side] == 3) v = full_I(reinterpret_cast<const S*>(g.gdir[side]), (long long)f * nd * nbp + e, b, I0ref);
       else {
         const int r = ax == 0 ? dirs[d].rx : (ax == 1 ? dirs[d].ry : dirs[d].rz);
         v = full_I(I, base + (long long)r * nbp + b, b, I0ref);
@@ -533,6 +534,64 @@ __global__ void diffuse_ghost_kernel(const S* I, const double* I0ref, double* I0
   }
 }
 
+// Partially specular side: one CTA of kPartWarps warps per wall face.  The
+// diffuse value per band, D_b = sum_{out} |S_ax| I / sum_{in} |S_ax| of the
+// wall cell (warps over direction ranges, added in warp order), then for
+// every direction and band the ghost p I(mirror of d) + (1 - p) D_b, stored in
+// the storage type (a deviation from I0_b(T_ref) in the reduced modes).
+constexpr int kPartWarps = 8;
+
+template <typename S>
+__global__ void __launch_bounds__(32 * kPartWarps) partial_ghost_kernel(const S* I, const double* I0ref,
+                                                                        const DevGeom* geoms, int geom, int side,
+                                                                        const double* Sd, const DirInfo* dirs, int nd,
+                                                                        int nbp, int nfaces, double p, S* out) {
+  extern __shared__ double part[];  // [kPartWarps][nbp] partial numerators, then D [nbp]
+  const DevGeom g = geoms[geom];
+  const int ax = side >> 1;
+  const bool high = side & 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long row = (long long)nd * nbp;
+  const int d0 = (int)((long long)wid * nd / kPartWarps), d1 = (int)((long long)(wid + 1) * nd / kPartWarps);
+  double den = 0.0;
+  for (int d = 0; d < nd; ++d) {
+    const double sd = Sd[3 * d + ax];
+    if (!(high ? sd > 0.0 : sd < 0.0) && sd != 0.0) den += fabs(sd);
+  }
+  for (int f = blockIdx.x; f < nfaces; f += gridDim.x) {
+    int i, j, k;  // wall cell of face f (x sides: j + ny k, y sides: i + nx k, z sides: i + nx j)
+    if (ax == 0) { i = high ? g.nx - 1 : 0; j = f % g.ny; k = f / g.ny; }
+    else if (ax == 1) { j = high ? g.ny - 1 : 0; i = f % g.nx; k = f / g.nx; }
+    else { k = high ? g.nz - 1 : 0; i = f % g.nx; j = f / g.nx; }
+    const long long P = g.cell0 + ((long long)k * g.ny + j) * g.nx + i;
+    for (int b = lane; b < nbp; b += 32) {
+      double num = 0.0;
+      for (int d = d0; d < d1; ++d) {
+        const double sd = Sd[3 * d + ax];
+        if (high ? sd > 0.0 : sd < 0.0) num = fma(fabs(sd), full_I(I, P * row + (long long)d * nbp + b, b, I0ref), num);
+      }
+      part[wid * nbp + b] = num;
+    }
+    __syncthreads();
+    double* D = part + kPartWarps * nbp;
+    for (int b = threadIdx.x; b < nbp; b += blockDim.x) {
+      double num = 0.0;
+      for (int w = 0; w < kPartWarps; ++w) num += part[w * nbp + b];
+      D[b] = num / den;
+    }
+    __syncthreads();
+    for (long long e = threadIdx.x; e < row; e += blockDim.x) {
+      const int d = (int)(e / nbp), b = (int)(e - (long long)d * nbp);
+      const int r = ax == 0 ? dirs[d].rx : (ax == 1 ? dirs[d].ry : dirs[d].rz);
+      const double v = fma(p, full_I(I, P * row + (long long)r * nbp + b, b, I0ref), (1.0 - p) * D[b]);
+      if constexpr (sizeof(S) == 8) out[f * row + e] = v;
+      else if constexpr (sizeof(S) == 4) out[f * row + e] = (float)(v - I0ref[b]);
+      else out[f * row + e] = __double2bfloat16(v - I0ref[b]);
+    }
+    __syncthreads();
+  }
+}
+
 inline int grid_for(long long n, int threads) {
   long long g = (n + threads - 1) / threads;
   if (g > 152LL * 64) g = 152LL * 64;
@@ -572,6 +631,24 @@ cudaError_t launch_diffuse_ghosts(int precision, const void* I, const double* I0
   else
     diffuse_ghost_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>((const __nv_bfloat16*)I, I0ref, I0wall, I0wall_dev, geoms,
                                                              geom, side, S, nd, nbp, nfaces);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_partial_ghosts(int precision, const void* I, const double* I0ref, const DevGeom* geoms, int geom,
+                                  int side, const double* S, const DirInfo* dirs, int nd, int nbp, int nfaces,
+                                  double p, void* out, cudaStream_t s) {
+  const int grid = (int)std::min<long long>(std::max(nfaces, 1), 152LL * 16);
+  const size_t sm = (size_t)(kPartWarps + 1) * nbp * sizeof(double);
+  if (precision == 0)
+    partial_ghost_kernel<double><<<grid, 32 * kPartWarps, sm, s>>>((const double*)I, I0ref, geoms, geom, side, S, dirs,
+                                                                   nd, nbp, nfaces, p, (double*)out);
+  else if (precision == 1)
+    partial_ghost_kernel<float><<<grid, 32 * kPartWarps, sm, s>>>((const float*)I, I0ref, geoms, geom, side, S, dirs, nd,
+                                                                  nbp, nfaces, p, (float*)out);
+  else
+    partial_ghost_kernel<__nv_bfloat16><<<grid, 32 * kPartWarps, sm, s>>>((const __nv_bfloat16*)I, I0ref, geoms, geom,
+                                                                          side, S, dirs, nd, nbp, nfaces, p,
+                                                                          (__nv_bfloat16*)out);
   return cudaGetLastError();
 }
 

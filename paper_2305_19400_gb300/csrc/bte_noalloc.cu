@@ -84,6 +84,7 @@ __global__ void wall_faces_static_kernel(const double* I, const double* I0wall, 
       double v;
       if (sn > 0.0) v = row[e];
       else if (bc == 0) v = I0wall[(f0 + f) * nbp + b];
+      else if (bc == 3) v = reinterpret_cast<const double*>(g.gdir[side])[(long long)f * nd * nbp + e];
       else {
         const int r = ax == 0 ? dirs[d].rx : (ax == 1 ? dirs[d].ry : dirs[d].rz);
         v = row[(long long)r * nbp + b];

@@ -55,16 +55,21 @@ struct CellAddr {
 };
 
 // Address of the Eq. 6 ghost of a wall side for (cell, direction): I0 of the
-// face (isothermal; a deviation from I0_b(T_ref) in the reduced modes) or the
-// cell's own value in the mirrored direction (specular).
+// face (isothermal, or a refreshed diffuse value; a deviation from I0_b(T_ref)
+// in the reduced modes), the side's per-direction ghost row (partially
+// specular), or the cell's own value in the mirrored direction (specular).
+// off: the direction's row offset d * nbo.
 template <int AX, typename S>
 __device__ __forceinline__ const void* wall_ghost_src(const SweepArgs& a, const DevGeom* gp, const CellAddr<S>& c,
-                                                      const int4 di, bool from_low, int b0) {
+                                                      const int4 di, bool from_low, int b0, long long off) {
   const int nbp = a.th.nbo;
   const int side = 2 * AX + (from_low ? 0 : 1);
-  if (gp->bc[side] == 0) {  // wall data stay in memory (L1): only wall cells get here
-    const long long f = gp->face0[side] + (AX == 0 ? c.cj + (long long)gp->ny * c.ck
-                                                  : (AX == 1 ? c.ci + (long long)gp->nx * c.ck : c.ci + (long long)gp->nx * c.cj));
+  const int bc = gp->bc[side];
+  if (bc == 0 || bc == 3) {  // wall data stay in memory (L1): only wall cells get here
+    const long long fl = AX == 0 ? c.cj + (long long)gp->ny * c.ck
+                                 : (AX == 1 ? c.ci + (long long)gp->nx * c.ck : c.ci + (long long)gp->nx * c.cj);
+    if (bc == 3) return reinterpret_cast<const S*>(gp->gdir[side]) + fl * ((long long)a.nd * nbp) + off + b0;
+    const long long f = gp->face0[side] + fl;
     if constexpr (sizeof(S) == 8) return a.I0wall + f * nbp + b0;
     else return a.I0wall_dev + f * nbp + b0;
   }
@@ -82,7 +87,7 @@ __device__ __forceinline__ const void* upwind_src(const SweepArgs& a, const DevG
     const long long st = AX == 0 ? c.sx : (AX == 1 ? c.sy : c.sz);
     return c.ik + (from_low ? -st : st) + off;
   }
-  return wall_ghost_src<AX, S>(a, gp, c, di, from_low, b0);
+  return wall_ghost_src<AX, S>(a, gp, c, di, from_low, b0, off);
 }
 
 // Asynchronous global -> shared copy of one lane vector (16 or 8 bytes), L2 only.

@@ -157,25 +157,43 @@ __global__ void umesh_gout_kernel(const int* cf_ptr, const double* g, int nd, lo
 }
 
 // Diffuse ghosts: for each listed boundary face, per band,
-// sum_{S.n > 0} (S.n) I / sum_{S.n < 0} |S.n| of the owner cell.  One warp per face.
-__global__ void umesh_diffuse_kernel(const double* I, const long long* bfs, int nlist, const long long* bface,
-                                     const long long* owner, const double* nA, const double* S, int nd, int nbp,
-                                     double* ghost) {
-  const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
-  for (int k = blockIdx.x * warps + threadIdx.x / 32; k < nlist; k += gridDim.x * warps) {
+// sum_{S.n > 0} (S.n) I / sum_{S.n < 0} |S.n| of the owner cell.  One CTA of
+// kDiffWarps warps per face: warp w sums the directions [w nd/W, (w+1) nd/W)
+// (lanes over bands); the partial sums are added in warp order.
+constexpr int kDiffWarps = 8;
+
+__global__ void __launch_bounds__(32 * kDiffWarps) umesh_diffuse_kernel(const double* I, const long long* bfs, int nlist,
+                                                                        const long long* bface, const long long* owner,
+                                                                        const double* nA, const double* S, int nd,
+                                                                        int nbp, double* ghost) {
+  extern __shared__ double part[];  // [kDiffWarps][2][nbp]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int d0 = (int)((long long)wid * nd / kDiffWarps), d1 = (int)((long long)(wid + 1) * nd / kDiffWarps);
+  for (int k = blockIdx.x; k < nlist; k += gridDim.x) {
     const long long bf = bfs[k], f = bface[bf], P = owner[f];
     const double* n = nA + 3 * f;
     const double* row = I + P * (long long)nd * nbp;
     for (int b = lane; b < nbp; b += 32) {
       double num = 0.0, den = 0.0;
-#pragma unroll 8
-      for (int e = 0; e < nd; ++e) {
+#pragma unroll 4
+      for (int e = d0; e < d1; ++e) {
         const double sn = S[3 * e] * n[0] + S[3 * e + 1] * n[1] + S[3 * e + 2] * n[2];
         if (sn > 0.0) num = fma(sn, row[(long long)e * nbp + b], num);
         else den -= sn;
       }
+      part[(wid * 2) * nbp + b] = num;
+      part[(wid * 2 + 1) * nbp + b] = den;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbp; b += blockDim.x) {
+      double num = 0.0, den = 0.0;
+      for (int w = 0; w < kDiffWarps; ++w) {
+        num += part[(w * 2) * nbp + b];
+        den += part[(w * 2 + 1) * nbp + b];
+      }
       ghost[bf * nbp + b] = den > 0.0 ? num / den : 0.0;
     }
+    __syncthreads();
   }
 }
 
@@ -440,8 +458,9 @@ int upload_bc(bte_umesh_ctx* u) {
 
 cudaError_t refresh_diffuse(bte_umesh_ctx* u, const double* I) {
   if (u->ndiff == 0) return cudaSuccess;
-  umesh_diffuse_kernel<<<grid_for(u->ndiff, 4), 128, 0, u->stream>>>(I, u->diff_d, u->ndiff, u->bface_d, u->owner_d,
-                                                                     u->nA_d, u->S_d, u->nd, u->nbp, u->ghost);
+  const int grid = (int)std::min<long long>(u->ndiff, 152LL * 16);
+  umesh_diffuse_kernel<<<grid, 32 * kDiffWarps, (size_t)kDiffWarps * 2 * u->nbp * sizeof(double), u->stream>>>(
+      I, u->diff_d, u->ndiff, u->bface_d, u->owner_d, u->nA_d, u->S_d, u->nd, u->nbp, u->ghost);
   return cudaGetLastError();
 }
 

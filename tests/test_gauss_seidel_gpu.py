@@ -199,3 +199,21 @@ def test_full_size_pass_sampled_against_oracle():
         assert abs(TL_1[P] - TL_ref) <= 1e-12 * TL_ref
     assert worst <= 1e-12, worst
     s.close()
+
+
+@pytest.mark.parametrize("dims,nbands,dirs", [((2, 1, 1, 1), 4, W.Dirs("inplane", n_inplane=8)),
+                                              ((2, 9, 1, 1), 1, W.Dirs("inplane", n_inplane=12)),
+                                              ((3, 1, 1, 5), 3, W.Dirs("polar_azim", n_polar=4, n_azim=8)),
+                                              ((2, 3, 2, 1), 3, W.Dirs("polar_azim", n_polar=32, n_azim=64))])
+def test_degenerate_grids_one_band_and_the_largest_direction_set(dims, nbands, dirs):
+    dim, nx, ny, nz = dims
+    g = W.Geometry(dim, nx, ny, nz, 10e-9, 10e-9, 10e-9)
+    kinds = [W.BC_ISOTHERMAL, W.BC_ISOTHERMAL] + [W.BC_SPECULAR] * (2 * dim - 2)
+    W.uniform_walls(g, kinds, [305.0, 300.0] + [0.0] * (2 * dim - 2))
+    bands = W.make_bands(nbands, 0, 61) if nbands > 1 else W.make_bands(1, 0, 61)
+    wl = W.Workload("edge", [g], dirs, bands, 1e-12, 2, 3)
+    s = bte.Solver(wl)
+    s.step(nsteps=2, ninner=3, scheme=GS)
+    _, ost = oracle_run(wl, 2, 3)
+    assert_matches(s, ost)
+    s.close()

@@ -234,3 +234,47 @@ def test_rotating_the_mesh_by_a_quarter_turn_relabels_the_solution():
     ub.run(sb, 1e-12, 3, 6)
     assert np.max(np.abs(sa["TL"] - sb["TL"]) / sa["TL"]) < 1e-13
     assert np.max(np.abs(sa["Tp"] - sb["Tp"]) / sa["Tp"]) < 1e-13
+
+
+def test_the_c_abi_rejects_bad_mesh_descriptions():
+    """Argument checks of bte_umesh_create run before any CUDA call."""
+    import ctypes as C
+    from paper_2305_19400_gb300 import build as B, bte
+    B.build()
+    L = bte.lib()
+    m = M.tri_grid(2, 2, 20e-9, 20e-9)
+
+    def create(**change):
+        arr = {"volume": m.volume.copy(), "owner": m.owner.copy(), "neighbor": m.neighbor.copy(),
+               "nA": m.nA.copy(), "tag": m.tag.copy()}
+        dim = change.pop("dim", 2)
+        for k, v in change.items():
+            v(arr[k])
+        d = bte.bte_umesh_desc()
+        d.dim, d.ncells, d.nfaces = dim, m.ncells, m.nfaces
+        keep = [np.ascontiguousarray(arr[k], dtype=t) for k, t in
+                (("volume", np.float64), ("owner", np.int64), ("neighbor", np.int64), ("nA", np.float64), ("tag", np.int32))]
+        d.volume = keep[0].ctypes.data_as(C.POINTER(C.c_double))
+        d.owner = keep[1].ctypes.data_as(C.POINTER(C.c_longlong))
+        d.neighbor = keep[2].ctypes.data_as(C.POINTER(C.c_longlong))
+        d.nA = keep[3].ctypes.data_as(C.POINTER(C.c_double))
+        d.tag = keep[4].ctypes.data_as(C.POINTER(C.c_int))
+        o = bte.bte_default_opts()
+        h = C.c_void_p()
+        return L.bte_umesh_create(C.byref(d), C.byref(o), C.byref(h)), h
+
+    def setv(idx, val):
+        def f(a):
+            a[idx] = val
+        return f
+    for change in ({"dim": 4}, {"volume": setv(0, -1.0)}, {"owner": setv(0, m.ncells)},
+                   {"neighbor": setv(int(np.nonzero(m.neighbor >= 0)[0][0]), int(m.owner[np.nonzero(m.neighbor >= 0)[0][0]]))},
+                   {"nA": setv((0, 2), 1e-9)}, {"tag": setv(int(m.boundary_faces()[0]), -3)}):
+        rc, h = create(**change)
+        assert rc == -1 and not h.value, change
+    o = bte.bte_default_opts()
+    o.precision = bte.BTE_FP32
+    d = bte.bte_umesh_desc()
+    h = C.c_void_p()
+    assert L.bte_umesh_create(None, C.byref(o), C.byref(h)) == -1
+    assert b"NULL" in L.bte_umesh_last_error(None)

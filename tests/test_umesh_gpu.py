@@ -190,3 +190,39 @@ def test_sampled_outputs_on_a_64x64x2_triangle_mesh():
         assert abs(TL_1[P] - TL_ref) <= 1e-12 * TL_ref
     assert worst <= 1e-12, worst
     s.close()
+
+
+def test_single_triangle_and_one_band():
+    pts = np.array([[0.0, 0.0, 0.0], [10e-9, 0.0, 0.0], [0.0, 10e-9, 0.0]])
+    m = M.from_elements(pts, [("tri", (0, 1, 2))], {frozenset((0, 1)): 0, frozenset((0, 2)): 1, frozenset((1, 2)): 2})
+    bands = W.make_bands(1, 0, 62)
+    bc = {0: (bte.BTE_BC_ISOTHERMAL, 310.0), 1: (bte.BTE_BC_SPECULAR, None), 2: (bte.BTE_BC_DIFFUSE, None)}
+    s, u, ost, _ = run_both(m, W.Dirs("inplane", n_inplane=12), bands, bc, 1e-12, 5, 4)
+    assert_matches(s, u, ost)
+    s.close()
+
+
+def test_hexahedral_gmsh_mesh(tmp_path):
+    nx, ny, nz, L = 3, 2, 2, 10e-9
+    x, y, z = np.arange(nx + 1) * L, np.arange(ny + 1) * L, np.arange(nz + 1) * L
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    vid = lambda i, j, k: (k * (ny + 1) + j) * (nx + 1) + i
+    el, bf = [], []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                el.append(("hex", (vid(i, j, k), vid(i + 1, j, k), vid(i + 1, j + 1, k), vid(i, j + 1, k),
+                                   vid(i, j, k + 1), vid(i + 1, j, k + 1), vid(i + 1, j + 1, k + 1), vid(i, j + 1, k + 1))))
+    for k in range(nz):
+        for j in range(ny):
+            bf.append((1, (vid(0, j, k), vid(0, j + 1, k), vid(0, j + 1, k + 1), vid(0, j, k + 1))))
+            bf.append((2, (vid(nx, j, k), vid(nx, j + 1, k), vid(nx, j + 1, k + 1), vid(nx, j, k + 1))))
+    path = str(tmp_path / "hex.msh")
+    M.write_gmsh(path, pts, el, bf)
+    m = M.read_gmsh(path)           # y and z sides are untagged: default tag 0
+    assert m.tags == [0, 1, 2] and m.closure_residual() < 1e-14
+    bc = {0: (bte.BTE_BC_SPECULAR, None), 1: (bte.BTE_BC_ISOTHERMAL, 307.0), 2: (bte.BTE_BC_ISOTHERMAL, 300.0)}
+    s, u, ost, _ = run_both(m, W.Dirs("polar_azim", n_polar=4, n_azim=8), W.make_bands(6, 2, 63), bc, 1e-12, 3, 4)
+    assert_matches(s, u, ost)
+    s.close()
