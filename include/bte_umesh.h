@@ -14,7 +14,8 @@
  *               / [1/dt + beta_b + v_b sum_{g>0} g]
  *   Explicit (Eq. 3): I^{n+1} = I^n + dt [beta_b (I0_b - I^n) - v_b sum_f g_f I_f^n].
  * followed by the per-cell reduction, the T_p solve and the I0 refresh of
- * bte.h (all FP64).  Storage is FP64 only.
+ * bte.h (all FP64).  Storage: FP64, or as in bte.h the deviation
+ * I - I0_b(T_ref) in FP32 or BF16 with the update in FP32.
  *
  * Boundary faces carry an integer tag; each tag gets one condition:
  *   BTE_BC_ISOTHERMAL  ghost I0_b(T_face) (Eq. 6);
@@ -61,8 +62,8 @@ typedef struct {
   const int* tag;
 } bte_umesh_desc;
 
-/* Creates a handle.  opts: as in bte.h (precision must be BTE_FP64; learned
- * and beta_T_exp must be 0); may be NULL for the defaults.  *out receives
+/* Creates a handle.  opts: as in bte.h (precision BTE_FP64, BTE_FP32 or
+ * BTE_BF16; learned and beta_T_exp must be 0); may be NULL for the defaults.  *out receives
  * the handle, NULL on failure (message in bte_umesh_last_error(NULL)). */
 int bte_umesh_create(const bte_umesh_desc* mesh, const bte_opts* opts, bte_umesh* out);
 

@@ -431,9 +431,10 @@ class UMeshSolver:
     over the mesh's faces indexed by face id), BTE_BC_SPECULAR or
     BTE_BC_DIFFUSE (T ignored)."""
 
-    def __init__(self, mesh, dirs, bands, bc, T_init=None, stream=None, n_gauss=16):
+    def __init__(self, mesh, dirs, bands, bc, T_init=None, stream=None, n_gauss=16, precision=BTE_FP64):
         import torch
         o = bte_default_opts()
+        o.precision = precision
         if dirs.kind == "inplane":
             o.dir_kind, o.n_inplane = BTE_DIRS_INPLANE, dirs.n_inplane
         else:

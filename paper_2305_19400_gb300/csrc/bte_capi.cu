@@ -631,7 +631,7 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaSt
       if (e == cudaSuccess && a.beta_exp != 0.0)
         e = launch_beta_scale(h->bscale, h->Tp, a.beta_Tref, a.beta_exp, h->ncells, s);
       if (e == cudaSuccess) e = launch_gs_sweep(a, dim, h->gs_threads, s);
-      if (e == cudaSuccess) e = launch_gs_reduce(a, h->ncells, s);
+      if (e == cudaSuccess) e = launch_gs_reduce(BTE_FP64, a, h->ncells, s);
     } else if (e == cudaSuccess) {
       e = launch_sweep(h->opts.precision, h->pd, a, dim, h->threads, h->grid, s);
     }

@@ -381,8 +381,8 @@ __global__ void solve_cells_kernel(SweepArgs a, long long ncells) {
   flush_counters(a, lane, solves, badc);
 }
 
-// Per-cell step after a sweep-ordered pass (FP64 storage): one CTA of 8 warps
-// per cell.  Warp w sums the directions [w nd/8, (w+1) nd/8) for every stored
+// Per-cell step after a separate sweep (the sweep-ordered pass, the
+// unstructured sweep): one CTA of 8 warps per cell.  Warp w sums the directions [w nd/8, (w+1) nd/8) for every stored
 // band (lanes over band pairs); the 8 partials are added in warp order in
 // shared memory (deterministic), then warp 0 forms
 // G_b = sum_d w_d I^{k+1}_{d,b}, E_L = sum_b G_b / v_b, E_p = sum_b beta_b G_b / v_b
@@ -393,17 +393,55 @@ __global__ void solve_cells_kernel(SweepArgs a, long long ncells) {
 // cell's I0 of exponent E; a value up to 32 I0 adds at most 2^55, so a run of
 // 256 cannot overflow), closed by one FP64 FMA (sum x w x unit).  Values
 // beyond that range (or negative, NaN) take the FP64 FMA directly.
+// Reduced storage (deviations from I0_b(T_ref)): each lane sums w_d x deviation
+// in FP32, flushed to FP64 every 16 directions, and G_b gets W I0_b(T_ref).
 constexpr int kRedWarps = 8;
 
+template <typename S>
+__device__ __forceinline__ void reduce_dev_warp(const SweepArgs& a, const S* row, int d0, int d1, int lane,
+                                                double* gpart_w) {
+  const int nbo = a.th.nbo;
+  for (int b0 = 2 * lane; b0 < nbo; b0 += 64) {  // two bands per lane
+    double G0 = 0.0, G1 = 0.0;
+    for (int d = d0; d < d1; d += 16) {  // 16 directions: loads first, then the float sums
+      const int m = min(16, d1 - d);
+      float x0[16], x1[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        x0[k] = x1[k] = 0.f;
+        if (k < m) {
+          const S* p = row + (long long)(d + k) * nbo + b0;
+          x0[k] = Tr<S>::to_float(p[0]);
+          x1[k] = Tr<S>::to_float(p[1]);
+        }
+      }
+      float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float w = k < m ? a.wdir32[d + k] : 0.f;
+        acc0 = fmaf(w, x0[k], acc0);
+        acc1 = fmaf(w, x1[k], acc1);
+      }
+      G0 += (double)acc0;
+      G1 += (double)acc1;
+    }
+    gpart_w[b0] = G0;
+    gpart_w[b0 + 1] = G1;
+  }
+}
+
+template <typename S>
 __global__ void __launch_bounds__(256, 4) gs_reduce_kernel(SweepArgs a, long long ncells) {
   extern __shared__ double gpart[];  // [kRedWarps][nbo]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nbo = a.th.nbo, nd = a.nd, lpc = nbo / 2;
   const int d0 = (int)((long long)wid * nd / kRedWarps), d1 = (int)((long long)(wid + 1) * nd / kRedWarps);
-  const double* __restrict__ I = reinterpret_cast<const double*>(a.Iout);
   unsigned long long solves = 0, badc = 0;
   for (long long P = blockIdx.x; P < ncells; P += gridDim.x) {
-    const double* row = I + P * (long long)nd * nbo;
+    if constexpr (sizeof(S) != 8) {
+      reduce_dev_warp<S>(a, reinterpret_cast<const S*>(a.Iout) + P * (long long)nd * nbo, d0, d1, lane, gpart + wid * nbo);
+    } else {
+    const double* row = reinterpret_cast<const double*>(a.Iout) + P * (long long)nd * nbo;
     for (int lp = lane; lp < lpc; lp += 32) {
       const int b0 = 2 * lp;
       double G[2] = {0.0, 0.0};
@@ -467,12 +505,14 @@ __global__ void __launch_bounds__(256, 4) gs_reduce_kernel(SweepArgs a, long lon
         gpart[wid * nbo + b0 + v] = G[v];
       }
     }
+    }
     __syncthreads();
     if (wid == 0) {
       double el = 0.0, ep = 0.0;
       for (int b = lane; b < nbo; b += 32) {
         double G = gpart[b];
         for (int w = 1; w < kRedWarps; ++w) G += gpart[w * nbo + b];
+        if constexpr (sizeof(S) != 8) G = fma(a.Wtot, a.I0ref[b], G);  // the reference part, sum_d w_d I0_b(T_ref)
         const double e = G * a.th.inv_v[b];
         el += e;
         ep = fma(a.th.beta[b], e, ep);
@@ -657,9 +697,12 @@ cudaError_t launch_solve_cells(const SweepArgs& a, long long ncells, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_gs_reduce(const SweepArgs& a, long long ncells, cudaStream_t s) {
+cudaError_t launch_gs_reduce(int precision, const SweepArgs& a, long long ncells, cudaStream_t s) {
   const int grid = (int)std::min<long long>(std::max(ncells, 1LL), 152LL * 64);
-  gs_reduce_kernel<<<grid, 32 * kRedWarps, (size_t)kRedWarps * a.th.nbo * sizeof(double), s>>>(a, ncells);
+  const size_t sm = (size_t)kRedWarps * a.th.nbo * sizeof(double);
+  if (precision == 0) gs_reduce_kernel<double><<<grid, 32 * kRedWarps, sm, s>>>(a, ncells);
+  else if (precision == 1) gs_reduce_kernel<float><<<grid, 32 * kRedWarps, sm, s>>>(a, ncells);
+  else gs_reduce_kernel<__nv_bfloat16><<<grid, 32 * kRedWarps, sm, s>>>(a, ncells);
   return cudaGetLastError();
 }
 

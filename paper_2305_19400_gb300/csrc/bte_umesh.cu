@@ -26,6 +26,7 @@
 
 #include "../../include/bte_umesh.h"
 #include "bte_internal.h"
+#include "bte_store.cuh"
 #include "bte_tables.h"
 
 using namespace bte;
@@ -33,6 +34,7 @@ using namespace bte;
 namespace {
 
 constexpr int kMaxCellFaces = 64;
+constexpr int kRegFaces = 6;  // faces per cell kept in registers by the reduced-storage sweep
 
 struct UArgs {
   const double* In;        // I^n, or B = (I^n/dt) R (implicit, BM = 2)
@@ -54,7 +56,119 @@ struct UArgs {
   double dt, rdt;
   long long nc;
   int nd, nbp, lpc, dteam;
+  // reduced storage (deviations from I0_b(T_ref)): buffers in the storage type,
+  // R and the ghost deviations as float
+  const void* Ind;
+  const void* Ikd;
+  void* Ioutd;
+  void* Boutd;
+  const float* Rf;
+  const float* ghost_dev;
+  const double* I0ref;
 };
+
+// V consecutive floats (16-byte loads).
+template <int V>
+__device__ __forceinline__ void ldf(const float* p, float (&x)[V]) {
+#pragma unroll
+  for (int i = 0; i < V; i += 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p + i));
+    x[i] = v.x; x[i + 1] = v.y; x[i + 2] = v.z; x[i + 3] = v.w;
+  }
+}
+
+// Reduced-storage form of umesh_sweep_kernel: I = I0_b(T_ref) + deviation, the
+// deviation stored in S (FP32 or BF16) and updated in FP32 with the same
+// equation (both direction sets are point-symmetric, so a closed cell's inflow
+// and outflow sums of |g| are equal and the reference part cancels):
+// implicit R [v sum |g| dev_up + beta (I0 - I0ref)] + (dev^n/dt) R, explicit
+// dev + dt [beta (I0 - I0ref - dev) - v (gout dev - sum |g| dev_up)].
+// A lane holds V bands (16 bytes of storage).
+template <typename S, bool EXPL, int BM>
+__global__ void __launch_bounds__(256) umesh_sweep_dev_kernel(UArgs a) {
+  using T = Tr<S>;
+  constexpr int V = T::V;
+  const int team = a.lpc * a.dteam;
+  const int cpb = blockDim.x / team;
+  const int slot = threadIdx.x / team, tl = threadIdx.x - slot * team;
+  const int dg = tl / a.lpc, lane = tl - dg * a.lpc;
+  const int b0 = V * lane;
+  if (slot >= cpb) return;  // no barrier or shuffle below
+  const long long row = (long long)a.nd * a.nbp;
+  const S* In = reinterpret_cast<const S*>(a.Ind);
+  const S* Isrc = EXPL ? In : reinterpret_cast<const S*>(a.Ikd);
+  S* Io = reinterpret_cast<S*>(a.Ioutd);
+  S* Bo = reinterpret_cast<S*>(a.Boutd);
+  const float dt = (float)a.dt, rdt = (float)a.rdt;
+  float vb[V], bb[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    vb[v] = (float)a.vb[b0 + v];
+    bb[v] = (float)a.bb[b0 + v];
+  }
+  for (long long P = (long long)blockIdx.x * cpb + slot; P < a.nc; P += (long long)gridDim.x * cpb) {
+    const int e0 = a.cf_ptr[P], e1 = a.cf_ptr[P + 1];
+    float src[V];  // beta (I0 - I0ref)
+#pragma unroll
+    for (int v = 0; v < V; ++v) src[v] = bb[v] * (float)(a.I0cell[P * a.nbp + b0 + v] - a.I0ref[b0 + v]);
+    // up to kRegFaces faces (triangles .. hexahedra): their upwind codes stay in
+    // registers, and each direction loads all its g values before any row
+    const int nfc = e1 - e0;
+    const bool small = nfc <= kRegFaces;
+    long long upc[kRegFaces];
+#pragma unroll
+    for (int j = 0; j < kRegFaces; ++j) upc[j] = (small && j < nfc) ? a.cf_up[e0 + j] : 0;
+    for (int d = dg; d < a.nd; d += a.dteam) {
+      const long long off = P * row + (long long)d * a.nbp + b0;
+      float in[V], f[V];
+      T::ld(In + off, in);
+#pragma unroll
+      for (int v = 0; v < V; ++v) f[v] = 0.f;
+      // upwind value of entry e with code up for this direction
+      auto gather = [&](long long up, double ge) {
+        float u[V];
+        if (up >= 0) {
+          T::ld(Isrc + up * row + (long long)d * a.nbp + b0, u);
+        } else {
+          const long long bf = -1 - up;
+          if (a.bf_mirror[bf]) T::ld(Isrc + P * row + (long long)a.refl[a.bf_axis[bf] * a.nd + d] * a.nbp + b0, u);
+          else ldf<V>(a.ghost_dev + bf * a.nbp + b0, u);
+        }
+        const float gf = (float)(-ge);
+#pragma unroll
+        for (int v = 0; v < V; ++v) f[v] = fmaf(gf, u[v], f[v]);
+      };
+      if (small) {
+        double gj[kRegFaces];
+#pragma unroll
+        for (int j = 0; j < kRegFaces; ++j) gj[j] = j < nfc ? a.g[(long long)(e0 + j) * a.nd + d] : 0.0;
+#pragma unroll
+        for (int j = 0; j < kRegFaces; ++j)
+          if (j < nfc && __double_as_longlong(gj[j]) < 0) gather(upc[j], gj[j]);  // inflow: the sign bit
+      } else {
+        for (int e = e0; e < e1; ++e) {
+          const double ge = a.g[(long long)e * a.nd + d];
+          if (__double_as_longlong(ge) < 0) gather(a.cf_up[e], ge);
+        }
+      }
+      float r[V];
+      if (EXPL) {
+        const float go = (float)a.gout[P * a.nd + d];
+#pragma unroll
+        for (int v = 0; v < V; ++v) r[v] = fmaf(dt, fmaf(-bb[v], in[v], src[v]) - vb[v] * fmaf(go, in[v], -f[v]), in[v]);
+      } else {
+        float R[V], B[V];
+        ldf<V>(a.Rf + off, R);
+#pragma unroll
+        for (int v = 0; v < V; ++v) B[v] = BM == 2 ? in[v] : in[v] * rdt * R[v];
+        if (BM == 1) T::st(Bo + off, B);
+#pragma unroll
+        for (int v = 0; v < V; ++v) r[v] = fmaf(R[v], fmaf(vb[v], f[v], src[v]), B[v]);
+      }
+      T::st(Io + off, r);
+    }
+  }
+}
 
 __device__ __forceinline__ double2 ld2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
 
@@ -119,12 +233,13 @@ __global__ void __launch_bounds__(256) umesh_sweep_kernel(UArgs a) {
 
 // R[P][d][b] = 1 / (1/dt + beta_b + v_b gout[P][d]): the implicit update's
 // reciprocal diagonal, fixed while dt is (one thread per element).
+template <typename R_t>
 __global__ void umesh_rcp_kernel(const double* gout, const double* vb, const double* bb, double rdt, long long nc,
-                                 int nd, int nbp, double* R) {
+                                 int nd, int nbp, R_t* R) {
   const long long n = nc * nd * nbp;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(i % nbp);
-    R[i] = 1.0 / fma(vb[b], gout[i / nbp], rdt + bb[b]);
+    R[i] = (R_t)(1.0 / fma(vb[b], gout[i / nbp], rdt + bb[b]));
   }
 }
 
@@ -159,26 +274,29 @@ __global__ void umesh_gout_kernel(const int* cf_ptr, const double* g, int nd, lo
 // Diffuse ghosts: for each listed boundary face, per band,
 // sum_{S.n > 0} (S.n) I / sum_{S.n < 0} |S.n| of the owner cell.  One CTA of
 // kDiffWarps warps per face: warp w sums the directions [w nd/W, (w+1) nd/W)
-// (lanes over bands); the partial sums are added in warp order.
+// (lanes over bands); the partial sums are added in warp order.  Reduced
+// storage sums the stored deviations and writes the ghost deviation (the
+// reference part passes through the ratio: the sets are point-symmetric).
 constexpr int kDiffWarps = 8;
 
-__global__ void __launch_bounds__(32 * kDiffWarps) umesh_diffuse_kernel(const double* I, const long long* bfs, int nlist,
+template <typename St>
+__global__ void __launch_bounds__(32 * kDiffWarps) umesh_diffuse_kernel(const St* I, const long long* bfs, int nlist,
                                                                         const long long* bface, const long long* owner,
                                                                         const double* nA, const double* S, int nd,
-                                                                        int nbp, double* ghost) {
+                                                                        int nbp, double* ghost, float* ghost_dev) {
   extern __shared__ double part[];  // [kDiffWarps][2][nbp]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int d0 = (int)((long long)wid * nd / kDiffWarps), d1 = (int)((long long)(wid + 1) * nd / kDiffWarps);
   for (int k = blockIdx.x; k < nlist; k += gridDim.x) {
     const long long bf = bfs[k], f = bface[bf], P = owner[f];
     const double* n = nA + 3 * f;
-    const double* row = I + P * (long long)nd * nbp;
+    const St* row = I + P * (long long)nd * nbp;
     for (int b = lane; b < nbp; b += 32) {
       double num = 0.0, den = 0.0;
 #pragma unroll 4
       for (int e = d0; e < d1; ++e) {
         const double sn = S[3 * e] * n[0] + S[3 * e + 1] * n[1] + S[3 * e + 2] * n[2];
-        if (sn > 0.0) num = fma(sn, row[(long long)e * nbp + b], num);
+        if (sn > 0.0) num = fma(sn, Tr<St>::to_double(row[(long long)e * nbp + b]), num);
         else den -= sn;
       }
       part[(wid * 2) * nbp + b] = num;
@@ -191,30 +309,34 @@ __global__ void __launch_bounds__(32 * kDiffWarps) umesh_diffuse_kernel(const do
         num += part[(w * 2) * nbp + b];
         den += part[(w * 2 + 1) * nbp + b];
       }
-      ghost[bf * nbp + b] = den > 0.0 ? num / den : 0.0;
+      const double v = den > 0.0 ? num / den : 0.0;
+      if constexpr (sizeof(St) == 8) ghost[bf * nbp + b] = v;
+      else ghost_dev[bf * nbp + b] = (float)v;
     }
     __syncthreads();
   }
 }
 
 // Net heat flow out through each boundary face: one warp per face.
-__global__ void umesh_face_flux_kernel(const double* I, const double* ghost, const long long* bface, long long nbf,
-                                       const long long* owner, const double* nA, const int* bf_mirror,
-                                       const int* bf_axis, const int* refl, const double* S, int nd, int nbp, int nb,
-                                       double* Qb) {
+template <typename St>
+__global__ void umesh_face_flux_kernel(const St* I, const double* I0ref, const double* ghost, const float* ghost_dev,
+                                       const long long* bface, long long nbf, const long long* owner, const double* nA,
+                                       const int* bf_mirror, const int* bf_axis, const int* refl, const double* S,
+                                       int nd, int nbp, int nb, double* Qb) {
   const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
   for (long long bf = blockIdx.x * (long long)warps + threadIdx.x / 32; bf < nbf; bf += (long long)gridDim.x * warps) {
     const long long f = bface[bf], P = owner[f];
     const double* n = nA + 3 * f;
-    const double* row = I + P * (long long)nd * nbp;
+    const long long base = P * (long long)nd * nbp;
     double s = 0.0;
     for (int d = 0; d < nd; ++d) {
       const double sn = S[3 * d] * n[0] + S[3 * d + 1] * n[1] + S[3 * d + 2] * n[2];
       for (int b = lane; b < nb; b += 32) {
         double v;
-        if (sn > 0.0) v = row[(long long)d * nbp + b];
-        else if (bf_mirror[bf]) v = row[(long long)refl[bf_axis[bf] * nd + d] * nbp + b];
-        else v = ghost[bf * nbp + b];
+        if (sn > 0.0) v = full_I(I, base + (long long)d * nbp + b, b, I0ref);
+        else if (bf_mirror[bf]) v = full_I(I, base + (long long)refl[bf_axis[bf] * nd + d] * nbp + b, b, I0ref);
+        else if constexpr (sizeof(St) == 8) v = ghost[bf * nbp + b];
+        else v = I0ref[b] + (double)ghost_dev[bf * nbp + b];
         s = fma(sn, v, s);
       }
     }
@@ -263,8 +385,13 @@ struct bte_umesh_ctx {
   double *I0cell = nullptr, *J = nullptr, *Teval = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr;
   double *ghost = nullptr, *g = nullptr, *gout = nullptr, *S_d = nullptr, *w_d = nullptr, *nA_d = nullptr;
   double *vb_d = nullptr, *bb_d = nullptr, *bfT_d = nullptr, *scratch = nullptr, *Qb = nullptr, *qbuf = nullptr;
-  double* R = nullptr;     // implicit reciprocal diagonal for R_dt
+  double* R = nullptr;     // implicit reciprocal diagonal for R_dt (FP64 storage)
+  float* Rf = nullptr;     //   the same as float (reduced storage)
   double R_dt = -1.0;
+  int prec = BTE_FP64;     // storage of I: FP64, or FP32 / BF16 deviations from I0_b(T_ref)
+  double* I0ref = nullptr; // [nbp] I0_b(T_ref)
+  float* ghost_dev = nullptr;  // [bface][nbp] ghost deviations (reduced storage)
+  float* w32_d = nullptr;  // [nd] direction weights as float
   double *node_c = nullptr, *node_C = nullptr, *a_p = nullptr, *a_L = nullptr, *inv_v = nullptr, *beta_d = nullptr;
   int *cf_ptr = nullptr, *bf_mirror_d = nullptr, *bf_axis_d = nullptr, *refl_d = nullptr;
   long long *cf_up = nullptr, *bface_d = nullptr, *owner_d = nullptr, *diff_d = nullptr;
@@ -343,6 +470,9 @@ SweepArgs cell_args(bte_umesh_ctx* u, double* Inew) {
   a.fix = u->fix;
   a.fix_count = u->fix_count;
   a.partial = 0;
+  a.I0ref = u->I0ref;
+  a.Wtot = u->Wtot;
+  a.wdir32 = u->w32_d;
   a.th = uthermo(u);
   return a;
 }
@@ -352,9 +482,19 @@ int ensure_mem(bte_umesh_ctx* u) {
   if (u->mem_ready) return BTE_OK;
   int rc;
   const long long nc = u->nc, nd = u->nd, nbp = u->nbp, nbf = (long long)u->bface.size();
-  for (int i = 0; i < 3; ++i)
-    if ((rc = dalloc(u, &u->I[i], (size_t)(nc * nd * nbp)))) return rc;
-  if ((rc = dalloc(u, &u->R, (size_t)(nc * nd * nbp)))) return rc;
+  const size_t eb = u->prec == BTE_FP64 ? 8 : (u->prec == BTE_FP32 ? 4 : 2);
+  for (int i = 0; i < 3; ++i) {
+    char* q = nullptr;
+    if ((rc = dalloc(u, &q, (size_t)(nc * nd * nbp) * eb))) return rc;
+    u->I[i] = reinterpret_cast<double*>(q);
+  }
+  if (u->prec == BTE_FP64) {
+    if ((rc = dalloc(u, &u->R, (size_t)(nc * nd * nbp)))) return rc;
+  } else if ((rc = dalloc(u, &u->Rf, (size_t)(nc * nd * nbp)))) {
+    return rc;
+  }
+  if ((rc = dalloc(u, &u->I0ref, nbp)) || (rc = dalloc(u, &u->ghost_dev, nbf * nbp)) || (rc = dalloc(u, &u->w32_d, nd)))
+    return rc;
   if ((rc = dalloc(u, &u->I0cell, nc * nbp)) || (rc = dalloc(u, &u->J, nc * 3 * nbp)) ||
       (rc = dalloc(u, &u->Teval, nc)) || (rc = dalloc(u, &u->Tp, nc)) || (rc = dalloc(u, &u->TL, nc)) ||
       (rc = dalloc(u, &u->EL, nc)) || (rc = dalloc(u, &u->ghost, nbf * nbp)) || (rc = dalloc(u, &u->bfT_d, nbf)) ||
@@ -423,12 +563,21 @@ int ensure_mem(bte_umesh_ctx* u) {
       (rc = upload(u, u->inv_v, iv.data(), iv.size())) || (rc = upload(u, u->beta_d, be.data(), be.size())) ||
       (rc = upload(u, u->vb_d, vbp.data(), nbp)) || (rc = upload(u, u->bb_d, bbp.data(), nbp)))
     return rc;
-  for (int i = 0; i < 3; ++i) UTRY(u, cudaMemsetAsync(u->I[i], 0, (size_t)(nc * nd * nbp) * 8, s));
+  for (int i = 0; i < 3; ++i) UTRY(u, cudaMemsetAsync(u->I[i], 0, (size_t)(nc * nd * nbp) * eb, s));
   UTRY(u, cudaMemsetAsync(u->ghost, 0, (size_t)std::max(nbf * nbp, 1LL) * 8, s));
+  UTRY(u, cudaMemsetAsync(u->ghost_dev, 0, (size_t)std::max(nbf * nbp, 1LL) * 4, s));
+  {
+    std::vector<float> w32(u->w.begin(), u->w.end());
+    if ((rc = upload(u, u->w32_d, w32.data(), nd))) return rc;
+    // I0_b(T_ref): the reference the reduced storage keeps deviations from
+    const double tref = u->opts.T_ref;
+    if ((rc = upload(u, u->scratch, &tref, 1))) return rc;
+    UTRY(u, launch_wall_I0(u->I0ref, u->scratch, 1, uthermo(u), s));
+  }
   UTRY(u, cudaMemsetAsync(u->counters, 0, sizeof(DevCounters), s));
   UTRY(u, cudaMemsetAsync(u->fix_count, 0, 4, s));
   UTRY(u, cudaStreamSynchronize(s));
-  u->lpc = u->nbp / 2;
+  u->lpc = u->nbp / values_per_lane(u->prec);
   u->dteam = std::max(1, std::min(256 / u->lpc, u->nd));
   u->mem_ready = true;
   return BTE_OK;
@@ -452,15 +601,26 @@ int upload_bc(bte_umesh_ctx* u) {
     return rc;
   u->ndiff = (int)diffl.size();
   if (nbf > 0) UTRY(u, launch_wall_I0(u->ghost, u->bfT_d, nbf, uthermo(u), u->stream));
+  if (nbf > 0 && u->prec != BTE_FP64) UTRY(u, launch_wall_dev(u->ghost_dev, u->ghost, u->I0ref, nbf, u->nbp, u->stream));
   UTRY(u, cudaStreamSynchronize(u->stream));
   return BTE_OK;
 }
 
-cudaError_t refresh_diffuse(bte_umesh_ctx* u, const double* I) {
+cudaError_t refresh_diffuse(bte_umesh_ctx* u, const void* I) {
   if (u->ndiff == 0) return cudaSuccess;
   const int grid = (int)std::min<long long>(u->ndiff, 152LL * 16);
-  umesh_diffuse_kernel<<<grid, 32 * kDiffWarps, (size_t)kDiffWarps * 2 * u->nbp * sizeof(double), u->stream>>>(
-      I, u->diff_d, u->ndiff, u->bface_d, u->owner_d, u->nA_d, u->S_d, u->nd, u->nbp, u->ghost);
+  const size_t sm = (size_t)kDiffWarps * 2 * u->nbp * sizeof(double);
+  if (u->prec == BTE_FP64)
+    umesh_diffuse_kernel<double><<<grid, 32 * kDiffWarps, sm, u->stream>>>(
+        (const double*)I, u->diff_d, u->ndiff, u->bface_d, u->owner_d, u->nA_d, u->S_d, u->nd, u->nbp, u->ghost, nullptr);
+  else if (u->prec == BTE_FP32)
+    umesh_diffuse_kernel<float><<<grid, 32 * kDiffWarps, sm, u->stream>>>(
+        (const float*)I, u->diff_d, u->ndiff, u->bface_d, u->owner_d, u->nA_d, u->S_d, u->nd, u->nbp, nullptr,
+        u->ghost_dev);
+  else
+    umesh_diffuse_kernel<__nv_bfloat16><<<grid, 32 * kDiffWarps, sm, u->stream>>>(
+        (const __nv_bfloat16*)I, u->diff_d, u->ndiff, u->bface_d, u->owner_d, u->nA_d, u->S_d, u->nd, u->nbp, nullptr,
+        u->ghost_dev);
   return cudaGetLastError();
 }
 
@@ -487,7 +647,8 @@ int bte_umesh_create(const bte_umesh_desc* m, const bte_opts* opts, bte_umesh* o
   bte_opts o;
   bte_default_opts(&o);
   if (opts) o = *opts;
-  if (o.precision != BTE_FP64) return ufail(nullptr, BTE_E_ARG, "unstructured meshes store FP64 only");
+  if (o.precision != BTE_FP64 && o.precision != BTE_FP32 && o.precision != BTE_BF16)
+    return ufail(nullptr, BTE_E_ARG, "unknown precision %d", o.precision);
   if (o.learned || o.beta_T_exp != 0.0) return ufail(nullptr, BTE_E_ARG, "learned mode and beta_T_exp are not offered here");
   if (o.n_gauss < 1 || o.n_gauss > kMaxGauss) return ufail(nullptr, BTE_E_ARG, "n_gauss must be in [1, %d]", kMaxGauss);
   for (long long P = 0; P < m->ncells; ++P)
@@ -503,6 +664,7 @@ int bte_umesh_create(const bte_umesh_desc* m, const bte_opts* opts, bte_umesh* o
   }
   auto* u = new bte_umesh_ctx();
   u->opts = o;
+  u->prec = o.precision;
   u->stream = (cudaStream_t)o.cuda_stream;
   u->dim = m->dim;
   u->nc = m->ncells;
@@ -615,7 +777,7 @@ int bte_umesh_set_initial(bte_umesh u, const double* T_cells, double T_uniform) 
   int rc = upload(u, u->scratch, T.data(), u->nc);
   if (rc) return rc;
   u->cur = 0;
-  UTRY(u, launch_init_cells(BTE_FP64, u->I[0], u->I0cell, u->J, u->Tp, u->Teval, u->TL, u->EL, u->scratch, nullptr, 0,
+  UTRY(u, launch_init_cells(u->prec, u->I[0], u->I0cell, u->J, u->Tp, u->Teval, u->TL, u->EL, u->scratch, u->I0ref, 0,
                             (int)u->nc, u->nd, uthermo(u), u->stream));
   UTRY(u, cudaStreamSynchronize(u->stream));
   u->init_done = true;
@@ -635,8 +797,11 @@ int bte_umesh_step(bte_umesh u, double dt, int nsteps, int ninner, int scheme, b
   if (ninner < 1) return ufail(u, BTE_E_ARG, "ninner must be >= 1");
   cudaStream_t s = u->stream;
   if (scheme != BTE_EXPLICIT && u->R_dt != dt) {
-    umesh_rcp_kernel<<<grid_for(u->nc * u->nd * u->nbp, 256), 256, 0, s>>>(u->gout, u->vb_d, u->bb_d, 1.0 / dt, u->nc,
-                                                                           u->nd, u->nbp, u->R);
+    const int gr = grid_for(u->nc * u->nd * u->nbp, 256);
+    if (u->prec == BTE_FP64)
+      umesh_rcp_kernel<double><<<gr, 256, 0, s>>>(u->gout, u->vb_d, u->bb_d, 1.0 / dt, u->nc, u->nd, u->nbp, u->R);
+    else
+      umesh_rcp_kernel<float><<<gr, 256, 0, s>>>(u->gout, u->vb_d, u->bb_d, 1.0 / dt, u->nc, u->nd, u->nbp, u->Rf);
     UTRY(u, cudaGetLastError());
     u->R_dt = dt;
   }
@@ -646,6 +811,9 @@ int bte_umesh_step(bte_umesh u, double dt, int nsteps, int ninner, int scheme, b
   }
   UArgs a{};
   a.R = u->R;
+  a.Rf = u->Rf;
+  a.ghost_dev = u->ghost_dev;
+  a.I0ref = u->I0ref;
   a.I0cell = u->I0cell;
   a.ghost = u->ghost;
   a.cf_ptr = u->cf_ptr;
@@ -694,15 +862,31 @@ int bte_umesh_step(bte_umesh u, double dt, int nsteps, int ninner, int scheme, b
       }
       a.Ik = u->I[k];
       a.Iout = u->I[o];
+      a.Ind = a.In;
+      a.Ikd = a.Ik;
+      a.Ioutd = a.Iout;
+      a.Boutd = a.Bout;
       UTRY(u, cudaMemsetAsync(u->fix_count, 0, 4, s));
       UTRY(u, refresh_diffuse(u, a.Ik));
-      if (scheme == BTE_EXPLICIT) umesh_sweep_kernel<true, 0><<<grid, threads, 0, s>>>(a);
-      else if (bm == 1) umesh_sweep_kernel<false, 1><<<grid, threads, 0, s>>>(a);
-      else if (bm == 2) umesh_sweep_kernel<false, 2><<<grid, threads, 0, s>>>(a);
-      else umesh_sweep_kernel<false, 0><<<grid, threads, 0, s>>>(a);
+      if (u->prec == BTE_FP64) {
+        if (scheme == BTE_EXPLICIT) umesh_sweep_kernel<true, 0><<<grid, threads, 0, s>>>(a);
+        else if (bm == 1) umesh_sweep_kernel<false, 1><<<grid, threads, 0, s>>>(a);
+        else if (bm == 2) umesh_sweep_kernel<false, 2><<<grid, threads, 0, s>>>(a);
+        else umesh_sweep_kernel<false, 0><<<grid, threads, 0, s>>>(a);
+      } else if (u->prec == BTE_FP32) {
+        if (scheme == BTE_EXPLICIT) umesh_sweep_dev_kernel<float, true, 0><<<grid, threads, 0, s>>>(a);
+        else if (bm == 1) umesh_sweep_dev_kernel<float, false, 1><<<grid, threads, 0, s>>>(a);
+        else if (bm == 2) umesh_sweep_dev_kernel<float, false, 2><<<grid, threads, 0, s>>>(a);
+        else umesh_sweep_dev_kernel<float, false, 0><<<grid, threads, 0, s>>>(a);
+      } else {
+        if (scheme == BTE_EXPLICIT) umesh_sweep_dev_kernel<__nv_bfloat16, true, 0><<<grid, threads, 0, s>>>(a);
+        else if (bm == 1) umesh_sweep_dev_kernel<__nv_bfloat16, false, 1><<<grid, threads, 0, s>>>(a);
+        else if (bm == 2) umesh_sweep_dev_kernel<__nv_bfloat16, false, 2><<<grid, threads, 0, s>>>(a);
+        else umesh_sweep_dev_kernel<__nv_bfloat16, false, 0><<<grid, threads, 0, s>>>(a);
+      }
       UTRY(u, cudaGetLastError());
       SweepArgs c = cell_args(u, a.Iout);
-      UTRY(u, launch_gs_reduce(c, u->nc, s));
+      UTRY(u, launch_gs_reduce(u->prec, c, u->nc, s));
       if (u->solve_tp) UTRY(u, launch_fixup(c, nullptr, s));
       launches += 2 + (u->solve_tp ? 1 : 0) + (u->ndiff ? 1 : 0);
       k = o;
@@ -754,9 +938,22 @@ int bte_umesh_get_T(bte_umesh u, int which, double* out, int on_device) {
 int bte_umesh_get_intensity(bte_umesh u, double* out) {
   if (!u || !out) return u ? ufail(u, BTE_E_ARG, "out is NULL") : BTE_E_ARG;
   if (!u->init_done) return ufail(u, BTE_E_STATE, "no state");
-  UTRY(u, cudaMemcpy2DAsync(out, (size_t)u->nb * 8, u->I[u->cur], (size_t)u->nbp * 8, (size_t)u->nb * 8,
-                            (size_t)(u->nc * u->nd), cudaMemcpyDeviceToHost, u->stream));
-  UTRY(u, cudaStreamSynchronize(u->stream));
+  if (u->prec == BTE_FP64) {
+    UTRY(u, cudaMemcpy2DAsync(out, (size_t)u->nb * 8, u->I[u->cur], (size_t)u->nbp * 8, (size_t)u->nb * 8,
+                              (size_t)(u->nc * u->nd), cudaMemcpyDeviceToHost, u->stream));
+    UTRY(u, cudaStreamSynchronize(u->stream));
+    return BTE_OK;
+  }
+  // reduced storage: full FP64 values (I0_b(T_ref) + deviation) through a temporary device buffer
+  double* tmp = nullptr;
+  const size_t n = (size_t)(u->nc * u->nd) * u->nb;
+  cudaError_t e = cudaMalloc(&tmp, n * 8);
+  if (e != cudaSuccess) return ufail(u, BTE_E_NOMEM, "cudaMalloc(%zu bytes): %s", n * 8, cudaGetErrorString(e));
+  e = launch_pack(u->prec, nullptr, tmp, u->I[u->cur], nullptr, u->I0ref, u->nc, u->nd, u->nb, u->nbp, 0, u->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, n * 8, cudaMemcpyDeviceToHost, u->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return ufail(u, BTE_E_CUDA, "reading the intensities: %s", cudaGetErrorString(e));
   return BTE_OK;
 }
 
@@ -766,7 +963,7 @@ int bte_umesh_get_flux(bte_umesh u, double* q, double* Q) {
   cudaStream_t s = u->stream;
   const double* I = u->I[u->cur];
   if (q) {
-    UTRY(u, launch_flux_cells(BTE_FP64, I, nullptr, u->qbuf, u->S_d, 0, (int)u->nc, u->nd, u->nbp, 3, s));
+    UTRY(u, launch_flux_cells(u->prec, I, u->I0ref, u->qbuf, u->S_d, 0, (int)u->nc, u->nd, u->nbp, 3, s));
     UTRY(u, cudaMemcpyAsync(q, u->qbuf, (size_t)u->nc * 3 * 8, cudaMemcpyDeviceToHost, s));
     UTRY(u, cudaStreamSynchronize(s));
   }
@@ -774,9 +971,20 @@ int bte_umesh_get_flux(bte_umesh u, double* q, double* Q) {
     const long long nbf = (long long)u->bface.size();
     UTRY(u, refresh_diffuse(u, I));
     if (nbf > 0) {
-      umesh_face_flux_kernel<<<grid_for(nbf, 4), 128, 0, s>>>(I, u->ghost, u->bface_d, nbf, u->owner_d, u->nA_d,
-                                                              u->bf_mirror_d, u->bf_axis_d, u->refl_d, u->S_d, u->nd,
-                                                              u->nbp, u->nb, u->Qb);
+      const int gr = grid_for(nbf, 4);
+      if (u->prec == BTE_FP64)
+        umesh_face_flux_kernel<double><<<gr, 128, 0, s>>>((const double*)I, u->I0ref, u->ghost, u->ghost_dev, u->bface_d,
+                                                          nbf, u->owner_d, u->nA_d, u->bf_mirror_d, u->bf_axis_d,
+                                                          u->refl_d, u->S_d, u->nd, u->nbp, u->nb, u->Qb);
+      else if (u->prec == BTE_FP32)
+        umesh_face_flux_kernel<float><<<gr, 128, 0, s>>>((const float*)I, u->I0ref, u->ghost, u->ghost_dev, u->bface_d,
+                                                         nbf, u->owner_d, u->nA_d, u->bf_mirror_d, u->bf_axis_d,
+                                                         u->refl_d, u->S_d, u->nd, u->nbp, u->nb, u->Qb);
+      else
+        umesh_face_flux_kernel<__nv_bfloat16><<<gr, 128, 0, s>>>((const __nv_bfloat16*)I, u->I0ref, u->ghost,
+                                                                 u->ghost_dev, u->bface_d, nbf, u->owner_d, u->nA_d,
+                                                                 u->bf_mirror_d, u->bf_axis_d, u->refl_d, u->S_d, u->nd,
+                                                                 u->nbp, u->nb, u->Qb);
       UTRY(u, cudaGetLastError());
     }
     std::vector<double> Qb(nbf);

@@ -226,3 +226,48 @@ def test_hexahedral_gmsh_mesh(tmp_path):
     s, u, ost, _ = run_both(m, W.Dirs("polar_azim", n_polar=4, n_azim=8), W.make_bands(6, 2, 63), bc, 1e-12, 3, 4)
     assert_matches(s, u, ost)
     s.close()
+
+
+@pytest.mark.parametrize("precision,tol,scheme,dt,nsteps,ninner", [
+    (bte.BTE_FP32, 1e-4, bte.BTE_IMPLICIT_JACOBI, 1e-12, 3, 8),
+    (bte.BTE_FP32, 1e-4, bte.BTE_EXPLICIT, 2e-13, 12, 1),
+    (bte.BTE_BF16, 2e-3, bte.BTE_IMPLICIT_JACOBI, 1e-12, 3, 8)])
+def test_reduced_storage_on_jittered_triangles(precision, tol, scheme, dt, nsteps, ninner):
+    """FP32 (BF16) deviation storage against the FP64 oracle: max |dT| within
+    1e-4 K (2e-3 K for BF16, short runs only) on the 400-direction mesh with
+    every wall kind; heat flux within the same relative bound x 100."""
+    m = M.tri_grid(13, 9, 130e-9, 90e-9, jitter=0.3, seed=21)
+    dirs = W.Dirs("polar_azim", n_polar=20, n_azim=20)
+    bands = W.make_bands(40, 15, 19406)
+    bc = {0: (bte.BTE_BC_ISOTHERMAL, hot_wall(m, 0, 305.0, 5.0)), 1: (bte.BTE_BC_ISOTHERMAL, 300.0),
+          2: (bte.BTE_BC_SPECULAR, None), 3: (bte.BTE_BC_DIFFUSE, None)}
+    s = bte.UMeshSolver(m, dirs, bands, bc, precision=precision)
+    rc, st = s.step(dt, nsteps, ninner, scheme)
+    assert rc >= 0 and st["nonfinite"] == 0
+    u = O.UMeshProblem(m, O.dirs_for(dirs), bands, bc)
+    ost = u.init_state(m.T_init)
+    u.run(ost, dt, nsteps, ninner, O.EXPLICIT if scheme == bte.BTE_EXPLICIT else O.IMPLICIT)
+    assert np.max(np.abs(s.T(bte.BTE_T_LATTICE) - ost["TL"])) <= tol
+    assert np.max(np.abs(s.T(bte.BTE_T_PSEUDO) - ost["Tp"])) <= tol
+    q, Q = s.flux()
+    q_ref, Q_ref = u.flux(ost["I"])
+    assert np.linalg.norm(q - q_ref) <= 100 * tol * np.linalg.norm(q_ref)
+    assert np.max(np.abs(Q - Q_ref)) <= 100 * tol * np.max(np.abs(Q_ref))
+    I = s.intensity()
+    assert np.max(np.abs(I - ost["I"]) / np.abs(ost["I"])) <= 100 * tol
+    s.close()
+
+
+def test_fp32_tetrahedra_with_diffuse_walls():
+    m = M.tet_box(3, 3, 2, 30e-9, 30e-9, 20e-9)
+    bc = {0: (bte.BTE_BC_ISOTHERMAL, 306.0), 1: (bte.BTE_BC_ISOTHERMAL, 300.0), 2: (bte.BTE_BC_DIFFUSE, None),
+          3: (bte.BTE_BC_SPECULAR, None), 4: (bte.BTE_BC_DIFFUSE, None), 5: (bte.BTE_BC_SPECULAR, None)}
+    dirs = W.Dirs("polar_azim", n_polar=4, n_azim=8)
+    bands = W.make_bands(8, 3, 52)
+    s = bte.UMeshSolver(m, dirs, bands, bc, precision=bte.BTE_FP32)
+    s.step(1e-12, 3, 4)
+    u = O.UMeshProblem(m, O.dirs_for(dirs), bands, bc)
+    ost = u.init_state(m.T_init)
+    u.run(ost, 1e-12, 3, 4)
+    assert np.max(np.abs(s.T(bte.BTE_T_LATTICE) - ost["TL"])) <= 1e-4
+    s.close()
