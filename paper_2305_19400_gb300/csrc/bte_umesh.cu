@@ -34,7 +34,6 @@ using namespace bte;
 namespace {
 
 constexpr int kMaxCellFaces = 64;
-constexpr int kRegFaces = 6;  // faces per cell kept in registers by the reduced-storage sweep
 
 struct UArgs {
   const double* In;        // I^n, or B = (I^n/dt) R (implicit, BM = 2)
@@ -111,44 +110,27 @@ __global__ void __launch_bounds__(256) umesh_sweep_dev_kernel(UArgs a) {
     float src[V];  // beta (I0 - I0ref)
 #pragma unroll
     for (int v = 0; v < V; ++v) src[v] = bb[v] * (float)(a.I0cell[P * a.nbp + b0 + v] - a.I0ref[b0 + v]);
-    // up to kRegFaces faces (triangles .. hexahedra): their upwind codes stay in
-    // registers, and each direction loads all its g values before any row
-    const int nfc = e1 - e0;
-    const bool small = nfc <= kRegFaces;
-    long long upc[kRegFaces];
-#pragma unroll
-    for (int j = 0; j < kRegFaces; ++j) upc[j] = (small && j < nfc) ? a.cf_up[e0 + j] : 0;
     for (int d = dg; d < a.nd; d += a.dteam) {
       const long long off = P * row + (long long)d * a.nbp + b0;
       float in[V], f[V];
       T::ld(In + off, in);
 #pragma unroll
       for (int v = 0; v < V; ++v) f[v] = 0.f;
-      // upwind value of entry e with code up for this direction
-      auto gather = [&](long long up, double ge) {
-        float u[V];
-        if (up >= 0) {
-          T::ld(Isrc + up * row + (long long)d * a.nbp + b0, u);
-        } else {
-          const long long bf = -1 - up;
-          if (a.bf_mirror[bf]) T::ld(Isrc + P * row + (long long)a.refl[a.bf_axis[bf] * a.nd + d] * a.nbp + b0, u);
-          else ldf<V>(a.ghost_dev + bf * a.nbp + b0, u);
-        }
-        const float gf = (float)(-ge);
+      for (int e = e0; e < e1; ++e) {
+        const double ge = a.g[(long long)e * a.nd + d];
+        if (__double_as_longlong(ge) < 0) {  // inflow: the sign bit, tested on the integer pipe
+          const long long up = a.cf_up[e];
+          float u[V];
+          if (up >= 0) {
+            T::ld(Isrc + up * row + (long long)d * a.nbp + b0, u);
+          } else {
+            const long long bf = -1 - up;
+            if (a.bf_mirror[bf]) T::ld(Isrc + P * row + (long long)a.refl[a.bf_axis[bf] * a.nd + d] * a.nbp + b0, u);
+            else ldf<V>(a.ghost_dev + bf * a.nbp + b0, u);
+          }
+          const float gf = (float)(-ge);
 #pragma unroll
-        for (int v = 0; v < V; ++v) f[v] = fmaf(gf, u[v], f[v]);
-      };
-      if (small) {
-        double gj[kRegFaces];
-#pragma unroll
-        for (int j = 0; j < kRegFaces; ++j) gj[j] = j < nfc ? a.g[(long long)(e0 + j) * a.nd + d] : 0.0;
-#pragma unroll
-        for (int j = 0; j < kRegFaces; ++j)
-          if (j < nfc && __double_as_longlong(gj[j]) < 0) gather(upc[j], gj[j]);  // inflow: the sign bit
-      } else {
-        for (int e = e0; e < e1; ++e) {
-          const double ge = a.g[(long long)e * a.nd + d];
-          if (__double_as_longlong(ge) < 0) gather(a.cf_up[e], ge);
+          for (int v = 0; v < V; ++v) f[v] = fmaf(gf, u[v], f[v]);
         }
       }
       float r[V];
