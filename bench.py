@@ -338,7 +338,7 @@ def run_gs_variant(peaks):
                          "frac": fl / FP64_PEAK_FLOPS}}
 
 
-def run_umesh_variant(peaks):
+def run_umesh_variant(peaks, precision=None):
     """Unstructured mesh: a 1.28 um square of 128x128 grid squares split into
     32768 jittered triangles, 400 directions (20 x 20) x 55 band-pols, FP64,
     walls hot 305 K / cold 300 K / mirror / diffuse, 15 inner iterations per
@@ -353,7 +353,8 @@ def run_umesh_variant(peaks):
     bands = W.make_bands(40, 15, 19406)
     bc = {0: (bte.BTE_BC_ISOTHERMAL, 305.0), 1: (bte.BTE_BC_ISOTHERMAL, 300.0),
           2: (bte.BTE_BC_SPECULAR, None), 3: (bte.BTE_BC_DIFFUSE, None)}
-    s = bte.UMeshSolver(m, dirs, bands, bc)
+    prec = bte.BTE_FP64 if precision is None else precision
+    s = bte.UMeshSolver(m, dirs, bands, bc, precision=prec)
     dt, ninner, steps = 1e-12, 15, 3
     s.step(dt, 1, ninner, want_stats=False)
     torch.cuda.synchronize()
@@ -377,11 +378,20 @@ def run_umesh_variant(peaks):
     s.close()
     del s
     torch.cuda.empty_cache()
-    return {"workload": "fp64_unstructured_32768_triangles_400dir", "dtype": "f64", "value": ups, "unit": UNIT,
+    if prec == bte.BTE_FP64:
+        roof = {"bound": "alu", "achieved": fl / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": fl / FP64_PEAK_FLOPS, "flop_per_update": flops}
+    else:  # B (or I^n), R and I^{k+1} in the sweep, I^{k+1} again in the per-cell step
+        bpu = 16 if prec == bte.BTE_FP32 else 10   # BF16: 2-byte I, R stays a 4-byte float
+        gbs = ups * bpu / 1e9
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"], "bytes_per_update": bpu}
+    name = {bte.BTE_FP64: "fp64", bte.BTE_FP32: "fp32", bte.BTE_BF16: "bf16"}[prec]
+    return {"workload": f"{name}_unstructured_32768_triangles_400dir",
+            "dtype": {bte.BTE_FP64: "f64", bte.BTE_FP32: "f32", bte.BTE_BF16: "bf16-storage/f32"}[prec],
+            "value": ups, "unit": UNIT,
             "ms_per_step": ms / steps, "steps": steps, "inner_iterations_per_step": ninner, "cells": m.ncells,
-            "inflow_faces_per_cell_direction": float(nin),
-            "roofline": {"bound": "alu", "achieved": fl / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                         "frac": fl / FP64_PEAK_FLOPS, "flop_per_update": flops}}
+            "inflow_faces_per_cell_direction": float(nin), "roofline": roof}
 
 
 def main():
@@ -515,6 +525,7 @@ def main():
         variants = run_variants(peaks)
         variants.append(run_gs_variant(peaks))
         variants.append(run_umesh_variant(peaks))
+        variants.append(run_umesh_variant(peaks, 1))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "strong" if partitioned else "weak",

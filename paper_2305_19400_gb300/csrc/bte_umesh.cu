@@ -82,9 +82,11 @@ __device__ __forceinline__ void ldf(const float* p, float (&x)[V]) {
 // and outflow sums of |g| are equal and the reference part cancels):
 // implicit R [v sum |g| dev_up + beta (I0 - I0ref)] + (dev^n/dt) R, explicit
 // dev + dt [beta (I0 - I0ref - dev) - v (gout dev - sum |g| dev_up)].
-// A lane holds V bands (16 bytes of storage).
+// A lane holds V bands (16 bytes of storage).  The kernel is bound by the
+// latency of the face gathers, so it is capped at 6 CTAs of 252 threads per SM
+// (more warps in flight; measured faster than 3-5 CTAs despite small spills).
 template <typename S, bool EXPL, int BM>
-__global__ void __launch_bounds__(256) umesh_sweep_dev_kernel(UArgs a) {
+__global__ void __launch_bounds__(256, 6) umesh_sweep_dev_kernel(UArgs a) {
   using T = Tr<S>;
   constexpr int V = T::V;
   const int team = a.lpc * a.dteam;
