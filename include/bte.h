@@ -211,7 +211,7 @@ int bte_set_initial(bte_handle h, int geom, const double* T_cells, double T_unif
  *   I^{k+1} = [I^n/dt + beta I0^k + v sum_ax c_ax I_up^k]/[1/dt + beta + v sum_ax c_ax]
  *   (c_ax = |S_ax|/(w_d Delta_ax)), then reduction, T_p solve, I0 refresh.
  * scheme BTE_EXPLICIT: forward Euler (Eq. 3 with Eq. 5), ninner ignored.
- * scheme BTE_IMPLICIT_GS (FP64 storage only, else BTE_E_ARG): backward Euler
+ * scheme BTE_IMPLICIT_GS (every storage precision): backward Euler
  *   with sweep-ordered (Gauss-Seidel) inner iterations, an extension beyond
  *   the paper's point-Jacobi form: each (d, b) visits the cells in its upwind
  *   order, so an interior upwind neighbour holds its value of the current

@@ -289,7 +289,7 @@ void build_gs(bte_ctx* h, int ndc, int tx, int ty) {
     }
   }
   start[noct] = (int)h->gs_dirs.size();
-  const int lanes = h->nbp / 2;
+  const int lanes = h->nbp / values_per_lane(h->opts.precision);
   ndc = std::max(1, std::min(ndc, 256 / lanes));
   for (size_t gi = 0; gi < h->geoms.size(); ++gi)
     for (int o = 0; o < noct; ++o)
@@ -630,8 +630,8 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaSt
     if (scheme == BTE_IMPLICIT_GS) {
       if (e == cudaSuccess && a.beta_exp != 0.0)
         e = launch_beta_scale(h->bscale, h->Tp, a.beta_Tref, a.beta_exp, h->ncells, s);
-      if (e == cudaSuccess) e = launch_gs_sweep(a, dim, h->gs_threads, s);
-      if (e == cudaSuccess) e = launch_gs_reduce(BTE_FP64, a, h->ncells, s);
+      if (e == cudaSuccess) e = launch_gs_sweep(h->opts.precision, a, dim, h->gs_threads, s);
+      if (e == cudaSuccess) e = launch_gs_reduce(h->opts.precision, a, h->ncells, s);
     } else if (e == cudaSuccess) {
       e = launch_sweep(h->opts.precision, h->pd, a, dim, h->threads, h->grid, s);
     }
@@ -964,8 +964,6 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
   if (nsteps < 0) return fail(h, BTE_E_ARG, "nsteps must be >= 0");
   if (scheme != BTE_IMPLICIT_JACOBI && scheme != BTE_EXPLICIT && scheme != BTE_IMPLICIT_GS)
     return fail(h, BTE_E_ARG, "unknown scheme %d", scheme);
-  if (scheme == BTE_IMPLICIT_GS && h->opts.precision != BTE_FP64)
-    return fail(h, BTE_E_ARG, "the sweep-ordered scheme needs FP64 storage");
   if (scheme == BTE_EXPLICIT) ninner = 1;
   if (ninner < 1) return fail(h, BTE_E_ARG, "ninner must be >= 1");
   const int cscheme = scheme == BTE_EXPLICIT ? BTE_EXPLICIT : BTE_IMPLICIT_JACOBI;  // coefficient set
@@ -1084,9 +1082,9 @@ int autotune_gs(bte_ctx* h, char* report, size_t report_len) {
       a.Bout = nullptr;
       a.In = a.Ik = h->Ibuf[h->cur];
       a.Iout = h->Ibuf[spare];
-      CUDA_TRY(h, launch_gs_sweep(a, dim, h->gs_threads, s));
+      CUDA_TRY(h, launch_gs_sweep(h->opts.precision, a, dim, h->gs_threads, s));
       CUDA_TRY(h, cudaEventRecord(h->ev0, s));
-      for (int r = 0; r < 3; ++r) CUDA_TRY(h, launch_gs_sweep(a, dim, h->gs_threads, s));
+      for (int r = 0; r < 3; ++r) CUDA_TRY(h, launch_gs_sweep(h->opts.precision, a, dim, h->gs_threads, s));
       CUDA_TRY(h, cudaEventRecord(h->ev1, s));
       CUDA_TRY(h, cudaEventSynchronize(h->ev1));
       float ms = 0.f;
@@ -1101,7 +1099,8 @@ int autotune_gs(bte_ctx* h, char* report, size_t report_len) {
   char buf[128];
   h->gs_tune_report = "directions_per_cta,tile_x,tile_y,threads,ms_per_pass\n";
   for (auto& c : tried) {
-    snprintf(buf, sizeof buf, "%d,%d,%d,%d,%.4f\n", c.ndc, c.tx, c.ty, (h->nbp / 2) * c.ndc * std::max(1, 256 / ((h->nbp / 2) * c.ndc)), c.ms);
+    const int lanes = h->nbp / values_per_lane(h->opts.precision);
+    snprintf(buf, sizeof buf, "%d,%d,%d,%d,%.4f\n", c.ndc, c.tx, c.ty, lanes * c.ndc * std::max(1, 256 / (lanes * c.ndc)), c.ms);
     h->gs_tune_report += buf;
   }
   snprintf(buf, sizeof buf, "chosen,%d,%d,%d,%d\n", best.ndc, best.tx, best.ty, h->gs_threads);
@@ -1119,8 +1118,6 @@ int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t repor
   if (!(dt > 0 && std::isfinite(dt))) return fail(h, BTE_E_ARG, "dt must be > 0");
   if (scheme != BTE_IMPLICIT_JACOBI && scheme != BTE_EXPLICIT && scheme != BTE_IMPLICIT_GS)
     return fail(h, BTE_E_ARG, "unknown scheme %d", scheme);
-  if (scheme == BTE_IMPLICIT_GS && h->opts.precision != BTE_FP64)
-    return fail(h, BTE_E_ARG, "the sweep-ordered scheme needs FP64 storage");
   int rc = ensure_coef(h, dt, scheme == BTE_EXPLICIT ? BTE_EXPLICIT : BTE_IMPLICIT_JACOBI);
   if (rc) return rc;
   if (scheme == BTE_IMPLICIT_GS) return autotune_gs(h, report, report_len);

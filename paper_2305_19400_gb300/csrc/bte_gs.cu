@@ -22,6 +22,7 @@
 // another.  Upwind values written in this pass are read with ld.global.cg
 // (L2), everything else is read-only here.
 #include "bte_internal.h"
+#include "bte_store.cuh"
 
 namespace bte {
 
@@ -43,6 +44,43 @@ __device__ __forceinline__ double2 upwind(const SweepArgs& a, const DevGeom* gp,
   if (gp->bc[side] == 3)
     return ldg2(reinterpret_cast<const double*>(gp->gdir[side]) + face * ((long long)a.nd * nbp) + (base - Prow));
   return ldg2(Ik + Prow + (long long)rdir * nbp + b0);
+}
+
+// The walk of one unit: column tiles in upwind order, wavefronts a + b + l = t
+// within a tile, one CTA barrier per wavefront; update(i, j, k) for every cell
+// of this thread's cell slots.  Every thread of the CTA runs the same loops.
+template <int DIM, typename F>
+__device__ __forceinline__ void walk(const SweepArgs& a, int nx, int ny, int nz, bool act, int grp, int ngrp, bool ax_,
+                                     bool ay_, bool az_, F&& update) {
+  if constexpr (DIM == 2) {
+    for (int u0 = 0; u0 < nx; u0 += a.gs_tx) {  // strips of columns, upwind first
+      const int w = min(a.gs_tx, nx - u0);
+      for (int t = 0; t < w + ny - 1; ++t) {
+        const int lo = max(0, t - (ny - 1)), hi = min(w - 1, t);
+        if (act)
+          for (int s = lo + grp; s <= hi; s += ngrp) {
+            const int ux = u0 + s, uy = t - s;
+            update(ax_ ? ux : nx - 1 - ux, ay_ ? uy : ny - 1 - uy, 0);
+          }
+        __syncthreads();
+      }
+    }
+  } else {
+    for (int v0 = 0; v0 < ny; v0 += a.gs_ty)
+      for (int u0 = 0; u0 < nx; u0 += a.gs_tx) {  // column tiles, upwind first
+        const int wx = min(a.gs_tx, nx - u0), wy = min(a.gs_ty, ny - v0);
+        for (int t = 0; t < wx + wy + nz - 2; ++t) {
+          if (act)
+            for (int s = grp; s < wx * wy; s += ngrp) {
+              const int p = s % wx, q = s / wx, l = t - p - q;
+              if (l < 0 || l >= nz) continue;
+              const int ux = u0 + p, uy = v0 + q;
+              update(ax_ ? ux : nx - 1 - ux, ay_ ? uy : ny - 1 - uy, az_ ? l : nz - 1 - l);
+            }
+          __syncthreads();
+        }
+      }
+  }
 }
 
 // BM: 0 In is I^n; 1 In is I^n and B = A_n I^n is also stored; 2 In holds B.
@@ -124,35 +162,101 @@ __global__ void __launch_bounds__(256, 3) gs_sweep_kernel(SweepArgs a) {
       st2(Io + base, rx, ry);
     };
 
-    if constexpr (DIM == 2) {
-      for (int u0 = 0; u0 < nx; u0 += a.gs_tx) {  // strips of columns, upwind first
-        const int w = min(a.gs_tx, nx - u0);
-        for (int t = 0; t < w + ny - 1; ++t) {
-          const int lo = max(0, t - (ny - 1)), hi = min(w - 1, t);
-          if (act)
-            for (int s = lo + grp; s <= hi; s += ngrp) {
-              const int ux = u0 + s, uy = t - s;
-              update(ax_ ? ux : nx - 1 - ux, ay_ ? uy : ny - 1 - uy, 0);
-            }
-          __syncthreads();
+    walk<DIM>(a, nx, ny, nz, act, grp, ngrp, ax_, ay_, az_, update);
+  }
+}
+
+// Reduced storage (FP32 / BF16 deviations from I0_b(T_ref), update in FP32):
+// the same walk and equation on deviations,
+//   dev' = P dev^n + Q [v_b sum_ax c_ax dev_up + beta_b (I0 - I0ref)],
+//   Q = 1 / (1/dt + beta_b + v_b sum_ax c_ax), P = Q / dt,
+// with beta_b scaled per cell when tau depends on T.  A lane holds V bands
+// (16 bytes of storage); wall ghosts are the float deviation rows (isothermal,
+// diffuse), the side's per-direction rows (partially specular) or the cell's
+// own previous iterate mirrored.
+template <typename S, int DIM>
+__global__ void __launch_bounds__(256, 3) gs_sweep_dev_kernel(SweepArgs a) {
+  using T = Tr<S>;
+  constexpr int V = T::V;
+  const int nbp = a.th.nbo, nd = a.nd;
+  const int lpc = nbp / V;
+  const int team = lpc * a.gs_ndc;
+  const int ngrp = blockDim.x / team;
+  const int grp = threadIdx.x / team;
+  const int tl = threadIdx.x - grp * team;
+  const int dc = tl / lpc, lane = tl - dc * lpc;
+  const int b0 = V * lane;
+  const long long row = (long long)nd * nbp;
+  const S* __restrict__ In = reinterpret_cast<const S*>(a.In);
+  const S* __restrict__ Ik = reinterpret_cast<const S*>(a.Ik);
+  S* Io = reinterpret_cast<S*>(a.Iout);
+  const bool tT = a.beta_exp != 0.0;
+  float vb[V], bb[V], i0r[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    vb[v] = a.vb32[b0 + v];
+    bb[v] = a.bb32[b0 + v];
+    i0r[v] = (float)a.I0ref[b0 + v];
+  }
+  for (int u = blockIdx.x; u < a.gs_nunits; u += gridDim.x) {
+    const GsUnit un = a.gs_units[u];
+    const DevGeom* gp = a.geoms + un.geom;
+    const int nx = gp->nx, ny = gp->ny, nz = DIM == 3 ? gp->nz : 1;
+    const bool act = grp < ngrp && dc < un.ndc;
+    const int d = a.gs_dirs[un.dir0 + (act ? dc : 0)];
+    const DirInfo di = a.dirs[d];
+    const bool ax_ = di.up & 1, ay_ = (di.up >> 1) & 1, az_ = (di.up >> 2) & 1;
+    const float4 cc = a.dirc[(size_t)gp->cls * nd + d];  // c_x, c_y, c_z, sum
+    const long long off = (long long)d * nbp + b0;
+    const long long sx = row, sy = (long long)nx * row, sz = (long long)nx * ny * row;
+    // upwind deviations along one axis: this pass's neighbour, or the wall ghost
+    auto upwind_dev = [&](int side, bool interior, long long base, long long step, long long Prow, int rdir,
+                          long long face, float (&x)[V]) {
+      if (interior) {
+        const S* p = Io + base + step;
+        if constexpr (sizeof(S) == 4) {
+          const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+          x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+        } else {
+          T::unpack(__ldcg(reinterpret_cast<const uint4*>(p)), x);
         }
+      } else if (gp->bc[side] == 0) {
+        ldgv<float, V>(a.I0wall_dev + (gp->face0[side] + face) * nbp + b0, x);
+      } else if (gp->bc[side] == 3) {
+        T::ld(reinterpret_cast<const S*>(gp->gdir[side]) + face * row + (base - Prow), x);
+      } else {
+        T::ld(Ik + Prow + (long long)rdir * nbp + b0, x);
       }
-    } else {
-      for (int v0 = 0; v0 < ny; v0 += a.gs_ty)
-        for (int u0 = 0; u0 < nx; u0 += a.gs_tx) {  // column tiles, upwind first
-          const int wx = min(a.gs_tx, nx - u0), wy = min(a.gs_ty, ny - v0);
-          for (int t = 0; t < wx + wy + nz - 2; ++t) {
-            if (act)
-              for (int s = grp; s < wx * wy; s += ngrp) {
-                const int p = s % wx, q = s / wx, l = t - p - q;
-                if (l < 0 || l >= nz) continue;
-                const int ux = u0 + p, uy = v0 + q;
-                update(ax_ ? ux : nx - 1 - ux, ay_ ? uy : ny - 1 - uy, az_ ? l : nz - 1 - l);
-              }
-            __syncthreads();
-          }
-        }
-    }
+    };
+    auto update = [&](int i, int j, int k) {
+      const long long P = gp->cell0 + ((long long)k * ny + j) * nx + i;
+      const long long Prow = P * row;
+      const long long base = Prow + off;
+      float in[V], ux[V], uy[V], uz[V];
+      T::ld(In + base, in);
+      upwind_dev(ax_ ? 0 : 1, ax_ ? i > 0 : i < nx - 1, base, ax_ ? -sx : sx, Prow, di.rx,
+                 (long long)j + (long long)ny * k, ux);
+      upwind_dev(ay_ ? 2 : 3, ay_ ? j > 0 : j < ny - 1, base, ay_ ? -sy : sy, Prow, di.ry,
+                 (long long)i + (long long)nx * k, uy);
+      if (DIM == 3)
+        upwind_dev(az_ ? 4 : 5, az_ ? k > 0 : k < nz - 1, base, az_ ? -sz : sz, Prow, di.rz,
+                   (long long)i + (long long)nx * j, uz);
+      const float sc = tT ? (float)a.bscale[P] : 1.f;
+      float r[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const float be = bb[v] * sc;
+        const float src = be * ((float)a.I0cell[P * nbp + b0 + v] - i0r[v]);
+        float Q;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(Q) : "f"(a.rdt32 + fmaf(vb[v], cc.w, be)));
+        float f = cc.x * ux[v];
+        f = fmaf(cc.y, uy[v], f);
+        if (DIM == 3) f = fmaf(cc.z, uz[v], f);
+        r[v] = fmaf(Q, fmaf(vb[v], f, src), Q * a.rdt32 * in[v]);
+      }
+      T::st(Io + base, r);
+    };
+    walk<DIM>(a, nx, ny, nz, act, grp, ngrp, ax_, ay_, az_, update);
   }
 }
 
@@ -178,9 +282,19 @@ __global__ void beta_scale_kernel(double* out, const double* Tp, double Tref, do
 }  // namespace
 
 // threads: a multiple of lpc * gs_ndc, at most 256; one CTA per unit.
-cudaError_t launch_gs_sweep(const SweepArgs& a, int dim, int threads, cudaStream_t s) {
+cudaError_t launch_gs_sweep(int precision, const SweepArgs& a, int dim, int threads, cudaStream_t s) {
   if (a.gs_nunits <= 0) return cudaSuccess;
   const int grid = a.gs_nunits;
+  if (precision == 1) {
+    if (dim == 3) gs_sweep_dev_kernel<float, 3><<<grid, threads, 0, s>>>(a);
+    else gs_sweep_dev_kernel<float, 2><<<grid, threads, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  if (precision == 2) {
+    if (dim == 3) gs_sweep_dev_kernel<__nv_bfloat16, 3><<<grid, threads, 0, s>>>(a);
+    else gs_sweep_dev_kernel<__nv_bfloat16, 2><<<grid, threads, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   return dim == 3 ? launch_dim<3>(a, threads, grid, s) : launch_dim<2>(a, threads, grid, s);
 }
 

@@ -161,7 +161,7 @@ cudaError_t launch_solve_cells(const SweepArgs& a, long long ncells, cudaStream_
 // sweep-ordered pass (bte_gs.cu) and its per-cell step (bte_kernels.cu): the
 // pass writes Iout; the reduction writes E_L, E_p of the stored bands to Epart
 // (partial) or solves T_p and refreshes I0 at once (whole handle)
-cudaError_t launch_gs_sweep(const SweepArgs& a, int dim, int threads, cudaStream_t s);
+cudaError_t launch_gs_sweep(int precision, const SweepArgs& a, int dim, int threads, cudaStream_t s);
 cudaError_t launch_gs_reduce(int precision, const SweepArgs& a, long long ncells, cudaStream_t s);
 cudaError_t launch_beta_scale(double* out, const double* Tp, double Tref, double p, long long ncells, cudaStream_t s);
 cudaError_t launch_diffuse_ghosts(int precision, const void* I, const double* I0ref, double* I0wall, float* I0wall_dev,
