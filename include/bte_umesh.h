@@ -93,6 +93,12 @@ int bte_umesh_get_T(bte_umesh u, int which, double* out, int on_device);
 /* Intensities into host out[ncells][nd][nb]. */
 int bte_umesh_get_intensity(bte_umesh u, double* out);
 
+/* Checkpoint restore: replaces the intensities with host in[ncells][nd][nb]
+ * (FP64; stored as deviations in the reduced modes) and T_p with host
+ * Tp_cells[ncells]; I0 and the cached temperature models are recomputed from
+ * T_p and E_L from the intensities.  Needs bte_umesh_set_initial first. */
+int bte_umesh_set_intensity(bte_umesh u, const double* in, const double* Tp_cells);
+
 /* Heat flux: q (host [ncells][3], may be NULL) = sum_b sum_d S_d I_{d,b} per
  * cell; Q (host [nfaces], may be NULL) = the net heat flow out through each
  * boundary face, sum_b sum_d (S_d . n_f A_f) I_face (own value leaving,

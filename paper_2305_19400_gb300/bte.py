@@ -91,6 +91,7 @@ SIGNATURES = {
     "bte_umesh_get_T": (C.c_int, [_h, C.c_int, _vp, C.c_int]),
     "bte_umesh_get_intensity": (C.c_int, [_h, _dp]),
     "bte_umesh_get_flux": (C.c_int, [_h, _dp, _dp]),
+    "bte_umesh_set_intensity": (C.c_int, [_h, _dp, _dp]),
     "bte_umesh_last_error": (C.c_char_p, [_h]),
     "bte_umesh_destroy": (None, [_h]),
 }
@@ -490,6 +491,12 @@ class UMeshSolver:
         out = np.zeros((self.mesh.ncells, self.dirs.nd, len(self.bands.vg)))
         _ucheck(self.h, lib().bte_umesh_get_intensity(self.h, out.ctypes.data_as(_dp)))
         return out
+
+    def set_state(self, I, Tp):
+        """Checkpoint restore: intensities [ncells, nd, nb] and T_p [ncells]."""
+        I = np.ascontiguousarray(I, dtype=np.float64)
+        Tp = np.ascontiguousarray(Tp, dtype=np.float64)
+        _ucheck(self.h, lib().bte_umesh_set_intensity(self.h, I.ctypes.data_as(_dp), Tp.ctypes.data_as(_dp)))
 
     def flux(self):
         q = np.zeros((self.mesh.ncells, 3))

@@ -941,6 +941,31 @@ int bte_umesh_get_intensity(bte_umesh u, double* out) {
   return BTE_OK;
 }
 
+int bte_umesh_set_intensity(bte_umesh u, const double* in, const double* Tp_cells) {
+  if (!u) return BTE_E_ARG;
+  if (!in || !Tp_cells) return ufail(u, BTE_E_ARG, "in and Tp_cells are required");
+  if (!u->init_done) return ufail(u, BTE_E_STATE, "bte_umesh_set_initial must come first");
+  for (long long P = 0; P < u->nc; ++P)
+    if (!(std::isfinite(Tp_cells[P]) && Tp_cells[P] >= kTmin && Tp_cells[P] <= kTmax))
+      return ufail(u, BTE_E_ARG, "cell %lld: T_p must lie in [1, 5000] K", P);
+  cudaStream_t s = u->stream;
+  const size_t n = (size_t)(u->nc * u->nd) * u->nb;
+  double* tmp = nullptr;
+  cudaError_t e = cudaMalloc(&tmp, n * 8);
+  if (e != cudaSuccess) return ufail(u, BTE_E_NOMEM, "cudaMalloc(%zu bytes): %s", n * 8, cudaGetErrorString(e));
+  e = cudaMemcpyAsync(tmp, in, n * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_pack(u->prec, tmp, nullptr, nullptr, u->I[u->cur], u->I0ref, u->nc, u->nd, u->nb, u->nbp, 1, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(u->Tp, Tp_cells, u->nc * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_state_from_Tp(u->I0cell, u->J, u->Tp, u->Teval, u->nc, uthermo(u), s);
+  if (e == cudaSuccess) e = launch_energy_L(u->prec, u->I[u->cur], u->I0ref, u->EL, u->w_d, u->nc, u->nd, uthermo(u), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return ufail(u, BTE_E_CUDA, "restoring the state: %s", cudaGetErrorString(e));
+  u->TL_valid = false;
+  return BTE_OK;
+}
+
 int bte_umesh_get_flux(bte_umesh u, double* q, double* Q) {
   if (!u) return BTE_E_ARG;
   if (!u->init_done) return ufail(u, BTE_E_STATE, "no state");

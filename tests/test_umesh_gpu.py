@@ -271,3 +271,25 @@ def test_fp32_tetrahedra_with_diffuse_walls():
     u.run(ost, 1e-12, 3, 4)
     assert np.max(np.abs(s.T(bte.BTE_T_LATTICE) - ost["TL"])) <= 1e-4
     s.close()
+
+
+@pytest.mark.parametrize("precision", [bte.BTE_FP64, bte.BTE_FP32])
+def test_checkpoint_restore_continues_the_run(precision):
+    m = M.tri_grid(9, 7, 90e-9, 70e-9, jitter=0.2, seed=41)
+    dirs = W.Dirs("inplane", n_inplane=16)
+    bands = W.make_bands(6, 2, 64)
+    bc = {0: (bte.BTE_BC_ISOTHERMAL, 309.0), 1: (bte.BTE_BC_ISOTHERMAL, 300.0), 2: (bte.BTE_BC_SPECULAR, None),
+          3: (bte.BTE_BC_DIFFUSE, None)}
+    a = bte.UMeshSolver(m, dirs, bands, bc, precision=precision)
+    a.step(1e-12, 3, 5)
+    I, Tp = a.intensity(), a.T(bte.BTE_T_PSEUDO)
+    a.step(1e-12, 2, 5)
+    b = bte.UMeshSolver(m, dirs, bands, bc, precision=precision)
+    b.set_state(I, Tp)
+    b.step(1e-12, 2, 5)
+    # the restore evaluates I0 exactly at T_p where the run carried its cached model: round-off apart
+    tol_T, tol_I = (1e-14, 1e-13) if precision == bte.BTE_FP64 else (1e-12, 1e-6)
+    assert np.max(np.abs(b.T(bte.BTE_T_LATTICE) - a.T(bte.BTE_T_LATTICE)) / a.T(bte.BTE_T_LATTICE)) <= tol_T
+    assert np.max(np.abs(b.intensity() - a.intensity()) / a.intensity()) <= tol_I
+    a.close()
+    b.close()
