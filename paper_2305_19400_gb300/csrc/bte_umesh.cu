@@ -64,6 +64,7 @@ struct UArgs {
   const float* Rf;
   const float* ghost_dev;
   const double* I0ref;
+  const float* g32;        // [entries][nd] g as float (reduced storage)
 };
 
 // V consecutive floats (16-byte loads).
@@ -119,8 +120,8 @@ __global__ void __launch_bounds__(256, 6) umesh_sweep_dev_kernel(UArgs a) {
 #pragma unroll
       for (int v = 0; v < V; ++v) f[v] = 0.f;
       for (int e = e0; e < e1; ++e) {
-        const double ge = a.g[(long long)e * a.nd + d];
-        if (__double_as_longlong(ge) < 0) {  // inflow: the sign bit, tested on the integer pipe
+        const float ge = a.g32[(long long)e * a.nd + d];
+        if (__float_as_int(ge) < 0) {  // inflow: the sign bit, tested on the integer pipe
           const long long up = a.cf_up[e];
           float u[V];
           if (up >= 0) {
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(256, 6) umesh_sweep_dev_kernel(UArgs a) {
             if (a.bf_mirror[bf]) T::ld(Isrc + P * row + (long long)a.refl[a.bf_axis[bf] * a.nd + d] * a.nbp + b0, u);
             else ldf<V>(a.ghost_dev + bf * a.nbp + b0, u);
           }
-          const float gf = (float)(-ge);
+          const float gf = -ge;
 #pragma unroll
           for (int v = 0; v < V; ++v) f[v] = fmaf(gf, u[v], f[v]);
         }
@@ -239,6 +240,11 @@ __global__ void umesh_geom_kernel(const long long* ent_face, const int* ent_sign
     const double sn = S[3 * d] * n[0] + S[3 * d + 1] * n[1] + S[3 * d + 2] * n[2];
     g[i] = ent_sign[e] * sn / (w[d] * vol[ent_cell[e]]);
   }
+}
+
+__global__ void to_float_kernel(const double* x, long long n, float* y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
 }
 
 // gout[P][d] = sum over the cell's entries (in order) of the positive g.
@@ -376,6 +382,7 @@ struct bte_umesh_ctx {
   double* I0ref = nullptr; // [nbp] I0_b(T_ref)
   float* ghost_dev = nullptr;  // [bface][nbp] ghost deviations (reduced storage)
   float* w32_d = nullptr;  // [nd] direction weights as float
+  float* g32 = nullptr;    // [entries][nd] g as float (reduced storage)
   double *node_c = nullptr, *node_C = nullptr, *a_p = nullptr, *a_L = nullptr, *inv_v = nullptr, *beta_d = nullptr;
   int *cf_ptr = nullptr, *bf_mirror_d = nullptr, *bf_axis_d = nullptr, *refl_d = nullptr;
   long long *cf_up = nullptr, *bface_d = nullptr, *owner_d = nullptr, *diff_d = nullptr;
@@ -536,6 +543,11 @@ int ensure_mem(bte_umesh_ctx* u) {
   UTRY(u, cudaGetLastError());
   umesh_gout_kernel<<<grid_for(nc * nd, 256), 256, 0, s>>>(u->cf_ptr, u->g, (int)nd, nc, u->gout);
   UTRY(u, cudaGetLastError());
+  if (u->prec != BTE_FP64) {
+    if ((rc = dalloc(u, &u->g32, nent * nd))) return rc;
+    to_float_kernel<<<grid_for(nent * nd, 256), 256, 0, s>>>(u->g, nent * nd, u->g32);
+    UTRY(u, cudaGetLastError());
+  }
   // band tables
   std::vector<double> nC, nCC, ap, aL, iv, be;
   build_thermo(u->nb, u->nbp, u->ng, u->wlo.data(), u->whi.data(), u->vg.data(), u->beta.data(), u->deg.data(), u->Wtot,
@@ -796,6 +808,7 @@ int bte_umesh_step(bte_umesh u, double dt, int nsteps, int ninner, int scheme, b
   UArgs a{};
   a.R = u->R;
   a.Rf = u->Rf;
+  a.g32 = u->g32;
   a.ghost_dev = u->ghost_dev;
   a.I0ref = u->I0ref;
   a.I0cell = u->I0cell;
