@@ -246,3 +246,24 @@ def test_band_ranks_as_processes_over_gloo():
     scale = np.max(np.abs(ref["I"]))
     for r, (lo, hi) in enumerate(ranges):
         assert np.max(np.abs(out[r][3] - ref["I"][:, :, lo:hi])) <= 1e-12 * scale
+
+
+def test_band_ranks_with_diffuse_and_partially_specular_walls():
+    """Wall ghosts of a rank's own bands (diffuse rows, per-direction partial
+    rows) under the band partition, against the oracle's whole-band run."""
+    def mk():
+        wl = W.cfg2(12, 9)
+        wl.geoms[0].bc[2] = (W.BC_DIFFUSE, None)
+        wl.geoms[0].bc[3] = (W.BC_PARTIAL, 0.3)
+        return wl
+    wl = mk()
+    ranges = [(0, 20), (20, 55)]
+    solvers, stats, x = run_ranks(wl, ranges, 2, 4)
+    _, ref = oracle_run(mk(), 2, 4)
+    for s in solvers:
+        assert np.max(np.abs(s.T(0, bte.BTE_T_LATTICE) - ref["TL"]) / ref["TL"]) <= 1e-12
+    I = ref["I"]
+    for s, (b0, b1) in zip(solvers, ranges):
+        assert np.max(np.abs(s.intensity(0) - I[:, :, b0:b1]) / np.abs(I[:, :, b0:b1])) <= 1e-11
+    for s in solvers:
+        s.close()
