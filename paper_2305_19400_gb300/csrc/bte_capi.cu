@@ -83,6 +83,7 @@ struct bte_ctx {
   double *I0cell = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr, *I0wall = nullptr;
   void* coef = nullptr;
   double *J = nullptr, *Teval = nullptr, *I0ref = nullptr, *scratch_pack = nullptr;
+  double* Msum = nullptr;     // [cell][3] the T_p model's sums sum_b a_p,b J_k,b
   double* I0ref_o = nullptr;  // I0_b(T_ref) of the stored bands (aliases I0ref unless a band range is set)
   double* Epart = nullptr;    // band-range handles: [ncells][2] partial (E_L, E_p) for the exchange
   float *I0wall_dev = nullptr, *wdir32 = nullptr, *vb32 = nullptr, *bb32 = nullptr;
@@ -183,6 +184,7 @@ size_t carve(bte_ctx* h, char* base) {
   h->I0cell = (double*)take((size_t)h->ncells * h->nbp * 8);
   h->J = (double*)take((size_t)h->ncells * 3 * h->nbp_all * 8);
   h->Teval = (double*)take((size_t)h->ncells * 8);
+  h->Msum = (double*)take((size_t)h->ncells * 3 * 8);
   h->I0ref = (double*)take((size_t)h->nbp_all * 8);
   const bool ranged = h->nb != h->nb_all;
   h->I0ref_o = ranged ? (double*)take((size_t)h->nbp * 8) : h->I0ref;
@@ -516,6 +518,7 @@ SweepArgs sweep_args(bte_ctx* h) {
   a.Tp = h->Tp;
   a.Teval = h->Teval;
   a.J = h->J;
+  a.Msum = h->Msum;
   a.EL = h->EL;
   a.I0wall = h->I0wall;
   a.I0wall_dev = h->I0wall_dev;
@@ -948,7 +951,7 @@ int bte_set_initial(bte_handle h, int geom, const double* T_cells, double T_unif
     if (!(t >= kTmin && t <= kTmax)) return fail(h, BTE_E_ARG, "initial temperature %g outside [1, 5000] K", t);
   if ((rc = ensure_memory(h))) return rc;
   CUDA_TRY(h, cudaMemcpyAsync(h->scratch_T, T.data(), nc * 8, cudaMemcpyHostToDevice, h->stream));
-  CUDA_TRY(h, launch_init_cells(h->opts.precision, h->Ibuf[h->cur], h->I0cell, h->J, h->Tp, h->Teval, h->TL, h->EL,
+  CUDA_TRY(h, launch_init_cells(h->opts.precision, h->Ibuf[h->cur], h->I0cell, h->J, h->Msum, h->Tp, h->Teval, h->TL, h->EL,
                                 h->scratch_T, h->I0ref_o, h->cell0[geom], (int)nc, h->nd, thermo(h), h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->init_set[geom] = true;
@@ -1297,6 +1300,7 @@ int bte_set_intensity(bte_handle h, int geom, const double* in, const double* Tp
     CUDA_TRY(h, cudaMemcpyAsync(h->Tp + h->cell0[geom], Tp_cells, nc * 8, cudaMemcpyHostToDevice, s));
   }
   CUDA_TRY(h, launch_state_from_Tp(h->I0cell + h->cell0[geom] * h->nbp, h->J + h->cell0[geom] * 3 * h->nbp_all,
+                                   h->Msum + h->cell0[geom] * 3,
                                    h->Tp + h->cell0[geom], h->Teval + h->cell0[geom], nc, thermo(h), s));
   if (h->Epart) {
     h->EL_partial = true;  // this handle holds only its bands' share of E_L until the next step's exchange

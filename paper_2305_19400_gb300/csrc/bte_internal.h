@@ -106,6 +106,7 @@ struct SweepArgs {
   double* Tp;               // [cell] in/out
   double* Teval;            // [cell] evaluation point of the cached quadrature model
   double* J;                // [cell][3][nbp] I0, dI0/dT, d2I0/dT2 at Teval
+  double* Msum;             // [cell][3] sum_b a_p,b J_k,b: the T_p model's sums, kept with J
   double* EL;               // [cell] out
   const double* I0wall;     // [face][nbp] FP64 ghosts
   const float* I0wall_dev;  // [face][nbp] FP32 ghosts minus I0ref (reduced modes)
@@ -184,10 +185,10 @@ cudaError_t mlp_forward_backward(const float* p, int k, const float* X, int ldx,
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, int step, cudaStream_t s);
 cudaError_t launch_solve_batch(ThermoTables th, const double* Ep, const double* T0, int n, double trust_rel, int maxit,
                                const MLPView* mlp, double* Tout, int* evals, cudaStream_t s);
-cudaError_t launch_init_cells(int precision, void* I, double* I0cell, double* J, double* Tp, double* Te, double* TL,
-                              double* EL, const double* Tcells, const double* I0ref, long long cell0, int ncells, int nd,
-                              ThermoTables th, cudaStream_t s);
-cudaError_t launch_state_from_Tp(double* I0cell, double* J, const double* Tp, double* Te, long long ncells,
+cudaError_t launch_init_cells(int precision, void* I, double* I0cell, double* J, double* Msum, double* Tp, double* Te,
+                              double* TL, double* EL, const double* Tcells, const double* I0ref, long long cell0,
+                              int ncells, int nd, ThermoTables th, cudaStream_t s);
+cudaError_t launch_state_from_Tp(double* I0cell, double* J, double* Msum, const double* Tp, double* Te, long long ncells,
                                  ThermoTables th, cudaStream_t s);
 cudaError_t launch_wall_I0(double* I0wall, const double* Tfaces, long long nfaces, ThermoTables th, cudaStream_t s);
 cudaError_t launch_wall_dev(float* out, const double* I0wall, const double* I0ref, long long nfaces, int nbp,

@@ -55,6 +55,9 @@ __global__ void fixup_kernel(SweepArgs a, int learned, MLPView m) {
     if (lane == 0) {
       a.Teval[P] = r.Te;
       a.Tp[P] = r.Te + r.delta;
+      a.Msum[3 * P] = r.M[0];  // the model just written to J
+      a.Msum[3 * P + 1] = r.M[1];
+      a.Msum[3 * P + 2] = r.M[2];
     }
   }
   if (lane == 0 && a.counters) {
@@ -65,9 +68,11 @@ __global__ void fixup_kernel(SweepArgs a, int learned, MLPView m) {
 }
 
 // ---------------------------------------------------------------------------
-// Per-cell thermodynamic state at temperature T: I0cell, cached model J at T,
-// T_e = T_p = T.  One CTA per cell (grid-stride); bands over threads.
-__device__ void cell_state_at(double* I0cell, double* J, long long P, double T, ThermoTables th, double* row) {
+// Per-cell thermodynamic state at temperature T: I0cell, cached model J at T
+// with its T_p sums Msum, T_e = T_p = T.  One CTA per cell (grid-stride);
+// bands over threads.
+__device__ void cell_state_at(double* I0cell, double* J, double* Msum, long long P, double T, ThermoTables th,
+                              double* row) {
   const double rT = 1.0 / T;
   for (int b = threadIdx.x; b < th.nbp; b += blockDim.x) {  // every band (the temperature model)
     double f, d1, d2;
@@ -80,19 +85,31 @@ __device__ void cell_state_at(double* I0cell, double* J, long long P, double T, 
   __syncthreads();
   for (int b = threadIdx.x; b < th.nbo; b += blockDim.x)  // stored bands
     I0cell[P * th.nbo + b] = b < th.nbr ? row[th.band0 + b] : 0.0;
+  if (threadIdx.x == 0) {  // the model's sums with the T_p weights
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+    for (int b = 0; b < th.nbp; ++b) {
+      const double ap = th.a_p[b];
+      m0 = fma(ap, J[(P * 3 + 0) * th.nbp + b], m0);
+      m1 = fma(ap, J[(P * 3 + 1) * th.nbp + b], m1);
+      m2 = fma(ap, J[(P * 3 + 2) * th.nbp + b], m2);
+    }
+    Msum[3 * P] = m0;
+    Msum[3 * P + 1] = m1;
+    Msum[3 * P + 2] = m2;
+  }
 }
 
 // Equilibrium initial state: I = I0_b(T_P) for every direction (stored as the
 // deviation I0_b(T_P) - I0_b(T_ref) in the reduced modes).
 template <typename S>
-__global__ void init_cells_kernel(S* I, double* I0cell, double* J, double* Tp, double* Te, double* TL, double* EL,
-                                  const double* Tcells, const double* I0ref, long long cell0, int ncells, int nd,
-                                  ThermoTables th) {
+__global__ void init_cells_kernel(S* I, double* I0cell, double* J, double* Msum, double* Tp, double* Te, double* TL,
+                                  double* EL, const double* Tcells, const double* I0ref, long long cell0, int ncells,
+                                  int nd, ThermoTables th) {
   extern __shared__ double row[];  // [nbp]
   for (int c = blockIdx.x; c < ncells; c += gridDim.x) {
     const long long P = cell0 + c;
     const double T = Tcells[c];
-    cell_state_at(I0cell, J, P, T, th, row);
+    cell_state_at(I0cell, J, Msum, P, T, th, row);
     __syncthreads();
     const long long n = (long long)nd * th.nbo;
     for (long long e = threadIdx.x; e < n; e += blockDim.x) {
@@ -114,11 +131,11 @@ __global__ void init_cells_kernel(S* I, double* I0cell, double* J, double* Tp, d
 }
 
 // Thermodynamic state from T_p after a state restore: I0cell, J, T_e.
-__global__ void state_from_Tp_kernel(double* I0cell, double* J, const double* Tp, double* Te, long long ncells,
-                                     ThermoTables th) {
+__global__ void state_from_Tp_kernel(double* I0cell, double* J, double* Msum, const double* Tp, double* Te,
+                                     long long ncells, ThermoTables th) {
   extern __shared__ double row[];
   for (long long P = blockIdx.x; P < ncells; P += gridDim.x) {
-    cell_state_at(I0cell, J, P, Tp[P], th, row);
+    cell_state_at(I0cell, J, Msum, P, Tp[P], th, row);
     if (threadIdx.x == 0) Te[P] = Tp[P];
     __syncthreads();
   }
@@ -323,19 +340,9 @@ __device__ void solve_cell_warp(const SweepArgs& a, long long P, double EL, doub
     }
     return;
   }
-  double F = 0.0, F1 = 0.0, F2 = 0.0;
-  for (int b = lane; b < nbp; b += 32) {
-    const double ap = a.th.a_p[b];
-    F = fma(ap, a.J[(P * 3 + 0) * nbp + b], F);
-    F1 = fma(ap, a.J[(P * 3 + 1) * nbp + b], F1);
-    F2 = fma(ap, a.J[(P * 3 + 2) * nbp + b], F2);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    F += __shfl_xor_sync(0xffffffffu, F, o);
-    F1 += __shfl_xor_sync(0xffffffffu, F1, o);
-    F2 += __shfl_xor_sync(0xffffffffu, F2, o);
-  }
-  F -= Ep;
+  // the model's sums, kept with J (sum_b a_p,b J_k,b)
+  double F = a.Msum[3 * P] - Ep;
+  const double F1 = a.Msum[3 * P + 1], F2 = a.Msum[3 * P + 2];
   const double Te = a.Teval[P];
   const double disc = F1 * F1 - 2.0 * F * F2;
   const double delta = (disc >= 0.0 && F1 > 0.0) ? -2.0 * F / (F1 + sqrt(disc)) : -F / F1;
@@ -706,24 +713,27 @@ cudaError_t launch_gs_reduce(int precision, const SweepArgs& a, long long ncells
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_cells(int precision, void* I, double* I0cell, double* J, double* Tp, double* Te, double* TL,
-                              double* EL, const double* Tcells, const double* I0ref, long long cell0, int ncells, int nd,
-                              ThermoTables th, cudaStream_t s) {
+cudaError_t launch_init_cells(int precision, void* I, double* I0cell, double* J, double* Msum, double* Tp, double* Te,
+                              double* TL, double* EL, const double* Tcells, const double* I0ref, long long cell0,
+                              int ncells, int nd, ThermoTables th, cudaStream_t s) {
   const int grid = cell_grid(ncells);
   const size_t sm = th.nbp * sizeof(double);
   if (precision == 0)
-    init_cells_kernel<double><<<grid, 256, sm, s>>>((double*)I, I0cell, J, Tp, Te, TL, EL, Tcells, I0ref, cell0, ncells, nd, th);
+    init_cells_kernel<double><<<grid, 256, sm, s>>>((double*)I, I0cell, J, Msum, Tp, Te, TL, EL, Tcells, I0ref, cell0,
+                                                    ncells, nd, th);
   else if (precision == 1)
-    init_cells_kernel<float><<<grid, 256, sm, s>>>((float*)I, I0cell, J, Tp, Te, TL, EL, Tcells, I0ref, cell0, ncells, nd, th);
+    init_cells_kernel<float><<<grid, 256, sm, s>>>((float*)I, I0cell, J, Msum, Tp, Te, TL, EL, Tcells, I0ref, cell0,
+                                                   ncells, nd, th);
   else
-    init_cells_kernel<__nv_bfloat16><<<grid, 256, sm, s>>>((__nv_bfloat16*)I, I0cell, J, Tp, Te, TL, EL, Tcells, I0ref,
-                                                           cell0, ncells, nd, th);
+    init_cells_kernel<__nv_bfloat16><<<grid, 256, sm, s>>>((__nv_bfloat16*)I, I0cell, J, Msum, Tp, Te, TL, EL, Tcells,
+                                                           I0ref, cell0, ncells, nd, th);
   return cudaGetLastError();
 }
 
-cudaError_t launch_state_from_Tp(double* I0cell, double* J, const double* Tp, double* Te, long long ncells,
-                                 ThermoTables th, cudaStream_t s) {
-  state_from_Tp_kernel<<<cell_grid(ncells), 64, th.nbp * sizeof(double), s>>>(I0cell, J, Tp, Te, ncells, th);  // row: all bands
+cudaError_t launch_state_from_Tp(double* I0cell, double* J, double* Msum, const double* Tp, double* Te,
+                                 long long ncells, ThermoTables th, cudaStream_t s) {
+  state_from_Tp_kernel<<<cell_grid(ncells), 64, th.nbp * sizeof(double), s>>>(I0cell, J, Msum, Tp, Te, ncells,
+                                                                               th);  // row: all bands
   return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@ struct SolveResult {
   int evals;     // exact band-quadrature evaluations
   int fallback;  // 1 when bisection was needed
   int bad;       // 1 when no temperature in [1, 5000] K was found
+  double M[3];   // sum_b w_b (I0_b, dI0_b/dT, d2I0_b/dT2) at Te: the cell's model sums
 };
 
 // Solves sum_b w_b I0_b(T) = Ep (w = a_p unless given) from T0 by Halley steps on the exact band
@@ -26,7 +27,7 @@ __device__ inline SolveResult exact_solve_warp(const ThermoTables& th, double Ep
   double T = (T0 >= kTmin && T0 <= kTmax && isfinite(T0)) ? T0 : 300.0;
   double lo = kTmin, hi = kTmax, delta = 0.0;
   int mode = 0, iters = 0;  // 0 Halley, 1 bisection, 2 final
-  SolveResult r{T, 0.0, 0, 0, 0};
+  SolveResult r{T, 0.0, 0, 0, 0, {0.0, 0.0, 0.0}};
   bool done = false;
   for (int loop = 0; loop < maxit + 224 && !done; ++loop) {
     const double rT = 1.0 / T;
@@ -49,6 +50,9 @@ __device__ inline SolveResult exact_solve_warp(const ThermoTables& th, double Ep
       F1 += __shfl_xor_sync(0xffffffffu, F1, o);
       F2 += __shfl_xor_sync(0xffffffffu, F2, o);
     }
+    r.M[0] = F;
+    r.M[1] = F1;
+    r.M[2] = F2;
     F -= Ep;
     ++r.evals;
     r.Te = T;

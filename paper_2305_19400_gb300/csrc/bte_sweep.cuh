@@ -148,10 +148,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   const int dg = tl / lpc, lane = tl - dg * lpc;      // direction offset in a step, band vector
   DirSm* dsm = reinterpret_cast<DirSm*>(sm);          // [nd]
   double* gsm = sm + (sizeof(DirSm) / 8) * nd;        // [blockDim.x][V] per-lane band partials
-  double* red = gsm + (size_t)V * blockDim.x;         // [cpb * lpc][5] per-band-vector sums
+  double* red = gsm + (size_t)V * blockDim.x;         // [cpb * lpc][2] per-band-vector E_L, E_p sums
   // staging ring of the far operands: [kStages][kOps][blockDim.x] x 16 bytes
   char* ring = reinterpret_cast<char*>(
-      (reinterpret_cast<uintptr_t>(red + 5 * (size_t)cpb * lpc) + 15) & ~static_cast<uintptr_t>(15));
+      (reinterpret_cast<uintptr_t>(red + 2 * (size_t)cpb * lpc) + 15) & ~static_cast<uintptr_t>(15));
   const S* __restrict__ In = reinterpret_cast<const S*>(a.In);
   const S* __restrict__ Ik = reinterpret_cast<const S*>(a.Ik);
   S* __restrict__ Io = reinterpret_cast<S*>(a.Iout);
@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
     for (int v = 0; v < V; ++v) gb[(size_t)threadIdx.x * V + v] = G[v];
     __syncthreads();
     if (dg == 0) {
-      double eL = 0.0, ep = 0.0, F = 0.0, F1 = 0.0, F2 = 0.0;
+      double eL = 0.0, ep = 0.0;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         double Gb = kDev ? a.Wtot * a.I0ref[b0 + v] : 0.0;
@@ -482,40 +482,22 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         eL += e;
         ep = fma(a.th.beta[b0 + v], e, ep);
       }
-      if (active && a.solve_tp && !a.partial) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const double ap = a.th.a_p[b0 + v];
-          F = fma(ap, a.J[(P * 3 + 0) * nbp_all + b0 + v], F);
-          F1 = fma(ap, a.J[(P * 3 + 1) * nbp_all + b0 + v], F1);
-          F2 = fma(ap, a.J[(P * 3 + 2) * nbp_all + b0 + v], F2);
-        }
-      }
-      double* r5 = rb + 5 * (size_t)(slot * lpc + lane);
-      r5[0] = eL;
-      r5[1] = ep;
-      r5[2] = F;
-      r5[3] = F1;
-      r5[4] = F2;
+      double* r2 = rb + 2 * (size_t)(slot * lpc + lane);
+      r2[0] = eL;
+      r2[1] = ep;
     }
     __syncthreads();
     for (int cs = wid; wid < nwarps && cs < wi.cell_count; cs += nwarps) {  // warp per cell
       const long long Pc = gp->cell0 + wi.cell_begin + cs;
-      double EL = 0.0, Ep = 0.0, Fs = 0.0, F1s = 0.0, F2s = 0.0;
+      double EL = 0.0, Ep = 0.0;
       for (int l = wl; l < lpc; l += 32) {
-        const double* r5 = rb + 5 * (size_t)(cs * lpc + l);
-        EL += r5[0];
-        Ep += r5[1];
-        Fs += r5[2];
-        F1s += r5[3];
-        F2s += r5[4];
+        const double* r2 = rb + 2 * (size_t)(cs * lpc + l);
+        EL += r2[0];
+        Ep += r2[1];
       }
       for (int o = 16; o > 0; o >>= 1) {
         EL += __shfl_xor_sync(0xffffffffu, EL, o);
         Ep += __shfl_xor_sync(0xffffffffu, Ep, o);
-        Fs += __shfl_xor_sync(0xffffffffu, Fs, o);
-        F1s += __shfl_xor_sync(0xffffffffu, F1s, o);
-        F2s += __shfl_xor_sync(0xffffffffu, F2s, o);
       }
       const bool lead = wl == 0;  // writes the cell's outputs
       if (a.partial) {  // band-range handle: partial sums for the caller's all-reduce
@@ -532,8 +514,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       }
       if (!a.solve_tp) continue;
       if (lead) atomicAdd(&cnt_solves, 1ULL);
-      // root of (F - E_p) + F1 d + F2 d^2 / 2 nearest 0
-      Fs -= Ep;
+      // root of (F - E_p) + F1 d + F2 d^2 / 2 nearest 0; F, F1, F2: the model's
+      // sums sum_b a_p,b J_k,b, kept with J
+      const double Fs = a.Msum[3 * Pc] - Ep, F1s = a.Msum[3 * Pc + 1], F2s = a.Msum[3 * Pc + 2];
       const double Te = a.Teval[Pc];
       const double disc = F1s * F1s - 2.0 * Fs * F2s;
       const double delta = (disc >= 0.0 && F1s > 0.0) ? -2.0 * Fs / (F1s + sqrt(disc)) : -Fs / F1s;
@@ -568,7 +551,7 @@ template <typename S, int MINB, int BM, bool TT>
 cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   const int team = a.lpc * a.dteam, cpb = threads / team;
   const size_t smem = sizeof(DirSm) * (size_t)a.nd + (size_t)Tr<S>::V * threads * sizeof(double) +
-                      5 * (size_t)cpb * a.lpc * sizeof(double) + 16 +
+                      2 * (size_t)cpb * a.lpc * sizeof(double) + 16 +
                       (size_t)(dim == 3 ? Ring<3, S>::kStages * Ring<3, S>::kOps : Ring<2, S>::kStages * Ring<2, S>::kOps) *
                           threads * 16;
   if (dim == 3) {

@@ -373,6 +373,7 @@ struct bte_umesh_ctx {
   double* I[3] = {nullptr, nullptr, nullptr};
   int cur = 0;
   double *I0cell = nullptr, *J = nullptr, *Teval = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr;
+  double* Msum = nullptr;  // [cell][3] the T_p model's sums, kept with J
   double *ghost = nullptr, *g = nullptr, *gout = nullptr, *S_d = nullptr, *w_d = nullptr, *nA_d = nullptr;
   double *vb_d = nullptr, *bb_d = nullptr, *bfT_d = nullptr, *scratch = nullptr, *Qb = nullptr, *qbuf = nullptr;
   double* R = nullptr;     // implicit reciprocal diagonal for R_dt (FP64 storage)
@@ -451,6 +452,7 @@ SweepArgs cell_args(bte_umesh_ctx* u, double* Inew) {
   a.Tp = u->Tp;
   a.Teval = u->Teval;
   a.J = u->J;
+  a.Msum = u->Msum;
   a.EL = u->EL;
   a.wdir = u->w_d;
   a.nd = u->nd;
@@ -486,7 +488,7 @@ int ensure_mem(bte_umesh_ctx* u) {
   }
   if ((rc = dalloc(u, &u->I0ref, nbp)) || (rc = dalloc(u, &u->ghost_dev, nbf * nbp)) || (rc = dalloc(u, &u->w32_d, nd)))
     return rc;
-  if ((rc = dalloc(u, &u->I0cell, nc * nbp)) || (rc = dalloc(u, &u->J, nc * 3 * nbp)) ||
+  if ((rc = dalloc(u, &u->I0cell, nc * nbp)) || (rc = dalloc(u, &u->J, nc * 3 * nbp)) || (rc = dalloc(u, &u->Msum, nc * 3)) ||
       (rc = dalloc(u, &u->Teval, nc)) || (rc = dalloc(u, &u->Tp, nc)) || (rc = dalloc(u, &u->TL, nc)) ||
       (rc = dalloc(u, &u->EL, nc)) || (rc = dalloc(u, &u->ghost, nbf * nbp)) || (rc = dalloc(u, &u->bfT_d, nbf)) ||
       (rc = dalloc(u, &u->S_d, nd * 3)) || (rc = dalloc(u, &u->w_d, nd)) || (rc = dalloc(u, &u->nA_d, u->nf * 3)) ||
@@ -773,7 +775,7 @@ int bte_umesh_set_initial(bte_umesh u, const double* T_cells, double T_uniform) 
   int rc = upload(u, u->scratch, T.data(), u->nc);
   if (rc) return rc;
   u->cur = 0;
-  UTRY(u, launch_init_cells(u->prec, u->I[0], u->I0cell, u->J, u->Tp, u->Teval, u->TL, u->EL, u->scratch, u->I0ref, 0,
+  UTRY(u, launch_init_cells(u->prec, u->I[0], u->I0cell, u->J, u->Msum, u->Tp, u->Teval, u->TL, u->EL, u->scratch, u->I0ref, 0,
                             (int)u->nc, u->nd, uthermo(u), u->stream));
   UTRY(u, cudaStreamSynchronize(u->stream));
   u->init_done = true;
@@ -970,7 +972,7 @@ int bte_umesh_set_intensity(bte_umesh u, const double* in, const double* Tp_cell
   if (e == cudaSuccess)
     e = launch_pack(u->prec, tmp, nullptr, nullptr, u->I[u->cur], u->I0ref, u->nc, u->nd, u->nb, u->nbp, 1, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(u->Tp, Tp_cells, u->nc * 8, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = launch_state_from_Tp(u->I0cell, u->J, u->Tp, u->Teval, u->nc, uthermo(u), s);
+  if (e == cudaSuccess) e = launch_state_from_Tp(u->I0cell, u->J, u->Msum, u->Tp, u->Teval, u->nc, uthermo(u), s);
   if (e == cudaSuccess) e = launch_energy_L(u->prec, u->I[u->cur], u->I0ref, u->EL, u->w_d, u->nc, u->nd, uthermo(u), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(tmp);
