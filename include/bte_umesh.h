@@ -63,7 +63,9 @@ typedef struct {
 } bte_umesh_desc;
 
 /* Creates a handle.  opts: as in bte.h (precision BTE_FP64, BTE_FP32 or
- * BTE_BF16; learned and beta_T_exp must be 0); may be NULL for the defaults.  *out receives
+ * BTE_BF16; learned and beta_T_exp must be 0; use_graph and autotune are not
+ * used by this handle, which launches each kernel directly with a fixed
+ * shape); may be NULL for the defaults.  *out receives
  * the handle, NULL on failure (message in bte_umesh_last_error(NULL)). */
 int bte_umesh_create(const bte_umesh_desc* mesh, const bte_opts* opts, bte_umesh* out);
 
