@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--ny", type=int, default=128)
     ap.add_argument("--ninner", type=int, default=15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="plain launches: no autotuning, no CUDA graph")
@@ -167,7 +168,31 @@ def run_oracle_sample(wl):
     st = p.init_state(g.T_init)
     t0 = time.perf_counter()
     p.run(st, wl.dt, wl.nsteps, wl.ninner)
-    return wl.updates, time.perf_counter() - t0
+    return wl.updates, time.perf_counter() - t0, st
+
+
+def run_oracle_only(args):
+    """One oracle time step on an nx x ny sub-grid of the workload, printed as JSON; run in a
+    child process so that OMP_NUM_THREADS set for it takes effect."""
+    from oracle import oracle as O
+    from paper_2305_19400_gb300 import workloads as W
+    O.build()
+    wl = W.cfg2(args.nx, args.ny, nsteps=1, ninner=args.ninner)
+    u, s, _ = run_oracle_sample(wl)
+    print(json.dumps({"updates": u, "seconds": s, "cores": O.num_threads()}), flush=True)
+    return 0
+
+
+def oracle_single_thread(ninner, n=32):
+    """The oracle with one OpenMP thread on an n x n sub-grid (same directions, bands and walls)."""
+    import subprocess
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-only", "--nx", str(n), "--ny", str(n),
+                        "--ninner", str(ninner)], env=env, capture_output=True, text=True, check=True)
+    rec = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": rec["updates"] / rec["seconds"], "unit": UNIT, "cores": rec["cores"],
+            "sample": f"{n}x{n} sub-grid, 1 time step x {ninner} inner iterations "
+                      f"({rec['updates']:.3g} updates, {rec['seconds']:.1f} s)"}
 
 
 def run_reference(args):
@@ -181,7 +206,7 @@ def run_reference(args):
         run_oracle_sample(wl)
     tot_u, tot_s = 0, 0.0
     for _ in range(args.steps):
-        u, s = run_oracle_sample(wl)
+        u, s, _ = run_oracle_sample(wl)
         tot_u += u
         tot_s += s
     v = tot_u / tot_s
@@ -206,7 +231,8 @@ def cpu_baseline_for(args):
     from paper_2305_19400_gb300 import workloads as W
     O.build()
     wl = W.cfg2(args.nx, args.ny, nsteps=1, ninner=args.ninner)
-    u, s = run_oracle_sample(wl)
+    u, s, st = run_oracle_sample(wl)
+    single = oracle_single_thread(args.ninner)
     # the paper's own device (the FP64 variant of the same name): 20 of its 100 steps
     pd = W.paper_hot_spot(nsteps=20)
     g = pd.geoms[0]
@@ -215,7 +241,7 @@ def cpu_baseline_for(args):
     t0 = time.perf_counter()
     p.run(st, pd.dt, pd.nsteps, pd.ninner)
     sp = time.perf_counter() - t0
-    return {"value": u / s, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+    return st, {"value": u / s, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "single_thread": single,
             "sample": f"full {args.nx}x{args.ny} grid, 1 time step x {args.ninner} inner iterations ({u:.3g} updates, {s:.1f} s)",
             "paper_device": {"value": pd.dof * pd.nsteps / sp, "unit": UNIT, "ms_per_step": 1e3 * sp / pd.nsteps,
                              "sample": f"120x120 x 20 x 55, 20 of the 100 steps of 1 ns, one inner iteration each ({sp:.1f} s)"}}
@@ -396,6 +422,8 @@ def run_umesh_variant(peaks, precision=None):
 
 def main():
     args = parse()
+    if args.oracle_only:
+        return run_oracle_only(args)
     if args.impl == "reference":
         return run_reference(args)
     world, rank, local = dist_env()
@@ -432,7 +460,9 @@ def main():
         rc, st = bte.bte_step(solver.h, wl.dt, 1, args.ninner, bte.BTE_IMPLICIT_JACOBI, want_stats=False)
         return rc
 
-    for _ in range(args.warmup):
+    step()   # the first warm-up step, from the initial state: kept for the accuracy check against the oracle
+    TL_first = solver.T(0, bte.BTE_T_LATTICE) if world == 1 else None
+    for _ in range(args.warmup - 1):
         step()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
@@ -517,9 +547,14 @@ def main():
                 "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
                 "hbm": {"achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"],
                         "peak_source": f"hbm_gbs of {peak_src} peaks"}}
-    cpu = None
+    cpu = accuracy = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_for(args)
+        ost, cpu = cpu_baseline_for(args)
+        accuracy = {"max_abs_dTL_K": float(np.max(np.abs(TL_first - ost["TL"]))),
+                    "max_rel_dTL": float(np.max(np.abs(TL_first - ost["TL"]) / ost["TL"])),
+                    "against": f"FP64 oracle, full {args.nx}x{args.ny} grid, first time step x {args.ninner} "
+                               "inner iterations, same launch configuration as the timed steps"}
+        del ost
     variants = None
     if world == 1 and not args.no_variants:
         variants = run_variants(peaks)
@@ -538,7 +573,7 @@ def main():
                                  + tune_choice) if tuned else "eager launches, default tiles",
                       "parallelism": f"band-partition x{world}" if partitioned else f"replicas x{world}"},
            "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-           "variants": variants}
+           "accuracy": accuracy, "variants": variants}
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

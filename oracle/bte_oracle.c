@@ -681,7 +681,8 @@ int orc_wall_I0(const orc_problem* p, double* out) {
 /* upwind one: the neighbour's, or at a boundary face its ghost (isothermal:  */
 /* I0_b(T_face); mirror: the cell's own value in the direction reflected     */
 /* across the face, whose normal must lie along an axis; diffuse: every       */
-/* incoming direction gets sum_out (S.n) I / sum_in |S.n| of the cell).       */
+/* incoming direction gets sum_out (S.n) I / sum_in |S.n| of the cell;        */
+/* partially specular with specularity p: p x mirror + (1 - p) x diffuse).    */
 /* Implicit (one point-Jacobi sweep of the inner iteration):                  */
 /*   I^{k+1} = [I^n/dt + beta I0 + v sum_{g<0} |g| I_up^k] / [1/dt + beta + v sum_{g>0} g] */
 /* Explicit: I^{n+1} = I^n + dt [beta (I0 - I^n) - v sum_f g_f I_f^n].       */
@@ -696,6 +697,7 @@ typedef struct {
   const double* nA;    /* [nf][3] */
   const int* btype;    /* [nf] ORC_* on boundary faces */
   const double* Twall; /* [nf] isothermal face temperature */
+  const double* spec;  /* [nf] specularity of ORC_PARTIAL faces (NULL when there are none) */
 } orc_umesh;
 
 /* cell -> faces (CSR), built once per call that needs it */
@@ -726,25 +728,37 @@ static int um_axis(const orc_umesh* m, long f) {
   return ax;
 }
 
+/* diffuse value of boundary face f for band b: the owner's outgoing
+   intensities weighted by S.n, over the incoming directions' sum of |S.n| */
+static double um_diffuse(const orc_problem* p, const orc_umesh* m, const double* Isrc, long f, int b) {
+  int nd = p->nd, nb = p->nb;
+  long P = m->owner[f];
+  const double* n = m->nA + 3 * f;
+  double num = 0.0, den = 0.0;
+  for (int e = 0; e < nd; ++e) {
+    double sn = p->S[3 * e] * n[0] + p->S[3 * e + 1] * n[1] + p->S[3 * e + 2] * n[2];
+    if (sn > 0) num += sn * Isrc[P * nd * nb + (long)e * nb + b];
+    else den -= sn;
+  }
+  return num / den;
+}
+
+/* mirror value of boundary face f: the owner's intensity in the direction
+   reflected across the face's axis */
+static double um_mirror(const orc_problem* p, const orc_umesh* m, const double* Isrc, long f, int d, int b) {
+  int ax = um_axis(m, f);
+  const int* r = ax == 0 ? p->rx : (ax == 1 ? p->ry : p->rz);
+  return Isrc[m->owner[f] * p->nd * p->nb + (long)r[d] * p->nb + b];
+}
+
 /* ghost value of boundary face f (owner P) for incoming direction d, band b */
 static double um_ghost(const orc_problem* p, const orc_umesh* m, const double* Isrc, const double* I0w, long f, int d,
                        int b) {
-  int nd = p->nd, nb = p->nb;
-  long P = m->owner[f];
-  if (m->btype[f] == ORC_ISOTHERMAL) return I0w[f * nb + b];
-  if (m->btype[f] == ORC_DIFFUSE) {
-    const double* n = m->nA + 3 * f;
-    double num = 0.0, den = 0.0;
-    for (int e = 0; e < nd; ++e) {
-      double sn = p->S[3 * e] * n[0] + p->S[3 * e + 1] * n[1] + p->S[3 * e + 2] * n[2];
-      if (sn > 0) num += sn * Isrc[P * nd * nb + (long)e * nb + b];
-      else den -= sn;
-    }
-    return num / den;
-  }
-  int ax = um_axis(m, f);
-  const int* r = ax == 0 ? p->rx : (ax == 1 ? p->ry : p->rz);
-  return Isrc[P * nd * nb + (long)r[d] * nb + b];
+  if (m->btype[f] == ORC_ISOTHERMAL) return I0w[f * p->nb + b];
+  if (m->btype[f] == ORC_DIFFUSE) return um_diffuse(p, m, Isrc, f, b);
+  if (m->btype[f] == ORC_PARTIAL)
+    return m->spec[f] * um_mirror(p, m, Isrc, f, d, b) + (1.0 - m->spec[f]) * um_diffuse(p, m, Isrc, f, b);
+  return um_mirror(p, m, Isrc, f, d, b);
 }
 
 static double um_update_one(const orc_problem* p, const orc_umesh* m, const long* fptr, const long* flist, double dt,

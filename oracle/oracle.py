@@ -304,7 +304,7 @@ class Problem:
 class _UMesh(C.Structure):
     _fields_ = [("dim", C.c_int), ("nc", C.c_long), ("nf", C.c_long), ("vol", C.POINTER(C.c_double)),
                 ("owner", C.POINTER(C.c_long)), ("nbr", C.POINTER(C.c_long)), ("nA", C.POINTER(C.c_double)),
-                ("btype", C.POINTER(C.c_int)), ("Twall", C.POINTER(C.c_double))]
+                ("btype", C.POINTER(C.c_int)), ("Twall", C.POINTER(C.c_double)), ("spec", C.POINTER(C.c_double))]
 
 
 class UMeshProblem:
@@ -312,8 +312,9 @@ class UMeshProblem:
     its direction set, bands and boundary conditions.
 
     bc: {tag: (kind, T)} with kind ISOTHERMAL (T a float, or an array over the
-    mesh's faces indexed by face id), SPECULAR or DIFFUSE (T ignored).  The
-    direction and band tables live in a Problem on a one-cell grid."""
+    mesh's faces indexed by face id), SPECULAR or DIFFUSE (T ignored), or
+    PARTIAL (T the specularity p in [0, 1]).  The direction and band tables
+    live in a Problem on a one-cell grid."""
 
     def __init__(self, mesh, dirs, bands, bc, ngauss: int = 16, newton_rtol: float = 1e-14, newton_maxit: int = 50,
                  beta_exp: float = 0.0, beta_Tref: float = 300.0):
@@ -332,14 +333,17 @@ class UMeshProblem:
         self.nA = np.ascontiguousarray(mesh.nA, dtype=np.float64)
         self.btype = np.full(nf, SPECULAR, dtype=np.int32)
         self.Twall = np.zeros(nf)
+        self.spec = np.zeros(nf)
         for f in np.nonzero(self.nbr < 0)[0]:
             kind, T = bc[int(mesh.tag[f])]
             self.btype[f] = kind
             if kind == ISOTHERMAL:
                 self.Twall[f] = T if np.isscalar(T) else T[f]
+            elif kind == PARTIAL:
+                self.spec[f] = float(T)
         m = _UMesh()
         m.dim, m.nc, m.nf = mesh.dim, self.nc, nf
-        m.vol, m.nA, m.Twall = _dp(self.vol), _dp(self.nA), _dp(self.Twall)
+        m.vol, m.nA, m.Twall, m.spec = _dp(self.vol), _dp(self.nA), _dp(self.Twall), _dp(self.spec)
         m.owner = self.owner.ctypes.data_as(C.POINTER(C.c_long))
         m.nbr = self.nbr.ctypes.data_as(C.POINTER(C.c_long))
         m.btype = _ip(self.btype)

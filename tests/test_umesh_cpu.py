@@ -96,21 +96,25 @@ def _tet_box_elements(nx, ny, nz, Lx, Ly, Lz):
 
 
 # ------------------------------------------------------------ oracle pins
-def _mixed_rectangle(nx, ny, dx):
+def _mixed_rectangle(nx, ny, dx, walls=((W.BC_SPECULAR, None), (W.BC_DIFFUSE, None))):
+    """A rectangle with isothermal x sides and the given y sides, as a structured
+    grid and as a quad mesh with the same walls (tags 0-3 = sides -x, +x, -y, +y)."""
     g = W.Geometry(2, nx, ny, 1, dx, dx, dx)
     Th = W.random_temperatures(ny, 3, 300.0, 310.0)
-    g.bc = [(W.BC_ISOTHERMAL, Th), (W.BC_ISOTHERMAL, np.full(ny, 300.0)), (W.BC_SPECULAR, None), (W.BC_DIFFUSE, None)]
+    g.bc = [(W.BC_ISOTHERMAL, Th), (W.BC_ISOTHERMAL, np.full(ny, 300.0))] + list(walls)
     m = M.quad_grid(nx, ny, nx * dx, ny * dx)
     Twall = np.zeros(m.nfaces)
     for f in m.boundary_faces(0):
         Twall[f] = Th[int(m.face_center[f, 1] // dx)]
-    bc = {0: (O.ISOTHERMAL, Twall), 1: (O.ISOTHERMAL, 300.0), 2: (O.SPECULAR, None), 3: (O.DIFFUSE, None)}
+    bc = {0: (O.ISOTHERMAL, Twall), 1: (O.ISOTHERMAL, 300.0), 2: walls[0], 3: walls[1]}
     return g, m, bc
 
 
+@pytest.mark.parametrize("walls", [((W.BC_SPECULAR, None), (W.BC_DIFFUSE, None)),
+                                   ((W.BC_PARTIAL, 0.3), (W.BC_PARTIAL, 0.8))])
 @pytest.mark.parametrize("scheme,dt,nsteps,ninner", [(O.IMPLICIT, 1e-12, 3, 5), (O.EXPLICIT, 2e-13, 20, 1)])
-def test_quad_mesh_reproduces_the_structured_oracle(scheme, dt, nsteps, ninner):
-    g, m, bc = _mixed_rectangle(6, 5, 10e-9)
+def test_quad_mesh_reproduces_the_structured_oracle(scheme, dt, nsteps, ninner, walls):
+    g, m, bc = _mixed_rectangle(6, 5, 10e-9, walls)
     dirs, bands = O.dirs_inplane(16), W.make_bands(6, 2, 5)
     T0 = W.random_temperatures(30, 4, 298.0, 304.0)
     p = O.Problem(g, dirs, bands)
@@ -184,11 +188,12 @@ def test_uniform_equilibrium_on_a_jittered_triangle_mesh_stays_at_round_off(kind
     assert np.max(np.abs(st["TL"] - 300.0)) < 1e-12
 
 
-@pytest.mark.parametrize("kind", [O.SPECULAR, O.DIFFUSE])
+@pytest.mark.parametrize("kind", [O.SPECULAR, O.DIFFUSE, O.PARTIAL])
 def test_closed_triangle_enclosure_conserves_energy(kind):
     m = M.tri_grid(6, 5, 60e-9, 50e-9, jitter=0.3, seed=6)
     bands = W.make_bands(4, 1, 9)
-    u = O.UMeshProblem(m, O.dirs_inplane(12), bands, {t: (kind, None) for t in range(4)})
+    u = O.UMeshProblem(m, O.dirs_inplane(12), bands, {t: (kind, 0.25 + 0.2 * t if kind == O.PARTIAL else None)
+                                                       for t in range(4)})
     st = u.init_state(W.random_temperatures(m.ncells, 10, 290.0, 310.0))
 
     def total(I):
@@ -201,6 +206,20 @@ def test_closed_triangle_enclosure_conserves_energy(kind):
     q, Q = u.flux(st["I"])
     scale = np.max(np.abs(q))
     assert np.max(np.abs(Q)) <= 1e-12 * scale * np.max(np.linalg.norm(m.nA, axis=1))  # no net flow through the walls
+
+
+def test_partial_walls_at_p_one_and_zero_are_the_mirror_and_the_diffuse_wall_bit_for_bit():
+    m = M.tri_grid(5, 4, 50e-9, 40e-9, jitter=0.3, seed=8)
+    bands, dirs = W.make_bands(4, 1, 14), O.dirs_inplane(12)
+    T0 = W.random_temperatures(m.ncells, 15, 296.0, 306.0)
+    for p, kind in ((1.0, O.SPECULAR), (0.0, O.DIFFUSE)):
+        res = []
+        for wall in ((O.PARTIAL, p), (kind, None)):
+            u = O.UMeshProblem(m, dirs, bands, {0: (O.ISOTHERMAL, 308.0), 1: (O.ISOTHERMAL, 300.0), 2: wall, 3: wall})
+            st = u.init_state(T0)
+            u.run(st, 1e-12, 3, 4)
+            res.append(st["I"])
+        assert np.array_equal(res[0], res[1]), p
 
 
 def test_rotating_the_mesh_by_a_quarter_turn_relabels_the_solution():
