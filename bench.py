@@ -237,14 +237,14 @@ def cpu_baseline_for(args):
     pd = W.paper_hot_spot(nsteps=20)
     g = pd.geoms[0]
     p = O.Problem(g, O.dirs_for(pd.dirs), pd.bands)
-    st = p.init_state(g.T_init)
+    pst = p.init_state(g.T_init)
     t0 = time.perf_counter()
-    p.run(st, pd.dt, pd.nsteps, pd.ninner)
+    p.run(pst, pd.dt, pd.nsteps, pd.ninner)
     sp = time.perf_counter() - t0
     return st, {"value": u / s, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "single_thread": single,
-            "sample": f"full {args.nx}x{args.ny} grid, 1 time step x {args.ninner} inner iterations ({u:.3g} updates, {s:.1f} s)",
-            "paper_device": {"value": pd.dof * pd.nsteps / sp, "unit": UNIT, "ms_per_step": 1e3 * sp / pd.nsteps,
-                             "sample": f"120x120 x 20 x 55, 20 of the 100 steps of 1 ns, one inner iteration each ({sp:.1f} s)"}}
+                "sample": f"full {args.nx}x{args.ny} grid, 1 time step x {args.ninner} inner iterations ({u:.3g} updates, {s:.1f} s)",
+                "paper_device": {"value": pd.dof * pd.nsteps / sp, "unit": UNIT, "ms_per_step": 1e3 * sp / pd.nsteps,
+                                 "sample": f"120x120 x 20 x 55, 20 of the 100 steps of 1 ns, one inner iteration each ({sp:.1f} s)"}}
 
 
 def run_variants(peaks):

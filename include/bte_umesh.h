@@ -76,7 +76,14 @@ int bte_umesh_set_bands(bte_umesh u, int nb, const double* omega_lo, const doubl
 /* Condition of every boundary face with tag `tag`.  type: BTE_BC_ISOTHERMAL
  * (T_faces: host [nfaces] temperatures indexed by face id, read on this
  * tag's faces, or NULL for T_uniform), BTE_BC_SPECULAR or BTE_BC_DIFFUSE
- * (T ignored).  A tag no boundary face carries returns BTE_E_ARG. */
+ * (T ignored), or BTE_BC_PARTIAL (an extension beyond the paper's walls, as
+ * bte_set_specularity: every incoming direction gets p x the mirrored value
+ * + (1 - p) x the diffuse value; p from T_faces indexed by face id, or
+ * T_uniform when T_faces is NULL, each in [0, 1]).  Specular and partial
+ * faces must be normal to an axis.  A tag no boundary face carries, an
+ * unknown type or a value out of range returns BTE_E_ARG and changes
+ * nothing.  May be called again after bte_umesh_set_initial to change a
+ * tag's condition for the following steps. */
 int bte_umesh_set_bc(bte_umesh u, int tag, int type, const double* T_faces, double T_uniform);
 
 /* Equilibrium initial state at T_cells (host [ncells], or NULL for T_uniform). */

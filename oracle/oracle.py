@@ -313,7 +313,8 @@ class UMeshProblem:
 
     bc: {tag: (kind, T)} with kind ISOTHERMAL (T a float, or an array over the
     mesh's faces indexed by face id), SPECULAR or DIFFUSE (T ignored), or
-    PARTIAL (T the specularity p in [0, 1]).  The direction and band tables
+    PARTIAL (T the specularity p in [0, 1], a float or an array over the
+    faces).  The direction and band tables
     live in a Problem on a one-cell grid."""
 
     def __init__(self, mesh, dirs, bands, bc, ngauss: int = 16, newton_rtol: float = 1e-14, newton_maxit: int = 50,
@@ -340,7 +341,7 @@ class UMeshProblem:
             if kind == ISOTHERMAL:
                 self.Twall[f] = T if np.isscalar(T) else T[f]
             elif kind == PARTIAL:
-                self.spec[f] = float(T)
+                self.spec[f] = T if np.isscalar(T) else T[f]
         m = _UMesh()
         m.dim, m.nc, m.nf = mesh.dim, self.nc, nf
         m.vol, m.nA, m.Twall, m.spec = _dp(self.vol), _dp(self.nA), _dp(self.Twall), _dp(self.spec)

@@ -430,7 +430,8 @@ class UMeshSolver:
 
     bc: {tag: (kind, T)} with kind BTE_BC_ISOTHERMAL (T a float, or an array
     over the mesh's faces indexed by face id), BTE_BC_SPECULAR or
-    BTE_BC_DIFFUSE (T ignored)."""
+    BTE_BC_DIFFUSE (T ignored), or BTE_BC_PARTIAL (T the specularity p, a
+    float or an array over the faces)."""
 
     def __init__(self, mesh, dirs, bands, bc, T_init=None, stream=None, n_gauss=16, precision=BTE_FP64):
         import torch
@@ -464,16 +465,20 @@ class UMeshSolver:
         arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (b.omega_lo, b.omega_hi, b.vg, b.beta, b.degeneracy)]
         _ucheck(h, lib().bte_umesh_set_bands(h, len(arrs[2]), *(a.ctypes.data_as(_dp) for a in arrs)))
         for t, (kind, T) in bc.items():
-            if kind == BTE_BC_ISOTHERMAL and not np.isscalar(T):
-                Tf = np.ascontiguousarray(T, dtype=np.float64)
-                _ucheck(h, lib().bte_umesh_set_bc(h, int(t), kind, Tf.ctypes.data_as(_dp), 0.0))
-            else:
-                _ucheck(h, lib().bte_umesh_set_bc(h, int(t), kind, None, float(T) if T is not None else 0.0))
+            self.set_bc(t, kind, T)
         if T_init is None:
             _ucheck(h, lib().bte_umesh_set_initial(h, None, float(mesh.T_init)))
         else:
             Tc = np.ascontiguousarray(np.broadcast_to(np.asarray(T_init, dtype=np.float64), (mesh.ncells,)))
             _ucheck(h, lib().bte_umesh_set_initial(h, Tc.ctypes.data_as(_dp), 0.0))
+
+    def set_bc(self, tag, kind, T=None):
+        """Condition of one boundary tag (as in bc); may be called between steps."""
+        if kind in (BTE_BC_ISOTHERMAL, BTE_BC_PARTIAL) and T is not None and not np.isscalar(T):
+            Tf = np.ascontiguousarray(T, dtype=np.float64)
+            _ucheck(self.h, lib().bte_umesh_set_bc(self.h, int(tag), kind, Tf.ctypes.data_as(_dp), 0.0))
+        else:
+            _ucheck(self.h, lib().bte_umesh_set_bc(self.h, int(tag), kind, None, float(T) if T is not None else 0.0))
 
     def step(self, dt, nsteps, ninner, scheme=BTE_IMPLICIT_JACOBI, want_stats=True):
         st = bte_stats() if want_stats else None

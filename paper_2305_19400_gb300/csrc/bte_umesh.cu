@@ -9,8 +9,10 @@
 //               or -1 - boundary face index) and g[entry][dir] =
 //               (S_d . n A)/(w_d V) with n out of the cell; gout[cell][dir] =
 //               sum of the positive g (outflow)
-//   boundary    per boundary face: kind (ghost row or mirror), mirror axis,
-//               ghost rows [bface][nbp] (isothermal I0, refreshed diffuse values)
+//   boundary    per boundary face: kind (ghost row, mirror, or p x mirror +
+//               ghost row), mirror axis, specularity p, ghost rows
+//               [bface][nbp] (isothermal I0, refreshed diffuse values, scaled
+//               by 1 - p on partially specular faces)
 //   R           [cell][dir][nbp] implicit reciprocal diagonal 1/(1/dt + beta_b +
 //               v_b gout), rebuilt when dt changes (one division per element
 //               instead of one per update)
@@ -46,8 +48,9 @@ struct UArgs {
   const long long* cf_up;  // [entries] neighbour cell, or -1 - bface
   const double* g;         // [entries][nd]
   const double* gout;      // [nc][nd]
-  const int* bf_mirror;    // [bface] 1: mirror, 0: ghost row
+  const int* bf_mirror;    // [bface] 0: ghost row, 1: mirror, 2: p x mirror + ghost row
   const int* bf_axis;      // [bface]
+  const double* bf_spec;   // [bface] specularity p of kind-2 faces
   const int* refl;         // [3][nd]
   const double* R;         // [nc][nd][nbp] implicit: 1 / (1/dt + beta_b + v_b gout)
   const double* vb;        // [nbp] v_b (0 on padding)
@@ -123,17 +126,33 @@ __global__ void __launch_bounds__(256, 6) umesh_sweep_dev_kernel(UArgs a) {
         const float ge = a.g32[(long long)e * a.nd + d];
         if (__float_as_int(ge) < 0) {  // inflow: the sign bit, tested on the integer pipe
           const long long up = a.cf_up[e];
-          float u[V];
-          if (up >= 0) {
-            T::ld(Isrc + up * row + (long long)d * a.nbp + b0, u);
-          } else {
-            const long long bf = -1 - up;
-            if (a.bf_mirror[bf]) T::ld(Isrc + P * row + (long long)a.refl[a.bf_axis[bf] * a.nd + d] * a.nbp + b0, u);
-            else ldf<V>(a.ghost_dev + bf * a.nbp + b0, u);
-          }
           const float gf = -ge;
+          if (up >= 0) {
+            float u[V];
+            T::ld(Isrc + up * row + (long long)d * a.nbp + b0, u);
 #pragma unroll
-          for (int v = 0; v < V; ++v) f[v] = fmaf(gf, u[v], f[v]);
+            for (int v = 0; v < V; ++v) f[v] = fmaf(gf, u[v], f[v]);
+          } else {
+            // ghost row (isothermal, diffuse, or (1 - p) x diffuse) and/or the
+            // mirrored value (weight p on a partially specular face), one row
+            // live at a time
+            const long long bf = -1 - up;
+            const int mk = a.bf_mirror[bf];
+            float wm = gf;
+            if (mk != 1) {
+              float u[V];
+              ldf<V>(a.ghost_dev + bf * a.nbp + b0, u);
+#pragma unroll
+              for (int v = 0; v < V; ++v) f[v] = fmaf(gf, u[v], f[v]);
+              wm = mk == 2 ? gf * (float)a.bf_spec[bf] : 0.f;
+            }
+            if (mk != 0) {
+              float u[V];
+              T::ld(Isrc + P * row + (long long)a.refl[a.bf_axis[bf] * a.nd + d] * a.nbp + b0, u);
+#pragma unroll
+              for (int v = 0; v < V; ++v) f[v] = fmaf(wm, u[v], f[v]);
+            }
+          }
         }
       }
       float r[V];
@@ -159,9 +178,11 @@ __device__ __forceinline__ double2 ld2(const double* p) { return __ldg(reinterpr
 
 // EXPL: explicit scheme.  BM (implicit): 0 In is I^n; 1 In is I^n and B =
 // (I^n/dt) R is stored; 2 In holds B (the same in every inner iteration of a
-// step), so the update is R (beta I0 + v sum |g| I_up) + B.
+// step), so the update is R (beta I0 + v sum |g| I_up) + B.  Capped at 5 CTAs
+// of 256 threads per SM (48 registers, a few bytes of spill outside the face
+// loop): uncapped it takes 58 registers and 4 CTAs, measured 7 % slower.
 template <bool EXPL, int BM>
-__global__ void __launch_bounds__(256) umesh_sweep_kernel(UArgs a) {
+__global__ void __launch_bounds__(256, 5) umesh_sweep_kernel(UArgs a) {
   const int team = a.lpc * a.dteam;
   const int cpb = blockDim.x / team;
   const int slot = threadIdx.x / team, tl = threadIdx.x - slot * team;
@@ -183,16 +204,28 @@ __global__ void __launch_bounds__(256) umesh_sweep_kernel(UArgs a) {
         const double ge = a.g[(long long)e * a.nd + d];
         if (__double_as_longlong(ge) < 0) {  // inflow: the sign bit, tested on the integer pipe
           const long long up = a.cf_up[e];
-          double2 u;
           if (up >= 0) {
-            u = ld2(Isrc + up * row + (long long)d * a.nbp + b0);
+            const double2 u = ld2(Isrc + up * row + (long long)d * a.nbp + b0);
+            f0 = fma(-ge, u.x, f0);
+            f1 = fma(-ge, u.y, f1);
           } else {
+            // ghost row (isothermal, diffuse, or (1 - p) x diffuse) and/or the
+            // mirrored value (weight p on a partially specular face)
             const long long bf = -1 - up;
-            if (a.bf_mirror[bf]) u = ld2(Isrc + P * row + (long long)a.refl[a.bf_axis[bf] * a.nd + d] * a.nbp + b0);
-            else u = ld2(a.ghost + bf * a.nbp + b0);
+            const int mk = a.bf_mirror[bf];
+            double wm = -ge;
+            if (mk != 1) {
+              const double2 u = ld2(a.ghost + bf * a.nbp + b0);
+              f0 = fma(-ge, u.x, f0);
+              f1 = fma(-ge, u.y, f1);
+              wm = mk == 2 ? -ge * a.bf_spec[bf] : 0.0;
+            }
+            if (mk != 0) {
+              const double2 u = ld2(Isrc + P * row + (long long)a.refl[a.bf_axis[bf] * a.nd + d] * a.nbp + b0);
+              f0 = fma(wm, u.x, f0);
+              f1 = fma(wm, u.y, f1);
+            }
           }
-          f0 = fma(-ge, u.x, f0);
-          f1 = fma(-ge, u.y, f1);
         }
       }
       double r0, r1;
@@ -267,13 +300,16 @@ __global__ void umesh_gout_kernel(const int* cf_ptr, const double* g, int nd, lo
 // (lanes over bands); the partial sums are added in warp order.  Reduced
 // storage sums the stored deviations and writes the ghost deviation (the
 // reference part passes through the ratio: the sets are point-symmetric).
+// On a partially specular face the row receives (1 - p) x the diffuse value
+// (the sweep adds p x the mirrored value).
 constexpr int kDiffWarps = 8;
 
 template <typename St>
 __global__ void __launch_bounds__(32 * kDiffWarps) umesh_diffuse_kernel(const St* I, const long long* bfs, int nlist,
                                                                         const long long* bface, const long long* owner,
                                                                         const double* nA, const double* S, int nd,
-                                                                        int nbp, double* ghost, float* ghost_dev) {
+                                                                        int nbp, const double* spec, double* ghost,
+                                                                        float* ghost_dev) {
   extern __shared__ double part[];  // [kDiffWarps][2][nbp]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int d0 = (int)((long long)wid * nd / kDiffWarps), d1 = (int)((long long)(wid + 1) * nd / kDiffWarps);
@@ -299,7 +335,7 @@ __global__ void __launch_bounds__(32 * kDiffWarps) umesh_diffuse_kernel(const St
         num += part[(w * 2) * nbp + b];
         den += part[(w * 2 + 1) * nbp + b];
       }
-      const double v = den > 0.0 ? num / den : 0.0;
+      const double v = (1.0 - spec[bf]) * (den > 0.0 ? num / den : 0.0);
       if constexpr (sizeof(St) == 8) ghost[bf * nbp + b] = v;
       else ghost_dev[bf * nbp + b] = (float)v;
     }
@@ -311,8 +347,8 @@ __global__ void __launch_bounds__(32 * kDiffWarps) umesh_diffuse_kernel(const St
 template <typename St>
 __global__ void umesh_face_flux_kernel(const St* I, const double* I0ref, const double* ghost, const float* ghost_dev,
                                        const long long* bface, long long nbf, const long long* owner, const double* nA,
-                                       const int* bf_mirror, const int* bf_axis, const int* refl, const double* S,
-                                       int nd, int nbp, int nb, double* Qb) {
+                                       const int* bf_mirror, const int* bf_axis, const double* bf_spec,
+                                       const int* refl, const double* S, int nd, int nbp, int nb, double* Qb) {
   const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
   for (long long bf = blockIdx.x * (long long)warps + threadIdx.x / 32; bf < nbf; bf += (long long)gridDim.x * warps) {
     const long long f = bface[bf], P = owner[f];
@@ -323,10 +359,16 @@ __global__ void umesh_face_flux_kernel(const St* I, const double* I0ref, const d
       const double sn = S[3 * d] * n[0] + S[3 * d + 1] * n[1] + S[3 * d + 2] * n[2];
       for (int b = lane; b < nb; b += 32) {
         double v;
-        if (sn > 0.0) v = full_I(I, base + (long long)d * nbp + b, b, I0ref);
-        else if (bf_mirror[bf]) v = full_I(I, base + (long long)refl[bf_axis[bf] * nd + d] * nbp + b, b, I0ref);
-        else if constexpr (sizeof(St) == 8) v = ghost[bf * nbp + b];
-        else v = I0ref[b] + (double)ghost_dev[bf * nbp + b];
+        const int mk = bf_mirror[bf];
+        if (sn > 0.0) {
+          v = full_I(I, base + (long long)d * nbp + b, b, I0ref);
+        } else if (mk == 1) {
+          v = full_I(I, base + (long long)refl[bf_axis[bf] * nd + d] * nbp + b, b, I0ref);
+        } else {  // the ghost row, plus p x the mirrored value on a partially specular face
+          if constexpr (sizeof(St) == 8) v = ghost[bf * nbp + b];
+          else v = I0ref[b] * (mk == 2 ? 1.0 - bf_spec[bf] : 1.0) + (double)ghost_dev[bf * nbp + b];
+          if (mk == 2) v += bf_spec[bf] * full_I(I, base + (long long)refl[bf_axis[bf] * nd + d] * nbp + b, b, I0ref);
+        }
         s = fma(sn, v, s);
       }
     }
@@ -355,7 +397,7 @@ struct bte_umesh_ctx {
   // boundary faces
   std::vector<long long> bface;  // face id of each boundary face
   std::vector<int> bf_tag, bf_type, bf_axis, bf_ok_axis;
-  std::vector<double> bf_T;
+  std::vector<double> bf_T, bf_p;  // isothermal temperature / specularity
   std::vector<int> tags;          // distinct boundary tags
   std::vector<char> tag_set;      // per entry of tags
   // directions
@@ -376,6 +418,7 @@ struct bte_umesh_ctx {
   double* Msum = nullptr;  // [cell][3] the T_p model's sums, kept with J
   double *ghost = nullptr, *g = nullptr, *gout = nullptr, *S_d = nullptr, *w_d = nullptr, *nA_d = nullptr;
   double *vb_d = nullptr, *bb_d = nullptr, *bfT_d = nullptr, *scratch = nullptr, *Qb = nullptr, *qbuf = nullptr;
+  double* bf_spec_d = nullptr;  // [bface] specularity of partially specular faces, 0 elsewhere
   double* R = nullptr;     // implicit reciprocal diagonal for R_dt (FP64 storage)
   float* Rf = nullptr;     //   the same as float (reduced storage)
   double R_dt = -1.0;
@@ -493,7 +536,7 @@ int ensure_mem(bte_umesh_ctx* u) {
       (rc = dalloc(u, &u->EL, nc)) || (rc = dalloc(u, &u->ghost, nbf * nbp)) || (rc = dalloc(u, &u->bfT_d, nbf)) ||
       (rc = dalloc(u, &u->S_d, nd * 3)) || (rc = dalloc(u, &u->w_d, nd)) || (rc = dalloc(u, &u->nA_d, u->nf * 3)) ||
       (rc = dalloc(u, &u->vb_d, nbp)) || (rc = dalloc(u, &u->bb_d, nbp)) || (rc = dalloc(u, &u->scratch, nc)) ||
-      (rc = dalloc(u, &u->Qb, nbf)) || (rc = dalloc(u, &u->qbuf, nc * 3)) || (rc = dalloc(u, &u->bf_mirror_d, nbf)) || (rc = dalloc(u, &u->bf_axis_d, nbf)) ||
+      (rc = dalloc(u, &u->Qb, nbf)) || (rc = dalloc(u, &u->qbuf, nc * 3)) || (rc = dalloc(u, &u->bf_mirror_d, nbf)) || (rc = dalloc(u, &u->bf_axis_d, nbf)) || (rc = dalloc(u, &u->bf_spec_d, nbf)) ||
       (rc = dalloc(u, &u->refl_d, 3 * nd)) || (rc = dalloc(u, &u->bface_d, nbf)) || (rc = dalloc(u, &u->owner_d, u->nf)) ||
       (rc = dalloc(u, &u->diff_d, nbf)) || (rc = dalloc(u, &u->fix, nc)) || (rc = dalloc(u, &u->fix_count, 4)) ||
       (rc = dalloc(u, &u->counters, 1)) || (rc = dalloc(u, &u->node_c, nbp * u->ng)) ||
@@ -587,14 +630,17 @@ int upload_bc(bte_umesh_ctx* u) {
   const long long nbf = (long long)u->bface.size();
   std::vector<int> mirror(nbf), diff;
   std::vector<long long> diffl;
-  std::vector<double> T(nbf);
+  std::vector<double> T(nbf), spec(nbf, 0.0);
   for (long long k = 0; k < nbf; ++k) {
-    mirror[k] = u->bf_type[k] == BTE_BC_SPECULAR ? 1 : 0;
-    T[k] = u->bf_type[k] == BTE_BC_ISOTHERMAL ? u->bf_T[k] : u->opts.T_ref;
-    if (u->bf_type[k] == BTE_BC_DIFFUSE) diffl.push_back(k);
+    const int t = u->bf_type[k];
+    mirror[k] = t == BTE_BC_SPECULAR ? 1 : (t == BTE_BC_PARTIAL ? 2 : 0);
+    T[k] = t == BTE_BC_ISOTHERMAL ? u->bf_T[k] : u->opts.T_ref;
+    if (t == BTE_BC_PARTIAL) spec[k] = u->bf_p[k];
+    if (t == BTE_BC_DIFFUSE || t == BTE_BC_PARTIAL) diffl.push_back(k);
   }
   int rc;
   if ((rc = upload(u, u->bf_mirror_d, mirror.data(), nbf)) || (rc = upload(u, u->bf_axis_d, u->bf_axis.data(), nbf)) ||
+      (rc = upload(u, u->bf_spec_d, spec.data(), nbf)) ||
       (rc = upload(u, u->bfT_d, T.data(), nbf)) || (rc = upload(u, u->diff_d, diffl.data(), diffl.size())))
     return rc;
   u->ndiff = (int)diffl.size();
@@ -610,15 +656,16 @@ cudaError_t refresh_diffuse(bte_umesh_ctx* u, const void* I) {
   const size_t sm = (size_t)kDiffWarps * 2 * u->nbp * sizeof(double);
   if (u->prec == BTE_FP64)
     umesh_diffuse_kernel<double><<<grid, 32 * kDiffWarps, sm, u->stream>>>(
-        (const double*)I, u->diff_d, u->ndiff, u->bface_d, u->owner_d, u->nA_d, u->S_d, u->nd, u->nbp, u->ghost, nullptr);
+        (const double*)I, u->diff_d, u->ndiff, u->bface_d, u->owner_d, u->nA_d, u->S_d, u->nd, u->nbp, u->bf_spec_d,
+        u->ghost, nullptr);
   else if (u->prec == BTE_FP32)
     umesh_diffuse_kernel<float><<<grid, 32 * kDiffWarps, sm, u->stream>>>(
-        (const float*)I, u->diff_d, u->ndiff, u->bface_d, u->owner_d, u->nA_d, u->S_d, u->nd, u->nbp, nullptr,
-        u->ghost_dev);
+        (const float*)I, u->diff_d, u->ndiff, u->bface_d, u->owner_d, u->nA_d, u->S_d, u->nd, u->nbp, u->bf_spec_d,
+        nullptr, u->ghost_dev);
   else
     umesh_diffuse_kernel<__nv_bfloat16><<<grid, 32 * kDiffWarps, sm, u->stream>>>(
-        (const __nv_bfloat16*)I, u->diff_d, u->ndiff, u->bface_d, u->owner_d, u->nA_d, u->S_d, u->nd, u->nbp, nullptr,
-        u->ghost_dev);
+        (const __nv_bfloat16*)I, u->diff_d, u->ndiff, u->bface_d, u->owner_d, u->nA_d, u->S_d, u->nd, u->nbp,
+        u->bf_spec_d, nullptr, u->ghost_dev);
   return cudaGetLastError();
 }
 
@@ -678,6 +725,7 @@ int bte_umesh_create(const bte_umesh_desc* m, const bte_opts* opts, bte_umesh* o
     u->bf_tag.push_back(u->tag[f]);
     u->bf_type.push_back(-1);
     u->bf_T.push_back(0.0);
+    u->bf_p.push_back(0.0);
     const double* a = &u->nA[3 * f];
     int ax = 0;
     for (int c = 1; c < 3; ++c)
@@ -740,12 +788,16 @@ int bte_umesh_set_bc(bte_umesh u, int tag, int type, const double* T_faces, doub
   if (!u->mem_ready) return ufail(u, BTE_E_STATE, "bte_umesh_set_bands must come first");
   const auto it = std::find(u->tags.begin(), u->tags.end(), tag);
   if (it == u->tags.end()) return ufail(u, BTE_E_ARG, "no boundary face has tag %d", tag);
-  if (type != BTE_BC_ISOTHERMAL && type != BTE_BC_SPECULAR && type != BTE_BC_DIFFUSE)
+  if (type != BTE_BC_ISOTHERMAL && type != BTE_BC_SPECULAR && type != BTE_BC_DIFFUSE && type != BTE_BC_PARTIAL)
     return ufail(u, BTE_E_ARG, "unknown boundary type %d", type);
   for (size_t k = 0; k < u->bface.size(); ++k) {
     if (u->bf_tag[k] != tag) continue;
-    if (type == BTE_BC_SPECULAR && !u->bf_ok_axis[k])
+    if ((type == BTE_BC_SPECULAR || type == BTE_BC_PARTIAL) && !u->bf_ok_axis[k])
       return ufail(u, BTE_E_ARG, "tag %d: face %lld is not normal to an axis (a mirror needs that)", tag, u->bface[k]);
+    if (type == BTE_BC_PARTIAL) {
+      const double p = T_faces ? T_faces[u->bface[k]] : T_uniform;
+      if (!(p >= 0.0 && p <= 1.0)) return ufail(u, BTE_E_ARG, "tag %d: specularity must lie in [0, 1]", tag);
+    }
     if (type == BTE_BC_ISOTHERMAL) {
       const double T = T_faces ? T_faces[u->bface[k]] : T_uniform;
       if (!(std::isfinite(T) && T >= kTmin && T <= kTmax))
@@ -756,6 +808,7 @@ int bte_umesh_set_bc(bte_umesh u, int tag, int type, const double* T_faces, doub
     if (u->bf_tag[k] != tag) continue;
     u->bf_type[k] = type;
     u->bf_T[k] = type == BTE_BC_ISOTHERMAL ? (T_faces ? T_faces[u->bface[k]] : T_uniform) : 0.0;
+    u->bf_p[k] = type == BTE_BC_PARTIAL ? (T_faces ? T_faces[u->bface[k]] : T_uniform) : 0.0;
   }
   u->tag_set[it - u->tags.begin()] = 1;
   for (char c : u->tag_set)
@@ -821,6 +874,7 @@ int bte_umesh_step(bte_umesh u, double dt, int nsteps, int ninner, int scheme, b
   a.gout = u->gout;
   a.bf_mirror = u->bf_mirror_d;
   a.bf_axis = u->bf_axis_d;
+  a.bf_spec = u->bf_spec_d;
   a.refl = u->refl_d;
   a.vb = u->vb_d;
   a.bb = u->bb_d;
@@ -998,16 +1052,16 @@ int bte_umesh_get_flux(bte_umesh u, double* q, double* Q) {
       const int gr = grid_for(nbf, 4);
       if (u->prec == BTE_FP64)
         umesh_face_flux_kernel<double><<<gr, 128, 0, s>>>((const double*)I, u->I0ref, u->ghost, u->ghost_dev, u->bface_d,
-                                                          nbf, u->owner_d, u->nA_d, u->bf_mirror_d, u->bf_axis_d,
+                                                          nbf, u->owner_d, u->nA_d, u->bf_mirror_d, u->bf_axis_d, u->bf_spec_d,
                                                           u->refl_d, u->S_d, u->nd, u->nbp, u->nb, u->Qb);
       else if (u->prec == BTE_FP32)
         umesh_face_flux_kernel<float><<<gr, 128, 0, s>>>((const float*)I, u->I0ref, u->ghost, u->ghost_dev, u->bface_d,
-                                                         nbf, u->owner_d, u->nA_d, u->bf_mirror_d, u->bf_axis_d,
+                                                         nbf, u->owner_d, u->nA_d, u->bf_mirror_d, u->bf_axis_d, u->bf_spec_d,
                                                          u->refl_d, u->S_d, u->nd, u->nbp, u->nb, u->Qb);
       else
         umesh_face_flux_kernel<__nv_bfloat16><<<gr, 128, 0, s>>>((const __nv_bfloat16*)I, u->I0ref, u->ghost,
                                                                  u->ghost_dev, u->bface_d, nbf, u->owner_d, u->nA_d,
-                                                                 u->bf_mirror_d, u->bf_axis_d, u->refl_d, u->S_d, u->nd,
+                                                                 u->bf_mirror_d, u->bf_axis_d, u->bf_spec_d, u->refl_d, u->S_d, u->nd,
                                                                  u->nbp, u->nb, u->Qb);
       UTRY(u, cudaGetLastError());
     }
