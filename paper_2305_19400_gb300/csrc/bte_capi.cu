@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <numeric>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -247,7 +248,11 @@ void build_items(bte_ctx* h, int cpb = 0) {
   const int rowb = h->nbp * (int)elem_bytes(h->opts.precision);
   h->dteam = std::max(1, std::min(std::min(896 / rowb, 256 / h->lpc), h->nd / 32));
   const int team = h->lpc * h->dteam;
-  h->cpb = cpb > 0 ? cpb : std::max(1, 256 / team);
+  // default: the most cells whose CTA (at most 256 threads) is whole warps, else
+  // the most that fit
+  const int whole = 32 / std::gcd(team, 32);
+  const int cpb_whole = (256 / team) / whole * whole;
+  h->cpb = cpb > 0 ? cpb : (cpb_whole > 0 ? cpb_whole : std::max(1, 256 / team));
   h->threads = h->cpb * team;
   h->items.clear();
   for (size_t gi = 0; gi < h->geoms.size(); ++gi) {
@@ -1130,14 +1135,19 @@ int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t repor
   const int spare = (h->cur + 1) % 3;  // timing launches write here; the state is untouched (dry epilogue)
   struct Cand { int cpb, grid, pd; float ms; };
   std::vector<Cand> tried;
-  const int tpc_list[2] = {128, 256};
+  // cells per CTA: about 128 or 256 threads, and every count up to 256 threads
+  // whose CTA is whole warps (a partial warp still occupies the FP64 pipe's
+  // issue slots of a full one)
+  const int team = h->lpc * h->dteam;
+  std::vector<int> cpb_list = {std::max(1, 128 / team), std::max(1, 256 / team)};
+  const int whole = 32 / std::gcd(team, 32);
+  for (int c = whole; c * team <= 256; c += whole) cpb_list.push_back(c);
   const int pd_list[2] = {1, 2};
   int best_cpb = h->cpb, best_grid = h->grid, best_pd = h->pd;
   float best_ms = 1e30f;
   int dim = 2;
   for (auto& g : h->geoms) dim = std::max(dim, g.dim);
-  for (int tpc : tpc_list) {
-    const int cpb = std::max(1, tpc / (h->lpc * h->dteam));
+  for (int cpb : cpb_list) {
     bool seen = false;
     for (auto& c : tried) seen |= c.cpb == cpb;
     if (seen) continue;

@@ -25,42 +25,55 @@ namespace bte {
 namespace {
 
 // Exact temperature solve of the cells the sweep could not settle on their
-// cached model: one warp per cell.  The start is the model root (plain mode)
-// or the learned guess (net A, then surrogate Newton steps on net B); the
-// exact FP64 quadrature then refines it (each evaluation becomes the cell's
-// cached model) and I0 is refreshed.
-__global__ void fixup_kernel(SweepArgs a, int learned, MLPView m) {
-  extern __shared__ float fsm[];  // per warp: 2*nb + 4*kHidden floats (learned mode)
-  const int warps = blockDim.x / 32;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x / 32;
+// cached model: one CTA per cell (exact_solve_cta spreads each evaluation over
+// the SM's four FP64 units; with a handful of such cells per step the solve's
+// latency, not its throughput, is what the step waits for).  The start is the
+// model root (plain mode) or the learned guess (net A, then surrogate Newton
+// steps on net B, by warp 0); the exact FP64 quadrature then refines it (each
+// evaluation becomes the cell's cached model) and I0 is refreshed.
+constexpr int kFixThreads = 128;
+
+__global__ void __launch_bounds__(kFixThreads) fixup_kernel(SweepArgs a, int learned, MLPView m) {
+  extern __shared__ double fsm[];  // exact_solve_cta scratch, T0, then the learned-mode buffers
   const int nbp = a.th.nbp;
-  float* ybuf = fsm + (size_t)wid * (2 * nbp + 4 * kHidden);
+  double* solve_sm = fsm;
+  double* t0_sm = fsm + cta_solve_smem_doubles(nbp);
+  float* ybuf = reinterpret_cast<float*>(t0_sm + 2);
   float* hbuf = ybuf + 2 * nbp;
   const unsigned count = *a.fix_count;
   unsigned long long evals = 0, fb = 0, bad = 0;
-  for (unsigned w = blockIdx.x * warps + wid; w < count; w += gridDim.x * warps) {
+  for (unsigned w = blockIdx.x; w < count; w += gridDim.x) {
     const FixItem it = a.fix[w];
     const long long P = it.P;
-    const double T0 = learned ? mlp_guess_T(m, a.th.a_p, it.Ep, 2, ybuf, hbuf) : it.T0;
-    const SolveResult r = exact_solve_warp(a.th, it.Ep, T0, a.trust_rel, a.maxit, a.J + (P * 3) * nbp);
+    if (learned) {
+      if (threadIdx.x < 32) {
+        const double g = mlp_guess_T(m, a.th.a_p, it.Ep, 2, ybuf, hbuf);
+        if (threadIdx.x == 0) t0_sm[0] = g;
+      }
+      __syncthreads();
+    }
+    const double T0 = learned ? t0_sm[0] : it.T0;
+    const SolveResult r = exact_solve_cta(a.th, it.Ep, T0, a.trust_rel, a.maxit, a.J + (P * 3) * nbp, solve_sm);
     evals += r.evals;
     fb += r.fallback;
     bad += r.bad;
+    __syncthreads();  // the model row written by the solve, before the I0 refresh reads it
     // I0 refresh of the stored bands from the (just written) model at r.Te
     const double hd2 = 0.5 * r.delta * r.delta;
-    for (int b = lane; b < a.th.nbo; b += 32) {
+    for (int b = threadIdx.x; b < a.th.nbo; b += blockDim.x) {
       const long long j = (P * 3) * nbp + a.th.band0 + b;
       a.I0cell[P * a.th.nbo + b] = b < a.th.nbr ? fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], r.delta, a.J[j])) : 0.0;
     }
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
       a.Teval[P] = r.Te;
       a.Tp[P] = r.Te + r.delta;
       a.Msum[3 * P] = r.M[0];  // the model just written to J
       a.Msum[3 * P + 1] = r.M[1];
       a.Msum[3 * P + 2] = r.M[2];
     }
+    __syncthreads();  // t0_sm and the solve scratch are reused by the next item
   }
-  if (lane == 0 && a.counters) {
+  if (threadIdx.x == 0 && a.counters) {
     if (evals) atomicAdd(&a.counters->evals, evals);
     if (fb) atomicAdd(&a.counters->fallbacks, fb);
     if (bad) atomicAdd(&a.counters->nonfinite, bad);
@@ -658,10 +671,11 @@ cudaError_t launch_sweep(int precision, int pd, const SweepArgs& a, int dim, int
 }
 
 cudaError_t launch_fixup(const SweepArgs& a, const MLPView* mlp, cudaStream_t s) {
-  const size_t sm = mlp ? 4 * (2 * (size_t)a.th.nbp + 4 * kHidden) * sizeof(float) : 0;
+  const size_t sm = (cta_solve_smem_doubles(a.th.nbp) + 2) * sizeof(double) +
+                    (mlp ? (2 * (size_t)a.th.nbp + 4 * kHidden) * sizeof(float) : 0);
   MLPView m{};
   if (mlp) m = *mlp;
-  fixup_kernel<<<152, 128, sm, s>>>(a, mlp ? 1 : 0, m);
+  fixup_kernel<<<2 * 152, kFixThreads, sm, s>>>(a, mlp ? 1 : 0, m);
   return cudaGetLastError();
 }
 
