@@ -148,10 +148,11 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   const int dg = tl / lpc, lane = tl - dg * lpc;      // direction offset in a step, band vector
   DirSm* dsm = reinterpret_cast<DirSm*>(sm);          // [nd]
   double* gsm = sm + (sizeof(DirSm) / 8) * nd;        // [blockDim.x][V] per-lane band partials
-  double* red = gsm + (size_t)V * blockDim.x;         // [cpb * lpc][2] per-band-vector E_L, E_p sums
+  double* red = gsm + (size_t)V * blockDim.x;         // [cpb * lpc][2] per-band-vector E_L, E_p sums,
+                                                      // then [cpb][4] per-cell scratch
   // staging ring of the far operands: [kStages][kOps][blockDim.x] x 16 bytes
   char* ring = reinterpret_cast<char*>(
-      (reinterpret_cast<uintptr_t>(red + 2 * (size_t)cpb * lpc) + 15) & ~static_cast<uintptr_t>(15));
+      (reinterpret_cast<uintptr_t>(red + 2 * (size_t)cpb * lpc + 4 * (size_t)cpb) + 15) & ~static_cast<uintptr_t>(15));
   const S* __restrict__ In = reinterpret_cast<const S*>(a.In);
   const S* __restrict__ Ik = reinterpret_cast<const S*>(a.Ik);
   S* __restrict__ Io = reinterpret_cast<S*>(a.Iout);
@@ -461,12 +462,12 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
 
     // ---- per-cell reduction.  The lanes of a cell hold band partials over their
     // direction subsets; the band owners (dg == 0) add them in a fixed order to
-    // G_b, then E_L = sum_b G_b / v_b, E_p = sum_b beta_b G_b / v_b and the sums of
-    // the T_p equation's terms on the cached quadratic model around T_e, per band
-    // vector.  Then one warp per cell adds the band vectors (shuffle tree),
-    // solves the model and refreshes all of the cell's I0.  Two barriers per
-    // item: every read of gsm precedes the second, every read of red precedes
-    // the next item's first.
+    // G_b, then E_L = sum_b G_b / v_b and E_p = sum_b beta_b G_b / v_b per band
+    // vector.  One warp per cell adds the band vectors (shuffle tree); one warp
+    // then solves every cell's model (lanes over cells), and all threads refresh
+    // the accepted cells' I0.  Four barriers per item: every read of gsm
+    // precedes the second, every read of red the third, and every read of the
+    // per-cell scratch the next item's second.
     double* gb = gsm;
     double* rb = red;
 #pragma unroll
@@ -487,8 +488,8 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       r2[1] = ep;
     }
     __syncthreads();
-    for (int cs = wid; wid < nwarps && cs < wi.cell_count; cs += nwarps) {  // warp per cell
-      const long long Pc = gp->cell0 + wi.cell_begin + cs;
+    double* cst = rb + 2 * (size_t)cpb * lpc;  // [cpb][4]: E_L, E_p, model step, accepted
+    for (int cs = wid; wid < nwarps && cs < wi.cell_count; cs += nwarps) {  // warp per cell: E_L, E_p
       double EL = 0.0, Ep = 0.0;
       for (int l = wl; l < lpc; l += 32) {
         const double* r2 = rb + 2 * (size_t)(cs * lpc + l);
@@ -499,45 +500,67 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         EL += __shfl_xor_sync(0xffffffffu, EL, o);
         Ep += __shfl_xor_sync(0xffffffffu, Ep, o);
       }
-      const bool lead = wl == 0;  // writes the cell's outputs
-      if (a.partial) {  // band-range handle: partial sums for the caller's all-reduce
-        if (lead && !a.dry) {
-          a.Epart[2 * Pc] = EL;
-          a.Epart[2 * Pc + 1] = Ep;
-        }
-        continue;
+      if (wl == 0) {
+        cst[4 * cs] = EL;
+        cst[4 * cs + 1] = Ep;
       }
-      if (lead && !a.dry) a.EL[Pc] = EL;
-      if (!isfinite(EL) || !isfinite(Ep)) {
-        if (lead) atomicAdd(&cnt_bad, 1ULL);
-        continue;
-      }
-      if (!a.solve_tp) continue;
-      if (lead) atomicAdd(&cnt_solves, 1ULL);
-      // root of (F - E_p) + F1 d + F2 d^2 / 2 nearest 0; F, F1, F2: the model's
-      // sums sum_b a_p,b J_k,b, kept with J
-      const double Fs = a.Msum[3 * Pc] - Ep, F1s = a.Msum[3 * Pc + 1], F2s = a.Msum[3 * Pc + 2];
-      const double Te = a.Teval[Pc];
-      const double disc = F1s * F1s - 2.0 * Fs * F2s;
-      const double delta = (disc >= 0.0 && F1s > 0.0) ? -2.0 * Fs / (F1s + sqrt(disc)) : -Fs / F1s;
-      const double Tn = Te + delta;
-      if (isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn) {
-        if (!a.dry) {  // I0 refresh of every band of the cell from the model
-          const double hd2 = 0.5 * delta * delta;
-          for (int b = wl; b < nbp; b += 32) {
-            const long long j = (Pc * 3) * nbp_all + band0 + b;
-            a.I0cell[Pc * nbp + b] = b < nbr ? fma(a.J[j + 2 * nbp_all], hd2, fma(a.J[j + nbp_all], delta, a.J[j])) : 0.0;
+    }
+    __syncthreads();
+    // The cells' scalar steps with lanes over cells: one warp instruction serves
+    // every cell of the item (a warp per cell would spend a whole warp's FP64
+    // issue slots on each cell's square root and divisions).
+    if (wid == 0) {
+      for (int cs = wl; cs < wi.cell_count; cs += 32) {
+        const long long Pc = gp->cell0 + wi.cell_begin + cs;
+        const double EL = cst[4 * cs], Ep = cst[4 * cs + 1];
+        double accepted = 0.0;
+        if (a.partial) {  // band-range handle: partial sums for the caller's all-reduce
+          if (!a.dry) {
+            a.Epart[2 * Pc] = EL;
+            a.Epart[2 * Pc + 1] = Ep;
           }
-          if (lead) a.Tp[Pc] = Tn;
+        } else {
+          if (!a.dry) a.EL[Pc] = EL;
+          if (!isfinite(EL) || !isfinite(Ep)) {
+            atomicAdd(&cnt_bad, 1ULL);
+          } else if (a.solve_tp) {
+            atomicAdd(&cnt_solves, 1ULL);
+            // root of (F - E_p) + F1 d + F2 d^2 / 2 nearest 0; F, F1, F2: the model's
+            // sums sum_b a_p,b J_k,b, kept with J
+            const double Fs = a.Msum[3 * Pc] - Ep, F1s = a.Msum[3 * Pc + 1], F2s = a.Msum[3 * Pc + 2];
+            const double Te = a.Teval[Pc];
+            const double disc = F1s * F1s - 2.0 * Fs * F2s;
+            const double delta = (disc >= 0.0 && F1s > 0.0) ? -2.0 * Fs / (F1s + sqrt(disc)) : -Fs / F1s;
+            const double Tn = Te + delta;
+            if (isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn) {
+              if (!a.dry) {
+                a.Tp[Pc] = Tn;
+                cst[4 * cs + 2] = delta;
+                accepted = 1.0;
+              }
+            } else if (!a.dry) {  // exact quadrature needed: hand the cell to the fix-up kernel
+              const unsigned k = atomicAdd(a.fix_count, 1u);
+              FixItem fi;
+              fi.P = Pc;
+              fi.Ep = Ep;
+              fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[Pc];
+              a.fix[k] = fi;
+            }
+          }
         }
-      } else if (lead && !a.dry) {  // exact quadrature needed: hand the cell to the fix-up kernel
-        const unsigned k = atomicAdd(a.fix_count, 1u);
-        FixItem fi;
-        fi.P = Pc;
-        fi.Ep = Ep;
-        fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[Pc];
-        a.fix[k] = fi;
+        cst[4 * cs + 3] = accepted;
       }
+    }
+    __syncthreads();
+    // I0 refresh of every band of the accepted cells from their models: threads
+    // over (cell, band).  Every read of cst precedes the next item's second barrier.
+    for (int e = threadIdx.x; e < wi.cell_count * nbp; e += blockDim.x) {
+      const int cs = e / nbp, b = e - cs * nbp;
+      if (cst[4 * cs + 3] == 0.0) continue;
+      const long long Pc = gp->cell0 + wi.cell_begin + cs;
+      const double delta = cst[4 * cs + 2], hd2 = 0.5 * delta * delta;
+      const long long j = (Pc * 3) * nbp_all + band0 + b;
+      a.I0cell[Pc * nbp + b] = b < nbr ? fma(a.J[j + 2 * nbp_all], hd2, fma(a.J[j + nbp_all], delta, a.J[j])) : 0.0;
     }
   }
   __syncthreads();
@@ -551,7 +574,7 @@ template <typename S, int MINB, int BM, bool TT>
 cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   const int team = a.lpc * a.dteam, cpb = threads / team;
   const size_t smem = sizeof(DirSm) * (size_t)a.nd + (size_t)Tr<S>::V * threads * sizeof(double) +
-                      2 * (size_t)cpb * a.lpc * sizeof(double) + 16 +
+                      (2 * (size_t)cpb * a.lpc + 4 * (size_t)cpb) * sizeof(double) + 16 +
                       (size_t)(dim == 3 ? Ring<3, S>::kStages * Ring<3, S>::kOps : Ring<2, S>::kStages * Ring<2, S>::kOps) *
                           threads * 16;
   if (dim == 3) {
