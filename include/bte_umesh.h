@@ -63,10 +63,12 @@ typedef struct {
 } bte_umesh_desc;
 
 /* Creates a handle.  opts: as in bte.h (precision BTE_FP64, BTE_FP32 or
- * BTE_BF16; learned and beta_T_exp must be 0; use_graph and autotune are not
- * used by this handle, which launches each kernel directly with a fixed
- * shape); may be NULL for the defaults.  *out receives
- * the handle, NULL on failure (message in bte_umesh_last_error(NULL)). */
+ * BTE_BF16; beta_T_exp as in bte.h, |beta_T_exp| <= 16, the relaxation rates
+ * beta_b (T_p / T_ref)^beta_T_exp per cell, refreshed before every sweep;
+ * learned must be 0; use_graph and autotune are not used by this handle,
+ * which launches each kernel directly with a fixed shape); may be NULL for
+ * the defaults.  *out receives the handle, NULL on failure (message in
+ * bte_umesh_last_error(NULL)). */
 int bte_umesh_create(const bte_umesh_desc* mesh, const bte_opts* opts, bte_umesh* out);
 
 /* Band table, as bte_set_bands. */
@@ -91,8 +93,9 @@ int bte_umesh_set_initial(bte_umesh u, const double* T_cells, double T_uniform);
 
 /* nsteps time steps of dt [s]; scheme BTE_IMPLICIT_JACOBI (ninner inner
  * iterations) or BTE_EXPLICIT (ninner ignored).  Each inner iteration is a
- * sweep kernel, the per-cell step and the fix-up (and one kernel per tag
- * with diffuse faces).  stats: as bte_step, may be NULL. */
+ * sweep kernel, the per-cell step and the fix-up (plus one kernel for the
+ * diffuse and partially specular faces, and one for the per-cell relaxation
+ * scale when beta_T_exp != 0).  stats: as bte_step, may be NULL. */
 int bte_umesh_step(bte_umesh u, double dt, int nsteps, int ninner, int scheme, bte_stats* stats);
 
 /* Cell temperatures (BTE_T_PSEUDO or BTE_T_LATTICE) into out: ncells doubles,

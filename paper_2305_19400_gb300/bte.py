@@ -431,12 +431,16 @@ class UMeshSolver:
     bc: {tag: (kind, T)} with kind BTE_BC_ISOTHERMAL (T a float, or an array
     over the mesh's faces indexed by face id), BTE_BC_SPECULAR or
     BTE_BC_DIFFUSE (T ignored), or BTE_BC_PARTIAL (T the specularity p, a
-    float or an array over the faces)."""
+    float or an array over the faces).  beta_exp: relaxation rates
+    beta_b (T_p / T_ref)^beta_exp per cell (0: tau fixed)."""
 
-    def __init__(self, mesh, dirs, bands, bc, T_init=None, stream=None, n_gauss=16, precision=BTE_FP64):
+    def __init__(self, mesh, dirs, bands, bc, T_init=None, stream=None, n_gauss=16, precision=BTE_FP64,
+                 beta_exp=0.0, T_ref=300.0):
         import torch
         o = bte_default_opts()
         o.precision = precision
+        o.beta_T_exp = beta_exp
+        o.T_ref = T_ref
         if dirs.kind == "inplane":
             o.dir_kind, o.n_inplane = BTE_DIRS_INPLANE, dirs.n_inplane
         else:

@@ -68,6 +68,7 @@ struct UArgs {
   const float* ghost_dev;
   const double* I0ref;
   const float* g32;        // [entries][nd] g as float (reduced storage)
+  const double* bscale;    // TT: [nc] s = (T_p / T_ref)^p, beta_b(T_p) = beta_b s
 };
 
 // V consecutive floats (16-byte loads).
@@ -89,7 +90,7 @@ __device__ __forceinline__ void ldf(const float* p, float (&x)[V]) {
 // A lane holds V bands (16 bytes of storage).  The kernel is bound by the
 // latency of the face gathers, so it is capped at 6 CTAs of 252 threads per SM
 // (more warps in flight; measured faster than 3-5 CTAs despite small spills).
-template <typename S, bool EXPL, int BM>
+template <typename S, bool EXPL, int BM, bool TT>
 __global__ void __launch_bounds__(256, 6) umesh_sweep_dev_kernel(UArgs a) {
   using T = Tr<S>;
   constexpr int V = T::V;
@@ -113,9 +114,16 @@ __global__ void __launch_bounds__(256, 6) umesh_sweep_dev_kernel(UArgs a) {
   }
   for (long long P = (long long)blockIdx.x * cpb + slot; P < a.nc; P += (long long)gridDim.x * cpb) {
     const int e0 = a.cf_ptr[P], e1 = a.cf_ptr[P + 1];
-    float src[V];  // beta (I0 - I0ref)
+    float bs[V], sm1[V];  // beta_b(T_p) = beta_b s; (s - 1) beta_b
+    const double sc = TT ? a.bscale[P] : 1.0;
 #pragma unroll
-    for (int v = 0; v < V; ++v) src[v] = bb[v] * (float)(a.I0cell[P * a.nbp + b0 + v] - a.I0ref[b0 + v]);
+    for (int v = 0; v < V; ++v) {
+      bs[v] = TT ? (float)(sc * (double)bb[v]) : bb[v];
+      sm1[v] = TT ? (float)((sc - 1.0) * (double)bb[v]) : 0.f;
+    }
+    float src[V];  // beta_b(T_p) (I0 - I0ref)
+#pragma unroll
+    for (int v = 0; v < V; ++v) src[v] = bs[v] * (float)(a.I0cell[P * a.nbp + b0 + v] - a.I0ref[b0 + v]);
     for (int d = dg; d < a.nd; d += a.dteam) {
       const long long off = P * row + (long long)d * a.nbp + b0;
       float in[V], f[V];
@@ -159,7 +167,7 @@ __global__ void __launch_bounds__(256, 6) umesh_sweep_dev_kernel(UArgs a) {
       if (EXPL) {
         const float go = (float)a.gout[P * a.nd + d];
 #pragma unroll
-        for (int v = 0; v < V; ++v) r[v] = fmaf(dt, fmaf(-bb[v], in[v], src[v]) - vb[v] * fmaf(go, in[v], -f[v]), in[v]);
+        for (int v = 0; v < V; ++v) r[v] = fmaf(dt, fmaf(-bs[v], in[v], src[v]) - vb[v] * fmaf(go, in[v], -f[v]), in[v]);
       } else {
         float R[V], B[V];
         ldf<V>(a.Rf + off, R);
@@ -168,6 +176,10 @@ __global__ void __launch_bounds__(256, 6) umesh_sweep_dev_kernel(UArgs a) {
         if (BM == 1) T::st(Bo + off, B);
 #pragma unroll
         for (int v = 0; v < V; ++v) r[v] = fmaf(R[v], fmaf(vb[v], f[v], src[v]), B[v]);
+        if constexpr (TT) {  // R_s = R / (1 + (s - 1) beta R): the cached R is at s = 1
+#pragma unroll
+          for (int v = 0; v < V; ++v) r[v] *= __frcp_rn(fmaf(sm1[v], R[v], 1.f));
+        }
       }
       T::st(Io + off, r);
     }
@@ -181,7 +193,7 @@ __device__ __forceinline__ double2 ld2(const double* p) { return __ldg(reinterpr
 // step), so the update is R (beta I0 + v sum |g| I_up) + B.  Capped at 5 CTAs
 // of 256 threads per SM (48 registers, a few bytes of spill outside the face
 // loop): uncapped it takes 58 registers and 4 CTAs, measured 7 % slower.
-template <bool EXPL, int BM>
+template <bool EXPL, int BM, bool TT>
 __global__ void __launch_bounds__(256, 5) umesh_sweep_kernel(UArgs a) {
   const int team = a.lpc * a.dteam;
   const int cpb = blockDim.x / team;
@@ -194,7 +206,11 @@ __global__ void __launch_bounds__(256, 5) umesh_sweep_kernel(UArgs a) {
   for (long long P = (long long)blockIdx.x * cpb + slot; P < a.nc; P += (long long)gridDim.x * cpb) {
     const int e0 = a.cf_ptr[P], e1 = a.cf_ptr[P + 1];
     const double2 i0 = ld2(a.I0cell + P * a.nbp + b0);
-    const double bi0 = be0 * i0.x, bi1 = be1 * i0.y;
+    // beta_b(T_p) = beta_b s (s = 1 unless TT) and (s - 1) beta_b
+    const double sc = TT ? a.bscale[P] : 1.0;
+    const double bs0 = TT ? sc * be0 : be0, bs1 = TT ? sc * be1 : be1;
+    const double sm0 = TT ? (sc - 1.0) * be0 : 0.0, sm1 = TT ? (sc - 1.0) * be1 : 0.0;
+    const double bi0 = bs0 * i0.x, bi1 = bs1 * i0.y;
     for (int d = dg; d < a.nd; d += a.dteam) {
       const long long off = P * row + (long long)d * a.nbp + b0;
       const double2 in = ld2(a.In + off);
@@ -231,8 +247,8 @@ __global__ void __launch_bounds__(256, 5) umesh_sweep_kernel(UArgs a) {
       double r0, r1;
       if (EXPL) {  // I + dt [beta (I0 - I) - v (gout I - sum |g| I_up)]
         const double go = a.gout[P * a.nd + d];
-        r0 = fma(a.dt, fma(be0, i0.x - in.x, -v0 * fma(go, in.x, -f0)), in.x);
-        r1 = fma(a.dt, fma(be1, i0.y - in.y, -v1 * fma(go, in.y, -f1)), in.y);
+        r0 = fma(a.dt, fma(bs0, i0.x - in.x, -v0 * fma(go, in.x, -f0)), in.x);
+        r1 = fma(a.dt, fma(bs1, i0.y - in.y, -v1 * fma(go, in.y, -f1)), in.y);
       } else {  // R [beta I0 + v sum |g| I_up] + (I^n/dt) R, R = 1 / [1/dt + beta + v gout]
         const double2 rr = ld2(a.R + off);
         double B0 = in.x, B1 = in.y;
@@ -243,6 +259,10 @@ __global__ void __launch_bounds__(256, 5) umesh_sweep_kernel(UArgs a) {
         }
         r0 = fma(rr.x, fma(v0, f0, bi0), B0);
         r1 = fma(rr.y, fma(v1, f1, bi1), B1);
+        if constexpr (TT) {  // R_s = R / (1 + (s - 1) beta R): the cached R is at s = 1
+          r0 *= __drcp_rn(fma(sm0, rr.x, 1.0));
+          r1 *= __drcp_rn(fma(sm1, rr.y, 1.0));
+        }
       }
       *reinterpret_cast<double2*>(a.Iout + off) = make_double2(r0, r1);
     }
@@ -377,6 +397,29 @@ __global__ void umesh_face_flux_kernel(const St* I, const double* I0ref, const d
   }
 }
 
+// One sweep launch: storage precision, scheme, B mode (0 plain, 1 store B, 2
+// read B) and TT (per-cell relaxation scale).
+template <bool TT>
+cudaError_t launch_umesh_sweep(int prec, bool expl, int bm, const UArgs& a, int grid, int threads, cudaStream_t s) {
+  if (prec == BTE_FP64) {
+    if (expl) umesh_sweep_kernel<true, 0, TT><<<grid, threads, 0, s>>>(a);
+    else if (bm == 1) umesh_sweep_kernel<false, 1, TT><<<grid, threads, 0, s>>>(a);
+    else if (bm == 2) umesh_sweep_kernel<false, 2, TT><<<grid, threads, 0, s>>>(a);
+    else umesh_sweep_kernel<false, 0, TT><<<grid, threads, 0, s>>>(a);
+  } else if (prec == BTE_FP32) {
+    if (expl) umesh_sweep_dev_kernel<float, true, 0, TT><<<grid, threads, 0, s>>>(a);
+    else if (bm == 1) umesh_sweep_dev_kernel<float, false, 1, TT><<<grid, threads, 0, s>>>(a);
+    else if (bm == 2) umesh_sweep_dev_kernel<float, false, 2, TT><<<grid, threads, 0, s>>>(a);
+    else umesh_sweep_dev_kernel<float, false, 0, TT><<<grid, threads, 0, s>>>(a);
+  } else {
+    if (expl) umesh_sweep_dev_kernel<__nv_bfloat16, true, 0, TT><<<grid, threads, 0, s>>>(a);
+    else if (bm == 1) umesh_sweep_dev_kernel<__nv_bfloat16, false, 1, TT><<<grid, threads, 0, s>>>(a);
+    else if (bm == 2) umesh_sweep_dev_kernel<__nv_bfloat16, false, 2, TT><<<grid, threads, 0, s>>>(a);
+    else umesh_sweep_dev_kernel<__nv_bfloat16, false, 0, TT><<<grid, threads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
 thread_local std::string g_umesh_err;
 
 int grid_for(long long n, int per_block) {
@@ -419,6 +462,7 @@ struct bte_umesh_ctx {
   double *ghost = nullptr, *g = nullptr, *gout = nullptr, *S_d = nullptr, *w_d = nullptr, *nA_d = nullptr;
   double *vb_d = nullptr, *bb_d = nullptr, *bfT_d = nullptr, *scratch = nullptr, *Qb = nullptr, *qbuf = nullptr;
   double* bf_spec_d = nullptr;  // [bface] specularity of partially specular faces, 0 elsewhere
+  double* bscale = nullptr;     // [nc] relaxation scale (T_p / T_ref)^beta_T_exp
   double* R = nullptr;     // implicit reciprocal diagonal for R_dt (FP64 storage)
   float* Rf = nullptr;     //   the same as float (reduced storage)
   double R_dt = -1.0;
@@ -536,7 +580,7 @@ int ensure_mem(bte_umesh_ctx* u) {
       (rc = dalloc(u, &u->EL, nc)) || (rc = dalloc(u, &u->ghost, nbf * nbp)) || (rc = dalloc(u, &u->bfT_d, nbf)) ||
       (rc = dalloc(u, &u->S_d, nd * 3)) || (rc = dalloc(u, &u->w_d, nd)) || (rc = dalloc(u, &u->nA_d, u->nf * 3)) ||
       (rc = dalloc(u, &u->vb_d, nbp)) || (rc = dalloc(u, &u->bb_d, nbp)) || (rc = dalloc(u, &u->scratch, nc)) ||
-      (rc = dalloc(u, &u->Qb, nbf)) || (rc = dalloc(u, &u->qbuf, nc * 3)) || (rc = dalloc(u, &u->bf_mirror_d, nbf)) || (rc = dalloc(u, &u->bf_axis_d, nbf)) || (rc = dalloc(u, &u->bf_spec_d, nbf)) ||
+      (rc = dalloc(u, &u->Qb, nbf)) || (rc = dalloc(u, &u->qbuf, nc * 3)) || (rc = dalloc(u, &u->bf_mirror_d, nbf)) || (rc = dalloc(u, &u->bf_axis_d, nbf)) || (rc = dalloc(u, &u->bf_spec_d, nbf)) || (rc = dalloc(u, &u->bscale, nc)) ||
       (rc = dalloc(u, &u->refl_d, 3 * nd)) || (rc = dalloc(u, &u->bface_d, nbf)) || (rc = dalloc(u, &u->owner_d, u->nf)) ||
       (rc = dalloc(u, &u->diff_d, nbf)) || (rc = dalloc(u, &u->fix, nc)) || (rc = dalloc(u, &u->fix_count, 4)) ||
       (rc = dalloc(u, &u->counters, 1)) || (rc = dalloc(u, &u->node_c, nbp * u->ng)) ||
@@ -694,7 +738,8 @@ int bte_umesh_create(const bte_umesh_desc* m, const bte_opts* opts, bte_umesh* o
   if (opts) o = *opts;
   if (o.precision != BTE_FP64 && o.precision != BTE_FP32 && o.precision != BTE_BF16)
     return ufail(nullptr, BTE_E_ARG, "unknown precision %d", o.precision);
-  if (o.learned || o.beta_T_exp != 0.0) return ufail(nullptr, BTE_E_ARG, "learned mode and beta_T_exp are not offered here");
+  if (o.learned) return ufail(nullptr, BTE_E_ARG, "learned mode is not offered here");
+  if (!(std::fabs(o.beta_T_exp) <= 16.0)) return ufail(nullptr, BTE_E_ARG, "beta_T_exp must lie in [-16, 16]");
   if (o.n_gauss < 1 || o.n_gauss > kMaxGauss) return ufail(nullptr, BTE_E_ARG, "n_gauss must be in [1, %d]", kMaxGauss);
   for (long long P = 0; P < m->ncells; ++P)
     if (!(std::isfinite(m->volume[P]) && m->volume[P] > 0)) return ufail(nullptr, BTE_E_ARG, "cell %lld: volume must be > 0", P);
@@ -893,6 +938,8 @@ int bte_umesh_step(bte_umesh u, double dt, int nsteps, int ninner, int scheme, b
   // third buffer: iteration 0 reads I^n and writes I^1 and B; iteration k reads
   // B and I^k and overwrites the buffer I^n (or I^{k-2}) was in
   const bool use_b = scheme != BTE_EXPLICIT && ninner >= 2;
+  const bool tt = u->opts.beta_T_exp != 0.0 && u->solve_tp;  // tau(T); with every beta_b = 0 there is no relaxation
+  a.bscale = tt ? u->bscale : nullptr;
   for (int st = 0; st < nsteps; ++st) {
     const int n = u->cur;
     int k = n, z = -1;
@@ -921,27 +968,16 @@ int bte_umesh_step(bte_umesh u, double dt, int nsteps, int ninner, int scheme, b
       a.Boutd = a.Bout;
       UTRY(u, cudaMemsetAsync(u->fix_count, 0, 4, s));
       UTRY(u, refresh_diffuse(u, a.Ik));
-      if (u->prec == BTE_FP64) {
-        if (scheme == BTE_EXPLICIT) umesh_sweep_kernel<true, 0><<<grid, threads, 0, s>>>(a);
-        else if (bm == 1) umesh_sweep_kernel<false, 1><<<grid, threads, 0, s>>>(a);
-        else if (bm == 2) umesh_sweep_kernel<false, 2><<<grid, threads, 0, s>>>(a);
-        else umesh_sweep_kernel<false, 0><<<grid, threads, 0, s>>>(a);
-      } else if (u->prec == BTE_FP32) {
-        if (scheme == BTE_EXPLICIT) umesh_sweep_dev_kernel<float, true, 0><<<grid, threads, 0, s>>>(a);
-        else if (bm == 1) umesh_sweep_dev_kernel<float, false, 1><<<grid, threads, 0, s>>>(a);
-        else if (bm == 2) umesh_sweep_dev_kernel<float, false, 2><<<grid, threads, 0, s>>>(a);
-        else umesh_sweep_dev_kernel<float, false, 0><<<grid, threads, 0, s>>>(a);
+      if (tt) {  // beta_b(T_p) of the current T_p, as the oracle takes it
+        UTRY(u, launch_beta_scale(u->bscale, u->Tp, u->opts.T_ref, u->opts.beta_T_exp, u->nc, s));
+        UTRY(u, launch_umesh_sweep<true>(u->prec, scheme == BTE_EXPLICIT, bm, a, grid, threads, s));
       } else {
-        if (scheme == BTE_EXPLICIT) umesh_sweep_dev_kernel<__nv_bfloat16, true, 0><<<grid, threads, 0, s>>>(a);
-        else if (bm == 1) umesh_sweep_dev_kernel<__nv_bfloat16, false, 1><<<grid, threads, 0, s>>>(a);
-        else if (bm == 2) umesh_sweep_dev_kernel<__nv_bfloat16, false, 2><<<grid, threads, 0, s>>>(a);
-        else umesh_sweep_dev_kernel<__nv_bfloat16, false, 0><<<grid, threads, 0, s>>>(a);
+        UTRY(u, launch_umesh_sweep<false>(u->prec, scheme == BTE_EXPLICIT, bm, a, grid, threads, s));
       }
-      UTRY(u, cudaGetLastError());
       SweepArgs c = cell_args(u, a.Iout);
       UTRY(u, launch_gs_reduce(u->prec, c, u->nc, s));
       if (u->solve_tp) UTRY(u, launch_fixup(c, nullptr, s));
-      launches += 2 + (u->solve_tp ? 1 : 0) + (u->ndiff ? 1 : 0);
+      launches += 2 + (u->solve_tp ? 1 : 0) + (u->ndiff ? 1 : 0) + (tt ? 1 : 0);
       k = o;
     }
     u->cur = k;

@@ -7,7 +7,8 @@ cell fluxes within 1e-10 of the largest and boundary-face heat flows within
 bands and all three wall kinds (implicit and explicit), a tetrahedral box,
 a mesh read from a Gmsh file, and a quad mesh checked against the
 structured handle on the same grid.  A 64x64x2-triangle mesh is checked at
-sampled outputs one by one."""
+sampled outputs one by one.  Temperature-dependent relaxation rates
+(beta_exp) are checked in FP64 (implicit and explicit) and FP32."""
 import numpy as np
 import pytest
 
@@ -146,6 +147,9 @@ def test_argument_and_order_errors():
         mt = M.UMesh(2, pts_turned.volume, pts_turned.owner, pts_turned.neighbor, pts_turned.nA @ R.T,
                      pts_turned.tag, pts_turned.centroid @ R.T, pts_turned.face_center @ R.T)
         bte.UMeshSolver(mt, dirs, bands, {0: (bte.BTE_BC_SPECULAR, None), 1: (0, 300.0), 2: (0, 300.0), 3: (0, 300.0)})
+    assert e.value.code == -1
+    with pytest.raises(bte.BTEError) as e:      # so does a partially specular tag
+        bte.UMeshSolver(mt, dirs, bands, {0: (bte.BTE_BC_PARTIAL, 0.5), 1: (0, 300.0), 2: (0, 300.0), 3: (0, 300.0)})
     assert e.value.code == -1
     with pytest.raises(bte.BTEError) as e:      # an unknown tag
         bte.UMeshSolver(m, dirs, bands, {7: (bte.BTE_BC_SPECULAR, None)})
@@ -293,3 +297,39 @@ def test_checkpoint_restore_continues_the_run(precision):
     assert np.max(np.abs(b.intensity() - a.intensity()) / a.intensity()) <= tol_I
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision,scheme,dt,nsteps,ninner", [
+    (bte.BTE_FP64, bte.BTE_IMPLICIT_JACOBI, 1e-12, 3, 5),
+    (bte.BTE_FP64, bte.BTE_EXPLICIT, 2e-13, 12, 1),
+    (bte.BTE_FP32, bte.BTE_IMPLICIT_JACOBI, 1e-12, 3, 5)])
+def test_temperature_dependent_relaxation_on_jittered_triangles(precision, scheme, dt, nsteps, ninner):
+    """beta_b(T_p) = beta_b (T_p / 300 K)^-1.2 per cell against the oracle: FP64
+    within rel 1e-12 on T and 1e-11 on I, FP32 within 1e-4 K."""
+    m = M.tri_grid(13, 9, 130e-9, 90e-9, jitter=0.3, seed=25)
+    dirs = W.Dirs("polar_azim", n_polar=20, n_azim=20)
+    bands = W.make_bands(40, 15, 19408)
+    bc = {0: (bte.BTE_BC_ISOTHERMAL, hot_wall(m, 0, 320.0, 10.0)), 1: (bte.BTE_BC_ISOTHERMAL, 300.0),
+          2: (bte.BTE_BC_SPECULAR, None), 3: (bte.BTE_BC_DIFFUSE, None)}
+    s = bte.UMeshSolver(m, dirs, bands, bc, precision=precision, beta_exp=-1.2)
+    rc, st = s.step(dt, nsteps, ninner, scheme)
+    assert rc >= 0 and st["nonfinite"] == 0
+    assert st["launches"] == nsteps * ninner * 5     # + the relaxation scale before every sweep
+    u = O.UMeshProblem(m, O.dirs_for(dirs), bands, bc, beta_exp=-1.2, beta_Tref=300.0)
+    ost = u.init_state(m.T_init)
+    u.run(ost, dt, nsteps, ninner, O.EXPLICIT if scheme == bte.BTE_EXPLICIT else O.IMPLICIT)
+    assert np.max(ost["TL"]) > 300.5                   # the hot wall moved the cells' rates
+    if precision == bte.BTE_FP64:
+        assert_matches(s, u, ost)
+    else:
+        assert np.max(np.abs(s.T(bte.BTE_T_LATTICE) - ost["TL"])) <= 1e-4
+        assert np.max(np.abs(s.T(bte.BTE_T_PSEUDO) - ost["Tp"])) <= 1e-4
+    s.close()
+
+
+def test_relaxation_exponent_out_of_range_is_refused():
+    m = M.tri_grid(3, 2, 30e-9, 20e-9)
+    with pytest.raises(bte.BTEError) as e:
+        bte.UMeshSolver(m, W.Dirs("inplane", n_inplane=8), W.make_bands(2, 0, 3),
+                        {t: (bte.BTE_BC_SPECULAR, None) for t in range(4)}, beta_exp=20.0)
+    assert e.value.code == -1
