@@ -514,6 +514,12 @@ class UMeshSolver:
         return q, Q
 
     def close(self):
-        if self.h:
+        if getattr(self, "h", None):
             lib().bte_umesh_destroy(self.h)
             self.h = None
+
+    def __del__(self):  # also frees the handle when the constructor failed after bte_umesh_create
+        try:
+            self.close()
+        except Exception:
+            pass
