@@ -11,6 +11,15 @@ Arms:
   --impl reference   the plain FP64 CPU oracle on this machine's host cores, on a
                      bounded sub-grid sample of the same workload.
 
+Beside the metric the JSON line carries: the roofline of the dominant sweep
+kernel (FP64 pipe, with its HBM figures and the ncu DRAM traffic of the
+committed record), the end-to-end rate through the C ABI with host buffers,
+SM clocks sampled during the timed region, the launch count, the oracle's own
+rate on the host cores (all cores on the full grid, and one thread on a 32x32
+sub-grid), "accuracy" (max |dT_L| of the first, untimed step against the FP64
+oracle's run of the same step on the full grid) and the reduced-precision,
+batched, paper-device, sweep-ordered and unstructured variants.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 launch with torch.distributed.run; every rank runs one replica of the
 workload on its own GPU (the path has no exchange step between replicas).
