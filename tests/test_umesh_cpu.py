@@ -128,21 +128,22 @@ def test_quad_mesh_reproduces_the_structured_oracle(scheme, dt, nsteps, ninner, 
     assert np.max(np.abs(su["I"] - st["I"]) / st["I"]) < 1e-13
 
 
-def test_quad_mesh_with_temperature_dependent_tau_reproduces_the_structured_oracle():
+@pytest.mark.parametrize("scheme,dt,nsteps,ninner", [(O.IMPLICIT, 1e-12, 3, 5), (O.EXPLICIT, 2e-13, 15, 1)])
+def test_quad_mesh_with_temperature_dependent_tau_reproduces_the_structured_oracle(scheme, dt, nsteps, ninner):
     g, m, bc = _mixed_rectangle(6, 5, 10e-9, ((W.BC_PARTIAL, 0.4), (W.BC_DIFFUSE, None)))
     dirs, bands = O.dirs_inplane(16), W.make_bands(6, 2, 5)
     T0 = W.random_temperatures(30, 4, 290.0, 330.0)
     p = O.Problem(g, dirs, bands, beta_exp=-1.5, beta_Tref=300.0)
     st = p.init_state(T0)
-    p.run(st, 1e-12, 3, 5)
+    p.run(st, dt, nsteps, ninner, scheme)
     u = O.UMeshProblem(m, dirs, bands, bc, beta_exp=-1.5, beta_Tref=300.0)
     su = u.init_state(T0)
-    u.run(su, 1e-12, 3, 5)
+    u.run(su, dt, nsteps, ninner, scheme)
     assert np.max(np.abs(su["TL"] - st["TL"]) / st["TL"]) < 1e-14
     assert np.max(np.abs(su["I"] - st["I"]) / st["I"]) < 1e-13
     fixed = O.UMeshProblem(m, dirs, bands, bc)   # and tau(T) does change the answer
     sf = fixed.init_state(T0)
-    fixed.run(sf, 1e-12, 3, 5)
+    fixed.run(sf, dt, nsteps, ninner, scheme)
     assert np.max(np.abs(sf["TL"] - su["TL"])) > 1e-6
 
 
