@@ -126,3 +126,26 @@ def test_explicit_single_cell_with_specular_walls_is_exactly_steady():
     assert np.max(np.abs(s.intensity(0) - I_start) / I_start) <= 1e-14
     assert np.max(np.abs(s.T(0, bte.BTE_T_LATTICE) - 300.0)) <= 1e-12 * 300
     s.close()
+
+
+def test_exact_fixup_with_32_gauss_nodes_and_110_bands():
+    """The exact solve of the fix-up takes the band quadrature in chunks of at
+    most 1024 (band, node) pairs: 110 bands x 32 nodes is four chunks.  A
+    cold start far from equilibrium sends cells to the fix-up; T and I match
+    the oracle with the same quadrature within the FP64 bar."""
+    g = W.Geometry(2, 7, 5, 1, 10e-9, 10e-9, 10e-9)
+    W.uniform_walls(g, [W.BC_ISOTHERMAL, W.BC_ISOTHERMAL, W.BC_SPECULAR, W.BC_DIFFUSE], [340.0, 290.0, 0.0, 0.0])
+    wl = W.Workload("32 nodes", [g], W.Dirs("inplane", n_inplane=12), W.make_bands(80, 30, 44), 2e-12, 3, 4)
+    assert wl.bands.nb == 110
+    T0 = W.random_temperatures(g.ncells, 45, 280.0, 340.0)
+    s = bte.Solver(wl, n_gauss=32, T_init=[T0])
+    rc, st = s.step(nsteps=3, ninner=4)
+    assert rc >= 0 and st["nonfinite"] == 0
+    assert st["solve_evals"] > 0                 # the fix-up ran
+    p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands, ngauss=32)
+    ost = p.init_state(T0)
+    p.run(ost, wl.dt, 3, 4)
+    for which, key in ((bte.BTE_T_LATTICE, "TL"), (bte.BTE_T_PSEUDO, "Tp")):
+        assert np.max(np.abs(s.T(0, which) - ost[key]) / ost[key]) <= 1e-12, key
+    assert np.max(np.abs(s.intensity(0) - ost["I"]) / np.abs(ost["I"])) <= 1e-11
+    s.close()
