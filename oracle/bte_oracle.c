@@ -25,7 +25,13 @@
  * exactness and an independent adaptive integral, direction-set moments,
  * Newton against bracketing, Jacobi against a dense LU solve, hand-computed
  * steps, equilibrium, energy conservation, Casimir and Fourier limits,
- * relabelling symmetry).
+ * relabelling symmetry).  The extensions beyond the paper's scheme are pinned
+ * the same way: the sweep-ordered pass (dense LU, one-pass exactness with
+ * fixed ghosts), diffuse and partially specular walls (zero net wall flux,
+ * conservation, the p = 1 / p = 0 limits bit for bit), temperature-dependent
+ * relaxation, and the unstructured update (the structured result on a quad
+ * mesh for every wall kind and for tau(T), dense LU, equilibrium,
+ * conservation, a quarter turn of the mesh).
  */
 #include <math.h>
 #include <stdlib.h>
