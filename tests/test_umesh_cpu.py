@@ -241,6 +241,21 @@ def test_partial_walls_at_p_one_and_zero_are_the_mirror_and_the_diffuse_wall_bit
         assert np.array_equal(res[0], res[1]), p
 
 
+def test_per_face_specularity_equal_on_every_face_is_the_uniform_wall():
+    m = M.tri_grid(5, 4, 50e-9, 40e-9, jitter=0.3, seed=9)
+    bands, dirs = W.make_bands(4, 1, 15), O.dirs_inplane(12)
+    T0 = W.random_temperatures(m.ncells, 16, 296.0, 306.0)
+    p_faces = np.full(m.nfaces, 0.35)
+    res = []
+    for p in (0.35, p_faces):
+        u = O.UMeshProblem(m, dirs, bands, {0: (O.ISOTHERMAL, 308.0), 1: (O.ISOTHERMAL, 300.0),
+                                            2: (O.PARTIAL, p), 3: (O.SPECULAR, None)})
+        st = u.init_state(T0)
+        u.run(st, 1e-12, 2, 3)
+        res.append(st["I"])
+    assert np.array_equal(res[0], res[1])
+
+
 def test_rotating_the_mesh_by_a_quarter_turn_relabels_the_solution():
     """The in-plane set with n % 4 == 0 is invariant under a 90-degree turn, so
     turning the mesh (and its walls) leaves every cell's temperature unchanged."""
