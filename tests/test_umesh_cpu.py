@@ -227,6 +227,25 @@ def test_closed_triangle_enclosure_conserves_energy(kind):
     assert np.max(np.abs(Q)) <= 1e-12 * scale * np.max(np.linalg.norm(m.nA, axis=1))  # no net flow through the walls
 
 
+def test_closed_tetrahedral_box_conserves_energy_with_diffuse_and_partial_walls():
+    m = M.tet_box(3, 2, 2, 30e-9, 20e-9, 20e-9)
+    bands = W.make_bands(3, 1, 17)
+    walls = {0: (O.DIFFUSE, None), 1: (O.PARTIAL, 0.3), 2: (O.SPECULAR, None), 3: (O.PARTIAL, 0.8),
+             4: (O.DIFFUSE, None), 5: (O.SPECULAR, None)}
+    u = O.UMeshProblem(m, O.dirs_for(W.Dirs("polar_azim", n_polar=4, n_azim=8)), bands, walls)
+    st = u.init_state(W.random_temperatures(m.ncells, 18, 290.0, 310.0))
+
+    def total(I):
+        return sum(m.volume[P] * u.cell_energy(I[P])[0] for P in range(m.ncells))
+    E0 = total(st["I"])
+    T0 = st["TL"].copy()
+    u.run(st, 1e-13, 30, 1, O.EXPLICIT)
+    assert abs(total(st["I"]) - E0) <= 1e-13 * E0
+    assert np.max(np.abs(st["TL"] - T0)) > 0.1          # the field did evolve
+    q, Q = u.flux(st["I"])
+    assert np.max(np.abs(Q)) <= 1e-12 * np.max(np.abs(q)) * np.max(np.linalg.norm(m.nA, axis=1))
+
+
 def test_partial_walls_at_p_one_and_zero_are_the_mirror_and_the_diffuse_wall_bit_for_bit():
     m = M.tri_grid(5, 4, 50e-9, 40e-9, jitter=0.3, seed=8)
     bands, dirs = W.make_bands(4, 1, 14), O.dirs_inplane(12)
