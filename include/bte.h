@@ -118,7 +118,9 @@ typedef struct {
   double gpu_ms;              /* device time between the first and last launch */
 } bte_stats;
 
-/* Fills *opts with the defaults listed above.  Returns BTE_E_ARG on NULL. */
+/* Fills *opts with the defaults listed above (the discretisation choices of
+ * Sec. 3.1: direction set, band quadrature, precision).  Returns BTE_E_ARG on
+ * NULL. */
 int bte_default_opts(bte_opts* opts);
 
 /* Creates a solver for n_geom >= 1 independent geometries sharing one
@@ -169,7 +171,11 @@ int bte_set_exchange(bte_handle h, bte_allreduce_fn fn, void* user, double* dev_
 
 /* Device bytes the solver needs (valid after bte_set_bands), and binding of a
  * caller-owned device buffer of at least that size (e.g. a torch.empty
- * uint8 tensor).  The buffer must stay alive until bte_destroy; the library
+ * uint8 tensor).  The buffer holds the discretised state of Sec. 3.1-3.2:
+ * the intensity I_{d,b} of every cell (the unknown of Eq. 4-5, three
+ * buffers for I^n, the iterate and the next iterate), the per-cell mutable
+ * variables I0_b and T of Sec. 3.2, the wall ghosts of Eq. 6 and the
+ * coefficient tables of Eq. 5's volume and surface terms.  The buffer must stay alive until bte_destroy; the library
  * never frees it.  Without a bound buffer the library cudaMallocs its own at
  * the first call that needs device memory and frees it in bte_destroy.
  * bte_bind_workspace returns BTE_E_NOMEM if bytes is too small, BTE_E_STATE
@@ -231,30 +237,41 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
  * receives a CSV table of the candidates. */
 int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t report_len);
 
-/* Cell temperatures of one geometry: BTE_T_PSEUDO (T_p, the temperature whose
- * equilibrium the relaxation term drives toward) or BTE_T_LATTICE (T_L, the
- * energy-equivalent temperature).  out: ncells doubles, host or device
+/* Cell temperatures of one geometry (Sec. 3.1: temperature is derived from
+ * the intensity summed over all directions and bands; Sec. 2.2 and 3.2: the
+ * per-cell temperature update after each step, which sets I0_b and tau_b):
+ * BTE_T_PSEUDO (T_p, the temperature whose equilibrium I0_b(T_p) the
+ * relaxation term of Eq. 4 drives toward: sum_b W beta_b I0_b(T_p)/v_b =
+ * sum_b beta_b G_b/v_b) or BTE_T_LATTICE (T_L, the energy-equivalent
+ * temperature: sum_b W I0_b(T_L)/v_b = sum_b G_b/v_b), G_b = sum_d w_d I_{d,b}.  out: ncells doubles, host or device
  * (out_on_device != 0).  Waits for the stream. */
 int bte_get_T(bte_handle h, int geom, int which, double* out, int out_on_device);
 
-/* Heat flux of one geometry.  q_cells: ncells*dim doubles, q(P) = sum_b sum_d
+/* Heat flux of one geometry: the energy flux carried by the intensity, i.e.
+ * the surface term of Eq. 5 (|v_g|_b times the integral of I_{d,b} s_d . n
+ * over the cell boundary, summed over d and b) evaluated per cell and per
+ * wall.  q_cells: ncells*dim doubles, q(P) = sum_b sum_d
  * S_d I[P][d][b] (W/m^2), or NULL.  q_walls: 2*dim doubles, per side the mean
  * over its faces of sum_b sum_d (S_d . n_out) I_face (upwind face value,
  * ghost for incoming directions; positive = leaving), or NULL.  Host or
  * device per out_on_device.  Waits for the stream. */
 int bte_get_flux(bte_handle h, int geom, double* q_cells, double* q_walls, int out_on_device);
 
-/* Copies the intensity of one geometry out as FP64 [cell][dir][band]
+/* Copies the intensity I_{d,b} of one geometry (the unknown of Eq. 4-5,
+ * indexed as in Sec. 3.1) out as FP64 [cell][dir][band]
  * (ncells*nd*nb doubles, unpadded), host or device. */
 int bte_get_intensity(bte_handle h, int geom, double* out, int out_on_device);
 
 /* Replaces the intensity of one geometry with `in` (FP64 [cell][dir][band],
  * host or device per in_on_device) and sets T_p to Tp_cells (host/device,
- * ncells) -- a checkpoint restore.  I0 is recomputed from T_p. */
+ * ncells) -- a checkpoint restore, i.e. an arbitrary initial condition in
+ * place of the equilibrium one of Sec. 3.2.  I0 is recomputed from T_p (the
+ * per-cell variable of Sec. 3.2 that depends on temperature). */
 int bte_set_intensity(bte_handle h, int geom, const double* in, const double* Tp_cells, int in_on_device);
 
-/* Direction table the solver uses: S (nd*3, control-angle integrals of the
- * unit vector), w (nd, solid angles), refl (3*nd, mirror direction across an
+/* Direction table the solver uses (the discrete direction vectors s_d of
+ * Sec. 3.1 and the reflection index r of Eq. 6): S (nd*3, control-angle
+ * integrals of the unit vector), w (nd, solid angles), refl (3*nd, mirror direction across an
  * x, y, z wall).  Host arrays; any may be NULL.  Returns nd (>0) or an error. */
 int bte_get_directions(bte_handle h, double* S, double* w, int* refl);
 
@@ -308,11 +325,13 @@ int bte_mlp_grad(bte_handle h, int net, const float* x, const float* y, int n, f
  * [1, 5000] K) and evals[i] (exact quadrature evaluations; may be NULL). */
 int bte_solve_T(bte_handle h, const double* Ep, const double* T0, int n, int learned, double* T_out, int* evals);
 
-/* Frees everything the library allocated (not a bound workspace). */
+/* Frees everything the library allocated (not a bound workspace).  The
+ * paper has no counterpart (resource release of this library's handle). */
 int bte_destroy(bte_handle h);
 
 /* Last error message of the handle ("" if none); h may be NULL for errors
- * from bte_init_mesh.  The string lives until the next call on the handle. */
+ * from bte_init_mesh.  The paper has no counterpart (error reporting of this
+ * library).  The string lives until the next call on the handle. */
 const char* bte_last_error(bte_handle h);
 
 #ifdef __cplusplus

@@ -71,7 +71,7 @@ typedef struct {
  * bte_umesh_last_error(NULL)). */
 int bte_umesh_create(const bte_umesh_desc* mesh, const bte_opts* opts, bte_umesh* out);
 
-/* Band table, as bte_set_bands. */
+/* Band table, as bte_set_bands (Sec. 3.1: 40 bands -> 55 band-polarisations). */
 int bte_umesh_set_bands(bte_umesh u, int nb, const double* omega_lo, const double* omega_hi, const double* vg,
                         const double* beta, const double* degeneracy);
 
@@ -88,21 +88,24 @@ int bte_umesh_set_bands(bte_umesh u, int nb, const double* omega_lo, const doubl
  * tag's condition for the following steps. */
 int bte_umesh_set_bc(bte_umesh u, int tag, int type, const double* T_faces, double T_uniform);
 
-/* Equilibrium initial state at T_cells (host [ncells], or NULL for T_uniform). */
+/* Equilibrium initial state at T_cells (host [ncells], or NULL for T_uniform):
+ * I_{d,b} = I0_b(T_P) for every direction, the initial condition of Sec. 3.2. */
 int bte_umesh_set_initial(bte_umesh u, const double* T_cells, double T_uniform);
 
-/* nsteps time steps of dt [s]; scheme BTE_IMPLICIT_JACOBI (ninner inner
+/* nsteps time steps of dt [s] of the face-sum update of Eq. 5 (with Eq. 6
+ * ghosts on tagged faces); scheme BTE_IMPLICIT_JACOBI (ninner inner
  * iterations) or BTE_EXPLICIT (ninner ignored).  Each inner iteration is a
  * sweep kernel, the per-cell step and the fix-up (plus one kernel for the
  * diffuse and partially specular faces, and one for the per-cell relaxation
  * scale when beta_T_exp != 0).  stats: as bte_step, may be NULL. */
 int bte_umesh_step(bte_umesh u, double dt, int nsteps, int ninner, int scheme, bte_stats* stats);
 
-/* Cell temperatures (BTE_T_PSEUDO or BTE_T_LATTICE) into out: ncells doubles,
+/* Cell temperatures (BTE_T_PSEUDO or BTE_T_LATTICE, defined as in bte_get_T:
+ * the temperature update of Sec. 2.2 and 3.2) into out: ncells doubles,
  * host (on_device = 0) or device memory (1). */
 int bte_umesh_get_T(bte_umesh u, int which, double* out, int on_device);
 
-/* Intensities into host out[ncells][nd][nb]. */
+/* Intensities I_{d,b} (the unknown of Eq. 4-5) into host out[ncells][nd][nb]. */
 int bte_umesh_get_intensity(bte_umesh u, double* out);
 
 /* Checkpoint restore: replaces the intensities with host in[ncells][nd][nb]
@@ -111,12 +114,15 @@ int bte_umesh_get_intensity(bte_umesh u, double* out);
  * T_p and E_L from the intensities.  Needs bte_umesh_set_initial first. */
 int bte_umesh_set_intensity(bte_umesh u, const double* in, const double* Tp_cells);
 
-/* Heat flux: q (host [ncells][3], may be NULL) = sum_b sum_d S_d I_{d,b} per
+/* Heat flux, the surface term of Eq. 5 summed over directions and bands:
+ * q (host [ncells][3], may be NULL) = sum_b sum_d S_d I_{d,b} per
  * cell; Q (host [nfaces], may be NULL) = the net heat flow out through each
  * boundary face, sum_b sum_d (S_d . n_f A_f) I_face (own value leaving,
  * ghost entering), 0 on interior faces. */
 int bte_umesh_get_flux(bte_umesh u, double* q, double* Q);
 
+/* Last error message and release of the handle; the paper has no
+ * counterpart (error reporting and resource release of this library). */
 const char* bte_umesh_last_error(bte_umesh u);
 void bte_umesh_destroy(bte_umesh u);
 
