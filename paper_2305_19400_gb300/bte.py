@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(PKG, "libbte.so")
 BTE_OK, BTE_W_FALLBACK = 0, 1
 BTE_E = {-1: "BTE_E_ARG", -2: "BTE_E_STATE", -3: "BTE_E_CUDA", -4: "BTE_E_NOMEM", -5: "BTE_E_NONFINITE",
          -6: "BTE_E_TIMEOUT", -7: "BTE_E_EXCHANGE"}
+(BTE_E_ARG, BTE_E_STATE, BTE_E_CUDA, BTE_E_NOMEM, BTE_E_NONFINITE, BTE_E_TIMEOUT,
+ BTE_E_EXCHANGE) = -1, -2, -3, -4, -5, -6, -7
 BTE_DIRS_INPLANE, BTE_DIRS_POLAR_AZIM = 0, 1
 BTE_FP64, BTE_FP32, BTE_BF16 = 0, 1, 2
 BTE_BC_ISOTHERMAL, BTE_BC_SPECULAR, BTE_BC_DIFFUSE, BTE_BC_PARTIAL = 0, 1, 2, 3

@@ -693,8 +693,11 @@ int flux_view(bte_ctx* h, int geom, FluxView* out) {
   out->dim = g.dim;
   for (int s6 = 0; s6 < 6; ++s6) out->nfaces[s6] = s6 < 2 * g.dim ? (int)side_faces(g, s6) : 0;
   out->stream = h->stream;
+  out->dev = h->dev;
   return BTE_OK;
 }
+
+int handle_device(bte_ctx* h) { return h->dev; }
 
 int set_handle_error(bte_ctx* h, int code, const char* fmt, ...) {
   char buf[512];

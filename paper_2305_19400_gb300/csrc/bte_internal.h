@@ -219,8 +219,10 @@ struct FluxView {
   int nd, nbp, dim;
   int nfaces[6];          // faces per side (0 for sides beyond 2*dim)
   cudaStream_t stream;
+  int dev;                // device that holds the handle's memory and stream
 };
 int flux_view(bte_ctx* h, int geom, FluxView* out);
+int handle_device(bte_ctx* h);  // device that was current at bte_init_mesh
 int set_handle_error(bte_ctx* h, int code, const char* fmt, ...);
 
 }  // namespace bte

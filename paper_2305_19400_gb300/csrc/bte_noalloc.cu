@@ -30,11 +30,10 @@ static __device__ __align__(256) double g_wall_scratch[kNoAllocMaxFaces + 8];
 std::mutex g_setup_mu;
 double* g_scratch_addr[kNoAllocMaxDevices] = {nullptr};
 
-// Device address of g_wall_scratch on the current device (set up on first use).
-cudaError_t scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Device address of g_wall_scratch on device `dev`, which must be current
+// (set up on first use).
+cudaError_t scratch_address(int dev, double** out) {
+  cudaError_t e = cudaSuccess;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_setup_mu);
   if (!g_scratch_addr[dev]) {
@@ -108,22 +107,47 @@ __global__ void wall_mean_static_kernel(double* scratch, int n, int side) {
 }  // namespace
 }  // namespace bte
 
+namespace bte {
+namespace {
+int wall_flux_on_device(bte_handle h, const FluxView& v, int geom, double* q_walls, int out_on_device);
+}  // namespace
+}  // namespace bte
+
 using namespace bte;
 
 extern "C" int bte_get_wall_flux_noalloc(bte_handle h, int geom, double* q_walls, int out_on_device) {
   if (!h) return BTE_E_ARG;
+  if (!q_walls) return set_handle_error(h, BTE_E_ARG, "q_walls is NULL");
+  // The handle's memory and stream, and the scratch address used here, belong
+  // to the handle's device: make it current for the wall-ghost refresh, the
+  // address lookup and the launches, and give the caller's device back.
+  const int dev = handle_device(h);
+  int prev = 0;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e == cudaSuccess && prev != dev) e = cudaSetDevice(dev);
+  if (e != cudaSuccess) return set_handle_error(h, BTE_E_CUDA, "cudaSetDevice(%d): %s", dev, cudaGetErrorString(e));
   FluxView v;
   int rc = flux_view(h, geom, &v);
-  if (rc) return rc;
-  if (!q_walls) return set_handle_error(h, BTE_E_ARG, "q_walls is NULL");
-  if (v.precision != BTE_FP64)
-    return set_handle_error(h, BTE_E_ARG, "the no-allocation wall flux serves FP64 handles only");
-  for (int side = 0; side < 2 * v.dim; ++side)
-    if (v.nfaces[side] > kNoAllocMaxFaces)
-      return set_handle_error(h, BTE_E_ARG, "wall %d has %d faces; the no-allocation path holds at most %d per wall",
-                              side, v.nfaces[side], kNoAllocMaxFaces);
+  if (rc == BTE_OK) {
+    if (v.precision != BTE_FP64) {
+      rc = set_handle_error(h, BTE_E_ARG, "the no-allocation wall flux serves FP64 handles only");
+    } else {
+      for (int side = 0; side < 2 * v.dim && rc == BTE_OK; ++side)
+        if (v.nfaces[side] > kNoAllocMaxFaces)
+          rc = set_handle_error(h, BTE_E_ARG, "wall %d has %d faces; the no-allocation path holds at most %d per wall",
+                                side, v.nfaces[side], kNoAllocMaxFaces);
+      if (rc == BTE_OK) rc = wall_flux_on_device(h, v, geom, q_walls, out_on_device);
+    }
+  }
+  if (prev != dev) cudaSetDevice(prev);
+  return rc;
+}
+
+namespace bte {
+namespace {
+int wall_flux_on_device(bte_handle h, const FluxView& v, int geom, double* q_walls, int out_on_device) {
   double* scratch = nullptr;
-  cudaError_t e = scratch_address(&scratch);
+  cudaError_t e = scratch_address(v.dev, &scratch);
   if (e != cudaSuccess) return set_handle_error(h, BTE_E_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
   for (int side = 0; side < 2 * v.dim; ++side) {
     const int nf = v.nfaces[side];
@@ -140,3 +164,5 @@ extern "C" int bte_get_wall_flux_noalloc(bte_handle h, int geom, double* q_walls
   if (e != cudaSuccess) return set_handle_error(h, BTE_E_CUDA, "wall flux: %s", cudaGetErrorString(e));
   return BTE_OK;
 }
+}  // namespace
+}  // namespace bte

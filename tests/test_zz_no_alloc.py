@@ -5,9 +5,12 @@ bte_get_wall_flux_noalloc exists for callers that cannot call cudaMalloc
 latency-critical loop where an allocation would synchronize the device).  It
 keeps its per-face scratch in a static device array inside libbte.so.  This
 test checks, through the C ABI, that two calls in a row return the same
-per-side wall fluxes as bte_get_flux, within the tolerance the flux parity
-tests use, for host and device outputs.  It lives in its own file, collected
-last, and passes both alone in a fresh process and after the other tests.
+per-side wall fluxes as bte_get_flux, for host and device outputs, on every
+wall kind (isothermal, mirror, diffuse, partially specular) and on the z
+walls of a 3-D geometry.  Both paths add each face's terms in the same order
+and reduce them with the same 256-thread tree, so the results must agree bit
+for bit.  It lives in its own file, collected last, and passes both alone in
+a fresh process and after the other tests.
 """
 import numpy as np
 import pytest
@@ -26,11 +29,17 @@ def _built():
     B.build()
 
 
-def _flux_scale(s, geom):
-    """Largest per-cell absolute flux sum, the scale the flux tolerance is relative to."""
-    S, _, _ = bte.bte_get_directions(s.h)
-    I = s.intensity(geom)
-    return float(np.einsum("da,cdb->ca", np.abs(S), np.abs(I)).max())
+def _check_twice(s, gi, dim):
+    """Two calls in a row, host and device outputs, each equal to bte_get_flux bit for bit."""
+    _, qw_ref = s.flux(gi)
+    for _ in range(2):
+        qw = np.zeros(dim * 2)
+        bte.bte_get_wall_flux_noalloc(s.h, gi, qw)
+        assert np.array_equal(qw, qw_ref), (qw, qw_ref)
+        qd = torch.zeros(2 * dim, dtype=torch.float64, device="cuda")
+        bte.bte_get_wall_flux_noalloc(s.h, gi, qd)
+        assert np.array_equal(qd.cpu().numpy(), qw_ref)
+    return qw_ref
 
 
 @pytest.mark.parametrize("make", [lambda: W.cfg2(21, 13), lambda: W.cfg1()])
@@ -38,18 +47,40 @@ def test_noalloc_wall_flux_matches_bte_get_flux_twice(make):
     wl = make()
     s = bte.Solver(wl)
     s.step(nsteps=2, ninner=5)
-    g = wl.geoms[0]
-    _, qw_ref = s.flux(0)
-    tol = 1e-11 * _flux_scale(s, 0)
-    for _ in range(2):
-        qw = np.zeros(2 * g.dim)
-        bte.bte_get_wall_flux_noalloc(s.h, 0, qw)
-        assert np.all(np.abs(qw - qw_ref) <= tol), (qw, qw_ref)
-        qd = torch.zeros(2 * g.dim, dtype=torch.float64, device="cuda")
-        bte.bte_get_wall_flux_noalloc(s.h, 0, qd)
-        assert np.all(np.abs(qd.cpu().numpy() - qw_ref) <= tol)
+    qw_ref = _check_twice(s, 0, wl.geoms[0].dim)
     # the hot wall takes energy in (the cold wall is too far for the heat to arrive yet)
     assert qw_ref[0] < 0
+    s.close()
+
+
+def test_noalloc_wall_flux_on_diffuse_and_partially_specular_walls():
+    """-y diffuse (ghost rows refreshed from the current state first), +y
+    partially specular (per-direction ghost rows), x walls isothermal."""
+    g = W.Geometry(2, 11, 7, 1, 10e-9, 10e-9, 10e-9)
+    W.uniform_walls(g, [W.BC_ISOTHERMAL, W.BC_ISOTHERMAL, W.BC_DIFFUSE, W.BC_PARTIAL], [312.0, 300.0, 0, 0.35])
+    wl = W.Workload("diffuse+partial", [g], W.Dirs("polar_azim", n_polar=4, n_azim=8), W.make_bands(8, 3, 61),
+                    1e-12, 3, 4)
+    s = bte.Solver(wl)
+    s.step()
+    qw = _check_twice(s, 0, 2)
+    assert qw[0] < 0 and np.all(np.isfinite(qw))
+    s.step()
+    _check_twice(s, 0, 2)
+    s.close()
+
+
+def test_noalloc_wall_flux_on_the_z_walls_of_a_3d_geometry():
+    """5 x 4 x 3 cells; z walls isothermal (hot, cold) and the others mixed, so
+    every side index 0..5 is served."""
+    g = W.Geometry(3, 5, 4, 3, 10e-9, 10e-9, 10e-9)
+    W.uniform_walls(g, [W.BC_SPECULAR, W.BC_DIFFUSE, W.BC_PARTIAL, W.BC_SPECULAR, W.BC_ISOTHERMAL, W.BC_ISOTHERMAL],
+                    [0, 0, 0.6, 0, 309.0, 301.0])
+    wl = W.Workload("3d z walls", [g], W.Dirs("polar_azim", n_polar=4, n_azim=8), W.make_bands(6, 2, 62),
+                    1e-12, 2, 5)
+    s = bte.Solver(wl)
+    s.step()
+    qw = _check_twice(s, 0, 3)
+    assert qw[4] < 0 and np.all(np.isfinite(qw))   # the hot -z wall takes energy in
     s.close()
 
 
@@ -67,7 +98,7 @@ def test_noalloc_wall_flux_on_several_geometries_and_after_more_steps():
             _, qw_ref = s.flux(gi)
             qw = np.zeros(4)
             bte.bte_get_wall_flux_noalloc(s.h, gi, qw)
-            assert np.all(np.abs(qw - qw_ref) <= 1e-11 * _flux_scale(s, gi))
+            assert np.array_equal(qw, qw_ref)
     s.close()
 
 
