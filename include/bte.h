@@ -90,7 +90,16 @@ typedef struct {
  *             (T_p / T_ref)^beta_T_exp per cell, T_p the cell's current
  *             pseudo-temperature, beta_b the table value (at T_ref).  0
  *             (default) keeps tau fixed; |beta_T_exp| <= 16.  The factor is
- *             common to all bands, so the T_p equation keeps its root. */
+ *             common to all bands, so the T_p equation keeps its root.
+ *  fp64_strict BTE_FP64 only.  0 (default): the implicit point-Jacobi sweep
+ *             of a handle with fixed relaxation rates and isothermal or mirror
+ *             walls keeps its inner iterates in double-float form (two floats,
+ *             48-bit significand) and computes the update on the FP32 pipe
+ *             with error-free transformations; storage between time steps,
+ *             the reduction, the temperature solve and I0 stay IEEE FP64.  The
+ *             update then rounds to about 2^-48 relative instead of 2^-53,
+ *             for |I| in [2^-74, 2^127) (smaller values keep a float's 24
+ *             bits).  1: every update in IEEE FP64 arithmetic (DFMA). */
 typedef struct {
   int dir_kind;
   int n_inplane, n_polar, n_azim;
@@ -104,6 +113,7 @@ typedef struct {
   int use_graph;
   int autotune;
   double beta_T_exp;
+  int fp64_strict;
 } bte_opts;
 
 /* Per-call statistics of bte_step (filled only when a non-NULL pointer is
@@ -324,6 +334,33 @@ int bte_mlp_grad(bte_handle h, int net, const float* x, const float* y, int n, f
  * tolerance, bisection fallback.  T_out[i] (NaN when no root lies in
  * [1, 5000] K) and evals[i] (exact quadrature evaluations; may be NULL). */
 int bte_solve_T(bte_handle h, const double* Ep, const double* T0, int n, int learned, double* T_out, int* evals);
+
+/* Per-launch device time of the sweeps (the paper has no counterpart; it
+ * serves the roofline of the sweep kernel).  bte_set_sweep_timing(h, 1) makes
+ * every later bte_step record a CUDA event before and after each inner
+ * iteration's sweep launch (for BTE_IMPLICIT_GS: the pass and its per-cell
+ * step) on the solver's stream; with use_graph the events are recorded by
+ * nodes of the step's graph.  Switching it drops the handle's graphs.
+ * bte_sweep_times waits for the last event and writes the durations (ms) of
+ * the sweeps of the most recent time step, in inner-iteration order, to
+ * ms[0 .. n); it returns how many sweeps that step had (ms may be NULL when
+ * n = 0), or BTE_E_STATE when no step ran since timing was switched on. */
+int bte_set_sweep_timing(bte_handle h, int on);
+int bte_sweep_times(bte_handle h, float* ms, int n);
+
+/* Measured arithmetic peak of the current device (the roofline denominators of
+ * the sweeps; the paper has no counterpart).  kind BTE_PEAK_FP64_FMA: FP64
+ * fused multiply-adds (the FP64 sweep's pipe); BTE_PEAK_FP32X2_FMA: packed
+ * two-float FMAs (the pipe of the double-float sweep and the reduced modes).
+ * Loop kernels of independent FMA chains on 8 CTAs of 256 threads per SM,
+ * about 30 ms each, timed with CUDA events on a stream of their own; the best
+ * of three timed launches after one warm-up.  *flops receives flop/s (2 per
+ * FMA), *ms (may be NULL) that launch's time.  The figure scales with the SM
+ * clock of the moment; the caller samples it.  Allocates no memory on the
+ * device; runs on the current device and waits for its own stream.  Returns
+ * BTE_E_ARG for an unknown kind or NULL flops, BTE_E_CUDA on a CUDA error. */
+enum { BTE_PEAK_FP64_FMA = 0, BTE_PEAK_FP32X2_FMA = 1 };
+int bte_measure_peak(int kind, double* flops, double* ms);
 
 /* Frees everything the library allocated (not a bound workspace).  The
  * paper has no counterpart (resource release of this library's handle). */

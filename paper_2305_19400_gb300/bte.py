@@ -36,7 +36,8 @@ class bte_opts(C.Structure):
     _fields_ = [("dir_kind", C.c_int), ("n_inplane", C.c_int), ("n_polar", C.c_int), ("n_azim", C.c_int),
                 ("precision", C.c_int), ("learned", C.c_int), ("n_gauss", C.c_int), ("newton_rtol", C.c_double),
                 ("newton_maxit", C.c_int), ("cuda_stream", C.c_void_p), ("T_ref", C.c_double),
-                ("use_graph", C.c_int), ("autotune", C.c_int), ("beta_T_exp", C.c_double)]
+                ("use_graph", C.c_int), ("autotune", C.c_int), ("beta_T_exp", C.c_double),
+                ("fp64_strict", C.c_int)]
 
 
 class bte_stats(C.Structure):
@@ -77,6 +78,9 @@ SIGNATURES = {
     "bte_set_intensity": (C.c_int, [_h, C.c_int, _vp, _vp, C.c_int]),
     "bte_get_directions": (C.c_int, [_h, _dp, _dp, _ip]),
     "bte_get_wall_flux_noalloc": (C.c_int, [_h, C.c_int, _vp, C.c_int]),
+    "bte_measure_peak": (C.c_int, [C.c_int, _dp, _dp]),
+    "bte_set_sweep_timing": (C.c_int, [_h, C.c_int]),
+    "bte_sweep_times": (C.c_int, [_h, C.POINTER(C.c_float), C.c_int]),
     "bte_train_mlp": (C.c_int, [_h, C.c_longlong, C.c_double, C.c_double, C.c_int, C.c_ulonglong, _dp]),
     "bte_mlp_params": (C.c_int, [_h, C.c_int, C.POINTER(C.c_float), C.c_int]),
     "bte_mlp_set_params": (C.c_int, [_h, C.c_int, C.POINTER(C.c_float), C.c_int]),
@@ -289,6 +293,31 @@ def bte_solve_T(h, Ep, T0=None, learned=False):
     return T, ev
 
 
+def bte_set_sweep_timing(h, on=True):
+    return _check(h, lib().bte_set_sweep_timing(h, 1 if on else 0))
+
+
+def bte_sweep_times(h):
+    """Device time (ms) of each sweep launch of the most recent time step."""
+    n = _check(h, lib().bte_sweep_times(h, None, 0))
+    ms = np.zeros(n, dtype=np.float32)
+    _check(h, lib().bte_sweep_times(h, ms.ctypes.data_as(C.POINTER(C.c_float)), n))
+    return ms.astype(np.float64)
+
+
+BTE_PEAK_FP64_FMA, BTE_PEAK_FP32X2_FMA = 0, 1
+
+
+def bte_measure_peak(kind):
+    """(flop/s, ms of the timed launch) of the FMA loop of `kind` on the current device."""
+    f = np.zeros(1)
+    ms = np.zeros(1)
+    rc = lib().bte_measure_peak(int(kind), f.ctypes.data_as(_dp), ms.ctypes.data_as(_dp))
+    if rc < 0:
+        raise BTEError(rc, "bte_measure_peak failed")
+    return float(f[0]), float(ms[0])
+
+
 def bte_destroy(h):
     return _check(None, lib().bte_destroy(h))
 
@@ -326,7 +355,7 @@ class Solver:
 
     def __init__(self, workload, precision=BTE_FP64, stream=None, bind_workspace=True, n_gauss=16, T_init=None,
                  use_graph=False, autotune=False, learned=False, band_range=None, exchange=None, beta_exp=0.0,
-                 T_ref=None):
+                 T_ref=None, fp64_strict=False):
         """band_range=(lo, hi) stores and sweeps only bands [lo, hi); exchange(buf)
         then sums the float64 CUDA tensor buf of per-cell (E_L, E_p) partials
         over the ranks in place (e.g. allreduce_exchange()); it runs with this
@@ -347,6 +376,7 @@ class Solver:
         o.learned = 1 if learned else 0
         o.autotune = 1 if autotune else 0
         o.beta_T_exp = float(beta_exp)
+        o.fp64_strict = 1 if fp64_strict else 0
         if T_ref is not None:
             o.T_ref = float(T_ref)
         self.stream = stream if stream is not None else torch.cuda.current_stream()

@@ -83,6 +83,7 @@ struct bte_ctx {
   int cur = 0;
   double *I0cell = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr, *I0wall = nullptr;
   void* coef = nullptr;
+  void* coef_ff = nullptr;  // FP64: the coefficients as double-float pairs (bte_ff.cuh layout)
   double *J = nullptr, *Teval = nullptr, *I0ref = nullptr, *scratch_pack = nullptr;
   double* Msum = nullptr;     // [cell][3] the T_p model's sums sum_b a_p,b J_k,b
   double* I0ref_o = nullptr;  // I0_b(T_ref) of the stored bands (aliases I0ref unless a band range is set)
@@ -112,6 +113,12 @@ struct bte_ctx {
   double coef_dt = -1.0;
   int coef_scheme = -1;
   std::vector<double> coef_host;
+  std::vector<float> coef_ff_host;
+  // per-launch timing of the sweeps (bte_set_sweep_timing): events around each
+  // sweep of a step, recorded on the stream (captured into the step's graph)
+  bool time_sweeps = false;
+  std::vector<cudaEvent_t> tev;
+  int tev_n = 0;  // sweeps the events of the last step cover
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -197,6 +204,7 @@ size_t carve(bte_ctx* h, char* base) {
   h->EL = (double*)take((size_t)h->ncells * 8);
   h->I0wall = (double*)take((size_t)std::max(h->nfaces, 1LL) * h->nbp * 8);
   h->coef = take((size_t)h->cls_key.size() * row * (h->opts.precision == BTE_FP64 ? 5 * 8 : 2 * 4));
+  h->coef_ff = h->opts.precision == BTE_FP64 ? take((size_t)h->cls_key.size() * row * 5 * 8) : nullptr;
   h->dirc = (float4*)take((size_t)h->cls_key.size() * h->nd * sizeof(float4));
   h->vb32 = (float*)take((size_t)h->nbp * 4);
   h->bb32 = (float*)take((size_t)h->nbp * 4);
@@ -450,6 +458,12 @@ int ensure_coef(bte_ctx* h, double dt, int scheme) {
                  h->coef_host.data() + c * 5 * plane);
     }
     CUDA_TRY(h, cudaMemcpyAsync(h->coef, h->coef_host.data(), h->coef_host.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    h->coef_ff_host.resize(2 * h->coef_host.size());
+    for (size_t c = 0; c < ncls; ++c)
+      coef_to_ff(h->coef_host.data() + c * 5 * plane, h->nd, h->nbp, scheme != BTE_EXPLICIT,
+                 h->coef_ff_host.data() + c * 10 * plane);
+    CUDA_TRY(h, cudaMemcpyAsync(h->coef_ff, h->coef_ff_host.data(), h->coef_ff_host.size() * 4, cudaMemcpyHostToDevice,
+                                h->stream));
   } else {
     std::vector<float> pq(2 * plane * ncls), dc(4 * (size_t)h->nd * ncls);
     for (size_t c = 0; c < ncls; ++c) {
@@ -531,6 +545,7 @@ SweepArgs sweep_args(bte_ctx* h) {
   a.Epart = h->exchange_buf ? h->exchange_buf : h->Epart;
   a.partial = h->Epart ? 1 : 0;
   a.coef = h->coef;
+  a.coef_ff = h->coef_ff;
   a.dirs = h->dirs_d;
   a.wdir = h->wdir;
   a.wdir32 = h->wdir32;
@@ -598,6 +613,19 @@ cudaError_t refresh_partial(bte_ctx* h, const void* I, cudaStream_t s, int* laun
   return cudaSuccess;
 }
 
+// Whether the FP64 Jacobi sweep of this handle runs in double-float arithmetic:
+// FP64 storage without fp64_strict, fixed relaxation rates, and walls whose
+// ghosts the sweep reads directly (isothermal faces and mirrors; diffuse and
+// partially specular ghosts are refreshed between inner iterations by kernels
+// that read the iterate as doubles).
+bool ff_sweep(const bte_ctx* h) {
+  if (h->opts.precision != BTE_FP64 || h->opts.fp64_strict || h->opts.beta_T_exp != 0.0) return false;
+  for (size_t gi = 0; gi < h->geoms.size(); ++gi)
+    for (int side = 0; side < 2 * h->geoms[gi].dim; ++side)
+      if (h->bc_type[gi][side] == BTE_BC_DIFFUSE || h->bc_type[gi][side] == BTE_BC_PARTIAL) return false;
+  return true;
+}
+
 // One time step: ninner sweeps rotating the three intensity buffers from *cur.
 // scheme BTE_IMPLICIT_GS runs the sweep-ordered pass and the per-cell step as
 // two kernels in place of the fused Jacobi sweep.
@@ -610,11 +638,14 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaSt
   // the third buffer: iteration 0 reads I^n and writes I^1 and B; iteration k
   // reads B and I^k and overwrites the buffer I^n (or I^{k-2}) was in.
   const bool use_b = h->opts.precision == BTE_FP64 && !a.explicit_scheme && ninner >= 2 && !a.dry;
+  // double-float Jacobi sweeps: I^n in doubles -> ff iterates and B -> doubles again
+  const bool use_ff = use_b && scheme == BTE_IMPLICIT_JACOBI && ff_sweep(h);
   int z = -1;
   for (int it = 0; it < ninner; ++it) {
     int o = 0;
     a.bmode = 0;
     a.Bout = nullptr;
+    a.ff = use_ff ? (it == 0 ? 2 : (it == ninner - 1 ? 1 : 3)) : 0;
     if (use_b && it == 0) {
       while (o == n) ++o;
       z = 0;
@@ -635,6 +666,8 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaSt
     cudaError_t e = cudaMemsetAsync(h->fix_count, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = refresh_diffuse(h, a.Ik, s);
     if (e == cudaSuccess) e = refresh_partial(h, a.Ik, s);
+    const bool timed = h->time_sweeps && 2 * it + 1 < (int)h->tev.size();
+    if (e == cudaSuccess && timed) e = cudaEventRecord(h->tev[2 * it], s);
     if (scheme == BTE_IMPLICIT_GS) {
       if (e == cudaSuccess && a.beta_exp != 0.0)
         e = launch_beta_scale(h->bscale, h->Tp, a.beta_Tref, a.beta_exp, h->ncells, s);
@@ -643,6 +676,7 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaSt
     } else if (e == cudaSuccess) {
       e = launch_sweep(h->opts.precision, h->pd, a, dim, h->threads, h->grid, s);
     }
+    if (e == cudaSuccess && timed) e = cudaEventRecord(h->tev[2 * it + 1], s);
     if (e == cudaSuccess && a.partial) {
       // band-range handle: the caller sums the per-cell (E_L, E_p) partials over
       // the ranks that hold the other bands, then every rank solves every cell
@@ -730,6 +764,7 @@ int bte_default_opts(bte_opts* o) {
   o->use_graph = 0;
   o->autotune = 0;
   o->beta_T_exp = 0.0;
+  o->fp64_strict = 0;
   return BTE_OK;
 }
 
@@ -994,6 +1029,17 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
   const bool ranged = h->Epart != nullptr;
   if (ranged && !h->exchange) return fail(h, BTE_E_STATE, "a band-range handle needs bte_set_exchange before stepping");
   h->exchange_rc = 0;
+  if (h->time_sweeps && nsteps > 0) {
+    if ((int)h->tev.size() < 2 * ninner) {  // events for every sweep of a step; graphs captured before lack them
+      drop_graphs(h);
+      while ((int)h->tev.size() < 2 * ninner) {
+        cudaEvent_t ev = nullptr;
+        CUDA_TRY(h, cudaEventCreate(&ev));
+        h->tev.push_back(ev);
+      }
+    }
+    h->tev_n = ninner;
+  }
   for (int st = 0; st < nsteps; ++st) {
     if (h->opts.use_graph && !ranged) {  // the host-side exchange cannot sit inside a graph
       cudaGraphExec_t exec = nullptr;
@@ -1169,6 +1215,10 @@ int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t repor
         a.counters = nullptr;
         a.In = a.Ik = h->Ibuf[h->cur];
         a.Iout = h->Ibuf[spare];
+        if (scheme == BTE_IMPLICIT_JACOBI && ff_sweep(h)) {  // the middle inner iterations' variant
+          a.bmode = 2;
+          a.ff = 3;
+        }
         CUDA_TRY(h, launch_sweep(h->opts.precision, pd, a, dim, h->threads, grid, s));
         CUDA_TRY(h, cudaEventRecord(h->ev0, s));
         for (int r = 0; r < 3; ++r) CUDA_TRY(h, launch_sweep(h->opts.precision, pd, a, dim, h->threads, grid, s));
@@ -1538,8 +1588,25 @@ int bte_destroy(bte_handle h) {
       if (p) cudaFree(p);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  for (cudaEvent_t ev : h->tev) cudaEventDestroy(ev);
   delete h;
   return BTE_OK;
+}
+
+int bte_set_sweep_timing(bte_handle h, int on) {
+  if (!h) return BTE_E_ARG;
+  if ((on != 0) != h->time_sweeps) drop_graphs(h);  // the step graphs gain or lose the event nodes
+  h->time_sweeps = on != 0;
+  h->tev_n = 0;
+  return BTE_OK;
+}
+
+int bte_sweep_times(bte_handle h, float* ms, int n) {
+  if (!h || (n > 0 && !ms)) return BTE_E_ARG;
+  if (!h->time_sweeps || h->tev_n == 0) return fail(h, BTE_E_STATE, "no timed step since bte_set_sweep_timing");
+  CUDA_TRY(h, cudaEventSynchronize(h->tev[2 * h->tev_n - 1]));
+  for (int i = 0; i < n && i < h->tev_n; ++i) CUDA_TRY(h, cudaEventElapsedTime(ms + i, h->tev[2 * i], h->tev[2 * i + 1]));
+  return h->tev_n;
 }
 
 const char* bte_last_error(bte_handle h) {

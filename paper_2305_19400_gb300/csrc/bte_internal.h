@@ -111,6 +111,11 @@ struct SweepArgs {
   const double* I0wall;     // [face][nbp] FP64 ghosts
   const float* I0wall_dev;  // [face][nbp] FP32 ghosts minus I0ref (reduced modes)
   const double* I0ref;      // [nbp] I0_b(T_ref) (reduced modes)
+  const void* coef_ff;      // FP64: the same coefficients as double-float pairs, per 16 bytes
+                            // (two bands) h_b, h_b+1, l_b, l_b+1; the sum of the five is 1
+                            // (implicit) up to the pairs' resolution
+  int ff;                   // FP64: 0 DFMA arithmetic; else the double-float variant
+                            // (bit 0: I^k and B are ff pairs; bit 1: I^{k+1} and B are written as ff)
   const void* coef;         // FP64: [cls][5][nd][nbp] A_n, A_x, A_y, A_z, A_s;
                             // reduced: [cls][2][nd][nbp] float P, Q with
                             // I' = P I^n + Q (v_b sum_ax c_ax I_up + beta_b dI0)

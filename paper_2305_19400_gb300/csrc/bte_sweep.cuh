@@ -35,6 +35,7 @@
 #pragma once
 #include <type_traits>
 
+#include "bte_ff.cuh"
 #include "bte_store.cuh"
 
 namespace bte {
@@ -111,8 +112,8 @@ struct DirSm {
   int4 info;     // up flags, rx, ry, rz
   float4 c;      // reduced modes: c_ax = |S_d,ax| / (w_d Delta_ax)
   double w;      // w_d
-  float w32;
-  float pad;
+  float w32;     // w_d rounded to float
+  float wlo;     // w_d - w32 rounded to float (the ff form of w_d)
 };
 
 // Staging ring: per thread and stage, 16 bytes per operand.  Operands: I^n (or
@@ -131,11 +132,24 @@ struct Ring {
 // the same value, one FP64 multiply fewer per update).
 // TT (FP64 only): the relaxation rates depend on T (beta_exp != 0); the
 // reduced modes scale beta per cell outside the step loop and need no variant.
-template <int DIM, typename S, int MINB, int BM, bool TT>
+// FF (FP64 storage only, TT false): 0 the update runs in FP64 (DFMA); otherwise
+// it runs in double-float arithmetic on the FP32 pipe (bte_ff.cuh) with the
+// coefficients of a.coef_ff, and FF says which buffers hold ff pairs instead
+// of doubles: bit 0 the iterate I^k and B (the In operand when BM == 2), bit 1
+// the output I^{k+1} and B (BM == 1).  The first inner iteration of a step
+// reads the doubles of I^n and writes ff (FF = 2), the middle ones stay in ff
+// (FF = 3) and the last writes doubles again (FF = 1), so every buffer that
+// outlives a step holds doubles.  Isothermal wall ghosts are doubles in every
+// variant.  The direction sums G_b are summed in ff per run of equal weights
+// and enter G in ff; G becomes a double once per cell.
+template <int DIM, typename S, int MINB, int BM, bool TT, int FF = 0>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   using T = Tr<S>;
   using A = typename T::A;
   constexpr int V = T::V;
+  static_assert(FF == 0 || (sizeof(S) == 8 && !TT), "double-float variants are FP64 storage with fixed rates");
+  static_assert(FF == 0 || BM != 2 || (FF & 1) != 0, "B is an ff pair whenever the variant is double-float");
+  static_assert(FF == 0 || BM == 2 || (FF & 1) == 0, "the first inner iteration reads I^n in doubles");
   constexpr bool kDev = sizeof(S) != 8;  // reduced modes store deviations
   extern __shared__ double sm[];
   __shared__ unsigned long long cnt_solves, cnt_bad;
@@ -184,7 +198,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         e.c = kDev ? a.dirc[(size_t)gcls * nd + d] : make_float4(0.f, 0.f, 0.f, 0.f);
         e.w = a.wdir[d];
         e.w32 = a.wdir32[d];
-        e.pad = 0.f;
+        e.wlo = (float)(e.w - (double)e.w32);
         dsm[d] = e;
       }
       if (threadIdx.x == 0) cur_cls = gcls;
@@ -216,7 +230,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         src[v] = kDev ? bb[v] * (A)(i0 - a.I0ref[b0 + v]) : (A)i0;
       }
       const size_t plane = (size_t)nd * nbp;
-      const A* __restrict__ cf = coef + (size_t)gcls * 5 * plane + b0;
+      // coefficient rows of this class and band vector: FP64, or their ff pairs
+      // (same element offsets) in the FF variants
+      const A* __restrict__ cf =
+          (FF != 0 ? reinterpret_cast<const A*>(a.coef_ff) : coef) + (size_t)gcls * 5 * plane + b0;
       CellAddr<S> c;
       c.in = In + P * row + b0;
       c.ik = Ik + P * row + b0;
@@ -244,7 +261,11 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       int fe0[V];        // largest exponent field summed in fixed point (-1: none)
       long long wrun = 0;
       int nrun = 0;
-      if constexpr (!kDev) {
+      // FF variants: the run's sum S and the weighted sum G of this lane's two
+      // bands as ff pairs, the run's weight, and I0 of the cell as ff
+      ff::P2 Sff = ff::zero(), Gff = ff::zero(), wff = ff::zero(), srcff = ff::zero();
+      if constexpr (FF != 0) srcff = ff::from_doubles((double)src[0], (double)src[1]);
+      if constexpr (!kDev && FF == 0) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int e0 = (int)((unsigned long long)__double_as_longlong((double)src[v]) >> 52);  // src = I0 (>= 0)
@@ -334,7 +355,47 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         read_up(sb, 1, di, off, uy);
         if (DIM == 3) read_up(sb, 2, di, off, uz);
         A r[V];
-        if constexpr (!kDev) {
+        if constexpr (FF != 0) {
+          // double-float update of the lane's two bands (bte_ff.cuh):
+          // B (or A_n I^n) + A_x I_x + A_y I_y (+ A_z I_z) + A_s I0
+          ff::P2 rf;
+          if constexpr (BM == 2 && (FF & 1)) {
+            rf = ff::lds(sb);
+          } else {
+            rf = ff::norm(ff::mul(ff::ldg(cf + off), ff::lds_doubles(sb)));  // A_n I^n
+            if constexpr (BM == 1) {
+              if constexpr ((FF & 2) != 0) ff::st_stream(c.bout + off, rf);
+              else ff::st_stream_doubles(c.bout + off, rf);
+            }
+          }
+#pragma unroll
+          for (int ax = 0; ax < DIM; ++ax) {
+            // the upwind operand is an ff pair unless it is I^k in doubles or an
+            // isothermal wall ghost (doubles in every variant)
+            bool dbl = (FF & 1) == 0;
+            if ((FF & 1) != 0 && c.wall != 0) {
+              const int side = 2 * ax + (((di.x >> ax) & 1) ? 0 : 1);
+              dbl = ((c.wall >> side) & 1) && gp->bc[side] == 0;
+            }
+            const unsigned ua = sb + (1 + ax) * ostr;
+            const ff::P2 u = dbl ? ff::lds_doubles(ua) : ff::lds(ua);
+            ff::acc(rf, ff::mul(ff::lds(sb + (1 + DIM + ax) * ostr), u));
+          }
+          ff::acc(rf, ff::mul(ff::lds(sb + (1 + 2 * DIM) * ostr), srcff));
+          rf = ff::norm(rf);
+          if constexpr ((FF & 2) != 0) ff::st_stream(c.out + off, rf);
+          else ff::st_stream_doubles(c.out + off, rf);
+          // G_b: the run's sum in ff; a new weight closes the run into G
+          const long long wb = __double_as_longlong(dsm[d].w);
+          if (wb != wrun) {
+            ff::acc(Gff, ff::mul(wff, Sff));
+            Sff = ff::zero();
+            const float w32 = dsm[d].w32, wlo = dsm[d].wlo;
+            wff = ff::P2{ff::pack(w32, w32), ff::pack(wlo, wlo)};
+            wrun = wb;
+          }
+          ff::acc(Sff, rf);
+        } else if constexpr (!kDev) {
           A Ax[V], Ay[V], As[V];
           Tr<double>::lds(sb + (1 + DIM) * ostr, Ax);
           Tr<double>::lds(sb + (2 + DIM) * ostr, Ay);
@@ -450,7 +511,13 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         run(std::false_type{});
       }
       cp_async_wait<0>();
-      if constexpr (kDev) {
+      if constexpr (FF != 0) {
+        ff::acc(Gff, ff::mul(wff, Sff));
+        double g0, g1;
+        ff::to_doubles(ff::norm(Gff), g0, g1);
+        G[0] = g0;
+        G[1] = g1;
+      } else if constexpr (kDev) {
 #pragma unroll
         for (int v = 0; v < V; ++v) G[v] += (double)acc[v];
       } else {
@@ -570,7 +637,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   }
 }
 
-template <typename S, int MINB, int BM, bool TT>
+template <typename S, int MINB, int BM, bool TT, int FF>
 cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   const int team = a.lpc * a.dteam, cpb = threads / team;
   const size_t smem = sizeof(DirSm) * (size_t)a.nd + (size_t)Tr<S>::V * threads * sizeof(double) +
@@ -579,26 +646,33 @@ cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cuda
                           threads * 16;
   if (dim == 3) {
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(sweep_kernel<3, S, MINB, BM, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sweep_kernel<3, S, MINB, BM, TT><<<grid, threads, smem, s>>>(a);
+      cudaFuncSetAttribute(sweep_kernel<3, S, MINB, BM, TT, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sweep_kernel<3, S, MINB, BM, TT, FF><<<grid, threads, smem, s>>>(a);
   } else {
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(sweep_kernel<2, S, MINB, BM, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sweep_kernel<2, S, MINB, BM, TT><<<grid, threads, smem, s>>>(a);
+      cudaFuncSetAttribute(sweep_kernel<2, S, MINB, BM, TT, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sweep_kernel<2, S, MINB, BM, TT, FF><<<grid, threads, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
 
 // variant: 1 -> at least 2 resident CTAs per SM (<= 128 registers), 2 -> 3 CTAs (<= 80 registers)
-template <typename S, int BM, bool TT>
+template <typename S, int BM, bool TT, int FF = 0>
 cudaError_t launch_bm(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
-  if (variant >= 2) return launch_minb<S, 3, BM, TT>(a, dim, threads, grid, s);
-  return launch_minb<S, 2, BM, TT>(a, dim, threads, grid, s);
+  if (variant >= 2) return launch_minb<S, 3, BM, TT, FF>(a, dim, threads, grid, s);
+  return launch_minb<S, 2, BM, TT, FF>(a, dim, threads, grid, s);
 }
 
 template <typename S>
 cudaError_t launch(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   if constexpr (sizeof(S) == 8) {
+    if (a.ff != 0) {  // double-float arithmetic: the B form with fixed relaxation rates only
+      if (a.beta_exp != 0.0) return cudaErrorInvalidValue;
+      if (a.bmode == 1 && a.ff == 2) return launch_bm<S, 1, false, 2>(variant, a, dim, threads, grid, s);
+      if (a.bmode == 2 && a.ff == 3) return launch_bm<S, 2, false, 3>(variant, a, dim, threads, grid, s);
+      if (a.bmode == 2 && a.ff == 1) return launch_bm<S, 2, false, 1>(variant, a, dim, threads, grid, s);
+      return cudaErrorInvalidValue;
+    }
     if (a.beta_exp != 0.0) {
       if (a.bmode == 1) return launch_bm<S, 1, true>(variant, a, dim, threads, grid, s);
       if (a.bmode == 2) return launch_bm<S, 2, true>(variant, a, dim, threads, grid, s);
@@ -607,7 +681,7 @@ cudaError_t launch(int variant, const SweepArgs& a, int dim, int threads, int gr
     if (a.bmode == 1) return launch_bm<S, 1, false>(variant, a, dim, threads, grid, s);
     if (a.bmode == 2) return launch_bm<S, 2, false>(variant, a, dim, threads, grid, s);
   } else {
-    if (a.bmode != 0) return cudaErrorInvalidValue;  // the B form exists for FP64 storage only
+    if (a.bmode != 0 || a.ff != 0) return cudaErrorInvalidValue;  // the B form exists for FP64 storage only
   }
   return launch_bm<S, 0, false>(variant, a, dim, threads, grid, s);
 }
