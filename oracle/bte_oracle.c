@@ -31,7 +31,9 @@
  * conservation, the p = 1 / p = 0 limits bit for bit), temperature-dependent
  * relaxation, and the unstructured update (the structured result on a quad
  * mesh for every wall kind and for tau(T), dense LU, equilibrium,
- * conservation, a quarter turn of the mesh).
+ * conservation, a quarter turn of the mesh), and its rotationally periodic
+ * faces (an axisymmetric problem on one wedge) against the full ring of
+ * wedges solved without them.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -45,7 +47,7 @@ static const double ORC_HBAR = 1.054571817e-34; /* J s */
 static const double ORC_KB = 1.380649e-23;      /* J/K */
 static const double ORC_PI = 3.14159265358979323846;
 
-enum { ORC_ISOTHERMAL = 0, ORC_SPECULAR = 1, ORC_DIFFUSE = 2, ORC_PARTIAL = 3 };
+enum { ORC_ISOTHERMAL = 0, ORC_SPECULAR = 1, ORC_DIFFUSE = 2, ORC_PARTIAL = 3, ORC_ROTATIONAL = 4 };
 enum { ORC_IMPLICIT = 0, ORC_EXPLICIT = 1, ORC_GAUSS_SEIDEL = 2 };
 
 int orc_num_threads(void) {
@@ -704,7 +706,58 @@ typedef struct {
   const int* btype;    /* [nf] ORC_* on boundary faces */
   const double* Twall; /* [nf] isothermal face temperature */
   const double* spec;  /* [nf] specularity of ORC_PARTIAL faces (NULL when there are none) */
+  /* ORC_ROTATIONAL faces (axisymmetric problems, one wedge of angle rot_angle
+     about the z axis): across such a face lies the wedge itself rotated by
+     +-rot_angle, so by axial symmetry the ghost of direction s is the owner's
+     own intensity in the direction s rotated back (by -+rot_angle).  The sense
+     follows from the face: outward normal along +e_theta at the face centre
+     (the wedge's far side) or along -e_theta (its near side). */
+  double rot_angle;
+  const double* fc;    /* [nf][3] face centres (used by ORC_ROTATIONAL faces) */
+  const int* rot_map;  /* filled inside the oracle: [2][nd] direction rotated by -rot_angle, by +rot_angle */
 } orc_umesh;
+
+/* e with S_e = R_z(phi) S_d (rotation about the z axis), matched to 1e-9 of
+   |S_d|; -1 when the direction set has no such direction. */
+static void um_rotation_map(const orc_problem* p, double phi, int* map) {
+  double c = cos(phi), s = sin(phi);
+  for (int d = 0; d < p->nd; ++d) {
+    const double* S = p->S + 3 * d;
+    double r[3] = {c * S[0] - s * S[1], s * S[0] + c * S[1], S[2]};
+    double norm = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    map[d] = -1;
+    for (int e = 0; e < p->nd; ++e) {
+      const double* T = p->S + 3 * e;
+      double dd = sqrt((T[0] - r[0]) * (T[0] - r[0]) + (T[1] - r[1]) * (T[1] - r[1]) + (T[2] - r[2]) * (T[2] - r[2]));
+      if (dd <= 1e-9 * norm) {
+        map[d] = e;
+        break;
+      }
+    }
+  }
+}
+
+/* A copy of the mesh with rot_map filled (caller frees *maps); returns 0, or
+   -1 when a rotationally periodic face's rotation is not a symmetry of the
+   direction set. */
+static int um_with_rotation(const orc_problem* p, const orc_umesh* m, orc_umesh* out, int** maps) {
+  *out = *m;
+  *maps = NULL;
+  int any = 0;
+  for (long f = 0; f < m->nf; ++f) any |= m->nbr[f] < 0 && m->btype[f] == ORC_ROTATIONAL;
+  if (!any) return 0;
+  int* mp = (int*)malloc(sizeof(int) * 2 * p->nd);
+  um_rotation_map(p, -m->rot_angle, mp);
+  um_rotation_map(p, m->rot_angle, mp + p->nd);
+  for (int d = 0; d < 2 * p->nd; ++d)
+    if (mp[d] < 0) {
+      free(mp);
+      return -1;
+    }
+  out->rot_map = mp;
+  *maps = mp;
+  return 0;
+}
 
 /* cell -> faces (CSR), built once per call that needs it */
 static void um_cell_faces(const orc_umesh* m, long** ptr_out, long** list_out) {
@@ -757,10 +810,21 @@ static double um_mirror(const orc_problem* p, const orc_umesh* m, const double* 
   return Isrc[m->owner[f] * p->nd * p->nb + (long)r[d] * p->nb + b];
 }
 
+/* rotationally periodic face f: the owner's intensity in direction d rotated
+   back across the face (sense from the outward normal against e_theta) */
+static double um_rotated(const orc_problem* p, const orc_umesh* m, const double* Isrc, long f, int d, int b) {
+  const double* n = m->nA + 3 * f;
+  const double* c = m->fc + 3 * f;
+  double along = -c[1] * n[0] + c[0] * n[1]; /* n . e_theta times the centre's distance from the axis */
+  int e = m->rot_map[(along > 0 ? 0 : p->nd) + d];
+  return Isrc[m->owner[f] * p->nd * p->nb + (long)e * p->nb + b];
+}
+
 /* ghost value of boundary face f (owner P) for incoming direction d, band b */
 static double um_ghost(const orc_problem* p, const orc_umesh* m, const double* Isrc, const double* I0w, long f, int d,
                        int b) {
   if (m->btype[f] == ORC_ISOTHERMAL) return I0w[f * p->nb + b];
+  if (m->btype[f] == ORC_ROTATIONAL) return um_rotated(p, m, Isrc, f, d, b);
   if (m->btype[f] == ORC_DIFFUSE) return um_diffuse(p, m, Isrc, f, b);
   if (m->btype[f] == ORC_PARTIAL)
     return m->spec[f] * um_mirror(p, m, Isrc, f, d, b) + (1.0 - m->spec[f]) * um_diffuse(p, m, Isrc, f, b);
@@ -795,13 +859,18 @@ static double um_update_one(const orc_problem* p, const orc_umesh* m, const long
   return (in / dt + beta * i0 + v * inflow) / (1.0 / dt + beta + v * gout);
 }
 
-double orc_umesh_update_one(const orc_problem* p, const orc_umesh* m, double dt, int scheme, const double* In,
+double orc_umesh_update_one(const orc_problem* p, const orc_umesh* m0, double dt, int scheme, const double* In,
                             const double* Ik, const double* I0, const double* I0w, long P, int d, int b) {
+  orc_umesh mm;
+  int* maps;
+  if (um_with_rotation(p, m0, &mm, &maps)) return NAN;
+  const orc_umesh* m = &mm;
   long *fptr, *flist;
   um_cell_faces(m, &fptr, &flist);
   double r = um_update_one(p, m, fptr, flist, dt, scheme, In, Ik, I0, I0w, P, d, b, 1.0);
   free(fptr);
   free(flist);
+  free(maps);
   return r;
 }
 
@@ -819,8 +888,12 @@ void orc_umesh_wall_I0(const orc_problem* p, const orc_umesh* m, double* out) {
  * inner iterations or explicit steps), the same reduction, temperature solves
  * and I0 refresh per cell.  Returns the bisection fallbacks, -1 on an
  * unsolvable cell. */
-long orc_umesh_run(const orc_problem* p, const orc_umesh* m, double dt, int nsteps, int ninner, int scheme, double* I,
+long orc_umesh_run(const orc_problem* p, const orc_umesh* m0, double dt, int nsteps, int ninner, int scheme, double* I,
                    double* Tp, double* TL, double* I0) {
+  orc_umesh mm;
+  int* maps;
+  if (um_with_rotation(p, m0, &mm, &maps)) return -2;
+  const orc_umesh* m = &mm;
   long nc = m->nc;
   int nd = p->nd, nb = p->nb;
   size_t n = (size_t)nc * nd * nb;
@@ -856,6 +929,7 @@ long orc_umesh_run(const orc_problem* p, const orc_umesh* m, double dt, int nste
   free(I0w);
   free(fptr);
   free(flist);
+  free(maps);
   return bad ? -1 : fallbacks;
 }
 
@@ -863,7 +937,14 @@ long orc_umesh_run(const orc_problem* p, const orc_umesh* m, double dt, int nste
  * boundary face the net heat flow out of the domain,
  * Q_f = sum_b sum_d (S_d . n_f A_f) I_face (own value leaving, ghost entering),
  * 0 on interior faces. */
-void orc_umesh_flux(const orc_problem* p, const orc_umesh* m, const double* I, double* q, double* Qf) {
+void orc_umesh_flux(const orc_problem* p, const orc_umesh* m0, const double* I, double* q, double* Qf) {
+  orc_umesh mm;
+  int* maps;
+  if (um_with_rotation(p, m0, &mm, &maps)) {
+    for (long f = 0; f < m0->nf; ++f) Qf[f] = NAN;
+    return;
+  }
+  const orc_umesh* m = &mm;
   int nd = p->nd, nb = p->nb;
   double* I0w = (double*)malloc((size_t)(m->nf > 0 ? m->nf : 1) * nb * sizeof(double));
   orc_umesh_wall_I0(p, m, I0w);
@@ -890,4 +971,5 @@ void orc_umesh_flux(const orc_problem* p, const orc_umesh* m, const double* I, d
     Qf[f] = s;
   }
   free(I0w);
+  free(maps);
 }

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "bte_oracle.c")
 LIB = os.path.join(HERE, "_build", "liborc.so")
 
-ISOTHERMAL, SPECULAR, DIFFUSE, PARTIAL = 0, 1, 2, 3
+ISOTHERMAL, SPECULAR, DIFFUSE, PARTIAL, ROTATIONAL = 0, 1, 2, 3, 4
 IMPLICIT, EXPLICIT, GAUSS_SEIDEL = 0, 1, 2
 
 _lock = threading.Lock()
@@ -304,7 +304,8 @@ class Problem:
 class _UMesh(C.Structure):
     _fields_ = [("dim", C.c_int), ("nc", C.c_long), ("nf", C.c_long), ("vol", C.POINTER(C.c_double)),
                 ("owner", C.POINTER(C.c_long)), ("nbr", C.POINTER(C.c_long)), ("nA", C.POINTER(C.c_double)),
-                ("btype", C.POINTER(C.c_int)), ("Twall", C.POINTER(C.c_double)), ("spec", C.POINTER(C.c_double))]
+                ("btype", C.POINTER(C.c_int)), ("Twall", C.POINTER(C.c_double)), ("spec", C.POINTER(C.c_double)),
+                ("rot_angle", C.c_double), ("fc", C.POINTER(C.c_double)), ("rot_map", C.POINTER(C.c_int))]
 
 
 class UMeshProblem:
@@ -312,10 +313,11 @@ class UMeshProblem:
     its direction set, bands and boundary conditions.
 
     bc: {tag: (kind, T)} with kind ISOTHERMAL (T a float, or an array over the
-    mesh's faces indexed by face id), SPECULAR or DIFFUSE (T ignored), or
+    mesh's faces indexed by face id), SPECULAR or DIFFUSE (T ignored),
     PARTIAL (T the specularity p in [0, 1], a float or an array over the
-    faces).  The direction and band tables
-    live in a Problem on a one-cell grid."""
+    faces), or ROTATIONAL (T the wedge angle of an axisymmetric problem about
+    the z axis; every ROTATIONAL tag takes the same angle).  The direction and
+    band tables live in a Problem on a one-cell grid."""
 
     def __init__(self, mesh, dirs, bands, bc, ngauss: int = 16, newton_rtol: float = 1e-14, newton_maxit: int = 50,
                  beta_exp: float = 0.0, beta_Tref: float = 300.0):
@@ -335,6 +337,8 @@ class UMeshProblem:
         self.btype = np.full(nf, SPECULAR, dtype=np.int32)
         self.Twall = np.zeros(nf)
         self.spec = np.zeros(nf)
+        self.fc = np.ascontiguousarray(mesh.face_center, dtype=np.float64)
+        rot_angle = 0.0
         for f in np.nonzero(self.nbr < 0)[0]:
             kind, T = bc[int(mesh.tag[f])]
             self.btype[f] = kind
@@ -342,9 +346,12 @@ class UMeshProblem:
                 self.Twall[f] = T if np.isscalar(T) else T[f]
             elif kind == PARTIAL:
                 self.spec[f] = T if np.isscalar(T) else T[f]
+            elif kind == ROTATIONAL:
+                rot_angle = float(T)
         m = _UMesh()
         m.dim, m.nc, m.nf = mesh.dim, self.nc, nf
         m.vol, m.nA, m.Twall, m.spec = _dp(self.vol), _dp(self.nA), _dp(self.Twall), _dp(self.spec)
+        m.rot_angle, m.fc = rot_angle, _dp(self.fc)
         m.owner = self.owner.ctypes.data_as(C.POINTER(C.c_long))
         m.nbr = self.nbr.ctypes.data_as(C.POINTER(C.c_long))
         m.btype = _ip(self.btype)
@@ -366,6 +373,8 @@ class UMeshProblem:
     def run(self, st, dt, nsteps, ninner, scheme=IMPLICIT) -> int:
         r = lib().orc_umesh_run(self.tables.ptr, self.ptr, float(dt), int(nsteps), int(ninner), int(scheme),
                                 _dp(st["I"]), _dp(st["Tp"]), _dp(st["TL"]), _dp(st["I0"]))
+        if r == -2:
+            raise RuntimeError("oracle: the wedge angle is not a rotation symmetry of the direction set")
         if r < 0:
             raise RuntimeError("oracle: a cell has no temperature in [1, 5000] K")
         return int(r)

@@ -229,6 +229,50 @@ def tet_box(nx: int, ny: int, nz: int, Lx: float, Ly: float, Lz: float) -> UMesh
     return from_elements(pts, el, b)
 
 
+def wedge_ring(nr: int, nz: int, r_in: float, r_out: float, Lz: float, alpha: float, nwedge: int = 1) -> UMesh:
+    """A hollow cylinder about the z axis cut into wedges of angle alpha, each
+    wedge nr x nz hexahedral cells in (r, z) with planar faces; the first wedge
+    spans theta in [-alpha/2, alpha/2] (centred on +x) and wedge k is the first
+    rotated by k alpha.  nwedge = 1 gives the one-cell-thick wedge of an
+    axisymmetric problem; nwedge * alpha = 2 pi the full ring.  Cells are
+    numbered (wedge, iz, ir) with ir fastest.  Tags: 0 the inner surface
+    (r = r_in), 1 the outer one, 2 z = 0, 3 z = Lz, and on an open ring 4 the
+    side at theta = -alpha/2 and 5 the side at theta = -alpha/2 + nwedge alpha."""
+    if not (0.0 < r_in < r_out) or nr < 1 or nz < 1 or nwedge < 1 or not (0.0 < alpha * nwedge <= 2.0 * np.pi + 1e-12):
+        raise ValueError("need 0 < r_in < r_out, nr, nz, nwedge >= 1 and nwedge * alpha <= 2 pi")
+    closed = abs(alpha * nwedge - 2.0 * np.pi) < 1e-9
+    nk = nwedge if closed else nwedge + 1        # distinct angle lines
+    r = np.linspace(r_in, r_out, nr + 1)
+    z = np.linspace(0.0, Lz, nz + 1)
+    pts = []
+    for k in range(nk):
+        th = -0.5 * alpha + k * alpha
+        for iz in range(nz + 1):
+            for ir in range(nr + 1):
+                pts.append((r[ir] * np.cos(th), r[ir] * np.sin(th), z[iz]))
+    vid = lambda k, ir, iz: ((k % nk) * (nz + 1) + iz) * (nr + 1) + ir
+    el, b = [], {}
+    for k in range(nwedge):
+        for iz in range(nz):
+            for ir in range(nr):
+                el.append(("hex", (vid(k, ir, iz), vid(k, ir + 1, iz), vid(k + 1, ir + 1, iz), vid(k + 1, ir, iz),
+                                   vid(k, ir, iz + 1), vid(k, ir + 1, iz + 1), vid(k + 1, ir + 1, iz + 1),
+                                   vid(k + 1, ir, iz + 1))))
+        for iz in range(nz):
+            b[frozenset((vid(k, 0, iz), vid(k + 1, 0, iz), vid(k + 1, 0, iz + 1), vid(k, 0, iz + 1)))] = 0
+            b[frozenset((vid(k, nr, iz), vid(k + 1, nr, iz), vid(k + 1, nr, iz + 1), vid(k, nr, iz + 1)))] = 1
+        for ir in range(nr):
+            b[frozenset((vid(k, ir, 0), vid(k, ir + 1, 0), vid(k + 1, ir + 1, 0), vid(k + 1, ir, 0)))] = 2
+            b[frozenset((vid(k, ir, nz), vid(k, ir + 1, nz), vid(k + 1, ir + 1, nz), vid(k + 1, ir, nz)))] = 3
+    if not closed:
+        for iz in range(nz):
+            for ir in range(nr):
+                b[frozenset((vid(0, ir, iz), vid(0, ir + 1, iz), vid(0, ir + 1, iz + 1), vid(0, ir, iz + 1)))] = 4
+                b[frozenset((vid(nwedge, ir, iz), vid(nwedge, ir + 1, iz), vid(nwedge, ir + 1, iz + 1),
+                             vid(nwedge, ir, iz + 1)))] = 5
+    return from_elements(np.array(pts), el, b)
+
+
 def _box_face_tris(c, quad, t):
     """Both triangulations of a box face (the split around the main diagonal
     uses one of them); each triangle keyed to tag t."""
