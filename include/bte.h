@@ -47,9 +47,10 @@ extern "C" {
 /* ---- enumerations ---- */
 enum { BTE_DIRS_INPLANE = 0, BTE_DIRS_POLAR_AZIM = 1 };
 enum { BTE_FP64 = 0, BTE_FP32 = 1, BTE_BF16 = 2 };
-enum { BTE_BC_ISOTHERMAL = 0, BTE_BC_SPECULAR = 1, BTE_BC_DIFFUSE = 2, BTE_BC_PARTIAL = 3 };
+enum { BTE_BC_ISOTHERMAL = 0, BTE_BC_SPECULAR = 1, BTE_BC_DIFFUSE = 2, BTE_BC_PARTIAL = 3,
+       BTE_BC_ROTATIONAL = 4 /* unstructured meshes only (bte_umesh.h) */ };
 enum { BTE_IMPLICIT_JACOBI = 0, BTE_EXPLICIT = 1, BTE_IMPLICIT_GS = 2 };
-enum { BTE_T_PSEUDO = 0, BTE_T_LATTICE = 1 };
+enum { BTE_T_PSEUDO = 0, BTE_T_LATTICE = 1, BTE_E_LATTICE = 2 };
 
 typedef struct bte_ctx* bte_handle;
 
@@ -92,14 +93,18 @@ typedef struct {
  *             (default) keeps tau fixed; |beta_T_exp| <= 16.  The factor is
  *             common to all bands, so the T_p equation keeps its root.
  *  fp64_strict BTE_FP64 only.  0 (default): the implicit point-Jacobi sweep
- *             of a handle with fixed relaxation rates and isothermal or mirror
- *             walls keeps its inner iterates in double-float form (two floats,
- *             48-bit significand) and computes the update on the FP32 pipe
- *             with error-free transformations; storage between time steps,
- *             the reduction, the temperature solve and I0 stay IEEE FP64.  The
- *             update then rounds to about 2^-48 relative instead of 2^-53,
- *             for |I| in [2^-74, 2^127) (smaller values keep a float's 24
- *             bits).  1: every update in IEEE FP64 arithmetic (DFMA). */
+ *             (ninner >= 2) of a handle with fixed relaxation rates and
+ *             isothermal or mirror walls keeps the intensity in double-float
+ *             form (two floats, 48-bit significand) and computes the update on
+ *             the FP32 pipe with error-free transformations; the reduction,
+ *             the temperature solve and I0 stay IEEE FP64.  Between such steps
+ *             the intensity stays in that form; every call that reads or
+ *             writes intensities (bte_get_intensity, bte_set_intensity,
+ *             bte_get_flux, bte_get_wall_flux_noalloc, bte_set_initial) or
+ *             steps another way converts it to FP64 in place first (one
+ *             kernel).  The update rounds to about 2^-48 relative instead of
+ *             2^-53, for |I| in [2^-74, 2^127) (smaller values keep a float's
+ *             24 bits).  1: every update in IEEE FP64 arithmetic (DFMA). */
 typedef struct {
   int dir_kind;
   int n_inplane, n_polar, n_azim;
@@ -253,7 +258,11 @@ int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t repor
  * BTE_T_PSEUDO (T_p, the temperature whose equilibrium I0_b(T_p) the
  * relaxation term of Eq. 4 drives toward: sum_b W beta_b I0_b(T_p)/v_b =
  * sum_b beta_b G_b/v_b) or BTE_T_LATTICE (T_L, the energy-equivalent
- * temperature: sum_b W I0_b(T_L)/v_b = sum_b G_b/v_b), G_b = sum_d w_d I_{d,b}.  out: ncells doubles, host or device
+ * temperature: sum_b W I0_b(T_L)/v_b = sum_b G_b/v_b), G_b = sum_d w_d I_{d,b};
+ * or, with which = BTE_E_LATTICE, the right-hand side of the T_L equation
+ * itself, E_L = sum_b G_b/v_b, the cell's energy density (J/m^3) after the
+ * last inner iteration (what Sec. 2.2's first-law temperature update works
+ * from; cell volume times E_L summed over cells is the stored energy).  out: ncells doubles, host or device
  * (out_on_device != 0).  Waits for the stream. */
 int bte_get_T(bte_handle h, int geom, int which, double* out, int out_on_device);
 

@@ -51,6 +51,8 @@ typedef struct bte_umesh_ctx* bte_umesh;
  *  nA         [nfaces][3] area vector, pointing out of the owner.
  *  tag        [nfaces] boundary tag (>= 0) of boundary faces; ignored on
  *             interior faces.
+ *  fc         [nfaces][3] face centres, or NULL; needed only by faces that
+ *             take BTE_BC_ROTATIONAL.
  * A cell may have at most 64 faces. */
 typedef struct {
   int dim;
@@ -60,6 +62,7 @@ typedef struct {
   const long long* neighbor;
   const double* nA;
   const int* tag;
+  const double* fc;
 } bte_umesh_desc;
 
 /* Creates a handle.  opts: as in bte.h (precision BTE_FP64, BTE_FP32 or
@@ -78,11 +81,21 @@ int bte_umesh_set_bands(bte_umesh u, int nb, const double* omega_lo, const doubl
 /* Condition of every boundary face with tag `tag`.  type: BTE_BC_ISOTHERMAL
  * (T_faces: host [nfaces] temperatures indexed by face id, read on this
  * tag's faces, or NULL for T_uniform), BTE_BC_SPECULAR or BTE_BC_DIFFUSE
- * (T ignored), or BTE_BC_PARTIAL (an extension beyond the paper's walls, as
+ * (T ignored), BTE_BC_PARTIAL (an extension beyond the paper's walls, as
  * bte_set_specularity: every incoming direction gets p x the mirrored value
  * + (1 - p) x the diffuse value; p from T_faces indexed by face id, or
- * T_uniform when T_faces is NULL, each in [0, 1]).  Specular and partial
- * faces must be normal to an axis.  A tag no boundary face carries, an
+ * T_uniform when T_faces is NULL, each in [0, 1]), or BTE_BC_ROTATIONAL (the
+ * axisymmetric problems of Sec. 3.1: the mesh is one wedge of angle alpha =
+ * T_uniform radians of a body of revolution about the z axis, and these are
+ * its two side faces, planes through the axis; across a side face lies the
+ * wedge itself rotated by alpha, so the ghost of direction s is the owner's
+ * own intensity in s rotated back by alpha, which sends the flux through the
+ * side faces from one azimuthal direction to the next (the discrete angular
+ * redistribution); the sense per face follows from its outward normal against
+ * e_theta at its centre (the mesh needs fc); alpha must map the direction set
+ * onto itself (polar x azimuthal sets: a multiple of the azimuthal bin width;
+ * in-plane sets: of 2 pi / n), and every rotational tag takes the same
+ * alpha).  Specular and partial faces must be normal to an axis.  A tag no boundary face carries, an
  * unknown type or a value out of range returns BTE_E_ARG and changes
  * nothing.  May be called again after bte_umesh_set_initial to change a
  * tag's condition for the following steps. */

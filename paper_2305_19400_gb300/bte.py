@@ -22,9 +22,9 @@ BTE_E = {-1: "BTE_E_ARG", -2: "BTE_E_STATE", -3: "BTE_E_CUDA", -4: "BTE_E_NOMEM"
  BTE_E_EXCHANGE) = -1, -2, -3, -4, -5, -6, -7
 BTE_DIRS_INPLANE, BTE_DIRS_POLAR_AZIM = 0, 1
 BTE_FP64, BTE_FP32, BTE_BF16 = 0, 1, 2
-BTE_BC_ISOTHERMAL, BTE_BC_SPECULAR, BTE_BC_DIFFUSE, BTE_BC_PARTIAL = 0, 1, 2, 3
+BTE_BC_ISOTHERMAL, BTE_BC_SPECULAR, BTE_BC_DIFFUSE, BTE_BC_PARTIAL, BTE_BC_ROTATIONAL = 0, 1, 2, 3, 4
 BTE_IMPLICIT_JACOBI, BTE_EXPLICIT, BTE_IMPLICIT_GS = 0, 1, 2
-BTE_T_PSEUDO, BTE_T_LATTICE = 0, 1
+BTE_T_PSEUDO, BTE_T_LATTICE, BTE_E_LATTICE = 0, 1, 2
 
 
 class bte_geom(C.Structure):
@@ -52,7 +52,8 @@ class bte_stats(C.Structure):
 class bte_umesh_desc(C.Structure):
     _fields_ = [("dim", C.c_int), ("ncells", C.c_longlong), ("nfaces", C.c_longlong),
                 ("volume", C.POINTER(C.c_double)), ("owner", C.POINTER(C.c_longlong)),
-                ("neighbor", C.POINTER(C.c_longlong)), ("nA", C.POINTER(C.c_double)), ("tag", C.POINTER(C.c_int))]
+                ("neighbor", C.POINTER(C.c_longlong)), ("nA", C.POINTER(C.c_double)), ("tag", C.POINTER(C.c_int)),
+                ("fc", C.POINTER(C.c_double))]
 
 
 # Every symbol include/bte.h and include/bte_umesh.h declare, with its ctypes signature.
@@ -462,9 +463,10 @@ class UMeshSolver:
 
     bc: {tag: (kind, T)} with kind BTE_BC_ISOTHERMAL (T a float, or an array
     over the mesh's faces indexed by face id), BTE_BC_SPECULAR or
-    BTE_BC_DIFFUSE (T ignored), or BTE_BC_PARTIAL (T the specularity p, a
-    float or an array over the faces).  beta_exp: relaxation rates
-    beta_b (T_p / T_ref)^beta_exp per cell (0: tau fixed)."""
+    BTE_BC_DIFFUSE (T ignored), BTE_BC_PARTIAL (T the specularity p, a
+    float or an array over the faces), or BTE_BC_ROTATIONAL (T the wedge
+    angle of an axisymmetric mesh, mesh.wedge_ring).  beta_exp: relaxation
+    rates beta_b (T_p / T_ref)^beta_exp per cell (0: tau fixed)."""
 
     def __init__(self, mesh, dirs, bands, bc, T_init=None, stream=None, n_gauss=16, precision=BTE_FP64,
                  beta_exp=0.0, T_ref=300.0):
@@ -485,8 +487,9 @@ class UMeshSolver:
                       np.ascontiguousarray(mesh.owner, dtype=np.int64),
                       np.ascontiguousarray(mesh.neighbor, dtype=np.int64),
                       np.ascontiguousarray(mesh.nA, dtype=np.float64),
-                      np.ascontiguousarray(mesh.tag, dtype=np.int32)]
-        vol, own, nbr, nA, tag = self._keep
+                      np.ascontiguousarray(mesh.tag, dtype=np.int32),
+                      np.ascontiguousarray(mesh.face_center, dtype=np.float64)]
+        vol, own, nbr, nA, tag, fc = self._keep
         d = bte_umesh_desc()
         d.dim, d.ncells, d.nfaces = mesh.dim, mesh.ncells, mesh.nfaces
         d.volume = vol.ctypes.data_as(_dp)
@@ -494,6 +497,7 @@ class UMeshSolver:
         d.neighbor = nbr.ctypes.data_as(C.POINTER(C.c_longlong))
         d.nA = nA.ctypes.data_as(_dp)
         d.tag = tag.ctypes.data_as(_ip)
+        d.fc = fc.ctypes.data_as(_dp)
         h = C.c_void_p()
         _ucheck(None, lib().bte_umesh_create(C.byref(d), C.byref(o), C.byref(h)))
         self.h = h

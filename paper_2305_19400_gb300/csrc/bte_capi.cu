@@ -64,6 +64,7 @@ struct bte_ctx {
   // CUDA graphs of one time step, keyed by (scheme, ninner, starting buffer)
   struct GraphEntry {
     int scheme, ninner, cur_in, cur_out;
+    bool ff_in;  // the step starts from ff pairs
     cudaGraphExec_t exec;
   };
   std::vector<GraphEntry> graphs;
@@ -81,6 +82,11 @@ struct bte_ctx {
   bool ws_owned = false, mem_ready = false;
   char* Ibuf[3] = {nullptr, nullptr, nullptr};
   int cur = 0;
+  // FP64 handles whose Jacobi steps run in double-float arithmetic keep the
+  // current intensity buffer as ff pairs between steps; every entry point that
+  // reads or writes intensities (or steps another way) first converts it to
+  // doubles in place (ensure_state_doubles)
+  bool state_ff = false;
   double *I0cell = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr, *I0wall = nullptr;
   void* coef = nullptr;
   void* coef_ff = nullptr;  // FP64: the coefficients as double-float pairs (bte_ff.cuh layout)
@@ -626,10 +632,28 @@ bool ff_sweep(const bte_ctx* h) {
   return true;
 }
 
+// The current intensity buffer as doubles (in place) when it holds ff pairs.
+cudaError_t ensure_state_doubles(bte_ctx* h) {
+  if (!h->state_ff) return cudaSuccess;
+  const cudaError_t e = launch_ff_to_doubles(h->Ibuf[h->cur], (long long)h->ncells * h->nd * h->nbp / 2, h->stream);
+  if (e == cudaSuccess) h->state_ff = false;
+  return e;
+}
+
+// A timing event on stream s: inside a stream capture it must become an event
+// record node of the graph (cudaEventRecordExternal), so that every replay
+// records it and the host can read it.
+cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &st);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecordWithFlags(ev, s, st == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
 // One time step: ninner sweeps rotating the three intensity buffers from *cur.
 // scheme BTE_IMPLICIT_GS runs the sweep-ordered pass and the per-cell step as
 // two kernels in place of the fused Jacobi sweep.
-cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaStream_t s, int* cur) {
+cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaStream_t s, int* cur, bool* state_ff) {
   int dim = 2;
   for (auto& g : h->geoms) dim = std::max(dim, g.dim);
   const int n = *cur;
@@ -638,14 +662,16 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaSt
   // the third buffer: iteration 0 reads I^n and writes I^1 and B; iteration k
   // reads B and I^k and overwrites the buffer I^n (or I^{k-2}) was in.
   const bool use_b = h->opts.precision == BTE_FP64 && !a.explicit_scheme && ninner >= 2 && !a.dry;
-  // double-float Jacobi sweeps: I^n in doubles -> ff iterates and B -> doubles again
+  // double-float Jacobi sweeps: every iterate and B as ff pairs; the first
+  // inner iteration reads I^n in the state's format
   const bool use_ff = use_b && scheme == BTE_IMPLICIT_JACOBI && ff_sweep(h);
+  if (*state_ff && !use_ff) return cudaErrorInvalidValue;  // the caller converts the state first
   int z = -1;
   for (int it = 0; it < ninner; ++it) {
     int o = 0;
     a.bmode = 0;
     a.Bout = nullptr;
-    a.ff = use_ff ? (it == 0 ? 2 : (it == ninner - 1 ? 1 : 3)) : 0;
+    a.ff = use_ff ? (it == 0 && !*state_ff ? 2 : 3) : 0;
     if (use_b && it == 0) {
       while (o == n) ++o;
       z = 0;
@@ -667,7 +693,7 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaSt
     if (e == cudaSuccess) e = refresh_diffuse(h, a.Ik, s);
     if (e == cudaSuccess) e = refresh_partial(h, a.Ik, s);
     const bool timed = h->time_sweeps && 2 * it + 1 < (int)h->tev.size();
-    if (e == cudaSuccess && timed) e = cudaEventRecord(h->tev[2 * it], s);
+    if (e == cudaSuccess && timed) e = record_timing_event(h->tev[2 * it], s);
     if (scheme == BTE_IMPLICIT_GS) {
       if (e == cudaSuccess && a.beta_exp != 0.0)
         e = launch_beta_scale(h->bscale, h->Tp, a.beta_Tref, a.beta_exp, h->ncells, s);
@@ -676,7 +702,7 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaSt
     } else if (e == cudaSuccess) {
       e = launch_sweep(h->opts.precision, h->pd, a, dim, h->threads, h->grid, s);
     }
-    if (e == cudaSuccess && timed) e = cudaEventRecord(h->tev[2 * it + 1], s);
+    if (e == cudaSuccess && timed) e = record_timing_event(h->tev[2 * it + 1], s);
     if (e == cudaSuccess && a.partial) {
       // band-range handle: the caller sums the per-cell (E_L, E_p) partials over
       // the ranks that hold the other bands, then every rank solves every cell
@@ -699,6 +725,7 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaSt
     k = o;
   }
   *cur = k;
+  if (use_ff) *state_ff = true;
   return cudaSuccess;
 }
 
@@ -711,6 +738,10 @@ int flux_view(bte_ctx* h, int geom, FluxView* out) {
   if (rc) return rc;
   if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "geometry %d has no state", geom);
   const bte_geom& g = h->geoms[geom];
+  {
+    const cudaError_t e = ensure_state_doubles(h);
+    if (e != cudaSuccess) return fail(h, BTE_E_CUDA, "state conversion: %s", cudaGetErrorString(e));
+  }
   out->precision = h->opts.precision;
   out->I = (const double*)h->Ibuf[h->cur];
   {  // diffuse and partially specular wall ghosts of the current state (kernel launches, no allocation)
@@ -993,6 +1024,7 @@ int bte_set_initial(bte_handle h, int geom, const double* T_cells, double T_unif
   for (double t : T)
     if (!(t >= kTmin && t <= kTmax)) return fail(h, BTE_E_ARG, "initial temperature %g outside [1, 5000] K", t);
   if ((rc = ensure_memory(h))) return rc;
+  CUDA_TRY(h, ensure_state_doubles(h));  // the other geometries keep their state
   CUDA_TRY(h, cudaMemcpyAsync(h->scratch_T, T.data(), nc * 8, cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, launch_init_cells(h->opts.precision, h->Ibuf[h->cur], h->I0cell, h->J, h->Msum, h->Tp, h->Teval, h->TL, h->EL,
                                 h->scratch_T, h->I0ref_o, h->cell0[geom], (int)nc, h->nd, thermo(h), h->stream));
@@ -1029,6 +1061,8 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
   const bool ranged = h->Epart != nullptr;
   if (ranged && !h->exchange) return fail(h, BTE_E_STATE, "a band-range handle needs bte_set_exchange before stepping");
   h->exchange_rc = 0;
+  const bool ff_step = h->opts.precision == BTE_FP64 && scheme == BTE_IMPLICIT_JACOBI && ninner >= 2 && ff_sweep(h);
+  if (!ff_step && nsteps > 0) CUDA_TRY(h, ensure_state_doubles(h));
   if (h->time_sweeps && nsteps > 0) {
     if ((int)h->tev.size() < 2 * ninner) {  // events for every sweep of a step; graphs captured before lack them
       drop_graphs(h);
@@ -1045,13 +1079,17 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
       cudaGraphExec_t exec = nullptr;
       int cur_out = -1;
       for (auto& e : h->graphs)
-        if (e.scheme == scheme && e.ninner == ninner && e.cur_in == h->cur) { exec = e.exec; cur_out = e.cur_out; }
+        if (e.scheme == scheme && e.ninner == ninner && e.cur_in == h->cur && e.ff_in == h->state_ff) {
+          exec = e.exec;
+          cur_out = e.cur_out;
+        }
       if (!exec) {
         if (!h->cap_stream) CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
         CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
         int cur = h->cur;
-        cudaError_t e = enqueue_step(h, a, ninner, scheme, h->cap_stream, &cur);
+        bool sff = h->state_ff;
+        cudaError_t e = enqueue_step(h, a, ninner, scheme, h->cap_stream, &cur, &sff);
         cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
           if (graph) cudaGraphDestroy(graph);
@@ -1060,13 +1098,14 @@ int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_st
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return fail(h, BTE_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
-        h->graphs.push_back({scheme, ninner, h->cur, cur, exec});
+        h->graphs.push_back({scheme, ninner, h->cur, cur, h->state_ff, exec});
         cur_out = cur;
       }
       CUDA_TRY(h, cudaGraphLaunch(exec, s));
       h->cur = cur_out;
+      if (ff_step) h->state_ff = true;
     } else {
-      const cudaError_t e = enqueue_step(h, a, ninner, scheme, s, &h->cur);
+      const cudaError_t e = enqueue_step(h, a, ninner, scheme, s, &h->cur, &h->state_ff);
       if (e != cudaSuccess && h->exchange_rc)
         return fail(h, BTE_E_EXCHANGE, "the exchange callback returned %d", h->exchange_rc);
       CUDA_TRY(h, e);
@@ -1177,6 +1216,7 @@ int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t repor
     return fail(h, BTE_E_ARG, "unknown scheme %d", scheme);
   int rc = ensure_coef(h, dt, scheme == BTE_EXPLICIT ? BTE_EXPLICIT : BTE_IMPLICIT_JACOBI);
   if (rc) return rc;
+  if (scheme != BTE_IMPLICIT_JACOBI || !ff_sweep(h)) CUDA_TRY(h, ensure_state_doubles(h));  // timed reads of doubles
   if (scheme == BTE_IMPLICIT_GS) return autotune_gs(h, report, report_len);
   cudaStream_t s = h->stream;
   int sms = 152;
@@ -1257,11 +1297,15 @@ int bte_get_T(bte_handle h, int geom, int which, double* out, int on_device) {
   if (rc) return rc;
   if (!out) return fail(h, BTE_E_ARG, "out is NULL");
   if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "geometry %d has no state", geom);
-  if (which != BTE_T_PSEUDO && which != BTE_T_LATTICE) return fail(h, BTE_E_ARG, "which must be BTE_T_PSEUDO or BTE_T_LATTICE");
+  if (which != BTE_T_PSEUDO && which != BTE_T_LATTICE && which != BTE_E_LATTICE)
+    return fail(h, BTE_E_ARG, "which must be BTE_T_PSEUDO, BTE_T_LATTICE or BTE_E_LATTICE");
   const bte_geom& g = h->geoms[geom];
   const size_t nc = (size_t)g.nx * g.ny * g.nz;
   const double* src;
-  if (which == BTE_T_PSEUDO && h->solve_tp) {
+  if (which == BTE_E_LATTICE) {
+    if (h->EL_partial) return fail(h, BTE_E_STATE, "E_L of a band-range handle needs a step after bte_set_intensity");
+    src = h->EL;
+  } else if (which == BTE_T_PSEUDO && h->solve_tp) {
     src = h->Tp;
   } else {
     if (h->EL_partial) return fail(h, BTE_E_STATE, "T_L of a band-range handle needs a step after bte_set_intensity");
@@ -1277,6 +1321,7 @@ int bte_get_flux(bte_handle h, int geom, double* q_cells, double* q_walls, int o
   if (!h->mem_ready || !h->init_set[geom]) return fail(h, BTE_E_STATE, "geometry %d has no state", geom);
   const bte_geom& g = h->geoms[geom];
   const int nc = g.nx * g.ny * g.nz;
+  CUDA_TRY(h, ensure_state_doubles(h));
   const void* I = h->Ibuf[h->cur];
   const int prec = h->opts.precision;
   cudaStream_t s = h->stream;
@@ -1316,6 +1361,7 @@ int bte_get_intensity(bte_handle h, int geom, double* out, int on_device) {
   const long long nc = (long long)g.nx * g.ny * g.nz;
   const int prec = h->opts.precision;
   const size_t es = elem_bytes(prec);
+  CUDA_TRY(h, ensure_state_doubles(h));
   const char* I = h->Ibuf[h->cur] + (size_t)h->cell0[geom] * h->nd * h->nbp * es;
   if (on_device) {
     CUDA_TRY(h, launch_pack(prec, nullptr, out, I, nullptr, h->I0ref_o, nc, h->nd, h->nb, h->nbp, 0, h->stream));
@@ -1343,6 +1389,7 @@ int bte_set_intensity(bte_handle h, int geom, const double* in, const double* Tp
   const long long nc = (long long)g.nx * g.ny * g.nz;
   const int prec = h->opts.precision;
   const size_t es = elem_bytes(prec);
+  CUDA_TRY(h, ensure_state_doubles(h));  // the other geometries keep their state
   char* I = h->Ibuf[h->cur] + (size_t)h->cell0[geom] * h->nd * h->nbp * es;
   cudaStream_t s = h->stream;
   if (on_device) {

@@ -91,6 +91,16 @@ __device__ __forceinline__ P2 mul(const P2& c, const P2& u) {
   return p;
 }
 
+// x + y of two (unnormalised) pairs: TwoSum of the high parts, the low parts
+// and the rounding error added (left unnormalised).
+__device__ __forceinline__ P2 add(const P2& x, const P2& y) {
+  P2 r;
+  x2 e;
+  two_sum(x.h, y.h, r.h, e);
+  r.l = add(add(x.l, y.l), e);
+  return r;
+}
+
 // s += p (s left unnormalised: its low part collects p's and the rounding error).
 __device__ __forceinline__ void acc(P2& s, const P2& p) {
   x2 h, e;

@@ -114,8 +114,8 @@ struct SweepArgs {
   const void* coef_ff;      // FP64: the same coefficients as double-float pairs, per 16 bytes
                             // (two bands) h_b, h_b+1, l_b, l_b+1; the sum of the five is 1
                             // (implicit) up to the pairs' resolution
-  int ff;                   // FP64: 0 DFMA arithmetic; else the double-float variant
-                            // (bit 0: I^k and B are ff pairs; bit 1: I^{k+1} and B are written as ff)
+  int ff;                   // FP64: 0 DFMA arithmetic; else the double-float variant (bit 0: In and
+                            // I^k are ff pairs; bit 1: I^{k+1} and B are written as ff; B is always ff)
   const void* coef;         // FP64: [cls][5][nd][nbp] A_n, A_x, A_y, A_z, A_s;
                             // reduced: [cls][2][nd][nbp] float P, Q with
                             // I' = P I^n + Q (v_b sum_ax c_ax I_up + beta_b dI0)
@@ -207,6 +207,8 @@ cudaError_t launch_flux_faces(int precision, const void* I, const double* I0ref,
                               const DevGeom* geoms, int geom, int side, const DirInfo* dirs, const double* S, int nd,
                               int nbp, double* face_out, int nfaces, cudaStream_t s);
 cudaError_t launch_mean(const double* v, int n, double* out, cudaStream_t s);
+// In place: npairs 16-byte ff pairs of two bands (bte_ff.cuh layout) -> two doubles each.
+cudaError_t launch_ff_to_doubles(void* buf, long long npairs, cudaStream_t s);
 cudaError_t launch_pack(int precision, const double* src, double* dst_out, const void* Isrc, void* Idst,
                         const double* I0ref, long long ncells, int nd, int nb, int nbp, int to_padded, cudaStream_t s);
 cudaError_t launch_energy_L(int precision, const void* I, const double* I0ref, double* EL, const double* wdir,

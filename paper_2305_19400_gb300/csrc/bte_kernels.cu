@@ -15,6 +15,7 @@
 //                       heat flux, FP64 <-> storage packing, E_L after a restore.
 #include <algorithm>
 
+#include "bte_ff.cuh"
 #include "bte_mlp.cuh"
 #include "bte_quad.cuh"
 #include "bte_solve.cuh"
@@ -792,6 +793,23 @@ cudaError_t launch_flux_faces(int precision, const void* I, const double* I0ref,
   else
     flux_faces_kernel<__nv_bfloat16><<<grid, 256, sm, s>>>((const __nv_bfloat16*)I, I0ref, I0wall, geoms, geom, side, dirs, S,
                                                            nd, nbp, face_out, nfaces);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void ff_to_doubles_kernel(ulonglong2* buf, long long npairs) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npairs; i += (long long)gridDim.x * blockDim.x) {
+    const ulonglong2 v = buf[i];
+    double a, b;
+    ff::to_doubles(ff::P2{v.x, v.y}, a, b);
+    buf[i] = make_ulonglong2((unsigned long long)__double_as_longlong(a), (unsigned long long)__double_as_longlong(b));
+  }
+}
+}  // namespace
+
+cudaError_t launch_ff_to_doubles(void* buf, long long npairs, cudaStream_t s) {
+  if (npairs <= 0) return cudaSuccess;
+  ff_to_doubles_kernel<<<grid_for(npairs, 256), 256, 0, s>>>(reinterpret_cast<ulonglong2*>(buf), npairs);
   return cudaGetLastError();
 }
 

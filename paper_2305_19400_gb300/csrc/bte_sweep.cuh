@@ -135,13 +135,15 @@ struct Ring {
 // FF (FP64 storage only, TT false): 0 the update runs in FP64 (DFMA); otherwise
 // it runs in double-float arithmetic on the FP32 pipe (bte_ff.cuh) with the
 // coefficients of a.coef_ff, and FF says which buffers hold ff pairs instead
-// of doubles: bit 0 the iterate I^k and B (the In operand when BM == 2), bit 1
-// the output I^{k+1} and B (BM == 1).  The first inner iteration of a step
-// reads the doubles of I^n and writes ff (FF = 2), the middle ones stay in ff
-// (FF = 3) and the last writes doubles again (FF = 1), so every buffer that
-// outlives a step holds doubles.  Isothermal wall ghosts are doubles in every
-// variant.  The direction sums G_b are summed in ff per run of equal weights
-// and enter G in ff; G becomes a double once per cell.
+// of doubles: bit 0 the In operand (I^n, or B when BM == 2) and the iterate
+// I^k, bit 1 the output I^{k+1} and B (BM == 1).  B is an ff pair in every
+// variant.  A step from an intensity state in doubles starts with FF = 2 (the
+// first inner iteration converts I^n and I^k as it reads them); every other
+// inner iteration, and every step from a state already in ff pairs, is
+// FF = 3.  The handle converts the state to doubles in place before anything
+// else reads it.  Isothermal wall ghosts are doubles in every variant.  The
+// direction sums G_b are summed in ff per run of equal weights and enter G in
+// ff; G becomes a double once per cell.
 template <int DIM, typename S, int MINB, int BM, bool TT, int FF = 0>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   using T = Tr<S>;
@@ -149,7 +151,6 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   constexpr int V = T::V;
   static_assert(FF == 0 || (sizeof(S) == 8 && !TT), "double-float variants are FP64 storage with fixed rates");
   static_assert(FF == 0 || BM != 2 || (FF & 1) != 0, "B is an ff pair whenever the variant is double-float");
-  static_assert(FF == 0 || BM == 2 || (FF & 1) == 0, "the first inner iteration reads I^n in doubles");
   constexpr bool kDev = sizeof(S) != 8;  // reduced modes store deviations
   extern __shared__ double sm[];
   __shared__ unsigned long long cnt_solves, cnt_bad;
@@ -359,15 +360,19 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
           // double-float update of the lane's two bands (bte_ff.cuh):
           // B (or A_n I^n) + A_x I_x + A_y I_y (+ A_z I_z) + A_s I0
           ff::P2 rf;
-          if constexpr (BM == 2 && (FF & 1)) {
-            rf = ff::lds(sb);
+          if constexpr (BM == 2) {
+            rf = ff::lds(sb);  // B
           } else {
-            rf = ff::norm(ff::mul(ff::ldg(cf + off), ff::lds_doubles(sb)));  // A_n I^n
+            const ff::P2 vin = (FF & 1) ? ff::lds(sb) : ff::lds_doubles(sb);
+            rf = ff::norm(ff::mul(ff::ldg(cf + off), vin));  // A_n I^n
             if constexpr (BM == 1) {
               if constexpr ((FF & 2) != 0) ff::st_stream(c.bout + off, rf);
               else ff::st_stream_doubles(c.bout + off, rf);
             }
           }
+          // the DIM + 1 products are independent; they are summed pairwise with
+          // B (a shorter dependency chain than one running sum)
+          ff::P2 pr[DIM + 1];
 #pragma unroll
           for (int ax = 0; ax < DIM; ++ax) {
             // the upwind operand is an ff pair unless it is I^k in doubles or an
@@ -379,10 +384,14 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
             }
             const unsigned ua = sb + (1 + ax) * ostr;
             const ff::P2 u = dbl ? ff::lds_doubles(ua) : ff::lds(ua);
-            ff::acc(rf, ff::mul(ff::lds(sb + (1 + DIM + ax) * ostr), u));
+            pr[ax] = ff::mul(ff::lds(sb + (1 + DIM + ax) * ostr), u);
           }
-          ff::acc(rf, ff::mul(ff::lds(sb + (1 + 2 * DIM) * ostr), srcff));
-          rf = ff::norm(rf);
+          pr[DIM] = ff::mul(ff::lds(sb + (1 + 2 * DIM) * ostr), srcff);
+          if constexpr (DIM == 2) {
+            rf = ff::norm(ff::add(ff::add(rf, pr[0]), ff::add(pr[1], pr[2])));
+          } else {
+            rf = ff::norm(ff::add(ff::add(ff::add(rf, pr[0]), ff::add(pr[1], pr[2])), pr[3]));
+          }
           if constexpr ((FF & 2) != 0) ff::st_stream(c.out + off, rf);
           else ff::st_stream_doubles(c.out + off, rf);
           // G_b: the run's sum in ff; a new weight closes the run into G
@@ -669,8 +678,8 @@ cudaError_t launch(int variant, const SweepArgs& a, int dim, int threads, int gr
     if (a.ff != 0) {  // double-float arithmetic: the B form with fixed relaxation rates only
       if (a.beta_exp != 0.0) return cudaErrorInvalidValue;
       if (a.bmode == 1 && a.ff == 2) return launch_bm<S, 1, false, 2>(variant, a, dim, threads, grid, s);
+      if (a.bmode == 1 && a.ff == 3) return launch_bm<S, 1, false, 3>(variant, a, dim, threads, grid, s);
       if (a.bmode == 2 && a.ff == 3) return launch_bm<S, 2, false, 3>(variant, a, dim, threads, grid, s);
-      if (a.bmode == 2 && a.ff == 1) return launch_bm<S, 2, false, 1>(variant, a, dim, threads, grid, s);
       return cudaErrorInvalidValue;
     }
     if (a.beta_exp != 0.0) {

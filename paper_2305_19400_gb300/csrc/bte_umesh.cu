@@ -440,13 +440,16 @@ struct bte_umesh_ctx {
   // boundary faces
   std::vector<long long> bface;  // face id of each boundary face
   std::vector<int> bf_tag, bf_type, bf_axis, bf_ok_axis;
+  std::vector<int> bf_geo_axis;  // axis of the face normal; bf_axis is it, or 3 / 4 on rotational faces
+  std::vector<double> fc;        // [nf][3] face centres (empty when the mesh gave none)
+  double rot_alpha = 0.0;        // wedge angle of the rotational faces (0: none set)
   std::vector<double> bf_T, bf_p;  // isothermal temperature / specularity
   std::vector<int> tags;          // distinct boundary tags
   std::vector<char> tag_set;      // per entry of tags
   // directions
   int nd = 0;
   std::vector<double> S, w;
-  std::vector<int> refl;
+  std::vector<int> refl;  // [5][nd]: mirror across x, y, z; rotation about z by -alpha, by +alpha
   double Wtot = 0.0;
   // bands
   bool bands_set = false, solve_tp = false;
@@ -581,7 +584,7 @@ int ensure_mem(bte_umesh_ctx* u) {
       (rc = dalloc(u, &u->S_d, nd * 3)) || (rc = dalloc(u, &u->w_d, nd)) || (rc = dalloc(u, &u->nA_d, u->nf * 3)) ||
       (rc = dalloc(u, &u->vb_d, nbp)) || (rc = dalloc(u, &u->bb_d, nbp)) || (rc = dalloc(u, &u->scratch, nc)) ||
       (rc = dalloc(u, &u->Qb, nbf)) || (rc = dalloc(u, &u->qbuf, nc * 3)) || (rc = dalloc(u, &u->bf_mirror_d, nbf)) || (rc = dalloc(u, &u->bf_axis_d, nbf)) || (rc = dalloc(u, &u->bf_spec_d, nbf)) || (rc = dalloc(u, &u->bscale, nc)) ||
-      (rc = dalloc(u, &u->refl_d, 3 * nd)) || (rc = dalloc(u, &u->bface_d, nbf)) || (rc = dalloc(u, &u->owner_d, u->nf)) ||
+      (rc = dalloc(u, &u->refl_d, 5 * nd)) || (rc = dalloc(u, &u->bface_d, nbf)) || (rc = dalloc(u, &u->owner_d, u->nf)) ||
       (rc = dalloc(u, &u->diff_d, nbf)) || (rc = dalloc(u, &u->fix, nc)) || (rc = dalloc(u, &u->fix_count, 4)) ||
       (rc = dalloc(u, &u->counters, 1)) || (rc = dalloc(u, &u->node_c, nbp * u->ng)) ||
       (rc = dalloc(u, &u->node_C, nbp * u->ng)) || (rc = dalloc(u, &u->a_p, nbp)) || (rc = dalloc(u, &u->a_L, nbp)) ||
@@ -624,7 +627,7 @@ int ensure_mem(bte_umesh_ctx* u) {
       (rc = upload(u, ef_d, ent_face.data(), nent)) || (rc = upload(u, ec_d, ent_cell.data(), nent)) ||
       (rc = upload(u, es_d, ent_sign.data(), nent)) || (rc = upload(u, vol_d, u->vol.data(), nc)) ||
       (rc = upload(u, u->nA_d, u->nA.data(), u->nf * 3)) || (rc = upload(u, u->S_d, u->S.data(), nd * 3)) ||
-      (rc = upload(u, u->w_d, u->w.data(), nd)) || (rc = upload(u, u->refl_d, u->refl.data(), 3 * nd)) ||
+      (rc = upload(u, u->w_d, u->w.data(), nd)) || (rc = upload(u, u->refl_d, u->refl.data(), 5 * nd)) ||
       (rc = upload(u, u->bface_d, u->bface.data(), nbf)) || (rc = upload(u, u->owner_d, u->owner.data(), u->nf)))
     return rc;
   umesh_geom_kernel<<<grid_for(nent * nd, 256), 256, 0, s>>>(ef_d, es_d, ec_d, u->nA_d, vol_d, u->S_d, u->w_d, (int)nd,
@@ -668,6 +671,25 @@ int ensure_mem(bte_umesh_ctx* u) {
   return BTE_OK;
 }
 
+// map[d] = e with S_e = R_z(phi) S_d (rotation about the z axis), matched to
+// 1e-9 of |S_d|; false when some direction has no image in the set.
+bool rotation_map(const std::vector<double>& S, int nd, double phi, int* map) {
+  const double c = std::cos(phi), s = std::sin(phi);
+  for (int d = 0; d < nd; ++d) {
+    const double* v = &S[3 * d];
+    const double r[3] = {c * v[0] - s * v[1], s * v[0] + c * v[1], v[2]};
+    const double tol = 1e-9 * std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    map[d] = -1;
+    for (int e = 0; e < nd && map[d] < 0; ++e) {
+      const double* q = &S[3 * e];
+      const double dx = q[0] - r[0], dy = q[1] - r[1], dz = q[2] - r[2];
+      if (std::sqrt(dx * dx + dy * dy + dz * dz) <= tol) map[d] = e;
+    }
+    if (map[d] < 0) return false;
+  }
+  return true;
+}
+
 // Ghost rows of the boundary faces: isothermal I0_b(T_face) and the mirror /
 // ghost selector of each face (after every tag has a condition).
 int upload_bc(bte_umesh_ctx* u) {
@@ -677,13 +699,14 @@ int upload_bc(bte_umesh_ctx* u) {
   std::vector<double> T(nbf), spec(nbf, 0.0);
   for (long long k = 0; k < nbf; ++k) {
     const int t = u->bf_type[k];
-    mirror[k] = t == BTE_BC_SPECULAR ? 1 : (t == BTE_BC_PARTIAL ? 2 : 0);
+    mirror[k] = (t == BTE_BC_SPECULAR || t == BTE_BC_ROTATIONAL) ? 1 : (t == BTE_BC_PARTIAL ? 2 : 0);
     T[k] = t == BTE_BC_ISOTHERMAL ? u->bf_T[k] : u->opts.T_ref;
     if (t == BTE_BC_PARTIAL) spec[k] = u->bf_p[k];
     if (t == BTE_BC_DIFFUSE || t == BTE_BC_PARTIAL) diffl.push_back(k);
   }
   int rc;
   if ((rc = upload(u, u->bf_mirror_d, mirror.data(), nbf)) || (rc = upload(u, u->bf_axis_d, u->bf_axis.data(), nbf)) ||
+      (rc = upload(u, u->refl_d, u->refl.data(), 5 * (size_t)u->nd)) ||
       (rc = upload(u, u->bf_spec_d, spec.data(), nbf)) ||
       (rc = upload(u, u->bfT_d, T.data(), nbf)) || (rc = upload(u, u->diff_d, diffl.data(), diffl.size())))
     return rc;
@@ -777,6 +800,7 @@ int bte_umesh_create(const bte_umesh_desc* m, const bte_opts* opts, bte_umesh* o
       if (std::fabs(a[c]) > std::fabs(a[ax])) ax = c;
     const double off = std::sqrt(a[(ax + 1) % 3] * a[(ax + 1) % 3] + a[(ax + 2) % 3] * a[(ax + 2) % 3]);
     u->bf_axis.push_back(ax);
+    u->bf_geo_axis.push_back(ax);
     u->bf_ok_axis.push_back(off <= 1e-12 * std::fabs(a[ax]) ? 1 : 0);
     if (std::find(u->tags.begin(), u->tags.end(), u->tag[f]) == u->tags.end()) u->tags.push_back(u->tag[f]);
   }
@@ -789,6 +813,9 @@ int bte_umesh_create(const bte_umesh_desc* m, const bte_opts* opts, bte_umesh* o
     return ufail(nullptr, BTE_E_ARG, "bad direction set");
   }
   u->nd = (int)u->w.size();
+  u->refl.resize(5 * (size_t)u->nd);
+  for (int d = 0; d < u->nd; ++d) u->refl[3 * u->nd + d] = u->refl[4 * u->nd + d] = d;  // until a rotation is set
+  if (m->fc) u->fc.assign(m->fc, m->fc + 3 * m->nfaces);
   if (u->nd > 2048) {
     delete u;
     return ufail(nullptr, BTE_E_ARG, "at most 2048 directions");
@@ -833,10 +860,31 @@ int bte_umesh_set_bc(bte_umesh u, int tag, int type, const double* T_faces, doub
   if (!u->mem_ready) return ufail(u, BTE_E_STATE, "bte_umesh_set_bands must come first");
   const auto it = std::find(u->tags.begin(), u->tags.end(), tag);
   if (it == u->tags.end()) return ufail(u, BTE_E_ARG, "no boundary face has tag %d", tag);
-  if (type != BTE_BC_ISOTHERMAL && type != BTE_BC_SPECULAR && type != BTE_BC_DIFFUSE && type != BTE_BC_PARTIAL)
+  if (type != BTE_BC_ISOTHERMAL && type != BTE_BC_SPECULAR && type != BTE_BC_DIFFUSE && type != BTE_BC_PARTIAL &&
+      type != BTE_BC_ROTATIONAL)
     return ufail(u, BTE_E_ARG, "unknown boundary type %d", type);
+  std::vector<int> rot(2 * (size_t)u->nd);
+  if (type == BTE_BC_ROTATIONAL) {
+    const double alpha = T_uniform;
+    if (u->fc.empty()) return ufail(u, BTE_E_ARG, "tag %d: rotational faces need the face centres (fc) of the mesh", tag);
+    if (!(std::isfinite(alpha) && alpha > 0.0 && alpha < kPi))
+      return ufail(u, BTE_E_ARG, "tag %d: the wedge angle must lie in (0, pi)", tag);
+    if (u->rot_alpha != 0.0 && u->rot_alpha != alpha)
+      return ufail(u, BTE_E_ARG, "tag %d: every rotational tag takes the same wedge angle (%g set before)", tag,
+                   u->rot_alpha);
+    if (!rotation_map(u->S, u->nd, -alpha, rot.data()) || !rotation_map(u->S, u->nd, alpha, rot.data() + u->nd))
+      return ufail(u, BTE_E_ARG, "tag %d: a rotation by %g rad does not map the direction set onto itself", tag, alpha);
+  }
   for (size_t k = 0; k < u->bface.size(); ++k) {
     if (u->bf_tag[k] != tag) continue;
+    if (type == BTE_BC_ROTATIONAL) {  // a plane through the z axis
+      const double* a = &u->nA[3 * u->bface[k]];
+      const double* c = &u->fc[3 * u->bface[k]];
+      const double an = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      const double cr = std::sqrt(c[0] * c[0] + c[1] * c[1]);
+      if (!(cr > 0.0) || std::fabs(a[2]) > 1e-12 * an || std::fabs(a[0] * c[0] + a[1] * c[1]) > 1e-9 * an * cr)
+        return ufail(u, BTE_E_ARG, "tag %d: face %lld is not a plane through the z axis", tag, u->bface[k]);
+    }
     if ((type == BTE_BC_SPECULAR || type == BTE_BC_PARTIAL) && !u->bf_ok_axis[k])
       return ufail(u, BTE_E_ARG, "tag %d: face %lld is not normal to an axis (a mirror needs that)", tag, u->bface[k]);
     if (type == BTE_BC_PARTIAL) {
@@ -854,6 +902,16 @@ int bte_umesh_set_bc(bte_umesh u, int tag, int type, const double* T_faces, doub
     u->bf_type[k] = type;
     u->bf_T[k] = type == BTE_BC_ISOTHERMAL ? (T_faces ? T_faces[u->bface[k]] : T_uniform) : 0.0;
     u->bf_p[k] = type == BTE_BC_PARTIAL ? (T_faces ? T_faces[u->bface[k]] : T_uniform) : 0.0;
+    u->bf_axis[k] = u->bf_geo_axis[k];
+    if (type == BTE_BC_ROTATIONAL) {  // outward along +e_theta: the far side, ghost rotated back by -alpha (row 3)
+      const double* a = &u->nA[3 * u->bface[k]];
+      const double* c = &u->fc[3 * u->bface[k]];
+      u->bf_axis[k] = (-c[1] * a[0] + c[0] * a[1]) > 0.0 ? 3 : 4;
+    }
+  }
+  if (type == BTE_BC_ROTATIONAL) {
+    u->rot_alpha = T_uniform;
+    std::copy(rot.begin(), rot.end(), u->refl.begin() + 3 * (size_t)u->nd);
   }
   u->tag_set[it - u->tags.begin()] = 1;
   for (char c : u->tag_set)
