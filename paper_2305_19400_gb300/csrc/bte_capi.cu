@@ -90,6 +90,11 @@ struct bte_ctx {
   double *I0cell = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr, *I0wall = nullptr;
   void* coef = nullptr;
   void* coef_ff = nullptr;  // FP64: the coefficients as double-float pairs (bte_ff.cuh layout)
+  // FP64: tables of the factored double-float sweep (bte_sweep_ff.cuh)
+  void* coef_R = nullptr;     // [cls][nd][nbp] R pairs
+  float* dirc_ff = nullptr;   // [cls][nd][3][2]
+  float* band_ff = nullptr;   // [2][nbp] v_b, beta_b pairs
+  float rdt_ff[2] = {0.0f, 0.0f};
   double *J = nullptr, *Teval = nullptr, *I0ref = nullptr, *scratch_pack = nullptr;
   double* Msum = nullptr;     // [cell][3] the T_p model's sums sum_b a_p,b J_k,b
   double* I0ref_o = nullptr;  // I0_b(T_ref) of the stored bands (aliases I0ref unless a band range is set)
@@ -119,7 +124,7 @@ struct bte_ctx {
   double coef_dt = -1.0;
   int coef_scheme = -1;
   std::vector<double> coef_host;
-  std::vector<float> coef_ff_host;
+  std::vector<float> coef_ff_host, R_host, dirc_host, band_host;
   // per-launch timing of the sweeps (bte_set_sweep_timing): events around each
   // sweep of a step, recorded on the stream (captured into the step's graph)
   bool time_sweeps = false;
@@ -211,6 +216,9 @@ size_t carve(bte_ctx* h, char* base) {
   h->I0wall = (double*)take((size_t)std::max(h->nfaces, 1LL) * h->nbp * 8);
   h->coef = take((size_t)h->cls_key.size() * row * (h->opts.precision == BTE_FP64 ? 5 * 8 : 2 * 4));
   h->coef_ff = h->opts.precision == BTE_FP64 ? take((size_t)h->cls_key.size() * row * 5 * 8) : nullptr;
+  h->coef_R = h->opts.precision == BTE_FP64 ? take((size_t)h->cls_key.size() * row * 8) : nullptr;
+  h->dirc_ff = h->opts.precision == BTE_FP64 ? (float*)take((size_t)h->cls_key.size() * h->nd * 6 * 4) : nullptr;
+  h->band_ff = h->opts.precision == BTE_FP64 ? (float*)take((size_t)h->nbp * 4 * 4) : nullptr;
   h->dirc = (float4*)take((size_t)h->cls_key.size() * h->nd * sizeof(float4));
   h->vb32 = (float*)take((size_t)h->nbp * 4);
   h->bb32 = (float*)take((size_t)h->nbp * 4);
@@ -470,6 +478,20 @@ int ensure_coef(bte_ctx* h, double dt, int scheme) {
                  h->coef_ff_host.data() + c * 10 * plane);
     CUDA_TRY(h, cudaMemcpyAsync(h->coef_ff, h->coef_ff_host.data(), h->coef_ff_host.size() * 4, cudaMemcpyHostToDevice,
                                 h->stream));
+    // the factored double-float tables (implicit update only)
+    h->R_host.assign(2 * plane * ncls, 0.0f);
+    h->dirc_host.assign(6 * (size_t)h->nd * ncls, 0.0f);
+    h->band_host.assign(4 * (size_t)h->nbp, 0.0f);
+    if (scheme != BTE_EXPLICIT)
+      for (size_t c = 0; c < ncls; ++c) {
+        const double delta[3] = {std::get<1>(h->cls_key[c]), std::get<2>(h->cls_key[c]), std::get<3>(h->cls_key[c])};
+        build_ff_factored(std::get<0>(h->cls_key[c]), delta, h->nd, h->S.data(), h->w.data(), h->nb, h->nbp,
+                          h->vg.data() + h->band0, h->beta.data() + h->band0, dt, h->R_host.data() + c * 2 * plane,
+                          h->dirc_host.data() + c * 6 * (size_t)h->nd, h->band_host.data(), h->rdt_ff);
+      }
+    CUDA_TRY(h, cudaMemcpyAsync(h->coef_R, h->R_host.data(), h->R_host.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->dirc_ff, h->dirc_host.data(), h->dirc_host.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->band_ff, h->band_host.data(), h->band_host.size() * 4, cudaMemcpyHostToDevice, h->stream));
   } else {
     std::vector<float> pq(2 * plane * ncls), dc(4 * (size_t)h->nd * ncls);
     for (size_t c = 0; c < ncls; ++c) {
@@ -552,6 +574,11 @@ SweepArgs sweep_args(bte_ctx* h) {
   a.partial = h->Epart ? 1 : 0;
   a.coef = h->coef;
   a.coef_ff = h->coef_ff;
+  a.coef_R = h->coef_R;
+  a.dirc_ff = h->dirc_ff;
+  a.band_ff = h->band_ff;
+  a.rdt_h = h->rdt_ff[0];
+  a.rdt_l = h->rdt_ff[1];
   a.dirs = h->dirs_d;
   a.wdir = h->wdir;
   a.wdir32 = h->wdir32;

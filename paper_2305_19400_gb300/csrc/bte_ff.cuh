@@ -50,6 +50,9 @@ __device__ __forceinline__ x2 fma(x2 a, x2 b, x2 c) {
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
+// -a by flipping the two sign bits.  (Written as a packed subtract from zero,
+// the negated product in TwoProd's fma(a, b, -fl(a b)) measured float-level
+// errors on GB300: the error term was lost.  The bit flip keeps it exact.)
 __device__ __forceinline__ x2 neg(x2 a) { return a ^ 0x8000000080000000ull; }
 __device__ __forceinline__ x2 pack(float a, float b) {
   return (x2)__float_as_uint(a) | ((x2)__float_as_uint(b) << 32);

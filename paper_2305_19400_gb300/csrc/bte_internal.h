@@ -116,6 +116,12 @@ struct SweepArgs {
                             // (implicit) up to the pairs' resolution
   int ff;                   // FP64: 0 DFMA arithmetic; else the double-float variant (bit 0: In and
                             // I^k are ff pairs; bit 1: I^{k+1} and B are written as ff; B is always ff)
+  // FP64 double-float sweep with factored coefficients (bte_sweep_ff.cuh), tables
+  // in the double-float pair layout of bte_ff.cuh (h_b, h_b+1, l_b, l_b+1 per two bands):
+  const void* coef_R;       // [cls][nd][nbp] R = 1/(1/dt + beta_b + v_b sum_ax c_ax,d)
+  const float* band_ff;     // [2][nbp] v_b, beta_b of the stored bands
+  const float* dirc_ff;     // [cls][nd][3][2] c_ax,d as (h, l)
+  float rdt_h, rdt_l;       // 1/dt as a double-float pair
   const void* coef;         // FP64: [cls][5][nd][nbp] A_n, A_x, A_y, A_z, A_s;
                             // reduced: [cls][2][nd][nbp] float P, Q with
                             // I' = P I^n + Q (v_b sum_ax c_ax I_up + beta_b dI0)

@@ -127,6 +127,125 @@ struct Ring {
   static constexpr int kStages = (kCoef && DIM == 3) ? 3 : 4;
 };
 
+// Lane coordinates of a sweep CTA and the shared regions of its item epilogue.
+struct ItemCtx {
+  int team, cpb, slot, dg, lane, lpc, dstep, b0, wid, wl, nwarps, nbp, nbp_all, band0, nbr;
+  double* gsm;  // [blockDim.x][V] per-lane band partials
+  double* red;  // [cpb * lpc][2] per-band-vector E_L, E_p sums, then [cpb][4] per-cell scratch
+};
+
+// The end of an item of a sweep CTA (every thread calls it; it holds four CTA
+// barriers): G[v] is this lane's partial G_b = sum_d w_d I_{d,b} over its
+// directions (in the reduced modes without the W I0_b(T_ref) term of their
+// deviation storage, which is added here).
+template <int V, bool kDev>
+__device__ __forceinline__ void item_epilogue(const SweepArgs& a, const ItemCtx& x, const WorkItem& wi,
+                                              const DevGeom* gp, const double (&G)[V], unsigned long long& cnt_solves,
+                                              unsigned long long& cnt_bad) {
+  // ---- per-cell reduction.  The lanes of a cell hold band partials over their
+  // direction subsets; the band owners (dg == 0) add them in a fixed order to
+  // G_b, then E_L = sum_b G_b / v_b and E_p = sum_b beta_b G_b / v_b per band
+  // vector.  One warp per cell adds the band vectors (shuffle tree); one warp
+  // then solves every cell's model (lanes over cells), and all threads refresh
+  // the accepted cells' I0.  Four barriers per item: every read of gsm
+  // precedes the second, every read of red the third, and every read of the
+  // per-cell scratch the next item's second.
+  double* gb = x.gsm;
+  double* rb = x.red;
+#pragma unroll
+  for (int v = 0; v < V; ++v) gb[(size_t)threadIdx.x * V + v] = G[v];
+  __syncthreads();
+  if (x.dg == 0) {
+    double eL = 0.0, ep = 0.0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      double Gb = kDev ? a.Wtot * a.I0ref[x.b0 + v] : 0.0;
+      for (int q = 0; q < x.dstep; ++q) Gb += gb[(size_t)(x.slot * x.team + q * x.lpc + x.lane) * V + v];
+      const double e = Gb * a.th.inv_v[x.b0 + v];
+      eL += e;
+      ep = fma(a.th.beta[x.b0 + v], e, ep);
+    }
+    double* r2 = rb + 2 * (size_t)(x.slot * x.lpc + x.lane);
+    r2[0] = eL;
+    r2[1] = ep;
+  }
+  __syncthreads();
+  double* cst = rb + 2 * (size_t)x.cpb * x.lpc;  // [cpb][4]: E_L, E_p, model step, accepted
+  for (int cs = x.wid; x.wid < x.nwarps && cs < wi.cell_count; cs += x.nwarps) {  // warp per cell: E_L, E_p
+    double EL = 0.0, Ep = 0.0;
+    for (int l = x.wl; l < x.lpc; l += 32) {
+      const double* r2 = rb + 2 * (size_t)(cs * x.lpc + l);
+      EL += r2[0];
+      Ep += r2[1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      EL += __shfl_xor_sync(0xffffffffu, EL, o);
+      Ep += __shfl_xor_sync(0xffffffffu, Ep, o);
+    }
+    if (x.wl == 0) {
+      cst[4 * cs] = EL;
+      cst[4 * cs + 1] = Ep;
+    }
+  }
+  __syncthreads();
+  // The cells' scalar steps with lanes over cells: one warp instruction serves
+  // every cell of the item (a warp per cell would spend a whole warp's FP64
+  // issue slots on each cell's square root and divisions).
+  if (x.wid == 0) {
+    for (int cs = x.wl; cs < wi.cell_count; cs += 32) {
+      const long long Pc = gp->cell0 + wi.cell_begin + cs;
+      const double EL = cst[4 * cs], Ep = cst[4 * cs + 1];
+      double accepted = 0.0;
+      if (a.partial) {  // band-range handle: partial sums for the caller's all-reduce
+        if (!a.dry) {
+          a.Epart[2 * Pc] = EL;
+          a.Epart[2 * Pc + 1] = Ep;
+        }
+      } else {
+        if (!a.dry) a.EL[Pc] = EL;
+        if (!isfinite(EL) || !isfinite(Ep)) {
+          atomicAdd(&cnt_bad, 1ULL);
+        } else if (a.solve_tp) {
+          atomicAdd(&cnt_solves, 1ULL);
+          // root of (F - E_p) + F1 d + F2 d^2 / 2 nearest 0; F, F1, F2: the model's
+          // sums sum_b a_p,b J_k,b, kept with J
+          const double Fs = a.Msum[3 * Pc] - Ep, F1s = a.Msum[3 * Pc + 1], F2s = a.Msum[3 * Pc + 2];
+          const double Te = a.Teval[Pc];
+          const double disc = F1s * F1s - 2.0 * Fs * F2s;
+          const double delta = (disc >= 0.0 && F1s > 0.0) ? -2.0 * Fs / (F1s + sqrt(disc)) : -Fs / F1s;
+          const double Tn = Te + delta;
+          if (isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn) {
+            if (!a.dry) {
+              a.Tp[Pc] = Tn;
+              cst[4 * cs + 2] = delta;
+              accepted = 1.0;
+            }
+          } else if (!a.dry) {  // exact quadrature needed: hand the cell to the fix-up kernel
+            const unsigned k = atomicAdd(a.fix_count, 1u);
+            FixItem fi;
+            fi.P = Pc;
+            fi.Ep = Ep;
+            fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[Pc];
+            a.fix[k] = fi;
+          }
+        }
+      }
+      cst[4 * cs + 3] = accepted;
+    }
+  }
+  __syncthreads();
+  // I0 refresh of every band of the accepted cells from their models: threads
+  // over (cell, band).  Every read of cst precedes the next item's second barrier.
+  for (int e = threadIdx.x; e < wi.cell_count * x.nbp; e += blockDim.x) {
+    const int cs = e / x.nbp, b = e - cs * x.nbp;
+    if (cst[4 * cs + 3] == 0.0) continue;
+    const long long Pc = gp->cell0 + wi.cell_begin + cs;
+    const double delta = cst[4 * cs + 2], hd2 = 0.5 * delta * delta;
+    const long long j = (Pc * 3) * x.nbp_all + x.band0 + b;
+    a.I0cell[Pc * x.nbp + b] = b < x.nbr ? fma(a.J[j + 2 * x.nbp_all], hd2, fma(a.J[j + x.nbp_all], delta, a.J[j])) : 0.0;
+  }
+  }
+
 // BM (FP64 implicit only): 0 plain; 1 also stores B = A_n I^n; 2 the In operand
 // holds B, so the update is B + A_x I_x + A_y I_y (+ A_z I_z) + A_s I0 (bitwise
 // the same value, one FP64 multiply fewer per update).
@@ -536,108 +655,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       }
     }
 
-    // ---- per-cell reduction.  The lanes of a cell hold band partials over their
-    // direction subsets; the band owners (dg == 0) add them in a fixed order to
-    // G_b, then E_L = sum_b G_b / v_b and E_p = sum_b beta_b G_b / v_b per band
-    // vector.  One warp per cell adds the band vectors (shuffle tree); one warp
-    // then solves every cell's model (lanes over cells), and all threads refresh
-    // the accepted cells' I0.  Four barriers per item: every read of gsm
-    // precedes the second, every read of red the third, and every read of the
-    // per-cell scratch the next item's second.
-    double* gb = gsm;
-    double* rb = red;
-#pragma unroll
-    for (int v = 0; v < V; ++v) gb[(size_t)threadIdx.x * V + v] = G[v];
-    __syncthreads();
-    if (dg == 0) {
-      double eL = 0.0, ep = 0.0;
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        double Gb = kDev ? a.Wtot * a.I0ref[b0 + v] : 0.0;
-        for (int q = 0; q < dstep; ++q) Gb += gb[(size_t)(slot * team + q * lpc + lane) * V + v];
-        const double e = Gb * a.th.inv_v[b0 + v];
-        eL += e;
-        ep = fma(a.th.beta[b0 + v], e, ep);
-      }
-      double* r2 = rb + 2 * (size_t)(slot * lpc + lane);
-      r2[0] = eL;
-      r2[1] = ep;
-    }
-    __syncthreads();
-    double* cst = rb + 2 * (size_t)cpb * lpc;  // [cpb][4]: E_L, E_p, model step, accepted
-    for (int cs = wid; wid < nwarps && cs < wi.cell_count; cs += nwarps) {  // warp per cell: E_L, E_p
-      double EL = 0.0, Ep = 0.0;
-      for (int l = wl; l < lpc; l += 32) {
-        const double* r2 = rb + 2 * (size_t)(cs * lpc + l);
-        EL += r2[0];
-        Ep += r2[1];
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        EL += __shfl_xor_sync(0xffffffffu, EL, o);
-        Ep += __shfl_xor_sync(0xffffffffu, Ep, o);
-      }
-      if (wl == 0) {
-        cst[4 * cs] = EL;
-        cst[4 * cs + 1] = Ep;
-      }
-    }
-    __syncthreads();
-    // The cells' scalar steps with lanes over cells: one warp instruction serves
-    // every cell of the item (a warp per cell would spend a whole warp's FP64
-    // issue slots on each cell's square root and divisions).
-    if (wid == 0) {
-      for (int cs = wl; cs < wi.cell_count; cs += 32) {
-        const long long Pc = gp->cell0 + wi.cell_begin + cs;
-        const double EL = cst[4 * cs], Ep = cst[4 * cs + 1];
-        double accepted = 0.0;
-        if (a.partial) {  // band-range handle: partial sums for the caller's all-reduce
-          if (!a.dry) {
-            a.Epart[2 * Pc] = EL;
-            a.Epart[2 * Pc + 1] = Ep;
-          }
-        } else {
-          if (!a.dry) a.EL[Pc] = EL;
-          if (!isfinite(EL) || !isfinite(Ep)) {
-            atomicAdd(&cnt_bad, 1ULL);
-          } else if (a.solve_tp) {
-            atomicAdd(&cnt_solves, 1ULL);
-            // root of (F - E_p) + F1 d + F2 d^2 / 2 nearest 0; F, F1, F2: the model's
-            // sums sum_b a_p,b J_k,b, kept with J
-            const double Fs = a.Msum[3 * Pc] - Ep, F1s = a.Msum[3 * Pc + 1], F2s = a.Msum[3 * Pc + 2];
-            const double Te = a.Teval[Pc];
-            const double disc = F1s * F1s - 2.0 * Fs * F2s;
-            const double delta = (disc >= 0.0 && F1s > 0.0) ? -2.0 * Fs / (F1s + sqrt(disc)) : -Fs / F1s;
-            const double Tn = Te + delta;
-            if (isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn) {
-              if (!a.dry) {
-                a.Tp[Pc] = Tn;
-                cst[4 * cs + 2] = delta;
-                accepted = 1.0;
-              }
-            } else if (!a.dry) {  // exact quadrature needed: hand the cell to the fix-up kernel
-              const unsigned k = atomicAdd(a.fix_count, 1u);
-              FixItem fi;
-              fi.P = Pc;
-              fi.Ep = Ep;
-              fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[Pc];
-              a.fix[k] = fi;
-            }
-          }
-        }
-        cst[4 * cs + 3] = accepted;
-      }
-    }
-    __syncthreads();
-    // I0 refresh of every band of the accepted cells from their models: threads
-    // over (cell, band).  Every read of cst precedes the next item's second barrier.
-    for (int e = threadIdx.x; e < wi.cell_count * nbp; e += blockDim.x) {
-      const int cs = e / nbp, b = e - cs * nbp;
-      if (cst[4 * cs + 3] == 0.0) continue;
-      const long long Pc = gp->cell0 + wi.cell_begin + cs;
-      const double delta = cst[4 * cs + 2], hd2 = 0.5 * delta * delta;
-      const long long j = (Pc * 3) * nbp_all + band0 + b;
-      a.I0cell[Pc * nbp + b] = b < nbr ? fma(a.J[j + 2 * nbp_all], hd2, fma(a.J[j + nbp_all], delta, a.J[j])) : 0.0;
-    }
+    item_epilogue<V, kDev>(a, ItemCtx{team, cpb, slot, dg, lane, lpc, dstep, b0, wid, wl, nwarps, nbp, nbp_all, band0,
+                                      nbr, gsm, red},
+                           wi, gp, G, cnt_solves, cnt_bad);
   }
   __syncthreads();
   if (threadIdx.x == 0 && a.counters) {

@@ -1,0 +1,297 @@
+// bte_sweep_ff.cuh -- the FP64-mode Jacobi sweep in double-float arithmetic
+// with factored coefficients (sm_103a).
+//
+// The implicit point-Jacobi update of Sec. 3.1 (Eq. 5 with backward Euler),
+//   I^{k+1} = R (I^n/dt + v_b sum_ax c_ax,d I_up,ax^k + beta_b I0_b^k),
+//   R = 1 / (1/dt + beta_b + v_b sum_ax c_ax,d),  c_ax,d = |S_d,ax| / (w_d Delta_ax),
+// is evaluated as B + R (v_b sum_ax c_ax u_ax + beta_b I0) with B = (R/dt) I^n
+// kept across the inner iterations of a step, in double-float arithmetic on
+// the FP32 pipe (bte_ff.cuh): c_ax per direction sits in a shared table, v_b
+// and beta_b of the lane's two bands in registers, beta_b I0_b per cell in
+// registers, and only R per (direction, band) is read per step.  A step
+// therefore stages four 16-byte operands (B or I^n, the upwind value per axis
+// in 2-D, R) instead of the six of the five-coefficient form: with a 3-stage
+// ring about 63 KB of shared memory per 224-thread CTA in 2-D, so three CTAs
+// can share an SM (the autotuner picks two or three).  The tables come from the host in double-float form with R
+// chosen so that R (1/dt + beta_b + v_b sum c_ax) = 1 holds for the table
+// values to double-double accuracy, which keeps a uniform equilibrium in place.
+//
+// Work layout, staging, walls, direction sums and the item epilogue are those
+// of sweep_kernel (bte_sweep.cuh); FF has the meaning described there.
+#pragma once
+#include <type_traits>
+
+#include "bte_ff.cuh"
+#include "bte_sweep.cuh"
+
+namespace bte {
+namespace sweep_ff {
+
+using sweep::CellAddr;
+using sweep::cp_async;
+using sweep::cp_async_commit;
+using sweep::cp_async_wait;
+using sweep::ItemCtx;
+
+// Shared per-direction table of the current cell-size class (64 bytes): the
+// coefficients already packed for the two-band operations.
+struct DirFF {
+  int up;          // bit a set: the upwind neighbour lies on the low side along axis a
+  unsigned wkey;   // bits of w32 ^ bits of wlo: equal weights, equal keys (the runs of the direction sums)
+  float w32, wlo;  // w_d as a double-float pair
+  ff::x2 ch[3];    // c_ax,d high part in both halves, for ax = x, y, z
+  ff::x2 cl[3];    // c_ax,d low part in both halves
+};
+
+// Ring depth: 4 stages when two CTAs share an SM, 3 when three do (the
+// shared memory of three 224-thread CTAs).
+template <int DIM, int MINB>
+struct RingFF {
+  static constexpr int kOps = 2 + DIM;  // B or I^n, upwind per axis, R
+  static constexpr int kStages = MINB >= 3 ? 3 : 4;
+};
+
+// Threads per CTA the register cap is computed for: three resident CTAs are
+// meant for the 224-thread CTAs of 55-56 bands (4 cells x 28 lanes x 2
+// directions), which leaves up to 97 registers per thread.
+template <int MINB>
+struct MaxThreadsFF {
+  static constexpr int value = MINB >= 3 ? 224 : 256;
+};
+// Registers per thread of MINB resident CTAs of MaxThreadsFF threads (multiples of 8).
+template <int MINB>
+struct MaxRegFF {
+  static constexpr int value = (65536 / (MINB * MaxThreadsFF<MINB>::value)) / 8 * 8;
+};
+
+template <int DIM, int MINB, int BM, int FF>
+__global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegFF<MINB>::value) sweep_ff_kernel(SweepArgs a) {
+  static_assert(FF != 0 && BM != 0, "double-float B-form variants only");
+  static_assert(BM != 2 || (FF & 1) != 0, "B is an ff pair");
+  constexpr int V = 2;
+  constexpr int kOps = RingFF<DIM, MINB>::kOps;
+  constexpr int kStages = RingFF<DIM, MINB>::kStages;
+  extern __shared__ double sm[];
+  __shared__ unsigned long long cnt_solves, cnt_bad;
+  __shared__ int cur_cls;
+  const int lpc = a.lpc, nd = a.nd, nbp = a.th.nbo, dstep = a.dteam;
+  const int nbp_all = a.th.nbp, band0 = a.th.band0, nbr = a.th.nbr;
+  const int team = lpc * dstep;
+  const int cpb = blockDim.x / team;
+  const int slot = threadIdx.x / team, tl = threadIdx.x - slot * team;
+  const int dg = tl / lpc, lane = tl - dg * lpc;
+  DirFF* dsm = reinterpret_cast<DirFF*>(sm);
+  double* gsm = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(dsm + nd) + 15) & ~static_cast<uintptr_t>(15));
+  double* red = gsm + (size_t)V * blockDim.x;
+  char* ring = reinterpret_cast<char*>(
+      (reinterpret_cast<uintptr_t>(red + 2 * (size_t)cpb * lpc + 4 * (size_t)cpb) + 15) & ~static_cast<uintptr_t>(15));
+  const double* __restrict__ In = reinterpret_cast<const double*>(a.In);
+  const double* __restrict__ Ik = reinterpret_cast<const double*>(a.Ik);
+  double* __restrict__ Io = reinterpret_cast<double*>(a.Iout);
+  const long long row = (long long)nd * nbp;
+  const int b0 = V * lane;
+  if (threadIdx.x == 0) { cnt_solves = 0; cnt_bad = 0; cur_cls = -1; }
+  const int wid = threadIdx.x >> 5, wl = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  // v_b and beta_b of the lane's two bands, 1/dt
+  const ff::P2 v2 = ff::ldg(a.band_ff + 2 * b0);
+  const ff::P2 beta2 = ff::ldg(a.band_ff + 2 * (nbp + b0));
+  const ff::P2 rdt2{ff::pack(a.rdt_h, a.rdt_h), ff::pack(a.rdt_l, a.rdt_l)};
+  __syncthreads();
+
+  for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    const WorkItem wi = a.items[item];
+    const DevGeom* gp = a.geoms + wi.geom;
+    const int gnx = gp->nx, gny = gp->ny, gcls = gp->cls;
+    const int gnz = DIM == 3 ? gp->nz : 1;
+    if (gcls != cur_cls) {  // (block-uniform) direction table of this cell-size class
+      __syncthreads();
+      for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+        DirFF e;
+        e.up = a.dirs[d].up;
+        e.w32 = a.wdir32[d];
+        e.wlo = (float)(a.wdir[d] - (double)e.w32);
+        e.wkey = __float_as_uint(e.w32) ^ __float_as_uint(e.wlo);
+        const float* cc = a.dirc_ff + ((size_t)gcls * nd + d) * 6;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          e.ch[k] = ff::pack(cc[2 * k], cc[2 * k]);
+          e.cl[k] = ff::pack(cc[2 * k + 1], cc[2 * k + 1]);
+        }
+        dsm[d] = e;
+      }
+      if (threadIdx.x == 0) cur_cls = gcls;
+      __syncthreads();
+    }
+    const bool active = slot < wi.cell_count;
+    const int lc = wi.cell_begin + (active ? slot : 0);
+    const int ci = lc % gnx, cj = (lc / gnx) % gny, ck = lc / (gnx * gny);
+    const long long P = gp->cell0 + lc;
+    double G[V] = {0.0, 0.0};
+
+    if (active) {
+      // beta_b I0_b of the cell, constant over its directions
+      const ff::P2 srcb =
+          ff::norm(ff::mul(beta2, ff::from_doubles(a.I0cell[P * nbp + b0], a.I0cell[P * nbp + b0 + 1])));
+      CellAddr<double> c;
+      c.in = In + P * row + b0;
+      c.ik = Ik + P * row + b0;
+      c.out = Io + P * row + b0;
+      c.bout = BM == 1 ? reinterpret_cast<double*>(a.Bout) + P * row + b0 : nullptr;
+      c.sx = row;
+      c.sy = (long long)gnx * row;
+      c.sz = (long long)gnx * gny * row;
+      c.ci = ci; c.cj = cj; c.ck = ck;
+      c.wall = (ci == 0) | ((ci == gnx - 1) << 1) | ((cj == 0) << 2) | ((cj == gny - 1) << 3) |
+               (DIM == 3 ? ((ck == 0) << 4) | ((ck == gnz - 1) << 5) : 0);
+      const long long sx_ = c.sx, sy_ = c.sy, sz_ = c.sz;
+      const double* __restrict__ Rrow = reinterpret_cast<const double*>(a.coef_R) + (size_t)gcls * row + b0;
+      const int nsteps = dg < nd ? (nd - dg + dstep - 1) / dstep : 0;
+      const unsigned rb0 = (unsigned)__cvta_generic_to_shared(ring) + threadIdx.x * 16u;
+      const unsigned ostr = blockDim.x * 16u, sstr = kOps * ostr;
+      const long long dst = (long long)dstep * nbp;  // elements from one step's row to the next
+      // direction sums: per run of equal weights in ff, the runs into G in ff
+      ff::P2 Sff = ff::zero(), Gff = ff::zero(), wff = ff::zero();
+      unsigned wrun = 0xffffffffu;
+      // The step loop, once for interior cells (every upwind row a neighbour's,
+      // every operand an ff pair when FF & 1) and once for wall cells.
+      auto run = [&](auto interior_tag) {
+        constexpr bool kInt = decltype(interior_tag)::value;
+        // issue side: the rows of step ji advance by dst elements per step
+        const double* pin = c.in + (long long)dg * nbp;
+        const double* pik = c.ik + (long long)dg * nbp;
+        const double* pR = Rrow + (long long)dg * nbp;
+        int ji = 0;
+        unsigned sbi = rb0;
+        auto issue = [&]() {
+          if (ji < nsteps) {
+            const int d = dg + ji * dstep;
+            cp_async<16>(sbi, pin);
+            if constexpr (kInt) {
+              const int up = dsm[d].up;
+              cp_async<16>(sbi + ostr, pik + ((up & 1) ? -sx_ : sx_));
+              cp_async<16>(sbi + 2 * ostr, pik + ((up & 2) ? -sy_ : sy_));
+              if (DIM == 3) cp_async<16>(sbi + 3 * ostr, pik + ((up & 4) ? -sz_ : sz_));
+            } else {
+              const DirInfo dinf = a.dirs[d];
+              const int4 di = make_int4(dinf.up, dinf.rx, dinf.ry, dinf.rz);
+              const int off = d * nbp;
+              cp_async<16>(sbi + ostr, sweep::upwind_src<0, double>(a, gp, c, di, off, b0));
+              cp_async<16>(sbi + 2 * ostr, sweep::upwind_src<1, double>(a, gp, c, di, off, b0));
+              if (DIM == 3) cp_async<16>(sbi + 3 * ostr, sweep::upwind_src<2, double>(a, gp, c, di, off, b0));
+            }
+            cp_async<16>(sbi + (1 + DIM) * ostr, pR);
+            pin += dst;
+            pik += dst;
+            pR += dst;
+          }
+          cp_async_commit();
+          ++ji;
+          sbi = (ji % kStages == 0) ? rb0 : sbi + sstr;
+        };
+#pragma unroll
+        for (int j = 0; j < kStages - 1; ++j) issue();
+        double* pout = c.out + (long long)dg * nbp;
+        double* pbout = BM == 1 ? c.bout + (long long)dg * nbp : nullptr;
+        unsigned sb = rb0;
+        for (int j = 0; j < nsteps; ++j) {
+          issue();
+          cp_async_wait<kStages - 1>();
+          const int d = dg + j * dstep;
+          const DirFF& e = dsm[d];
+          // sum_ax c_ax u_ax; an upwind operand is an ff pair unless it is I^k in
+          // doubles or an isothermal wall ghost (doubles in every variant)
+          ff::P2 t;
+#pragma unroll
+          for (int ax = 0; ax < DIM; ++ax) {
+            const unsigned ua = sb + (1 + ax) * ostr;
+            ff::P2 u;
+            if constexpr (kInt) {
+              u = (FF & 1) ? ff::lds(ua) : ff::lds_doubles(ua);
+            } else {
+              const int side = 2 * ax + (((e.up >> ax) & 1) ? 0 : 1);
+              const bool dbl = (FF & 1) == 0 || (((c.wall >> side) & 1) && gp->bc[side] == 0);
+              u = dbl ? ff::lds_doubles(ua) : ff::lds(ua);
+            }
+            const ff::P2 pr = ff::mul(ff::P2{e.ch[ax], e.cl[ax]}, u);
+            if (ax == 0) t = pr;
+            else t = ff::add(t, pr);
+          }
+          const ff::P2 Rv = ff::lds(sb + (1 + DIM) * ostr);
+          const ff::P2 p = ff::mul(Rv, ff::add(ff::mul(v2, t), srcb));
+          ff::P2 rf;
+          if constexpr (BM == 2) {
+            rf = ff::norm(ff::add(ff::lds(sb), p));
+          } else {  // B = (R / dt) I^n, kept for the later inner iterations
+            const ff::P2 vin = (FF & 1) ? ff::lds(sb) : ff::lds_doubles(sb);
+            const ff::P2 B = ff::norm(ff::mul(rdt2, ff::mul(Rv, vin)));
+            if constexpr ((FF & 2) != 0) ff::st_stream(pbout, B);
+            else ff::st_stream_doubles(pbout, B);
+            pbout += dst;
+            rf = ff::norm(ff::add(B, p));
+          }
+          if constexpr ((FF & 2) != 0) ff::st_stream(pout, rf);
+          else ff::st_stream_doubles(pout, rf);
+          pout += dst;
+          if (e.wkey != wrun) {
+            ff::acc(Gff, ff::mul(wff, Sff));
+            Sff = ff::zero();
+            wff = ff::P2{ff::pack(e.w32, e.w32), ff::pack(e.wlo, e.wlo)};
+            wrun = e.wkey;
+          }
+          ff::acc(Sff, rf);
+          sb = ((j + 1) % kStages == 0) ? rb0 : sb + sstr;
+        }
+      };
+      if (c.wall == 0) run(std::true_type{});
+      else run(std::false_type{});
+      cp_async_wait<0>();
+      ff::acc(Gff, ff::mul(wff, Sff));
+      ff::to_doubles(ff::norm(Gff), G[0], G[1]);
+    }
+    sweep::item_epilogue<V, false>(a, ItemCtx{team, cpb, slot, dg, lane, lpc, dstep, b0, wid, wl, nwarps, nbp,
+                                              nbp_all, band0, nbr, gsm, red},
+                                   wi, gp, G, cnt_solves, cnt_bad);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && a.counters) {
+    if (cnt_solves) atomicAdd(&a.counters->solves, cnt_solves);
+    if (cnt_bad) atomicAdd(&a.counters->nonfinite, cnt_bad);
+  }
+}
+
+template <int DIM, int MINB, int BM, int FF>
+cudaError_t launch_shape(const SweepArgs& a, int threads, int grid, cudaStream_t s) {
+  const int team = a.lpc * a.dteam, cpb = threads / team;
+  const size_t smem = sizeof(DirFF) * (size_t)a.nd + 16 + 2 * (size_t)threads * sizeof(double) +
+                      (2 * (size_t)cpb * a.lpc + 4 * (size_t)cpb) * sizeof(double) + 16 +
+                      (size_t)RingFF<DIM, MINB>::kStages * RingFF<DIM, MINB>::kOps * threads * 16;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(sweep_ff_kernel<DIM, MINB, BM, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  sweep_ff_kernel<DIM, MINB, BM, FF><<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int BM, int FF>
+cudaError_t launch_variant(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
+  const bool three = variant >= 2 && threads <= MaxThreadsFF<3>::value;
+  if (dim == 3) {
+    if (three) return launch_shape<3, 3, BM, FF>(a, threads, grid, s);
+    return launch_shape<3, 2, BM, FF>(a, threads, grid, s);
+  }
+  if (three) return launch_shape<2, 3, BM, FF>(a, threads, grid, s);
+  return launch_shape<2, 2, BM, FF>(a, threads, grid, s);
+}
+
+// variant: 1 -> at least 2 resident CTAs per SM, 2 -> 3 CTAs (the register caps;
+// CTAs of more than 224 threads take variant 1)
+inline cudaError_t launch(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
+  if (a.beta_exp != 0.0) return cudaErrorInvalidValue;
+  if (a.bmode == 1 && a.ff == 2) return launch_variant<1, 2>(variant, a, dim, threads, grid, s);
+  if (a.bmode == 1 && a.ff == 3) return launch_variant<1, 3>(variant, a, dim, threads, grid, s);
+  if (a.bmode == 2 && a.ff == 3) return launch_variant<2, 3>(variant, a, dim, threads, grid, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace sweep_ff
+}  // namespace bte

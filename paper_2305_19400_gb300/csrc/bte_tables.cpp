@@ -217,6 +217,89 @@ void coef_to_ff(const double* coef, int nd, int nbp, bool sum_to_one, float* out
     }
 }
 
+namespace {
+// Double-double values (hi + lo) for the factored tables.
+struct DD {
+  double hi, lo;
+};
+DD dd_of(float h, float l) {  // exact: a float pair is a double-double
+  const double a = h, b = l;
+  const double s = a + b;
+  return {s, b - (s - a)};
+}
+DD dd_add(DD x, DD y) {
+  const double s = x.hi + y.hi;
+  const double bv = s - x.hi;
+  const double e = (x.hi - (s - bv)) + (y.hi - bv) + x.lo + y.lo;
+  const double r = s + e;
+  return {r, e - (r - s)};
+}
+DD dd_mul(DD x, DD y) {
+  const double p = x.hi * y.hi;
+  const double e = std::fma(x.hi, y.hi, -p) + (std::fma(x.hi, y.lo, 0.0) + std::fma(x.lo, y.hi, 0.0));
+  const double r = p + e;
+  return {r, e - (r - p)};
+}
+DD dd_recip(DD d) {  // one Newton step from the double reciprocal
+  const double r0 = 1.0 / d.hi;
+  const double p = d.hi * r0;
+  const double e = ((1.0 - p) - std::fma(d.hi, r0, -p)) - d.lo * r0;
+  const double r = r0 + r0 * e;
+  return {r, (r0 - r) + r0 * e};
+}
+void ff_of(double x, float& h, float& l) {
+  h = (float)x;
+  l = (float)(x - (double)h);
+}
+void ff_of_dd(DD x, float& h, float& l) {
+  h = (float)x.hi;
+  l = (float)((x.hi - (double)h) + x.lo);
+}
+}  // namespace
+
+void build_ff_factored(int dim, const double delta[3], int nd, const double* S, const double* w, int nb, int nbp,
+                       const double* vg, const double* beta, double dt, float* R, float* dirc, float* band, float* rdt) {
+  float rh, rl;
+  ff_of(1.0 / dt, rh, rl);
+  rdt[0] = rh;
+  rdt[1] = rl;
+  const DD rdt_dd = dd_of(rh, rl);
+  for (size_t e = 0; e < 4 * (size_t)nbp; ++e) band[e] = 0.0f;
+  std::vector<DD> v_dd(nb), b_dd(nb);
+  for (int b = 0; b < nb; ++b) {  // pair layout: element b of an [nbp] array at float (b - b%2)*2 + b%2 (+2 for l)
+    float h, l;
+    const size_t o = (size_t)(b - (b & 1)) * 2 + (b & 1);
+    ff_of(vg[b], h, l);
+    band[o] = h;
+    band[o + 2] = l;
+    v_dd[b] = dd_of(h, l);
+    ff_of(beta[b], h, l);
+    band[2 * (size_t)nbp + o] = h;
+    band[2 * (size_t)nbp + o + 2] = l;
+    b_dd[b] = dd_of(h, l);
+  }
+  for (size_t e = 0; e < 2 * (size_t)nd * nbp; ++e) R[e] = 0.0f;
+  for (int d = 0; d < nd; ++d) {
+    DD csum{0.0, 0.0};
+    for (int ax = 0; ax < 3; ++ax) {
+      const double c = ax < dim ? std::fabs(S[3 * d + ax]) / (w[d] * delta[ax]) : 0.0;
+      float h, l;
+      ff_of(c, h, l);
+      dirc[(size_t)d * 6 + 2 * ax] = h;
+      dirc[(size_t)d * 6 + 2 * ax + 1] = l;
+      csum = dd_add(csum, dd_of(h, l));
+    }
+    for (int b = 0; b < nb; ++b) {
+      const DD D = dd_add(dd_add(rdt_dd, b_dd[b]), dd_mul(v_dd[b], csum));
+      float h, l;
+      ff_of_dd(dd_recip(D), h, l);
+      const size_t o = ((size_t)d * nbp + b - (b & 1)) * 2 + (b & 1);
+      R[o] = h;
+      R[o + 2] = l;
+    }
+  }
+}
+
 // Reduced-precision form of the same update: I' = P I^n + Q (v_b sum_ax c_ax I_up + beta_b I0),
 // P and Q per (d, b) as float, c_ax = |S_d,ax|/(w_d Delta_ax) per direction.
 //   implicit: Q = 1/(1/dt + beta_b + v_b sum c), P = Q/dt;  explicit: P = 1 - dt(beta_b + v_b sum c), Q = dt.
