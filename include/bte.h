@@ -72,10 +72,14 @@ typedef struct {
  *             BTE_FP32 or BTE_BF16 (FP32 arithmetic); the reduction, the
  *             temperature solve and I0 are FP64 in every mode.
  *  learned    0 (default): cells the cached-model solve cannot settle start
- *             their exact solve from the model root; 1: they start from the
- *             trained networks' guess (net A: E_p -> T, then surrogate Newton
- *             steps on net B: T -> I0_b) before the exact FP64 refinement.
- *             Requires bte_train_mlp before the first bte_step.
+ *             their exact solve from the model root, or from their previous
+ *             T_p when the model has no root in [1, 5000] K; 1: in the second
+ *             case they start from the trained networks' guess instead (net
+ *             A: E_p -> T, then surrogate Newton steps on net B: T -> I0_b)
+ *             before the exact FP64 refinement (a model root is the closer
+ *             start whenever there is one).  bte_solve_T takes the networks'
+ *             guess for every energy.  Requires bte_train_mlp before the
+ *             first bte_step.
  *  n_gauss    Gauss-Legendre points per band for I0_b(T) (default 16, <= 32).
  *  newton_rtol target relative accuracy of the temperature solve (1e-14).
  *  newton_maxit iteration cap before the bisection fallback (50).

@@ -89,7 +89,6 @@ struct bte_ctx {
   bool state_ff = false;
   double *I0cell = nullptr, *Tp = nullptr, *TL = nullptr, *EL = nullptr, *I0wall = nullptr;
   void* coef = nullptr;
-  void* coef_ff = nullptr;  // FP64: the coefficients as double-float pairs (bte_ff.cuh layout)
   // FP64: tables of the factored double-float sweep (bte_sweep_ff.cuh)
   void* coef_R = nullptr;     // [cls][nd][nbp] R pairs
   float* dirc_ff = nullptr;   // [cls][nd][3][2]
@@ -124,7 +123,7 @@ struct bte_ctx {
   double coef_dt = -1.0;
   int coef_scheme = -1;
   std::vector<double> coef_host;
-  std::vector<float> coef_ff_host, R_host, dirc_host, band_host;
+  std::vector<float> R_host, dirc_host, band_host;
   // per-launch timing of the sweeps (bte_set_sweep_timing): events around each
   // sweep of a step, recorded on the stream (captured into the step's graph)
   bool time_sweeps = false;
@@ -215,7 +214,6 @@ size_t carve(bte_ctx* h, char* base) {
   h->EL = (double*)take((size_t)h->ncells * 8);
   h->I0wall = (double*)take((size_t)std::max(h->nfaces, 1LL) * h->nbp * 8);
   h->coef = take((size_t)h->cls_key.size() * row * (h->opts.precision == BTE_FP64 ? 5 * 8 : 2 * 4));
-  h->coef_ff = h->opts.precision == BTE_FP64 ? take((size_t)h->cls_key.size() * row * 5 * 8) : nullptr;
   h->coef_R = h->opts.precision == BTE_FP64 ? take((size_t)h->cls_key.size() * row * 8) : nullptr;
   h->dirc_ff = h->opts.precision == BTE_FP64 ? (float*)take((size_t)h->cls_key.size() * h->nd * 6 * 4) : nullptr;
   h->band_ff = h->opts.precision == BTE_FP64 ? (float*)take((size_t)h->nbp * 4 * 4) : nullptr;
@@ -472,12 +470,6 @@ int ensure_coef(bte_ctx* h, double dt, int scheme) {
                  h->coef_host.data() + c * 5 * plane);
     }
     CUDA_TRY(h, cudaMemcpyAsync(h->coef, h->coef_host.data(), h->coef_host.size() * 8, cudaMemcpyHostToDevice, h->stream));
-    h->coef_ff_host.resize(2 * h->coef_host.size());
-    for (size_t c = 0; c < ncls; ++c)
-      coef_to_ff(h->coef_host.data() + c * 5 * plane, h->nd, h->nbp, scheme != BTE_EXPLICIT,
-                 h->coef_ff_host.data() + c * 10 * plane);
-    CUDA_TRY(h, cudaMemcpyAsync(h->coef_ff, h->coef_ff_host.data(), h->coef_ff_host.size() * 4, cudaMemcpyHostToDevice,
-                                h->stream));
     // the factored double-float tables (implicit update only)
     h->R_host.assign(2 * plane * ncls, 0.0f);
     h->dirc_host.assign(6 * (size_t)h->nd * ncls, 0.0f);
@@ -573,7 +565,6 @@ SweepArgs sweep_args(bte_ctx* h) {
   a.Epart = h->exchange_buf ? h->exchange_buf : h->Epart;
   a.partial = h->Epart ? 1 : 0;
   a.coef = h->coef;
-  a.coef_ff = h->coef_ff;
   a.coef_R = h->coef_R;
   a.dirc_ff = h->dirc_ff;
   a.band_ff = h->band_ff;

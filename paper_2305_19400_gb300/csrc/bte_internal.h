@@ -71,6 +71,8 @@ struct FixItem {
   long long P;  // global cell
   double Ep;    // right-hand side of the T_p equation: sum_b beta_b G_b / v_b
   double T0;    // start temperature of the exact solve
+  int model;    // 1: T0 is the cached model's root (a warm start); 0: the previous T_p
+  int pad;
 };
 
 // Counters written by the kernels (atomics), read back for bte_stats.
@@ -111,11 +113,9 @@ struct SweepArgs {
   const double* I0wall;     // [face][nbp] FP64 ghosts
   const float* I0wall_dev;  // [face][nbp] FP32 ghosts minus I0ref (reduced modes)
   const double* I0ref;      // [nbp] I0_b(T_ref) (reduced modes)
-  const void* coef_ff;      // FP64: the same coefficients as double-float pairs, per 16 bytes
-                            // (two bands) h_b, h_b+1, l_b, l_b+1; the sum of the five is 1
-                            // (implicit) up to the pairs' resolution
-  int ff;                   // FP64: 0 DFMA arithmetic; else the double-float variant (bit 0: In and
-                            // I^k are ff pairs; bit 1: I^{k+1} and B are written as ff; B is always ff)
+  int ff;                   // FP64: 0 DFMA arithmetic (sweep_kernel); else the double-float sweep
+                            // (sweep_ff_kernel; bit 0: In and I^k are ff pairs, bit 1: I^{k+1} and B
+                            // are written as ff; B is always ff)
   // FP64 double-float sweep with factored coefficients (bte_sweep_ff.cuh), tables
   // in the double-float pair layout of bte_ff.cuh (h_b, h_b+1, l_b, l_b+1 per two bands):
   const void* coef_R;       // [cls][nd][nbp] R = 1/(1/dt + beta_b + v_b sum_ax c_ax,d)

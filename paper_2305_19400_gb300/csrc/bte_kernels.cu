@@ -29,9 +29,10 @@ namespace {
 // cached model: one CTA per cell (exact_solve_cta spreads each evaluation over
 // the SM's four FP64 units; with a handful of such cells per step the solve's
 // latency, not its throughput, is what the step waits for).  The start is the
-// model root (plain mode) or the learned guess (net A, then surrogate Newton
-// steps on net B, by warp 0); the exact FP64 quadrature then refines it (each
-// evaluation becomes the cell's cached model) and I0 is refreshed.
+// model root, or when there is none the previous T_p (plain mode) or the
+// learned guess (net A, then surrogate Newton steps on net B, by warp 0); the
+// exact FP64 quadrature then refines it (each evaluation becomes the cell's
+// cached model) and I0 is refreshed.
 constexpr int kFixThreads = 128;
 
 __global__ void __launch_bounds__(kFixThreads) fixup_kernel(SweepArgs a, int learned, MLPView m) {
@@ -46,14 +47,19 @@ __global__ void __launch_bounds__(kFixThreads) fixup_kernel(SweepArgs a, int lea
   for (unsigned w = blockIdx.x; w < count; w += gridDim.x) {
     const FixItem it = a.fix[w];
     const long long P = it.P;
-    if (learned) {
+    // learned mode: the networks' guess starts the cells that have no usable
+    // root of their cached model (a cold or far-off start); a model root, when
+    // there is one, is the closer start (measured: twice the evaluations from
+    // the networks' guess on the learned 3-D workload)
+    const bool net = learned && !it.model;  // uniform over the CTA (one item)
+    if (net) {
       if (threadIdx.x < 32) {
         const double g = mlp_guess_T(m, a.th.a_p, it.Ep, 2, ybuf, hbuf);
         if (threadIdx.x == 0) t0_sm[0] = g;
       }
       __syncthreads();
     }
-    const double T0 = learned ? t0_sm[0] : it.T0;
+    const double T0 = net ? t0_sm[0] : it.T0;
     const SolveResult r = exact_solve_cta(a.th, it.Ep, T0, a.trust_rel, a.maxit, a.J + (P * 3) * nbp, solve_sm);
     evals += r.evals;
     fb += r.fallback;
@@ -371,7 +377,9 @@ __device__ void solve_cell_warp(const SweepArgs& a, long long P, double EL, doub
       FixItem fi;
       fi.P = P;
       fi.Ep = Ep;
-      fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[P];
+      fi.model = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? 1 : 0;
+      fi.T0 = fi.model ? Tn : a.Tp[P];
+      fi.pad = 0;
       a.fix[k] = fi;
     }
     if (ok) a.Tp[P] = Tn;

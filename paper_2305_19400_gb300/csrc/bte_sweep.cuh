@@ -35,7 +35,6 @@
 #pragma once
 #include <type_traits>
 
-#include "bte_ff.cuh"
 #include "bte_store.cuh"
 
 namespace bte {
@@ -225,7 +224,9 @@ __device__ __forceinline__ void item_epilogue(const SweepArgs& a, const ItemCtx&
             FixItem fi;
             fi.P = Pc;
             fi.Ep = Ep;
-            fi.T0 = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? Tn : a.Tp[Pc];
+            fi.model = (isfinite(Tn) && Tn >= kTmin && Tn <= kTmax) ? 1 : 0;
+            fi.T0 = fi.model ? Tn : a.Tp[Pc];
+            fi.pad = 0;
             a.fix[k] = fi;
           }
         }
@@ -251,25 +252,12 @@ __device__ __forceinline__ void item_epilogue(const SweepArgs& a, const ItemCtx&
 // the same value, one FP64 multiply fewer per update).
 // TT (FP64 only): the relaxation rates depend on T (beta_exp != 0); the
 // reduced modes scale beta per cell outside the step loop and need no variant.
-// FF (FP64 storage only, TT false): 0 the update runs in FP64 (DFMA); otherwise
-// it runs in double-float arithmetic on the FP32 pipe (bte_ff.cuh) with the
-// coefficients of a.coef_ff, and FF says which buffers hold ff pairs instead
-// of doubles: bit 0 the In operand (I^n, or B when BM == 2) and the iterate
-// I^k, bit 1 the output I^{k+1} and B (BM == 1).  B is an ff pair in every
-// variant.  A step from an intensity state in doubles starts with FF = 2 (the
-// first inner iteration converts I^n and I^k as it reads them); every other
-// inner iteration, and every step from a state already in ff pairs, is
-// FF = 3.  The handle converts the state to doubles in place before anything
-// else reads it.  Isothermal wall ghosts are doubles in every variant.  The
-// direction sums G_b are summed in ff per run of equal weights and enter G in
-// ff; G becomes a double once per cell.
-template <int DIM, typename S, int MINB, int BM, bool TT, int FF = 0>
+// (The FP64 update in double-float arithmetic is sweep_ff_kernel, bte_sweep_ff.cuh.)
+template <int DIM, typename S, int MINB, int BM, bool TT>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   using T = Tr<S>;
   using A = typename T::A;
   constexpr int V = T::V;
-  static_assert(FF == 0 || (sizeof(S) == 8 && !TT), "double-float variants are FP64 storage with fixed rates");
-  static_assert(FF == 0 || BM != 2 || (FF & 1) != 0, "B is an ff pair whenever the variant is double-float");
   constexpr bool kDev = sizeof(S) != 8;  // reduced modes store deviations
   extern __shared__ double sm[];
   __shared__ unsigned long long cnt_solves, cnt_bad;
@@ -350,10 +338,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         src[v] = kDev ? bb[v] * (A)(i0 - a.I0ref[b0 + v]) : (A)i0;
       }
       const size_t plane = (size_t)nd * nbp;
-      // coefficient rows of this class and band vector: FP64, or their ff pairs
-      // (same element offsets) in the FF variants
-      const A* __restrict__ cf =
-          (FF != 0 ? reinterpret_cast<const A*>(a.coef_ff) : coef) + (size_t)gcls * 5 * plane + b0;
+      const A* __restrict__ cf = coef + (size_t)gcls * 5 * plane + b0;
       CellAddr<S> c;
       c.in = In + P * row + b0;
       c.ik = Ik + P * row + b0;
@@ -381,11 +366,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       int fe0[V];        // largest exponent field summed in fixed point (-1: none)
       long long wrun = 0;
       int nrun = 0;
-      // FF variants: the run's sum S and the weighted sum G of this lane's two
-      // bands as ff pairs, the run's weight, and I0 of the cell as ff
-      ff::P2 Sff = ff::zero(), Gff = ff::zero(), wff = ff::zero(), srcff = ff::zero();
-      if constexpr (FF != 0) srcff = ff::from_doubles((double)src[0], (double)src[1]);
-      if constexpr (!kDev && FF == 0) {
+      if constexpr (!kDev) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int e0 = (int)((unsigned long long)__double_as_longlong((double)src[v]) >> 52);  // src = I0 (>= 0)
@@ -475,55 +456,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         read_up(sb, 1, di, off, uy);
         if (DIM == 3) read_up(sb, 2, di, off, uz);
         A r[V];
-        if constexpr (FF != 0) {
-          // double-float update of the lane's two bands (bte_ff.cuh):
-          // B (or A_n I^n) + A_x I_x + A_y I_y (+ A_z I_z) + A_s I0
-          ff::P2 rf;
-          if constexpr (BM == 2) {
-            rf = ff::lds(sb);  // B
-          } else {
-            const ff::P2 vin = (FF & 1) ? ff::lds(sb) : ff::lds_doubles(sb);
-            rf = ff::norm(ff::mul(ff::ldg(cf + off), vin));  // A_n I^n
-            if constexpr (BM == 1) {
-              if constexpr ((FF & 2) != 0) ff::st_stream(c.bout + off, rf);
-              else ff::st_stream_doubles(c.bout + off, rf);
-            }
-          }
-          // the DIM + 1 products are independent; they are summed pairwise with
-          // B (a shorter dependency chain than one running sum)
-          ff::P2 pr[DIM + 1];
-#pragma unroll
-          for (int ax = 0; ax < DIM; ++ax) {
-            // the upwind operand is an ff pair unless it is I^k in doubles or an
-            // isothermal wall ghost (doubles in every variant)
-            bool dbl = (FF & 1) == 0;
-            if ((FF & 1) != 0 && c.wall != 0) {
-              const int side = 2 * ax + (((di.x >> ax) & 1) ? 0 : 1);
-              dbl = ((c.wall >> side) & 1) && gp->bc[side] == 0;
-            }
-            const unsigned ua = sb + (1 + ax) * ostr;
-            const ff::P2 u = dbl ? ff::lds_doubles(ua) : ff::lds(ua);
-            pr[ax] = ff::mul(ff::lds(sb + (1 + DIM + ax) * ostr), u);
-          }
-          pr[DIM] = ff::mul(ff::lds(sb + (1 + 2 * DIM) * ostr), srcff);
-          if constexpr (DIM == 2) {
-            rf = ff::norm(ff::add(ff::add(rf, pr[0]), ff::add(pr[1], pr[2])));
-          } else {
-            rf = ff::norm(ff::add(ff::add(ff::add(rf, pr[0]), ff::add(pr[1], pr[2])), pr[3]));
-          }
-          if constexpr ((FF & 2) != 0) ff::st_stream(c.out + off, rf);
-          else ff::st_stream_doubles(c.out + off, rf);
-          // G_b: the run's sum in ff; a new weight closes the run into G
-          const long long wb = __double_as_longlong(dsm[d].w);
-          if (wb != wrun) {
-            ff::acc(Gff, ff::mul(wff, Sff));
-            Sff = ff::zero();
-            const float w32 = dsm[d].w32, wlo = dsm[d].wlo;
-            wff = ff::P2{ff::pack(w32, w32), ff::pack(wlo, wlo)};
-            wrun = wb;
-          }
-          ff::acc(Sff, rf);
-        } else if constexpr (!kDev) {
+        if constexpr (!kDev) {
           A Ax[V], Ay[V], As[V];
           Tr<double>::lds(sb + (1 + DIM) * ostr, Ax);
           Tr<double>::lds(sb + (2 + DIM) * ostr, Ay);
@@ -639,13 +572,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         run(std::false_type{});
       }
       cp_async_wait<0>();
-      if constexpr (FF != 0) {
-        ff::acc(Gff, ff::mul(wff, Sff));
-        double g0, g1;
-        ff::to_doubles(ff::norm(Gff), g0, g1);
-        G[0] = g0;
-        G[1] = g1;
-      } else if constexpr (kDev) {
+      if constexpr (kDev) {
 #pragma unroll
         for (int v = 0; v < V; ++v) G[v] += (double)acc[v];
       } else {
@@ -666,7 +593,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
   }
 }
 
-template <typename S, int MINB, int BM, bool TT, int FF>
+template <typename S, int MINB, int BM, bool TT>
 cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   const int team = a.lpc * a.dteam, cpb = threads / team;
   const size_t smem = sizeof(DirSm) * (size_t)a.nd + (size_t)Tr<S>::V * threads * sizeof(double) +
@@ -675,33 +602,27 @@ cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cuda
                           threads * 16;
   if (dim == 3) {
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(sweep_kernel<3, S, MINB, BM, TT, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sweep_kernel<3, S, MINB, BM, TT, FF><<<grid, threads, smem, s>>>(a);
+      cudaFuncSetAttribute(sweep_kernel<3, S, MINB, BM, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sweep_kernel<3, S, MINB, BM, TT><<<grid, threads, smem, s>>>(a);
   } else {
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(sweep_kernel<2, S, MINB, BM, TT, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    sweep_kernel<2, S, MINB, BM, TT, FF><<<grid, threads, smem, s>>>(a);
+      cudaFuncSetAttribute(sweep_kernel<2, S, MINB, BM, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sweep_kernel<2, S, MINB, BM, TT><<<grid, threads, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
 
 // variant: 1 -> at least 2 resident CTAs per SM (<= 128 registers), 2 -> 3 CTAs (<= 80 registers)
-template <typename S, int BM, bool TT, int FF = 0>
+template <typename S, int BM, bool TT>
 cudaError_t launch_bm(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
-  if (variant >= 2) return launch_minb<S, 3, BM, TT, FF>(a, dim, threads, grid, s);
-  return launch_minb<S, 2, BM, TT, FF>(a, dim, threads, grid, s);
+  if (variant >= 2) return launch_minb<S, 3, BM, TT>(a, dim, threads, grid, s);
+  return launch_minb<S, 2, BM, TT>(a, dim, threads, grid, s);
 }
 
 template <typename S>
 cudaError_t launch(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   if constexpr (sizeof(S) == 8) {
-    if (a.ff != 0) {  // double-float arithmetic: the B form with fixed relaxation rates only
-      if (a.beta_exp != 0.0) return cudaErrorInvalidValue;
-      if (a.bmode == 1 && a.ff == 2) return launch_bm<S, 1, false, 2>(variant, a, dim, threads, grid, s);
-      if (a.bmode == 1 && a.ff == 3) return launch_bm<S, 1, false, 3>(variant, a, dim, threads, grid, s);
-      if (a.bmode == 2 && a.ff == 3) return launch_bm<S, 2, false, 3>(variant, a, dim, threads, grid, s);
-      return cudaErrorInvalidValue;
-    }
+    if (a.ff != 0) return cudaErrorInvalidValue;  // the double-float variants are sweep_ff_kernel's
     if (a.beta_exp != 0.0) {
       if (a.bmode == 1) return launch_bm<S, 1, true>(variant, a, dim, threads, grid, s);
       if (a.bmode == 2) return launch_bm<S, 2, true>(variant, a, dim, threads, grid, s);

@@ -173,51 +173,6 @@ void build_coef(int dim, const double delta[3], int nd, const double* S, const d
 }
 
 namespace {
-// s + e += x, double-double accumulation (TwoSum in double)
-void dd_add(double& s, double& e, double x) {
-  const double t = s + x;
-  const double bv = t - s;
-  e += (s - (t - bv)) + (x - bv);
-  s = t;
-}
-}  // namespace
-
-void coef_to_ff(const double* coef, int nd, int nbp, bool sum_to_one, float* out) {
-  const size_t plane = (size_t)nd * nbp;
-  for (int d = 0; d < nd; ++d)
-    for (int b = 0; b < nbp; ++b) {
-      const size_t o = (size_t)d * nbp + b;
-      float h[5], l[5];
-      for (int k = 0; k < 5; ++k) {
-        const double c = coef[k * plane + o];
-        h[k] = (float)c;
-        l[k] = (float)(c - (double)h[k]);
-      }
-      if (sum_to_one) {
-        int order[5] = {0, 1, 2, 3, 4};
-        std::sort(order, order + 5, [&](int x, int y) { return std::fabs(h[x]) > std::fabs(h[y]); });
-        for (int q = 0; q < 5; ++q) {
-          const int k = order[q];
-          if (h[k] == 0.0f) break;
-          double S = 0.0, E = 0.0;
-          for (int j = 0; j < 5; ++j) {
-            dd_add(S, E, (double)h[j]);
-            dd_add(S, E, (double)l[j]);
-          }
-          const double r = (1.0 - S) - E;  // 1 - S is exact (S is within rounding of 1)
-          l[k] = (float)((double)l[k] + r);
-        }
-      }
-      for (int k = 0; k < 5; ++k) {
-        const size_t e = k * plane + o;        // element index; its pair starts at e - b % 2
-        const size_t v = (e - (b & 1)) * 2;    // float offset of the 16-byte vector
-        out[v + (b & 1)] = h[k];
-        out[v + 2 + (b & 1)] = l[k];
-      }
-    }
-}
-
-namespace {
 // Double-double values (hi + lo) for the factored tables.
 struct DD {
   double hi, lo;

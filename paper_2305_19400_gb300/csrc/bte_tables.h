@@ -14,15 +14,6 @@ void build_thermo(int nb, int nbp, int ng, const double* wlo, const double* whi,
 void build_coef(int dim, const double delta[3], int nd, const double* S, const double* w, int nb, int nbp,
                 const double* vg, const double* beta, double dt, int explicit_scheme, double* out);
 
-// The FP64 coefficients [5][nd][nbp] of one class as double-float pairs for the
-// sweep's double-float variants: out[(5 * nd * nbp) * 2] floats, per two bands
-// (16 bytes) h_b, h_b+1, l_b, l_b+1 with c = h + l.  sum_to_one: the five
-// coefficients of a (direction, band) sum to 1 in exact arithmetic (the
-// implicit update is a convex combination); their low parts are then
-// adjusted, largest coefficient first, so that the pairs' exact sum is 1 to
-// within the finest low part's resolution (a uniform equilibrium stays put).
-void coef_to_ff(const double* coef, int nd, int nbp, bool sum_to_one, float* out);
-
 // Tables of the factored double-float sweep (bte_sweep_ff.cuh) for one class:
 // dirc[nd][3][2] c_ax,d = |S_d,ax|/(w_d Delta_ax) as double-float pairs (h, l);
 // band[2][nbp] v_b and beta_b and R[nd][nbp] in the pair layout of bte_ff.cuh

@@ -4,11 +4,14 @@
   row in one cell; the next step's per-cell energy of that cell is not finite
   and the call says so.  Restoring finite data makes the handle step again.
 * BTE_W_FALLBACK: learned mode with deliberately wrong network weights (net A
-  answers 1.5 K for every energy, net B is flat).  The cells handed to the
-  exact solve start from that guess, their Halley step leaves [1, 5000] K and
-  the solve falls back to bisection.  The call reports the fallbacks, and the
-  temperatures still equal the FP64 oracle's to rel 1e-12, because bisection
-  runs to the same root.
+  answers 1.5 K for every energy, net B is flat).  The networks start the
+  exact solve of cells whose cached temperature model has no usable root; a
+  checkpoint restore that claims T_p = 1 K for a 300 K field makes that so
+  for every cell (the model at 1 K puts its root far above 5000 K).  From
+  the 1.5 K guess the Halley step leaves [1, 5000] K and the solve falls back
+  to bisection.  The call reports the fallbacks, and the temperatures still
+  equal the FP64 oracle's (same restore, same step) to rel 1e-12, because
+  bisection runs to the same root.
 """
 import numpy as np
 import pytest
@@ -63,17 +66,22 @@ def _wrong_nets(wl, T_lo, T_hi, T_guess):
 
 def test_wrong_network_weights_fall_back_to_bisection_with_unchanged_results():
     wl = W.cfg2(13, 9)
+    g = wl.geoms[0]
     s = bte.Solver(wl, learned=True)
     bte.bte_train_mlp(s.h, 1 << 14, 250.0, 400.0, 1, seed=3)
     pa, pb = _wrong_nets(wl, 250.0, 400.0, 1.5)
     bte.bte_mlp_set_params(s.h, 0, pa)
     bte.bte_mlp_set_params(s.h, 1, pb)
-    rc, st = s.step(nsteps=2, ninner=4)
-    assert rc == bte.BTE_W_FALLBACK and st["fallbacks"] > 0, (rc, st)
-    g = wl.geoms[0]
+    # restore the 300 K field with T_p = 1 K: no cell keeps a usable model root
     p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands)
     ost = p.init_state(g.T_init)
-    p.run(ost, wl.dt, 2, 4)
+    Tp1 = np.full(g.ncells, 1.0)
+    bte.bte_set_intensity(s.h, 0, ost["I"], Tp1)
+    rc, st = s.step(nsteps=1, ninner=3)
+    assert rc == bte.BTE_W_FALLBACK and st["fallbacks"] > 0, (rc, st)
+    ost["Tp"] = Tp1.copy()
+    ost["I0"] = np.tile(O.I0(wl.bands, 1.0)[0], (g.ncells, 1))
+    p.run(ost, wl.dt, 1, 3)
     for which, key in ((bte.BTE_T_LATTICE, "TL"), (bte.BTE_T_PSEUDO, "Tp")):
         assert np.max(np.abs(s.T(0, which) - ost[key]) / ost[key]) <= 1e-12
     # the same wrong start through the batch solve: every root still exact
