@@ -54,7 +54,7 @@ METRIC = "cell·dir·band updates/s and % HBM roofline at stated max|ΔT| vs FP6
 UNIT = "updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.json")
-KERNEL_SRCS = [os.path.join(ROOT, "paper_2305_19400_gb300", "csrc", f) for f in ("bte_sweep.cuh", "bte_store.cuh")]
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2305_19400_gb300", "csrc", f) for f in ("bte_sweep_ff.cuh", "bte_ff.cuh", "bte_sweep.cuh", "bte_store.cuh")]
 # Algorithmic bytes of one implicit update: I^n (or B) read, I^k read once, I^{k+1} written.
 BYTES_PER_UPDATE_FP64 = 24
 # Work of the dominant kernel (the double-float sweep of inner iterations 2..n-1,
@@ -521,9 +521,10 @@ def run_umesh_variant(peaks, fp64_peak, precision=None):
     """Unstructured mesh: a 1.28 um square of 128x128 grid squares split into
     32768 jittered triangles, 400 directions (20 x 20) x 55 band-pols, FP64,
     walls hot 305 K / cold 300 K / mirror / diffuse, 15 inner iterations per
-    step, device-timed like the main line.  Flops per update: the B-form update
-    (2 FMAs) plus one FMA per inflow face and the reduction's FMA, the inflow
-    count averaged over the mesh's (cell, direction) pairs."""
+    step, device-timed like the main line.  FP64 work per update: the B-form
+    update (2 FMAs) plus one FMA per inflow face, the inflow count averaged
+    over the mesh's (cell, direction) pairs (the per-cell sums of the separate
+    reduction run in fixed point on the integer pipe)."""
     import numpy as np
     import torch
     from paper_2305_19400_gb300 import bte, mesh as M, workloads as W
@@ -552,7 +553,7 @@ def run_umesh_variant(peaks, fp64_peak, precision=None):
     sn = m.nA[:, :2] @ sdir.T                       # [face, azimuth], out of the owner
     inflow = (sn < 0).sum() + (sn[m.neighbor >= 0] > 0).sum()
     nin = inflow / (m.ncells * dirs.n_azim)
-    flops = 2.0 * (2 + nin) + 2.0
+    flops = 2.0 * (2 + nin)
     fl = ups * flops
     s.close()
     del s
@@ -561,8 +562,9 @@ def run_umesh_variant(peaks, fp64_peak, precision=None):
         roof = {"bound": "alu", "achieved": fl / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
                 "frac": fl / fp64_peak, "flop_per_update": flops,
                 "peak_source": "bte_measure_peak(BTE_PEAK_FP64_FMA), measured"}
-    else:  # B (or I^n), R and I^{k+1} in the sweep, I^{k+1} again in the per-cell step
-        bpu = 16 if prec == bte.BTE_FP32 else 10   # BF16: 2-byte I, R stays a 4-byte float
+    else:  # algorithmic: I^n (or B), I^k (each row once from DRAM) and I^{k+1}; the sweep also
+        # reads the R table and the per-cell step reads I^{k+1} again (not counted)
+        bpu = 12 if prec == bte.BTE_FP32 else 6
         gbs = ups * bpu / 1e9
         roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": gbs / peaks["hbm_gbs"], "bytes_per_update": bpu}

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <tuple>
@@ -750,6 +751,22 @@ cudaError_t enqueue_step(bte_ctx* h, SweepArgs a, int ninner, int scheme, cudaSt
 }  // namespace
 
 namespace bte {
+
+cudaError_t raise_dynamic_smem(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> granted;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& g = granted[{dev, func}];
+  if (bytes <= g) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) g = bytes;
+  return e;
+}
+
 
 int flux_view(bte_ctx* h, int geom, FluxView* out) {
   int rc = check_geom(h, geom);

@@ -163,6 +163,12 @@ struct SweepArgs {
 
 // Launchers (bte_kernels.cu).  precision: BTE_FP64 = 0, BTE_FP32 = 1, BTE_BF16 = 2.
 int values_per_lane(int precision);
+// Raises the dynamic shared memory limit of kernel func on the current device
+// to at least bytes (no call below 48 KB).  The limit only grows, under a
+// lock: handles on several host threads launch the same kernel with different
+// needs, and a per-launch setting could lower another thread's limit between
+// its own setting and its launch.
+cudaError_t raise_dynamic_smem(const void* func, size_t bytes);
 cudaError_t launch_sweep(int precision, int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
 cudaError_t launch_sweep_fp64(int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);
 cudaError_t launch_sweep_fp32(int pd, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s);

@@ -601,12 +601,12 @@ cudaError_t launch_minb(const SweepArgs& a, int dim, int threads, int grid, cuda
                       (size_t)(dim == 3 ? Ring<3, S>::kStages * Ring<3, S>::kOps : Ring<2, S>::kStages * Ring<2, S>::kOps) *
                           threads * 16;
   if (dim == 3) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(sweep_kernel<3, S, MINB, BM, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = raise_dynamic_smem((const void*)sweep_kernel<3, S, MINB, BM, TT>, smem);
+    if (e != cudaSuccess) return e;
     sweep_kernel<3, S, MINB, BM, TT><<<grid, threads, smem, s>>>(a);
   } else {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(sweep_kernel<2, S, MINB, BM, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = raise_dynamic_smem((const void*)sweep_kernel<2, S, MINB, BM, TT>, smem);
+    if (e != cudaSuccess) return e;
     sweep_kernel<2, S, MINB, BM, TT><<<grid, threads, smem, s>>>(a);
   }
   return cudaGetLastError();

@@ -266,8 +266,8 @@ cudaError_t launch_shape(const SweepArgs& a, int threads, int grid, cudaStream_t
   const size_t smem = sizeof(DirFF) * (size_t)a.nd + 16 + 2 * (size_t)threads * sizeof(double) +
                       (2 * (size_t)cpb * a.lpc + 4 * (size_t)cpb) * sizeof(double) + 16 +
                       (size_t)RingFF<DIM, MINB>::kStages * RingFF<DIM, MINB>::kOps * threads * 16;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(sweep_ff_kernel<DIM, MINB, BM, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const cudaError_t e = raise_dynamic_smem((const void*)sweep_ff_kernel<DIM, MINB, BM, FF>, smem);
+  if (e != cudaSuccess) return e;
   sweep_ff_kernel<DIM, MINB, BM, FF><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
