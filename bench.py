@@ -365,7 +365,7 @@ def run_variants(peaks, fp64_peak):
                     "peak_source": "bte_measure_peak(BTE_PEAK_FP64_FMA), measured", "hbm": roof}
         dtype = {bte.BTE_FP64: "f64 storage, double-float (f32x2) sweep arithmetic", bte.BTE_FP32: "f32",
                  bte.BTE_BF16: "bf16-storage/f32"}[prec]
-        if kw.get("fp64_strict") or (prec == bte.BTE_FP64 and ninner < 2):
+        if kw.get("fp64_strict"):
             dtype = "f64"
         out.append({"workload": name, "dtype": dtype, "value": ups,
                     "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "inner_iterations_per_step": ninner,
@@ -435,7 +435,8 @@ def run_paper_device_20us(peaks):
     TL = s.T(0, bte.BTE_T_LATTICE).reshape(g.ny, g.nx)
     ups = wl.dof * wl.nsteps / (dev_ms * 1e-3)
     rows = list(range(0, g.ny, 10)) + [g.ny // 2]
-    out = {"workload": "fp64_paper_device_120x120_20dir_20us", "dtype": "f64", "value": ups, "unit": UNIT,
+    out = {"workload": "fp64_paper_device_120x120_20dir_20us",
+           "dtype": "f64 storage, double-float (f32x2) sweep arithmetic", "value": ups, "unit": UNIT,
            "steps": wl.nsteps, "inner_iterations_per_step": 1, "ms_per_step": dev_ms / wl.nsteps,
            "simulated_s": wl.nsteps * wl.dt, "launch": choice, "roofline": hbm_roof(ups, 24, peaks),
            "energy_record": {
@@ -725,8 +726,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": hbm / peaks["hbm_gbs"], "traffic": (tpu * upd_launch) if tpu else None,
                 "peak_source": f"hbm_gbs of {peak_src} peaks (copy bandwidth)",
-                "kernel": "sweep_kernel<2, double, MINB, 2, false, 3> (double-float variant of inner iterations "
-                          "2..14: B and I^k read as ff pairs, I^{k+1} written as ff pairs)",
+                "kernel": "sweep_ff_kernel<2, MINB, 2, 3> (double-float sweep of inner iterations 2..15: "
+                          "B and I^k read as ff pairs, I^{k+1} written as ff pairs)",
                 "launch_ms": launch_ms, "launches_averaged": len(mid), "bytes_per_update": BYTES_PER_UPDATE_FP64,
                 "sweep_ms_last_step": [round(float(x), 4) for x in sweep_ms],
                 "timing": "CUDA events recorded by the step graph around each sweep launch, last timed step",

@@ -97,7 +97,7 @@ typedef struct {
  *             (default) keeps tau fixed; |beta_T_exp| <= 16.  The factor is
  *             common to all bands, so the T_p equation keeps its root.
  *  fp64_strict BTE_FP64 only.  0 (default): the implicit point-Jacobi sweep
- *             (ninner >= 2) of a handle with fixed relaxation rates and
+ *             (any ninner) of a handle with fixed relaxation rates and
  *             isothermal or mirror walls keeps the intensity in double-float
  *             form (two floats, 48-bit significand) and computes the update on
  *             the FP32 pipe with error-free transformations; the reduction,

@@ -5,7 +5,9 @@
 //   I^{k+1} = R (I^n/dt + v_b sum_ax c_ax,d I_up,ax^k + beta_b I0_b^k),
 //   R = 1 / (1/dt + beta_b + v_b sum_ax c_ax,d),  c_ax,d = |S_d,ax| / (w_d Delta_ax),
 // is evaluated as B + R (v_b sum_ax c_ax u_ax + beta_b I0) with B = (R/dt) I^n
-// kept across the inner iterations of a step, in double-float arithmetic on
+// kept across the inner iterations of a step (BM 1 forms and stores B, BM 2
+// reads it, BM 0, a step of one inner iteration, forms it only), in
+// double-float arithmetic on
 // the FP32 pipe (bte_ff.cuh): c_ax per direction sits in a shared table, v_b
 // and beta_b of the lane's two bands in registers, beta_b I0_b per cell in
 // registers, and only R per (direction, band) is read per step.  A step
@@ -66,7 +68,7 @@ struct MaxRegFF {
 
 template <int DIM, int MINB, int BM, int FF>
 __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegFF<MINB>::value) sweep_ff_kernel(SweepArgs a) {
-  static_assert(FF != 0 && BM != 0, "double-float B-form variants only");
+  static_assert(FF != 0, "double-float variants only");
   static_assert(BM != 2 || (FF & 1) != 0, "B is an ff pair");
   constexpr int V = 2;
   constexpr int kOps = RingFF<DIM, MINB>::kOps;
@@ -222,12 +224,14 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
           ff::P2 rf;
           if constexpr (BM == 2) {
             rf = ff::norm(ff::add(ff::lds(sb), p));
-          } else {  // B = (R / dt) I^n, kept for the later inner iterations
+          } else {  // B = (R / dt) I^n, kept for the later inner iterations when BM == 1
             const ff::P2 vin = (FF & 1) ? ff::lds(sb) : ff::lds_doubles(sb);
             const ff::P2 B = ff::norm(ff::mul(rdt2, ff::mul(Rv, vin)));
-            if constexpr ((FF & 2) != 0) ff::st_stream(pbout, B);
-            else ff::st_stream_doubles(pbout, B);
-            pbout += dst;
+            if constexpr (BM == 1) {
+              if constexpr ((FF & 2) != 0) ff::st_stream(pbout, B);
+              else ff::st_stream_doubles(pbout, B);
+              pbout += dst;
+            }
             rf = ff::norm(ff::add(B, p));
           }
           if constexpr ((FF & 2) != 0) ff::st_stream(pout, rf);
@@ -287,6 +291,8 @@ cudaError_t launch_variant(int variant, const SweepArgs& a, int dim, int threads
 // CTAs of more than 224 threads take variant 1)
 inline cudaError_t launch(int variant, const SweepArgs& a, int dim, int threads, int grid, cudaStream_t s) {
   if (a.beta_exp != 0.0) return cudaErrorInvalidValue;
+  if (a.bmode == 0 && a.ff == 2) return launch_variant<0, 2>(variant, a, dim, threads, grid, s);
+  if (a.bmode == 0 && a.ff == 3) return launch_variant<0, 3>(variant, a, dim, threads, grid, s);
   if (a.bmode == 1 && a.ff == 2) return launch_variant<1, 2>(variant, a, dim, threads, grid, s);
   if (a.bmode == 1 && a.ff == 3) return launch_variant<1, 3>(variant, a, dim, threads, grid, s);
   if (a.bmode == 2 && a.ff == 3) return launch_variant<2, 3>(variant, a, dim, threads, grid, s);
