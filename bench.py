@@ -759,7 +759,7 @@ def main():
            "scaling": "strong" if partitioned else "weak",
            "vs_baseline": None, "dtype": "f64 storage, double-float (f32x2) sweep arithmetic", "data": "synthetic",
            "config": workload_config(args, world, partitioned),
-           "launch": ("CUDA graph per time step, autotuned (cells_per_cta,threads,grid,min_ctas_variant): "
+           "launch": ("CUDA graph per time step, autotuned (cells_per_cta,threads,grid,min_ctas_variant,directions_per_step): "
                       + tune_choice) if (tuned and not partitioned) else
                      ("eager launches (band-range exchange on the host between launches), " + tune_choice),
            "l2": "inputs larger than L2 (three FP64 intensity buffers of %.2f GB each)" % (wl.dof * 8 / 1e9),

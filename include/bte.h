@@ -247,8 +247,9 @@ int bte_set_initial(bte_handle h, int geom, const double* T_cells, double T_unif
  * stats: host, may be NULL (then the call only queues work and returns). */
 int bte_step(bte_handle h, double dt, int nsteps, int ninner, int scheme, bte_stats* stats);
 
-/* Times the sweep over candidate launch shapes (cells per CTA x grid size,
- * persistent grids of 2/4/8 CTAs per SM or one CTA per work item) with the
+/* Times the sweep over candidate launch shapes (directions per team step:
+ * the default and half of it; cells per CTA; grid size, persistent grids of
+ * 2/4 CTAs per SM or one CTA per work item; 2 or 3 CTAs per SM) with the
  * current state and keeps the fastest for this handle.  With scheme
  * BTE_IMPLICIT_GS it times the sweep-ordered pass instead, over directions
  * per CTA and the column-tile size.  The timing launches write only a spare

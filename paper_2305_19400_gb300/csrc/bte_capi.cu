@@ -265,13 +265,13 @@ size_t carve(bte_ctx* h, char* base) {
 // geometries are walked in column blocks of bx x by cells marching in z, so
 // the z-upwind plane of a block (bx*by cells back) is still in L2 when reused.
 constexpr int kStrip2D = 64;
-void build_items(bte_ctx* h, int cpb = 0) {
+void build_items(bte_ctx* h, int cpb = 0, int dteam = 0) {
   h->lpc = h->nbp / values_per_lane(h->opts.precision);  // one vector of bands per lane
   // a cell team covers dteam directions per step: ~896 contiguous bytes of a row,
   // but at least ~32 steps per lane, so the per-cell epilogue stays a small share
   // when there are few directions
   const int rowb = h->nbp * (int)elem_bytes(h->opts.precision);
-  h->dteam = std::max(1, std::min(std::min(896 / rowb, 256 / h->lpc), h->nd / 32));
+  h->dteam = dteam > 0 ? dteam : std::max(1, std::min(std::min(896 / rowb, 256 / h->lpc), h->nd / 32));
   const int team = h->lpc * h->dteam;
   // default: the most cells whose CTA (at most 256 threads) is whole warps, else
   // the most that fit
@@ -1265,25 +1265,31 @@ int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t repor
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev);
   const int spare = (h->cur + 1) % 3;  // timing launches write here; the state is untouched (dry epilogue)
-  struct Cand { int cpb, grid, pd; float ms; };
+  struct Cand { int cpb, dteam, grid, pd; float ms; };
   std::vector<Cand> tried;
-  // cells per CTA: about 128 or 256 threads, and every count up to 256 threads
-  // whose CTA is whole warps (a partial warp still occupies the FP64 pipe's
-  // issue slots of a full one)
-  const int team = h->lpc * h->dteam;
-  std::vector<int> cpb_list = {std::max(1, 128 / team), std::max(1, 256 / team)};
-  const int whole = 32 / std::gcd(team, 32);
-  for (int c = whole; c * team <= 256; c += whole) cpb_list.push_back(c);
+  // directions per team step: the default and half of it (fewer lanes per
+  // cell, longer items: the per-item epilogue is spread over more updates)
+  build_items(h);
+  std::vector<int> dteam_list = {h->dteam};
+  if (h->dteam >= 2) dteam_list.push_back(h->dteam / 2);
   const int pd_list[2] = {1, 2};
-  int best_cpb = h->cpb, best_grid = h->grid, best_pd = h->pd;
+  int best_cpb = h->cpb, best_dteam = h->dteam, best_grid = h->grid, best_pd = h->pd;
   float best_ms = 1e30f;
   int dim = 2;
   for (auto& g : h->geoms) dim = std::max(dim, g.dim);
+  for (int dteam : dteam_list) {
+  // cells per CTA: about 128 or 256 threads, and every count up to 256 threads
+  // whose CTA is whole warps (a partial warp still occupies the FP64 pipe's
+  // issue slots of a full one)
+  const int team = h->lpc * dteam;
+  std::vector<int> cpb_list = {std::max(1, 128 / team), std::max(1, 256 / team)};
+  const int whole = 32 / std::gcd(team, 32);
+  for (int c = whole; c * team <= 256; c += whole) cpb_list.push_back(c);
   for (int cpb : cpb_list) {
     bool seen = false;
-    for (auto& c : tried) seen |= c.cpb == cpb;
+    for (auto& c : tried) seen |= c.cpb == cpb && c.dteam == dteam;
     if (seen) continue;
-    build_items(h, cpb);
+    build_items(h, cpb, dteam);
     CUDA_TRY(h, cudaMemcpyAsync(h->items_d, h->items.data(), h->items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
     const int nit = (int)h->items.size();
     const int grids[3] = {std::min(nit, 65535), std::min(nit, 2 * sms), std::min(nit, 4 * sms)};
@@ -1291,7 +1297,7 @@ int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t repor
       for (int pd : pd_list) {
         const int grid = grids[gi];
         bool dup = false;
-        for (auto& c : tried) dup |= c.cpb == cpb && c.grid == grid && c.pd == pd;
+        for (auto& c : tried) dup |= c.cpb == cpb && c.dteam == dteam && c.grid == grid && c.pd == pd;
         if (dup) continue;
         SweepArgs a = sweep_args(h);
         a.dry = 1;
@@ -1310,23 +1316,25 @@ int bte_autotune(bte_handle h, double dt, int scheme, char* report, size_t repor
         float ms = 0.f;
         CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
         ms /= 3.f;
-        tried.push_back({cpb, grid, pd, ms});
-        if (ms < best_ms) { best_ms = ms; best_cpb = cpb; best_grid = grid; best_pd = pd; }
+        tried.push_back({cpb, dteam, grid, pd, ms});
+        if (ms < best_ms) { best_ms = ms; best_cpb = cpb; best_dteam = dteam; best_grid = grid; best_pd = pd; }
       }
   }
-  build_items(h, best_cpb);
+  }
+  build_items(h, best_cpb, best_dteam);
   h->grid = best_grid;
   h->pd = best_pd;
   CUDA_TRY(h, cudaMemcpyAsync(h->items_d, h->items.data(), h->items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaStreamSynchronize(s));
   drop_graphs(h);
   char buf[256];
-  h->tune_report = "cells_per_cta,threads,grid,min_ctas_variant,ms_per_launch\n";
+  h->tune_report = "cells_per_cta,threads,grid,min_ctas_variant,ms_per_launch,directions_per_step\n";
   for (auto& c : tried) {
-    snprintf(buf, sizeof buf, "%d,%d,%d,%d,%.4f\n", c.cpb, c.cpb * h->lpc * h->dteam, c.grid, c.pd, c.ms);
+    snprintf(buf, sizeof buf, "%d,%d,%d,%d,%.4f,%d\n", c.cpb, c.cpb * h->lpc * c.dteam, c.grid, c.pd, c.ms, c.dteam);
     h->tune_report += buf;
   }
-  snprintf(buf, sizeof buf, "chosen,%d,%d,%d,%d\n", best_cpb, best_cpb * h->lpc * h->dteam, best_grid, best_pd);
+  snprintf(buf, sizeof buf, "chosen,%d,%d,%d,%d,%d\n", best_cpb, best_cpb * h->lpc * h->dteam, best_grid, best_pd,
+           h->dteam);
   h->tune_report += buf;
   if (report && report_len) {
     std::strncpy(report, h->tune_report.c_str(), report_len - 1);

@@ -45,6 +45,26 @@ struct DirFF {
   ff::x2 cl[3];    // c_ax,d low part in both halves
 };
 
+// L2 cache policies of the staged copies: the R table (one row per
+// direction and band, read by every item of the launch) is kept
+// (evict_last); B or I^n, read once per launch, leaves first (evict_first).
+// The upwind rows of I^k, read again by the neighbouring cells, keep the
+// default policy.
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void cp_async_l2(unsigned smem, const void* g, unsigned long long policy) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(smem), "l"(g), "l"(policy)
+               : "memory");
+}
+
 // Ring depth: 4 stages when two CTAs share an SM, 3 when three do (the
 // shared memory of three 224-thread CTAs).
 template <int DIM, int MINB>
@@ -165,10 +185,11 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
         const double* pR = Rrow + (long long)dg * nbp;
         int ji = 0;
         unsigned sbi = rb0;
+        const unsigned long long keep = l2_evict_last(), once = l2_evict_first();
         auto issue = [&]() {
           if (ji < nsteps) {
             const int d = dg + ji * dstep;
-            cp_async<16>(sbi, pin);
+            cp_async_l2(sbi, pin, once);
             if constexpr (kInt) {
               const int up = dsm[d].up;
               cp_async<16>(sbi + ostr, pik + ((up & 1) ? -sx_ : sx_));
@@ -182,7 +203,7 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
               cp_async<16>(sbi + 2 * ostr, sweep::upwind_src<1, double>(a, gp, c, di, off, b0));
               if (DIM == 3) cp_async<16>(sbi + 3 * ostr, sweep::upwind_src<2, double>(a, gp, c, di, off, b0));
             }
-            cp_async<16>(sbi + (1 + DIM) * ostr, pR);
+            cp_async_l2(sbi + (1 + DIM) * ostr, pR, keep);
             pin += dst;
             pik += dst;
             pR += dst;
