@@ -19,7 +19,8 @@
 //   Fast2Sum (Dekker): the same when |a| >= |b|.
 //   TwoProd via FMA: p = fl(a b), e = fma(a, b, -p) = a b - p exactly.
 // The conversions between doubles and ff pairs use integer operations only
-// (no FP64 instruction): a double x with 2^-74 <= |x| < 2^127 splits into
+// (no FP64 or int/float conversion instruction on the common paths: on GB300
+// those share the slow FP64 pipe, measured): a double x with 2^-74 <= |x| < 2^127 splits into
 // hi = x rounded to 24 bits and lo = x - hi rounded to 24 bits (error below
 // 2^-49 |x|); other values (zero, tiny, huge, Inf, NaN) become (float(x), 0).
 #pragma once
@@ -113,18 +114,33 @@ __device__ __forceinline__ void acc(P2& s, const P2& p) {
 }
 
 // ---------------------------------------------------------------- conversions
-// Round-to-nearest split of one double (see the header).
+// Round-to-nearest split of one double (see the header), on the two 32-bit
+// words of its bits.
 __device__ __forceinline__ void split(double x, float& h, float& l) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned sgn = (unsigned)(u >> 32) & 0x80000000u;
-  const unsigned long long a = u & 0x7fffffffffffffffull;
-  const unsigned e = (unsigned)(a >> 52);
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sgn = hi & 0x80000000u;
+  const unsigned ahi = hi & 0x7fffffffu;  // |x|: ahi, lo
+  const unsigned e = ahi >> 20;
   if (e - 949u <= 200u) {  // 2^-74 <= |x| < 2^127
-    const unsigned long long ar = (a + 0x10000000ull) & ~0x1fffffffull;  // |x| to 24 bits, ties away from zero
-    h = __uint_as_float((unsigned)((ar >> 29) - (896ull << 23)) | sgn);    // rebias 1023 -> 127
-    const int k = (int)((unsigned)a - (unsigned)ar);                      // |x| - hi in units of 2^(e-1075)
-    const float sc = __uint_as_float((e - 948u) << 23);                   // 2^(e - 1075)
-    l = __uint_as_float(__float_as_uint(__int2float_rn(k) * sc) ^ sgn);
+    // |x| to 24 significant bits, ties away from zero: add 2^28 (carry into
+    // the high word) and keep the low word's top 3 bits
+    const unsigned lo2 = lo + 0x10000000u;
+    const unsigned ahr = ahi + (lo2 < lo ? 1u : 0u);
+    const unsigned lor = lo2 & 0xe0000000u;
+    h = __uint_as_float((((ahr << 3) | (lor >> 29)) - (896u << 23)) | sgn);  // rebias 1023 -> 127
+    const int k = (int)(lo - lor);                        // |x| - hi in units of 2^(e-1075)
+    const float sc = __uint_as_float((e - 948u) << 23);  // 2^(e - 1075)
+    // k sc rounded to float without an int-to-float conversion (those run on
+    // the slow FP64 pipe): |k| <= 2^28 as 2^14 kh + kl, each half exact
+    // through the 2^23 magic number, one FMA rounding the sum
+    const unsigned m = (unsigned)(k < 0 ? -k : k);
+    const float fh = __uint_as_float(0x4B000000u | (m >> 14)) - 8388608.0f;
+    const float fl = __uint_as_float(0x4B000000u | (m & 0x3fffu)) - 8388608.0f;
+    const float lv = fmaf(fh, sc * 16384.0f, fl * sc);
+    l = __uint_as_float(__float_as_uint(lv) ^ sgn ^ (k < 0 ? 0x80000000u : 0u));
+  } else if ((ahi | lo) == 0u) {  // zero (the padding bands): no conversion instruction
+    h = __uint_as_float(sgn);
+    l = 0.0f;
   } else {
     h = __double2float_rn(x);
     l = 0.0f;
@@ -139,24 +155,32 @@ __device__ __forceinline__ P2 from_doubles(double a, double b) {
 }
 
 // h + l of a normalised pair as a double (truncated to 53 bits, below the
-// pair's own rounding).  Zero gives zero; Inf and NaN keep their class.
+// pair's own rounding), built on the two 32-bit words of its bits.  Zero gives
+// zero; Inf and NaN keep their class.
 __device__ __forceinline__ double to_double(float h, float l) {
   const unsigned hb = __float_as_uint(h), lb = __float_as_uint(l);
   const unsigned ah = hb & 0x7fffffffu;
   const unsigned eh = ah >> 23;
-  const unsigned long long sg = (unsigned long long)(hb & 0x80000000u) << 32;
-  if (eh == 0u) return __longlong_as_double((long long)sg);  // zero (and subnormal hi, flushed)
-  if (eh == 255u)                                              // Inf / NaN
-    return __longlong_as_double((long long)(sg | 0x7ff0000000000000ull | ((ah & 0x7fffffu) ? (1ull << 51) : 0ull)));
-  unsigned long long D = ((unsigned long long)((ah >> 3) + (896u << 20)) << 32) | (unsigned long long)(ah << 29);
+  const unsigned sg = hb & 0x80000000u;
+  if (eh == 0u) return __hiloint2double((int)sg, 0);  // zero (and subnormal hi, flushed)
+  if (eh == 255u)                                       // Inf / NaN
+    return __hiloint2double((int)(sg | 0x7ff00000u | ((ah & 0x7fffffu) ? 0x80000u : 0u)), 0);
+  unsigned dhi = (ah >> 3) + (896u << 20), dlo = ah << 29;  // h as a double's bits
   const unsigned el = (lb >> 23) & 0xffu;
   const unsigned ml = el ? ((lb & 0x7fffffu) | 0x800000u) : 0u;
   const int sh = (int)el - (int)eh + 29;  // l in units of the double ulp of h: ml * 2^sh, sh <= 5
   unsigned k = sh >= 0 ? (ml << sh) : (ml >> min(-sh, 31));
   const bool opp = ((hb ^ lb) >> 31) != 0u;
   if (opp && (ah & 0x7fffffu) == 0u) k <<= 1;  // just below a power of two the double ulp halves
-  D = opp ? D - k : D + k;
-  return __longlong_as_double((long long)(D | sg));
+  if (opp) {  // subtract k with the borrow into the high word
+    dhi -= dlo < k ? 1u : 0u;
+    dlo -= k;
+  } else {    // add k with the carry
+    const unsigned s2 = dlo + k;
+    dhi += s2 < dlo ? 1u : 0u;
+    dlo = s2;
+  }
+  return __hiloint2double((int)(dhi | sg), (int)dlo);
 }
 
 __device__ __forceinline__ void to_doubles(const P2& p, double& a, double& b) {
