@@ -35,6 +35,7 @@
 #pragma once
 #include <type_traits>
 
+#include "bte_ff.cuh"
 #include "bte_store.cuh"
 
 namespace bte {
@@ -290,6 +291,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
     vb[v] = kDev ? (A)a.vb32[b0 + v] : (A)0;
     bb[v] = kDev ? (A)a.bb32[b0 + v] : (A)0;
   }
+  // reduced modes: the scheme's scalars in both halves of a packed pair
+  const bool expl = a.explicit_scheme != 0;
+  const ff::x2 dt2 = ff::pack(a.dt32, a.dt32), ndt2 = ff::pack(-a.dt32, -a.dt32), rdt2 = ff::pack(a.rdt32, a.rdt32),
+               one2 = ff::pack(1.0f, 1.0f);
   __syncthreads();
 
   for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
@@ -525,24 +530,36 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
           }
         } else {
           // P and Q from v_b, beta_b and sum_ax c_ax (no table loads):
-          // implicit Q = 1/(1/dt + beta_b + v_b sum c), P = Q/dt; explicit P = 1 - dt(beta_b + v_b sum c), Q = dt
+          // implicit Q = 1/(1/dt + beta_b + v_b sum c), P = Q/dt; explicit P = 1 - dt(beta_b + v_b sum c), Q = dt.
+          // Two bands per packed f32x2 instruction (each half rounds as the
+          // scalar instruction would: the same values as band by band).
           const float4 cc = dsm[d].c;
+          const ff::x2 ccw = ff::pack(cc.w, cc.w), ccx = ff::pack(cc.x, cc.x), ccy = ff::pack(cc.y, cc.y),
+                       ccz = ff::pack(cc.z, cc.z);
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const A rate = fma(vb[v], cc.w, bb[v]);
-            A Pc, Qc;
-            if (a.explicit_scheme) {
-              Qc = a.dt32;
-              Pc = fma(-a.dt32, rate, 1.0f);
+          for (int q = 0; q < V / 2; ++q) {
+            const int v = 2 * q;
+            const ff::x2 vb2 = ff::pack(vb[v], vb[v + 1]);
+            const ff::x2 rate = ff::fma(vb2, ccw, ff::pack(bb[v], bb[v + 1]));
+            ff::x2 Pc, Qc;
+            if (expl) {
+              Qc = dt2;
+              Pc = ff::fma(ndt2, rate, one2);
             } else {
-              asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(Qc) : "f"(a.rdt32 + rate));
-              Pc = Qc * a.rdt32;
+              const ff::x2 den = ff::add(rdt2, rate);
+              float q0, q1;
+              asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q0) : "f"(ff::lo_of(den)));
+              asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q1) : "f"(ff::hi_of(den)));
+              Qc = ff::pack(q0, q1);
+              Pc = ff::mul(Qc, rdt2);
             }
-            A f = cc.x * ux[v];
-            f = fma(cc.y, uy[v], f);
-            if (DIM == 3) f = fma(cc.z, uz[v], f);
-            const A t = fma(vb[v], f, src[v]);
-            r[v] = fma(Qc, t, Pc * vn[v]);
+            ff::x2 f = ff::mul(ccx, ff::pack(ux[v], ux[v + 1]));
+            f = ff::fma(ccy, ff::pack(uy[v], uy[v + 1]), f);
+            if (DIM == 3) f = ff::fma(ccz, ff::pack(uz[v], uz[v + 1]), f);
+            const ff::x2 t = ff::fma(vb2, f, ff::pack(src[v], src[v + 1]));
+            const ff::x2 rr = ff::fma(Qc, t, ff::mul(Pc, ff::pack(vn[v], vn[v + 1])));
+            r[v] = ff::lo_of(rr);
+            r[v + 1] = ff::hi_of(rr);
           }
           if constexpr (sizeof(S) == 2) {
             // store the rounded values and sum exactly what was stored
@@ -553,8 +570,13 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
             T::st(c.out + off, r);
           }
           const float wd = dsm[d].w32;
+          const ff::x2 wd2 = ff::pack(wd, wd);
 #pragma unroll
-          for (int v = 0; v < V; ++v) acc[v] = fma(wd, r[v], acc[v]);
+          for (int q = 0; q < V / 2; ++q) {
+            const ff::x2 a2 = ff::fma(wd2, ff::pack(r[2 * q], r[2 * q + 1]), ff::pack(acc[2 * q], acc[2 * q + 1]));
+            acc[2 * q] = ff::lo_of(a2);
+            acc[2 * q + 1] = ff::hi_of(a2);
+          }
           // FP32 partials go to FP64 every 16 directions (every 64 for BF16 storage,
           // whose 2^-8 rounding dwarfs the float sum's)
           if (++nacc == (sizeof(S) == 2 ? 64 : 16)) {
