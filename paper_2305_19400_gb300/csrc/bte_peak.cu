@@ -1,6 +1,6 @@
 // bte_peak.cu -- arithmetic peaks of the current GPU, measured by FMA loops.
 //
-// The FP64-mode sweep is judged against the FP64 pipe's rate and its
+// The FP64-mode sweep is measured against the FP64 pipe's rate and its
 // double-float form against the FP32 pipe's rate; neither is in a vendor table
 // one can trust for a given part and clock, so the library measures them:
 // every thread runs kChains independent FMA chains (enough to cover the
