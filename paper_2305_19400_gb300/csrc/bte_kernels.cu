@@ -26,32 +26,41 @@ namespace bte {
 namespace {
 
 // Exact temperature solve of the cells the sweep could not settle on their
-// cached model: one CTA per cell (exact_solve_cta spreads each evaluation over
-// the SM's four FP64 units; with a handful of such cells per step the solve's
-// latency, not its throughput, is what the step waits for).  The start is the
-// model root, or when there is none the previous T_p (plain mode) or the
-// learned guess (net A, then surrogate Newton steps on net B, by warp 0); the
-// exact FP64 quadrature then refines it (each evaluation becomes the cell's
-// cached model) and I0 is refreshed.
+// cached model: one thread-block cluster of kFixCluster CTAs per cell
+// (exact_solve_cluster spreads each evaluation's bands over the cluster's SMs;
+// with a handful of such cells per step the solve's latency, not its
+// throughput, is what the step waits for).  The start is the model root, or
+// when there is none the previous T_p (plain mode) or the learned guess (net
+// A, then surrogate Newton steps on net B, by warp 0 of each CTA: the same
+// value everywhere); the exact FP64 quadrature then refines it (each
+// evaluation becomes the cell's cached model) and every CTA refreshes I0 of
+// the bands whose model row it wrote.
 constexpr int kFixThreads = 128;
+constexpr int kFixCluster = 4;
 
-__global__ void __launch_bounds__(kFixThreads) fixup_kernel(SweepArgs a, int learned, MLPView m) {
-  extern __shared__ double fsm[];  // exact_solve_cta scratch, T0, then the learned-mode buffers
+__global__ void __cluster_dims__(kFixCluster, 1, 1) __launch_bounds__(kFixThreads)
+    fixup_kernel(SweepArgs a, int learned, MLPView m) {
+  extern __shared__ double fsm[];  // exact_solve_cluster scratch, T0, then the learned-mode buffers
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), nr = (int)cl.num_blocks();
+  const unsigned cid = blockIdx.x / (unsigned)nr, ncl = gridDim.x / (unsigned)nr;
   const int nbp = a.th.nbp;
+  const int own0 = rank * nbp / nr, own1 = (rank + 1) * nbp / nr;  // bands whose model row this CTA writes
   double* solve_sm = fsm;
   double* t0_sm = fsm + cta_solve_smem_doubles(nbp);
   float* ybuf = reinterpret_cast<float*>(t0_sm + 2);
   float* hbuf = ybuf + 2 * nbp;
   const unsigned count = *a.fix_count;
   unsigned long long evals = 0, fb = 0, bad = 0;
-  for (unsigned w = blockIdx.x; w < count; w += gridDim.x) {
+  for (unsigned w = cid; w < count; w += ncl) {  // the same items, in the same order, in every CTA of the cluster
     const FixItem it = a.fix[w];
     const long long P = it.P;
     // learned mode: the networks' guess starts the cells that have no usable
     // root of their cached model (a cold or far-off start); a model root, when
     // there is one, is the closer start (measured: twice the evaluations from
     // the networks' guess on the learned 3-D workload)
-    const bool net = learned && !it.model;  // uniform over the CTA (one item)
+    const bool net = learned && !it.model;  // uniform over the cluster (one item)
     if (net) {
       if (threadIdx.x < 32) {
         const double g = mlp_guess_T(m, a.th.a_p, it.Ep, 2, ybuf, hbuf);
@@ -60,18 +69,19 @@ __global__ void __launch_bounds__(kFixThreads) fixup_kernel(SweepArgs a, int lea
       __syncthreads();
     }
     const double T0 = net ? t0_sm[0] : it.T0;
-    const SolveResult r = exact_solve_cta(a.th, it.Ep, T0, a.trust_rel, a.maxit, a.J + (P * 3) * nbp, solve_sm);
+    const SolveResult r = exact_solve_cluster(a.th, it.Ep, T0, a.trust_rel, a.maxit, a.J + (P * 3) * nbp, solve_sm);
     evals += r.evals;
     fb += r.fallback;
     bad += r.bad;
-    __syncthreads();  // the model row written by the solve, before the I0 refresh reads it
-    // I0 refresh of the stored bands from the (just written) model at r.Te
+    __syncthreads();  // this CTA's model rows, written by the solve, before its I0 refresh reads them
+    // I0 refresh of the stored bands whose model rows this CTA wrote, at r.Te
     const double hd2 = 0.5 * r.delta * r.delta;
-    for (int b = threadIdx.x; b < a.th.nbo; b += blockDim.x) {
+    const int s0 = max(own0 - a.th.band0, 0), s1 = min(own1 - a.th.band0, a.th.nbo);
+    for (int b = s0 + (int)threadIdx.x; b < s1; b += blockDim.x) {
       const long long j = (P * 3) * nbp + a.th.band0 + b;
       a.I0cell[P * a.th.nbo + b] = b < a.th.nbr ? fma(a.J[j + 2 * nbp], hd2, fma(a.J[j + nbp], r.delta, a.J[j])) : 0.0;
     }
-    if (threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
       a.Teval[P] = r.Te;
       a.Tp[P] = r.Te + r.delta;
       a.Msum[3 * P] = r.M[0];  // the model just written to J
@@ -80,7 +90,8 @@ __global__ void __launch_bounds__(kFixThreads) fixup_kernel(SweepArgs a, int lea
     }
     __syncthreads();  // t0_sm and the solve scratch are reused by the next item
   }
-  if (threadIdx.x == 0 && a.counters) {
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+  if (rank == 0 && threadIdx.x == 0 && a.counters) {
     if (evals) atomicAdd(&a.counters->evals, evals);
     if (fb) atomicAdd(&a.counters->fallbacks, fb);
     if (bad) atomicAdd(&a.counters->nonfinite, bad);
@@ -684,7 +695,7 @@ cudaError_t launch_fixup(const SweepArgs& a, const MLPView* mlp, cudaStream_t s)
                     (mlp ? (2 * (size_t)a.th.nbp + 4 * kHidden) * sizeof(float) : 0);
   MLPView m{};
   if (mlp) m = *mlp;
-  fixup_kernel<<<2 * 152, kFixThreads, sm, s>>>(a, mlp ? 1 : 0, m);
+  fixup_kernel<<<2 * 152, kFixThreads, sm, s>>>(a, mlp ? 1 : 0, m);  // 76 clusters of kFixCluster CTAs
   return cudaGetLastError();
 }
 

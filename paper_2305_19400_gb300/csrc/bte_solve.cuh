@@ -1,5 +1,6 @@
-// bte_solve.cuh -- exact FP64 solve of the T_p equation for one cell, by one warp or one CTA.
+// bte_solve.cuh -- exact FP64 solve of the T_p equation for one cell, by one warp or one thread-block cluster.
 #pragma once
+#include <cooperative_groups.h>
 #include "bte_quad.cuh"
 
 namespace bte {
@@ -116,32 +117,41 @@ __device__ inline SolveResult exact_solve_warp(const ThermoTables& th, double Ep
   return c.finish();
 }
 
-// Shared memory (doubles) of exact_solve_cta.
+// Shared memory (doubles) of exact_solve_cluster, per CTA.
 __host__ __device__ constexpr int kCtaSolvePairs = 1024;  // (band, node) pairs per chunk
 __host__ __device__ inline int cta_solve_smem_doubles(int nbp) { return 3 * kCtaSolvePairs + 3 * nbp + 4; }
 
-// The same solve by a whole CTA, bit for bit the warp form's results: the
-// costly per-node terms (expm1, the reciprocal, the derivative factors) are
-// spread over every thread of the CTA, each band's node sum then runs in node
-// order on one thread, and warp 0 adds the bands exactly as the warp form
-// does.  A single cell's evaluation thus uses every FP64 unit of the SM
-// instead of one sub-partition's.  sm: cta_solve_smem_doubles(nbp) doubles.
-// All threads of the CTA must call it (it synchronises the CTA).
-__device__ inline SolveResult exact_solve_cta(const ThermoTables& th, double Ep, double T0, double trust_rel, int maxit,
-                                              double* Jrow, double* sm) {
+// The same solve by a thread-block cluster, bit for bit the warp form's
+// results.  CTA r of the C in the cluster evaluates the bands
+// [r nbp / C, (r + 1) nbp / C): the costly per-node terms (expm1, the
+// reciprocal, the derivative factors) are spread over its threads, and each
+// band's node sum runs in node order on one thread, writing f, f', f'' to the
+// CTA's own shared memory (and the cell's model row Jrow).  After a cluster
+// barrier warp 0 of CTA 0 adds the bands through distributed shared memory
+// in the warp form's order and publishes F, F', F''; after a second barrier
+// every CTA reads them and advances the same controller, so the loop ends on
+// the same evaluation everywhere.  One cell's evaluation thus runs on C SMs'
+// FP64 units.  sm: cta_solve_smem_doubles(nbp) doubles per CTA.  Every thread
+// of every CTA of the cluster must call it (it synchronises the cluster).
+__device__ inline SolveResult exact_solve_cluster(const ThermoTables& th, double Ep, double T0, double trust_rel,
+                                                  int maxit, double* Jrow, double* sm) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), nr = (int)cl.num_blocks();
   const double* wb = th.a_p;
   const int nbp = th.nbp, ng = th.ng;
+  const int own0 = rank * nbp / nr, own1 = (rank + 1) * nbp / nr;  // this CTA's bands
   const int cb = kCtaSolvePairs / ng;  // bands per chunk (ng <= kMaxGauss)
   double* pn = sm;                      // [pairs] n = 1 / expm1(x)
   double* pq = pn + kCtaSolvePairs;     // [pairs] n (1 + n) x
   double* pu = pq + kCtaSolvePairs;     // [pairs] (1 + 2n) x - 2
-  double* bv = pu + kCtaSolvePairs;     // [3][nbp] per band f, d1, d2
-  double* sums = bv + 3 * nbp;          // [3]
+  double* bv = pu + kCtaSolvePairs;     // [3][nbp] per band f, d1, d2 (own bands)
+  double* sums = bv + 3 * nbp;          // [3] (CTA 0 publishes)
   SolveCtl c(T0);
   for (int loop = 0; loop < maxit + 224 && !c.done; ++loop) {
     const double rT = 1.0 / c.T;
-    for (int b0 = 0; b0 < nbp; b0 += cb) {
-      const int npair = min(cb, nbp - b0) * ng;
+    for (int b0 = own0; b0 < own1; b0 += cb) {
+      const int npair = min(cb, own1 - b0) * ng;
       const double* cn = th.node_c + b0 * ng;
       for (int p = threadIdx.x; p < npair; p += blockDim.x) {
         const double x = cn[p] * rT;
@@ -173,14 +183,19 @@ __device__ inline SolveResult exact_solve_cta(const ThermoTables& th, double Ep,
       }
       __syncthreads();
     }
-    if (threadIdx.x < 32) {
+    cl.sync();  // every CTA's bands are in its bv
+    if (rank == 0 && threadIdx.x < 32) {
       const int lane = threadIdx.x;
       double F = 0.0, F1 = 0.0, F2 = 0.0;
       for (int b = lane; b < nbp; b += 32) {
+        int o = (int)(((long long)b * nr) / nbp);  // the CTA whose range holds b
+        while (o + 1 < nr && (o + 1) * nbp / nr <= b) ++o;
+        while (o > 0 && o * nbp / nr > b) --o;
+        const double* ob = cl.map_shared_rank(bv, (unsigned)o);
         const double ap = wb[b];
-        F = fma(ap, bv[b], F);
-        F1 = fma(ap, bv[nbp + b], F1);
-        F2 = fma(ap, bv[2 * nbp + b], F2);
+        F = fma(ap, ob[b], F);
+        F1 = fma(ap, ob[nbp + b], F1);
+        F2 = fma(ap, ob[2 * nbp + b], F2);
       }
       for (int o = 16; o > 0; o >>= 1) {
         F += __shfl_xor_sync(0xffffffffu, F, o);
@@ -193,8 +208,9 @@ __device__ inline SolveResult exact_solve_cta(const ThermoTables& th, double Ep,
         sums[2] = F2;
       }
     }
-    __syncthreads();
-    c.advance(sums[0], sums[1], sums[2], Ep, trust_rel, maxit);
+    cl.sync();  // the sums are published; every read of a remote bv is done
+    const double* s0 = cl.map_shared_rank(sums, 0u);
+    c.advance(s0[0], s0[1], s0[2], Ep, trust_rel, maxit);
   }
   return c.finish();
 }
