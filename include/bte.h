@@ -40,7 +40,8 @@ extern "C" {
 #define BTE_E_CUDA (-3)      /* a CUDA runtime call failed (message names it) */
 #define BTE_E_NOMEM (-4)     /* workspace too small or device allocation failed */
 #define BTE_E_NONFINITE (-5) /* a cell energy or temperature became NaN/Inf */
-#define BTE_E_TIMEOUT (-6)   /* a bounded device-side wait gave up */
+#define BTE_E_TIMEOUT (-6)   /* reserved for a bounded device-side wait that gave up; no kernel of this
+                              * library waits on another, so no call returns it */
 #define BTE_E_EXCHANGE (-7)  /* the band-range exchange callback returned non-zero */
 #define BTE_W_FALLBACK 1     /* success; some temperature solves fell back to bisection */
 
