@@ -53,6 +53,7 @@ __global__ void __cluster_dims__(kFixCluster, 1, 1) __launch_bounds__(kFixThread
   float* hbuf = ybuf + 2 * nbp;
   const unsigned count = *a.fix_count;
   unsigned long long evals = 0, fb = 0, bad = 0;
+  unsigned par = 0;  // evaluations of this cluster so far (the solve's buffer parity)
   for (unsigned w = cid; w < count; w += ncl) {  // the same items, in the same order, in every CTA of the cluster
     const FixItem it = a.fix[w];
     const long long P = it.P;
@@ -69,7 +70,7 @@ __global__ void __cluster_dims__(kFixCluster, 1, 1) __launch_bounds__(kFixThread
       __syncthreads();
     }
     const double T0 = net ? t0_sm[0] : it.T0;
-    const SolveResult r = exact_solve_cluster(a.th, it.Ep, T0, a.trust_rel, a.maxit, a.J + (P * 3) * nbp, solve_sm);
+    const SolveResult r = exact_solve_cluster(a.th, it.Ep, T0, a.trust_rel, a.maxit, a.J + (P * 3) * nbp, solve_sm, par);
     evals += r.evals;
     fb += r.fallback;
     bad += r.bad;

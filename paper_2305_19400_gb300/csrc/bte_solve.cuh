@@ -119,22 +119,26 @@ __device__ inline SolveResult exact_solve_warp(const ThermoTables& th, double Ep
 
 // Shared memory (doubles) of exact_solve_cluster, per CTA.
 __host__ __device__ constexpr int kCtaSolvePairs = 1024;  // (band, node) pairs per chunk
-__host__ __device__ inline int cta_solve_smem_doubles(int nbp) { return 3 * kCtaSolvePairs + 3 * nbp + 4; }
+__host__ __device__ inline int cta_solve_smem_doubles(int nbp) { return 3 * kCtaSolvePairs + 6 * nbp + 4; }
 
 // The same solve by a thread-block cluster, bit for bit the warp form's
 // results.  CTA r of the C in the cluster evaluates the bands
 // [r nbp / C, (r + 1) nbp / C): the costly per-node terms (expm1, the
 // reciprocal, the derivative factors) are spread over its threads, and each
 // band's node sum runs in node order on one thread, writing f, f', f'' to the
-// CTA's own shared memory (and the cell's model row Jrow).  After a cluster
-// barrier warp 0 of CTA 0 adds the bands through distributed shared memory
-// in the warp form's order and publishes F, F', F''; after a second barrier
-// every CTA reads them and advances the same controller, so the loop ends on
-// the same evaluation everywhere.  One cell's evaluation thus runs on C SMs'
-// FP64 units.  sm: cta_solve_smem_doubles(nbp) doubles per CTA.  Every thread
-// of every CTA of the cluster must call it (it synchronises the cluster).
+// CTA's own shared memory (and the cell's model row Jrow).  After one cluster
+// barrier warp 0 of every CTA adds all bands through distributed shared
+// memory in the warp form's order, so every CTA holds the same F, F', F'' and
+// advances the same controller, and the loop ends on the same evaluation
+// everywhere.  The band values alternate between two buffers over the
+// cluster's successive evaluations (par counts them across calls): evaluation
+// k writes buffer k % 2 after the barrier of evaluation k - 1, which every
+// reader of buffer (k - 2) % 2 has passed.  One cell's evaluation thus runs
+// on C SMs' FP64 units.  sm: cta_solve_smem_doubles(nbp) doubles per CTA.
+// Every thread of every CTA of the cluster must call it (it synchronises the
+// cluster).
 __device__ inline SolveResult exact_solve_cluster(const ThermoTables& th, double Ep, double T0, double trust_rel,
-                                                  int maxit, double* Jrow, double* sm) {
+                                                  int maxit, double* Jrow, double* sm, unsigned& par) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), nr = (int)cl.num_blocks();
@@ -145,10 +149,11 @@ __device__ inline SolveResult exact_solve_cluster(const ThermoTables& th, double
   double* pn = sm;                      // [pairs] n = 1 / expm1(x)
   double* pq = pn + kCtaSolvePairs;     // [pairs] n (1 + n) x
   double* pu = pq + kCtaSolvePairs;     // [pairs] (1 + 2n) x - 2
-  double* bv = pu + kCtaSolvePairs;     // [3][nbp] per band f, d1, d2 (own bands)
-  double* sums = bv + 3 * nbp;          // [3] (CTA 0 publishes)
+  double* bv2 = pu + kCtaSolvePairs;    // [2][3][nbp] per band f, d1, d2 (own bands), two buffers
+  double* sums = bv2 + 6 * nbp;         // [3] this CTA's copy of F, F', F''
   SolveCtl c(T0);
   for (int loop = 0; loop < maxit + 224 && !c.done; ++loop) {
+    double* bv = bv2 + (size_t)(par++ & 1u) * 3 * nbp;
     const double rT = 1.0 / c.T;
     for (int b0 = own0; b0 < own1; b0 += cb) {
       const int npair = min(cb, own1 - b0) * ng;
@@ -184,7 +189,7 @@ __device__ inline SolveResult exact_solve_cluster(const ThermoTables& th, double
       __syncthreads();
     }
     cl.sync();  // every CTA's bands are in its bv
-    if (rank == 0 && threadIdx.x < 32) {
+    if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       double F = 0.0, F1 = 0.0, F2 = 0.0;
       for (int b = lane; b < nbp; b += 32) {
@@ -208,9 +213,8 @@ __device__ inline SolveResult exact_solve_cluster(const ThermoTables& th, double
         sums[2] = F2;
       }
     }
-    cl.sync();  // the sums are published; every read of a remote bv is done
-    const double* s0 = cl.map_shared_rank(sums, 0u);
-    c.advance(s0[0], s0[1], s0[2], Ep, trust_rel, maxit);
+    __syncthreads();
+    c.advance(sums[0], sums[1], sums[2], Ep, trust_rel, maxit);
   }
   return c.finish();
 }
