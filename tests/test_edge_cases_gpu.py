@@ -149,3 +149,30 @@ def test_exact_fixup_with_32_gauss_nodes_and_110_bands():
         assert np.max(np.abs(s.T(0, which) - ost[key]) / ost[key]) <= 1e-12, key
     assert np.max(np.abs(s.intensity(0) - ost["I"]) / np.abs(ost["I"])) <= 1e-11
     s.close()
+
+
+@pytest.mark.parametrize("nb_split", [(1, 0), (2, 1)])
+def test_exact_fixup_with_fewer_bands_than_cluster_ctas(nb_split):
+    """The fix-up solves each cell on a cluster of four CTAs, CTA r owning the
+    bands [r nbp / 4, (r + 1) nbp / 4) of the padded band count nbp.  With one
+    band (nbp 2) or three (nbp 4, one padding band) some CTAs own no real band
+    or none at all, yet every CTA adds all bands in the same order and
+    advances the same solve.  A cold start far from equilibrium sends cells
+    to the fix-up; T and I match the oracle within the FP64 bar."""
+    g = W.Geometry(2, 6, 4, 1, 10e-9, 10e-9, 10e-9)
+    W.uniform_walls(g, [W.BC_ISOTHERMAL, W.BC_ISOTHERMAL, W.BC_SPECULAR, W.BC_SPECULAR], [340.0, 290.0, 0.0, 0.0])
+    wl = W.Workload("few bands", [g], W.Dirs("inplane", n_inplane=8), W.make_bands(nb_split[0], nb_split[1], 46),
+                    2e-12, 3, 3)
+    assert wl.bands.nb == sum(nb_split)
+    T0 = W.random_temperatures(g.ncells, 47, 280.0, 340.0)
+    s = bte.Solver(wl, T_init=[T0])
+    rc, st = s.step(nsteps=3, ninner=3)
+    assert rc >= 0 and st["nonfinite"] == 0
+    assert st["solve_evals"] > 0                 # the fix-up ran
+    p = O.Problem(g, O.dirs_for(wl.dirs), wl.bands)
+    ost = p.init_state(T0)
+    p.run(ost, wl.dt, 3, 3)
+    for which, key in ((bte.BTE_T_LATTICE, "TL"), (bte.BTE_T_PSEUDO, "Tp")):
+        assert np.max(np.abs(s.T(0, which) - ost[key]) / ost[key]) <= 1e-12, key
+    assert np.max(np.abs(s.intensity(0) - ost["I"]) / np.abs(ost["I"])) <= 1e-11
+    s.close()
