@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
         int ji = 0;
         unsigned sbi = rb0;
         const unsigned long long keep = l2_evict_last(), once = l2_evict_first();
-        auto issue = [&]() {
-          if (ji < nsteps) {
+        auto issue = [&](auto checked) {
+          if (!decltype(checked)::value || ji < nsteps) {
             const int d = dg + ji * dstep;
             cp_async_l2(sbi, pin, once);
             if constexpr (kInt) {
@@ -213,12 +213,11 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
           sbi = (ji % kStages == 0) ? rb0 : sbi + sstr;
         };
 #pragma unroll
-        for (int j = 0; j < kStages - 1; ++j) issue();
+        for (int j = 0; j < kStages - 1; ++j) issue(std::true_type{});
         double* pout = c.out + (long long)dg * nbp;
         double* pbout = BM == 1 ? c.bout + (long long)dg * nbp : nullptr;
         unsigned sb = rb0;
-        for (int j = 0; j < nsteps; ++j) {
-          issue();
+        auto step = [&](int j) {
           cp_async_wait<kStages - 1>();
           const int d = dg + j * dstep;
           const DirFF& e = dsm[d];
@@ -266,6 +265,19 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
           }
           ff::acc(Sff, rf);
           sb = ((j + 1) % kStages == 0) ? rb0 : sb + sstr;
+        };
+        // Every step but the last kStages - 1 stages a later direction (no
+        // bounds test); those last ones commit an empty group, so that the
+        // wait above still finds its own group complete.
+        const int nmain = nsteps - (kStages - 1);
+        int j = 0;
+        for (; j < nmain; ++j) {
+          issue(std::false_type{});
+          step(j);
+        }
+        for (; j < nsteps; ++j) {
+          cp_async_commit();
+          step(j);
         }
       };
       if (c.wall == 0) run(std::true_type{});
