@@ -58,8 +58,9 @@ KERNEL_SRCS = [os.path.join(ROOT, "paper_2305_19400_gb300", "csrc", f) for f in 
 # Algorithmic bytes of one implicit update: I^n (or B) read, I^k read once, I^{k+1} written.
 BYTES_PER_UPDATE_FP64 = 24
 # Work of the dominant kernel (the double-float sweep of inner iterations 2..n-1,
-# 2-D): per lane step of two bands, 3 products of 4 packed ops, 3 accumulations
-# of 8, a normalisation of 3 and the direction sum's accumulation of 8 = 47
+# 2-D): per lane step of two bands, 3 products of 4 packed ops (c_x u_x, c_y u_y,
+# and R times the sum), 3 pair sums of 8 (the two products, the source term,
+# B), a normalisation of 3 and the direction sum's accumulation of 8 = 47
 # packed f32x2 instructions for 2 updates, i.e. 47 FP32 lane operations per
 # update; counted against the measured packed-FMA rate in lane operations.
 FP32_LANE_OPS_PER_UPDATE_FF_2D = 47

@@ -93,8 +93,7 @@ struct bte_ctx {
   // FP64: tables of the factored double-float sweep (bte_sweep_ff.cuh)
   void* coef_R = nullptr;     // [cls][nd][nbp] R pairs
   float* dirc_ff = nullptr;   // [cls][nd][3][2]
-  float* band_ff = nullptr;   // [2][nbp] v_b, beta_b pairs
-  float rdt_ff[2] = {0.0f, 0.0f};
+  float* band_ff = nullptr;   // [2][nbp] 1/(v_b dt), beta_b/v_b pairs
   double *J = nullptr, *Teval = nullptr, *I0ref = nullptr, *scratch_pack = nullptr;
   double* Msum = nullptr;     // [cell][3] the T_p model's sums sum_b a_p,b J_k,b
   double* I0ref_o = nullptr;  // I0_b(T_ref) of the stored bands (aliases I0ref unless a band range is set)
@@ -486,7 +485,7 @@ int ensure_coef(bte_ctx* h, double dt, int scheme) {
         const double delta[3] = {std::get<1>(h->cls_key[c]), std::get<2>(h->cls_key[c]), std::get<3>(h->cls_key[c])};
         build_ff_factored(std::get<0>(h->cls_key[c]), delta, h->nd, h->S.data(), h->w.data(), h->nb, h->nbp,
                           h->vg.data() + h->band0, h->beta.data() + h->band0, dt, h->R_host.data() + c * 2 * plane,
-                          h->dirc_host.data() + c * 6 * (size_t)h->nd, h->band_host.data(), h->rdt_ff);
+                          h->dirc_host.data() + c * 6 * (size_t)h->nd, h->band_host.data());
       }
     CUDA_TRY(h, cudaMemcpyAsync(h->coef_R, h->R_host.data(), h->R_host.size() * 4, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(h->dirc_ff, h->dirc_host.data(), h->dirc_host.size() * 4, cudaMemcpyHostToDevice, h->stream));
@@ -575,8 +574,6 @@ SweepArgs sweep_args(bte_ctx* h) {
   a.coef_R = h->coef_R;
   a.dirc_ff = h->dirc_ff;
   a.band_ff = h->band_ff;
-  a.rdt_h = h->rdt_ff[0];
-  a.rdt_l = h->rdt_ff[1];
   a.dirs = h->dirs_d;
   a.wdir = h->wdir;
   a.wdir32 = h->wdir32;

@@ -118,10 +118,9 @@ struct SweepArgs {
                             // are written as ff; B is always ff)
   // FP64 double-float sweep with factored coefficients (bte_sweep_ff.cuh), tables
   // in the double-float pair layout of bte_ff.cuh (h_b, h_b+1, l_b, l_b+1 per two bands):
-  const void* coef_R;       // [cls][nd][nbp] R = 1/(1/dt + beta_b + v_b sum_ax c_ax,d)
-  const float* band_ff;     // [2][nbp] v_b, beta_b of the stored bands
+  const void* coef_R;       // [cls][nd][nbp] R = 1/(1/(v_b dt) + beta_b/v_b + sum_ax c_ax,d)
+  const float* band_ff;     // [2][nbp] 1/(v_b dt), beta_b/v_b of the stored bands (0 on padding)
   const float* dirc_ff;     // [cls][nd][3][2] c_ax,d as (h, l)
-  float rdt_h, rdt_l;       // 1/dt as a double-float pair
   const void* coef;         // FP64: [cls][5][nd][nbp] A_n, A_x, A_y, A_z, A_s;
                             // reduced: [cls][2][nd][nbp] float P, Q with
                             // I' = P I^n + Q (v_b sum_ax c_ax I_up + beta_b dI0)

@@ -2,21 +2,25 @@
 // with factored coefficients (sm_103a).
 //
 // The implicit point-Jacobi update of Sec. 3.1 (Eq. 5 with backward Euler),
-//   I^{k+1} = R (I^n/dt + v_b sum_ax c_ax,d I_up,ax^k + beta_b I0_b^k),
-//   R = 1 / (1/dt + beta_b + v_b sum_ax c_ax,d),  c_ax,d = |S_d,ax| / (w_d Delta_ax),
-// is evaluated as B + R (v_b sum_ax c_ax u_ax + beta_b I0) with B = (R/dt) I^n
-// kept across the inner iterations of a step (BM 1 forms and stores B, BM 2
-// reads it, BM 0, a step of one inner iteration, forms it only), in
-// double-float arithmetic on
-// the FP32 pipe (bte_ff.cuh): c_ax per direction sits in a shared table, v_b
-// and beta_b of the lane's two bands in registers, beta_b I0_b per cell in
-// registers, and only R per (direction, band) is read per step.  A step
-// therefore stages four 16-byte operands (B or I^n, the upwind value per axis
-// in 2-D, R) instead of the six of the five-coefficient form: with a 3-stage
-// ring about 63 KB of shared memory per 224-thread CTA in 2-D, so three CTAs
-// can share an SM (the autotuner picks two or three).  The tables come from the host in double-float form with R
-// chosen so that R (1/dt + beta_b + v_b sum c_ax) = 1 holds for the table
-// values to double-double accuracy, which keeps a uniform equilibrium in place.
+//   I^{k+1} = (I^n/dt + v_b sum_ax c_ax,d I_up,ax^k + beta_b I0_b^k) / (1/dt + beta_b + v_b sum_ax c_ax,d),
+//   c_ax,d = |S_d,ax| / (w_d Delta_ax),
+// is divided through by v_b (> 0 on every real band) and evaluated as
+//   B + R (sum_ax c_ax u_ax + (beta_b / v_b) I0),  R = 1 / (1/(v_b dt) + beta_b/v_b + sum_ax c_ax,d),
+// with B = (1/(v_b dt)) R I^n kept across the inner iterations of a step (BM 1
+// forms and stores B, BM 2 reads it, BM 0, a step of one inner iteration,
+// forms it only), in double-float arithmetic on the FP32 pipe (bte_ff.cuh):
+// c_ax per direction sits in a shared table, 1/(v_b dt) and beta_b/v_b of the
+// lane's two bands and (beta_b/v_b) I0_b per cell in registers, and only R per
+// (direction, band) is read per step: three products and three pair sums per
+// update in 2-D.  A step therefore stages four 16-byte operands (B or I^n, the
+// upwind value per axis in 2-D, R) instead of the six of the five-coefficient
+// form.  Shared memory per CTA is the 25.6 KB direction table of 400
+// directions, the ring and the epilogue's scratch: 58 KB with the driver's
+// reserve for a 112-thread CTA in 2-D, four of which share an SM, as many as
+// its registers allow.  The tables come from the host in double-float form
+// with R chosen so that R (1/(v_b dt) + beta_b/v_b + sum c_ax) = 1 holds for
+// the table values to double-double accuracy, which keeps a uniform
+// equilibrium in place.
 //
 // Work layout, staging, walls, direction sums and the item epilogue are those
 // of sweep_kernel (bte_sweep.cuh); FF has the meaning described there.
@@ -115,10 +119,9 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
   if (threadIdx.x == 0) { cnt_solves = 0; cnt_bad = 0; cur_cls = -1; }
   const int wid = threadIdx.x >> 5, wl = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
-  // v_b and beta_b of the lane's two bands, 1/dt
-  const ff::P2 v2 = ff::ldg(a.band_ff + 2 * b0);
-  const ff::P2 beta2 = ff::ldg(a.band_ff + 2 * (nbp + b0));
-  const ff::P2 rdt2{ff::pack(a.rdt_h, a.rdt_h), ff::pack(a.rdt_l, a.rdt_l)};
+  // 1/(v_b dt) and beta_b/v_b of the lane's two bands
+  const ff::P2 rdtv2 = ff::ldg(a.band_ff + 2 * b0);
+  const ff::P2 betav2 = ff::ldg(a.band_ff + 2 * (nbp + b0));
   __syncthreads();
 
   for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
@@ -152,9 +155,9 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
     double G[V] = {0.0, 0.0};
 
     if (active) {
-      // beta_b I0_b of the cell, constant over its directions
+      // (beta_b / v_b) I0_b of the cell, constant over its directions
       const ff::P2 srcb =
-          ff::norm(ff::mul(beta2, ff::from_doubles(a.I0cell[P * nbp + b0], a.I0cell[P * nbp + b0 + 1])));
+          ff::norm(ff::mul(betav2, ff::from_doubles(a.I0cell[P * nbp + b0], a.I0cell[P * nbp + b0 + 1])));
       CellAddr<double> c;
       c.in = In + P * row + b0;
       c.ik = Ik + P * row + b0;
@@ -240,13 +243,13 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
             else t = ff::add(t, pr);
           }
           const ff::P2 Rv = ff::lds(sb + (1 + DIM) * ostr);
-          const ff::P2 p = ff::mul(Rv, ff::add(ff::mul(v2, t), srcb));
+          const ff::P2 p = ff::mul(Rv, ff::add(t, srcb));
           ff::P2 rf;
           if constexpr (BM == 2) {
             rf = ff::norm(ff::add(ff::lds(sb), p));
-          } else {  // B = (R / dt) I^n, kept for the later inner iterations when BM == 1
+          } else {  // B = (R / (v_b dt)) I^n, kept for the later inner iterations when BM == 1
             const ff::P2 vin = (FF & 1) ? ff::lds(sb) : ff::lds_doubles(sb);
-            const ff::P2 B = ff::norm(ff::mul(rdt2, ff::mul(Rv, vin)));
+            const ff::P2 B = ff::norm(ff::mul(rdtv2, ff::mul(Rv, vin)));
             if constexpr (BM == 1) {
               if constexpr ((FF & 2) != 0) ff::st_stream(pbout, B);
               else ff::st_stream_doubles(pbout, B);

@@ -213,25 +213,20 @@ void ff_of_dd(DD x, float& h, float& l) {
 }  // namespace
 
 void build_ff_factored(int dim, const double delta[3], int nd, const double* S, const double* w, int nb, int nbp,
-                       const double* vg, const double* beta, double dt, float* R, float* dirc, float* band, float* rdt) {
-  float rh, rl;
-  ff_of(1.0 / dt, rh, rl);
-  rdt[0] = rh;
-  rdt[1] = rl;
-  const DD rdt_dd = dd_of(rh, rl);
+                       const double* vg, const double* beta, double dt, float* R, float* dirc, float* band) {
   for (size_t e = 0; e < 4 * (size_t)nbp; ++e) band[e] = 0.0f;
-  std::vector<DD> v_dd(nb), b_dd(nb);
+  std::vector<DD> rv_dd(nb), bv_dd(nb);
   for (int b = 0; b < nb; ++b) {  // pair layout: element b of an [nbp] array at float (b - b%2)*2 + b%2 (+2 for l)
     float h, l;
     const size_t o = (size_t)(b - (b & 1)) * 2 + (b & 1);
-    ff_of(vg[b], h, l);
+    ff_of(1.0 / (vg[b] * dt), h, l);  // 1 / (v_b dt)
     band[o] = h;
     band[o + 2] = l;
-    v_dd[b] = dd_of(h, l);
-    ff_of(beta[b], h, l);
+    rv_dd[b] = dd_of(h, l);
+    ff_of(beta[b] / vg[b], h, l);  // beta_b / v_b
     band[2 * (size_t)nbp + o] = h;
     band[2 * (size_t)nbp + o + 2] = l;
-    b_dd[b] = dd_of(h, l);
+    bv_dd[b] = dd_of(h, l);
   }
   for (size_t e = 0; e < 2 * (size_t)nd * nbp; ++e) R[e] = 0.0f;
   for (int d = 0; d < nd; ++d) {
@@ -245,7 +240,7 @@ void build_ff_factored(int dim, const double delta[3], int nd, const double* S, 
       csum = dd_add(csum, dd_of(h, l));
     }
     for (int b = 0; b < nb; ++b) {
-      const DD D = dd_add(dd_add(rdt_dd, b_dd[b]), dd_mul(v_dd[b], csum));
+      const DD D = dd_add(dd_add(rv_dd[b], bv_dd[b]), csum);
       float h, l;
       ff_of_dd(dd_recip(D), h, l);
       const size_t o = ((size_t)d * nbp + b - (b & 1)) * 2 + (b & 1);
