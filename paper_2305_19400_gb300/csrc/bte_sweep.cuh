@@ -398,11 +398,11 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
       // interior test (a second copy measured slower there).
       auto run = [&](auto interior_tag) {
       constexpr bool kInterior = decltype(interior_tag)::value;
-      auto issue = [&](int j) {
-        if (j < nsteps) {
+      // stage the operands of step j into the ring slot at shared address sb
+      auto issue = [&](auto checked, int j, const unsigned sb) {
+        if (!decltype(checked)::value || j < nsteps) {
           const int d = dg + j * dstep;
           const int off = d * nbp;
-          const unsigned sb = rb0 + (unsigned)(j % kStages) * sstr;
           cp_async<kVB>(sb, c.in + off);
           if (kInterior || c.wall == 0) {  // interior cell: the upwind rows are the neighbours' (the common case)
             const int up = dsm[d].info.x;
@@ -447,13 +447,11 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
         T::lds(sb + (1 + ax) * ostr, x);
       };
 #pragma unroll
-      for (int j = 0; j < kStages - 1; ++j) issue(j);
-      for (int j = 0; j < nsteps; ++j) {
-        issue(j + kStages - 1);
+      for (int j = 0; j < kStages - 1; ++j) issue(std::true_type{}, j, rb0 + (unsigned)j * sstr);
+      auto step = [&](int j, const unsigned sb) {
         cp_async_wait<kStages - 1>();
         const int d = dg + j * dstep;
         const int off = d * nbp;
-        const unsigned sb = rb0 + (unsigned)(j % kStages) * sstr;
         const int4 di = dsm[d].info;
         A vn[V], ux[V], uy[V], uz[V];
         T::lds(sb, vn);
@@ -585,6 +583,24 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
             nacc = 0;
           }
         }
+      };
+      // Every step but the last kStages - 1 stages a later direction (no bounds
+      // test), step j + kStages - 1 into the slot step j - 1 has just read; the
+      // last steps commit an empty group, so that the wait still finds its own.
+      const int nmain = nsteps - (kStages - 1);
+      const unsigned slast = rb0 + (unsigned)(kStages - 1) * sstr;
+      unsigned sb = rb0, sprev = slast;
+      int j = 0;
+      for (; j < nmain; ++j) {
+        issue(std::false_type{}, j + kStages - 1, sprev);
+        step(j, sb);
+        sprev = sb;
+        sb = sb == slast ? rb0 : sb + sstr;
+      }
+      for (; j < nsteps; ++j) {
+        cp_async_commit();
+        step(j, sb);
+        sb = sb == slast ? rb0 : sb + sstr;
       }
       };
       if constexpr (sizeof(S) == 2) {

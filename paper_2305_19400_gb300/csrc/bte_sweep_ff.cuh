@@ -187,9 +187,9 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
         const double* pik = c.ik + (long long)dg * nbp;
         const double* pR = Rrow + (long long)dg * nbp;
         int ji = 0;
-        unsigned sbi = rb0;
         const unsigned long long keep = l2_evict_last(), once = l2_evict_first();
-        auto issue = [&](auto checked) {
+        // stage the operands of step ji into the ring slot at shared address sbi
+        auto issue = [&](auto checked, const unsigned sbi) {
           if (!decltype(checked)::value || ji < nsteps) {
             const int d = dg + ji * dstep;
             cp_async_l2(sbi, pin, once);
@@ -213,10 +213,9 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
           }
           cp_async_commit();
           ++ji;
-          sbi = (ji % kStages == 0) ? rb0 : sbi + sstr;
         };
 #pragma unroll
-        for (int j = 0; j < kStages - 1; ++j) issue(std::true_type{});
+        for (int j = 0; j < kStages - 1; ++j) issue(std::true_type{}, rb0 + (unsigned)j * sstr);
         double* pout = c.out + (long long)dg * nbp;
         double* pbout = BM == 1 ? c.bout + (long long)dg * nbp : nullptr;
         unsigned sb = rb0;
@@ -267,20 +266,25 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
             wrun = e.wkey;
           }
           ff::acc(Sff, rf);
-          sb = ((j + 1) % kStages == 0) ? rb0 : sb + sstr;
         };
         // Every step but the last kStages - 1 stages a later direction (no
         // bounds test); those last ones commit an empty group, so that the
         // wait above still finds its own group complete.
         const int nmain = nsteps - (kStages - 1);
+        // Step j + kStages - 1 goes into the slot step j - 1 has just read.
+        const unsigned slast = rb0 + (unsigned)(kStages - 1) * sstr;
+        unsigned sprev = slast;
         int j = 0;
         for (; j < nmain; ++j) {
-          issue(std::false_type{});
+          issue(std::false_type{}, sprev);
           step(j);
+          sprev = sb;
+          sb = sb == slast ? rb0 : sb + sstr;
         }
         for (; j < nsteps; ++j) {
           cp_async_commit();
           step(j);
+          sb = sb == slast ? rb0 : sb + sstr;
         }
       };
       if (c.wall == 0) run(std::true_type{});
