@@ -31,7 +31,9 @@
 // DRAM once (adjacent cells, processed together, re-read it from L2).  Each
 // thread copies the operands of its next directions into shared memory with
 // cp.async kStages-1 steps before it uses them.  MINB is the launch-bounds
-// minimum of resident CTAs per SM (a register cap).
+// minimum of resident CTAs per SM (a register cap).  BM: FP64 storage, the
+// inner-iteration form (0 I^n read, 1 B = A_n I^n also stored, 2 B read);
+// reduced modes, the scheme (0 implicit, 3 explicit).
 #pragma once
 #include <type_traits>
 
@@ -291,8 +293,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
     vb[v] = kDev ? (A)a.vb32[b0 + v] : (A)0;
     bb[v] = kDev ? (A)a.bb32[b0 + v] : (A)0;
   }
-  // reduced modes: the scheme's scalars in both halves of a packed pair
-  const bool expl = a.explicit_scheme != 0;
+  // reduced modes: the scheme (BM 3: explicit, BM 0: implicit) and its scalars
+  // in both halves of a packed pair
+  constexpr bool kExpl = kDev && BM == 3;
   const ff::x2 dt2 = ff::pack(a.dt32, a.dt32), ndt2 = ff::pack(-a.dt32, -a.dt32), rdt2 = ff::pack(a.rdt32, a.rdt32),
                one2 = ff::pack(1.0f, 1.0f);
   __syncthreads();
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
             const ff::x2 vb2 = ff::pack(vb[v], vb[v + 1]);
             const ff::x2 rate = ff::fma(vb2, ccw, ff::pack(bb[v], bb[v + 1]));
             ff::x2 Pc, Qc;
-            if (expl) {
+            if constexpr (kExpl) {
               Qc = dt2;
               Pc = ff::fma(ndt2, rate, one2);
             } else {
@@ -670,6 +673,7 @@ cudaError_t launch(int variant, const SweepArgs& a, int dim, int threads, int gr
     if (a.bmode == 2) return launch_bm<S, 2, false>(variant, a, dim, threads, grid, s);
   } else {
     if (a.bmode != 0 || a.ff != 0) return cudaErrorInvalidValue;  // the B form exists for FP64 storage only
+    if (a.explicit_scheme) return launch_bm<S, 3, false>(variant, a, dim, threads, grid, s);
   }
   return launch_bm<S, 0, false>(variant, a, dim, threads, grid, s);
 }
