@@ -140,6 +140,30 @@ struct ItemCtx {
 // barriers): G[v] is this lane's partial G_b = sum_d w_d I_{d,b} over its
 // directions (in the reduced modes without the W I0_b(T_ref) term of their
 // deviation storage, which is added here).
+// Root nearest 0 of F + F1 d + F2 d^2 / 2, the step of the cell's cached
+// temperature model: an FP32 estimate from the stable form
+// -2F / (F1 + sqrt(F1^2 - 2 F F2)) (-F / F1 without a real root), then one
+// Newton step in FP64 with the FP32 reciprocal of the derivative.  The
+// estimate is good to about 1e-7 and the step to about 1e-14 of d (the FP32
+// rounding squared), while an accepted d is below 3e-5 T.  The FP64 pipe of
+// GB300 takes about 76 cycles per warp instruction: this form issues five
+// FP64 operations where a square root and a division take twenty-odd, and its
+// conversions run on the integer pipe (bte_ff.cuh).
+__device__ __forceinline__ double model_step(double F, double F1, double F2) {
+  float f, f1, f2, lo;
+  ff::split(F, f, lo);
+  ff::split(F1, f1, lo);
+  ff::split(F2, f2, lo);
+  const float disc = fmaf(f1, f1, -2.0f * f * f2);
+  const float d0f = (disc >= 0.0f && f1 > 0.0f) ? -2.0f * f / (f1 + sqrtf(disc)) : -f / f1;
+  const double d0 = ff::to_double(d0f, 0.0f);
+  const double q = fma(fma(0.5 * F2, d0, F1), d0, F);
+  float qp;
+  ff::split(fma(F2, d0, F1), qp, lo);
+  const double r = ff::to_double(1.0f / qp, 0.0f);
+  return fma(-q, r, d0);
+}
+
 template <int V, bool kDev>
 __device__ __forceinline__ void item_epilogue(const SweepArgs& a, const ItemCtx& x, const WorkItem& wi,
                                               const DevGeom* gp, const double (&G)[V], unsigned long long& cnt_solves,
@@ -213,8 +237,7 @@ __device__ __forceinline__ void item_epilogue(const SweepArgs& a, const ItemCtx&
           // sums sum_b a_p,b J_k,b, kept with J
           const double Fs = a.Msum[3 * Pc] - Ep, F1s = a.Msum[3 * Pc + 1], F2s = a.Msum[3 * Pc + 2];
           const double Te = a.Teval[Pc];
-          const double disc = F1s * F1s - 2.0 * Fs * F2s;
-          const double delta = (disc >= 0.0 && F1s > 0.0) ? -2.0 * Fs / (F1s + sqrt(disc)) : -Fs / F1s;
+          const double delta = model_step(Fs, F1s, F2s);
           const double Tn = Te + delta;
           if (isfinite(Tn) && fabs(delta) <= a.trust_rel * Tn) {
             if (!a.dry) {
