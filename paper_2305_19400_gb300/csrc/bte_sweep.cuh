@@ -26,7 +26,7 @@
 // T_e).  The model root is accepted inside the trust radius
 // |T - T_e| <= trust_rel T, where the Taylor remainder is below the solve
 // tolerance, and the warp refreshes the cell's I0 from it; other cells go to
-// the fix-up kernel (exact FP64 band quadrature).  Two CTA barriers per item.
+// the fix-up kernel (exact FP64 band quadrature).  Five CTA barriers per item.
 // Memory: I^n is read once, I^{k+1} written once, and each I^k row read from
 // DRAM once (adjacent cells, processed together, re-read it from L2).  Each
 // thread copies the operands of its next directions into shared memory with
@@ -133,7 +133,8 @@ struct Ring {
 struct ItemCtx {
   int team, cpb, slot, dg, lane, lpc, dstep, b0, wid, wl, nwarps, nbp, nbp_all, band0, nbr;
   double* gsm;  // [blockDim.x][V] per-lane band partials
-  double* red;  // [cpb * lpc][2] per-band-vector E_L, E_p sums, then [cpb][4] per-cell scratch
+  double* red;  // [cpb * lpc][2] per-band-vector E_L, E_p sums (may lie inside gsm)
+  double* cst;  // [cpb][4] per-cell scratch (apart from gsm)
 };
 
 // The end of an item of a sweep CTA (every thread calls it; it holds four CTA
@@ -173,16 +174,17 @@ __device__ __forceinline__ void item_epilogue(const SweepArgs& a, const ItemCtx&
   // G_b, then E_L = sum_b G_b / v_b and E_p = sum_b beta_b G_b / v_b per band
   // vector.  One warp per cell adds the band vectors (shuffle tree); one warp
   // then solves every cell's model (lanes over cells), and all threads refresh
-  // the accepted cells' I0.  Four barriers per item: every read of gsm
-  // precedes the second, every read of red the third, and every read of the
-  // per-cell scratch the next item's second.
+  // the accepted cells' I0.  Five barriers per item: every read of gsm
+  // precedes the second (so the band-vector sums may overwrite it), every
+  // read of red the fourth, and every read of the per-cell scratch the next
+  // item's first.
   double* gb = x.gsm;
   double* rb = x.red;
 #pragma unroll
   for (int v = 0; v < V; ++v) gb[(size_t)threadIdx.x * V + v] = G[v];
   __syncthreads();
+  double eL = 0.0, ep = 0.0;
   if (x.dg == 0) {
-    double eL = 0.0, ep = 0.0;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       double Gb = kDev ? a.Wtot * a.I0ref[x.b0 + v] : 0.0;
@@ -191,12 +193,15 @@ __device__ __forceinline__ void item_epilogue(const SweepArgs& a, const ItemCtx&
       eL += e;
       ep = fma(a.th.beta[x.b0 + v], e, ep);
     }
+  }
+  __syncthreads();
+  if (x.dg == 0) {
     double* r2 = rb + 2 * (size_t)(x.slot * x.lpc + x.lane);
     r2[0] = eL;
     r2[1] = ep;
   }
   __syncthreads();
-  double* cst = rb + 2 * (size_t)x.cpb * x.lpc;  // [cpb][4]: E_L, E_p, model step, accepted
+  double* cst = x.cst;  // [cpb][4]: E_L, E_p, model step, accepted
   for (int cs = x.wid; x.wid < x.nwarps && cs < wi.cell_count; cs += x.nwarps) {  // warp per cell: E_L, E_p
     double EL = 0.0, Ep = 0.0;
     for (int l = x.wl; l < x.lpc; l += 32) {
@@ -647,7 +652,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs a) {
     }
 
     item_epilogue<V, kDev>(a, ItemCtx{team, cpb, slot, dg, lane, lpc, dstep, b0, wid, wl, nwarps, nbp, nbp_all, band0,
-                                      nbr, gsm, red},
+                                      nbr, gsm, red, red + 2 * (size_t)cpb * lpc},
                            wi, gp, G, cnt_solves, cnt_bad);
   }
   __syncthreads();

@@ -39,14 +39,15 @@ using sweep::cp_async_commit;
 using sweep::cp_async_wait;
 using sweep::ItemCtx;
 
-// Shared per-direction table of the current cell-size class (64 bytes): the
-// coefficients already packed for the two-band operations.
+// Shared per-direction table of the current cell-size class (16 + 16 DIM
+// bytes): the coefficients already packed for the two-band operations.
+template <int DIM>
 struct DirFF {
   int up;          // bit a set: the upwind neighbour lies on the low side along axis a
   unsigned wkey;   // bits of w32 ^ bits of wlo: equal weights, equal keys (the runs of the direction sums)
   float w32, wlo;  // w_d as a double-float pair
-  ff::x2 ch[3];    // c_ax,d high part in both halves, for ax = x, y, z
-  ff::x2 cl[3];    // c_ax,d low part in both halves
+  ff::x2 ch[DIM];  // c_ax,d high part in both halves, for the axes in use
+  ff::x2 cl[DIM];  // c_ax,d low part in both halves
 };
 
 // L2 cache policies of the staged copies: the R table (one row per
@@ -69,12 +70,13 @@ __device__ __forceinline__ void cp_async_l2(unsigned smem, const void* g, unsign
                : "memory");
 }
 
-// Ring depth: 4 stages when two CTAs share an SM, 3 when three do (the
-// shared memory of three 224-thread CTAs).
+// Ring depth: 5 stages in 2-D and 4 in 3-D under the two-CTA register cap
+// (four 112-thread CTAs of 58 KB share an SM in 2-D), 3 when three 224-thread
+// CTAs share one.
 template <int DIM, int MINB>
 struct RingFF {
   static constexpr int kOps = 2 + DIM;  // B or I^n, upwind per axis, R
-  static constexpr int kStages = MINB >= 3 ? 3 : 4;
+  static constexpr int kStages = MINB >= 3 ? 3 : (DIM == 2 ? 5 : 4);
 };
 
 // Threads per CTA the register cap is computed for: three resident CTAs are
@@ -106,11 +108,12 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
   const int cpb = blockDim.x / team;
   const int slot = threadIdx.x / team, tl = threadIdx.x - slot * team;
   const int dg = tl / lpc, lane = tl - dg * lpc;
-  DirFF* dsm = reinterpret_cast<DirFF*>(sm);
+  DirFF<DIM>* dsm = reinterpret_cast<DirFF<DIM>*>(sm);
   double* gsm = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(dsm + nd) + 15) & ~static_cast<uintptr_t>(15));
-  double* red = gsm + (size_t)V * blockDim.x;
+  double* red = gsm;                            // the band-vector sums overwrite the read partials
+  double* cst = gsm + (size_t)V * blockDim.x;   // [cpb][4] per-cell scratch
   char* ring = reinterpret_cast<char*>(
-      (reinterpret_cast<uintptr_t>(red + 2 * (size_t)cpb * lpc + 4 * (size_t)cpb) + 15) & ~static_cast<uintptr_t>(15));
+      (reinterpret_cast<uintptr_t>(cst + 4 * (size_t)cpb) + 15) & ~static_cast<uintptr_t>(15));
   const double* __restrict__ In = reinterpret_cast<const double*>(a.In);
   const double* __restrict__ Ik = reinterpret_cast<const double*>(a.Ik);
   double* __restrict__ Io = reinterpret_cast<double*>(a.Iout);
@@ -132,14 +135,14 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
     if (gcls != cur_cls) {  // (block-uniform) direction table of this cell-size class
       __syncthreads();
       for (int d = threadIdx.x; d < nd; d += blockDim.x) {
-        DirFF e;
+        DirFF<DIM> e;
         e.up = a.dirs[d].up;
         e.w32 = a.wdir32[d];
         e.wlo = (float)(a.wdir[d] - (double)e.w32);
         e.wkey = __float_as_uint(e.w32) ^ __float_as_uint(e.wlo);
         const float* cc = a.dirc_ff + ((size_t)gcls * nd + d) * 6;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < DIM; ++k) {
           e.ch[k] = ff::pack(cc[2 * k], cc[2 * k]);
           e.cl[k] = ff::pack(cc[2 * k + 1], cc[2 * k + 1]);
         }
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
         auto step = [&](int j) {
           cp_async_wait<kStages - 1>();
           const int d = dg + j * dstep;
-          const DirFF& e = dsm[d];
+          const DirFF<DIM>& e = dsm[d];
           // sum_ax c_ax u_ax; an upwind operand is an ff pair unless it is I^k in
           // doubles or an isothermal wall ghost (doubles in every variant)
           ff::P2 t;
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
       ff::to_doubles(ff::norm(Gff), G[0], G[1]);
     }
     sweep::item_epilogue<V, false>(a, ItemCtx{team, cpb, slot, dg, lane, lpc, dstep, b0, wid, wl, nwarps, nbp,
-                                              nbp_all, band0, nbr, gsm, red},
+                                              nbp_all, band0, nbr, gsm, red, cst},
                                    wi, gp, G, cnt_solves, cnt_bad);
   }
   __syncthreads();
@@ -307,8 +310,8 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
 template <int DIM, int MINB, int BM, int FF>
 cudaError_t launch_shape(const SweepArgs& a, int threads, int grid, cudaStream_t s) {
   const int team = a.lpc * a.dteam, cpb = threads / team;
-  const size_t smem = sizeof(DirFF) * (size_t)a.nd + 16 + 2 * (size_t)threads * sizeof(double) +
-                      (2 * (size_t)cpb * a.lpc + 4 * (size_t)cpb) * sizeof(double) + 16 +
+  const size_t smem = sizeof(DirFF<DIM>) * (size_t)a.nd + 16 + 2 * (size_t)threads * sizeof(double) +
+                      4 * (size_t)cpb * sizeof(double) + 16 +
                       (size_t)RingFF<DIM, MINB>::kStages * RingFF<DIM, MINB>::kOps * threads * 16;
   const cudaError_t e = raise_dynamic_smem((const void*)sweep_ff_kernel<DIM, MINB, BM, FF>, smem);
   if (e != cudaSuccess) return e;
