@@ -14,10 +14,10 @@
 // (direction, band) is read per step: three products and three pair sums per
 // update in 2-D.  A step therefore stages four 16-byte operands (B or I^n, the
 // upwind value per axis in 2-D, R) instead of the six of the five-coefficient
-// form.  Shared memory per CTA is the 25.6 KB direction table of 400
-// directions, the ring and the epilogue's scratch: 58 KB with the driver's
-// reserve for a 112-thread CTA in 2-D, four of which share an SM, as many as
-// its registers allow.  The tables come from the host in double-float form
+// form.  Shared memory per CTA is the direction table (19.2 KB for 400
+// directions in 2-D, 48 bytes a direction), a 5-stage ring (35 KB) and the
+// epilogue's scratch: 58 KB with the driver's reserve for a 112-thread CTA
+// in 2-D, four of which share an SM, as many as its registers allow.  The tables come from the host in double-float form
 // with R chosen so that R (1/(v_b dt) + beta_b/v_b + sum c_ax) = 1 holds for
 // the table values to double-double accuracy, which keeps a uniform
 // equilibrium in place.
