@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(MaxThreadsFF<MINB>::value) __maxnreg__(MaxRegF
 #pragma unroll
         for (int j = 0; j < kStages - 1; ++j) issue(std::true_type{}, rb0 + (unsigned)j * sstr);
         double* pout = c.out + (long long)dg * nbp;
-        double* pbout = BM == 1 ? c.bout + (long long)dg * nbp : nullptr;
+        [[maybe_unused]] double* pbout = BM == 1 ? c.bout + (long long)dg * nbp : nullptr;  // BM 1 only
         unsigned sb = rb0;
         auto step = [&](int j) {
           cp_async_wait<kStages - 1>();
