@@ -118,7 +118,7 @@ __device__ inline SolveResult exact_solve_warp(const ThermoTables& th, double Ep
 }
 
 // Shared memory (doubles) of exact_solve_cluster, per CTA.
-__host__ __device__ constexpr int kCtaSolvePairs = 1024;  // (band, node) pairs per chunk
+constexpr int kCtaSolvePairs = 1024;  // (band, node) pairs per chunk
 __host__ __device__ inline int cta_solve_smem_doubles(int nbp) { return 3 * kCtaSolvePairs + 6 * nbp + 4; }
 
 // The same solve by a thread-block cluster, bit for bit the warp form's
